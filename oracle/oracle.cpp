@@ -1,0 +1,851 @@
+// oracle.cpp -- plain FP64 CPU oracle for delta-tracking walk on spheres.
+//
+// TEST INFRASTRUCTURE ONLY: loaded by the test suite, the smoke check and the
+// CPU-baseline leg of the benchmark.  The product library never includes,
+// links or calls it, and it shares no source with the CUDA path.
+//
+// Every function follows one passage of Sawhney, Seyb, Jarosz, Crane,
+// "Grid-Free Monte Carlo for PDEs with Spatially Varying Coefficients"
+// (SIGGRAPH 2022); the passage is named above the function.  Speed is not a
+// goal: closed forms are evaluated as printed, with a power series only where
+// the printed form cancels catastrophically in double precision, and roots
+// are found by safeguarded Newton iteration run to convergence.
+#include "oracle.h"
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <omp.h>
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+const double kEulerGamma = 0.57721566490153286061;
+
+// ---------------------------------------------------------------------------
+// Bessel functions: the C++17 special functions of libstdc++ (library step).
+// ---------------------------------------------------------------------------
+double bI0(double x) { return std::cyl_bessel_i(0.0, x); }
+double bI1(double x) { return std::cyl_bessel_i(1.0, x); }
+double bK0(double x) { return std::cyl_bessel_k(0.0, x); }
+double bK1(double x) { return std::cyl_bessel_k(1.0, x); }
+
+// ---------------------------------------------------------------------------
+// Supplemental Sec. 1.1, 2D.  Small-argument forms from the power series of
+// I0 and K0 (DLMF 10.25.2 and 10.31.2): with b_k = (a^2/4)^k / (k!)^2 and
+// H_k the harmonic numbers,
+//   I0(a) = sum_k b_k,   K0(a) = -(ln(a/2) + gamma_E) I0(a) + S(a),
+//   S(a) = sum_{k>=1} H_k b_k.
+// Substituting into Q2D(a rho) = K0(a rho) - K0(a) I0(a rho) / I0(a) the
+// logarithms of a cancel, leaving
+//   Q2D(a rho) = -ln(rho) I0(a rho) + S(a rho) - beta I0(a rho),
+//   beta = S(a) / I0(a),
+// and the radial integral N(rho) = a^2 int_0^rho t Q2D(a t) dt term by term:
+//   N(rho)/a^2 = sum_k b_k rho^(2k+2) [1/(2k+2)^2 - ln(rho)/(2k+2)
+//                                       + (H_k - beta)/(2k+2)].
+// ---------------------------------------------------------------------------
+struct Series2D {
+  double b[40];
+  double H[40];
+  int n;
+  double beta;
+};
+
+void series2d_init(double a, Series2D* s) {
+  double q = a * a / 4.0;
+  double bk = 1.0, Hk = 0.0, I0 = 0.0, S = 0.0;
+  int k = 0;
+  for (; k < 40; ++k) {
+    if (k > 0) {
+      bk *= q / ((double)k * (double)k);
+      Hk += 1.0 / k;
+    }
+    s->b[k] = bk;
+    s->H[k] = Hk;
+    I0 += bk;
+    S += Hk * bk;
+    if (k > 2 && bk < 1e-20 * I0) { ++k; break; }
+  }
+  s->n = k;
+  s->beta = S / I0;
+}
+
+// N(rho) / a^2 from the series
+double series2d_N(const Series2D& s, double rho) {
+  if (rho <= 0.0) return 0.0;
+  double lr = std::log(rho);
+  double r2 = rho * rho, rp = r2, acc = 0.0;
+  for (int k = 0; k < s.n; ++k) {
+    double m = 2.0 * k + 2.0;
+    acc += s.b[k] * rp * (1.0 / (m * m) - lr / m + (s.H[k] - s.beta) / m);
+    rp *= r2;
+  }
+  return acc;
+}
+
+// Q2D(a rho) from the series
+double series2d_Q(const Series2D& s, double rho) {
+  double lr = std::log(rho);
+  double r2 = rho * rho, rp = 1.0, I0 = 0.0, S = 0.0;
+  for (int k = 0; k < s.n; ++k) {
+    I0 += s.b[k] * rp;
+    S += s.H[k] * s.b[k] * rp;
+    rp *= r2;
+  }
+  return -lr * I0 + S - s.beta * I0;
+}
+
+// 1 - t K1(t) for t < 2, from DLMF 10.31.1 (n = 1), no cancellation:
+//   1 - t K1(t) = -t ln(t/2) I1(t)
+//                 + (t^2/4) sum_k (psi(k+1) + psi(k+2)) (t^2/4)^k / (k! (k+1)!)
+double one_minus_tK1_small(double t) {
+  double q = t * t / 4.0;
+  double term = 1.0;  // (t^2/4)^k / (k! (k+1)!)
+  double Hk = 0.0;    // H_k
+  double acc = 0.0;
+  for (int k = 0; k < 40; ++k) {
+    if (k > 0) {
+      term *= q / ((double)k * (double)(k + 1));
+      Hk += 1.0 / k;
+    }
+    double psi1 = -kEulerGamma + Hk;
+    double psi2 = -kEulerGamma + Hk + 1.0 / (k + 1);
+    acc += (psi1 + psi2) * term;
+    if (k > 2 && std::fabs(term) < 1e-22) break;
+  }
+  return -t * std::log(t / 2.0) * bI1(t) + q * acc;
+}
+
+// ---------------------------------------------------------------------------
+// Supplemental Sec. 1.1, 3D.  N(rho) = a^2 int_0^rho t sinh(a(1-t)) dt with
+//   N(rho) = sinh a - sinh(a(1-rho)) - a rho cosh(a(1-rho)),
+//   D = N(1) = sinh a - a.
+// For a < 1 the Taylor series of sinh in a is integrated term by term:
+//   N(rho) = a^3 sum_j a^(2j)/(2j+1)! J_{2j+1}(rho),
+//   J_m(rho) = int_0^rho t (1-t)^m dt = [1 - (1-rho)^(m+1)(1+(m+1)rho)] / ((m+1)(m+2)).
+// For a >= 1 both N and D are multiplied by 2 e^{-a} (no overflow):
+//   N~(rho) = h(-a rho) - e^{-2a} h(a rho),  h(x) = 1 - e^x (1 - x),
+//   D~ = 1 - 2 a e^{-a} - e^{-2a}.
+// ---------------------------------------------------------------------------
+double J_m(int m, double rho) {
+  if (rho < 0.25) {
+    // sum_i C(m,i) (-1)^i rho^(i+2) / (i+2)
+    double acc = 0.0, c = 1.0, rp = rho * rho;
+    for (int i = 0; i <= m; ++i) {
+      acc += ((i & 1) ? -c : c) * rp / (i + 2);
+      c = c * (m - i) / (i + 1);
+      rp *= rho;
+    }
+    return acc;
+  }
+  double om = 1.0 - rho;
+  return (1.0 - std::pow(om, m + 1) * (1.0 + (m + 1) * rho)) / ((m + 1.0) * (m + 2.0));
+}
+
+// h(x) = 1 - e^x (1 - x) = sum_{m>=2} x^m (m-1)/m!  (h(-x) = 1 - e^{-x}(1+x))
+double h_fn(double x) {
+  if (std::fabs(x) < 0.5) {
+    double acc = 0.0, term = x;  // x^m / m!
+    for (int m = 2; m < 30; ++m) {
+      term *= x / m;
+      acc += term * (m - 1);
+      if (std::fabs(term) < 1e-20) break;
+    }
+    return acc;
+  }
+  return 1.0 - std::exp(x) * (1.0 - x);
+}
+
+// e^{-2a} h(a rho), written without overflow
+double e2a_h(double a, double rho) {
+  double x = a * rho;
+  if (x < 0.5) return std::exp(-2.0 * a) * h_fn(x);
+  return std::exp(-2.0 * a) - std::exp(-a * (2.0 - rho)) * (1.0 - x);
+}
+
+double cdf3(double a, double rho) {
+  if (rho <= 0.0) return 0.0;
+  if (rho >= 1.0) return 1.0;
+  if (a < 1.0) {
+    double num = 0.0, den = 0.0, c = 1.0;  // c = a^(2j)/(2j+1)!
+    for (int j = 0; j < 30; ++j) {
+      int m = 2 * j + 1;
+      num += c * J_m(m, rho);
+      den += c / ((m + 1.0) * (m + 2.0));
+      c *= a * a / ((2.0 * j + 2.0) * (2.0 * j + 3.0));
+      if (c < 1e-22) break;
+    }
+    return num / den;
+  }
+  double num = h_fn(-a * rho) - e2a_h(a, rho);
+  double den = 1.0 - 2.0 * a * std::exp(-a) - std::exp(-2.0 * a);
+  return num / den;
+}
+
+// dF/drho
+double pdf3(double a, double rho) {
+  if (rho <= 0.0 || rho >= 1.0) return 0.0;
+  if (a < 1.0) {
+    double num = 0.0, den = 0.0, c = 1.0;
+    for (int j = 0; j < 30; ++j) {
+      int m = 2 * j + 1;
+      num += c * rho * std::pow(1.0 - rho, m);
+      den += c / ((m + 1.0) * (m + 2.0));
+      c *= a * a / ((2.0 * j + 2.0) * (2.0 * j + 3.0));
+      if (c < 1e-22) break;
+    }
+    return num / den;
+  }
+  double num = a * a * rho * (std::exp(-a * rho) - std::exp(-a * (2.0 - rho)));
+  double den = 1.0 - 2.0 * a * std::exp(-a) - std::exp(-2.0 * a);
+  return num / den;
+}
+
+// 2D radial CDF: F = N(rho) / N(1),
+//   N(rho) = 1 - t K1(t) - (K0(a)/I0(a)) t I1(t),  t = a rho,  N(1) = 1 - 1/I0(a)
+double cdf2(double a, double rho) {
+  if (rho <= 0.0) return 0.0;
+  if (rho >= 1.0) return 1.0;
+  if (a <= 2.0) {
+    Series2D s;
+    series2d_init(a, &s);
+    return series2d_N(s, rho) / series2d_N(s, 1.0);
+  }
+  double t = a * rho;
+  double c = bK0(a) / bI0(a);
+  double first = (t < 2.0) ? one_minus_tK1_small(t) : 1.0 - t * bK1(t);
+  double num = first - c * t * bI1(t);
+  double den = 1.0 - 1.0 / bI0(a);
+  return num / den;
+}
+
+double pdf2(double a, double rho) {
+  if (rho <= 0.0 || rho >= 1.0) return 0.0;
+  if (a <= 2.0) {
+    Series2D s;
+    series2d_init(a, &s);
+    return rho * series2d_Q(s, rho) / series2d_N(s, 1.0);
+  }
+  double t = a * rho;
+  double c = bK0(a) / bI0(a);
+  double den = 1.0 - 1.0 / bI0(a);
+  return a * a * rho * (bK0(t) - c * bI0(t)) / den;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11.  Round: two 32x32->64 products of counter words 0 and 2
+// with the round multipliers, outputs (hi1^c1^k0, lo1, hi0^c3^k1, lo0); the
+// key is bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+void philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+double uniform01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+// ---------------------------------------------------------------------------
+// Fields: sum of separable terms, grids, manufactured source.
+// ---------------------------------------------------------------------------
+void atom(int type, double k, double phi, double x, double* h, double* h1, double* h2) {
+  double t = k * x + phi;
+  switch (type) {
+    case ORC_ONE: *h = 1.0; *h1 = 0.0; *h2 = 0.0; break;
+    case ORC_SIN: *h = std::sin(t); *h1 = k * std::cos(t); *h2 = -k * k * std::sin(t); break;
+    case ORC_COS: *h = std::cos(t); *h1 = -k * std::sin(t); *h2 = -k * k * std::cos(t); break;
+    case ORC_EXP: *h = std::exp(t); *h1 = k * std::exp(t); *h2 = k * k * std::exp(t); break;
+    case ORC_SINH: *h = std::sinh(t); *h1 = k * std::cosh(t); *h2 = k * k * std::sinh(t); break;
+    case ORC_COSH: *h = std::cosh(t); *h1 = k * std::sinh(t); *h2 = k * k * std::cosh(t); break;
+    case ORC_LIN: *h = t; *h1 = k; *h2 = 0.0; break;
+    case ORC_QUAD: *h = t * t; *h1 = 2.0 * k * t; *h2 = 2.0 * k * k; break;
+    default: *h = NAN; *h1 = NAN; *h2 = NAN; break;
+  }
+}
+
+void sst_eval(int dim, const orc_field* fl, const double* x, double* v, double* g, double* lap) {
+  *v = 0.0;
+  *lap = 0.0;
+  for (int i = 0; i < 3; ++i) g[i] = 0.0;
+  for (int n = 0; n < fl->nterms; ++n) {
+    const orc_term& tm = fl->terms[n];
+    double h[3], h1[3], h2[3];
+    for (int i = 0; i < 3; ++i) { h[i] = 1.0; h1[i] = 0.0; h2[i] = 0.0; }
+    for (int i = 0; i < dim; ++i) atom(tm.type[i], tm.k[i], tm.phi[i], x[i], &h[i], &h1[i], &h2[i]);
+    *v += tm.c * h[0] * h[1] * h[2];
+    g[0] += tm.c * h1[0] * h[1] * h[2];
+    g[1] += tm.c * h[0] * h1[1] * h[2];
+    g[2] += tm.c * h[0] * h[1] * h1[2];
+    *lap += tm.c * (h2[0] * h[1] * h[2] + h[0] * h2[1] * h[2] + h[0] * h[1] * h2[2]);
+  }
+}
+
+// node-centred multilinear interpolation, coordinates clamped to the grid box
+void grid_linear(int dim, const orc_field* fl, const double* x, double* v, double* g, double* lap) {
+  int i0[3] = {0, 0, 0};
+  double t[3] = {0, 0, 0}, hh[3] = {1, 1, 1};
+  for (int d = 0; d < dim; ++d) {
+    hh[d] = (fl->hi[d] - fl->lo[d]) / (fl->res[d] - 1);
+    double s = (x[d] - fl->lo[d]) / hh[d];
+    if (s < 0.0) s = 0.0;
+    if (s > fl->res[d] - 1) s = fl->res[d] - 1;
+    int i = (int)std::floor(s);
+    if (i > fl->res[d] - 2) i = fl->res[d] - 2;
+    i0[d] = i;
+    t[d] = s - i;
+  }
+  *v = 0.0;
+  *lap = 0.0;
+  for (int d = 0; d < 3; ++d) g[d] = 0.0;
+  int nc = (dim == 3) ? 8 : 4;
+  for (int c = 0; c < nc; ++c) {
+    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    long idx = 0, stride = 1;
+    double w = 1.0, dw[3] = {1, 1, 1};
+    for (int d = 0; d < dim; ++d) {
+      idx += (long)(i0[d] + o[d]) * stride;
+      stride *= fl->res[d];
+      double wd = o[d] ? t[d] : 1.0 - t[d];
+      double dd = (o[d] ? 1.0 : -1.0) / hh[d];
+      for (int e = 0; e < dim; ++e) dw[e] *= (e == d) ? dd : wd;
+      w *= wd;
+    }
+    double val = fl->data[idx];
+    *v += w * val;
+    for (int d = 0; d < dim; ++d) g[d] += dw[d] * val;
+  }
+}
+
+// uniform cubic B-spline basis and derivatives at fraction t
+void bspline_basis(double t, double B[4], double B1[4], double B2[4]) {
+  double u = 1.0 - t;
+  B[0] = u * u * u / 6.0;
+  B[1] = (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;
+  B[2] = (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;
+  B[3] = t * t * t / 6.0;
+  B1[0] = -u * u / 2.0;
+  B1[1] = (3.0 * t * t - 4.0 * t) / 2.0;
+  B1[2] = (-3.0 * t * t + 2.0 * t + 1.0) / 2.0;
+  B1[3] = t * t / 2.0;
+  B2[0] = u;
+  B2[1] = 3.0 * t - 2.0;
+  B2[2] = -3.0 * t + 1.0;
+  B2[3] = t;
+}
+
+// cubic B-spline with the grid values as control points at the nodes; control
+// indices are clamped to the grid (constant extension), which keeps it C^2.
+void grid_bspline(int dim, const orc_field* fl, const double* x, double* v, double* g, double* lap) {
+  int ib[3] = {0, 0, 0};
+  double B[3][4], B1[3][4], B2[3][4], hh[3] = {1, 1, 1};
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 4; ++a) { B[d][a] = (a == 0); B1[d][a] = 0; B2[d][a] = 0; }
+  for (int d = 0; d < dim; ++d) {
+    hh[d] = (fl->hi[d] - fl->lo[d]) / (fl->res[d] - 1);
+    double s = (x[d] - fl->lo[d]) / hh[d];
+    double fs = std::floor(s);
+    ib[d] = (int)fs - 1;
+    bspline_basis(s - fs, B[d], B1[d], B2[d]);
+    for (int a = 0; a < 4; ++a) { B1[d][a] /= hh[d]; B2[d][a] /= hh[d] * hh[d]; }
+  }
+  *v = 0.0;
+  *lap = 0.0;
+  for (int d = 0; d < 3; ++d) g[d] = 0.0;
+  int n2 = (dim == 3) ? 4 : 1;
+  for (int c2 = 0; c2 < n2; ++c2)
+    for (int c1 = 0; c1 < 4; ++c1)
+      for (int c0 = 0; c0 < 4; ++c0) {
+        int c[3] = {c0, c1, c2};
+        long idx = 0, stride = 1;
+        for (int d = 0; d < dim; ++d) {
+          int j = ib[d] + c[d];
+          if (j < 0) j = 0;
+          if (j > fl->res[d] - 1) j = fl->res[d] - 1;
+          idx += (long)j * stride;
+          stride *= fl->res[d];
+        }
+        double val = fl->data[idx];
+        double b0 = B[0][c0], b1 = B[1][c1], b2 = B[2][c2];
+        *v += val * b0 * b1 * b2;
+        g[0] += val * B1[0][c0] * b1 * b2;
+        g[1] += val * b0 * B1[1][c1] * b2;
+        g[2] += val * b0 * b1 * B1[2][c2];
+        *lap += val * (B2[0][c0] * b1 * b2 + b0 * B2[1][c1] * b2 + b0 * b1 * B2[2][c2]);
+      }
+}
+
+int field_eval(const orc_problem* P, const orc_field* fl, const double* x, double* v, double* g,
+               double* lap) {
+  int dim = P->dim;
+  switch (fl->kind) {
+    case ORC_FIELD_ZERO:
+      *v = 0.0; *lap = 0.0; g[0] = g[1] = g[2] = 0.0;
+      return 0;
+    case ORC_FIELD_CONST:
+      *v = fl->value; *lap = 0.0; g[0] = g[1] = g[2] = 0.0;
+      return 0;
+    case ORC_FIELD_SST:
+      sst_eval(dim, fl, x, v, g, lap);
+      return 0;
+    case ORC_FIELD_GRID_LINEAR:
+      grid_linear(dim, fl, x, v, g, lap);
+      return 0;
+    case ORC_FIELD_GRID_BSPLINE:
+      grid_bspline(dim, fl, x, v, g, lap);
+      return 0;
+    case ORC_FIELD_MANUFACTURED: {
+      // eq. 1 solved for f at a known u:  f = -div(alpha grad u) - omega.grad u + sigma u,
+      // div(alpha grad u) = alpha Lap u + grad alpha . grad u,  omega = alpha grad Phi.
+      double u, gu[3], lu, a, ga[3], la, ph, gp[3], lp, s, gs[3], ls;
+      if (field_eval(P, &P->um, x, &u, gu, &lu)) return -1;
+      if (field_eval(P, &P->alpha, x, &a, ga, &la)) return -1;
+      if (field_eval(P, &P->phi, x, &ph, gp, &lp)) return -1;
+      if (field_eval(P, &P->sigma, x, &s, gs, &ls)) return -1;
+      double dot_a = 0.0, dot_p = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        dot_a += ga[d] * gu[d];
+        dot_p += gp[d] * gu[d];
+      }
+      *v = -(a * lu + dot_a) - a * dot_p + s * u;
+      *lap = NAN;
+      g[0] = g[1] = g[2] = NAN;
+      return 0;
+    }
+    default:
+      return -1;
+  }
+}
+
+// Sec. 4.1 (eq. 7-8) and App. A: gamma = 1/2 ln(alpha) + 1/2 Phi,
+// sigma' = sigma/alpha + Lap(gamma) + |grad gamma|^2, f' = e^gamma f / alpha.
+void coeffs(const orc_problem* P, const double* x, double* gamma, double* sp, double* fp,
+            double* fv, double* av) {
+  int dim = P->dim;
+  double a, ga[3], la, ph, gp[3], lp, s, gs[3], ls, f, gf[3], lf;
+  field_eval(P, &P->alpha, x, &a, ga, &la);
+  field_eval(P, &P->phi, x, &ph, gp, &lp);
+  field_eval(P, &P->sigma, x, &s, gs, &ls);
+  field_eval(P, &P->f, x, &f, gf, &lf);
+  double ggam[3] = {0, 0, 0}, na2 = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    ggam[d] = 0.5 * (ga[d] / a + gp[d]);
+    na2 += ga[d] * ga[d];
+  }
+  double lgam = 0.5 * (la / a - na2 / (a * a) + lp);
+  double ng2 = 0.0;
+  for (int d = 0; d < dim; ++d) ng2 += ggam[d] * ggam[d];
+  *gamma = 0.5 * std::log(a) + 0.5 * ph;
+  *sp = s / a + lgam + ng2;
+  *fp = std::exp(*gamma) * f / a;
+  *fv = f;
+  *av = a;
+}
+
+double gamma_at(const orc_problem* P, const double* x) {
+  double a, ga[3], la, ph, gp[3], lp;
+  field_eval(P, &P->alpha, x, &a, ga, &la);
+  field_eval(P, &P->phi, x, &ph, gp, &lp);
+  return 0.5 * std::log(a) + 0.5 * ph;
+}
+
+// ---------------------------------------------------------------------------
+// Distance to the boundary (Alg. 1 "DistanceToBoundary"), analytic shapes.
+// ---------------------------------------------------------------------------
+double distance(const orc_problem* P, const double* x, double* xb) {
+  int dim = P->dim;
+  const double* p = P->domain.p;
+  for (int d = 0; d < 3; ++d) xb[d] = (d < dim) ? x[d] : 0.0;
+  switch (P->domain.kind) {
+    case ORC_DOM_BOX: {
+      double best = INFINITY;
+      int bd = 0;
+      double bv = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        double dl = x[d] - p[d], dh = p[3 + d] - x[d];
+        if (dl < best) { best = dl; bd = d; bv = p[d]; }
+        if (dh < best) { best = dh; bd = d; bv = p[3 + d]; }
+      }
+      xb[bd] = bv;
+      return best;
+    }
+    case ORC_DOM_BALL: {
+      double v[3] = {0, 0, 0}, r2 = 0.0;
+      for (int d = 0; d < dim; ++d) { v[d] = x[d] - p[d]; r2 += v[d] * v[d]; }
+      double r = std::sqrt(r2);
+      if (r == 0.0) { v[0] = 1.0; r = 1.0; }
+      for (int d = 0; d < dim; ++d) xb[d] = p[d] + v[d] / r * p[3];
+      return p[3] - std::sqrt(r2);
+    }
+    case ORC_DOM_ANNULUS: {
+      double v[3] = {0, 0, 0}, r2 = 0.0;
+      for (int d = 0; d < dim; ++d) { v[d] = x[d] - p[d]; r2 += v[d] * v[d]; }
+      double r = std::sqrt(r2);
+      double din = r - p[3], dout = p[4] - r;
+      double rad = (din < dout) ? p[3] : p[4];
+      if (r == 0.0) { v[0] = 1.0; r = 1.0; }
+      for (int d = 0; d < dim; ++d) xb[d] = p[d] + v[d] / r * rad;
+      return (din < dout) ? din : dout;
+    }
+    case ORC_DOM_ROUNDED_BOX: {
+      // Minkowski sum of the inner box (half extents b - rc) and a ball of radius rc
+      double rc = p[6];
+      double q[3] = {0, 0, 0}, rel[3] = {0, 0, 0}, inner[3] = {0, 0, 0};
+      double outside2 = 0.0, qmax = -INFINITY;
+      int imax = 0;
+      for (int d = 0; d < dim; ++d) {
+        rel[d] = x[d] - p[d];
+        inner[d] = p[3 + d] - rc;
+        q[d] = std::fabs(rel[d]) - inner[d];
+        if (q[d] > 0.0) outside2 += q[d] * q[d];
+        if (q[d] > qmax) { qmax = q[d]; imax = d; }
+      }
+      if (outside2 > 0.0) {
+        double od = std::sqrt(outside2);
+        for (int d = 0; d < dim; ++d) {
+          double c = rel[d];
+          if (c > inner[d]) c = inner[d];
+          if (c < -inner[d]) c = -inner[d];
+          xb[d] = p[d] + c + (rel[d] - c) / od * rc;
+        }
+        return rc - od;
+      }
+      xb[imax] = p[imax] + ((rel[imax] >= 0.0) ? p[3 + imax] : -p[3 + imax]);
+      return rc - qmax;
+    }
+    default:
+      return NAN;
+  }
+}
+
+void domain_bbox(const orc_problem* P, double lo[3], double hi[3]) {
+  const double* p = P->domain.p;
+  for (int d = 0; d < 3; ++d) { lo[d] = 0.0; hi[d] = 0.0; }
+  for (int d = 0; d < P->dim; ++d) {
+    switch (P->domain.kind) {
+      case ORC_DOM_BOX: lo[d] = p[d]; hi[d] = p[3 + d]; break;
+      case ORC_DOM_BALL: lo[d] = p[d] - p[3]; hi[d] = p[d] + p[3]; break;
+      case ORC_DOM_ANNULUS: lo[d] = p[d] - p[4]; hi[d] = p[d] + p[4]; break;
+      case ORC_DOM_ROUNDED_BOX: lo[d] = p[d] - p[3 + d]; hi[d] = p[d] + p[3 + d]; break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Centred Green's function of Lap - sigma_bar on a ball (Supplemental 1.1).
+// ---------------------------------------------------------------------------
+double green_norm(int dim, double R, double sb) {
+  double a = std::sqrt(sb) * R;
+  if (dim == 2) {
+    // |G| = (1/sb)(1 - 1/I0(a)) = R^2 (I0(a) - 1) / (a^2 I0(a))
+    if (a == 0.0) return R * R / 4.0;
+    if (a < 2.0) {
+      double q = a * a / 4.0, bk = 1.0, s = 0.0;  // s = I0(a) - 1 = sum_{k>=1} b_k
+      for (int k = 1; k < 40; ++k) {
+        bk *= q / ((double)k * k);
+        s += bk;
+        if (bk < 1e-22 * s) break;
+      }
+      return R * R * (s / (a * a)) / (1.0 + s);
+    }
+    return (1.0 - 1.0 / bI0(a)) / sb;
+  }
+  // |G| = (1/sb)(1 - a/sinh a) = R^2 (sinh a - a) / (a^2 sinh a)
+  if (a == 0.0) return R * R / 6.0;
+  if (a < 1.0) {
+    double term = a, s = 0.0;  // sinh a - a = sum_{k>=1} a^(2k+1)/(2k+1)!
+    for (int k = 1; k < 30; ++k) {
+      term *= a * a / ((2.0 * k) * (2.0 * k + 1.0));
+      s += term;
+      if (term < 1e-22 * s) break;
+    }
+    return R * R * s / (a * a * std::sinh(a));
+  }
+  if (a > 30.0) return (1.0 - 2.0 * a * std::exp(-a) / (1.0 - std::exp(-2.0 * a))) / sb;
+  return (1.0 - a / std::sinh(a)) / sb;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported API
+// ===========================================================================
+extern "C" {
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  philox(ctr, key, out);
+}
+
+double orc_uniform(uint32_t x) { return uniform01(x); }
+
+void orc_bessel(double x, double out[4]) {
+  out[0] = bI0(x);
+  out[1] = bI1(x);
+  out[2] = bK0(x);
+  out[3] = bK1(x);
+}
+
+// Supplemental 1.1: G^sigma(x, y) at |y - x| = r on the centred ball, as printed
+// (Q2D / 2pi, Q3D / 4pi); sigma -> 0 gives the harmonic Green's function.
+double orc_green_G(int dim, double R, double sb, double r) {
+  double s = std::sqrt(sb);
+  if (dim == 2) {
+    if (sb == 0.0) return std::log(R / r) / (2.0 * kPi);
+    return (bK0(r * s) - bK0(R * s) / bI0(R * s) * bI0(r * s)) / (2.0 * kPi);
+  }
+  if (sb == 0.0) return (1.0 / r - 1.0 / R) / (4.0 * kPi);
+  double q = std::exp(-r * s) / r -
+             std::exp(-R * s) / R * (std::sinh(r * s) / (r * s)) * ((R * s) / std::sinh(R * s));
+  return q / (4.0 * kPi);
+}
+
+double orc_green_norm(int dim, double R, double sb) { return green_norm(dim, R, sb); }
+
+// Supplemental 1.1: P^sigma on the sphere of the centred ball, as printed.
+double orc_green_poisson(int dim, double R, double sb) {
+  double a = std::sqrt(sb) * R;
+  if (dim == 2) return 1.0 / (2.0 * kPi * R) / bI0(a);
+  double ratio = (a == 0.0) ? 1.0 : a / std::sinh(a);
+  return ratio / (4.0 * kPi * R * R);
+}
+
+double orc_green_cdf(int dim, double R, double sb, double r) {
+  double a = std::sqrt(sb) * R, rho = r / R;
+  return (dim == 2) ? cdf2(a, rho) : cdf3(a, rho);
+}
+
+double orc_green_pdf(int dim, double R, double sb, double r) {
+  double a = std::sqrt(sb) * R, rho = r / R;
+  return ((dim == 2) ? pdf2(a, rho) : pdf3(a, rho)) / R;
+}
+
+// F^{-1}(u): safeguarded Newton on rho in [0,1], run to convergence.
+double orc_green_inv(int dim, double R, double sb, double u) {
+  double a = std::sqrt(sb) * R;
+  double lo = 0.0, hi = 1.0, rho = 0.5;
+  for (int it = 0; it < 200; ++it) {
+    double F = (dim == 2) ? cdf2(a, rho) : cdf3(a, rho);
+    double fres = F - u;
+    if (fres > 0.0) hi = rho; else lo = rho;
+    double p = (dim == 2) ? pdf2(a, rho) : pdf3(a, rho);
+    double nr = (p > 0.0) ? rho - fres / p : 0.5 * (lo + hi);
+    if (!(nr > lo && nr < hi)) nr = 0.5 * (lo + hi);
+    double step = std::fabs(nr - rho);
+    rho = nr;
+    if (step < 1e-16 || hi - lo < 1e-16) break;
+  }
+  return rho * R;
+}
+
+int orc_field_eval(const orc_problem* prob, const orc_field* fld, const double* x, double* v,
+                   double* grad, double* lap) {
+  double g[3];
+  int rc = field_eval(prob, fld, x, v, g, lap);
+  for (int d = 0; d < prob->dim; ++d) grad[d] = g[d];
+  return rc;
+}
+
+int orc_coeffs(const orc_problem* prob, const double* x, double out[5]) {
+  coeffs(prob, x, &out[0], &out[1], &out[2], &out[3], &out[4]);
+  return 0;
+}
+
+double orc_distance(const orc_problem* prob, const double* x, double* xbar) {
+  double xb[3];
+  double d = distance(prob, x, xb);
+  for (int i = 0; i < prob->dim; ++i) xbar[i] = xb[i];
+  return d;
+}
+
+// Supplemental Algorithm 1 (delta-tracking WoS), unrolled into a loop.  The
+// recursion multiplies the estimate of the next point by sqrt(alpha(next) /
+// alpha(current)) -- in general e^{gamma(next) - gamma(current)} -- and, on a
+// null event, by (1 - sigma'(y)/sigma_bar); the source term
+// |G| f(y) / sqrt(alpha(x) alpha(y)) (in general |G| f'(y) e^{-gamma(x)}) is
+// added at every step.  The exponentials telescope, so the walk carries the
+// product W of null weights, accumulates W |G| f'(y) and W e^{gamma(x_n)} g(xbar_n)
+// on termination, and multiplies the sum by e^{-gamma(x_0)} at the end.
+double orc_walk(const orc_problem* P, const double* x0, uint32_t point, uint32_t walk,
+                uint64_t seed, double eps, double sb, int64_t max_steps, int64_t* steps_out,
+                int32_t* flags_out) {
+  int dim = P->dim;
+  double x[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) x[d] = x0[d];
+  double W = 1.0, acc = 0.0;
+  double g0 = gamma_at(P, x);
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  int64_t k = 0;
+  int32_t flags = 0;
+  for (;;) {
+    double xb[3];
+    double d = distance(P, x, xb);
+    if (d < eps) {
+      // epsilon shell: read g at the closest boundary point (Alg. 1, first branch)
+      double gv, gg[3], gl;
+      field_eval(P, &P->g, xb, &gv, gg, &gl);
+      acc += W * std::exp(gamma_at(P, x)) * gv;
+      break;
+    }
+    if (k >= max_steps) {
+      flags |= 1;
+      break;
+    }
+    double R = d;
+    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4], o1[4];
+    philox(ctr, key, o0);
+    double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
+    double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+    if (dim == 2) {
+      double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
+      dy[0] = std::cos(ty); dy[1] = std::sin(ty);
+      dz[0] = std::cos(tz); dz[1] = std::sin(tz);
+    } else {
+      ctr[3] = 1u;
+      philox(ctr, key, o1);
+      // uniform direction on the sphere from two uniforms (Archimedes' projection)
+      double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
+      double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
+      dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
+      double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
+      double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
+      dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
+    }
+    double Gn = green_norm(dim, R, sb);
+    double r = orc_green_inv(dim, R, sb, ur);
+    double y[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) y[i] = x[i] + r * dy[i];
+    double gam_y, sp_y, fp_y, f_y, a_y;
+    coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+    acc += W * Gn * fp_y;                       // source term, every step
+    if (mu <= sb * Gn) {                        // volume term: null event at y
+      W *= 1.0 - sp_y / sb;
+      for (int i = 0; i < dim; ++i) x[i] = y[i];
+    } else {                                    // boundary term: z uniform on the sphere
+      for (int i = 0; i < dim; ++i) x[i] = x[i] + R * dz[i];
+    }
+    ++k;
+  }
+  double u = acc * std::exp(-g0);
+  if (!std::isfinite(u)) flags |= 2;
+  if (steps_out) *steps_out = k;
+  if (flags_out) *flags_out = flags;
+  return u;
+}
+
+int orc_solve(const orc_problem* P, const double* pts, int64_t npts, const int32_t* walks,
+              int32_t walks_uniform, uint64_t walk_offset, uint64_t seed, double eps, double sb,
+              int64_t max_steps, double* sum, double* sumsq, int64_t* count, int64_t* stats,
+              int nthreads) {
+  if (P->dim != 2 && P->dim != 3) return -1;
+  if (!(sb > 0.0) || !(eps > 0.0)) return -1;
+  int dim = P->dim;
+  int64_t st_steps = 0, st_walks = 0, st_capped = 0, st_nonfinite = 0;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) \
+    reduction(+ : st_steps, st_walks, st_capped, st_nonfinite)
+  for (int64_t p = 0; p < npts; ++p) {
+    double x0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) x0[d] = pts[d * npts + p];
+    int32_t nw = walks ? walks[p] : walks_uniform;
+    double s1 = 0.0, s2 = 0.0;
+    for (int32_t j = 0; j < nw; ++j) {
+      int64_t k;
+      int32_t fl;
+      double u = orc_walk(P, x0, (uint32_t)p, (uint32_t)(walk_offset + (uint64_t)j), seed, eps, sb,
+                          max_steps, &k, &fl);
+      s1 += u;
+      s2 += u * u;
+      st_steps += k;
+      st_walks += 1;
+      st_capped += (fl & 1) ? 1 : 0;
+      st_nonfinite += (fl & 2) ? 1 : 0;
+    }
+    sum[p] += s1;
+    sumsq[p] += s2;
+    count[p] += nw;
+  }
+  if (stats) {
+    stats[0] += st_steps;
+    stats[1] += st_walks;
+    stats[2] += st_capped;
+    stats[3] += st_nonfinite;
+  }
+  return 0;
+}
+
+int orc_walks(const orc_problem* P, const double* pts, int64_t npts, int32_t wpp,
+              uint64_t walk_offset, uint64_t seed, double eps, double sb, int64_t max_steps,
+              double* uhat, int64_t* steps, int nthreads) {
+  if (!(sb > 0.0) || !(eps > 0.0)) return -1;
+  int dim = P->dim;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int64_t p = 0; p < npts; ++p) {
+    double x0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) x0[d] = pts[d * npts + p];
+    for (int32_t j = 0; j < wpp; ++j) {
+      int64_t k;
+      int32_t fl;
+      uhat[p * wpp + j] = orc_walk(P, x0, (uint32_t)p, (uint32_t)(walk_offset + (uint64_t)j), seed,
+                                   eps, sb, max_steps, &k, &fl);
+      if (steps) steps[p * wpp + j] = k;
+    }
+  }
+  return 0;
+}
+
+// Sec. 5.1 / Sec. 7.1: sigma_bar bounds sigma' over the domain.  The paper's
+// default is max(sigma') - min(sigma'); this oracle returns
+// max(max - min, max, 1e-3 / diam^2), which equals the paper's value whenever
+// min(sigma') < 0 and stays positive otherwise.
+int orc_sigma_bar(const orc_problem* P, int m, double* sigma_bar, double* smin, double* smax) {
+  int dim = P->dim;
+  double lo[3], hi[3];
+  domain_bbox(P, lo, hi);
+  double mn = INFINITY, mx = -INFINITY;
+  int64_t total = 1;
+  for (int d = 0; d < dim; ++d) total *= m;
+  for (int64_t idx = 0; idx < total; ++idx) {
+    double x[3] = {0, 0, 0}, xb[3];
+    int64_t r = idx;
+    for (int d = 0; d < dim; ++d) {
+      x[d] = lo[d] + (r % m + 0.5) * (hi[d] - lo[d]) / m;
+      r /= m;
+    }
+    if (!(distance(P, x, xb) > 0.0)) continue;
+    double gm, sp, fp, fv, av;
+    coeffs(P, x, &gm, &sp, &fp, &fv, &av);
+    if (sp < mn) mn = sp;
+    if (sp > mx) mx = sp;
+  }
+  double diam2 = 0.0;
+  for (int d = 0; d < dim; ++d) diam2 += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+  double sbv = mx - mn;
+  if (mx > sbv) sbv = mx;
+  if (1e-3 / diam2 > sbv) sbv = 1e-3 / diam2;
+  *sigma_bar = sbv;
+  *smin = mn;
+  *smax = mx;
+  return 0;
+}
+
+}  // extern "C"

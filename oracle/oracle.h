@@ -1,0 +1,141 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for delta-tracking walk on spheres.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library includes, links or
+ * calls this code.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it.  It shares no source with the CUDA path.
+ *
+ * It computes, slowly and in double precision, what the paper's method defines
+ * (Sawhney, Seyb, Jarosz, Crane, "Grid-Free Monte Carlo for PDEs with Spatially
+ * Varying Coefficients", SIGGRAPH 2022):
+ *
+ *   PDE (eq. 1):   div(alpha grad u) + omega . grad u - sigma u = -f  in Omega,
+ *                  u = g on the boundary,   with omega = alpha grad(Phi).
+ *   Transform (Sec. 4.1 eq. 7-8 and App. A):
+ *                  gamma = 1/2 ln alpha + 1/2 Phi,   U = e^gamma u,
+ *                  sigma' = sigma/alpha + Lap(gamma) + |grad gamma|^2,
+ *                  f' = e^gamma f / alpha,           g' = e^gamma g,
+ *                  Lap U - sigma' U = -f'.
+ *   Delta tracking (eq. 11) and the mean-value estimator (eq. 14, Sec. 5.1,
+ *   Supplemental Algorithm 1) with centred Green's functions (Supplemental 1.1).
+ *
+ * All arrays are HOST memory owned by the caller.  Functions never allocate
+ * memory that outlives the call.  Errors are reported by return value < 0.
+ */
+#ifndef WOS_ORACLE_H
+#define WOS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* atom types of a separable term: h(t) with t = k*x_i + phi */
+enum { ORC_ONE = 0, ORC_SIN = 1, ORC_COS = 2, ORC_EXP = 3, ORC_SINH = 4,
+       ORC_COSH = 5, ORC_LIN = 6, ORC_QUAD = 7 };
+
+/* value = c * prod_i h_{type[i]}(k[i] * x_i + phi[i]) */
+typedef struct {
+  double c;
+  int32_t type[3];
+  double k[3];
+  double phi[3];
+} orc_term;
+
+enum { ORC_FIELD_ZERO = 0, ORC_FIELD_CONST = 1, ORC_FIELD_SST = 2,
+       ORC_FIELD_MANUFACTURED = 3, ORC_FIELD_GRID_LINEAR = 4,
+       ORC_FIELD_GRID_BSPLINE = 5 };
+
+typedef struct {
+  int32_t kind;
+  int32_t nterms;
+  const orc_term* terms;   /* SST: nterms terms */
+  double value;            /* CONST */
+  int32_t res[3];          /* GRID: nodes per axis, node i at lo + i*(hi-lo)/(res-1) */
+  double lo[3];
+  double hi[3];
+  const float* data;       /* GRID: x fastest, [res2][res1][res0] */
+} orc_field;
+
+enum { ORC_DOM_BOX = 0, ORC_DOM_BALL = 1, ORC_DOM_ANNULUS = 2,
+       ORC_DOM_ROUNDED_BOX = 3 };
+
+typedef struct {
+  int32_t kind;
+  double p[16];
+  /* BOX: lo p[0..2], hi p[3..5]
+     BALL: centre p[0..2], radius p[3]
+     ANNULUS: centre p[0..2], inner radius p[3], outer radius p[4]
+     ROUNDED_BOX: centre p[0..2], half extents p[3..5], corner radius p[6] */
+} orc_domain;
+
+typedef struct {
+  int32_t dim;          /* 2 or 3 */
+  orc_domain domain;
+  orc_field alpha;      /* diffusion coefficient, > 0 */
+  orc_field phi;        /* drift potential: omega = alpha * grad(phi) */
+  orc_field sigma;      /* screening coefficient */
+  orc_field f;          /* source; MANUFACTURED: f = -div(alpha grad um) - omega.grad um + sigma um */
+  orc_field g;          /* Dirichlet data, read at the closest boundary point */
+  orc_field um;         /* manufactured solution used by f when f.kind == MANUFACTURED */
+} orc_problem;
+
+/* Philox4x32-10 block (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* uniform in (0,1): (x + 1/2) 2^-32 */
+double orc_uniform(uint32_t x);
+
+/* Bessel I0, I1, K0, K1 as used by the oracle (C++17 special functions). */
+void orc_bessel(double x, double out[4]);
+
+/* Centred screened-Poisson Green's function on a ball of radius R, sigma_bar >= 0
+   (Supplemental 1.1).  G(r) density value, |G| its integral over the ball,
+   F(r) the radial CDF of y ~ G/|G|, pdf = dF/dr, inv = F^{-1}(u). */
+double orc_green_G(int dim, double R, double sigma_bar, double r);
+double orc_green_norm(int dim, double R, double sigma_bar);
+double orc_green_poisson(int dim, double R, double sigma_bar);
+double orc_green_cdf(int dim, double R, double sigma_bar, double r);
+double orc_green_pdf(int dim, double R, double sigma_bar, double r);
+double orc_green_inv(int dim, double R, double sigma_bar, double u);
+
+/* Field value, gradient and Laplacian at x (MANUFACTURED needs the problem). */
+int orc_field_eval(const orc_problem* prob, const orc_field* fld, const double* x,
+                   double* v, double* grad, double* lap);
+
+/* Transformed coefficients at x: out = {gamma, sigma', f', f, alpha}. */
+int orc_coeffs(const orc_problem* prob, const double* x, double out[5]);
+
+/* Distance to the boundary (positive inside) and closest boundary point. */
+double orc_distance(const orc_problem* prob, const double* x, double* xbar);
+
+/* One delta-tracking walk from x0.  Randoms: Philox4x32-10, key = (seed lo, seed hi),
+   counter = (point, walk, step, block).  Returns the estimate of u(x0).
+   steps_out: number of sampling steps; flags_out: bit0 capped, bit1 non-finite. */
+double orc_walk(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk,
+                uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
+                int64_t* steps_out, int32_t* flags_out);
+
+/* Many walks: pts SoA [dim][npts].  walks[p] (or walks_uniform if walks == NULL)
+   walks per point with ids walk_offset .. walk_offset + walks - 1, accumulated
+   into sum / sumsq / count (FP64, caller-initialised).  stats: {steps, walks,
+   capped, nonfinite} added.  nthreads <= 0: all OpenMP threads. */
+int orc_solve(const orc_problem* prob, const double* pts, int64_t npts,
+              const int32_t* walks, int32_t walks_uniform, uint64_t walk_offset,
+              uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
+              double* sum, double* sumsq, int64_t* count, int64_t* stats, int nthreads);
+
+/* Per-walk estimates uhat[p * walks_per_point + j] and step counts. */
+int orc_walks(const orc_problem* prob, const double* pts, int64_t npts,
+              int32_t walks_per_point, uint64_t walk_offset, uint64_t seed, double eps,
+              double sigma_bar, int64_t max_steps, double* uhat, int64_t* steps,
+              int nthreads);
+
+/* Range of sigma' over interior nodes of an m^dim lattice on the domain's bounding box,
+   and the bound sigma_bar = max(max - min, max, 1e-3 / diam^2). */
+int orc_sigma_bar(const orc_problem* prob, int m, double* sigma_bar, double* smin,
+                  double* smax);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

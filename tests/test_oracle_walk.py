@@ -1,0 +1,98 @@
+"""End-to-end pins of the oracle's delta-tracking walk against exact solutions.
+
+Harmonic boundary data on a disk and a ball (Kakutani's principle, Sec. 2.4),
+constant screening with a known solution (Sec. 2.3), and the manufactured
+variable-coefficient problems (eq. 1 with alpha, sigma and a conservative drift
+chosen so that u is known).  Any sigma_bar > 0 leaves the estimator unbiased
+(Sec. 5.1), so estimates at sigma_bar and 2 sigma_bar must agree.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.stats_util import combined_z, four_se_rule
+
+
+def _run(orc, prob, pts, walks, eps, sb=None, seed=0, offset=0):
+    if sb is None:
+        sb = orc.sigma_bar(prob)[0]
+    acc, st = orc.solve(prob, pts, walks, seed=seed, eps=eps, sigma_bar=sb, walk_offset=offset)
+    m, v, se = orc.finalize(acc)
+    assert st["capped"] == 0 and st["nonfinite"] == 0
+    return m, se, st
+
+
+CASES = {
+    "laplace_disk": (W.laplace_disk_problem, lambda p: W.laplace_disk_exact(*p),
+                     lambda: W.uniform_in_ball(2, 12, [0, 0], 1.0, seed=1, margin=0.05), 4000, 1e-4),
+    "laplace_ball": (W.laplace_ball_problem, lambda p: W.laplace_ball_exact(*p),
+                     lambda: W.uniform_in_ball(3, 12, [0, 0, 0], 1.0, seed=2, margin=0.05), 3000, 1e-4),
+    "screened_square": (W.screened_square_problem, lambda p: W.screened_square_exact(*p),
+                        lambda: W.uniform_in_box(2, 12, 0.05, 0.95, seed=3), 4000, 1e-4),
+    "screened_ball": (W.screened_ball_problem, lambda p: W.screened_ball_exact(9.0, *p),
+                      lambda: W.uniform_in_ball(3, 12, [0, 0, 0], 1.0, seed=4, margin=0.05), 3000, 1e-4),
+    "square2d": (W.square2d_problem, lambda p: W.square2d_exact(*p),
+                 lambda: W.cell_centres(2, 32)[:, W.seeded_subset(1024, 16, 5)], 6000, 1e-3),
+    "cube3d": (W.cube3d_problem, lambda p: W.cube3d_exact(*p),
+               lambda: W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 10, 6)], 3000, 1e-4),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_walk_matches_exact_solution(orc, name):
+    mk, exact, ptsf, walks, eps = CASES[name]
+    prob = mk()
+    pts = ptsf()
+    m, se, st = _run(orc, prob, pts, walks, eps)
+    u = exact(pts.astype(np.float64))
+    z = (m - u) / se
+    ok, nout, mz = four_se_rule(z)
+    assert ok, (name, z)
+    assert st["steps"] > st["walks"]
+
+
+def test_sigma_bar_invariance(orc):
+    prob = W.square2d_problem()
+    pts = W.cell_centres(2, 32)[:, W.seeded_subset(1024, 12, 7)]
+    sb = orc.sigma_bar(prob)[0]
+    m1, se1, st1 = _run(orc, prob, pts, 3000, 1e-3, sb=sb, seed=1)
+    m2, se2, st2 = _run(orc, prob, pts, 3000, 1e-3, sb=2 * sb, seed=2)
+    ok, _, _ = four_se_rule(combined_z(m1, se1, m2, se2))
+    assert ok
+    # a larger bound makes more null events: more steps per walk (Sec. 5.2, Fig. 12)
+    assert st2["steps"] > 1.1 * st1["steps"]
+
+
+def test_walk_ids_continue_streams(orc):
+    """Walk j of a run at offset o is walk o + j of a run at offset 0 (bit for bit)."""
+    prob = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)[:, :3]
+    sb = orc.sigma_bar(prob)[0]
+    a, sa = orc.walks(prob, pts, 8, seed=11, eps=1e-4, sigma_bar=sb)
+    b, sb_ = orc.walks(prob, pts, 4, seed=11, eps=1e-4, sigma_bar=sb, walk_offset=4)
+    assert np.array_equal(a[:, 4:], b)
+    assert np.array_equal(sa[:, 4:], sb_)
+    c, _ = orc.walks(prob, pts, 8, seed=12, eps=1e-4, sigma_bar=sb)
+    assert not np.array_equal(a, c)
+
+
+def test_points_in_shell_return_boundary_value(orc):
+    """A point already within eps of the boundary returns g(xbar) exactly (Alg. 1)."""
+    prob = W.square2d_problem()
+    pts = np.array([[0.5, 1e-4, 0.3], [0.9995, 0.5, 1 - 2e-4]], dtype=np.float32)
+    sb = orc.sigma_bar(prob)[0]
+    uh, steps = orc.walks(prob, pts, 5, seed=0, eps=1e-3, sigma_bar=sb)
+    assert np.all(steps == 0)
+    for i in range(3):
+        d, xb = orc.distance(prob, pts[:, i].astype(np.float64))
+        want = W.square2d_exact(*xb)
+        assert np.allclose(uh[i], want, rtol=1e-12, atol=1e-14)
+
+
+def test_step_cap_is_reported(orc):
+    prob = W.square2d_problem()
+    pts = W.cell_centres(2, 4)
+    sb = orc.sigma_bar(prob)[0]
+    _, st = orc.solve(prob, pts, 50, seed=0, eps=1e-3, sigma_bar=sb, max_steps=2)
+    assert st["capped"] > 0
+    assert st["steps"] <= 2 * st["walks"]

@@ -1,0 +1,237 @@
+"""Seeded synthetic inputs for delta-tracking walk on spheres.
+
+This module only *describes* problems and generates inputs: domains, the
+closed-form coefficient families, the evaluation points and the seeds.  It
+holds none of the method's arithmetic, so both the CUDA path and the CPU
+oracle can take their inputs from here without sharing any computation.
+
+A problem is a plain dict::
+
+    {"dim": 2|3,
+     "domain": {"kind": "box"|"ball"|"annulus"|"rounded_box", "p": [..16 floats]},
+     "alpha": field, "phi": field, "sigma": field, "f": field, "g": field,
+     "um": field}
+
+and a field is ``{"kind": "zero"|"const"|"sst"|"manufactured"|"grid_linear"|
+"grid_bspline", ...}``.  An ``sst`` field is a sum of separable terms
+``c * prod_i h_i(k_i x_i + phi_i)`` with ``h`` one of ONE, SIN, COS, EXP,
+SINH, COSH, LIN (t) and QUAD (t^2).  ``manufactured`` asks for the source
+``f = -div(alpha grad um) - omega . grad um + sigma um`` of the PDE (Sec. 3,
+eq. 1) at the given ``um``, with ``omega = alpha grad phi``.
+
+The manufactured workloads are the paper's PDE with coefficients chosen so the
+exact solution is known (Sec. 3 eq. 1; App. A for the drift).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+ONE, SIN, COS, EXP, SINH, COSH, LIN, QUAD = range(8)
+ATOM_NAMES = ["ONE", "SIN", "COS", "EXP", "SINH", "COSH", "LIN", "QUAD"]
+
+PI = math.pi
+
+
+def term(c, *atoms):
+    """One separable term: c * prod_i h_i(k_i x_i + phi_i); atoms are (type, k, phi)."""
+    a = [tuple(x) if x is not None else (ONE, 0.0, 0.0) for x in atoms]
+    while len(a) < 3:
+        a.append((ONE, 0.0, 0.0))
+    return {"c": float(c), "atoms": [(int(t), float(k), float(p)) for t, k, p in a]}
+
+
+def sst(*terms):
+    return {"kind": "sst", "terms": list(terms)}
+
+
+def const(v):
+    return {"kind": "const", "value": float(v)}
+
+
+def zero():
+    return {"kind": "zero"}
+
+
+def manufactured():
+    return {"kind": "manufactured"}
+
+
+def box(lo, hi):
+    p = [0.0] * 16
+    for i, v in enumerate(lo):
+        p[i] = float(v)
+    for i, v in enumerate(hi):
+        p[3 + i] = float(v)
+    return {"kind": "box", "p": p}
+
+
+def ball(centre, radius):
+    p = [0.0] * 16
+    for i, v in enumerate(centre):
+        p[i] = float(v)
+    p[3] = float(radius)
+    return {"kind": "ball", "p": p}
+
+
+def annulus(centre, r_in, r_out):
+    p = [0.0] * 16
+    for i, v in enumerate(centre):
+        p[i] = float(v)
+    p[3] = float(r_in)
+    p[4] = float(r_out)
+    return {"kind": "annulus", "p": p}
+
+
+def rounded_box(centre, half, corner):
+    p = [0.0] * 16
+    for i, v in enumerate(centre):
+        p[i] = float(v)
+    for i, v in enumerate(half):
+        p[3 + i] = float(v)
+    p[6] = float(corner)
+    return {"kind": "rounded_box", "p": p}
+
+
+def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None):
+    return {
+        "dim": int(dim),
+        "domain": domain,
+        "alpha": alpha,
+        "phi": phi if phi is not None else zero(),
+        "sigma": sigma,
+        "f": f,
+        "g": g,
+        "um": um if um is not None else zero(),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Workload 1: 2D unit square, u = sin(pi x) cosh(y),
+#   alpha = 1 + 0.5 sin(2 pi x) cos(2 pi y), sigma = 2 + sin(3x + y), omega = 0,
+#   f derived from eq. 1, g = u; eps = 1e-3; 32 x 32 cell centres x 256 walks.
+# ---------------------------------------------------------------------------
+def square2d_problem():
+    u = sst(term(1.0, (SIN, PI, 0.0), (COSH, 1.0, 0.0)))
+    alpha = sst(term(1.0), term(0.5, (SIN, 2 * PI, 0.0), (COS, 2 * PI, 0.0)))
+    # sin(3x + y) = sin(3x) cos(y) + cos(3x) sin(y)
+    sigma = sst(term(2.0), term(1.0, (SIN, 3.0, 0.0), (COS, 1.0, 0.0)),
+                term(1.0, (COS, 3.0, 0.0), (SIN, 1.0, 0.0)))
+    return problem(2, box([0, 0], [1, 1]), alpha, sigma, manufactured(), u, um=u)
+
+
+def square2d_exact(x, y):
+    return np.sin(np.pi * x) * np.cosh(y)
+
+
+SQUARE2D = {"name": "square2d_manufactured", "eps": 1e-3, "grid": 32, "walks": 256,
+            "seed": 0}
+
+
+# ---------------------------------------------------------------------------
+# Workload 2: 3D unit cube with a conservative drift,
+#   u = exp(0.5 x) sin(pi y) cos(pi z), alpha = 1 + 0.3 |x|^2, sigma = 1 + x y,
+#   omega = alpha grad(Phi), Phi = x sin(2 pi y) + sin(2 pi z)/(2 pi) + 0.5 z,
+#   so omega/alpha = (sin 2pi y, 2pi x cos 2pi y, cos 2pi z + 0.5);
+#   eps = 1e-4; 64^3 cell centres x 1024 walks.
+# The paper removes a drift exactly only when omega/alpha is a gradient
+# (App. A), so the drift is given through its potential Phi.
+# ---------------------------------------------------------------------------
+def cube3d_problem():
+    u = sst(term(1.0, (EXP, 0.5, 0.0), (SIN, PI, 0.0), (COS, PI, 0.0)))
+    alpha = sst(term(1.0), term(0.3, (QUAD, 1.0, 0.0)), term(0.3, None, (QUAD, 1.0, 0.0)),
+                term(0.3, None, None, (QUAD, 1.0, 0.0)))
+    sigma = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)))
+    phi = sst(term(1.0, (LIN, 1.0, 0.0), (SIN, 2 * PI, 0.0)),
+              term(1.0 / (2 * PI), None, None, (SIN, 2 * PI, 0.0)),
+              term(0.5, None, None, (LIN, 1.0, 0.0)))
+    return problem(3, box([0, 0, 0], [1, 1, 1]), alpha, sigma, manufactured(), u, phi=phi, um=u)
+
+
+def cube3d_exact(x, y, z):
+    return np.exp(0.5 * x) * np.sin(np.pi * y) * np.cos(np.pi * z)
+
+
+CUBE3D = {"name": "cube3d_drift_manufactured", "eps": 1e-4, "grid": 64, "walks": 1024,
+          "seed": 0}
+
+
+# ---------------------------------------------------------------------------
+# Closed-form test families (Sec. 2.3-2.4): harmonic g (Kakutani), constant
+# screening with a known solution.
+# ---------------------------------------------------------------------------
+def laplace_disk_problem():
+    """Delta u = 0 on the unit disk, u = x^2 - y^2."""
+    u = sst(term(1.0, (QUAD, 1.0, 0.0)), term(-1.0, None, (QUAD, 1.0, 0.0)))
+    return problem(2, ball([0, 0], 1.0), const(1.0), zero(), zero(), u, um=u)
+
+
+def laplace_disk_exact(x, y):
+    return x * x - y * y
+
+
+def laplace_ball_problem():
+    """Delta u = 0 on the unit ball, u = x y z + x^2 - z^2."""
+    u = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)),
+            term(1.0, (QUAD, 1.0, 0.0)), term(-1.0, None, None, (QUAD, 1.0, 0.0)))
+    return problem(3, ball([0, 0, 0], 1.0), const(1.0), zero(), zero(), u, um=u)
+
+
+def laplace_ball_exact(x, y, z):
+    return x * y * z + x * x - z * z
+
+
+def screened_square_problem(sig=4.0):
+    """Delta u - sigma u = -f on the unit square with u = sin(x) sin(y), f = (2 + sigma) u."""
+    u = sst(term(1.0, (SIN, 1.0, 0.0), (SIN, 1.0, 0.0)))
+    return problem(2, box([0, 0], [1, 1]), const(1.0), const(sig), manufactured(), u, um=u)
+
+
+def screened_square_exact(x, y):
+    return np.sin(x) * np.sin(y)
+
+
+def screened_ball_problem(sig=9.0):
+    """Delta u - sigma u = 0 on the unit ball with u = cosh(sqrt(sigma) x)."""
+    s = math.sqrt(sig)
+    u = sst(term(1.0, (COSH, s, 0.0)))
+    return problem(3, ball([0, 0, 0], 1.0), const(1.0), const(sig), manufactured(), u, um=u)
+
+
+def screened_ball_exact(sig, x, y, z):
+    return np.cosh(np.sqrt(sig) * x)
+
+
+# ---------------------------------------------------------------------------
+# evaluation points (SoA float32 [dim][npts])
+# ---------------------------------------------------------------------------
+def cell_centres(dim, n, lo=0.0, hi=1.0):
+    """Cell centres of an n^dim grid on [lo, hi]^dim; x varies fastest."""
+    c = (np.arange(n, dtype=np.float64) + 0.5) / n * (hi - lo) + lo
+    mesh = np.meshgrid(*([c] * dim), indexing="ij")
+    # x fastest: reverse the axis order of the flattened index
+    pts = np.stack([m.transpose(tuple(range(dim))[::-1]).reshape(-1) for m in mesh])
+    return pts.astype(np.float32)
+
+
+def seeded_subset(npts, m, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(npts, size=min(m, npts), replace=False))
+
+
+def uniform_in_ball(dim, n, centre, radius, seed, margin=0.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    while sum(len(o) for o in out) < n:
+        x = rng.uniform(-1.0, 1.0, size=(4 * n, dim))
+        r = np.linalg.norm(x, axis=1)
+        out.append(x[r < 1.0 - margin])
+    x = np.concatenate(out)[:n] * radius + np.asarray(centre[:dim])
+    return np.ascontiguousarray(x.T.astype(np.float32))
+
+
+def uniform_in_box(dim, n, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(lo, hi, size=(dim, n))
+    return np.ascontiguousarray(x.astype(np.float32))
