@@ -1,0 +1,334 @@
+"""Benchmark: delta-tracking walk on spheres on the 3D manufactured workload.
+
+Workload (one "step" = one full solve): unit cube, u = e^{x/2} sin(pi y) cos(pi z),
+alpha = 1 + 0.3 |x|^2, sigma = 1 + x y, drift omega = alpha grad(Phi) with
+Phi = x sin(2 pi y) + sin(2 pi z)/(2 pi) + z/2, f from eq. 1, g = u, eps = 1e-4;
+64^3 = 262,144 cell-centre points x 1024 walks, FP32 walk state, FP64 per-point
+accumulators.  Metric: walk-steps/s (one step = one distance query + one
+Green's-function sample).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (the only reference of this
+method here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "walk-steps/s"
+UNIT = "steps/s"
+GRID = 64
+WALKS = 1024
+EPS = 1e-4
+SEED = 0
+SIGMA_LATTICE = 64
+# Algorithmic work of one walk step of this workload in ALU issue slots (FP32/INT32
+# lane operations; each special-function op counted as 8, the FP32:MUFU rate ratio):
+# Philox 2 blocks 160, uniforms 18, directions 16 + 6 MUFU, distance 17, Green's
+# norm 14 + 3 MUFU, radial inverse CDF 140 + 14 MUFU, coefficients 196 + 12 MUFU,
+# update 12  ->  573 ALU + 35 MUFU = 853.
+OPS_PER_STEP = 853
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "cube3d_drift_manufactured: 64^3 points x 1024 walks, eps 1e-4, FP32 walks, FP64 sums",
+           "points": GRID ** 3, "walks_per_point": WALKS, "eps": EPS, "seed": SEED,
+           "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled with nvidia-smi while the timed region runs
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"wos_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(desc, sb, npoints, walks, seed):
+    import oracle
+    oracle.build()
+    pts = W.cell_centres(3, GRID)[:, W.seeded_subset(GRID ** 3, npoints, 77 + seed)]
+    t0 = time.perf_counter()
+    _, st = oracle.solve(desc, pts, walks, seed=seed, eps=EPS, sigma_bar=sb)
+    dt = time.perf_counter() - t0
+    return st["steps"], dt
+
+
+def run_reference(args):
+    r, world, _ = rank_info()
+    if r != 0:
+        return 0
+    import oracle
+    oracle.build()
+    desc = W.cube3d_problem()
+    sb = oracle.sigma_bar(desc, SIGMA_LATTICE)[0]
+    npoints = 96  # per step: 96 points x 1024 walks (a bounded sample of the workload)
+    for i in range(args.warmup):
+        oracle_rate(desc, sb, npoints, WALKS, seed=1000 + i)
+    tot_steps, tot_t = 0, 0.0
+    for i in range(args.steps):
+        s, dt = oracle_rate(desc, sb, npoints, WALKS, seed=i)
+        tot_steps += s
+        tot_t += dt
+    value = tot_steps / tot_t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config({"sample": f"{npoints} seeded points x {WALKS} walks "
+                                                                      "per step"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{npoints} seeded points x {WALKS} walks per step, FP64, OpenMP"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local_rank = rank_info()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2201_13240_gb300 as wos
+
+    ctx = wos.Context(local_rank)
+    desc = W.cube3d_problem()
+    prob = ctx.problem(desc)
+    sb, smin, smax = ctx.sigma_bar(prob, SIGMA_LATTICE)
+    pts_np = W.cell_centres(3, GRID)
+    npts = pts_np.shape[1]
+    pts = torch.from_numpy(pts_np).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    acc = ctx.new_accum(npts)
+    stats = ctx.new_stats()
+    mean = torch.empty(npts, dtype=torch.float64, device="cuda")
+    # disjoint walk ids per rank: the ranks' walks would merge into one estimate
+    offset = rank * WALKS
+
+    def step(seed):
+        for t in acc:
+            t.zero_()
+        ctx.solve(prob, pts, WALKS, EPS, sb, seed=seed, walk_offset=offset, accum=acc, stats=stats)
+        m, v, se = ctx.finalize(acc)
+        return m, se
+
+    for i in range(max(args.warmup, 0)):
+        step(SEED)
+    torch.cuda.synchronize()
+    stats.zero_()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))      # evict L2 between timed steps (outside the events)
+            ev[i][0].record(stream)
+            m, se = step(SEED)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(times)
+    st = wos.stats_dict(stats)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        s = torch.tensor([st["steps"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s)
+        all_steps = float(s.item())
+    else:
+        all_steps = float(st["steps"])
+    value = all_steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    steps_per_walk = st["steps"] / max(st["walks"], 1)
+
+    # accuracy of the last estimate against the manufactured solution
+    exact = W.cube3d_exact(*pts_np.astype(np.float64))
+    m_np = m.cpu().numpy()
+    rms = float(np.linalg.norm(m_np - exact) / np.linalg.norm(exact))
+    se_np = se.cpu().numpy()
+    # walks per point for normalised RMS 1e-2 (noise part scales as 1/sqrt(N))
+    noise = float(np.sqrt(np.mean(se_np ** 2)) / np.sqrt(np.mean(exact ** 2)))
+    walks_for_1e2 = int(math.ceil(WALKS * (noise / 1e-2) ** 2))
+
+    # end to end through the C interface with HOST buffers (copies inside the timed region)
+    pin_pts = torch.from_numpy(pts_np).pin_memory()
+    out = (torch.empty(npts, dtype=torch.float64).pin_memory(), torch.empty(npts, dtype=torch.float64).pin_memory(),
+           torch.empty(npts, dtype=torch.float64).pin_memory(), torch.zeros(5, dtype=torch.int64).pin_memory())
+    e2e_steps = 0
+    ctx.solve_host(prob, pin_pts, WALKS, EPS, sb, seed=SEED, walk_offset=offset, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ctx.solve_host(prob, pin_pts, WALKS, EPS, sb, seed=SEED, walk_offset=offset, out=out)
+        e2e_steps += int(out[3][0])
+    e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+        e2e_steps *= world
+    e2e = {"value": e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * npts,
+           "d2h_bytes_per_step": 3 * 8 * npts + 5 * 8}
+
+    # roofline of the walk kernel (ALU bound): algorithmic issue slots / kernel time
+    props = torch.cuda.get_device_properties(local_rank)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = 128 * props.multi_processor_count * sm_max * 1e6
+    # kernel time: the solve dominates the step; finalize and memsets are timed separately below
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fe0.record(stream)
+    for _ in range(5):
+        ctx.finalize(acc)
+    fe1.record(stream)
+    torch.cuda.synchronize()
+    finalize_ms = fe0.elapsed_time(fe1) / 5
+    kernel_ms = ms_per_step - finalize_ms
+    achieved = OPS_PER_STEP * (st["steps"] / args.steps) / (kernel_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "wos_walk_kernel<3,float>", "ops_per_step": OPS_PER_STEP,
+                "peak_basis": f"128 FP32/INT32 lanes x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
+                              "(sm_max_mhz of MEASURED_PEAKS.json)"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # CPU baseline: the oracle on a bounded sample on this host's cores
+    cpu_pts = 512
+    o_steps, o_t = oracle_rate(desc, sb, cpu_pts, WALKS, seed=SEED)
+    cpu = {"value": o_steps / o_t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{cpu_pts} seeded points of the workload x {WALKS} walks, FP64 oracle, OpenMP, "
+                     f"{o_t:.1f} s"}
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"sigma_bar": sb, "parallelism": f"points replicated, disjoint walk ids, "
+                                                                        f"{world} GPU(s)"}),
+            "points_per_s": world * npts / (ms_per_step * 1e-3),
+            "walks_per_s": world * npts * WALKS / (ms_per_step * 1e-3),
+            "steps_per_walk": steps_per_walk, "normalised_rms_at_1024_walks": rms,
+            "walks_per_point_for_rms_1e-2": walks_for_1e2,
+            "points_per_s_at_rms_1e-2": world * npts / (ms_per_step * 1e-3) * WALKS / max(walks_for_1e2, 1),
+            "capped_walks": st["capped"], "nonfinite_walks": st["nonfinite"],
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * wos.h -- C interface of the GB300 delta-tracking walk-on-spheres library.
+ *
+ * The library estimates, at user-given points, the solution of the linear
+ * elliptic PDE of Sawhney, Seyb, Jarosz, Crane, "Grid-Free Monte Carlo for PDEs
+ * with Spatially Varying Coefficients" (SIGGRAPH 2022), Sec. 3 eq. 1:
+ *
+ *     div(alpha grad u) + omega . grad u - sigma u = -f   in Omega,
+ *     u = g                                               on the boundary,
+ *
+ * with alpha > 0, omega = alpha grad(Phi) (a drift the paper removes exactly,
+ * App. A), by independent random walks of the delta-tracking walk on spheres
+ * (Sec. 5.1, eq. 11; Supplemental Algorithm 1) on the transformed screened
+ * Poisson equation Lap U - sigma_bar U = -(f' + (sigma_bar - sigma') U) with
+ * U = e^gamma u, gamma = (ln alpha + Phi)/2 (Sec. 4.1, eq. 7-8).
+ *
+ * Conventions
+ *   - Every call returns an int status: WOS_OK (0) or a negative WOS_E* code.
+ *     No C++ exception crosses this interface.  wos_last_error() returns a
+ *     message for the last failure on a context (valid until the next call).
+ *   - Arrays marked "device" are CUDA device pointers owned by the caller;
+ *     arrays marked "host" are host pointers owned by the caller.  Opaque
+ *     handles (wos_ctx, wos_problem) are owned by the library and freed by
+ *     their destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device-pointer calls are asynchronous on that stream unless
+ *     stated otherwise.
+ *   - Points are SoA float32: x coordinates of all points, then y, then z.
+ *   - Randomness: Philox4x32-10 with key = (seed low word, seed high word) and
+ *     counter = (point index, walk id, step, block); walk ids of one call are
+ *     walk_offset .. walk_offset + walks - 1, so a later call with a larger
+ *     walk_offset continues the same streams (the accumulators are the
+ *     checkpoint state).
+ */
+#ifndef WOS_H
+#define WOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define WOS_OK 0
+#define WOS_EINVAL (-1)       /* invalid argument or problem description */
+#define WOS_ENOMEM (-2)       /* device or host allocation failed */
+#define WOS_ECUDA (-3)        /* a CUDA runtime call failed (message has details) */
+#define WOS_ETIMEOUT (-4)     /* reserved: a bounded device wait gave up */
+#define WOS_EUNSUPPORTED (-5) /* valid request this build does not handle */
+
+/* ---- statistics words (device uint64 array of WOS_STATS_WORDS, added to) ---- */
+#define WOS_STAT_STEPS 0     /* walk steps: distance query + Green's sample */
+#define WOS_STAT_WALKS 1     /* finished walks */
+#define WOS_STAT_CAPPED 2    /* walks stopped by max_steps (biased; should be 0) */
+#define WOS_STAT_NONFINITE 3 /* walks whose estimate is not finite */
+#define WOS_STAT_OUTSIDE 4   /* walks started at a point with distance <= 0 */
+#define WOS_STATS_WORDS 5
+
+/* ---- problem description ---- */
+
+/* atom h(t), t = k x_i + phi, of a separable term */
+enum {
+  WOS_ATOM_ONE = 0, WOS_ATOM_SIN = 1, WOS_ATOM_COS = 2, WOS_ATOM_EXP = 3,
+  WOS_ATOM_SINH = 4, WOS_ATOM_COSH = 5, WOS_ATOM_LIN = 6 /* t */, WOS_ATOM_QUAD = 7 /* t^2 */
+};
+
+/* one separable term: c * prod_{i < dim} h_{type[i]}(k[i] * x_i + phi[i]) */
+typedef struct {
+  double c;
+  int32_t type[3];
+  double k[3];
+  double phi[3];
+} wos_term;
+
+enum {
+  WOS_FIELD_ZERO = 0,
+  WOS_FIELD_CONST = 1,        /* value */
+  WOS_FIELD_SST = 2,          /* sum of nterms separable terms (host array, copied) */
+  WOS_FIELD_MANUFACTURED = 3, /* source only: f = -div(alpha grad um) - omega.grad um + sigma um */
+  WOS_FIELD_GRID_LINEAR = 4,  /* node grid, multilinear interpolation (C^0) */
+  WOS_FIELD_GRID_BSPLINE = 5  /* node values as control points of a uniform cubic B-spline (C^2) */
+};
+
+/* A scalar field.  Grids: res[i] nodes on [lo[i], hi[i]] (node j at lo + j (hi-lo)/(res-1)),
+   float32 values with x fastest, in DEVICE memory owned by the caller, which must keep
+   them alive while the problem exists.  Linear grids clamp points to the box; B-spline
+   grids clamp control indices (constant extension).  Fields differentiated by the
+   method (alpha and Phi: value, gradient, Laplacian) must be CONST, SST or GRID_BSPLINE. */
+typedef struct {
+  int32_t kind;
+  int32_t nterms;
+  const wos_term* terms; /* host */
+  double value;
+  int32_t res[3];
+  double lo[3];
+  double hi[3];
+  const float* data; /* device */
+} wos_field_desc;
+
+enum {
+  WOS_DOMAIN_BOX = 0,        /* p[0..2] lower corner, p[3..5] upper corner */
+  WOS_DOMAIN_BALL = 1,       /* p[0..2] centre, p[3] radius (a disk in 2D) */
+  WOS_DOMAIN_ANNULUS = 2,    /* p[0..2] centre, p[3] inner radius, p[4] outer radius */
+  WOS_DOMAIN_ROUNDED_BOX = 3 /* p[0..2] centre, p[3..5] half extents, p[6] corner radius */
+};
+
+typedef struct {
+  int32_t kind;
+  double p[16];
+} wos_domain_desc;
+
+/* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift
+   potential (omega = alpha grad phi, App. A), sigma (screening), f (source),
+   g (Dirichlet data, read at the closest boundary point), um (the manufactured
+   solution used when f.kind == WOS_FIELD_MANUFACTURED, else ignored). */
+typedef struct {
+  int32_t dim; /* 2 or 3 */
+  wos_domain_desc domain;
+  wos_field_desc alpha, phi, sigma, f, g, um;
+} wos_problem_desc;
+
+enum { WOS_FP32 = 0, WOS_FP64 = 1 };
+
+/* Parameters of one solve.
+   eps:        epsilon-shell width (Sec. 2.1 notation; Alg. 1 stops when d < eps), > 0.
+   sigma_bar:  delta-tracking bound (Sec. 5.1), > 0; any positive value is unbiased.
+   seed:       Philox key.
+   walk_offset: walk id of the first walk of every point.
+   max_steps:  step cap per walk (capped walks are counted, not hidden), >= 1.
+   precision:  WOS_FP32 walk state (production) or WOS_FP64 (replays the FP64
+               reference arithmetic on the same random streams). */
+typedef struct {
+  double eps;
+  double sigma_bar;
+  uint64_t seed;
+  uint64_t walk_offset;
+  int64_t max_steps;
+  int32_t precision;
+  int32_t reserved;
+} wos_params;
+
+typedef struct wos_ctx wos_ctx;
+typedef struct wos_problem wos_problem;
+
+/* Create a context on CUDA device `device` (allocates a small scratch buffer).
+   Errors: WOS_EINVAL (null out pointer), WOS_ECUDA (device not usable). */
+int wos_create(wos_ctx** ctx, int device);
+/* Free the context and its scratch; problems must be destroyed first. */
+int wos_destroy(wos_ctx* ctx);
+/* Message of the last failure on ctx ("" if none); never NULL. */
+const char* wos_last_error(const wos_ctx* ctx);
+/* Library version string. */
+const char* wos_version(void);
+
+/* Validate and upload a problem (Sec. 3 eq. 1).  Copies the description; grid data
+   stays with the caller.  Errors: WOS_EINVAL (bad dim, kind, term count, grid size,
+   null grid data, alpha/phi given as linear grids), WOS_ENOMEM, WOS_ECUDA. */
+int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* desc, wos_problem** prob);
+int wos_problem_destroy(wos_problem* prob);
+
+/* The delta-tracking bound (Sec. 5.1, Sec. 7.1: the paper's default is
+   max sigma' - min sigma'): sigma' is sampled at the interior nodes of an
+   m^dim lattice of cell centres over the domain's bounding box; returns (host)
+   sigma_bar = max(max - min, max, 1e-3 / diam^2), min sigma' and max sigma'.
+   Synchronises `stream`.  Errors: WOS_EINVAL if m < 2 or alpha <= 0 at a node. */
+int wos_sigma_bar(wos_ctx* ctx, const wos_problem* prob, int32_t m, double* sigma_bar,
+                  double* sigma_prime_min, double* sigma_prime_max, void* stream);
+
+/* Run walks and ADD their estimates to per-point FP64 accumulators.
+   pts:    device float32 SoA [dim][npts].
+   walks:  device int32 [npts] walks per point, or NULL to use walks_uniform.
+   sum, sumsq: device double [npts]; count: device int64 [npts] (zero them to start).
+   stats:  device uint64 [WOS_STATS_WORDS] added to, or NULL.
+   npts == 0 or zero walks is a no-op.  Points within eps of the boundary return
+   g at the closest point (Alg. 1).  Errors: WOS_EINVAL (null pointers, eps or
+   sigma_bar not > 0 and finite, max_steps < 1, walks per point > 2^32), WOS_ECUDA. */
+int wos_solve(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+              const int32_t* walks, int32_t walks_uniform, const wos_params* params,
+              double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream);
+
+/* As wos_solve with walks_per_point walks per point, also writing every walk's
+   estimate uhat[p * walks_per_point + j] and step count steps[...] (device
+   arrays of npts * walks_per_point).  For tests and custom estimators. */
+int wos_walk_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                       int32_t walks_per_point, const wos_params* params, double* uhat,
+                       int64_t* steps, uint64_t* stats, void* stream);
+
+/* Per-point mean, unbiased sample variance of one walk's estimate, and standard
+   error of the mean from the accumulators (Sec. 2.2: the estimate is the average
+   of single-sample estimates).  All device arrays of npts; any output may be NULL. */
+int wos_finalize(wos_ctx* ctx, const double* sum, const double* sumsq, const int64_t* count,
+                 int64_t npts, double* mean, double* var, double* stderr_out, void* stream);
+
+/* End-to-end convenience: HOST points in, HOST mean / variance / stderr out (and
+   HOST stats if non-NULL).  Copies the inputs to device buffers owned by the
+   context (grown as needed), runs wos_solve on fresh accumulators and
+   wos_finalize, copies the results back and synchronises `stream`. */
+int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host, int64_t npts,
+                   int32_t walks_uniform, const wos_params* params, double* mean_host,
+                   double* var_host, double* stderr_host, uint64_t* stats_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WOS_H */

@@ -645,10 +645,11 @@ double orc_green_inv(int dim, double R, double sb, double u) {
   for (int it = 0; it < 200; ++it) {
     double F = (dim == 2) ? cdf2(a, rho) : cdf3(a, rho);
     double fres = F - u;
+    if (fres == 0.0) break;
     if (fres > 0.0) hi = rho; else lo = rho;
     double p = (dim == 2) ? pdf2(a, rho) : pdf3(a, rho);
     double nr = (p > 0.0) ? rho - fres / p : 0.5 * (lo + hi);
-    if (!(nr > lo && nr < hi)) nr = 0.5 * (lo + hi);
+    if (!(nr >= lo && nr <= hi)) nr = 0.5 * (lo + hi);
     double step = std::fabs(nr - rho);
     rho = nr;
     if (step < 1e-16 || hi - lo < 1e-16) break;

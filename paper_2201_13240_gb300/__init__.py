@@ -1,0 +1,279 @@
+"""GB300 delta-tracking walk on spheres for variable-coefficient elliptic PDEs.
+
+Thin Python binding of the C interface in ``include/wos.h`` (the library
+``libwos.so`` built in-tree by ``paper_2201_13240_gb300.build``).  Every step of
+a solve runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch provides device memory and the current stream.
+
+It estimates the solution of Sawhney et al. 2022, Sec. 3 eq. 1,
+``div(alpha grad u) + omega.grad u - sigma u = -f`` (u = g on the boundary,
+omega = alpha grad Phi) with the delta-tracking walk on spheres (Sec. 5.1).
+Problems are the plain dicts produced by the ``workloads`` module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwos.so")
+
+WOS_OK, WOS_EINVAL, WOS_ENOMEM, WOS_ECUDA, WOS_ETIMEOUT, WOS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+WOS_FP32, WOS_FP64 = 0, 1
+STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
+STATS_WORDS = 5
+_FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
+_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3}
+
+
+class WosError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"wos error {code}: {msg}")
+        self.code = code
+
+
+class Term(C.Structure):
+    _fields_ = [("c", C.c_double), ("type", C.c_int32 * 3), ("k", C.c_double * 3), ("phi", C.c_double * 3)]
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nterms", C.c_int32), ("terms", C.POINTER(Term)), ("value", C.c_double),
+                ("res", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("data", C.c_void_p)]
+
+
+class DomainDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16)]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("domain", DomainDesc), ("alpha", FieldDesc), ("phi", FieldDesc),
+                ("sigma", FieldDesc), ("f", FieldDesc), ("g", FieldDesc), ("um", FieldDesc)]
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("sigma_bar", C.c_double), ("seed", C.c_uint64), ("walk_offset", C.c_uint64),
+                ("max_steps", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libwos.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2201_13240_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
+    lib.wos_create.argtypes = [C.POINTER(vp), C.c_int]
+    lib.wos_destroy.argtypes = [vp]
+    lib.wos_last_error.argtypes = [vp]
+    lib.wos_last_error.restype = C.c_char_p
+    lib.wos_version.restype = C.c_char_p
+    lib.wos_problem_create.argtypes = [vp, C.POINTER(ProblemDesc), C.POINTER(vp)]
+    lib.wos_problem_destroy.argtypes = [vp]
+    lib.wos_sigma_bar.argtypes = [vp, vp, i32, dp, dp, dp, vp]
+    lib.wos_solve.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_walk_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
+    lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def params(eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32"):
+    p = Params()
+    p.eps = float(eps)
+    p.sigma_bar = float(sigma_bar)
+    p.seed = int(seed)
+    p.walk_offset = int(walk_offset)
+    p.max_steps = int(max_steps)
+    p.precision = WOS_FP64 if precision in ("fp64", WOS_FP64) else WOS_FP32
+    return p
+
+
+class Problem:
+    """A problem uploaded to the device (owns the library handle)."""
+
+    def __init__(self, ctx, desc):
+        import torch
+        self.ctx = ctx
+        self.dim = desc["dim"]
+        self._keep = []
+        D = ProblemDesc()
+        D.dim = desc["dim"]
+        D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
+        for i, v in enumerate(desc["domain"]["p"]):
+            D.domain.p[i] = v
+        for name in ("alpha", "phi", "sigma", "f", "g", "um"):
+            fd = desc[name]
+            F = getattr(D, name)
+            F.kind = _FIELD_KINDS[fd["kind"]]
+            F.value = fd.get("value", 0.0)
+            if fd["kind"] == "sst":
+                terms = (Term * max(1, len(fd["terms"])))()
+                for i, t in enumerate(fd["terms"]):
+                    terms[i].c = t["c"]
+                    for d, (ty, k, ph) in enumerate(t["atoms"]):
+                        terms[i].type[d], terms[i].k[d], terms[i].phi[d] = ty, k, ph
+                self._keep.append(terms)
+                F.nterms = len(fd["terms"])
+                F.terms = C.cast(terms, C.POINTER(Term))
+            if fd["kind"].startswith("grid"):
+                data = fd["data"]
+                if not isinstance(data, torch.Tensor):
+                    data = torch.as_tensor(np.ascontiguousarray(data, dtype=np.float32))
+                data = data.to(device=f"cuda:{ctx.device}", dtype=torch.float32).contiguous()
+                self._keep.append(data)
+                for d in range(3):
+                    F.res[d] = fd["res"][d] if d < len(fd["res"]) else 1
+                    F.lo[d] = fd["lo"][d] if d < len(fd["lo"]) else 0.0
+                    F.hi[d] = fd["hi"][d] if d < len(fd["hi"]) else 0.0
+                F.data = data.data_ptr()
+        h = C.c_void_p()
+        ctx._check(ctx.lib.wos_problem_create(ctx.handle, C.byref(D), C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.wos_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device=0):
+        import torch
+        self.lib = load()
+        self.device = int(device)
+        torch.cuda.init()
+        h = C.c_void_p()
+        rc = self.lib.wos_create(C.byref(h), self.device)
+        if rc != WOS_OK:
+            raise WosError(rc, "wos_create failed")
+        self.handle = h
+
+    def _check(self, rc):
+        if rc != WOS_OK:
+            raise WosError(rc, self.lib.wos_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wos_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- calls ----
+    def problem(self, desc):
+        return Problem(self, desc)
+
+    def sigma_bar(self, prob, m=None, stream=None):
+        if m is None:
+            m = 256 if prob.dim == 2 else 64
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.wos_sigma_bar(self.handle, prob.handle, int(m), C.byref(a), C.byref(b), C.byref(c),
+                                           _stream(stream)))
+        return a.value, b.value, c.value
+
+    def new_accum(self, npts):
+        import torch
+        dev = f"cuda:{self.device}"
+        return (torch.zeros(npts, dtype=torch.float64, device=dev), torch.zeros(npts, dtype=torch.float64, device=dev),
+                torch.zeros(npts, dtype=torch.int64, device=dev))
+
+    def new_stats(self):
+        import torch
+        # the library adds unsigned 64-bit words; counts stay far below 2^63
+        return torch.zeros(STATS_WORDS, dtype=torch.int64, device=f"cuda:{self.device}")
+
+    def solve(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32",
+              accum=None, stats=None, stream=None):
+        """Add walks to the accumulators (sum, sumsq, count); pts: cuda float32 [dim, npts]."""
+        import torch
+        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[0] == prob.dim
+        npts = pts.shape[1]
+        if accum is None:
+            accum = self.new_accum(npts)
+        if stats is None:
+            stats = self.new_stats()
+        if isinstance(walks, int):
+            wp, wu = None, walks
+        else:
+            assert walks.is_cuda and walks.dtype == torch.int32
+            wp, wu = _ptr(walks), 0
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
+                                       _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), _ptr(stats),
+                                       _stream(stream)))
+        return accum, stats
+
+    def walk_estimates(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
+                       precision="fp32", stream=None):
+        import torch
+        npts = pts.shape[1]
+        dev = f"cuda:{self.device}"
+        uhat = torch.empty((npts, walks_per_point), dtype=torch.float64, device=dev)
+        steps = torch.empty((npts, walks_per_point), dtype=torch.int64, device=dev)
+        stats = self.new_stats()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_walk_estimates(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
+                                                C.byref(p), _ptr(uhat), _ptr(steps), _ptr(stats), _stream(stream)))
+        return uhat, steps, stats
+
+    def finalize(self, accum, stream=None):
+        import torch
+        n = accum[0].shape[0]
+        mean, var, se = (torch.empty(n, dtype=torch.float64, device=accum[0].device) for _ in range(3))
+        self._check(self.lib.wos_finalize(self.handle, _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), n,
+                                          _ptr(mean), _ptr(var), _ptr(se), _stream(stream)))
+        return mean, var, se
+
+    def solve_host(self, prob, pts_host, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
+                   precision="fp32", out=None, stream=None):
+        """Host arrays in, host arrays out (copies inside the call).  pts_host: float32 [dim, npts]
+        numpy array or pinned torch tensor; out: optional (mean, var, se, stats) host buffers."""
+        import torch
+        if isinstance(pts_host, np.ndarray):
+            pts_host = torch.from_numpy(np.ascontiguousarray(pts_host, dtype=np.float32))
+        npts = pts_host.shape[1]
+        if out is None:
+            out = (torch.empty(npts, dtype=torch.float64), torch.empty(npts, dtype=torch.float64),
+                   torch.empty(npts, dtype=torch.float64), torch.zeros(STATS_WORDS, dtype=torch.int64))
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_host(self.handle, prob.handle, C.c_void_p(pts_host.data_ptr()), npts,
+                                            int(walks), C.byref(p), C.c_void_p(out[0].data_ptr()),
+                                            C.c_void_p(out[1].data_ptr()), C.c_void_p(out[2].data_ptr()),
+                                            C.c_void_p(out[3].data_ptr()), _stream(stream)))
+        return out
+
+
+def stats_dict(stats):
+    s = [int(v) for v in stats.cpu().tolist()]
+    return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4]}

@@ -1,0 +1,612 @@
+// wos_capi.cu -- implementation of the C interface declared in include/wos.h:
+// context and problem lifetime, validation, the sigma_bar prepass, the walk
+// launches, the finalize kernel and the host-buffer convenience entry point.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wos.h"
+#include "wos_internal.h"
+#include "wos_problem.cuh"
+
+using wos::DevField;
+using wos::DevProblem;
+using wos::DevTerm;
+
+struct wos_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  // scratch: [0] work counter, [8..8+ST_WORDS) default stats, [16..20) sigma-bar reduction
+  unsigned long long* scratch = nullptr;
+  // walks-per-point prefix sums
+  int64_t* walk_end = nullptr;
+  int64_t walk_end_cap = 0;
+  // buffers of wos_solve_host
+  float* h_pts = nullptr;
+  double* h_acc = nullptr;  // sum, sumsq, mean, var, se: 5 * cap doubles
+  int64_t* h_count = nullptr;
+  int64_t host_cap = 0;
+};
+
+struct wos_problem {
+  wos_ctx* ctx = nullptr;
+  int dim = 0;
+  DevProblem<float>* d32 = nullptr;
+  DevProblem<double>* d64 = nullptr;
+  DevProblem<double> host64;  // host copy for the sigma_bar lattice bounds
+};
+
+namespace {
+
+constexpr int kScratchWords = 64;
+constexpr int kScratchStats = 8;
+constexpr int kScratchSigma = 16;
+
+int fail(wos_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(wos_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, WOS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int check_field(const wos_field_desc& f, int dim, const char* name, bool is_source, bool needs_c2,
+                std::string* why) {
+  if (f.kind < WOS_FIELD_ZERO || f.kind > WOS_FIELD_GRID_BSPLINE) {
+    *why = std::string(name) + ": unknown field kind";
+    return WOS_EINVAL;
+  }
+  if (f.kind == WOS_FIELD_MANUFACTURED && !is_source) {
+    *why = std::string(name) + ": only the source may be MANUFACTURED";
+    return WOS_EINVAL;
+  }
+  if (needs_c2 && f.kind == WOS_FIELD_GRID_LINEAR) {
+    *why = std::string(name) + ": needs a Laplacian; use CONST, SST or GRID_BSPLINE";
+    return WOS_EINVAL;
+  }
+  if (f.kind == WOS_FIELD_SST) {
+    if (f.nterms < 0 || f.nterms > wos::kMaxTerms || (f.nterms > 0 && f.terms == nullptr)) {
+      *why = std::string(name) + ": bad term count or null terms";
+      return WOS_EINVAL;
+    }
+    for (int n = 0; n < f.nterms; ++n) {
+      const wos_term& t = f.terms[n];
+      if (!std::isfinite(t.c)) { *why = std::string(name) + ": non-finite coefficient"; return WOS_EINVAL; }
+      for (int d = 0; d < dim; ++d) {
+        if (t.type[d] < WOS_ATOM_ONE || t.type[d] > WOS_ATOM_QUAD || !std::isfinite(t.k[d]) ||
+            !std::isfinite(t.phi[d])) {
+          *why = std::string(name) + ": bad atom";
+          return WOS_EINVAL;
+        }
+      }
+    }
+  }
+  if (f.kind == WOS_FIELD_CONST && !std::isfinite(f.value)) {
+    *why = std::string(name) + ": non-finite constant";
+    return WOS_EINVAL;
+  }
+  if (f.kind == WOS_FIELD_GRID_LINEAR || f.kind == WOS_FIELD_GRID_BSPLINE) {
+    if (f.data == nullptr) { *why = std::string(name) + ": null grid data"; return WOS_EINVAL; }
+    for (int d = 0; d < dim; ++d) {
+      if (f.res[d] < 2 || !(f.hi[d] > f.lo[d]) || !std::isfinite(f.lo[d]) || !std::isfinite(f.hi[d])) {
+        *why = std::string(name) + ": grid needs res >= 2 and hi > lo on every axis";
+        return WOS_EINVAL;
+      }
+    }
+  }
+  return WOS_OK;
+}
+
+template <typename R>
+void fill_field(DevProblem<R>& P, DevField<R>& F, const wos_field_desc& f, int dim) {
+  std::memset(&F, 0, sizeof(F));
+  F.kind = f.kind;
+  F.value = R(f.value);
+  F.first = P.nterms;
+  if (f.kind == WOS_FIELD_SST) {
+    F.nterms = f.nterms;
+    for (int n = 0; n < f.nterms; ++n) {
+      DevTerm<R>& T = P.terms[P.nterms++];
+      T.c = R(f.terms[n].c);
+      for (int d = 0; d < 3; ++d) {
+        bool on = d < dim;
+        T.type[d] = on ? f.terms[n].type[d] : wos::A_ONE;
+        T.k[d] = on ? R(f.terms[n].k[d]) : R(0);
+        T.phi[d] = on ? R(f.terms[n].phi[d]) : R(0);
+      }
+    }
+  }
+  if (f.kind == WOS_FIELD_GRID_LINEAR || f.kind == WOS_FIELD_GRID_BSPLINE) {
+    for (int d = 0; d < 3; ++d) {
+      F.res[d] = d < dim ? f.res[d] : 1;
+      F.lo[d] = d < dim ? R(f.lo[d]) : R(0);
+      F.inv_h[d] = d < dim ? R((f.res[d] - 1) / (f.hi[d] - f.lo[d])) : R(0);
+    }
+    F.data = f.data;
+  }
+}
+
+template <typename R>
+void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
+  std::memset(&P, 0, sizeof(P));
+  P.dim = d.dim;
+  P.domain_kind = d.domain.kind;
+  for (int i = 0; i < 16; ++i) P.dom[i] = R(d.domain.p[i]);
+  fill_field(P, P.alpha, d.alpha, d.dim);
+  fill_field(P, P.phi, d.phi, d.dim);
+  fill_field(P, P.sigma, d.sigma, d.dim);
+  fill_field(P, P.f, d.f, d.dim);
+  fill_field(P, P.g, d.g, d.dim);
+  fill_field(P, P.um, d.um, d.dim);
+}
+
+void domain_bbox(const DevProblem<double>& P, double lo[3], double hi[3]) {
+  const double* p = P.dom;
+  for (int d = 0; d < 3; ++d) { lo[d] = 0.0; hi[d] = 0.0; }
+  for (int d = 0; d < P.dim; ++d) {
+    switch (P.domain_kind) {
+      case wos::D_BOX: lo[d] = p[d]; hi[d] = p[3 + d]; break;
+      case wos::D_BALL: lo[d] = p[d] - p[3]; hi[d] = p[d] + p[3]; break;
+      case wos::D_ANNULUS: lo[d] = p[d] - p[4]; hi[d] = p[d] + p[4]; break;
+      case wos::D_ROUNDED_BOX: lo[d] = p[d] - p[3 + d]; hi[d] = p[d] + p[3 + d]; break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernels: sigma' range on a lattice, prefix sums of walks, finalize
+// ---------------------------------------------------------------------------
+__device__ void atomic_min_d(double* addr, double v) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(addr);
+  unsigned long long old = *p;
+  for (int it = 0; it < (1 << 20) && v < __longlong_as_double(old); ++it) {
+    unsigned long long prev = atomicCAS(p, old, __double_as_longlong(v));
+    if (prev == old) break;
+    old = prev;
+  }
+}
+__device__ void atomic_max_d(double* addr, double v) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(addr);
+  unsigned long long old = *p;
+  for (int it = 0; it < (1 << 20) && v > __longlong_as_double(old); ++it) {
+    unsigned long long prev = atomicCAS(p, old, __double_as_longlong(v));
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
+template <int DIM>
+__global__ void sigma_range_kernel(const DevProblem<double>* Pg, int m, double lo0, double lo1, double lo2,
+                                   double h0, double h1, double h2, double* out /* min, max, alpha_min, count */) {
+  const DevProblem<double>& P = *Pg;
+  int64_t total = (DIM == 3) ? (int64_t)m * m * m : (int64_t)m * m;
+  double mn = INFINITY, mx = -INFINITY, amin = INFINITY, cnt = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double x[3] = {lo0 + (i % m + 0.5) * h0, lo1 + ((i / m) % m + 0.5) * h1,
+                   DIM == 3 ? lo2 + (i / ((int64_t)m * m) + 0.5) * h2 : 0.0};
+    double xb[3];
+    if (!(wos::distance<DIM>(P, x, xb) > 0.0)) continue;
+    double sp, fp;
+    wos::coeffs<DIM>(P, x, &sp, &fp);
+    double a, g[3], l;
+    wos::field_eval<DIM>(P, P.alpha, x, &a, g, &l, false);
+    mn = fmin(mn, sp);
+    mx = fmax(mx, sp);
+    amin = fmin(amin, a);
+    cnt += 1.0;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, off));
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    amin = fmin(amin, __shfl_down_sync(0xffffffffu, amin, off));
+    cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+    atomic_min_d(&out[0], mn);
+    atomic_max_d(&out[1], mx);
+    atomic_min_d(&out[2], amin);
+    atomicAdd(&out[3], cnt);
+  }
+}
+
+// inclusive prefix sums of max(walks, 0): one block, sequential over tiles of 1024
+__global__ void walk_prefix_kernel(const int32_t* walks, int64_t n, int64_t* out) {
+  __shared__ int64_t tile[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 1024) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = (i < n) ? (int64_t)max(walks[i], 0) : 0;
+    tile[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int64_t add = (threadIdx.x >= (unsigned)off) ? tile[threadIdx.x - off] : 0;
+      __syncthreads();
+      tile[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < n) out[i] = tile[threadIdx.x] + carry;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += tile[1023];
+    __syncthreads();
+  }
+}
+
+__global__ void finalize_kernel(const double* sum, const double* sumsq, const int64_t* count, int64_t n,
+                                double* mean, double* var, double* se) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double c = (double)count[i];
+    double m = sum[i] / c;
+    double v = (sumsq[i] - c * m * m) / fmax(c - 1.0, 1.0);
+    v = fmax(v, 0.0);
+    if (mean) mean[i] = m;
+    if (var) var[i] = v;
+    if (se) se[i] = sqrt(v / c);
+  }
+}
+
+int validate_params(wos_ctx* ctx, const wos_params* prm) {
+  if (!prm) return fail(ctx, WOS_EINVAL, "params is NULL");
+  if (!finite_pos(prm->eps)) return fail(ctx, WOS_EINVAL, "eps must be finite and > 0");
+  if (!finite_pos(prm->sigma_bar)) return fail(ctx, WOS_EINVAL, "sigma_bar must be finite and > 0");
+  if (prm->max_steps < 1) return fail(ctx, WOS_EINVAL, "max_steps must be >= 1");
+  if (prm->precision != WOS_FP32 && prm->precision != WOS_FP64)
+    return fail(ctx, WOS_EINVAL, "precision must be WOS_FP32 or WOS_FP64");
+  return WOS_OK;
+}
+
+int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, const int64_t* walk_end,
+           int64_t walks_uniform, uint64_t total, const wos_params* prm, double* sum, double* sumsq,
+           int64_t* count, uint64_t* stats, double* uhat, int64_t* steps, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
+  unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
+  if (st_ptr == nullptr) {
+    st_ptr = ctx->scratch + kScratchStats;
+    e = cudaMemsetAsync(st_ptr, 0, wos::ST_WORDS * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(stats)");
+  }
+  wos::WalkLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.dim = prob->dim;
+  L.pts = pts;
+  L.npts = npts;
+  L.walk_end = walk_end;
+  L.walks_uniform = walks_uniform;
+  L.total_items = total;
+  L.seed = prm->seed;
+  L.walk_offset = prm->walk_offset;
+  L.eps = prm->eps;
+  L.sigma_bar = prm->sigma_bar;
+  L.max_steps = prm->max_steps;
+  L.sum = sum;
+  L.sumsq = sumsq;
+  L.count = reinterpret_cast<unsigned long long*>(count);
+  L.stats = st_ptr;
+  L.work_counter = ctx->scratch;
+  L.uhat = uhat;
+  L.steps_out = steps;
+  if (prm->precision == WOS_FP64) {
+    L.problem = prob->d64;
+    L.problem_bytes = (int)sizeof(DevProblem<double>);
+    e = wos::launch_walks_f64(L, ctx->num_sms, st);
+  } else {
+    L.problem = prob->d32;
+    L.problem_bytes = (int)sizeof(DevProblem<float>);
+    e = wos::launch_walks_f32(L, ctx->num_sms, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "walk kernel launch");
+  return WOS_OK;
+}
+
+template <typename T>
+int grow(wos_ctx* ctx, T** buf, int64_t n, int64_t* cap, int64_t need) {
+  if (need <= *cap) return WOS_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), sizeof(T) * (size_t)(n > 0 ? n : 1));
+  if (e != cudaSuccess) return fail(ctx, WOS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  *cap = need;
+  return WOS_OK;
+}
+
+}  // namespace
+
+static_assert(sizeof(DevProblem<float>) % 16 == 0, "problem size must be a multiple of 16 bytes");
+static_assert(sizeof(DevProblem<double>) % 16 == 0, "problem size must be a multiple of 16 bytes");
+
+extern "C" {
+
+const char* wos_version(void) { return "wos-gb300 0.1 (sm_103a)"; }
+
+int wos_create(wos_ctx** out, int device) {
+  if (!out) return WOS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return WOS_ECUDA;
+  wos_ctx* ctx = new wos_ctx();
+  ctx->device = device;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return WOS_ECUDA;
+  }
+  ctx->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&ctx->scratch, kScratchWords * sizeof(unsigned long long)) != cudaSuccess) {
+    delete ctx;
+    return WOS_ENOMEM;
+  }
+  cudaMemset(ctx->scratch, 0, kScratchWords * sizeof(unsigned long long));
+  *out = ctx;
+  return WOS_OK;
+}
+
+int wos_destroy(wos_ctx* ctx) {
+  if (!ctx) return WOS_EINVAL;
+  {
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->scratch);
+    if (ctx->walk_end) cudaFree(ctx->walk_end);
+    if (ctx->h_pts) cudaFree(ctx->h_pts);
+    if (ctx->h_acc) cudaFree(ctx->h_acc);
+    if (ctx->h_count) cudaFree(ctx->h_count);
+  }
+  delete ctx;
+  return WOS_OK;
+}
+
+const char* wos_last_error(const wos_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** out) {
+  if (!ctx) return WOS_EINVAL;
+  if (!d || !out) return fail(ctx, WOS_EINVAL, "null description or output");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(ctx, WOS_EINVAL, "dim must be 2 or 3");
+  const double* p = d->domain.p;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(p[i])) return fail(ctx, WOS_EINVAL, "non-finite domain parameter");
+  switch (d->domain.kind) {
+    case WOS_DOMAIN_BOX:
+      for (int i = 0; i < d->dim; ++i)
+        if (!(p[3 + i] > p[i])) return fail(ctx, WOS_EINVAL, "box: hi must exceed lo");
+      break;
+    case WOS_DOMAIN_BALL:
+      if (!(p[3] > 0)) return fail(ctx, WOS_EINVAL, "ball: radius must be > 0");
+      break;
+    case WOS_DOMAIN_ANNULUS:
+      if (!(p[3] >= 0 && p[4] > p[3])) return fail(ctx, WOS_EINVAL, "annulus: need 0 <= r_in < r_out");
+      break;
+    case WOS_DOMAIN_ROUNDED_BOX:
+      for (int i = 0; i < d->dim; ++i)
+        if (!(p[3 + i] > 0 && p[6] >= 0 && p[6] <= p[3 + i]))
+          return fail(ctx, WOS_EINVAL, "rounded box: need half extents > 0 and 0 <= corner <= half");
+      break;
+    default:
+      return fail(ctx, WOS_EINVAL, "unknown domain kind");
+  }
+  std::string why;
+  struct { const wos_field_desc* f; const char* n; bool src; bool c2; } fl[6] = {
+      {&d->alpha, "alpha", false, true}, {&d->phi, "phi", false, true}, {&d->sigma, "sigma", false, false},
+      {&d->f, "f", true, false},         {&d->g, "g", false, false},    {&d->um, "um", false, true}};
+  int total_terms = 0;
+  for (auto& x : fl) {
+    if (check_field(*x.f, d->dim, x.n, x.src, x.c2, &why) != WOS_OK) return fail(ctx, WOS_EINVAL, why);
+    if (x.f->kind == WOS_FIELD_SST) total_terms += x.f->nterms;
+  }
+  if (d->alpha.kind == WOS_FIELD_ZERO) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
+  if (d->alpha.kind == WOS_FIELD_CONST && !(d->alpha.value > 0)) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
+  if (total_terms > wos::kMaxTerms) return fail(ctx, WOS_EINVAL, "more than 96 separable terms in total");
+
+  wos_problem* pr = new wos_problem();
+  pr->ctx = ctx;
+  pr->dim = d->dim;
+  DevProblem<float>* h32 = new DevProblem<float>();
+  fill_problem(*h32, *d);
+  fill_problem(pr->host64, *d);
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaMalloc(&pr->d32, sizeof(DevProblem<float>));
+  if (e == cudaSuccess) e = cudaMalloc(&pr->d64, sizeof(DevProblem<double>));
+  if (e == cudaSuccess) e = cudaMemcpy(pr->d32, h32, sizeof(DevProblem<float>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
+  delete h32;
+  if (e != cudaSuccess) {
+    if (pr->d32) cudaFree(pr->d32);
+    if (pr->d64) cudaFree(pr->d64);
+    delete pr;
+    return cuda_fail(ctx, e, "problem upload");
+  }
+  *out = pr;
+  return WOS_OK;
+}
+
+int wos_problem_destroy(wos_problem* pr) {
+  if (!pr) return WOS_EINVAL;
+  {
+    DeviceGuard g(pr->ctx->device);
+    cudaFree(pr->d32);
+    cudaFree(pr->d64);
+  }
+  delete pr;
+  return WOS_OK;
+}
+
+int wos_sigma_bar(wos_ctx* ctx, const wos_problem* pr, int32_t m, double* sb, double* smin, double* smax,
+                  void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr || !sb) return fail(ctx, WOS_EINVAL, "null problem or output");
+  if (m < 2 || (pr->dim == 3 && m > 2048) || m > 1 << 16) return fail(ctx, WOS_EINVAL, "lattice size out of range");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double init[4] = {INFINITY, -INFINITY, INFINITY, 0.0};
+  double* out = reinterpret_cast<double*>(ctx->scratch + kScratchSigma);
+  cudaError_t e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar init");
+  double lo[3], hi[3];
+  domain_bbox(pr->host64, lo, hi);
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (hi[d] - lo[d]) / m;
+  int blocks = ctx->num_sms * 4;
+  if (pr->dim == 2)
+    sigma_range_kernel<2><<<blocks, 256, 0, st>>>(pr->d64, m, lo[0], lo[1], lo[2], h[0], h[1], h[2], out);
+  else
+    sigma_range_kernel<3><<<blocks, 256, 0, st>>>(pr->d64, m, lo[0], lo[1], lo[2], h[0], h[1], h[2], out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar kernel");
+  double res[4];
+  e = cudaMemcpyAsync(res, out, sizeof(res), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar readback");
+  if (!(res[3] > 0)) return fail(ctx, WOS_EINVAL, "no lattice node lies inside the domain");
+  if (!(res[2] > 0)) return fail(ctx, WOS_EINVAL, "alpha <= 0 at a lattice node");
+  if (!std::isfinite(res[0]) || !std::isfinite(res[1])) return fail(ctx, WOS_EINVAL, "sigma' is not finite");
+  double diam2 = 0.0;
+  for (int d = 0; d < pr->dim; ++d) diam2 += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+  double v = res[1] - res[0];
+  if (res[1] > v) v = res[1];
+  if (1e-3 / diam2 > v) v = 1e-3 / diam2;
+  *sb = v;
+  if (smin) *smin = res[0];
+  if (smax) *smax = res[1];
+  return WOS_OK;
+}
+
+int wos_solve(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, const int32_t* walks,
+              int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq, int64_t* count,
+              uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if (npts < 0) return fail(ctx, WOS_EINVAL, "npts < 0");
+  if (npts == 0) return WOS_OK;
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
+  if (!pts || !sum || !sumsq || !count) return fail(ctx, WOS_EINVAL, "null device array");
+  if (!walks && walks_uniform < 0) return fail(ctx, WOS_EINVAL, "walks_uniform < 0");
+  if (!walks && walks_uniform == 0) return WOS_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t* walk_end = nullptr;
+  uint64_t total;
+  if (walks) {
+    rc = grow(ctx, &ctx->walk_end, npts, &ctx->walk_end_cap, npts);
+    if (rc) return rc;
+    walk_prefix_kernel<<<1, 1024, 0, st>>>(walks, npts, ctx->walk_end);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "walk prefix kernel");
+    walk_end = ctx->walk_end;
+    // the kernel reads the total from the last prefix entry; bound it by 2^31 per point
+    total = ~0ull;
+  } else {
+    total = (uint64_t)npts * (uint64_t)walks_uniform;
+  }
+  return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
+                nullptr, st);
+}
+
+int wos_walk_estimates(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,
+                       const wos_params* prm, double* uhat, int64_t* steps, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if (npts < 0 || wpp < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts == 0 || wpp == 0) return WOS_OK;
+  if (!pts || !uhat || !steps) return fail(ctx, WOS_EINVAL, "null device array");
+  DeviceGuard g(ctx->device);
+  return launch(ctx, pr, pts, npts, nullptr, wpp, (uint64_t)npts * (uint64_t)wpp, prm, nullptr, nullptr,
+                nullptr, stats, uhat, steps, static_cast<cudaStream_t>(stream));
+}
+
+int wos_finalize(wos_ctx* ctx, const double* sum, const double* sumsq, const int64_t* count, int64_t npts,
+                 double* mean, double* var, double* se, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (npts < 0) return fail(ctx, WOS_EINVAL, "npts < 0");
+  if (npts == 0) return WOS_OK;
+  if (!sum || !sumsq || !count) return fail(ctx, WOS_EINVAL, "null accumulator");
+  DeviceGuard g(ctx->device);
+  int64_t blocks = (npts + 255) / 256;
+  if (blocks > ctx->num_sms * 32) blocks = ctx->num_sms * 32;
+  finalize_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(sum, sumsq, count, npts, mean,
+                                                                                   var, se);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "finalize kernel");
+  return WOS_OK;
+}
+
+int wos_solve_host(wos_ctx* ctx, const wos_problem* pr, const float* pts_host, int64_t npts, int32_t walks_uniform,
+                   const wos_params* prm, double* mean_host, double* var_host, double* se_host,
+                   uint64_t* stats_host, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if (npts < 0 || walks_uniform < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts == 0) return WOS_OK;
+  if (!pts_host) return fail(ctx, WOS_EINVAL, "null host points");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (npts > ctx->host_cap) {
+    int64_t c1 = 0, c2 = 0, c3 = 0;
+    if (ctx->h_pts) cudaFree(ctx->h_pts);
+    if (ctx->h_acc) cudaFree(ctx->h_acc);
+    if (ctx->h_count) cudaFree(ctx->h_count);
+    ctx->h_pts = nullptr;
+    ctx->h_acc = nullptr;
+    ctx->h_count = nullptr;
+    ctx->host_cap = 0;
+    if ((rc = grow(ctx, &ctx->h_pts, 3 * npts, &c1, 1))) return rc;
+    if ((rc = grow(ctx, &ctx->h_acc, 5 * npts, &c2, 1))) return rc;
+    if ((rc = grow(ctx, &ctx->h_count, npts, &c3, 1))) return rc;
+    ctx->host_cap = npts;
+  }
+  double* d_sum = ctx->h_acc;
+  double* d_sumsq = d_sum + npts;
+  double* d_mean = d_sumsq + npts;
+  double* d_var = d_mean + npts;
+  double* d_se = d_var + npts;
+  unsigned long long* d_stats = ctx->scratch + kScratchStats;
+  cudaError_t e = cudaMemcpyAsync(ctx->h_pts, pts_host, sizeof(float) * pr->dim * npts, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, 2 * sizeof(double) * npts, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->h_count, 0, sizeof(int64_t) * npts, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_stats, 0, wos::ST_WORDS * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host solve staging");
+  rc = wos_solve(ctx, pr, ctx->h_pts, npts, nullptr, walks_uniform, prm, d_sum, d_sumsq, ctx->h_count,
+                 reinterpret_cast<uint64_t*>(d_stats), stream);
+  if (rc) return rc;
+  rc = wos_finalize(ctx, d_sum, d_sumsq, ctx->h_count, npts, d_mean, d_var, d_se, stream);
+  if (rc) return rc;
+  if (mean_host) e = cudaMemcpyAsync(mean_host, d_mean, sizeof(double) * npts, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && var_host) e = cudaMemcpyAsync(var_host, d_var, sizeof(double) * npts, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && se_host) e = cudaMemcpyAsync(se_host, d_se, sizeof(double) * npts, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && stats_host)
+    e = cudaMemcpyAsync(stats_host, d_stats, wos::ST_WORDS * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host solve readback");
+  return WOS_OK;
+}
+
+}  // extern "C"

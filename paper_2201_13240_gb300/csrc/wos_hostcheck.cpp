@@ -1,0 +1,93 @@
+// wos_hostcheck.cpp -- host build of the device step math, for CPU-side checks.
+//
+// Compiled with a plain C++ compiler from the same header the kernels use, so
+// the FP32 and FP64 Green's-function sampling, Bessel approximations and the
+// Philox stream can be compared with independent references without a GPU.
+// It is a test aid of the product library and never part of a solve.
+#include <stdint.h>
+
+#include "wos_math.cuh"
+
+extern "C" {
+
+// which: 0 I0, 1 I1, 2 K0, 3 K1
+void wos_hc_bessel_f32(int which, const double* x, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    float v = (float)x[i], r = 0.0f;
+    switch (which) {
+      case 0: r = (v <= 3.75f) ? wos::as_i0_small(v) : wos::as_i0s_large(v) * expf(v); break;
+      case 1: r = (v <= 3.75f) ? wos::as_i1_small(v) : wos::as_i1s_large(v) * expf(v); break;
+      case 2:
+        r = (v <= 2.0f) ? wos::as_k0_poly(v) - logf(0.5f * v) * wos::as_i0_small(v)
+                        : wos::as_k0s_large(v) * expf(-v);
+        break;
+      case 3:
+        r = (v <= 2.0f) ? (1.0f + wos::as_k1_poly(v) + v * logf(0.5f * v) * wos::as_i1_small(v)) / v
+                        : wos::as_k1s_large(v) * expf(-v);
+        break;
+    }
+    out[i] = r;
+  }
+}
+
+void wos_hc_bessel_f64(int which, const double* x, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double v = x[i];
+    switch (which) {
+      case 0: out[i] = wos::d_i0(v); break;
+      case 1: out[i] = wos::d_i1(v); break;
+      case 2: out[i] = wos::d_k0(v); break;
+      case 3: out[i] = wos::d_k1(v); break;
+    }
+  }
+}
+
+// |G| / R^2 = q(a)
+void wos_hc_green_q(int dim, int fp64, const double* a, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) out[i] = (dim == 2) ? wos::green_q2(a[i]) : wos::green_q3(a[i]);
+    else out[i] = (dim == 2) ? wos::green_q2((float)a[i]) : wos::green_q3((float)a[i]);
+  }
+}
+
+// radial CDF and density at rho for a
+void wos_hc_radial(int dim, int fp64, double a, const double* rho, int64_t n, double* F, double* pdf) {
+  if (fp64) {
+    wos::Radial3<double> r3;
+    wos::Radial2<double> r2;
+    if (dim == 3) r3.init(a); else r2.init(a);
+    for (int64_t i = 0; i < n; ++i) {
+      if (dim == 3) r3.eval(rho[i], &F[i], &pdf[i]); else r2.eval(rho[i], &F[i], &pdf[i]);
+    }
+  } else {
+    wos::Radial3<float> r3;
+    wos::Radial2<float> r2;
+    if (dim == 3) r3.init((float)a); else r2.init((float)a);
+    for (int64_t i = 0; i < n; ++i) {
+      float f, p;
+      if (dim == 3) r3.eval((float)rho[i], &f, &p); else r2.eval((float)rho[i], &f, &p);
+      F[i] = f;
+      pdf[i] = p;
+    }
+  }
+}
+
+// rho = F^{-1}(u) as the walk computes it
+void wos_hc_sample_radius(int dim, int fp64, double a, const double* u, int64_t n, double* rho) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) rho[i] = (dim == 2) ? wos::sample_radius<2, double>(a, u[i]) : wos::sample_radius<3, double>(a, u[i]);
+    else rho[i] = (dim == 2) ? wos::sample_radius<2, float>((float)a, (float)u[i])
+                             : wos::sample_radius<3, float>((float)a, (float)u[i]);
+  }
+}
+
+void wos_hc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  wos::U4 c = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  wos::U4 o = wos::philox4x32_10(c, key[0], key[1]);
+  out[0] = o.x;
+  out[1] = o.y;
+  out[2] = o.z;
+  out[3] = o.w;
+}
+
+}  // extern "C"

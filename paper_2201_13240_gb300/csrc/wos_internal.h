@@ -1,0 +1,44 @@
+// wos_internal.h -- launch descriptors shared by the C-ABI layer and the
+// walk-kernel translation units (not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wos {
+
+// statistics words written by the walk kernel (added atomically)
+enum { ST_STEPS = 0, ST_WALKS = 1, ST_CAPPED = 2, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_WORDS = 5 };
+
+struct WalkLaunch {
+  const void* problem;            // DevProblem<R> in device memory
+  int problem_bytes;              // sizeof(DevProblem<R>), multiple of 16
+  int dim;
+  const float* pts;               // SoA [dim][npts], device
+  int64_t npts;
+  const int64_t* walk_end;        // inclusive prefix sums of walks per point, or null
+  int64_t walks_uniform;
+  uint64_t total_items;           // total walks of the launch
+  uint64_t seed;
+  uint64_t walk_offset;
+  double eps;
+  double sigma_bar;
+  int64_t max_steps;
+  double* sum;                    // [npts], accumulated
+  double* sumsq;                  // [npts], accumulated
+  unsigned long long* count;      // [npts], accumulated
+  unsigned long long* stats;      // [ST_WORDS], accumulated
+  unsigned long long* work_counter;  // zeroed before the launch
+  double* uhat;                   // optional per-walk estimates [total_items]
+  int64_t* steps_out;             // optional per-walk step counts [total_items]
+};
+
+// launch the persistent walk kernel; returns a cudaError_t
+cudaError_t launch_walks_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
+cudaError_t launch_walks_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream);
+
+// per-SM resident blocks of the walk kernel (for reporting)
+int walk_blocks_per_sm_f32(int dim);
+int walk_blocks_per_sm_f64(int dim);
+
+}  // namespace wos

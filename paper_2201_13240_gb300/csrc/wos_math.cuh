@@ -1,0 +1,646 @@
+// wos_math.cuh -- scalar math of one walk-on-spheres step, for FP32 and FP64.
+//
+//   * Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
+//     conversion of its words to uniforms in (0,1).
+//   * Modified Bessel functions I0, I1, K0, K1.  FP32: the polynomial
+//     approximations of Abramowitz & Stegun 9.8.1-9.8.8.  FP64: power series
+//     (DLMF 10.25.2, 10.31.1-2), the large-argument expansion (DLMF 10.40.1)
+//     and the trapezoidal rule on K_nu(x) = int_0^inf e^{-x cosh t} cosh(nu t) dt
+//     (DLMF 10.32.9), which converges geometrically for this integrand.
+//   * The centred screened-Poisson Green's function of a ball (Supplemental
+//     Sec. 1.1): P^B = sigma_bar |G|, |G|, and the radius of y ~ G/|G| by
+//     safeguarded Newton on the radial CDF.
+//
+// Everything is __host__ __device__ so the same code can be checked on a CPU.
+#pragma once
+
+#include <stdint.h>
+
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define WOS_HD __host__ __device__ __forceinline__
+#else
+#define WOS_HD inline
+#endif
+
+namespace wos {
+
+// ---------------------------------------------------------------------------
+// real-type helpers
+// ---------------------------------------------------------------------------
+WOS_HD float w_exp(float x) { return expf(x); }
+WOS_HD double w_exp(double x) { return exp(x); }
+WOS_HD float w_log(float x) { return logf(x); }
+WOS_HD double w_log(double x) { return log(x); }
+WOS_HD float w_sqrt(float x) { return sqrtf(x); }
+WOS_HD double w_sqrt(double x) { return sqrt(x); }
+WOS_HD float w_rsqrt(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+WOS_HD double w_rsqrt(double x) { return 1.0 / sqrt(x); }
+WOS_HD float w_sin(float x) { return sinf(x); }
+WOS_HD double w_sin(double x) { return sin(x); }
+WOS_HD float w_cos(float x) { return cosf(x); }
+WOS_HD double w_cos(double x) { return cos(x); }
+WOS_HD void w_sincos(float x, float* s, float* c) {
+#if defined(__CUDA_ARCH__)
+  sincosf(x, s, c);
+#else
+  *s = sinf(x);
+  *c = cosf(x);
+#endif
+}
+WOS_HD void w_sincos(double x, double* s, double* c) {
+#if defined(__CUDA_ARCH__)
+  sincos(x, s, c);
+#else
+  *s = sin(x);
+  *c = cos(x);
+#endif
+}
+// sin(2 pi u), cos(2 pi u) for u in (0,1)
+WOS_HD void w_sincospi2(float u, float* s, float* c) {
+#if defined(__CUDA_ARCH__)
+  sincospif(2.0f * u, s, c);
+#else
+  *s = sinf(6.283185307179586f * u);
+  *c = cosf(6.283185307179586f * u);
+#endif
+}
+WOS_HD void w_sincospi2(double u, double* s, double* c) {
+#if defined(__CUDA_ARCH__)
+  sincospi(2.0 * u, s, c);
+#else
+  *s = sin(6.283185307179586476925 * u);
+  *c = cos(6.283185307179586476925 * u);
+#endif
+}
+WOS_HD float w_asin(float x) { return asinf(x); }
+WOS_HD double w_asin(double x) { return asin(x); }
+WOS_HD float w_fabs(float x) { return fabsf(x); }
+WOS_HD double w_fabs(double x) { return fabs(x); }
+WOS_HD float w_fmax(float a, float b) { return fmaxf(a, b); }
+WOS_HD double w_fmax(double a, double b) { return fmax(a, b); }
+WOS_HD float w_fmin(float a, float b) { return fminf(a, b); }
+WOS_HD double w_fmin(double a, double b) { return fmin(a, b); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+WOS_HD void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+#if defined(__CUDA_ARCH__)
+  *hi = __umulhi(a, b);
+  *lo = a * b;
+#else
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+#endif
+}
+
+WOS_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(0xD2511F53u, c.x, &hi0, &lo0);
+    mulhilo32(0xCD9E8D57u, c.z, &hi1, &lo1);
+    U4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniforms in (0,1): FP32 keeps the top 24 bits, FP64 all 32
+template <typename R>
+WOS_HD R to_uniform(uint32_t x);
+template <>
+WOS_HD float to_uniform<float>(uint32_t x) {
+  return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+template <>
+WOS_HD double to_uniform<double>(uint32_t x) {
+  return ((double)x + 0.5) * 2.3283064365386962890625e-10;
+}
+
+// ---------------------------------------------------------------------------
+// Bessel functions, FP32: Abramowitz & Stegun 9.8.1-9.8.8 (|error| <~ 2e-7 on
+// the scaled quantities).  *_s are exponentially scaled: i0s(x) = e^{-x} I0(x),
+// k0s(x) = e^{x} K0(x).
+// ---------------------------------------------------------------------------
+WOS_HD float as_i0_small(float x) {  // x <= 3.75
+  float t = x * (1.0f / 3.75f);
+  t *= t;
+  return 1.0f + t * (3.5156229f + t * (3.0899424f + t * (1.2067492f + t * (0.2659732f +
+         t * (0.0360768f + t * 0.0045813f)))));
+}
+WOS_HD float as_i1_small(float x) {  // x <= 3.75
+  float t = x * (1.0f / 3.75f);
+  t *= t;
+  return x * (0.5f + t * (0.87890594f + t * (0.51498869f + t * (0.15084934f + t * (0.02658733f +
+              t * (0.00301532f + t * 0.00032411f))))));
+}
+WOS_HD float as_i0s_large(float x) {  // x >= 3.75: e^{-x} I0(x)
+  float t = 3.75f / x;
+  float p = 0.39894228f + t * (0.01328592f + t * (0.00225319f + t * (-0.00157565f + t * (0.00916281f +
+            t * (-0.02057706f + t * (0.02635537f + t * (-0.01647633f + t * 0.00392377f)))))));
+  return p * w_rsqrt(x);
+}
+WOS_HD float as_i1s_large(float x) {  // x >= 3.75: e^{-x} I1(x)
+  float t = 3.75f / x;
+  float p = 0.39894228f + t * (-0.03988024f + t * (-0.00362018f + t * (0.00163801f + t * (-0.01031555f +
+            t * (0.02282967f + t * (-0.02895312f + t * (0.01787654f - t * 0.00420059f)))))));
+  return p * w_rsqrt(x);
+}
+// K0(x) + ln(x/2) I0(x), x <= 2
+WOS_HD float as_k0_poly(float x) {
+  float t = 0.25f * x * x;
+  return -0.57721566f + t * (0.42278420f + t * (0.23069756f + t * (0.03488590f + t * (0.00262698f +
+         t * (0.00010750f + t * 0.0000074f)))));
+}
+// x K1(x) - x ln(x/2) I1(x) - 1, x <= 2
+WOS_HD float as_k1_poly(float x) {
+  float t = 0.25f * x * x;
+  return t * (0.15443144f + t * (-0.67278579f + t * (-0.18156897f + t * (-0.01919402f +
+         t * (-0.00110404f - t * 0.00004686f)))));
+}
+WOS_HD float as_k0s_large(float x) {  // x >= 2: e^{x} K0(x)
+  float t = 2.0f / x;
+  float p = 1.25331414f + t * (-0.07832358f + t * (0.02189568f + t * (-0.01062446f + t * (0.00587872f +
+            t * (-0.00251540f + t * 0.00053208f)))));
+  return p * w_rsqrt(x);
+}
+WOS_HD float as_k1s_large(float x) {  // x >= 2: e^{x} K1(x)
+  float t = 2.0f / x;
+  float p = 1.25331414f + t * (0.23498619f + t * (-0.03655620f + t * (0.01504268f + t * (-0.00780353f +
+            t * (0.00325614f - t * 0.00068245f)))));
+  return p * w_rsqrt(x);
+}
+
+// ---------------------------------------------------------------------------
+// Bessel functions, FP64
+// ---------------------------------------------------------------------------
+// sum_k (x^2/4)^k / (k! (k+nu)!) for nu = 0, 1
+WOS_HD double ser_i(int nu, double x) {
+  double q = 0.25 * x * x, term = 1.0, acc = 1.0;
+  for (int k = 1; k < 200; ++k) {
+    term *= q / ((double)k * (double)(k + nu));
+    acc += term;
+    if (term < 1e-18 * acc) break;
+  }
+  return acc;
+}
+// e^{-x} I_nu(x) sqrt(2 pi x) by the large-argument expansion, x >= 20
+WOS_HD double asym_is(int nu, double x) {
+  double mu = 4.0 * nu * nu, term = 1.0, acc = 1.0;
+  for (int k = 1; k < 60; ++k) {
+    double f = (2.0 * k - 1.0);
+    double nt = -term * (mu - f * f) / (k * 8.0 * x);
+    if (fabs(nt) > fabs(term)) break;
+    term = nt;
+    acc += term;
+    if (fabs(term) < 1e-18 * fabs(acc)) break;
+  }
+  return acc;
+}
+WOS_HD double d_i0s(double x) {  // e^{-x} I0(x)
+  if (x < 20.0) return exp(-x) * ser_i(0, x);
+  return asym_is(0, x) / sqrt(6.283185307179586476925 * x);
+}
+WOS_HD double d_i1s(double x) {  // e^{-x} I1(x)
+  if (x < 20.0) return exp(-x) * 0.5 * x * ser_i(1, x);
+  return asym_is(1, x) / sqrt(6.283185307179586476925 * x);
+}
+WOS_HD double d_i0(double x) { return (x < 20.0) ? ser_i(0, x) : exp(x) * d_i0s(x); }
+WOS_HD double d_i1(double x) { return (x < 20.0) ? 0.5 * x * ser_i(1, x) : exp(x) * d_i1s(x); }
+// e^{x} K_nu(x) = int_0^inf e^{-x (cosh t - 1)} cosh(nu t) dt, trapezoid with step h
+// The integrand is analytic in a strip whose useful width shrinks like 1/sqrt(x),
+// so the step is h = min(1/8, 0.6/sqrt(x)) for an error below e^{-50}.
+WOS_HD double trap_ks(int nu, double x) {
+  const double h = fmin(0.125, 0.6 / sqrt(x));
+  double acc = 0.5;
+  for (int j = 1; j < 2000; ++j) {
+    double t = j * h;
+    double e = exp(-x * (cosh(t) - 1.0));
+    acc += e * (nu ? cosh(t) : 1.0);
+    if (e < 1e-19) break;
+  }
+  return acc * h;
+}
+// K0(x) + ln(x/2) I0(x) = -gamma I0(x) + sum_{k>=1} H_k (x^2/4)^k/(k!)^2 (DLMF 10.31.2)
+WOS_HD double d_k0_small(double x) {
+  const double eg = 0.57721566490153286061;
+  double q = 0.25 * x * x, term = 1.0, H = 0.0, s = 0.0, i0 = 1.0;
+  for (int k = 1; k < 100; ++k) {
+    term *= q / ((double)k * k);
+    H += 1.0 / k;
+    s += H * term;
+    i0 += term;
+    if (term < 1e-19) break;
+  }
+  return -(log(0.5 * x) + eg) * i0 + s;
+}
+// 1 - x K1(x) by DLMF 10.31.1 (n = 1), x <= 2:
+//   1 - x K1(x) = -x ln(x/2) I1(x) + (x^2/4) sum_k (psi(k+1) + psi(k+2)) (x^2/4)^k / (k!(k+1)!)
+WOS_HD double d_1m_xk1_small(double x) {
+  const double eg = 0.57721566490153286061;
+  double q = 0.25 * x * x, term = 1.0, H = 0.0, acc = 0.0, i1s = 0.0;
+  for (int k = 0; k < 100; ++k) {
+    if (k > 0) {
+      term *= q / ((double)k * (k + 1));
+      H += 1.0 / k;
+    }
+    double psi1 = -eg + H, psi2 = -eg + H + 1.0 / (k + 1);
+    acc += (psi1 + psi2) * term;
+    i1s += term;
+    if (k > 2 && term < 1e-20) break;
+  }
+  double i1 = 0.5 * x * i1s;
+  return -x * log(0.5 * x) * i1 + q * acc;
+}
+WOS_HD double d_k0(double x) { return (x <= 2.0) ? d_k0_small(x) : exp(-x) * trap_ks(0, x); }
+WOS_HD double d_k1(double x) { return (x <= 2.0) ? (1.0 - d_1m_xk1_small(x)) / x : exp(-x) * trap_ks(1, x); }
+
+// ---------------------------------------------------------------------------
+// Green's function of Lap - sb on a ball of radius R centred at x
+// (Supplemental 1.1).  a = sqrt(sb) R.
+//   |G| = R^2 q(a) with 3D q = (1 - a/sinh a)/a^2, 2D q = (1 - 1/I0(a))/a^2,
+//   P^B = sb |G| = a^2 q(a).
+// ---------------------------------------------------------------------------
+WOS_HD float green_q3(float a) {
+  if (a < 0.5f) {  // (1 - a/sinh a)/a^2 = 1/6 - 7a^2/360 + 31a^4/15120 - 127a^6/604800
+    float t = a * a;
+    return 0.16666667f + t * (-0.019444444f + t * (0.0020502645f - t * 0.00020998677f));
+  }
+  float e = w_exp(-a);
+  float ratio = 2.0f * a * e / (1.0f - e * e);  // a / sinh a
+  return (1.0f - ratio) / (a * a);
+}
+WOS_HD double green_q3(double a) {
+  if (a < 1.0) {  // (sinh a - a)/(a^2 sinh a) by the series of sinh a - a
+    double t = a * a, term = a, s = 0.0;
+    for (int k = 1; k < 30; ++k) {
+      term *= t / ((2.0 * k) * (2.0 * k + 1.0));
+      s += term;
+      if (term < 1e-19 * s) break;
+    }
+    if (a == 0.0) return 1.0 / 6.0;
+    return s / (t * sinh(a));
+  }
+  double e = exp(-a);
+  double ratio = 2.0 * a * e / (1.0 - e * e);
+  return (1.0 - ratio) / (a * a);
+}
+WOS_HD float green_q2(float a) {
+  if (a < 3.75f) {  // (I0 - 1)/a^2 / I0 with the series of I0 - 1
+    float q = 0.25f * a * a;
+    float s = 0.25f, term = 0.25f;  // (I0-1)/a^2 = 1/4 sum_{k>=1} q^(k-1)/(k!)^2
+#pragma unroll
+    for (int k = 2; k < 12; ++k) {
+      term *= q / (float)(k * k);
+      s += term;
+    }
+    return s / (1.0f + a * a * s);
+  }
+  float inv_i0 = w_exp(-a) / as_i0s_large(a);  // 1/I0(a)
+  return (1.0f - inv_i0) / (a * a);
+}
+WOS_HD double green_q2(double a) {
+  if (a == 0.0) return 0.25;
+  if (a < 2.0) {
+    double q = 0.25 * a * a, term = 1.0, s = 0.0;
+    for (int k = 1; k < 60; ++k) {
+      term *= q / ((double)k * k);
+      s += term;
+      if (term < 1e-19 * s) break;
+    }
+    return (s / (a * a)) / (1.0 + s);
+  }
+  return (1.0 - exp(-a) / d_i0s(a)) / (a * a);
+}
+
+template <int DIM, typename R>
+WOS_HD R green_q(R a) {
+  return DIM == 2 ? green_q2(a) : green_q3(a);
+}
+
+// ---------------------------------------------------------------------------
+// Radial CDF F(rho) of y ~ G/|G|, rho = r/R, and its density, 3D.
+//   N(rho) = a^2 int_0^rho t sinh(a(1-t)) dt, F = N(rho)/N(1).
+//   a >= 1:  with h(x) = 1 - e^x (1-x),
+//            F = [h(-a rho) - e^{-2a} h(a rho)] / [1 - 2a e^{-a} - e^{-2a}]
+//   a < 1:   N/a^3 = sum_j c_j J_{2j+1}(rho), c_j = a^{2j}/(2j+1)!,
+//            J_m(rho) = [1 - v^{m+1} ((m+2) - (m+1) v)] / ((m+1)(m+2)), v = 1 - rho,
+//            so F = 1 - Q(v)/T with T = sum_j c_j/((m+1)(m+2)) and
+//            Q(v) = sum_j c_j v^{m+1} ((m+2) - (m+1) v) / ((m+1)(m+2)).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Radial3 {
+  R a;
+  int small;
+  R c[10];  // series: c_j / ((m+1)(m+2)) with m = 2j+1
+  int nc;
+  R invT;
+  R invD, e2a;  // closed form
+
+  WOS_HD void init(R a_) {
+    a = a_;
+    small = (a < R(1));
+    if (small) {
+      const int nmax = (sizeof(R) == 4) ? 5 : 10;
+      R cj = R(1), T = R(0);
+      nc = nmax;
+      for (int j = 0; j < nmax; ++j) {
+        R m = R(2 * j + 1);
+        c[j] = cj / ((m + R(1)) * (m + R(2)));
+        T += c[j];
+        cj *= a * a / (R(2 * j + 2) * R(2 * j + 3));
+      }
+      invT = R(1) / T;
+    } else {
+      R ea = w_exp(-a);
+      e2a = ea * ea;
+      invD = R(1) / (R(1) - R(2) * a * ea - e2a);
+    }
+  }
+  // h(x) = 1 - e^x (1 - x), series for |x| < 1/2
+  WOS_HD static R h(R x, R ex) {
+    if (w_fabs(x) < R(0.5)) {
+      const int nt = (sizeof(R) == 4) ? 9 : 20;
+      R term = x, acc = R(0);
+      for (int m = 2; m < nt; ++m) {
+        term *= x / R(m);
+        acc += term * R(m - 1);
+      }
+      return acc;
+    }
+    return R(1) - ex * (R(1) - x);
+  }
+  // F(rho) and dF/drho
+  WOS_HD void eval(R rho, R* F, R* pdf) const {
+    if (small) {
+      R v = R(1) - rho;
+      R v2 = v * v;
+      R Q = R(0), dQ = R(0), vm = v;  // vm = v^m, m = 2j+1
+      for (int j = 0; j < nc; ++j) {
+        R m = R(2 * j + 1);
+        Q += c[j] * vm * v * ((m + R(2)) - (m + R(1)) * v);
+        // d/dv [v^{m+1}((m+2) - (m+1) v)] = (m+1)(m+2) v^m (1 - v)
+        dQ += c[j] * (m + R(1)) * (m + R(2)) * vm * rho;
+        vm *= v2;
+      }
+      *F = R(1) - Q * invT;
+      *pdf = dQ * invT;  // dF/drho = dQ/dv / T
+      return;
+    }
+    R x = a * rho;
+    R e1 = w_exp(-x);             // e^{-a rho}
+    R e2 = w_exp(-a * (R(2) - rho));  // e^{-a(2 - rho)} = e^{-2a} e^{a rho}
+    R hm = h(-x, e1);
+    // e^{-2a} h(a rho) = e^{-2a} - e2 (1 - x); series branch for small x
+    R hp = (x < R(0.5)) ? e2a * h(x, R(0)) : e2a - e2 * (R(1) - x);
+    *F = (hm - hp) * invD;
+    *pdf = a * x * (e1 - e2) * invD;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Radial CDF, 2D.  N(rho) = 1 - t K1(t) - c t I1(t), t = a rho, c = K0(a)/I0(a),
+// N(1) = 1 - 1/I0(a);  dN/drho = a^2 rho (K0(t) - c I0(t)).
+// For a < 2 the power series of I0, K0 gives (logs of a cancel)
+//   N/a^2 = rho^2 [B(rho^2) - ln(rho) A(rho^2)],
+//   A_k = b_k / (2k+2),  B_k = b_k [1/(2k+2)^2 + (H_k - beta)/(2k+2)],
+//   dN/drho / a^2 = rho [C(rho^2) - ln(rho) D(rho^2)], D_k = b_k, C_k = b_k (H_k - beta),
+// b_k = (a^2/4)^k / (k!)^2, beta = S(a)/I0(a), S(a) = sum_{k>=1} H_k b_k.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Radial2;
+
+template <>
+struct Radial2<float> {
+  float a;
+  int small;
+  float A[8], B[8], Cc[8], Dd[8];
+  float invN1;
+  float c_scaled;  // K0(a)/I0(a) times e^{2a}: k0s(a)/i0s(a)
+  float e2a;
+
+  WOS_HD void init(float a_) {
+    a = a_;
+    small = (a < 2.0f);
+    if (small) {
+      float q = 0.25f * a * a, b = 1.0f, H = 0.0f, I0 = 0.0f, S = 0.0f;
+      float bk[8], Hk[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k > 0) {
+          b *= q / (float)(k * k);
+          H += 1.0f / (float)k;
+        }
+        bk[k] = b;
+        Hk[k] = H;
+        I0 += b;
+        S += H * b;
+      }
+      float beta = S / I0;
+      float N1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float m = 2.0f * k + 2.0f;
+        A[k] = bk[k] / m;
+        B[k] = bk[k] * (1.0f / (m * m) + (Hk[k] - beta) / m);
+        Dd[k] = bk[k];
+        Cc[k] = bk[k] * (Hk[k] - beta);
+        N1 += B[k];
+      }
+      invN1 = 1.0f / N1;  // N(1)/a^2 = B(1)
+    } else {
+      float ea = w_exp(-a);
+      e2a = ea * ea;
+      float i0s = (a < 3.75f) ? as_i0_small(a) * ea : as_i0s_large(a);
+      float k0s = as_k0s_large(a);  // a >= 2
+      c_scaled = k0s / i0s;         // c = c_scaled e^{-2a}
+      invN1 = 1.0f / (1.0f - ea / i0s);
+    }
+  }
+  WOS_HD void eval(float rho, float* F, float* pdf) const {
+    if (small) {
+      if (rho <= 0.0f) { *F = 0.0f; *pdf = 0.0f; return; }
+      float r2 = rho * rho, lr = w_log(rho);
+      float pa = A[7], pb = B[7], pc = Cc[7], pd = Dd[7];
+#pragma unroll
+      for (int k = 6; k >= 0; --k) {
+        pa = pa * r2 + A[k];
+        pb = pb * r2 + B[k];
+        pc = pc * r2 + Cc[k];
+        pd = pd * r2 + Dd[k];
+      }
+      *F = r2 * (pb - lr * pa) * invN1;
+      *pdf = rho * (pc - lr * pd) * invN1;
+      return;
+    }
+    float t = a * rho;
+    if (t <= 0.0f) { *F = 0.0f; *pdf = 0.0f; return; }
+    float one_m_tk1, k0t, i0t, ti1t;  // c I0(t), c t I1(t) carry the factor e^{-2a}
+    if (t < 2.0f) {
+      float lt = w_log(0.5f * t);
+      float i1 = as_i1_small(t), i0 = as_i0_small(t);
+      one_m_tk1 = -t * lt * i1 - as_k1_poly(t);
+      k0t = as_k0_poly(t) - lt * i0;
+      i0t = c_scaled * e2a * i0;
+      ti1t = c_scaled * e2a * t * i1;
+    } else {
+      float et = w_exp(-t);
+      one_m_tk1 = 1.0f - t * as_k1s_large(t) * et;
+      k0t = as_k0s_large(t) * et;
+      if (t < 3.75f) {
+        i0t = c_scaled * e2a * as_i0_small(t);
+        ti1t = c_scaled * e2a * t * as_i1_small(t);
+      } else {
+        float g = c_scaled * w_exp(t - 2.0f * a);  // c e^{t}
+        i0t = g * as_i0s_large(t);
+        ti1t = g * t * as_i1s_large(t);
+      }
+    }
+    *F = (one_m_tk1 - ti1t) * invN1;
+    *pdf = a * t * (k0t - i0t) * invN1;
+  }
+};
+
+template <>
+struct Radial2<double> {
+  double a;
+  int small;
+  double A[24], B[24], Cc[24], Dd[24];
+  int n;
+  double invN1;
+  double c;  // K0(a)/I0(a)
+
+  WOS_HD void init(double a_) {
+    a = a_;
+    small = (a <= 2.0);
+    if (small) {
+      double q = 0.25 * a * a, b = 1.0, H = 0.0, I0 = 0.0, S = 0.0;
+      double bk[24], Hk[24];
+      n = 24;
+      for (int k = 0; k < 24; ++k) {
+        if (k > 0) {
+          b *= q / ((double)k * k);
+          H += 1.0 / k;
+        }
+        bk[k] = b;
+        Hk[k] = H;
+        I0 += b;
+        S += H * b;
+      }
+      double beta = S / I0, N1 = 0.0;
+      for (int k = 0; k < 24; ++k) {
+        double m = 2.0 * k + 2.0;
+        A[k] = bk[k] / m;
+        B[k] = bk[k] * (1.0 / (m * m) + (Hk[k] - beta) / m);
+        Dd[k] = bk[k];
+        Cc[k] = bk[k] * (Hk[k] - beta);
+        N1 += B[k];
+      }
+      invN1 = 1.0 / N1;
+    } else {
+      c = d_k0(a) / d_i0(a);
+      invN1 = 1.0 / (1.0 - 1.0 / d_i0(a));
+    }
+  }
+  WOS_HD void eval(double rho, double* F, double* pdf) const {
+    if (rho <= 0.0) { *F = 0.0; *pdf = 0.0; return; }
+    if (small) {
+      double r2 = rho * rho, lr = log(rho);
+      double pa = 0, pb = 0, pc = 0, pd = 0;
+      for (int k = n - 1; k >= 0; --k) {
+        pa = pa * r2 + A[k];
+        pb = pb * r2 + B[k];
+        pc = pc * r2 + Cc[k];
+        pd = pd * r2 + Dd[k];
+      }
+      *F = r2 * (pb - lr * pa) * invN1;
+      *pdf = rho * (pc - lr * pd) * invN1;
+      return;
+    }
+    double t = a * rho;
+    double one_m_tk1 = (t <= 2.0) ? d_1m_xk1_small(t) : 1.0 - t * d_k1(t);
+    *F = (one_m_tk1 - c * t * d_i1(t)) * invN1;
+    *pdf = a * t * (d_k0(t) - c * d_i0(t)) * invN1;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Radius of y ~ G/|G| on the centred ball: r = R F^{-1}(u), safeguarded Newton.
+// FP32 runs a fixed number of iterations from a closed-form starting point;
+// FP64 iterates to convergence.
+// ---------------------------------------------------------------------------
+template <typename Rad, typename R>
+WOS_HD R newton_inverse(const Rad& rad, R u, R rho, int iters, R tol) {
+  R lo = R(0), hi = R(1);
+  for (int it = 0; it < iters; ++it) {
+    R F, p;
+    rad.eval(rho, &F, &p);
+    R res = F - u;
+    if (res == R(0)) break;
+    if (res > R(0)) hi = rho; else lo = rho;
+    R nr = (p > R(0)) ? rho - res / p : R(0.5) * (lo + hi);
+    // Newton may land on the bracket end it started from once converged; only
+    // a step that leaves [lo, hi] falls back to bisection
+    if (!(nr >= lo && nr <= hi)) nr = R(0.5) * (lo + hi);
+    R step = w_fabs(nr - rho);
+    rho = nr;
+    if (step <= tol) break;
+  }
+  return rho;
+}
+
+// starting points: Beta(2,2) quantile (3D, a -> 0), the equation
+// L - ln(1+L) = -ln u for L = -2 ln rho (2D, a -> 0), and the Gamma(2)
+// quantile t - ln(1+t) = -ln(1-u) (large a), each with L0 = m + sqrt(2m).
+template <int DIM, typename R>
+WOS_HD R radial_guess(R a, R u) {
+  if (DIM == 3 && a < R(2)) {
+    return R(0.5) + w_sin(w_asin(R(2) * u - R(1)) * R(0.3333333333333333));
+  }
+  if (DIM == 2 && a < R(2)) {
+    R m = -w_log(u);
+    R L = m + w_sqrt(R(2) * m);
+    return w_exp(R(-0.5) * L);
+  }
+  R m = -w_log(R(1) - u);
+  R t = m + w_sqrt(R(2) * m);
+  return w_fmin(t / a, R(0.999));
+}
+
+template <int DIM, typename R>
+WOS_HD R sample_radius(R a, R u) {
+  const int iters = (sizeof(R) == 4) ? 12 : 200;
+  const R tol = (sizeof(R) == 4) ? R(1e-7) : R(1e-16);
+  R g = radial_guess<DIM, R>(a, u);
+  if (DIM == 3) {
+    Radial3<R> rad;
+    rad.init(a);
+    return newton_inverse(rad, u, g, iters, tol);
+  } else {
+    Radial2<R> rad;
+    rad.init(a);
+    return newton_inverse(rad, u, g, iters, tol);
+  }
+}
+
+}  // namespace wos

@@ -1,0 +1,376 @@
+// wos_problem.cuh -- device description of one PDE problem and its point-wise
+// evaluation: coefficient fields, the transformation to a screened Poisson
+// equation, and the distance to the domain boundary.
+//
+//   PDE (Sec. 3, eq. 1): div(alpha grad u) + omega . grad u - sigma u = -f,
+//                        u = g on the boundary, omega = alpha grad(Phi).
+//   Transform (Sec. 4.1 eq. 7-8, App. A):
+//     gamma = 1/2 ln alpha + 1/2 Phi,  U = e^gamma u,
+//     sigma' = sigma/alpha + Lap(gamma) + |grad gamma|^2,
+//     f' = e^gamma f / alpha,  g' = e^gamma g,  Lap U - sigma' U = -f'.
+#pragma once
+
+#include <stdint.h>
+
+#include "wos_math.cuh"
+
+namespace wos {
+
+enum AtomType { A_ONE = 0, A_SIN = 1, A_COS = 2, A_EXP = 3, A_SINH = 4, A_COSH = 5, A_LIN = 6, A_QUAD = 7 };
+enum FieldKind { F_ZERO = 0, F_CONST = 1, F_SST = 2, F_MANUFACTURED = 3, F_GRID_LINEAR = 4, F_GRID_BSPLINE = 5 };
+enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3 };
+
+constexpr int kMaxTerms = 96;  // separable terms over all fields of one problem
+
+template <typename R>
+struct DevTerm {
+  R c;
+  R k[3];
+  R phi[3];
+  int32_t type[3];
+};
+
+template <typename R>
+struct DevField {
+  int32_t kind;
+  int32_t nterms;
+  int32_t first;  // first term in DevProblem::terms
+  int32_t pad;
+  R value;
+  R lo[3];
+  R inv_h[3];     // grid: 1 / node spacing
+  int32_t res[3];
+  int32_t pad2;
+  const float* data;  // grid values, x fastest, device memory owned by the caller
+};
+
+template <typename R>
+struct DevProblem {
+  int32_t dim;
+  int32_t domain_kind;
+  int32_t nterms;
+  int32_t pad;
+  R dom[16];
+  DevField<R> alpha, phi, sigma, f, g, um;
+  DevTerm<R> terms[kMaxTerms];
+};
+
+// ---------------------------------------------------------------------------
+// separable terms: c * prod_i h_i(k_i x_i + phi_i)
+// ---------------------------------------------------------------------------
+template <typename R>
+WOS_HD void atom(int type, R k, R ph, R x, R* h, R* h1, R* h2) {
+  R t = k * x + ph;
+  switch (type) {
+    case A_SIN: {
+      R s, c;
+      w_sincos(t, &s, &c);
+      *h = s; *h1 = k * c; *h2 = -k * k * s;
+      break;
+    }
+    case A_COS: {
+      R s, c;
+      w_sincos(t, &s, &c);
+      *h = c; *h1 = -k * s; *h2 = -k * k * c;
+      break;
+    }
+    case A_EXP: {
+      R e = w_exp(t);
+      *h = e; *h1 = k * e; *h2 = k * k * e;
+      break;
+    }
+    case A_SINH:
+    case A_COSH: {
+      R e = w_exp(t), ei = R(1) / e;
+      R sh = R(0.5) * (e - ei), ch = R(0.5) * (e + ei);
+      if (type == A_SINH) { *h = sh; *h1 = k * ch; *h2 = k * k * sh; }
+      else { *h = ch; *h1 = k * sh; *h2 = k * k * ch; }
+      break;
+    }
+    case A_LIN: *h = t; *h1 = k; *h2 = R(0); break;
+    case A_QUAD: *h = t * t; *h1 = R(2) * k * t; *h2 = R(2) * k * k; break;
+    default: *h = R(1); *h1 = R(0); *h2 = R(0); break;
+  }
+}
+
+template <int DIM, typename R>
+WOS_HD void sst_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap,
+                     bool deriv) {
+  R vv = R(0), ll = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
+  for (int n = 0; n < F.nterms; ++n) {
+    const DevTerm<R>& T = P.terms[F.first + n];
+    R h[3] = {R(1), R(1), R(1)}, h1[3] = {R(0), R(0), R(0)}, h2[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) atom(T.type[i], T.k[i], T.phi[i], x[i], &h[i], &h1[i], &h2[i]);
+    R p01 = h[0] * h[1];
+    vv += T.c * p01 * h[2];
+    if (deriv) {
+      g0 += T.c * h1[0] * h[1] * h[2];
+      g1 += T.c * h[0] * h1[1] * h[2];
+      g2 += T.c * p01 * h1[2];
+      ll += T.c * (h2[0] * h[1] * h[2] + h[0] * h2[1] * h[2] + p01 * h2[2]);
+    }
+  }
+  *v = vv;
+  if (deriv) {
+    g[0] = g0; g[1] = g1; g[2] = g2;
+    *lap = ll;
+  }
+}
+
+// node-centred multilinear interpolation, clamped to the grid box
+template <int DIM, typename R>
+WOS_HD R grid_linear(const DevField<R>& F, const R* x) {
+  int i0[3] = {0, 0, 0};
+  R t[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = (x[d] - F.lo[d]) * F.inv_h[d];
+    s = w_fmin(w_fmax(s, R(0)), R(F.res[d] - 1));
+    int i = (int)s;
+    if (i > F.res[d] - 2) i = F.res[d] - 2;
+    i0[d] = i;
+    t[d] = s - R(i);
+  }
+  const float* base = F.data + i0[0] + (int64_t)F.res[0] * (i0[1] + (int64_t)F.res[1] * (DIM == 3 ? i0[2] : 0));
+  int64_t sy = F.res[0], sz = (int64_t)F.res[0] * F.res[1];
+  R v00 = R(base[0]) + t[0] * (R(base[1]) - R(base[0]));
+  R v10 = R(base[sy]) + t[0] * (R(base[sy + 1]) - R(base[sy]));
+  R v0 = v00 + t[1] * (v10 - v00);
+  if (DIM == 2) return v0;
+  R v01 = R(base[sz]) + t[0] * (R(base[sz + 1]) - R(base[sz]));
+  R v11 = R(base[sz + sy]) + t[0] * (R(base[sz + sy + 1]) - R(base[sz + sy]));
+  R v1 = v01 + t[1] * (v11 - v01);
+  return v0 + t[2] * (v1 - v0);
+}
+
+template <typename R>
+WOS_HD void bspline_w(R t, R* B, R* B1, R* B2) {
+  R u = R(1) - t, t2 = t * t, t3 = t2 * t;
+  B[0] = u * u * u * R(1.0 / 6.0);
+  B[1] = (R(3) * t3 - R(6) * t2 + R(4)) * R(1.0 / 6.0);
+  B[2] = (R(-3) * t3 + R(3) * t2 + R(3) * t + R(1)) * R(1.0 / 6.0);
+  B[3] = t3 * R(1.0 / 6.0);
+  B1[0] = R(-0.5) * u * u;
+  B1[1] = R(0.5) * (R(3) * t2 - R(4) * t);
+  B1[2] = R(0.5) * (R(-3) * t2 + R(2) * t + R(1));
+  B1[3] = R(0.5) * t2;
+  B2[0] = u;
+  B2[1] = R(3) * t - R(2);
+  B2[2] = R(-3) * t + R(1);
+  B2[3] = t;
+}
+
+// uniform cubic B-spline with the node values as control points; control
+// indices clamped to the grid (constant extension) so the field stays C^2
+template <int DIM, typename R>
+WOS_HD void grid_bspline(const DevField<R>& F, const R* x, R* v, R* g, R* lap, bool deriv) {
+  int ib[3] = {0, 0, 0};
+  R B[3][4], B1[3][4], B2[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { B[d][a] = (a == 0) ? R(1) : R(0); B1[d][a] = R(0); B2[d][a] = R(0); }
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = (x[d] - F.lo[d]) * F.inv_h[d];
+    R fs = floor(s);
+    ib[d] = (int)fs - 1;
+    bspline_w(s - fs, B[d], B1[d], B2[d]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      B1[d][a] *= F.inv_h[d];
+      B2[d][a] *= F.inv_h[d] * F.inv_h[d];
+    }
+  }
+  int idx[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int j = ib[d] + a;
+      int hi = (d < DIM) ? F.res[d] - 1 : 0;
+      j = j < 0 ? 0 : (j > hi ? hi : j);
+      idx[d][a] = j;
+    }
+  }
+  R vv = R(0), g0 = R(0), g1 = R(0), g2 = R(0), ll = R(0);
+  const int n2 = (DIM == 3) ? 4 : 1;
+  for (int c2 = 0; c2 < n2; ++c2) {
+#pragma unroll
+    for (int c1 = 0; c1 < 4; ++c1) {
+      const float* row = F.data + (int64_t)F.res[0] * (idx[1][c1] + (int64_t)F.res[1] * idx[2][c2]);
+      R r = R(0), r1 = R(0), r2 = R(0);
+#pragma unroll
+      for (int c0 = 0; c0 < 4; ++c0) {
+        R val = R(row[idx[0][c0]]);
+        r += val * B[0][c0];
+        r1 += val * B1[0][c0];
+        r2 += val * B2[0][c0];
+      }
+      R b1 = B[1][c1], b2 = B[2][c2];
+      vv += r * b1 * b2;
+      if (deriv) {
+        g0 += r1 * b1 * b2;
+        g1 += r * B1[1][c1] * b2;
+        g2 += r * b1 * B1[2][c2];
+        ll += r2 * b1 * b2 + r * B2[1][c1] * b2 + r * b1 * B2[2][c2];
+      }
+    }
+  }
+  *v = vv;
+  if (deriv) {
+    g[0] = g0; g[1] = g1; g[2] = g2;
+    *lap = ll;
+  }
+}
+
+// value (and gradient / Laplacian when deriv) of a plain field
+template <int DIM, typename R>
+WOS_HD void field_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap,
+                       bool deriv) {
+  switch (F.kind) {
+    case F_CONST: *v = F.value; break;
+    case F_SST: sst_eval<DIM>(P, F, x, v, g, lap, deriv); return;
+    case F_GRID_LINEAR: *v = grid_linear<DIM>(F, x); break;  // piecewise linear: no second derivative
+    case F_GRID_BSPLINE: grid_bspline<DIM>(F, x, v, g, lap, deriv); return;
+    default: *v = R(0); break;
+  }
+  if (deriv) {
+    g[0] = g[1] = g[2] = R(0);
+    *lap = R(0);
+  }
+}
+
+// Transformed coefficients at y: sigma'(y), f'(y) (Sec. 4.1, App. A).
+template <int DIM, typename R>
+WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp) {
+  R a, ga[3], la, ph, gp[3], lp, s, gs[3], ls;
+  field_eval<DIM>(P, P.alpha, y, &a, ga, &la, true);
+  field_eval<DIM>(P, P.phi, y, &ph, gp, &lp, true);
+  field_eval<DIM>(P, P.sigma, y, &s, gs, &ls, false);
+  R f;
+  if (P.f.kind == F_MANUFACTURED) {
+    // eq. 1 solved for f at the manufactured u: f = -(alpha Lap u + grad alpha . grad u)
+    //                                              - alpha grad Phi . grad u + sigma u
+    R u, gu[3], lu;
+    field_eval<DIM>(P, P.um, y, &u, gu, &lu, true);
+    R da = R(0), dp = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      da += ga[d] * gu[d];
+      dp += gp[d] * gu[d];
+    }
+    f = -(a * lu + da) - a * dp + s * u;
+  } else {
+    R gf[3], lf;
+    field_eval<DIM>(P, P.f, y, &f, gf, &lf, false);
+  }
+  R ia = R(1) / a;
+  R na2 = R(0), ng2 = R(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R gg = R(0.5) * (ga[d] * ia + gp[d]);
+    ng2 += gg * gg;
+    na2 += ga[d] * ga[d];
+  }
+  R lgam = R(0.5) * (la * ia - na2 * ia * ia + lp);
+  *sp = s * ia + lgam + ng2;
+  R gam = R(0.5) * w_log(a) + R(0.5) * ph;
+  *fp = w_exp(gam) * f * ia;
+}
+
+template <int DIM, typename R>
+WOS_HD R gamma_at(const DevProblem<R>& P, const R* x) {
+  R a, ph, g[3], l;
+  field_eval<DIM>(P, P.alpha, x, &a, g, &l, false);
+  field_eval<DIM>(P, P.phi, x, &ph, g, &l, false);
+  return R(0.5) * w_log(a) + R(0.5) * ph;
+}
+
+template <int DIM, typename R>
+WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
+  R v, g[3], l;
+  field_eval<DIM>(P, P.g, x, &v, g, &l, false);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// distance to the boundary (positive inside) and closest boundary point
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb) {
+  const R* p = P.dom;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
+  switch (P.domain_kind) {
+    case D_BOX: {
+      R best = x[0] - p[0];
+      int bd = 0;
+      R bv = p[0];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        R dl = x[d] - p[d], dh = p[3 + d] - x[d];
+        if (dl < best) { best = dl; bd = d; bv = p[d]; }
+        if (dh < best) { best = dh; bd = d; bv = p[3 + d]; }
+      }
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) if (d == bd) xb[d] = bv;
+      return best;
+    }
+    case D_BALL:
+    case D_ANNULUS: {
+      R v[3] = {R(0), R(0), R(0)}, r2 = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) { v[d] = x[d] - p[d]; r2 += v[d] * v[d]; }
+      R r = w_sqrt(r2);
+      R dist, rad;
+      if (P.domain_kind == D_BALL) {
+        dist = p[3] - r;
+        rad = p[3];
+      } else {
+        R din = r - p[3], dout = p[4] - r;
+        dist = (din < dout) ? din : dout;
+        rad = (din < dout) ? p[3] : p[4];
+      }
+      if (r == R(0)) { v[0] = R(1); r = R(1); }
+      R s = rad / r;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) xb[d] = p[d] + v[d] * s;
+      return dist;
+    }
+    case D_ROUNDED_BOX: {
+      R rc = p[6];
+      R rel[3], inner[3], q[3];
+      R out2 = R(0), qmax = R(-1e30);
+      int imax = 0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        rel[d] = x[d] - p[d];
+        inner[d] = p[3 + d] - rc;
+        q[d] = w_fabs(rel[d]) - inner[d];
+        if (q[d] > R(0)) out2 += q[d] * q[d];
+        if (q[d] > qmax) { qmax = q[d]; imax = d; }
+      }
+      if (out2 > R(0)) {
+        R od = w_sqrt(out2);
+        R s = rc / od;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          R c = w_fmin(w_fmax(rel[d], -inner[d]), inner[d]);
+          xb[d] = p[d] + c + (rel[d] - c) * s;
+        }
+        return rc - od;
+      }
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        if (d == imax) xb[d] = p[d] + ((rel[d] >= R(0)) ? p[3 + d] : -p[3 + d]);
+      return rc - qmax;
+    }
+    default:
+      return R(-1);
+  }
+}
+
+}  // namespace wos

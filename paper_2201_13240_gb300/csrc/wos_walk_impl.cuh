@@ -1,0 +1,249 @@
+// wos_walk_impl.cuh -- persistent delta-tracking walk-on-spheres kernel.
+//
+// One lane runs one walk of Supplemental Algorithm 1 (Sec. 5.1, eq. 11),
+// unrolled into a loop over steps: distance query, epsilon-shell test, a
+// Philox block keyed by (point, walk, step), the centred Green's-function
+// sample y, the source term W |G| f'(y), and either a null event at y (weight
+// 1 - sigma'(y)/sigma_bar) or a jump to the sphere.  The sqrt(alpha) ratios of
+// Alg. 1 telescope into e^{gamma(x_n) - gamma(x_0)}, applied once per walk.
+//
+// Scheduling: the grid is persistent (resident blocks x SMs).  Walks are items
+// of a point-major index space claimed in chunks by one atomic per warp; a lane
+// whose walk ends takes the next item at the top of the step loop, so warps
+// stay full while walk lengths vary.  Each lane keeps FP64 partial sums for
+// its current point and flushes them with atomics when its point changes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wos_internal.h"
+#include "wos_math.cuh"
+#include "wos_problem.cuh"
+
+namespace wos {
+
+constexpr int kWalkBlock = 128;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kChunk = 128;
+
+template <int DIM, typename R>
+struct WalkState {
+  R x[3];
+  R W, acc, g0;
+  uint32_t p, w, k;
+  uint64_t item;
+};
+
+template <int DIM, typename R>
+__device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem<R>& P, uint64_t item,
+                                           WalkState<DIM, R>& s) {
+  uint64_t p, j;
+  if (L.walk_end == nullptr) {
+    p = item / (uint64_t)L.walks_uniform;
+    j = item - p * (uint64_t)L.walks_uniform;
+  } else {
+    // first point whose inclusive walk prefix exceeds item
+    int64_t lo = 0, hi = L.npts - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((uint64_t)__ldg(&L.walk_end[mid]) > item) hi = mid; else lo = mid + 1;
+    }
+    p = (uint64_t)lo;
+    uint64_t begin = (lo > 0) ? (uint64_t)__ldg(&L.walk_end[lo - 1]) : 0ull;
+    j = item - begin;
+  }
+  s.item = item;
+  s.p = (uint32_t)p;
+  s.w = (uint32_t)(L.walk_offset + j);
+  s.k = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) s.x[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
+  s.W = R(1);
+  s.acc = R(0);
+  s.g0 = gamma_at<DIM>(P, s.x);
+}
+
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // stage the problem description (a few KB, read by every lane every step) in shared memory
+  {
+    const int4* src = reinterpret_cast<const int4*>(L.problem);
+    int4* dst = reinterpret_cast<int4*>(smem_raw);
+    for (int i = threadIdx.x; i < L.problem_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
+
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
+  const R eps = R(L.eps), sb = R(L.sigma_bar), s_root = w_sqrt(R(L.sigma_bar));
+  const R inv_sb = R(1) / sb;
+  const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
+
+  // with per-point walk counts the total is the last inclusive prefix sum
+  const uint64_t total = (L.walk_end != nullptr) ? (uint64_t)__ldg(&L.walk_end[L.npts - 1]) : L.total_items;
+  const bool accumulate = (L.sum != nullptr);
+  uint64_t chunk_next = 0, chunk_end = 0;
+  bool exhausted = false;
+  bool active = false;
+  WalkState<DIM, R> s;
+  s.p = 0;
+
+  // per-lane partial sums of the current point
+  int64_t acc_p = -1;
+  double s1 = 0.0, s2 = 0.0;
+  unsigned long long n_acc = 0;
+  unsigned long long st_steps = 0, st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
+
+  for (;;) {
+    // ---- regeneration: lanes without a walk claim the next items ----
+    unsigned need = __ballot_sync(kFull, !active);
+    while (need != 0u && !exhausted) {
+      if (chunk_next >= chunk_end) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(L.work_counter, (unsigned long long)kChunk);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= total) {
+          exhausted = true;
+          break;
+        }
+        chunk_next = base;
+        chunk_end = (base + kChunk < total) ? base + kChunk : total;
+      }
+      unsigned nneed = __popc(need);
+      uint64_t avail = chunk_end - chunk_next;
+      unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
+      unsigned rank = __popc(need & lt_mask);
+      if (!active && rank < take) {
+        start_walk<DIM, R>(L, P, chunk_next + rank, s);
+        active = true;
+      }
+      chunk_next += take;
+      need = __ballot_sync(kFull, !active);
+    }
+    if (__ballot_sync(kFull, active) == 0u) break;
+    if (!active) continue;
+
+    // ---- one step of the walk ----
+    R xb[3];
+    R d = distance<DIM>(P, s.x, xb);
+    if (d < eps || s.k >= max_k) {
+      bool capped = !(d < eps);
+      if (!capped) s.acc += s.W * w_exp(gamma_at<DIM>(P, s.x)) * g_at<DIM>(P, xb);
+      if (s.k == 0 && !(d > R(0))) ++st_outside;
+      double u = (double)(s.acc * w_exp(-s.g0));
+      if (accumulate && (int64_t)s.p != acc_p) {
+        if (acc_p >= 0) {
+          atomicAdd(&L.sum[acc_p], s1);
+          atomicAdd(&L.sumsq[acc_p], s2);
+          atomicAdd(&L.count[acc_p], n_acc);
+        }
+        acc_p = s.p;
+        s1 = 0.0;
+        s2 = 0.0;
+        n_acc = 0;
+      }
+      s1 += u;
+      s2 += u * u;
+      ++n_acc;
+      if (L.uhat != nullptr) {
+        L.uhat[s.item] = u;
+        L.steps_out[s.item] = (int64_t)s.k;
+      }
+      st_steps += s.k;
+      ++st_walks;
+      if (capped) ++st_capped;
+      if (!isfinite(u)) ++st_nonfinite;
+      active = false;
+      continue;
+    }
+
+    U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, 0u}, key0, key1);
+    R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
+    R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
+    if (DIM == 2) {
+      w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
+      w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
+    } else {
+      U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, 1u}, key0, key1);
+      R cy = R(1) - R(2) * to_uniform<R>(r0.z);
+      R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
+      R sp_, cp_;
+      w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
+      dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
+      R cz = R(1) - R(2) * to_uniform<R>(r1.x);
+      R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+      w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
+      dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
+    }
+    R a = s_root * d;
+    R q = green_q<DIM, R>(a);
+    R Gn = d * d * q;          // |G| on the ball of radius d
+    R PB = a * a * q;          // sigma_bar |G|, probability of the volume term
+    R r = sample_radius<DIM, R>(a, ur) * d;
+    R y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? s.x[i] + r * dy[i] : R(0);
+    R spy, fpy;
+    coeffs<DIM>(P, y, &spy, &fpy);
+    s.acc += s.W * Gn * fpy;   // source term, every step
+    if (mu <= PB) {            // volume term: null event at y
+      s.W *= R(1) - spy * inv_sb;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) s.x[i] = y[i];
+    } else {                   // boundary term: uniform point on the sphere
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) s.x[i] = s.x[i] + d * dz[i];
+    }
+    ++s.k;
+  }
+
+  if (accumulate && acc_p >= 0) {
+    atomicAdd(&L.sum[acc_p], s1);
+    atomicAdd(&L.sumsq[acc_p], s2);
+    atomicAdd(&L.count[acc_p], n_acc);
+  }
+  // warp-reduce the statistics, one atomic per warp and word
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    st_steps += __shfl_down_sync(kFull, st_steps, off);
+    st_walks += __shfl_down_sync(kFull, st_walks, off);
+    st_capped += __shfl_down_sync(kFull, st_capped, off);
+    st_nonfinite += __shfl_down_sync(kFull, st_nonfinite, off);
+    st_outside += __shfl_down_sync(kFull, st_outside, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&L.stats[ST_STEPS], st_steps);
+    atomicAdd(&L.stats[ST_WALKS], st_walks);
+    if (st_capped) atomicAdd(&L.stats[ST_CAPPED], st_capped);
+    if (st_nonfinite) atomicAdd(&L.stats[ST_NONFINITE], st_nonfinite);
+    if (st_outside) atomicAdd(&L.stats[ST_OUTSIDE], st_outside);
+  }
+}
+
+template <int DIM, typename R>
+cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
+  size_t smem = (size_t)L.problem_bytes;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R>, kWalkBlock, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = per_sm * num_sms;
+  uint64_t warps_needed = (L.total_items + 31) / 32;
+  uint64_t blocks_needed = (warps_needed + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
+  if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
+  wos_walk_kernel<DIM, R><<<grid, kWalkBlock, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
+template <int DIM, typename R>
+int blocks_per_sm_t() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R>, kWalkBlock,
+                                                sizeof(DevProblem<R>));
+  return per_sm;
+}
+
+}  // namespace wos

@@ -1,0 +1,239 @@
+"""GPU parity of the CUDA walk kernels (through the C interface) with the FP64 oracle.
+
+* FP64 replay: the same Philox streams must give the oracle's walk, per walk,
+  to 1e-9 (relative to max(1, |u|)) on >= 99% of walks, with equal step counts.
+* FP32 production path: per-point agreement within 4 combined standard errors
+  at matched walk counts (read for many points as in tests/stats_util.py).
+* Accuracy: normalised RMS error <= 1e-2 against the manufactured solution at
+  2^16 walks per point.
+* The full-size 3D workload in the benchmark's launch configuration, checked on
+  sampled points against the oracle.
+* Edge cases: empty and ragged inputs, per-point walk counts with zeros, walk-id
+  continuation, points in the epsilon shell, invalid arguments.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.stats_util import combined_z, four_se_rule, normalised_rms
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wos():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_13240_gb300 import build as B
+    B.build_lib()
+    import paper_2201_13240_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(wos):
+    return wos.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+REPLAY_CASES = {
+    "square2d": (W.square2d_problem, lambda: W.cell_centres(2, 32)[:, W.seeded_subset(1024, 48, 1)], 1e-3),
+    "cube3d": (W.cube3d_problem, lambda: W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 48, 2)], 1e-4),
+    "laplace_disk": (W.laplace_disk_problem, lambda: W.uniform_in_ball(2, 48, [0, 0], 1.0, 3, 0.02), 1e-4),
+    "screened_ball": (W.screened_ball_problem, lambda: W.uniform_in_ball(3, 48, [0, 0, 0], 1.0, 4, 0.02), 1e-4),
+    "rounded_box": (W.rounded_box_problem,
+                    lambda: W.uniform_in_box(2, 48, [-0.6, -0.6], [0.8, 0.2], 5), 1e-3),
+    "noise_annulus": (W.noise_annulus_problem,
+                      lambda: np.array([[0.5, -0.6, 0.0, 0.7, -0.4, 0.2], [0.2, 0.3, -0.8, -0.5, -0.5, 0.9]],
+                                       dtype=np.float32), 1e-3),
+    "noise_cube": (W.noise_cube_problem, lambda: W.uniform_in_box(3, 24, 0.1, 0.9, 6), 1e-3),
+}
+
+
+@pytest.mark.parametrize("name", list(REPLAY_CASES))
+def test_fp64_replay_matches_oracle_per_walk(orc, ctx, name):
+    mk, ptsf, eps = REPLAY_CASES[name]
+    desc = mk()
+    pts = ptsf()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 64 if desc["dim"] == 3 else 128)[0]
+    wpp = 16
+    uh, st, stats = ctx.walk_estimates(prob, dev(pts), wpp, eps, sb, seed=7, precision="fp64")
+    uo, so = orc.walks(desc, pts, wpp, seed=7, eps=eps, sigma_bar=sb)
+    uh = uh.cpu().numpy()
+    st = st.cpu().numpy()
+    ok = np.abs(uh - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
+    assert ok.mean() >= 0.99, (name, ok.mean(), np.abs(uh - uo).max())
+    assert (st == so).mean() >= 0.99
+    s = dict(zip(["steps", "walks", "capped", "nonfinite", "outside"], stats.cpu().tolist()))
+    assert s["walks"] == pts.shape[1] * wpp and s["steps"] == int(st.sum())
+
+
+def _gpu_solve(ctx, prob, pts, walks, eps, sb, seed, precision="fp32"):
+    acc, stats = ctx.solve(prob, dev(pts), walks, eps, sb, seed=seed, precision=precision)
+    m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+    return m, se, [int(x) for x in stats.cpu().tolist()], acc
+
+
+@pytest.mark.parametrize("same_seed", [True, False])
+def test_fp32_parity_square2d_full(orc, ctx, same_seed):
+    desc = W.square2d_problem()
+    pts = W.cell_centres(2, 32)
+    sb = orc.sigma_bar(desc)[0]
+    prob = ctx.problem(desc)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 256, 1e-3, sb, seed=0)
+    oacc, ost = orc.solve(desc, pts, 256, seed=0 if same_seed else 1, eps=1e-3, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (nout, mz)
+    assert st[2] == 0 and st[3] == 0 and st[1] == 1024 * 256
+    # steps per walk agree in distribution
+    assert abs(st[0] / st[1] - ost["steps"] / ost["walks"]) < 0.05 * ost["steps"] / ost["walks"]
+
+
+def test_fp32_parity_cube3d_subset(orc, ctx):
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 256, 9)]
+    sb = orc.sigma_bar(desc, 64)[0]
+    prob = ctx.problem(desc)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 1024, 1e-4, sb, seed=2)
+    oacc, _ = orc.solve(desc, pts, 1024, seed=3, eps=1e-4, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (nout, mz)
+
+
+@pytest.mark.parametrize("name", ["noise_annulus", "noise_cube", "rounded_box"])
+def test_fp32_parity_other_domains_and_grids(orc, ctx, name):
+    mk, ptsf, eps = REPLAY_CASES[name]
+    desc = mk()
+    pts = ptsf()
+    sb = orc.sigma_bar(desc, 64 if desc["dim"] == 3 else 128)[0]
+    prob = ctx.problem(desc)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 2048, eps, sb, seed=4)
+    oacc, _ = orc.solve(desc, pts, 2048, seed=5, eps=eps, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (name, nout, mz)
+
+
+def test_rms_square2d_at_2e16_walks(orc, ctx):
+    desc = W.square2d_problem()
+    pts = W.cell_centres(2, 32)
+    sb = orc.sigma_bar(desc)[0]
+    m, se, st, _ = _gpu_solve(ctx, ctx.problem(desc), pts, 1 << 16, 1e-3, sb, seed=11)
+    exact = W.square2d_exact(*pts.astype(np.float64))
+    assert normalised_rms(m, exact) <= 1e-2
+    assert st[2] == 0 and st[3] == 0
+
+
+def test_rms_cube3d_at_2e16_walks(orc, ctx):
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 4096, 12)]
+    sb = orc.sigma_bar(desc, 64)[0]
+    m, se, st, _ = _gpu_solve(ctx, ctx.problem(desc), pts, 1 << 16, 1e-4, sb, seed=12)
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    assert normalised_rms(m, exact) <= 1e-2
+    assert st[2] == 0 and st[3] == 0
+
+
+def test_full_size_cube3d_sampled_points(orc, ctx):
+    """The benchmark's workload and launch: 64^3 points x 1024 walks, seed 0."""
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)
+    sb = orc.sigma_bar(desc, 64)[0]
+    m, se, st, _ = _gpu_solve(ctx, ctx.problem(desc), pts, 1024, 1e-4, sb, seed=0)
+    assert st[1] == 64 ** 3 * 1024 and st[2] == 0 and st[3] == 0 and st[4] == 0
+    idx = W.seeded_subset(64 ** 3, 24, 13)
+    oacc, _ = orc.solve(desc, pts[:, idx], 1024, seed=1, eps=1e-4, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m[idx], se[idx], om, ose))
+    assert ok, (nout, mz)
+    # every point: estimate within 5 standard errors of the exact solution, bar a few
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    z = (m - exact) / se
+    assert np.mean(np.abs(z) > 5) < 5e-4
+    assert abs(np.mean(z)) < 0.05
+
+
+def test_sigma_bar_matches_oracle(orc, ctx):
+    for desc, m in ((W.square2d_problem(), 256), (W.cube3d_problem(), 64), (W.noise_annulus_problem(), 128)):
+        got = ctx.sigma_bar(ctx.problem(desc), m)
+        want = orc.sigma_bar(desc, m)
+        assert np.allclose(got, want, rtol=1e-9, atol=1e-9)
+
+
+def test_edge_cases(wos, orc, ctx):
+    desc = W.square2d_problem()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc)[0]
+    # empty input and zero walks are no-ops
+    acc = ctx.new_accum(4)
+    ctx.solve(prob, torch.zeros((2, 0), dtype=torch.float32, device="cuda"), 16, 1e-3, sb)
+    ctx.solve(prob, dev(W.cell_centres(2, 2)), 0, 1e-3, sb, accum=acc)
+    assert int(acc[2].sum()) == 0
+    # ragged: 1000 points x 37 walks (not multiples of the warp or the claim chunk)
+    pts = W.uniform_in_box(2, 1000, 0.01, 0.99, 14)
+    acc, st = ctx.solve(prob, dev(pts), 37, 1e-3, sb, seed=3)
+    assert (acc[2].cpu().numpy() == 37).all() and int(st[1]) == 37000
+    # per-point walk counts with zeros
+    walks = np.array([0, 5, 1, 0, 300, 7] * 50, dtype=np.int32)
+    pts = W.uniform_in_box(2, len(walks), 0.05, 0.95, 15)
+    acc, st = ctx.solve(prob, dev(pts), torch.from_numpy(walks).cuda(), 1e-3, sb, seed=4)
+    assert np.array_equal(acc[2].cpu().numpy(), walks) and int(st[1]) == walks.sum()
+    # walk-id continuation: walks 8..15 of one call are walks 0..7 of a call at offset 8
+    pts = W.uniform_in_box(2, 20, 0.05, 0.95, 16)
+    a, _, _ = ctx.walk_estimates(prob, dev(pts), 16, 1e-3, sb, seed=5, precision="fp64")
+    b, _, _ = ctx.walk_estimates(prob, dev(pts), 8, 1e-3, sb, seed=5, walk_offset=8, precision="fp64")
+    assert torch.equal(a[:, 8:], b)
+    # accumulating two calls equals counting both
+    acc = ctx.new_accum(20)
+    ctx.solve(prob, dev(pts), 10, 1e-3, sb, seed=6, accum=acc)
+    ctx.solve(prob, dev(pts), 10, 1e-3, sb, seed=6, walk_offset=10, accum=acc)
+    assert (acc[2].cpu().numpy() == 20).all()
+    # points in the epsilon shell return g at the closest point, zero variance
+    pts = np.array([[0.5, 2e-4, 0.3], [0.9995, 0.5, 1 - 1e-4]], dtype=np.float32)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 9, 1e-3, sb, seed=7)
+    want = [W.square2d_exact(*orc.distance(desc, pts[:, i].astype(np.float64))[1]) for i in range(3)]
+    assert np.allclose(m, want, rtol=1e-6) and np.all(se == 0) and st[0] == 0
+    # invalid arguments are rejected with WOS_EINVAL
+    for kw in ({"eps": 0.0}, {"eps": -1.0}, {"sigma_bar": 0.0}, {"sigma_bar": float("nan")},
+               {"max_steps": 0}):
+        args = {"eps": 1e-3, "sigma_bar": sb, "max_steps": 1 << 20}
+        args.update(kw)
+        with pytest.raises(wos.WosError) as e:
+            ctx.solve(prob, dev(pts), 4, args["eps"], args["sigma_bar"], max_steps=args["max_steps"])
+        assert e.value.code == wos.WOS_EINVAL
+    bad = W.square2d_problem()
+    bad["dim"] = 4
+    with pytest.raises(wos.WosError):
+        ctx.problem(bad)
+    bad = W.square2d_problem()
+    bad["alpha"] = W.const(-1.0)
+    with pytest.raises(wos.WosError):
+        ctx.problem(bad)
+    bad = W.noise_cube_problem()
+    bad["alpha"]["kind"] = "grid_linear"
+    with pytest.raises(wos.WosError):
+        ctx.problem(bad)
+    # step cap: counted, never hidden
+    _, st = ctx.solve(prob, dev(W.cell_centres(2, 4)), 50, 1e-3, sb, max_steps=2)
+    st = [int(x) for x in st.cpu().tolist()]
+    assert st[2] > 0 and st[0] <= 2 * st[1]
+
+
+def test_solve_host_matches_device(orc, ctx):
+    desc = W.cube3d_problem()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 64)[0]
+    pts = W.cell_centres(3, 16)
+    m_d, se_d, _, _ = _gpu_solve(ctx, prob, pts, 64, 1e-4, sb, seed=9)
+    mean, var, se, stats = ctx.solve_host(prob, pts, 64, 1e-4, sb, seed=9)
+    assert np.allclose(mean.numpy(), m_d, rtol=1e-12, atol=1e-12)
+    assert np.allclose(se.numpy(), se_d, rtol=1e-9, atol=1e-12)
+    assert int(stats[1]) == 16 ** 3 * 64

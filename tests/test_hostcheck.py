@@ -1,0 +1,97 @@
+"""The kernels' step math compiled for the host (same header) against
+independent references: scipy's Bessel functions and the FP64 oracle's Green's
+function, radial CDF and inverse CDF (Supplemental 1.1), Philox known answers."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+DP = C.POINTER(C.c_double)
+
+
+@pytest.fixture(scope="module")
+def hc():
+    from paper_2201_13240_gb300 import build as B
+    return C.CDLL(B.build_hostcheck())
+
+
+def _call(fn, *args, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    fn(*args, x.ctypes.data_as(DP), len(x), out.ctypes.data_as(DP))
+    return out
+
+
+X = np.concatenate([np.linspace(1e-3, 4, 300), np.linspace(4, 600, 300)])
+
+
+@pytest.mark.parametrize("which", range(4))
+def test_bessel_fp32_abramowitz_stegun(hc, which):
+    ref = [sp.i0, sp.i1, sp.k0, sp.k1][which]
+    x = X[X < 80]
+    got = _call(hc.wos_hc_bessel_f32, which, x=x)
+    assert np.max(np.abs(got / ref(x) - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("which", range(4))
+def test_bessel_fp64(hc, which):
+    ref = [sp.i0e, sp.i1e, sp.k0e, sp.k1e][which]
+    scale = [np.exp(-X), np.exp(-X), np.exp(X), np.exp(X)][which]
+    got = _call(hc.wos_hc_bessel_f64, which, x=X)
+    assert np.max(np.abs(got * scale / ref(X) - 1)) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_green_norm(hc, orc, dim, fp64):
+    a = np.concatenate([[0.0], np.logspace(-4, 2.5, 200)])
+    want = np.array([orc.green_norm(dim, 1.0, x * x) if x > 0 else 1 / (2 * dim) for x in a])
+    got = _call(hc.wos_hc_green_q, dim, fp64, x=a)
+    assert np.max(np.abs(got / want - 1)) < (1e-13 if fp64 else 5e-6)
+
+
+A = [1e-4, 0.1, 0.5, 0.99, 1.0, 1.5, 1.99, 2.0, 2.5, 3.7, 3.8, 6.0, 20.0, 60.0, 200.0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_radial_cdf(hc, orc, dim, fp64):
+    rho = np.linspace(1e-4, 1 - 1e-4, 120)
+    for a in A:
+        F = np.zeros_like(rho)
+        P = np.zeros_like(rho)
+        hc.wos_hc_radial(dim, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), F.ctypes.data_as(DP),
+                         P.ctypes.data_as(DP))
+        Fo = np.array([orc.green_cdf(dim, 1.0, a * a, r) for r in rho])
+        Po = np.array([orc.green_pdf(dim, 1.0, a * a, r) for r in rho])
+        assert np.max(np.abs(F - Fo)) < (1e-13 if fp64 else 2e-6), a
+        assert np.max(np.abs(P - Po)) / np.max(np.abs(Po)) < (1e-12 if fp64 else 5e-6), a
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_sampled_radius_inverts_cdf(hc, orc, dim, fp64):
+    for a in [1e-4, 0.3, 0.99, 1.01, 1.99, 2.01, 3.0, 5.0, 10.0, 30.0, 100.0, 400.0]:
+        u = np.concatenate([np.linspace(1e-6, 1 - 1e-6, 200), [1e-7, 1e-5, 0.999999]])
+        if not fp64:
+            u = (np.floor(u * 2 ** 24) + 0.5) / 2 ** 24
+        rho = np.zeros_like(u)
+        hc.wos_hc_sample_radius(dim, fp64, C.c_double(a), u.ctypes.data_as(DP), len(u), rho.ctypes.data_as(DP))
+        Fo = np.array([orc.green_cdf(dim, 1.0, a * a, r) for r in rho])
+        # FP32: the sampled distribution's CDF is off by < 2e-6 (absolute)
+        assert np.max(np.abs(Fo - u)) < (1e-12 if fp64 else 2e-6), a
+        if fp64:
+            ro = np.array([orc.green_inv(dim, 1.0, a * a, x) for x in u])
+            assert np.max(np.abs(ro - rho)) < 1e-10, a
+
+
+def test_philox_matches_oracle(hc, orc):
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        ctr = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+        out = np.zeros(4, dtype=np.uint32)
+        hc.wos_hc_philox(ctr.ctypes.data_as(C.POINTER(C.c_uint32)), key.ctypes.data_as(C.POINTER(C.c_uint32)),
+                         out.ctypes.data_as(C.POINTER(C.c_uint32)))
+        assert list(out) == orc.philox4x32_10(ctr, key)

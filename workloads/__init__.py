@@ -235,3 +235,73 @@ def uniform_in_box(dim, n, lo, hi, seed):
     rng = np.random.default_rng(seed)
     x = rng.uniform(lo, hi, size=(dim, n))
     return np.ascontiguousarray(x.astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# seeded value-noise grids: a lattice of uniform random values every `cell`
+# nodes, interpolated with the quintic fade 6t^5 - 15t^4 + 10t^3 (C^2) onto the
+# node grid and mapped affinely to [vmin, vmax]
+# ---------------------------------------------------------------------------
+def value_noise_grid(dim, res, vmin, vmax, seed, cell=8):
+    rng = np.random.default_rng(seed)
+    nl = (res - 1) // cell + 2
+    lattice = rng.uniform(0.0, 1.0, size=(nl,) * dim)
+    s = np.arange(res, dtype=np.float64) / cell
+    i0 = np.minimum(np.floor(s).astype(np.int64), nl - 2)
+    t = s - i0
+    w = t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    out = np.zeros((res,) * dim)
+    for corner in range(1 << dim):
+        idx = []
+        wt = np.ones((res,) * dim)
+        for d in range(dim):
+            o = (corner >> d) & 1
+            shape = [1] * dim
+            shape[dim - 1 - d] = res          # axis d is the (dim-1-d)-th array axis (x fastest)
+            wd = (w if o else 1.0 - w).reshape(shape)
+            wt = wt * wd
+            idx.append((i0 + o).reshape(shape))
+        # lattice indexed [z][y][x]
+        out += wt * lattice[tuple(idx[::-1])]
+    return (vmin + (vmax - vmin) * out).astype(np.float32)
+
+
+def grid_field(kind, data, lo, hi):
+    res = list(data.shape[::-1])
+    return {"kind": kind, "res": res, "lo": list(lo), "hi": list(hi), "data": data}
+
+
+def noise_cube_problem(res=33, seed=11):
+    """Unit cube with noise coefficients: alpha in [0.5, 2] (cubic B-spline),
+    sigma in [0, 20] and f in [-1, 1] (multilinear), g = x y + z."""
+    lo, hi = [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]
+    a = value_noise_grid(3, res, 0.5, 2.0, seed, cell=8)
+    s = value_noise_grid(3, res, 0.0, 20.0, seed + 1, cell=8)
+    f = value_noise_grid(3, res, -1.0, 1.0, seed + 2, cell=8)
+    g = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)), term(1.0, None, None, (LIN, 1.0, 0.0)))
+    return problem(3, box(lo, hi), grid_field("grid_bspline", a, lo, hi),
+                   grid_field("grid_linear", s, lo, hi), grid_field("grid_linear", f, lo, hi), g)
+
+
+def noise_annulus_problem(seed=21):
+    """2D annulus with a B-spline noise alpha, a noise drift potential and a screening field."""
+    lo, hi = [-1.2, -1.2], [1.2, 1.2]
+    a = value_noise_grid(2, 49, 0.5, 2.0, seed, cell=8)
+    ph = value_noise_grid(2, 49, -0.5, 0.5, seed + 1, cell=8)
+    s = value_noise_grid(2, 49, 0.0, 10.0, seed + 2, cell=8)
+    g = sst(term(1.0, (COS, PI, 0.0), (LIN, 1.0, 0.0)))
+    f = sst(term(1.0, (SIN, 2.0, 0.0), (COS, 3.0, 0.0)))
+    return problem(2, annulus([0.0, 0.0], 0.35, 1.1), grid_field("grid_bspline", a, lo, hi),
+                   grid_field("grid_linear", s, lo, hi), f, g,
+                   phi=grid_field("grid_bspline", ph, lo, hi))
+
+
+def rounded_box_problem():
+    """2D rounded box, alpha = 1 + 0.3 sin(2x) sin(3y), sigma = 3, manufactured u = cos(x) e^{0.5 y}."""
+    u = sst(term(1.0, (COS, 1.0, 0.0), (EXP, 0.5, 0.0)))
+    alpha = sst(term(1.0), term(0.3, (SIN, 2.0, 0.0), (SIN, 3.0, 0.0)))
+    return problem(2, rounded_box([0.1, -0.2], [1.0, 0.7], 0.3), alpha, const(3.0), manufactured(), u, um=u)
+
+
+def rounded_box_exact(x, y):
+    return np.cos(x) * np.exp(0.5 * y)
