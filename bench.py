@@ -47,7 +47,8 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "cube3d_drift_manufactured: 64^3 points x 1024 walks, eps 1e-4, FP32 walks, FP64 sums",
+    cfg = {"workload": f"cube3d_drift_manufactured: {GRID}^3 points x {WALKS} walks, eps 1e-4, FP32 walks, "
+                       "FP64 sums",
            "points": GRID ** 3, "walks_per_point": WALKS, "eps": EPS, "seed": SEED,
            "l2": "flushed between timed steps (512 MiB write)"}
     if extra:
@@ -293,11 +294,13 @@ def run_ours(args):
         return 0
 
     # CPU baseline: the oracle on a bounded sample on this host's cores
-    cpu_pts = 512
-    o_steps, o_t = oracle_rate(desc, sb, cpu_pts, WALKS, seed=SEED)
-    cpu = {"value": o_steps / o_t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"{cpu_pts} seeded points of the workload x {WALKS} walks, FP64 oracle, OpenMP, "
-                     f"{o_t:.1f} s"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu_pts = 512
+        o_steps, o_t = oracle_rate(desc, sb, cpu_pts, WALKS, seed=SEED)
+        cpu = {"value": o_steps / o_t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{cpu_pts} seeded points of the workload x {WALKS} walks, FP64 oracle, OpenMP, "
+                         f"{o_t:.1f} s"}
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -319,12 +322,17 @@ def run_ours(args):
 
 
 def main():
+    global GRID, WALKS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
+    ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     args = ap.parse_args()
+    GRID, WALKS = args.grid, args.walks
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -96,6 +96,20 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+def _points(pts, dim, device):
+    """Validate a device point array [dim, npts] and return it as a contiguous float32 tensor."""
+    import torch
+    if not isinstance(pts, torch.Tensor) or not pts.is_cuda:
+        raise TypeError("points must be a CUDA tensor of shape [dim, npts]")
+    if pts.dim() != 2 or pts.shape[0] != dim:
+        raise ValueError(f"points must have shape [{dim}, npts], got {tuple(pts.shape)}")
+    if pts.dtype != torch.float32:
+        raise TypeError("points must be float32")
+    if pts.device.index != device:
+        raise ValueError(f"points live on {pts.device}, the context on cuda:{device}")
+    return pts.contiguous()
+
+
 def params(eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32"):
     p = Params()
     p.eps = float(eps)
@@ -217,16 +231,22 @@ class Context:
               accum=None, stats=None, stream=None):
         """Add walks to the accumulators (sum, sumsq, count); pts: cuda float32 [dim, npts]."""
         import torch
-        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[0] == prob.dim
+        pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
         if accum is None:
             accum = self.new_accum(npts)
+        if not (accum[0].dtype == torch.float64 and accum[1].dtype == torch.float64 and accum[2].dtype == torch.int64
+                and all(t.is_cuda and t.is_contiguous() and t.shape == (npts,) for t in accum)):
+            raise TypeError("accumulators must be contiguous CUDA (float64, float64, int64) tensors of length npts")
         if stats is None:
             stats = self.new_stats()
         if isinstance(walks, int):
             wp, wu = None, walks
         else:
-            assert walks.is_cuda and walks.dtype == torch.int32
+            if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                    and walks.shape == (npts,)):
+                raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+            walks = walks.contiguous()
             wp, wu = _ptr(walks), 0
         p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
         self._check(self.lib.wos_solve(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
@@ -237,6 +257,7 @@ class Context:
     def walk_estimates(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
                        precision="fp32", stream=None):
         import torch
+        pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
         dev = f"cuda:{self.device}"
         uhat = torch.empty((npts, walks_per_point), dtype=torch.float64, device=dev)
@@ -250,6 +271,8 @@ class Context:
     def finalize(self, accum, stream=None):
         import torch
         n = accum[0].shape[0]
+        if not all(t.is_cuda and t.is_contiguous() and t.shape == (n,) for t in accum):
+            raise TypeError("accumulators must be contiguous CUDA tensors of one length")
         mean, var, se = (torch.empty(n, dtype=torch.float64, device=accum[0].device) for _ in range(3))
         self._check(self.lib.wos_finalize(self.handle, _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), n,
                                           _ptr(mean), _ptr(var), _ptr(se), _stream(stream)))
@@ -262,6 +285,9 @@ class Context:
         import torch
         if isinstance(pts_host, np.ndarray):
             pts_host = torch.from_numpy(np.ascontiguousarray(pts_host, dtype=np.float32))
+        if pts_host.is_cuda or pts_host.dtype != torch.float32 or pts_host.dim() != 2 or pts_host.shape[0] != prob.dim:
+            raise TypeError(f"host points must be a float32 CPU array of shape [{prob.dim}, npts]")
+        pts_host = pts_host.contiguous()
         npts = pts_host.shape[1]
         if out is None:
             out = (torch.empty(npts, dtype=torch.float64), torch.empty(npts, dtype=torch.float64),

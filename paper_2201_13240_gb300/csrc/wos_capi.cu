@@ -27,6 +27,8 @@ struct wos_ctx {
   // walks-per-point prefix sums
   int64_t* walk_end = nullptr;
   int64_t walk_end_cap = 0;
+  // FP32 inverse radial CDF start tables for 2D and 3D (wos::kTabSize floats each)
+  float* radial_tab[2] = {nullptr, nullptr};
   // buffers of wos_solve_host
   float* h_pts = nullptr;
   double* h_acc = nullptr;  // sum, sumsq, mean, var, se: 5 * cap doubles
@@ -254,6 +256,17 @@ __global__ void walk_prefix_kernel(const int32_t* walks, int64_t n, int64_t* out
   }
 }
 
+// FP64 inverse radial CDF on the (a, u) grid of the FP32 Newton start table
+template <int DIM>
+__global__ void radial_table_kernel(float* tab) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= wos::kTabSize) return;
+  int ia = i / wos::kTabU, iu = i % wos::kTabU;
+  double a = ia * (double)wos::kTabDA, u = (double)iu / (wos::kTabU - 1);
+  double r = (iu == 0) ? 0.0 : (iu == wos::kTabU - 1) ? 1.0 : wos::sample_radius<DIM, double>(a, u);
+  tab[i] = (float)r;
+}
+
 __global__ void finalize_kernel(const double* sum, const double* sumsq, const int64_t* count, int64_t n,
                                 double* mean, double* var, double* se) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -308,6 +321,7 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.work_counter = ctx->scratch;
   L.uhat = uhat;
   L.steps_out = steps;
+  L.radial_tab = ctx->radial_tab[prob->dim - 2];
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
@@ -361,6 +375,19 @@ int wos_create(wos_ctx** out, int device) {
     return WOS_ENOMEM;
   }
   cudaMemset(ctx->scratch, 0, kScratchWords * sizeof(unsigned long long));
+  for (int k = 0; k < 2; ++k) {
+    if (cudaMalloc(&ctx->radial_tab[k], wos::kTabSize * sizeof(float)) != cudaSuccess) {
+      wos_destroy(ctx);
+      return WOS_ENOMEM;
+    }
+  }
+  int blocks = (wos::kTabSize + 127) / 128;
+  radial_table_kernel<2><<<blocks, 128>>>(ctx->radial_tab[0]);
+  radial_table_kernel<3><<<blocks, 128>>>(ctx->radial_tab[1]);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    wos_destroy(ctx);
+    return WOS_ECUDA;
+  }
   *out = ctx;
   return WOS_OK;
 }
@@ -370,6 +397,8 @@ int wos_destroy(wos_ctx* ctx) {
   {
     DeviceGuard g(ctx->device);
     cudaFree(ctx->scratch);
+    for (int k = 0; k < 2; ++k)
+      if (ctx->radial_tab[k]) cudaFree(ctx->radial_tab[k]);
     if (ctx->walk_end) cudaFree(ctx->walk_end);
     if (ctx->h_pts) cudaFree(ctx->h_pts);
     if (ctx->h_acc) cudaFree(ctx->h_acc);

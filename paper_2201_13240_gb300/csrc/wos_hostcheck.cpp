@@ -90,4 +90,35 @@ void wos_hc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
   out[3] = o.w;
 }
 
+// the inverse-CDF table the library builds on the device, built here on the host
+static float g_tab[2][wos::kTabSize];
+static int g_tab_ready[2] = {0, 0};
+static const float* host_table(int dim) {
+  int k = dim - 2;
+  if (!g_tab_ready[k]) {
+    for (int i = 0; i < wos::kTabSize; ++i) {
+      int ia = i / wos::kTabU, iu = i % wos::kTabU;
+      double a = ia * (double)wos::kTabDA, u = (double)iu / (wos::kTabU - 1);
+      double r = (iu == 0) ? 0.0 : (iu == wos::kTabU - 1) ? 1.0
+               : (dim == 2 ? wos::sample_radius<2, double>(a, u) : wos::sample_radius<3, double>(a, u));
+      g_tab[k][i] = (float)r;
+    }
+    g_tab_ready[k] = 1;
+  }
+  return g_tab[k];
+}
+
+// rho and the number of Newton iterations of the FP32 sampler; use_table selects the
+// tabulated start (as the kernels do) instead of the closed-form one
+void wos_hc_sample_f32(int dim, int use_table, double a, const double* u, int64_t n, double* rho, double* iters) {
+  const float* tab = use_table ? host_table(dim) : nullptr;
+  for (int64_t i = 0; i < n; ++i) {
+    int it = 0;
+    float r = (dim == 2) ? wos::sample_radius<2, float>((float)a, (float)u[i], &it, tab)
+                         : wos::sample_radius<3, float>((float)a, (float)u[i], &it, tab);
+    rho[i] = r;
+    iters[i] = it;
+  }
+}
+
 }  // extern "C"

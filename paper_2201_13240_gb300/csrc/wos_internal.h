@@ -31,6 +31,7 @@ struct WalkLaunch {
   unsigned long long* work_counter;  // zeroed before the launch
   double* uhat;                   // optional per-walk estimates [total_items]
   int64_t* steps_out;             // optional per-walk step counts [total_items]
+  const float* radial_tab;        // FP32 Newton start table of the launch's dimension
 };
 
 // launch the persistent walk kernel; returns a cudaError_t

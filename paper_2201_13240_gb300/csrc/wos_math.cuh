@@ -589,14 +589,17 @@ struct Radial2<double> {
 // FP32 runs a fixed number of iterations from a closed-form starting point;
 // FP64 iterates to convergence.
 // ---------------------------------------------------------------------------
+// Stops when the step is below tol or the CDF residual is below ftol (FP32: a few
+// ulps of u, the level at which rounding noise in F would make Newton oscillate).
 template <typename Rad, typename R>
-WOS_HD R newton_inverse(const Rad& rad, R u, R rho, int iters, R tol) {
+WOS_HD R newton_inverse(const Rad& rad, R u, R rho, int iters, R tol, R ftol, int* iters_used = nullptr) {
   R lo = R(0), hi = R(1);
-  for (int it = 0; it < iters; ++it) {
+  int it = 0;
+  for (; it < iters; ++it) {
     R F, p;
     rad.eval(rho, &F, &p);
     R res = F - u;
-    if (res == R(0)) break;
+    if (w_fabs(res) <= ftol) break;
     if (res > R(0)) hi = rho; else lo = rho;
     R nr = (p > R(0)) ? rho - res / p : R(0.5) * (lo + hi);
     // Newton may land on the bracket end it started from once converged; only
@@ -606,6 +609,7 @@ WOS_HD R newton_inverse(const Rad& rad, R u, R rho, int iters, R tol) {
     rho = nr;
     if (step <= tol) break;
   }
+  if (iters_used) *iters_used = it;
   return rho;
 }
 
@@ -627,19 +631,59 @@ WOS_HD R radial_guess(R a, R u) {
   return w_fmin(t / a, R(0.999));
 }
 
+// Tabulated inverse radial CDF rho(u; a) on a uniform grid a = i * kTabDA
+// (i < kTabA), u = j / (kTabU - 1), filled in FP64 by the sampler below; its
+// bilinear interpolation is the FP32 Newton start (within ~1e-3 of the root,
+// so one or two iterations reach the FP32 tolerance).
+constexpr int kTabA = 129;
+constexpr int kTabU = 129;
+constexpr float kTabDA = 0.25f;
+constexpr int kTabSize = kTabA * kTabU;
+
+WOS_HD float load_tab(const float* p) {
+#if defined(__CUDA_ARCH__)
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
+WOS_HD float table_guess(const float* tab, float a, float u) {
+  float fa = a * (1.0f / kTabDA);
+  int ia = (int)fa;
+  if (ia > kTabA - 2) ia = kTabA - 2;
+  float ta = fa - (float)ia;
+  float fu = u * (float)(kTabU - 1);
+  int iu = (int)fu;
+  if (iu > kTabU - 2) iu = kTabU - 2;
+  float tu = fu - (float)iu;
+  const float* r0 = tab + ia * kTabU + iu;
+  const float* r1 = r0 + kTabU;
+  float v0 = load_tab(r0) + tu * (load_tab(r0 + 1) - load_tab(r0));
+  float v1 = load_tab(r1) + tu * (load_tab(r1 + 1) - load_tab(r1));
+  return v0 + ta * (v1 - v0);
+}
+
 template <int DIM, typename R>
-WOS_HD R sample_radius(R a, R u) {
+WOS_HD R sample_radius(R a, R u, int* iters_used = nullptr, const float* tab = nullptr) {
   const int iters = (sizeof(R) == 4) ? 12 : 200;
   const R tol = (sizeof(R) == 4) ? R(1e-7) : R(1e-16);
-  R g = radial_guess<DIM, R>(a, u);
+  const R ftol = (sizeof(R) == 4) ? R(1e-6) : R(0);
+  R g;
+  if (tab != nullptr && a < R((kTabA - 1) * kTabDA)) {
+    g = R(table_guess(tab, (float)a, (float)u));
+    g = w_fmin(w_fmax(g, R(1e-6)), R(1) - R(1e-6));
+  } else {
+    g = radial_guess<DIM, R>(a, u);
+  }
   if (DIM == 3) {
     Radial3<R> rad;
     rad.init(a);
-    return newton_inverse(rad, u, g, iters, tol);
+    return newton_inverse(rad, u, g, iters, tol, ftol, iters_used);
   } else {
     Radial2<R> rad;
     rad.init(a);
-    return newton_inverse(rad, u, g, iters, tol);
+    return newton_inverse(rad, u, g, iters, tol, ftol, iters_used);
   }
 }
 

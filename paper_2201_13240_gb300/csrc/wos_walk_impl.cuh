@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
     R q = green_q<DIM, R>(a);
     R Gn = d * d * q;          // |G| on the ball of radius d
     R PB = a * a * q;          // sigma_bar |G|, probability of the volume term
-    R r = sample_radius<DIM, R>(a, ur) * d;
+    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * d;
     R y[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? s.x[i] + r * dy[i] : R(0);

@@ -207,7 +207,7 @@ def screened_ball_exact(sig, x, y, z):
 # evaluation points (SoA float32 [dim][npts])
 # ---------------------------------------------------------------------------
 def cell_centres(dim, n, lo=0.0, hi=1.0):
-    """Cell centres of an n^dim grid on [lo, hi]^dim; x varies fastest."""
+    """Cell centres of an n^dim grid on [lo, hi]^dim; x varies fastest (C-contiguous SoA)."""
     c = (np.arange(n, dtype=np.float64) + 0.5) / n * (hi - lo) + lo
     mesh = np.meshgrid(*([c] * dim), indexing="ij")
     # x fastest: reverse the axis order of the flattened index
@@ -232,9 +232,10 @@ def uniform_in_ball(dim, n, centre, radius, seed, margin=0.0):
 
 
 def uniform_in_box(dim, n, lo, hi, seed):
+    """n uniform points in the box [lo, hi] (scalars or per-axis bounds), SoA float32."""
     rng = np.random.default_rng(seed)
-    x = rng.uniform(lo, hi, size=(dim, n))
-    return np.ascontiguousarray(x.astype(np.float32))
+    x = rng.uniform(lo, hi, size=(n, dim))
+    return np.ascontiguousarray(x.T.astype(np.float32))
 
 
 # ---------------------------------------------------------------------------
