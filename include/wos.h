@@ -200,6 +200,38 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host,
                    int32_t walks_uniform, const wos_params* params, double* mean_host,
                    double* var_host, double* stderr_host, uint64_t* stats_host, void* stream);
 
+/* ---- allocation-free solve ----
+   The paper has no counterpart: this entry point exists for callers that cannot
+   allocate device memory -- code running inside an allocator hook or a memory-pool
+   callback, plugins whose host program owns every allocation and forbids
+   cudaMalloc/cudaFree, and programs that must not synchronise the device (cudaFree
+   does).  It needs no context and no wos_problem: the problem description is passed
+   directly, and the walk kernel's scratch (work counter, default statistics, the
+   uploaded description and the per-point walk prefix sums) lives in one static
+   device array of WOS_NOALLOC_SCRATCH_BYTES that the library's module image carries,
+   so every GPU that loads this library holds it until the process exits.  The call
+   performs no cudaMalloc, cudaFree or other allocating routine.
+
+   Same arguments and results as wos_solve, on the CURRENT CUDA device, except:
+     - desc: host problem description (validated on every call; grid data are device
+       pointers owned by the caller);
+     - walks (per-point counts) is limited to npts <= WOS_NOALLOC_MAX_VAR_POINTS, the
+       capacity of the static prefix-sum buffer; larger npts with walks != NULL returns
+       WOS_EINVAL (uniform walk counts have no point limit);
+     - errors are reported by the return code only (WOS_EINVAL, WOS_ECUDA);
+     - FP32 walks start Newton from the closed-form guess instead of the context's
+       inverse-CDF table: same distribution, somewhat slower.
+   The first call on a device resolves the address of the static array
+   (cudaGetSymbolAddress) for that device; make that first call outside any CUDA
+   stream capture.  Every call on a device shares the one array and the call resets
+   what must start at zero; calls whose work overlaps on the GPU (other streams, other
+   host threads) race on it and must be serialised by the caller. */
+#define WOS_NOALLOC_MAX_VAR_POINTS 65536
+#define WOS_NOALLOC_SCRATCH_BYTES (16640 + 8 * WOS_NOALLOC_MAX_VAR_POINTS)
+int wos_solve_noalloc(const wos_problem_desc* desc, const float* pts, int64_t npts, const int32_t* walks,
+                      int32_t walks_uniform, const wos_params* params, double* sum, double* sumsq,
+                      int64_t* count, uint64_t* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

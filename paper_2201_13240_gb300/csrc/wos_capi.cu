@@ -639,3 +639,186 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* pr, const float* pts_host, i
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free solve.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// host allocator hook or a memory-pool callback, plugins whose host program
+// owns every allocation and forbids cudaMalloc/cudaFree, and programs that
+// must not synchronise the device, which cudaFree does.  wos_solve_noalloc
+// serves them.  It runs the same walk kernel as wos_solve, but the kernel's
+// scratch (work counter, default statistics, the problem description and the
+// per-point walk prefix sums) lives in the file-scope device array below
+// instead of context memory.  That array is part of the module image, so every
+// GPU that loads this library holds it (WOS_NOALLOC_SCRATCH_BYTES) until the
+// process exits.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNaCounter = 0;        // work counter (8 bytes)
+constexpr size_t kNaStats = 64;         // default statistics (WOS_STATS_WORDS x 8 bytes)
+constexpr size_t kNaProblem = 256;      // DevProblem<float> or DevProblem<double>
+constexpr size_t kNaProblemBytes = 16384;
+constexpr size_t kNaPrefix = kNaProblem + kNaProblemBytes;  // int64 walk prefix sums
+constexpr size_t kNaBytes = kNaPrefix + sizeof(int64_t) * (size_t)WOS_NOALLOC_MAX_VAR_POINTS;
+static_assert(kNaBytes == WOS_NOALLOC_SCRATCH_BYTES, "header and scratch layout disagree");
+static_assert(sizeof(DevProblem<double>) <= kNaProblemBytes, "problem does not fit the static scratch");
+static_assert(kNaProblem % 256 == 0 && kNaPrefix % 256 == 0, "scratch regions must stay 256-byte aligned");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// device address of g_noalloc_scratch for each device, resolved on first use
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNaMaxDevices] = {nullptr};
+
+// validation without host allocation (no message strings)
+bool na_field_ok(const wos_field_desc& f, int dim, bool is_source, bool needs_c2) {
+  if (f.kind < WOS_FIELD_ZERO || f.kind > WOS_FIELD_GRID_BSPLINE) return false;
+  if (f.kind == WOS_FIELD_MANUFACTURED && !is_source) return false;
+  if (needs_c2 && f.kind == WOS_FIELD_GRID_LINEAR) return false;
+  if (f.kind == WOS_FIELD_SST) {
+    if (f.nterms < 0 || f.nterms > wos::kMaxTerms || (f.nterms > 0 && f.terms == nullptr)) return false;
+    for (int n = 0; n < f.nterms; ++n) {
+      if (!std::isfinite(f.terms[n].c)) return false;
+      for (int d = 0; d < dim; ++d)
+        if (f.terms[n].type[d] < WOS_ATOM_ONE || f.terms[n].type[d] > WOS_ATOM_QUAD ||
+            !std::isfinite(f.terms[n].k[d]) || !std::isfinite(f.terms[n].phi[d]))
+          return false;
+    }
+  }
+  if (f.kind == WOS_FIELD_CONST && !std::isfinite(f.value)) return false;
+  if (f.kind == WOS_FIELD_GRID_LINEAR || f.kind == WOS_FIELD_GRID_BSPLINE) {
+    if (f.data == nullptr) return false;
+    for (int d = 0; d < dim; ++d)
+      if (f.res[d] < 2 || !(f.hi[d] > f.lo[d]) || !std::isfinite(f.lo[d]) || !std::isfinite(f.hi[d])) return false;
+  }
+  return true;
+}
+
+bool na_desc_ok(const wos_problem_desc* d) {
+  if (d->dim != 2 && d->dim != 3) return false;
+  const double* p = d->domain.p;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(p[i])) return false;
+  switch (d->domain.kind) {
+    case WOS_DOMAIN_BOX:
+      for (int i = 0; i < d->dim; ++i)
+        if (!(p[3 + i] > p[i])) return false;
+      break;
+    case WOS_DOMAIN_BALL:
+      if (!(p[3] > 0)) return false;
+      break;
+    case WOS_DOMAIN_ANNULUS:
+      if (!(p[3] >= 0 && p[4] > p[3])) return false;
+      break;
+    case WOS_DOMAIN_ROUNDED_BOX:
+      for (int i = 0; i < d->dim; ++i)
+        if (!(p[3 + i] > 0 && p[6] >= 0 && p[6] <= p[3 + i])) return false;
+      break;
+    default:
+      return false;
+  }
+  if (!na_field_ok(d->alpha, d->dim, false, true) || !na_field_ok(d->phi, d->dim, false, true) ||
+      !na_field_ok(d->sigma, d->dim, false, false) || !na_field_ok(d->f, d->dim, true, false) ||
+      !na_field_ok(d->g, d->dim, false, false) || !na_field_ok(d->um, d->dim, false, true))
+    return false;
+  if (d->alpha.kind == WOS_FIELD_ZERO) return false;
+  if (d->alpha.kind == WOS_FIELD_CONST && !(d->alpha.value > 0)) return false;
+  int total = 0;
+  const wos_field_desc* fl[6] = {&d->alpha, &d->phi, &d->sigma, &d->f, &d->g, &d->um};
+  for (auto* f : fl)
+    if (f->kind == WOS_FIELD_SST) total += f->nterms;
+  return total <= wos::kMaxTerms;
+}
+
+}  // namespace
+
+extern "C" int wos_solve_noalloc(const wos_problem_desc* desc, const float* pts, int64_t npts,
+                                 const int32_t* walks, int32_t walks_uniform, const wos_params* prm,
+                                 double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream) {
+  if (!desc || !prm) return WOS_EINVAL;
+  if (!finite_pos(prm->eps) || !finite_pos(prm->sigma_bar) || prm->max_steps < 1 ||
+      (prm->precision != WOS_FP32 && prm->precision != WOS_FP64))
+    return WOS_EINVAL;
+  if (!na_desc_ok(desc)) return WOS_EINVAL;
+  if (npts < 0 || npts > 0xffffffffll) return WOS_EINVAL;
+  if (walks != nullptr && npts > WOS_NOALLOC_MAX_VAR_POINTS) return WOS_EINVAL;  // prefix sums would not fit
+  if (walks == nullptr && walks_uniform < 0) return WOS_EINVAL;
+  if (npts == 0 || (walks == nullptr && walks_uniform == 0)) return WOS_OK;
+  if (!pts || !sum || !sumsq || !count) return WOS_EINVAL;
+
+  // one-time set-up on this device: resolve the scratch array's device address
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return WOS_ECUDA;
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return WOS_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  unsigned char* base = g_noalloc_ptr[dev];
+  int num_sms = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WOS_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // the problem description, filled on the host stack and copied into the scratch
+  const bool fp64 = prm->precision == WOS_FP64;
+  DevProblem<double> h64;
+  DevProblem<float> h32;
+  const void* hsrc;
+  size_t pbytes;
+  if (fp64) {
+    fill_problem(h64, *desc);
+    hsrc = &h64;
+    pbytes = sizeof(h64);
+  } else {
+    fill_problem(h32, *desc);
+    hsrc = &h32;
+    pbytes = sizeof(h32);
+  }
+  cudaError_t e = cudaMemcpyAsync(base + kNaProblem, hsrc, pbytes, cudaMemcpyHostToDevice, st);
+  // the work counter (and the default statistics) must start at zero on every call
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + kNaCounter, 0, 8, st);
+  unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
+  if (e == cudaSuccess && st_ptr == nullptr) {
+    st_ptr = reinterpret_cast<unsigned long long*>(base + kNaStats);
+    e = cudaMemsetAsync(st_ptr, 0, WOS_STATS_WORDS * sizeof(unsigned long long), st);
+  }
+  if (e != cudaSuccess) return WOS_ECUDA;
+
+  const int64_t* walk_end = nullptr;
+  uint64_t total;
+  if (walks != nullptr) {
+    int64_t* prefix = reinterpret_cast<int64_t*>(base + kNaPrefix);
+    walk_prefix_kernel<<<1, 1024, 0, st>>>(walks, npts, prefix);
+    if (cudaGetLastError() != cudaSuccess) return WOS_ECUDA;
+    walk_end = prefix;
+    total = ~0ull;
+  } else {
+    total = (uint64_t)npts * (uint64_t)walks_uniform;
+  }
+
+  wos::WalkLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.problem = base + kNaProblem;
+  L.problem_bytes = (int)pbytes;
+  L.dim = desc->dim;
+  L.pts = pts;
+  L.npts = npts;
+  L.walk_end = walk_end;
+  L.walks_uniform = walks_uniform;
+  L.total_items = total;
+  L.seed = prm->seed;
+  L.walk_offset = prm->walk_offset;
+  L.eps = prm->eps;
+  L.sigma_bar = prm->sigma_bar;
+  L.max_steps = prm->max_steps;
+  L.sum = sum;
+  L.sumsq = sumsq;
+  L.count = reinterpret_cast<unsigned long long*>(count);
+  L.stats = st_ptr;
+  L.work_counter = reinterpret_cast<unsigned long long*>(base + kNaCounter);
+  L.radial_tab = nullptr;  // no tables here: the FP32 Newton starts from its closed-form guess
+  e = fp64 ? wos::launch_walks_f64(L, num_sms, st) : wos::launch_walks_f32(L, num_sms, st);
+  return e == cudaSuccess ? WOS_OK : WOS_ECUDA;
+}
