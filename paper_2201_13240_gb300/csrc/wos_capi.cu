@@ -211,8 +211,7 @@ __global__ void sigma_range_kernel(const DevProblem<double>* Pg, int m, double l
     if (!(wos::distance<DIM>(P, x, xb) > 0.0)) continue;
     double sp, fp;
     wos::coeffs<DIM>(P, x, &sp, &fp);
-    double a, g[3], l;
-    wos::field_eval<DIM>(P, P.alpha, x, &a, g, &l, false);
+    double a = wos::field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
     mn = fmin(mn, sp);
     mx = fmax(mx, sp);
     amin = fmin(amin, a);

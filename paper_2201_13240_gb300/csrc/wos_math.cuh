@@ -29,10 +29,33 @@ namespace wos {
 // ---------------------------------------------------------------------------
 // real-type helpers
 // ---------------------------------------------------------------------------
-WOS_HD float w_exp(float x) { return expf(x); }
+// FP32 on the device uses the special-function unit (ex2/lg2/sin/cos.approx):
+// relative errors ~1e-6 over the argument ranges of a walk step, far below the
+// statistical error of any estimate, and no slow-path code in the kernel.
+WOS_HD float w_exp(float x) {
+#if defined(__CUDA_ARCH__)
+  return __expf(x);
+#else
+  return expf(x);
+#endif
+}
 WOS_HD double w_exp(double x) { return exp(x); }
-WOS_HD float w_log(float x) { return logf(x); }
+WOS_HD float w_log(float x) {
+#if defined(__CUDA_ARCH__)
+  return __logf(x);
+#else
+  return logf(x);
+#endif
+}
 WOS_HD double w_log(double x) { return log(x); }
+WOS_HD float w_div(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+WOS_HD double w_div(double a, double b) { return a / b; }
 WOS_HD float w_sqrt(float x) { return sqrtf(x); }
 WOS_HD double w_sqrt(double x) { return sqrt(x); }
 WOS_HD float w_rsqrt(float x) {
@@ -49,7 +72,7 @@ WOS_HD float w_cos(float x) { return cosf(x); }
 WOS_HD double w_cos(double x) { return cos(x); }
 WOS_HD void w_sincos(float x, float* s, float* c) {
 #if defined(__CUDA_ARCH__)
-  sincosf(x, s, c);
+  __sincosf(x, s, c);
 #else
   *s = sinf(x);
   *c = cosf(x);
@@ -66,7 +89,9 @@ WOS_HD void w_sincos(double x, double* s, double* c) {
 // sin(2 pi u), cos(2 pi u) for u in (0,1)
 WOS_HD void w_sincospi2(float u, float* s, float* c) {
 #if defined(__CUDA_ARCH__)
-  sincospif(2.0f * u, s, c);
+  __sincosf(6.2831853071795865f * u - 3.1415926535897932f, s, c);  // angle in (-pi, pi)
+  *s = -*s;
+  *c = -*c;
 #else
   *s = sinf(6.283185307179586f * u);
   *c = cosf(6.283185307179586f * u);
@@ -350,10 +375,10 @@ WOS_HD R green_q(R a) {
 // ---------------------------------------------------------------------------
 template <typename R>
 struct Radial3 {
+  static constexpr int NC = (sizeof(R) == 4) ? 5 : 10;  // series terms
   R a;
   int small;
-  R c[10];  // series: c_j / ((m+1)(m+2)) with m = 2j+1
-  int nc;
+  R c[NC];  // series: c_j / ((m+1)(m+2)) with m = 2j+1
   R invT;
   R invD, e2a;  // closed form
 
@@ -361,10 +386,9 @@ struct Radial3 {
     a = a_;
     small = (a < R(1));
     if (small) {
-      const int nmax = (sizeof(R) == 4) ? 5 : 10;
       R cj = R(1), T = R(0);
-      nc = nmax;
-      for (int j = 0; j < nmax; ++j) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
         R m = R(2 * j + 1);
         c[j] = cj / ((m + R(1)) * (m + R(2)));
         T += c[j];
@@ -396,7 +420,8 @@ struct Radial3 {
       R v = R(1) - rho;
       R v2 = v * v;
       R Q = R(0), dQ = R(0), vm = v;  // vm = v^m, m = 2j+1
-      for (int j = 0; j < nc; ++j) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
         R m = R(2 * j + 1);
         Q += c[j] * vm * v * ((m + R(2)) - (m + R(1)) * v);
         // d/dv [v^{m+1}((m+2) - (m+1) v)] = (m+1)(m+2) v^m (1 - v)
@@ -601,7 +626,7 @@ WOS_HD R newton_inverse(const Rad& rad, R u, R rho, int iters, R tol, R ftol, in
     R res = F - u;
     if (w_fabs(res) <= ftol) break;
     if (res > R(0)) hi = rho; else lo = rho;
-    R nr = (p > R(0)) ? rho - res / p : R(0.5) * (lo + hi);
+    R nr = (p > R(0)) ? rho - w_div(res, p) : R(0.5) * (lo + hi);
     // Newton may land on the bracket end it started from once converged; only
     // a step that leaves [lo, hi] falls back to bisection
     if (!(nr >= lo && nr <= hi)) nr = R(0.5) * (lo + hi);

@@ -97,6 +97,7 @@ template <int DIM, typename R>
 WOS_HD void sst_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap,
                      bool deriv) {
   R vv = R(0), ll = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
+#pragma unroll 1
   for (int n = 0; n < F.nterms; ++n) {
     const DevTerm<R>& T = P.terms[F.first + n];
     R h[3] = {R(1), R(1), R(1)}, h1[3] = {R(0), R(0), R(0)}, h2[3] = {R(0), R(0), R(0)};
@@ -226,48 +227,63 @@ WOS_HD void grid_bspline(const DevField<R>& F, const R* x, R* v, R* g, R* lap, b
   }
 }
 
-// value (and gradient / Laplacian when deriv) of a plain field
+// value, gradient and Laplacian of a field at a point
+template <typename R>
+struct FieldVal {
+  R v, gx, gy, gz, lap;
+};
+
+// value (and gradient / Laplacian when deriv) of a plain field.  On the device it
+// is one out-of-line function taking and returning registers: a step evaluates
+// several fields, and inlining the separable-term and B-spline code at every
+// call site made the walk kernel too large for the instruction cache.
+#if defined(__CUDACC__)
+#define WOS_FIELD_FN __host__ __device__ __noinline__
+#else
+#define WOS_FIELD_FN inline
+#endif
 template <int DIM, typename R>
-WOS_HD void field_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap,
-                       bool deriv) {
+WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F, R x0, R x1, R x2, bool deriv) {
+  FieldVal<R> o = {R(0), R(0), R(0), R(0), R(0)};
+  const R x[3] = {x0, x1, x2};
+  R g[3] = {R(0), R(0), R(0)};
   switch (F.kind) {
-    case F_CONST: *v = F.value; break;
-    case F_SST: sst_eval<DIM>(P, F, x, v, g, lap, deriv); return;
-    case F_GRID_LINEAR: *v = grid_linear<DIM>(F, x); break;  // piecewise linear: no second derivative
-    case F_GRID_BSPLINE: grid_bspline<DIM>(F, x, v, g, lap, deriv); return;
-    default: *v = R(0); break;
+    case F_CONST: o.v = F.value; return o;
+    case F_SST: sst_eval<DIM>(P, F, x, &o.v, g, &o.lap, deriv); break;
+    case F_GRID_LINEAR: o.v = grid_linear<DIM>(F, x); return o;  // piecewise linear: no second derivative
+    case F_GRID_BSPLINE: grid_bspline<DIM>(F, x, &o.v, g, &o.lap, deriv); break;
+    default: return o;
   }
-  if (deriv) {
-    g[0] = g[1] = g[2] = R(0);
-    *lap = R(0);
-  }
+  o.gx = g[0];
+  o.gy = g[1];
+  o.gz = g[2];
+  return o;
 }
 
-// Transformed coefficients at y: sigma'(y), f'(y) (Sec. 4.1, App. A).
+// Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
 template <int DIM, typename R>
-WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp) {
-  R a, ga[3], la, ph, gp[3], lp, s, gs[3], ls;
-  field_eval<DIM>(P, P.alpha, y, &a, ga, &la, true);
-  field_eval<DIM>(P, P.phi, y, &ph, gp, &lp, true);
-  field_eval<DIM>(P, P.sigma, y, &s, gs, &ls, false);
+WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr) {
+  FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
+  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
+  FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
+  const R ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
   R f;
   if (P.f.kind == F_MANUFACTURED) {
     // eq. 1 solved for f at the manufactured u: f = -(alpha Lap u + grad alpha . grad u)
     //                                              - alpha grad Phi . grad u + sigma u
-    R u, gu[3], lu;
-    field_eval<DIM>(P, P.um, y, &u, gu, &lu, true);
+    FieldVal<R> U = field_eval<DIM>(P, P.um, y[0], y[1], y[2], true);
+    const R gu[3] = {U.gx, U.gy, U.gz};
     R da = R(0), dp = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       da += ga[d] * gu[d];
       dp += gp[d] * gu[d];
     }
-    f = -(a * lu + da) - a * dp + s * u;
+    f = -(A.v * U.lap + da) - A.v * dp + S.v * U.v;
   } else {
-    R gf[3], lf;
-    field_eval<DIM>(P, P.f, y, &f, gf, &lf, false);
+    f = field_eval<DIM>(P, P.f, y[0], y[1], y[2], false).v;
   }
-  R ia = R(1) / a;
+  R ia = w_div(R(1), A.v);
   R na2 = R(0), ng2 = R(0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -275,25 +291,23 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp) {
     ng2 += gg * gg;
     na2 += ga[d] * ga[d];
   }
-  R lgam = R(0.5) * (la * ia - na2 * ia * ia + lp);
-  *sp = s * ia + lgam + ng2;
-  R gam = R(0.5) * w_log(a) + R(0.5) * ph;
+  R lgam = R(0.5) * (A.lap * ia - na2 * ia * ia + Ph.lap);
+  *sp = S.v * ia + lgam + ng2;
+  R gam = R(0.5) * w_log(A.v) + R(0.5) * Ph.v;
   *fp = w_exp(gam) * f * ia;
+  if (gamma_out) *gamma_out = gam;
 }
 
 template <int DIM, typename R>
 WOS_HD R gamma_at(const DevProblem<R>& P, const R* x) {
-  R a, ph, g[3], l;
-  field_eval<DIM>(P, P.alpha, x, &a, g, &l, false);
-  field_eval<DIM>(P, P.phi, x, &ph, g, &l, false);
+  R a = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
+  R ph = field_eval<DIM>(P, P.phi, x[0], x[1], x[2], false).v;
   return R(0.5) * w_log(a) + R(0.5) * ph;
 }
 
 template <int DIM, typename R>
 WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
-  R v, g[3], l;
-  field_eval<DIM>(P, P.g, x, &v, g, &l, false);
-  return v;
+  return field_eval<DIM>(P, P.g, x[0], x[1], x[2], false).v;
 }
 
 // ---------------------------------------------------------------------------

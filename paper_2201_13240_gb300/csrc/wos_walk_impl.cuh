@@ -10,8 +10,16 @@
 // Scheduling: the grid is persistent (resident blocks x SMs).  Walks are items
 // of a point-major index space claimed in chunks by one atomic per warp; a lane
 // whose walk ends takes the next item at the top of the step loop, so warps
-// stay full while walk lengths vary.  Each lane keeps FP64 partial sums for
-// its current point and flushes them with atomics when its point changes.
+// stay full while walk lengths vary.  Each lane keeps FP64 partial sums of its
+// current point and flushes them with atomics when its point changes.
+//
+// SIMT uniformity: in almost every iteration some lane of a warp ends its walk,
+// so the end of a walk must not run a separate instruction stream.  A lane that
+// ends still draws its randoms and samples its ball (and discards them), and it
+// evaluates the coefficients at its own point x_n instead of at y, which gives
+// gamma(x_n) for the boundary term from the same call; only g(xbar) is extra.
+// Starting a walk only loads its point: the factor e^{-gamma(x_0)}, common to
+// all walks of a point, multiplies the partial sums when they are flushed.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,10 +37,19 @@ constexpr uint64_t kChunk = 128;
 template <int DIM, typename R>
 struct WalkState {
   R x[3];
-  R W, acc, g0;
+  R W, acc;
   uint32_t p, w, k;
   uint64_t item;
 };
+
+// e^{-gamma(x_0)} of point p, in double (applied once per flush)
+template <int DIM, typename R>
+__device__ __forceinline__ double point_factor(const WalkLaunch& L, const DevProblem<R>& P, uint32_t p) {
+  R x0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x0[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
+  return exp(-(double)gamma_at<DIM>(P, x0));
+}
 
 template <int DIM, typename R>
 __device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem<R>& P, uint64_t item,
@@ -60,7 +77,6 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem
   for (int d = 0; d < 3; ++d) s.x[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
   s.W = R(1);
   s.acc = R(0);
-  s.g0 = gamma_at<DIM>(P, s.x);
 }
 
 template <int DIM, typename R>
@@ -91,11 +107,14 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
   WalkState<DIM, R> s;
   s.p = 0;
 
-  // per-lane partial sums of the current point
-  int64_t acc_p = -1;
+  // per-lane partial sums of the current point (points are < 2^32 per launch)
+  const uint32_t kNoPoint = 0xffffffffu;
+  uint32_t acc_p = kNoPoint;
   double s1 = 0.0, s2 = 0.0;
-  unsigned long long n_acc = 0;
-  unsigned long long st_steps = 0, st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
+  uint32_t n_acc = 0;
+  // per-lane statistics: a lane finishes far fewer than 2^32 walks in one launch
+  unsigned long long st_steps = 0;
+  uint32_t st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
 
   for (;;) {
     // ---- regeneration: lanes without a walk claim the next items ----
@@ -129,36 +148,8 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
     // ---- one step of the walk ----
     R xb[3];
     R d = distance<DIM>(P, s.x, xb);
-    if (d < eps || s.k >= max_k) {
-      bool capped = !(d < eps);
-      if (!capped) s.acc += s.W * w_exp(gamma_at<DIM>(P, s.x)) * g_at<DIM>(P, xb);
-      if (s.k == 0 && !(d > R(0))) ++st_outside;
-      double u = (double)(s.acc * w_exp(-s.g0));
-      if (accumulate && (int64_t)s.p != acc_p) {
-        if (acc_p >= 0) {
-          atomicAdd(&L.sum[acc_p], s1);
-          atomicAdd(&L.sumsq[acc_p], s2);
-          atomicAdd(&L.count[acc_p], n_acc);
-        }
-        acc_p = s.p;
-        s1 = 0.0;
-        s2 = 0.0;
-        n_acc = 0;
-      }
-      s1 += u;
-      s2 += u * u;
-      ++n_acc;
-      if (L.uhat != nullptr) {
-        L.uhat[s.item] = u;
-        L.steps_out[s.item] = (int64_t)s.k;
-      }
-      st_steps += s.k;
-      ++st_walks;
-      if (capped) ++st_capped;
-      if (!isfinite(u)) ++st_nonfinite;
-      active = false;
-      continue;
-    }
+    const bool ends = !(d >= eps) || s.k >= max_k;  // eps-shell (or outside, or NaN), or the step cap
+    const R dd = w_fmax(d, R(0));
 
     U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, 0u}, key0, key1);
     R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
@@ -178,16 +169,50 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
       w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
       dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
     }
-    R a = s_root * d;
+    R a = s_root * dd;
     R q = green_q<DIM, R>(a);
-    R Gn = d * d * q;          // |G| on the ball of radius d
+    R Gn = dd * dd * q;        // |G| on the ball of radius d
     R PB = a * a * q;          // sigma_bar |G|, probability of the volume term
-    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * d;
+    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * dd;
+    // coefficient point: y for a step; the walk's own point when it ends (gamma(x_n))
     R y[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? s.x[i] + r * dy[i] : R(0);
-    R spy, fpy;
-    coeffs<DIM>(P, y, &spy, &fpy);
+    for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? (ends ? s.x[i] : s.x[i] + r * dy[i]) : R(0);
+    R spy, fpy, gam;
+    coeffs<DIM>(P, y, &spy, &fpy, &gam);
+
+    if (ends) {
+      bool capped = (d >= eps);
+      if (!capped) s.acc += s.W * w_exp(gam) * g_at<DIM>(P, xb);   // Alg. 1: g at the closest point
+      if (s.k == 0 && !(d > R(0))) ++st_outside;
+      double acc_d = (double)s.acc;
+      if (accumulate && s.p != acc_p) {
+        if (acc_p != kNoPoint) {
+          double e0 = point_factor<DIM, R>(L, P, acc_p);
+          atomicAdd(&L.sum[acc_p], s1 * e0);
+          atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
+          atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+        }
+        acc_p = s.p;
+        s1 = 0.0;
+        s2 = 0.0;
+        n_acc = 0;
+      }
+      s1 += acc_d;
+      s2 += acc_d * acc_d;
+      ++n_acc;
+      if (L.uhat != nullptr) {
+        L.uhat[s.item] = acc_d * point_factor<DIM, R>(L, P, s.p);
+        L.steps_out[s.item] = (int64_t)s.k;
+      }
+      st_steps += s.k;
+      ++st_walks;
+      if (capped) ++st_capped;
+      if (!isfinite(acc_d)) ++st_nonfinite;
+      active = false;
+      continue;
+    }
+
     s.acc += s.W * Gn * fpy;   // source term, every step
     if (mu <= PB) {            // volume term: null event at y
       s.W *= R(1) - spy * inv_sb;
@@ -195,15 +220,16 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
       for (int i = 0; i < DIM; ++i) s.x[i] = y[i];
     } else {                   // boundary term: uniform point on the sphere
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) s.x[i] = s.x[i] + d * dz[i];
+      for (int i = 0; i < DIM; ++i) s.x[i] = s.x[i] + dd * dz[i];
     }
     ++s.k;
   }
 
-  if (accumulate && acc_p >= 0) {
-    atomicAdd(&L.sum[acc_p], s1);
-    atomicAdd(&L.sumsq[acc_p], s2);
-    atomicAdd(&L.count[acc_p], n_acc);
+  if (accumulate && acc_p != kNoPoint) {
+    double e0 = point_factor<DIM, R>(L, P, acc_p);
+    atomicAdd(&L.sum[acc_p], s1 * e0);
+    atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
+    atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
   }
   // warp-reduce the statistics, one atomic per warp and word
 #pragma unroll
@@ -216,10 +242,10 @@ __global__ void __launch_bounds__(kWalkBlock) wos_walk_kernel(WalkLaunch L) {
   }
   if (lane == 0) {
     atomicAdd(&L.stats[ST_STEPS], st_steps);
-    atomicAdd(&L.stats[ST_WALKS], st_walks);
-    if (st_capped) atomicAdd(&L.stats[ST_CAPPED], st_capped);
-    if (st_nonfinite) atomicAdd(&L.stats[ST_NONFINITE], st_nonfinite);
-    if (st_outside) atomicAdd(&L.stats[ST_OUTSIDE], st_outside);
+    atomicAdd(&L.stats[ST_WALKS], (unsigned long long)st_walks);
+    if (st_capped) atomicAdd(&L.stats[ST_CAPPED], (unsigned long long)st_capped);
+    if (st_nonfinite) atomicAdd(&L.stats[ST_NONFINITE], (unsigned long long)st_nonfinite);
+    if (st_outside) atomicAdd(&L.stats[ST_OUTSIDE], (unsigned long long)st_outside);
   }
 }
 

@@ -200,7 +200,8 @@ def test_edge_cases(wos, orc, ctx):
     pts = np.array([[0.5, 2e-4, 0.3], [0.9995, 0.5, 1 - 1e-4]], dtype=np.float32)
     m, se, st, _ = _gpu_solve(ctx, prob, pts, 9, 1e-3, sb, seed=7)
     want = [W.square2d_exact(*orc.distance(desc, pts[:, i].astype(np.float64))[1]) for i in range(3)]
-    assert np.allclose(m, want, rtol=1e-6) and np.all(se == 0) and st[0] == 0
+    # every walk returns the same value: the spread is rounding of the FP64 sums only
+    assert np.allclose(m, want, rtol=1e-6) and np.all(se <= 1e-7 * np.abs(m) + 1e-12) and st[0] == 0
     # invalid arguments are rejected with WOS_EINVAL
     for kw in ({"eps": 0.0}, {"eps": -1.0}, {"sigma_bar": 0.0}, {"sigma_bar": float("nan")},
                {"max_steps": 0}):
