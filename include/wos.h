@@ -99,15 +99,25 @@ typedef struct {
 } wos_field_desc;
 
 enum {
-  WOS_DOMAIN_BOX = 0,        /* p[0..2] lower corner, p[3..5] upper corner */
-  WOS_DOMAIN_BALL = 1,       /* p[0..2] centre, p[3] radius (a disk in 2D) */
-  WOS_DOMAIN_ANNULUS = 2,    /* p[0..2] centre, p[3] inner radius, p[4] outer radius */
-  WOS_DOMAIN_ROUNDED_BOX = 3 /* p[0..2] centre, p[3..5] half extents, p[6] corner radius */
+  WOS_DOMAIN_BOX = 0,         /* p[0..2] lower corner, p[3..5] upper corner */
+  WOS_DOMAIN_BALL = 1,        /* p[0..2] centre, p[3] radius (a disk in 2D) */
+  WOS_DOMAIN_ANNULUS = 2,     /* p[0..2] centre, p[3] inner radius, p[4] outer radius */
+  WOS_DOMAIN_ROUNDED_BOX = 3, /* p[0..2] centre, p[3..5] half extents, p[6] corner radius */
+  WOS_DOMAIN_MESH = 4         /* 3D closed triangle mesh: verts / tris below */
 };
 
+/* Domain.  For WOS_DOMAIN_MESH, verts (HOST float32 [nverts][3]) and tris (HOST int32
+   [ntris][3], indices into verts) describe a closed surface; wos_problem_create builds
+   a bounding volume hierarchy for closest-point queries (Sec. 7.1) and keeps its own
+   copy, so the arrays may be freed afterwards.  Distances to a mesh are unsigned:
+   points must lie inside the surface (the library cannot tell). */
 typedef struct {
   int32_t kind;
   double p[16];
+  const float* verts;
+  int64_t nverts;
+  const int32_t* tris;
+  int64_t ntris;
 } wos_domain_desc;
 
 /* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift
@@ -154,8 +164,10 @@ const char* wos_last_error(const wos_ctx* ctx);
 const char* wos_version(void);
 
 /* Validate and upload a problem (Sec. 3 eq. 1).  Copies the description; grid data
-   stays with the caller.  Errors: WOS_EINVAL (bad dim, kind, term count, grid size,
-   null grid data, alpha/phi given as linear grids), WOS_ENOMEM, WOS_ECUDA. */
+   stays with the caller; a mesh boundary gets its BVH built here.  Errors: WOS_EINVAL
+   (bad dim, kind, term count, grid size, null grid data, alpha/phi given as linear
+   grids, mesh not 3D or with an out-of-range index or a non-finite vertex),
+   WOS_ENOMEM, WOS_ECUDA. */
 int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* desc, wos_problem** prob);
 int wos_problem_destroy(wos_problem* prob);
 
@@ -191,6 +203,21 @@ int wos_walk_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, 
    of single-sample estimates).  All device arrays of npts; any output may be NULL. */
 int wos_finalize(wos_ctx* ctx, const double* sum, const double* sumsq, const int64_t* count,
                  int64_t npts, double* mean, double* var, double* stderr_out, void* stream);
+
+/* Gradient of sum_p grad_u[p] * mean_p with respect to the node values of the
+   screening field sigma, where mean_p is the estimate wos_solve returns for point p
+   with the same points, walks_uniform and params (same seed and walk ids).  Not in
+   the paper: the walks are replayed from their Philox streams (no stored paths).
+   Given sigma_bar, a walk's path does not depend on sigma; sigma enters only the
+   null weights w = 1 - sigma'(y)/sigma_bar with d sigma'/d sigma_m = N_m(y)/alpha(y)
+   (Sec. 4.1, Sec. 5.1), so each walk runs twice: once for its total, once adding
+   (total - prefix)/w * dw/dsigma_m at every null event.
+   grad_u: device double [npts]; grad_sigma: device double [sigma grid nodes], ADDED to.
+   Errors: WOS_EUNSUPPORTED unless sigma is WOS_FIELD_GRID_LINEAR and f is not
+   WOS_FIELD_MANUFACTURED; WOS_EINVAL as wos_solve. */
+int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                      int32_t walks_uniform, const wos_params* params, const double* grad_u,
+                      double* grad_sigma, uint64_t* stats, void* stream);
 
 /* End-to-end convenience: HOST points in, HOST mean / variance / stderr out (and
    HOST stats if non-NULL).  Copies the inputs to device buffers owned by the

@@ -26,7 +26,7 @@ _lib = None
 
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4,
                 "grid_bspline": 5}
-_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3}
+_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4}
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +55,9 @@ class Field(C.Structure):
 
 
 class Domain(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16)]
+    _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.POINTER(C.c_float)),
+                ("nverts", C.c_int64), ("tris", C.POINTER(C.c_int32)), ("ntris", C.c_int64),
+                ("bvh", C.c_void_p)]
 
 
 class Problem(C.Structure):
@@ -96,6 +98,10 @@ def _load():
                               C.c_double, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64),
                               C.c_int]
     lib.orc_sigma_bar.argtypes = [pp, C.c_int, dp, dp, dp]
+    lib.orc_mesh_prepare.argtypes = [pp]
+    lib.orc_mesh_release.argtypes = [pp]
+    lib.orc_mesh_distance_brute.argtypes = [pp, dp, dp]
+    lib.orc_mesh_distance_brute.restype = C.c_double
     _lib = lib
     return lib
 
@@ -104,18 +110,42 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+_mesh_cache = {}
+
+
 class _Packed:
-    """A workloads problem dict packed into the oracle's structs (keeps arrays alive)."""
+    """A workloads problem dict packed into the oracle's structs (keeps arrays alive).
+    A mesh domain gets the oracle's BVH, built once per mesh and kept for the process."""
 
     def __init__(self, prob):
         self.keep = []
         P = Problem()
         P.dim = prob["dim"]
-        P.domain.kind = _DOM_KINDS[prob["domain"]["kind"]]
-        for i, v in enumerate(prob["domain"]["p"]):
+        dom = prob["domain"]
+        P.domain.kind = _DOM_KINDS[dom["kind"]]
+        for i, v in enumerate(dom["p"]):
             P.domain.p[i] = v
         for name in ("alpha", "phi", "sigma", "f", "g", "um"):
             self._field(getattr(P, name), prob[name])
+        if dom["kind"] == "mesh":
+            key = (id(dom["verts"]), id(dom["tris"]))
+            if key not in _mesh_cache:
+                verts = np.ascontiguousarray(dom["verts"], dtype=np.float32)
+                tris = np.ascontiguousarray(dom["tris"], dtype=np.int32)
+                M = Problem()
+                M.dim = 3
+                M.domain.kind = 4
+                M.domain.verts = verts.ctypes.data_as(C.POINTER(C.c_float))
+                M.domain.nverts = len(verts)
+                M.domain.tris = tris.ctypes.data_as(C.POINTER(C.c_int32))
+                M.domain.ntris = len(tris)
+                if _load().orc_mesh_prepare(C.pointer(M)) != 0:
+                    raise ValueError("orc_mesh_prepare failed")
+                _mesh_cache[key] = (verts, tris, M, dom["verts"], dom["tris"])
+            verts, tris, M, _, _ = _mesh_cache[key]
+            P.domain.verts, P.domain.nverts = M.domain.verts, M.domain.nverts
+            P.domain.tris, P.domain.ntris = M.domain.tris, M.domain.ntris
+            P.domain.bvh = M.domain.bvh
         self.P = P
         self.ptr = C.pointer(P)
 
@@ -216,6 +246,15 @@ def coeffs(prob, x, packed=None):
     out = np.zeros(5)
     _load().orc_coeffs(pk.ptr, _dptr(xx), _dptr(out))
     return tuple(out)
+
+
+def mesh_distance_brute(prob, x, packed=None):
+    pk = packed or pack(prob)
+    xx = np.zeros(3)
+    xx[: len(x)] = x
+    xb = np.zeros(3)
+    d = _load().orc_mesh_distance_brute(pk.ptr, _dptr(xx), _dptr(xb))
+    return d, xb
 
 
 def distance(prob, x, packed=None):

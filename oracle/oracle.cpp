@@ -12,9 +12,11 @@
 // are found by safeguarded Newton iteration run to convergence.
 #include "oracle.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 #include <omp.h>
 
 namespace {
@@ -469,6 +471,150 @@ double gamma_at(const orc_problem* P, const double* x) {
 }
 
 // ---------------------------------------------------------------------------
+// Triangle meshes: closest point on a triangle and a plain BVH (Sec. 7.1: the
+// distance query on a mesh is accelerated by a bounding volume hierarchy).
+// ---------------------------------------------------------------------------
+struct V3 {
+  double x, y, z;
+};
+V3 v3sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 v3add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+V3 v3mul(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+double v3dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 v3cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+
+V3 closest_on_segment(V3 p, V3 a, V3 b) {
+  V3 ab = v3sub(b, a);
+  double l2 = v3dot(ab, ab);
+  double t = (l2 > 0.0) ? v3dot(v3sub(p, a), ab) / l2 : 0.0;
+  t = std::min(1.0, std::max(0.0, t));
+  return v3add(a, v3mul(ab, t));
+}
+
+// The closest point of a triangle: the projection onto its plane when that
+// falls inside the triangle, else the closest of the closest points of its edges.
+V3 closest_on_triangle(V3 p, V3 a, V3 b, V3 c) {
+  V3 n = v3cross(v3sub(b, a), v3sub(c, a));
+  double n2 = v3dot(n, n);
+  if (n2 > 0.0) {
+    V3 q = v3sub(p, v3mul(n, v3dot(v3sub(p, a), n) / n2));
+    bool in = v3dot(v3cross(v3sub(b, a), v3sub(q, a)), n) >= 0.0 &&
+              v3dot(v3cross(v3sub(c, b), v3sub(q, b)), n) >= 0.0 &&
+              v3dot(v3cross(v3sub(a, c), v3sub(q, c)), n) >= 0.0;
+    if (in) return q;
+  }
+  V3 best = closest_on_segment(p, a, b);
+  double bd = v3dot(v3sub(p, best), v3sub(p, best));
+  V3 e[2] = {closest_on_segment(p, b, c), closest_on_segment(p, c, a)};
+  for (V3 q : e) {
+    double dq = v3dot(v3sub(p, q), v3sub(p, q));
+    if (dq < bd) { bd = dq; best = q; }
+  }
+  return best;
+}
+
+V3 mesh_vertex(const orc_domain& D, int64_t i) {
+  return {D.verts[3 * i], D.verts[3 * i + 1], D.verts[3 * i + 2]};
+}
+
+struct OrcNode {
+  double lo[3], hi[3];
+  int left, right;  // children (-1 for a leaf)
+  int first, count;  // leaf: range of the permuted triangle list
+};
+
+struct OrcBVH {
+  std::vector<OrcNode> nodes;
+  std::vector<int64_t> tri;  // permuted triangle indices
+};
+
+int bvh_build(const orc_domain& D, OrcBVH& B, std::vector<V3>& cent, int first, int count) {
+  OrcNode nd;
+  for (int d = 0; d < 3; ++d) { nd.lo[d] = INFINITY; nd.hi[d] = -INFINITY; }
+  for (int i = first; i < first + count; ++i) {
+    const int32_t* t = D.tris + 3 * B.tri[i];
+    for (int k = 0; k < 3; ++k) {
+      V3 v = mesh_vertex(D, t[k]);
+      double c[3] = {v.x, v.y, v.z};
+      for (int d = 0; d < 3; ++d) {
+        nd.lo[d] = std::min(nd.lo[d], c[d]);
+        nd.hi[d] = std::max(nd.hi[d], c[d]);
+      }
+    }
+  }
+  nd.left = nd.right = -1;
+  nd.first = first;
+  nd.count = count;
+  int idx = (int)B.nodes.size();
+  B.nodes.push_back(nd);
+  if (count <= 4) return idx;
+  // split at the median centroid along the longest axis of the box
+  int ax = 0;
+  for (int d = 1; d < 3; ++d)
+    if (nd.hi[d] - nd.lo[d] > nd.hi[ax] - nd.lo[ax]) ax = d;
+  auto key = [&](int64_t t) { V3 c = cent[t]; return ax == 0 ? c.x : (ax == 1 ? c.y : c.z); };
+  int mid = first + count / 2;
+  std::nth_element(B.tri.begin() + first, B.tri.begin() + mid, B.tri.begin() + first + count,
+                   [&](int64_t a, int64_t b) { return key(a) < key(b); });
+  int l = bvh_build(D, B, cent, first, mid - first);
+  int r = bvh_build(D, B, cent, mid, first + count - mid);
+  B.nodes[idx].left = l;
+  B.nodes[idx].right = r;
+  return idx;
+}
+
+double box_dist2(const OrcNode& n, V3 p) {
+  double c[3] = {p.x, p.y, p.z}, s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double e = std::max(0.0, std::max(n.lo[d] - c[d], c[d] - n.hi[d]));
+    s += e * e;
+  }
+  return s;
+}
+
+void bvh_query(const orc_domain& D, const OrcBVH& B, int ni, V3 p, double* best2, V3* bestq) {
+  const OrcNode& n = B.nodes[ni];
+  if (box_dist2(n, p) >= *best2) return;
+  if (n.left < 0) {
+    for (int i = n.first; i < n.first + n.count; ++i) {
+      const int32_t* t = D.tris + 3 * B.tri[i];
+      V3 q = closest_on_triangle(p, mesh_vertex(D, t[0]), mesh_vertex(D, t[1]), mesh_vertex(D, t[2]));
+      double d2 = v3dot(v3sub(p, q), v3sub(p, q));
+      if (d2 < *best2) { *best2 = d2; *bestq = q; }
+    }
+    return;
+  }
+  double dl = box_dist2(B.nodes[n.left], p), dr = box_dist2(B.nodes[n.right], p);
+  if (dl <= dr) {
+    bvh_query(D, B, n.left, p, best2, bestq);
+    bvh_query(D, B, n.right, p, best2, bestq);
+  } else {
+    bvh_query(D, B, n.right, p, best2, bestq);
+    bvh_query(D, B, n.left, p, best2, bestq);
+  }
+}
+
+double mesh_distance(const orc_domain& D, const double* x, double* xb) {
+  V3 p = {x[0], x[1], x[2]}, q = p;
+  double best2 = INFINITY;
+  const OrcBVH* B = static_cast<const OrcBVH*>(D.bvh);
+  if (B) {
+    bvh_query(D, *B, 0, p, &best2, &q);
+  } else {
+    for (int64_t i = 0; i < D.ntris; ++i) {
+      const int32_t* t = D.tris + 3 * i;
+      V3 c = closest_on_triangle(p, mesh_vertex(D, t[0]), mesh_vertex(D, t[1]), mesh_vertex(D, t[2]));
+      double d2 = v3dot(v3sub(p, c), v3sub(p, c));
+      if (d2 < best2) { best2 = d2; q = c; }
+    }
+  }
+  xb[0] = q.x;
+  xb[1] = q.y;
+  xb[2] = q.z;
+  return std::sqrt(best2);
+}
+
+// ---------------------------------------------------------------------------
 // Distance to the boundary (Alg. 1 "DistanceToBoundary"), analytic shapes.
 // ---------------------------------------------------------------------------
 double distance(const orc_problem* P, const double* x, double* xb) {
@@ -532,6 +678,8 @@ double distance(const orc_problem* P, const double* x, double* xb) {
       xb[imax] = p[imax] + ((rel[imax] >= 0.0) ? p[3 + imax] : -p[3 + imax]);
       return rc - qmax;
     }
+    case ORC_DOM_MESH:
+      return mesh_distance(P->domain, x, xb);
     default:
       return NAN;
   }
@@ -546,6 +694,14 @@ void domain_bbox(const orc_problem* P, double lo[3], double hi[3]) {
       case ORC_DOM_BALL: lo[d] = p[d] - p[3]; hi[d] = p[d] + p[3]; break;
       case ORC_DOM_ANNULUS: lo[d] = p[d] - p[4]; hi[d] = p[d] + p[4]; break;
       case ORC_DOM_ROUNDED_BOX: lo[d] = p[d] - p[3 + d]; hi[d] = p[d] + p[3 + d]; break;
+      case ORC_DOM_MESH:
+        lo[d] = INFINITY;
+        hi[d] = -INFINITY;
+        for (int64_t i = 0; i < P->domain.nverts; ++i) {
+          lo[d] = std::min(lo[d], (double)P->domain.verts[3 * i + d]);
+          hi[d] = std::max(hi[d], (double)P->domain.verts[3 * i + d]);
+        }
+        break;
     }
   }
 }
@@ -668,6 +824,35 @@ int orc_field_eval(const orc_problem* prob, const orc_field* fld, const double* 
 int orc_coeffs(const orc_problem* prob, const double* x, double out[5]) {
   coeffs(prob, x, &out[0], &out[1], &out[2], &out[3], &out[4]);
   return 0;
+}
+
+int orc_mesh_prepare(orc_problem* prob) {
+  orc_domain& D = prob->domain;
+  if (D.kind != ORC_DOM_MESH || prob->dim != 3 || !D.verts || !D.tris || D.ntris < 1) return -1;
+  if (D.bvh) return 0;
+  OrcBVH* B = new OrcBVH();
+  std::vector<V3> cent(D.ntris);
+  B->tri.resize(D.ntris);
+  for (int64_t i = 0; i < D.ntris; ++i) {
+    const int32_t* t = D.tris + 3 * i;
+    V3 a = mesh_vertex(D, t[0]), b = mesh_vertex(D, t[1]), c = mesh_vertex(D, t[2]);
+    cent[i] = v3mul(v3add(v3add(a, b), c), 1.0 / 3.0);
+    B->tri[i] = i;
+  }
+  bvh_build(D, *B, cent, 0, (int)D.ntris);
+  D.bvh = B;
+  return 0;
+}
+
+void orc_mesh_release(orc_problem* prob) {
+  delete static_cast<OrcBVH*>(prob->domain.bvh);
+  prob->domain.bvh = nullptr;
+}
+
+double orc_mesh_distance_brute(const orc_problem* prob, const double* x, double* xbar) {
+  orc_domain D = prob->domain;
+  D.bvh = nullptr;
+  return mesh_distance(D, x, xbar);
 }
 
 double orc_distance(const orc_problem* prob, const double* x, double* xbar) {

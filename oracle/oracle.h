@@ -58,7 +58,7 @@ typedef struct {
 } orc_field;
 
 enum { ORC_DOM_BOX = 0, ORC_DOM_BALL = 1, ORC_DOM_ANNULUS = 2,
-       ORC_DOM_ROUNDED_BOX = 3 };
+       ORC_DOM_ROUNDED_BOX = 3, ORC_DOM_MESH = 4 };
 
 typedef struct {
   int32_t kind;
@@ -66,7 +66,14 @@ typedef struct {
   /* BOX: lo p[0..2], hi p[3..5]
      BALL: centre p[0..2], radius p[3]
      ANNULUS: centre p[0..2], inner radius p[3], outer radius p[4]
-     ROUNDED_BOX: centre p[0..2], half extents p[3..5], corner radius p[6] */
+     ROUNDED_BOX: centre p[0..2], half extents p[3..5], corner radius p[6]
+     MESH (3D): closed triangle mesh, host arrays verts [nverts][3], tris [ntris][3];
+                orc_mesh_prepare builds the oracle's own BVH into `bvh`. */
+  const float* verts;
+  int64_t nverts;
+  const int32_t* tris;
+  int64_t ntris;
+  void* bvh;
 } orc_domain;
 
 typedef struct {
@@ -105,8 +112,16 @@ int orc_field_eval(const orc_problem* prob, const orc_field* fld, const double* 
 /* Transformed coefficients at x: out = {gamma, sigma', f', f, alpha}. */
 int orc_coeffs(const orc_problem* prob, const double* x, double out[5]);
 
-/* Distance to the boundary (positive inside) and closest boundary point. */
+/* Distance to the boundary (positive inside) and closest boundary point.  For a
+   mesh the distance is unsigned (points are assumed inside the closed surface). */
 double orc_distance(const orc_problem* prob, const double* x, double* xbar);
+
+/* Mesh domains: build / free the oracle's BVH (median split of triangle
+   centroids, <= 4 triangles per leaf), and the brute-force distance over all
+   triangles that pins it. */
+int orc_mesh_prepare(orc_problem* prob);
+void orc_mesh_release(orc_problem* prob);
+double orc_mesh_distance_brute(const orc_problem* prob, const double* x, double* xbar);
 
 /* One delta-tracking walk from x0.  Randoms: Philox4x32-10, key = (seed lo, seed hi),
    counter = (point, walk, step, block).  Returns the estimate of u(x0).

@@ -25,7 +25,7 @@ WOS_FP32, WOS_FP64 = 0, 1
 STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
 STATS_WORDS = 5
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
-_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3}
+_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4}
 
 
 class WosError(RuntimeError):
@@ -45,7 +45,8 @@ class FieldDesc(C.Structure):
 
 
 class DomainDesc(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16)]
+    _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.c_void_p), ("nverts", C.c_int64),
+                ("tris", C.c_void_p), ("ntris", C.c_int64)]
 
 
 class ProblemDesc(C.Structure):
@@ -82,6 +83,7 @@ def load():
     lib.wos_walk_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_adjoint_sigma.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -134,6 +136,12 @@ class Problem:
         D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
         for i, v in enumerate(desc["domain"]["p"]):
             D.domain.p[i] = v
+        if desc["domain"]["kind"] == "mesh":
+            verts = np.ascontiguousarray(desc["domain"]["verts"], dtype=np.float32)
+            tris = np.ascontiguousarray(desc["domain"]["tris"], dtype=np.int32)
+            self._keep += [verts, tris]
+            D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
+            D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
         for name in ("alpha", "phi", "sigma", "f", "g", "um"):
             fd = desc[name]
             F = getattr(D, name)
@@ -277,6 +285,22 @@ class Context:
         self._check(self.lib.wos_finalize(self.handle, _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), n,
                                           _ptr(mean), _ptr(var), _ptr(se), _stream(stream)))
         return mean, var, se
+
+    def adjoint_sigma(self, prob, pts, walks, grad_u, grad_sigma, eps, sigma_bar, seed=0, walk_offset=0,
+                      max_steps=1 << 20, precision="fp32", stats=None, stream=None):
+        """Add d(sum_p grad_u[p] mean_p)/d(sigma grid) to grad_sigma (CUDA float64, grid-sized)."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        if not (grad_u.is_cuda and grad_u.dtype == torch.float64 and grad_u.shape == (npts,)):
+            raise TypeError("grad_u must be a CUDA float64 tensor of shape [npts]")
+        if not (grad_sigma.is_cuda and grad_sigma.dtype == torch.float64 and grad_sigma.is_contiguous()):
+            raise TypeError("grad_sigma must be a contiguous CUDA float64 tensor")
+        grad_u = grad_u.contiguous()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_adjoint_sigma(self.handle, prob.handle, _ptr(pts), npts, int(walks), C.byref(p),
+                                               _ptr(grad_u), _ptr(grad_sigma), _ptr(stats), _stream(stream)))
+        return grad_sigma
 
     def solve_host(self, prob, pts_host, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
                    precision="fp32", out=None, stream=None):

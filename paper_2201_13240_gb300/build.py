@@ -21,8 +21,9 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libwos.so")
 HOSTCHECK = os.path.join(HERE, "libwos_hostcheck.so")
 
-CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu"]
-HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_internal.h"]
+CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_adjoint.cu", "wos_mesh.cpp"]
+HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_adjoint_impl.cuh", "wos_internal.h",
+           "wos_mesh.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -50,7 +51,7 @@ def build_lib(force: bool = False, verbose: bool = False) -> str:
     procs = []
     objs = []
     for src in CU_SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         objs.append(obj)
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

@@ -1,0 +1,224 @@
+// wos_adjoint_impl.cuh -- gradient of the delta-tracking estimate with respect to
+// the node values of a multilinear screening grid sigma, by replaying each walk.
+//
+// Given sigma_bar, nothing that steers a walk depends on sigma: distances, the
+// Green's-function samples, and the null/boundary decision mu <= sigma_bar |G|
+// use only the geometry, sigma_bar and the randoms (Sec. 5.1, eq. 11).  sigma
+// enters only through the null weights w_j = 1 - sigma'(y_j)/sigma_bar, with
+// sigma' = sigma/alpha + (terms of alpha and Phi) (Sec. 4.1), so
+//     d sigma'(y) / d sigma_m = N_m(y) / alpha(y),
+// N_m the multilinear weight of node m at y.  A walk's estimate is
+//     u = e^{-gamma(x_0)} A,   A = sum_k W_k |G_k| f'(y_k) + W_n e^{gamma(x_n)} g(xbar_n),
+// W_k the product of the null weights before step k.  The terms up to and
+// including step j do not contain w_j; every later term contains it once, so
+//     dA / dw_j = (A - P_{j+1}) / w_j,
+// P_{j+1} the sum of the terms up to step j.  Each walk therefore runs twice
+// on the same Philox stream: a first pass for A, a second that recomputes
+// the prefix and, at every null event j, adds
+//     c * (A - P_{j+1}) / w_j * (-N_m(y_j) / (alpha(y_j) sigma_bar))
+// to the gradient of node m, c = grad_u[p] e^{-gamma(x_0)} / (walks of point p).
+// The estimator's paths are not stored (path replay).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wos_internal.h"
+#include "wos_math.cuh"
+#include "wos_problem.cuh"
+
+namespace wos {
+
+constexpr int kAdjBlock = 128;
+
+template <int DIM, typename R>
+__device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, double val, double* grad) {
+  int i0[3] = {0, 0, 0};
+  R t[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = (y[d] - F.lo[d]) * F.inv_h[d];
+    s = w_fmin(w_fmax(s, R(0)), R(F.res[d] - 1));
+    int i = (int)s;
+    if (i > F.res[d] - 2) i = F.res[d] - 2;
+    i0[d] = i;
+    t[d] = s - R(i);
+  }
+  const int nc = (DIM == 3) ? 8 : 4;
+#pragma unroll
+  for (int c = 0; c < nc; ++c) {
+    double w = val;
+    int64_t idx = 0, stride = 1;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      int o = (c >> d) & 1;
+      w *= (double)(o ? t[d] : R(1) - t[d]);
+      idx += (int64_t)(i0[d] + o) * stride;
+      stride *= F.res[d];
+    }
+    if (w != 0.0) atomicAdd(&grad[idx], w);
+  }
+}
+
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int4* src = reinterpret_cast<const int4*>(L.problem);
+    int4* dst = reinterpret_cast<int4*>(smem_raw);
+    for (int i = threadIdx.x; i < L.problem_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
+  const R eps = R(L.eps), s_root = w_sqrt(R(L.sigma_bar));
+  const R inv_sb = R(1) / R(L.sigma_bar);
+  const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
+  const double inv_walks = 1.0 / (double)L.walks_uniform;
+
+  uint64_t chunk_next = 0, chunk_end = 0;
+  bool exhausted = false, active = false;
+  // walk state; phase 0 computes the total A, phase 1 replays and scatters
+  R x[3] = {R(0), R(0), R(0)}, W = R(1), acc = R(0), total = R(0);
+  uint32_t p = 0, w = 0, k = 0, phase = 0;
+  double coef = 0.0;
+  unsigned long long st_steps = 0;
+  uint32_t st_walks = 0, st_capped = 0;
+
+  for (;;) {
+    unsigned need = __ballot_sync(0xffffffffu, !active);
+    while (need != 0u && !exhausted) {
+      if (chunk_next >= chunk_end) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(L.work_counter, 64ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= L.total_items) {
+          exhausted = true;
+          break;
+        }
+        chunk_next = base;
+        chunk_end = (base + 64 < L.total_items) ? base + 64 : L.total_items;
+      }
+      unsigned nneed = __popc(need);
+      uint64_t avail = chunk_end - chunk_next;
+      unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
+      unsigned rank = __popc(need & lt_mask);
+      if (!active && rank < take) {
+        uint64_t item = chunk_next + rank;
+        uint64_t pp = item / (uint64_t)L.walks_uniform;
+        p = (uint32_t)pp;
+        w = (uint32_t)(L.walk_offset + (item - pp * (uint64_t)L.walks_uniform));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
+        W = R(1);
+        acc = R(0);
+        k = 0;
+        phase = 0;
+        coef = __ldg(&L.grad_u[p]) * inv_walks * exp(-(double)gamma_at<DIM>(P, x));
+        active = true;
+      }
+      chunk_next += take;
+      need = __ballot_sync(0xffffffffu, !active);
+    }
+    if (__ballot_sync(0xffffffffu, active) == 0u) break;
+    if (!active) continue;
+
+    R xb[3];
+    R d = distance<DIM>(P, x, xb);
+    const bool ends = !(d >= eps) || k >= max_k;
+    const R dd = w_fmax(d, R(0));
+    U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
+    R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
+    R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
+    if (DIM == 2) {
+      w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
+      w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
+    } else {
+      U4 r1 = philox4x32_10(U4{p, w, k, 1u}, key0, key1);
+      R cy = R(1) - R(2) * to_uniform<R>(r0.z);
+      R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
+      R sp_, cp_;
+      w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
+      dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
+      R cz = R(1) - R(2) * to_uniform<R>(r1.x);
+      R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+      w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
+      dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
+    }
+    R a = s_root * dd;
+    R q = green_q<DIM, R>(a);
+    R Gn = dd * dd * q, PB = a * a * q;
+    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * dd;
+    R y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? (ends ? x[i] : x[i] + r * dy[i]) : R(0);
+    R spy, fpy, gam, al;
+    coeffs<DIM>(P, y, &spy, &fpy, &gam, &al);
+
+    if (ends) {
+      bool capped = (d >= eps);
+      if (!capped) acc += W * w_exp(gam) * g_at<DIM>(P, xb);
+      if (phase == 0) {
+        total = acc;
+#pragma unroll
+        for (int dd2 = 0; dd2 < 3; ++dd2) x[dd2] = (dd2 < DIM) ? R(__ldg(&L.pts[(int64_t)dd2 * L.npts + (int64_t)p])) : R(0);
+        W = R(1);
+        acc = R(0);
+        k = 0;
+        phase = 1;
+        st_steps += 0;
+      } else {
+        ++st_walks;
+        if (capped) ++st_capped;
+        active = false;
+      }
+      continue;
+    }
+    acc += W * Gn * fpy;
+    if (mu <= PB) {
+      R wj = R(1) - spy * inv_sb;
+      if (phase == 1) {
+        // d total / d w_j = (A - P_{j+1}) / w_j ; d w_j / d sigma_m = -N_m(y) / (alpha(y) sigma_bar)
+        double rem = ((double)total - (double)acc) / (double)wj;
+        double val = -coef * rem / ((double)al * (double)L.sigma_bar);
+        if (isfinite(val) && val != 0.0) grid_scatter<DIM, R>(P.sigma, y, val, L.grad_sigma);
+      }
+      W *= wj;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) x[i] = y[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) x[i] = x[i] + dd * dz[i];
+    }
+    if (phase == 1) ++st_steps;
+    ++k;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    st_steps += __shfl_down_sync(0xffffffffu, st_steps, off);
+    st_walks += __shfl_down_sync(0xffffffffu, st_walks, off);
+    st_capped += __shfl_down_sync(0xffffffffu, st_capped, off);
+  }
+  if (lane == 0 && L.stats != nullptr) {
+    atomicAdd(&L.stats[ST_STEPS], st_steps);
+    atomicAdd(&L.stats[ST_WALKS], (unsigned long long)st_walks);
+    if (st_capped) atomicAdd(&L.stats[ST_CAPPED], (unsigned long long)st_capped);
+  }
+}
+
+template <int DIM, typename R>
+cudaError_t launch_adjoint_t(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
+  size_t smem = (size_t)L.problem_bytes;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_adjoint_kernel<DIM, R>, kAdjBlock, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = per_sm * num_sms;
+  uint64_t blocks_needed = (L.total_items + kAdjBlock - 1) / kAdjBlock;
+  if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
+  wos_adjoint_kernel<DIM, R><<<grid, kAdjBlock, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace wos

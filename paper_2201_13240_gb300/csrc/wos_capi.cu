@@ -12,6 +12,7 @@
 
 #include "wos.h"
 #include "wos_internal.h"
+#include "wos_mesh.h"
 #include "wos_problem.cuh"
 
 using wos::DevField;
@@ -42,6 +43,10 @@ struct wos_problem {
   DevProblem<float>* d32 = nullptr;
   DevProblem<double>* d64 = nullptr;
   DevProblem<double> host64;  // host copy for the sigma_bar lattice bounds
+  float* mesh_nodes = nullptr;  // device BVH of a mesh boundary
+  float* mesh_tris = nullptr;
+  double mesh_lo[3] = {0, 0, 0}, mesh_hi[3] = {0, 0, 0};
+  int mesh_depth = 0;
 };
 
 namespace {
@@ -163,7 +168,12 @@ void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
   fill_field(P, P.um, d.um, d.dim);
 }
 
-void domain_bbox(const DevProblem<double>& P, double lo[3], double hi[3]) {
+void domain_bbox(const wos_problem* pr, double lo[3], double hi[3]) {
+  const DevProblem<double>& P = pr->host64;
+  if (P.domain_kind == wos::D_MESH) {
+    for (int d = 0; d < 3; ++d) { lo[d] = pr->mesh_lo[d]; hi[d] = pr->mesh_hi[d]; }
+    return;
+  }
   const double* p = P.dom;
   for (int d = 0; d < 3; ++d) { lo[d] = 0.0; hi[d] = 0.0; }
   for (int d = 0; d < P.dim; ++d) {
@@ -433,6 +443,11 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
         if (!(p[3 + i] > 0 && p[6] >= 0 && p[6] <= p[3 + i]))
           return fail(ctx, WOS_EINVAL, "rounded box: need half extents > 0 and 0 <= corner <= half");
       break;
+    case WOS_DOMAIN_MESH:
+      if (d->dim != 3) return fail(ctx, WOS_EINVAL, "mesh domains are 3D");
+      if (!d->domain.verts || !d->domain.tris || d->domain.nverts < 3 || d->domain.ntris < 1)
+        return fail(ctx, WOS_EINVAL, "mesh: need vertices and triangles");
+      break;
     default:
       return fail(ctx, WOS_EINVAL, "unknown domain kind");
   }
@@ -456,7 +471,31 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   fill_problem(*h32, *d);
   fill_problem(pr->host64, *d);
   DeviceGuard g(ctx->device);
-  cudaError_t e = cudaMalloc(&pr->d32, sizeof(DevProblem<float>));
+  cudaError_t e = cudaSuccess;
+  if (d->domain.kind == WOS_DOMAIN_MESH) {
+    std::vector<wos::MeshNode> nodes;
+    std::vector<float> tri;
+    if (wos::mesh_build_bvh(d->domain.verts, d->domain.nverts, d->domain.tris, d->domain.ntris, &nodes, &tri,
+                            &pr->mesh_depth) != 0 || pr->mesh_depth > wos::kMeshStack - 2) {
+      delete h32;
+      delete pr;
+      return fail(ctx, WOS_EINVAL, "mesh: index out of range, non-finite vertex, or hierarchy too deep");
+    }
+    for (int k = 0; k < 3; ++k) {
+      pr->mesh_lo[k] = nodes[0].lo[k];
+      pr->mesh_hi[k] = nodes[0].hi[k];
+    }
+    e = cudaMalloc(&pr->mesh_nodes, nodes.size() * sizeof(wos::MeshNode));
+    if (e == cudaSuccess) e = cudaMalloc(&pr->mesh_tris, tri.size() * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pr->mesh_nodes, nodes.data(), nodes.size() * sizeof(wos::MeshNode), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pr->mesh_tris, tri.data(), tri.size() * sizeof(float), cudaMemcpyHostToDevice);
+    h32->mesh_nodes = pr->mesh_nodes;
+    h32->mesh_tris = pr->mesh_tris;
+    pr->host64.mesh_nodes = pr->mesh_nodes;
+    pr->host64.mesh_tris = pr->mesh_tris;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&pr->d32, sizeof(DevProblem<float>));
   if (e == cudaSuccess) e = cudaMalloc(&pr->d64, sizeof(DevProblem<double>));
   if (e == cudaSuccess) e = cudaMemcpy(pr->d32, h32, sizeof(DevProblem<float>), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
@@ -464,6 +503,8 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   if (e != cudaSuccess) {
     if (pr->d32) cudaFree(pr->d32);
     if (pr->d64) cudaFree(pr->d64);
+    if (pr->mesh_nodes) cudaFree(pr->mesh_nodes);
+    if (pr->mesh_tris) cudaFree(pr->mesh_tris);
     delete pr;
     return cuda_fail(ctx, e, "problem upload");
   }
@@ -477,6 +518,8 @@ int wos_problem_destroy(wos_problem* pr) {
     DeviceGuard g(pr->ctx->device);
     cudaFree(pr->d32);
     cudaFree(pr->d64);
+    if (pr->mesh_nodes) cudaFree(pr->mesh_nodes);
+    if (pr->mesh_tris) cudaFree(pr->mesh_tris);
   }
   delete pr;
   return WOS_OK;
@@ -494,7 +537,7 @@ int wos_sigma_bar(wos_ctx* ctx, const wos_problem* pr, int32_t m, double* sb, do
   cudaError_t e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar init");
   double lo[3], hi[3];
-  domain_bbox(pr->host64, lo, hi);
+  domain_bbox(pr, lo, hi);
   double h[3];
   for (int d = 0; d < 3; ++d) h[d] = (hi[d] - lo[d]) / m;
   int blocks = ctx->num_sms * 4;
@@ -638,6 +681,56 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* pr, const float* pts_host, i
 }
 
 }  // extern "C"
+
+extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts,
+                                 int32_t walks_uniform, const wos_params* prm, const double* grad_u,
+                                 double* grad_sigma, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if (npts < 0 || walks_uniform < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
+  if (npts == 0 || walks_uniform == 0) return WOS_OK;
+  if (!pts || !grad_u || !grad_sigma) return fail(ctx, WOS_EINVAL, "null device array");
+  const DevProblem<double>& H = pr->host64;
+  if (H.sigma.kind != wos::F_GRID_LINEAR)
+    return fail(ctx, WOS_EUNSUPPORTED, "the sigma gradient needs sigma given as a multilinear grid");
+  if (H.f.kind == wos::F_MANUFACTURED)
+    return fail(ctx, WOS_EUNSUPPORTED, "a manufactured source depends on sigma; give f explicitly");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
+  wos::AdjLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.dim = pr->dim;
+  L.pts = pts;
+  L.npts = npts;
+  L.walks_uniform = walks_uniform;
+  L.total_items = (uint64_t)npts * (uint64_t)walks_uniform;
+  L.seed = prm->seed;
+  L.walk_offset = prm->walk_offset;
+  L.eps = prm->eps;
+  L.sigma_bar = prm->sigma_bar;
+  L.max_steps = prm->max_steps;
+  L.grad_u = grad_u;
+  L.grad_sigma = grad_sigma;
+  L.stats = reinterpret_cast<unsigned long long*>(stats);
+  L.work_counter = ctx->scratch;
+  L.radial_tab = ctx->radial_tab[pr->dim - 2];
+  if (prm->precision == WOS_FP64) {
+    L.problem = pr->d64;
+    L.problem_bytes = (int)sizeof(DevProblem<double>);
+    e = wos::launch_adjoint_f64(L, ctx->num_sms, st);
+  } else {
+    L.problem = pr->d32;
+    L.problem_bytes = (int)sizeof(DevProblem<float>);
+    e = wos::launch_adjoint_f32(L, ctx->num_sms, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+  return WOS_OK;
+}
 
 // ===========================================================================
 // Allocation-free solve.

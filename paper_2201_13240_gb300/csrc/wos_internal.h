@@ -34,6 +34,30 @@ struct WalkLaunch {
   const float* radial_tab;        // FP32 Newton start table of the launch's dimension
 };
 
+// adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma
+struct AdjLaunch {
+  const void* problem;
+  int problem_bytes;
+  int dim;
+  const float* pts;
+  int64_t npts;
+  int64_t walks_uniform;
+  uint64_t total_items;
+  uint64_t seed;
+  uint64_t walk_offset;
+  double eps;
+  double sigma_bar;
+  int64_t max_steps;
+  const double* grad_u;           // [npts]
+  double* grad_sigma;             // [sigma grid nodes], accumulated
+  unsigned long long* stats;      // optional
+  unsigned long long* work_counter;
+  const float* radial_tab;
+};
+
+cudaError_t launch_adjoint_f32(const AdjLaunch& L, int num_sms, cudaStream_t stream);
+cudaError_t launch_adjoint_f64(const AdjLaunch& L, int num_sms, cudaStream_t stream);
+
 // launch the persistent walk kernel; returns a cudaError_t
 cudaError_t launch_walks_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
 cudaError_t launch_walks_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream);

@@ -11,14 +11,21 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #include "wos_math.cuh"
+
+#if defined(__CUDACC__)
+#define WOS_FIELD_FN __host__ __device__ __noinline__
+#else
+#define WOS_FIELD_FN inline
+#endif
 
 namespace wos {
 
 enum AtomType { A_ONE = 0, A_SIN = 1, A_COS = 2, A_EXP = 3, A_SINH = 4, A_COSH = 5, A_LIN = 6, A_QUAD = 7 };
 enum FieldKind { F_ZERO = 0, F_CONST = 1, F_SST = 2, F_MANUFACTURED = 3, F_GRID_LINEAR = 4, F_GRID_BSPLINE = 5 };
-enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3 };
+enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3, D_MESH = 4 };
 
 constexpr int kMaxTerms = 96;  // separable terms over all fields of one problem
 
@@ -52,6 +59,8 @@ struct DevProblem {
   int32_t pad;
   R dom[16];
   DevField<R> alpha, phi, sigma, f, g, um;
+  const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
+  const float* mesh_tris;   // 12 floats per triangle in leaf order, device
   DevTerm<R> terms[kMaxTerms];
 };
 
@@ -237,11 +246,6 @@ struct FieldVal {
 // is one out-of-line function taking and returning registers: a step evaluates
 // several fields, and inlining the separable-term and B-spline code at every
 // call site made the walk kernel too large for the instruction cache.
-#if defined(__CUDACC__)
-#define WOS_FIELD_FN __host__ __device__ __noinline__
-#else
-#define WOS_FIELD_FN inline
-#endif
 template <int DIM, typename R>
 WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F, R x0, R x1, R x2, bool deriv) {
   FieldVal<R> o = {R(0), R(0), R(0), R(0), R(0)};
@@ -262,7 +266,8 @@ WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F
 
 // Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
 template <int DIM, typename R>
-WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr) {
+WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr,
+                   R* alpha_out = nullptr) {
   FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
   FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
   FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
@@ -296,6 +301,7 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
   R gam = R(0.5) * w_log(A.v) + R(0.5) * Ph.v;
   *fp = w_exp(gam) * f * ia;
   if (gamma_out) *gamma_out = gam;
+  if (alpha_out) *alpha_out = A.v;
 }
 
 template <int DIM, typename R>
@@ -308,6 +314,137 @@ WOS_HD R gamma_at(const DevProblem<R>& P, const R* x) {
 template <int DIM, typename R>
 WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
   return field_eval<DIM>(P, P.g, x[0], x[1], x[2], false).v;
+}
+
+// ---------------------------------------------------------------------------
+// triangle-mesh boundary: closest point through the BVH built at problem
+// creation (Sec. 7.1).  Nodes and triangles are read through the read-only
+// cache; the traversal keeps a per-lane stack of (node, squared box distance),
+// visits the nearer child first and skips every box farther than the best
+// triangle so far.
+// ---------------------------------------------------------------------------
+constexpr int kMeshStack = 64;  // the builder caps the tree depth at 61
+
+struct F4 {
+  float x, y, z, w;
+};
+WOS_HD F4 ld4(const float* p) {
+#if defined(__CUDA_ARCH__)
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return F4{v.x, v.y, v.z, v.w};
+#else
+  return F4{p[0], p[1], p[2], p[3]};
+#endif
+}
+WOS_HD int f_as_i(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_int(f);
+#else
+  int i;
+  memcpy(&i, &f, 4);
+  return i;
+#endif
+}
+
+template <typename R>
+WOS_HD R box_d2(const R* x, const F4& lo, const F4& hi) {
+  R dx = w_fmax(w_fmax(R(lo.x) - x[0], x[0] - R(hi.x)), R(0));
+  R dy = w_fmax(w_fmax(R(lo.y) - x[1], x[1] - R(hi.y)), R(0));
+  R dz = w_fmax(w_fmax(R(lo.z) - x[2], x[2] - R(hi.z)), R(0));
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// Closest point of triangle (a, b, c) to p by its Voronoi regions (Ericson,
+// Real-Time Collision Detection, Sec. 5.1.5): barycentric (v, w) of the point.
+template <typename R>
+WOS_HD void tri_closest(const R* p, const float* t, R* v_out, R* w_out, R* d2_out) {
+  F4 A = ld4(t), B = ld4(t + 4), Cc = ld4(t + 8);
+  R ab[3] = {R(B.x) - R(A.x), R(B.y) - R(A.y), R(B.z) - R(A.z)};
+  R ac[3] = {R(Cc.x) - R(A.x), R(Cc.y) - R(A.y), R(Cc.z) - R(A.z)};
+  R ap[3] = {p[0] - R(A.x), p[1] - R(A.y), p[2] - R(A.z)};
+  R d1 = ab[0] * ap[0] + ab[1] * ap[1] + ab[2] * ap[2];
+  R d2 = ac[0] * ap[0] + ac[1] * ap[1] + ac[2] * ap[2];
+  R abab = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+  R acac = ac[0] * ac[0] + ac[1] * ac[1] + ac[2] * ac[2];
+  R abac = ab[0] * ac[0] + ab[1] * ac[1] + ab[2] * ac[2];
+  R d3 = d1 - abab, d4 = d2 - abac;  // ab.(p-b), ac.(p-b)
+  R d5 = d1 - abac, d6 = d2 - acac;  // ab.(p-c), ac.(p-c)
+  R v, w;
+  R vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+  if (d1 <= R(0) && d2 <= R(0)) { v = R(0); w = R(0); }                       // vertex a
+  else if (d3 >= R(0) && d4 <= d3) { v = R(1); w = R(0); }                    // vertex b
+  else if (d6 >= R(0) && d5 <= d6) { v = R(0); w = R(1); }                    // vertex c
+  else if (vc <= R(0) && d1 >= R(0) && d3 <= R(0)) { v = d1 / (d1 - d3); w = R(0); }   // edge ab
+  else if (vb <= R(0) && d2 >= R(0) && d6 <= R(0)) { v = R(0); w = d2 / (d2 - d6); }   // edge ac
+  else if (va <= R(0) && (d4 - d3) >= R(0) && (d5 - d6) >= R(0)) {                    // edge bc
+    w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    v = R(1) - w;
+  } else {                                                                              // interior
+    R den = R(1) / (va + vb + vc);
+    v = vb * den;
+    w = vc * den;
+  }
+  R q[3] = {ap[0] - ab[0] * v - ac[0] * w, ap[1] - ab[1] * v - ac[1] * w, ap[2] - ab[2] * v - ac[2] * w};
+  *v_out = v;
+  *w_out = w;
+  *d2_out = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+}
+
+template <typename R>
+struct MeshHit {
+  R d, x, y, z;
+};
+
+template <typename R>
+WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2) {
+  const R x[3] = {x0, x1, x2};
+  const float* nodes = P.mesh_nodes;
+  const float* tris = P.mesh_tris;
+  int stk_n[kMeshStack];
+  R stk_d[kMeshStack];
+  int sp = 0;
+  int node = 0;
+  R best = R(INFINITY), bv = R(0), bw = R(0);
+  int best_t = 0;
+  for (;;) {
+    F4 lo = ld4(nodes + 8 * node), hi = ld4(nodes + 8 * node + 4);
+    int left = f_as_i(lo.w), count = f_as_i(hi.w);
+    bool descend = false;
+    if (count > 0) {
+      for (int i = 0; i < count; ++i) {
+        R v, w, d2;
+        tri_closest(x, tris + 12 * (left + i), &v, &w, &d2);
+        if (d2 < best) { best = d2; best_t = left + i; bv = v; bw = w; }
+      }
+    } else {
+      F4 l0 = ld4(nodes + 8 * left), l1 = ld4(nodes + 8 * left + 4);
+      F4 r0 = ld4(nodes + 8 * (left + 1)), r1 = ld4(nodes + 8 * (left + 1) + 4);
+      R dl = box_d2(x, l0, l1), dr = box_d2(x, r0, r1);
+      int nn = (dl <= dr) ? left : left + 1;
+      R dn = (dl <= dr) ? dl : dr, df = (dl <= dr) ? dr : dl;
+      if (dn < best) {
+        if (df < best && sp < kMeshStack) { stk_n[sp] = (nn == left) ? left + 1 : left; stk_d[sp] = df; ++sp; }
+        node = nn;
+        descend = true;
+      }
+    }
+    if (descend) continue;
+    // pop the next node still closer than the best triangle
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (stk_d[sp] < best) { node = stk_n[sp]; found = true; break; }
+    }
+    if (!found) break;
+  }
+  const float* t = tris + 12 * best_t;
+  F4 A = ld4(t), B = ld4(t + 4), Cc = ld4(t + 8);
+  MeshHit<R> h;
+  h.x = R(A.x) + (R(B.x) - R(A.x)) * bv + (R(Cc.x) - R(A.x)) * bw;
+  h.y = R(A.y) + (R(B.y) - R(A.y)) * bv + (R(Cc.y) - R(A.y)) * bw;
+  h.z = R(A.z) + (R(B.z) - R(A.z)) * bv + (R(Cc.z) - R(A.z)) * bw;
+  h.d = w_sqrt(best);
+  return h;
 }
 
 // ---------------------------------------------------------------------------
@@ -381,6 +518,14 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb) {
       for (int d = 0; d < DIM; ++d)
         if (d == imax) xb[d] = p[d] + ((rel[d] >= R(0)) ? p[3 + d] : -p[3 + d]);
       return rc - qmax;
+    }
+    case D_MESH: {
+      if (DIM != 3) return R(-1);
+      MeshHit<R> h = mesh_query<R>(P, x[0], x[1], x[2]);
+      xb[0] = h.x;
+      xb[1] = h.y;
+      xb[2] = h.z;
+      return h.d;
     }
     default:
       return R(-1);

@@ -52,6 +52,7 @@ REPLAY_CASES = {
                       lambda: np.array([[0.5, -0.6, 0.0, 0.7, -0.4, 0.2], [0.2, 0.3, -0.8, -0.5, -0.5, 0.9]],
                                        dtype=np.float32), 1e-3),
     "noise_cube": (W.noise_cube_problem, lambda: W.uniform_in_box(3, 24, 0.1, 0.9, 6), 1e-3),
+    "mesh": (lambda: W.mesh_manufactured_problem(level=5), lambda: W.mesh_interior_points(32, 7), 1e-4),
 }
 
 
@@ -108,7 +109,7 @@ def test_fp32_parity_cube3d_subset(orc, ctx):
     assert ok, (nout, mz)
 
 
-@pytest.mark.parametrize("name", ["noise_annulus", "noise_cube", "rounded_box"])
+@pytest.mark.parametrize("name", ["noise_annulus", "noise_cube", "rounded_box", "mesh"])
 def test_fp32_parity_other_domains_and_grids(orc, ctx, name):
     mk, ptsf, eps = REPLAY_CASES[name]
     desc = mk()
@@ -238,3 +239,27 @@ def test_solve_host_matches_device(orc, ctx):
     assert np.allclose(mean.numpy(), m_d, rtol=1e-12, atol=1e-12)
     assert np.allclose(se.numpy(), se_d, rtol=1e-9, atol=1e-12)
     assert int(stats[1]) == 16 ** 3 * 64
+
+
+def test_mesh_noise_workload_sampled_points(orc, ctx):
+    """Displaced icosphere (327,680 triangles) with 128^3 noise grids: FP32 GPU against the
+    oracle on sampled interior points, and the manufactured solution on the same mesh."""
+    desc = W.mesh_noise_problem(level=7)
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 48)[0]
+    assert ctx.sigma_bar(prob, 48) == pytest.approx(orc.sigma_bar(desc, 48), rel=1e-9)
+    pts = W.mesh_interior_points(12, seed=8)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 1024, 1e-4, sb, seed=3)
+    oacc, _ = orc.solve(desc, pts, 512, seed=4, eps=1e-4, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (nout, mz)
+    assert st[2] == 0 and st[3] == 0
+    man = W.mesh_manufactured_problem(level=7)
+    mp = ctx.problem(man)
+    sbm = orc.sigma_bar(man, 48)[0]
+    pts = W.mesh_interior_points(2048, seed=9)
+    m, se, st, _ = _gpu_solve(ctx, mp, pts, 1 << 14, 1e-4, sbm, seed=5)
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    ok, nout, mz = four_se_rule((m - exact) / se)
+    assert ok, (nout, mz)

@@ -306,3 +306,94 @@ def rounded_box_problem():
 
 def rounded_box_exact(x, y):
     return np.cos(x) * np.exp(0.5 * y)
+
+
+# ---------------------------------------------------------------------------
+# Mesh workload: a displaced icosphere.  An icosahedron subdivided `level` times
+# (20 * 4^level triangles; level 7 = 327,680, the nearest icosphere to 2^18),
+# vertices on the unit sphere displaced radially to r = 1 + amp * n(v), with n a
+# seeded 3D value noise in [-1, 1] (lattice spacing 0.25, quintic fade).  The
+# surface stays star-shaped about the origin, closed and consistently oriented.
+# ---------------------------------------------------------------------------
+def icosphere(level):
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4], [11, 10, 2],
+                  [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5],
+                  [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    for _ in range(level):
+        e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+        key = np.sort(e, axis=1)
+        uniq, inv = np.unique(key[:, 0] * len(v) + key[:, 1], return_inverse=True)
+        a, b = uniq // len(v), uniq % len(v)
+        mid = v[a] + v[b]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        m = inv.reshape(3, -1).T + len(v)  # midpoints of edges (01, 12, 20) per face
+        v = np.concatenate([v, mid])
+        f = np.concatenate([np.stack([f[:, 0], m[:, 0], m[:, 2]], 1), np.stack([f[:, 1], m[:, 1], m[:, 0]], 1),
+                            np.stack([f[:, 2], m[:, 2], m[:, 1]], 1), m])
+    return v, f
+
+
+def value_noise_3d(x, seed, spacing=0.25, extent=2.0):
+    """Seeded value noise in [-1, 1] at points x (n x 3), lattice spacing `spacing` on [-extent, extent]^3."""
+    rng = np.random.default_rng(seed)
+    n = int(round(2 * extent / spacing)) + 2
+    lattice = rng.uniform(-1.0, 1.0, size=(n, n, n))
+    s = (np.asarray(x, dtype=np.float64) + extent) / spacing
+    i0 = np.clip(np.floor(s).astype(np.int64), 0, n - 2)
+    t = s - i0
+    w = t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    out = np.zeros(len(s))
+    for c in range(8):
+        o = [(c >> d) & 1 for d in range(3)]
+        wt = np.ones(len(s))
+        for d in range(3):
+            wt *= w[:, d] if o[d] else 1.0 - w[:, d]
+        out += wt * lattice[i0[:, 0] + o[0], i0[:, 1] + o[1], i0[:, 2] + o[2]]
+    return out
+
+
+def displaced_icosphere(level=7, amplitude=0.1, seed=3):
+    """Vertices (float32 n x 3) and triangles (int32 m x 3) of the displaced icosphere."""
+    v, f = icosphere(level)
+    r = 1.0 + amplitude * value_noise_3d(v, seed)
+    return (v * r[:, None]).astype(np.float32), f.astype(np.int32)
+
+
+def mesh_domain(verts, tris):
+    return {"kind": "mesh", "p": [0.0] * 16, "verts": verts, "tris": tris}
+
+
+def mesh_noise_problem(level=7, grid_res=128, seed=3):
+    """Displaced icosphere boundary; alpha in [0.5, 2] (cubic B-spline), sigma in [0, 20] and
+    f in [-1, 1] (multilinear) from seeded 128^3 value-noise grids over the mesh box plus 5%;
+    g = x y + z."""
+    verts, tris = displaced_icosphere(level, 0.1, seed)
+    lo = verts.min(axis=0).astype(np.float64)
+    hi = verts.max(axis=0).astype(np.float64)
+    pad = 0.05 * (hi - lo)
+    lo, hi = list(lo - pad), list(hi + pad)
+    a = value_noise_grid(3, grid_res, 0.5, 2.0, seed + 1, cell=8)
+    s = value_noise_grid(3, grid_res, 0.0, 20.0, seed + 2, cell=8)
+    f = value_noise_grid(3, grid_res, -1.0, 1.0, seed + 3, cell=8)
+    g = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)), term(1.0, None, None, (LIN, 1.0, 0.0)))
+    return problem(3, mesh_domain(verts, tris), grid_field("grid_bspline", a, lo, hi),
+                   grid_field("grid_linear", s, lo, hi), grid_field("grid_linear", f, lo, hi), g)
+
+
+def mesh_interior_points(n, seed, radius=0.88):
+    """Uniform points in the ball of radius 0.88: inside the displaced icosphere, whose
+    vertices lie at r >= 0.9 and whose flat triangles dip below that by < 1e-4."""
+    return uniform_in_ball(3, n, [0.0, 0.0, 0.0], radius, seed)
+
+
+def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3):
+    """The 3D manufactured problem (u, alpha, sigma, drift of the cube workload) on the
+    displaced-icosphere domain: u is exact on any domain, so the mesh walk has an exact answer."""
+    verts, tris = displaced_icosphere(level, amplitude, seed)
+    p = cube3d_problem()
+    p["domain"] = mesh_domain(verts, tris)
+    return p
