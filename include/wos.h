@@ -152,6 +152,7 @@ typedef struct {
 
 typedef struct wos_ctx wos_ctx;
 typedef struct wos_problem wos_problem;
+typedef struct wos_batch wos_batch;
 
 /* Create a context on CUDA device `device` (allocates a small scratch buffer).
    Errors: WOS_EINVAL (null out pointer), WOS_ECUDA (device not usable). */
@@ -218,6 +219,24 @@ int wos_finalize(wos_ctx* ctx, const double* sum, const double* sumsq, const int
 int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
                       int32_t walks_uniform, const wos_params* params, const double* grad_u,
                       double* grad_sigma, uint64_t* stats, void* stream);
+
+/* ---- batches of independent problems (not in the paper; many small solves in one launch) ----
+   wos_batch_create uploads nprob problems of one dimension (no mesh domains) with HOST
+   point offsets [nprob + 1] (points of problem i are offsets[i] .. offsets[i+1]-1 of the
+   batch's point array; offsets[0] = 0, non-decreasing) and HOST per-problem sigma_bar
+   [nprob] (> 0).  The batch keeps device copies of the problem descriptions (grid data
+   stays with the caller) and a prefix-sum buffer for per-point walk counts.
+   wos_solve_batch runs every walk of every problem in ONE persistent launch, claiming
+   (point, walk) items across problems as walks finish; it allocates nothing and does not
+   synchronise, so it can be captured in a CUDA graph.  Arguments and results as
+   wos_solve (pts: device SoA [dim][npts of the batch]); params->sigma_bar is ignored.
+   Walk streams are keyed by the point's index in the batch. */
+int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, int32_t nprob, const int64_t* pt_offsets,
+                     const double* sigma_bars, wos_batch** batch);
+int wos_batch_destroy(wos_batch* batch);
+int wos_solve_batch(wos_ctx* ctx, const wos_batch* batch, const float* pts, const int32_t* walks,
+                    int32_t walks_uniform, const wos_params* params, double* sum, double* sumsq, int64_t* count,
+                    uint64_t* stats, void* stream);
 
 /* End-to-end convenience: HOST points in, HOST mean / variance / stderr out (and
    HOST stats if non-NULL).  Copies the inputs to device buffers owned by the

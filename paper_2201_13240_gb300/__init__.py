@@ -84,6 +84,9 @@ def load():
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_adjoint_sigma.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
+    lib.wos_batch_create.argtypes = [vp, C.POINTER(vp), i32, vp, vp, C.POINTER(vp)]
+    lib.wos_batch_destroy.argtypes = [vp]
+    lib.wos_solve_batch.argtypes = [vp, vp, vp, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -131,6 +134,7 @@ class Problem:
         self.ctx = ctx
         self.dim = desc["dim"]
         self._keep = []
+        self._sigma_ptr = 0
         D = ProblemDesc()
         D.dim = desc["dim"]
         D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
@@ -167,13 +171,49 @@ class Problem:
                     F.lo[d] = fd["lo"][d] if d < len(fd["lo"]) else 0.0
                     F.hi[d] = fd["hi"][d] if d < len(fd["hi"]) else 0.0
                 F.data = data.data_ptr()
+                if name == "sigma":
+                    self._sigma_ptr = data.data_ptr()
         h = C.c_void_p()
         ctx._check(ctx.lib.wos_problem_create(ctx.handle, C.byref(D), C.byref(h)))
         self.handle = h
 
+    def sigma_data_ptr(self):
+        """Device address of the sigma grid the problem reads (0 if sigma is not a grid)."""
+        return self._sigma_ptr
+
     def close(self):
         if getattr(self, "handle", None):
             self.ctx.lib.wos_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent problems solved by one launch (owns the library handle)."""
+
+    def __init__(self, ctx, problems, pt_offsets, sigma_bars):
+        self.ctx = ctx
+        self.problems = list(problems)  # keep the problems (and their grid tensors) alive
+        self.dim = self.problems[0].dim
+        offs = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+        sbs = np.ascontiguousarray(sigma_bars, dtype=np.float64)
+        if len(offs) != len(self.problems) + 1 or len(sbs) != len(self.problems):
+            raise ValueError("need nprob + 1 offsets and nprob sigma_bars")
+        self.npts = int(offs[-1])
+        handles = (C.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        h = C.c_void_p()
+        ctx._check(ctx.lib.wos_batch_create(ctx.handle, handles, len(self.problems), offs.ctypes.data,
+                                            sbs.ctypes.data, C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.wos_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -285,6 +325,34 @@ class Context:
         self._check(self.lib.wos_finalize(self.handle, _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), n,
                                           _ptr(mean), _ptr(var), _ptr(se), _stream(stream)))
         return mean, var, se
+
+    def batch(self, problems, pt_offsets, sigma_bars):
+        return Batch(self, problems, pt_offsets, sigma_bars)
+
+    def solve_batch(self, batch, pts, walks, eps, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32",
+                    accum=None, stats=None, stream=None):
+        """One launch over every problem of the batch; pts: cuda float32 [dim, npts of the batch]."""
+        import torch
+        pts = _points(pts, batch.dim, self.device)
+        npts = pts.shape[1]
+        if npts != batch.npts:
+            raise ValueError(f"the batch has {batch.npts} points, got {npts}")
+        if accum is None:
+            accum = self.new_accum(npts)
+        if stats is None:
+            stats = self.new_stats()
+        if isinstance(walks, int):
+            wp, wu = None, walks
+        else:
+            if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                    and walks.shape == (npts,)):
+                raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+            wp, wu = _ptr(walks.contiguous()), 0
+        p = params(eps, 1.0, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_batch(self.handle, batch.handle, _ptr(pts), wp, wu, C.byref(p),
+                                             _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), _ptr(stats),
+                                             _stream(stream)))
+        return accum, stats
 
     def adjoint_sigma(self, prob, pts, walks, grad_u, grad_sigma, eps, sigma_bar, seed=0, walk_offset=0,
                       max_steps=1 << 20, precision="fp32", stats=None, stream=None):

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   bool exhausted = false, active = false;
   // walk state; phase 0 computes the total A, phase 1 replays and scatters
   R x[3] = {R(0), R(0), R(0)}, W = R(1), acc = R(0), total = R(0);
+  R xbp[3] = {R(0), R(0), R(0)};  // previous closest boundary point (bounds the next mesh query)
   uint32_t p = 0, w = 0, k = 0, phase = 0;
   double coef = 0.0;
   unsigned long long st_steps = 0;
@@ -125,7 +126,14 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     if (!active) continue;
 
     R xb[3];
-    R d = distance<DIM>(P, x, xb);
+    R bound2 = R(INFINITY);
+    if (P.domain_kind == D_MESH && k > 0) {
+      R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
+      bound2 = e0 * e0 + e1 * e1 + e2 * e2;
+    }
+    R d = distance<DIM>(P, x, xb, bound2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
     const bool ends = !(d >= eps) || k >= max_k;
     const R dd = w_fmax(d, R(0));
     U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);

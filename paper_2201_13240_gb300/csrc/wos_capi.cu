@@ -37,12 +37,25 @@ struct wos_ctx {
   int64_t host_cap = 0;
 };
 
+struct wos_batch {
+  wos_ctx* ctx = nullptr;
+  int dim = 0;
+  int32_t nprob = 0;
+  int64_t npts = 0;
+  DevProblem<float>* d32 = nullptr;   // [nprob]
+  DevProblem<double>* d64 = nullptr;  // [nprob]
+  int64_t* offsets = nullptr;         // [nprob + 1]
+  double* sigma_bars = nullptr;       // [nprob]
+  int64_t* walk_end = nullptr;        // [npts] prefix sums for per-point walk counts
+};
+
 struct wos_problem {
   wos_ctx* ctx = nullptr;
   int dim = 0;
   DevProblem<float>* d32 = nullptr;
   DevProblem<double>* d64 = nullptr;
   DevProblem<double> host64;  // host copy for the sigma_bar lattice bounds
+  DevProblem<float> host32;   // host copy for batches
   float* mesh_nodes = nullptr;  // device BVH of a mesh boundary
   float* mesh_tris = nullptr;
   double mesh_lo[3] = {0, 0, 0}, mesh_hi[3] = {0, 0, 0};
@@ -331,6 +344,7 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.uhat = uhat;
   L.steps_out = steps;
   L.radial_tab = ctx->radial_tab[prob->dim - 2];
+  L.mesh = prob->host64.domain_kind == wos::D_MESH;
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
@@ -497,6 +511,7 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   }
   if (e == cudaSuccess) e = cudaMalloc(&pr->d32, sizeof(DevProblem<float>));
   if (e == cudaSuccess) e = cudaMalloc(&pr->d64, sizeof(DevProblem<double>));
+  pr->host32 = *h32;
   if (e == cudaSuccess) e = cudaMemcpy(pr->d32, h32, sizeof(DevProblem<float>), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
   delete h32;
@@ -729,6 +744,131 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
     e = wos::launch_adjoint_f32(L, ctx->num_sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, int32_t nprob,
+                                const int64_t* pt_offsets, const double* sigma_bars, wos_batch** out) {
+  if (!ctx) return WOS_EINVAL;
+  if (!out || !probs || !pt_offsets || !sigma_bars || nprob < 1) return fail(ctx, WOS_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  int dim = probs[0] ? probs[0]->dim : 0;
+  if (pt_offsets[0] != 0) return fail(ctx, WOS_EINVAL, "point offsets must start at 0");
+  for (int32_t i = 0; i < nprob; ++i) {
+    if (!probs[i]) return fail(ctx, WOS_EINVAL, "null problem in batch");
+    if (probs[i]->ctx != ctx) return fail(ctx, WOS_EINVAL, "problem of another context in batch");
+    if (probs[i]->dim != dim) return fail(ctx, WOS_EINVAL, "all problems of a batch must have one dimension");
+    if (probs[i]->host64.domain_kind == wos::D_MESH) return fail(ctx, WOS_EUNSUPPORTED, "mesh domains in a batch");
+    if (pt_offsets[i + 1] < pt_offsets[i]) return fail(ctx, WOS_EINVAL, "point offsets must not decrease");
+    if (!finite_pos(sigma_bars[i])) return fail(ctx, WOS_EINVAL, "sigma_bar of every problem must be > 0");
+  }
+  int64_t npts = pt_offsets[nprob];
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in a batch");
+  DeviceGuard g(ctx->device);
+  wos_batch* b = new wos_batch();
+  b->ctx = ctx;
+  b->dim = dim;
+  b->nprob = nprob;
+  b->npts = npts;
+  std::vector<DevProblem<float>> h32(nprob);
+  std::vector<DevProblem<double>> h64(nprob);
+  for (int32_t i = 0; i < nprob; ++i) {
+    h32[i] = probs[i]->host32;
+    h64[i] = probs[i]->host64;
+  }
+  cudaError_t e = cudaMalloc(&b->d32, sizeof(DevProblem<float>) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d64, sizeof(DevProblem<double>) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->offsets, sizeof(int64_t) * (nprob + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sigma_bars, sizeof(double) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->walk_end, sizeof(int64_t) * (npts > 0 ? npts : 1));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d32, h32.data(), sizeof(DevProblem<float>) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d64, h64.data(), sizeof(DevProblem<double>) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->offsets, pt_offsets, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->sigma_bars, sigma_bars, sizeof(double) * nprob, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    wos_batch_destroy(b);
+    return cuda_fail(ctx, e, "batch upload");
+  }
+  *out = b;
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_destroy(wos_batch* b) {
+  if (!b) return WOS_EINVAL;
+  {
+    DeviceGuard g(b->ctx->device);
+    if (b->d32) cudaFree(b->d32);
+    if (b->d64) cudaFree(b->d64);
+    if (b->offsets) cudaFree(b->offsets);
+    if (b->sigma_bars) cudaFree(b->sigma_bars);
+    if (b->walk_end) cudaFree(b->walk_end);
+  }
+  delete b;
+  return WOS_OK;
+}
+
+extern "C" int wos_solve_batch(wos_ctx* ctx, const wos_batch* b, const float* pts, const int32_t* walks,
+                               int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq,
+                               int64_t* count, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!b || b->ctx != ctx) return fail(ctx, WOS_EINVAL, "null batch or batch of another context");
+  if (!prm) return fail(ctx, WOS_EINVAL, "params is NULL");
+  if (!finite_pos(prm->eps) || prm->max_steps < 1 || (prm->precision != WOS_FP32 && prm->precision != WOS_FP64))
+    return fail(ctx, WOS_EINVAL, "eps must be > 0, max_steps >= 1, precision FP32 or FP64");
+  if (!walks && walks_uniform < 0) return fail(ctx, WOS_EINVAL, "walks_uniform < 0");
+  if (b->npts == 0 || (!walks && walks_uniform == 0)) return WOS_OK;
+  if (!pts || !sum || !sumsq || !count) return fail(ctx, WOS_EINVAL, "null device array");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t* walk_end = nullptr;
+  uint64_t total;
+  if (walks) {
+    walk_prefix_kernel<<<1, 1024, 0, st>>>(walks, b->npts, b->walk_end);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "walk prefix kernel");
+    walk_end = b->walk_end;
+    total = ~0ull;
+  } else {
+    total = (uint64_t)b->npts * (uint64_t)walks_uniform;
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
+  unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
+  if (st_ptr == nullptr) {
+    st_ptr = ctx->scratch + kScratchStats;
+    e = cudaMemsetAsync(st_ptr, 0, wos::ST_WORDS * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(stats)");
+  }
+  wos::WalkLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.dim = b->dim;
+  L.pts = pts;
+  L.npts = b->npts;
+  L.walk_end = walk_end;
+  L.walks_uniform = walks_uniform;
+  L.total_items = total;
+  L.seed = prm->seed;
+  L.walk_offset = prm->walk_offset;
+  L.eps = prm->eps;
+  L.sigma_bar = 1.0;  // per problem: sigma_bars
+  L.max_steps = prm->max_steps;
+  L.sum = sum;
+  L.sumsq = sumsq;
+  L.count = reinterpret_cast<unsigned long long*>(count);
+  L.stats = st_ptr;
+  L.work_counter = ctx->scratch;
+  L.radial_tab = ctx->radial_tab[b->dim - 2];
+  L.prob_offsets = b->offsets;
+  L.sigma_bars = b->sigma_bars;
+  L.nprob = b->nprob;
+  if (prm->precision == WOS_FP64) {
+    L.probs = b->d64;
+    e = wos::launch_walks_f64(L, ctx->num_sms, st);
+  } else {
+    L.probs = b->d32;
+    e = wos::launch_walks_f32(L, ctx->num_sms, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batched walk kernel launch");
   return WOS_OK;
 }
 

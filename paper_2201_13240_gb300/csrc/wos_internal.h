@@ -32,6 +32,12 @@ struct WalkLaunch {
   double* uhat;                   // optional per-walk estimates [total_items]
   int64_t* steps_out;             // optional per-walk step counts [total_items]
   const float* radial_tab;        // FP32 Newton start table of the launch's dimension
+  int mesh;                       // the domain is a triangle mesh
+  // batched launches: many problems, points of problem i are prob_offsets[i] .. prob_offsets[i+1]-1
+  const void* probs;              // contiguous DevProblem<R>[nprob], device
+  const int64_t* prob_offsets;    // [nprob + 1], device
+  const double* sigma_bars;       // [nprob], device
+  int32_t nprob;
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

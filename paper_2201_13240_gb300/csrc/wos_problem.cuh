@@ -102,16 +102,38 @@ WOS_HD void atom(int type, R k, R ph, R x, R* h, R* h1, R* h2) {
   }
 }
 
-template <int DIM, typename R>
-WOS_HD void sst_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap,
-                     bool deriv) {
+// value of an atom only (value-only field evaluations)
+template <typename R>
+WOS_HD R atom_value(int type, R k, R ph, R x) {
+  R t = k * x + ph;
+  switch (type) {
+    case A_SIN: return w_sin(t);
+    case A_COS: return w_cos(t);
+    case A_EXP: return w_exp(t);
+    case A_SINH: { R e = w_exp(t); return R(0.5) * (e - R(1) / e); }
+    case A_COSH: { R e = w_exp(t); return R(0.5) * (e + R(1) / e); }
+    case A_LIN: return t;
+    case A_QUAD: return t * t;
+    default: return R(1);
+  }
+}
+
+// Sum of separable terms.  A constant (ONE) atom is skipped by a test that is
+// uniform across the warp (every lane reads the same term).
+template <int DIM, typename R, bool DERIV>
+WOS_HD void sst_eval(const DevProblem<R>& P, const DevField<R>& F, const R* x, R* v, R* g, R* lap) {
+  const bool deriv = DERIV;
   R vv = R(0), ll = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
 #pragma unroll 1
   for (int n = 0; n < F.nterms; ++n) {
     const DevTerm<R>& T = P.terms[F.first + n];
     R h[3] = {R(1), R(1), R(1)}, h1[3] = {R(0), R(0), R(0)}, h2[3] = {R(0), R(0), R(0)};
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) atom(T.type[i], T.k[i], T.phi[i], x[i], &h[i], &h1[i], &h2[i]);
+    for (int i = 0; i < DIM; ++i) {
+      if (T.type[i] == A_ONE) continue;
+      if (DERIV) atom(T.type[i], T.k[i], T.phi[i], x[i], &h[i], &h1[i], &h2[i]);
+      else h[i] = atom_value(T.type[i], T.k[i], T.phi[i], x[i]);
+    }
     R p01 = h[0] * h[1];
     vv += T.c * p01 * h[2];
     if (deriv) {
@@ -246,22 +268,27 @@ struct FieldVal {
 // is one out-of-line function taking and returning registers: a step evaluates
 // several fields, and inlining the separable-term and B-spline code at every
 // call site made the walk kernel too large for the instruction cache.
-template <int DIM, typename R>
-WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F, R x0, R x1, R x2, bool deriv) {
+template <int DIM, typename R, bool DERIV>
+WOS_FIELD_FN FieldVal<R> field_eval_t(const DevProblem<R>& P, const DevField<R>& F, R x0, R x1, R x2) {
   FieldVal<R> o = {R(0), R(0), R(0), R(0), R(0)};
   const R x[3] = {x0, x1, x2};
   R g[3] = {R(0), R(0), R(0)};
   switch (F.kind) {
     case F_CONST: o.v = F.value; return o;
-    case F_SST: sst_eval<DIM>(P, F, x, &o.v, g, &o.lap, deriv); break;
+    case F_SST: sst_eval<DIM, R, DERIV>(P, F, x, &o.v, g, &o.lap); break;
     case F_GRID_LINEAR: o.v = grid_linear<DIM>(F, x); return o;  // piecewise linear: no second derivative
-    case F_GRID_BSPLINE: grid_bspline<DIM>(F, x, &o.v, g, &o.lap, deriv); break;
+    case F_GRID_BSPLINE: grid_bspline<DIM>(F, x, &o.v, g, &o.lap, DERIV); break;
     default: return o;
   }
   o.gx = g[0];
   o.gy = g[1];
   o.gz = g[2];
   return o;
+}
+
+template <int DIM, typename R>
+WOS_HD FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F, R x0, R x1, R x2, bool deriv) {
+  return deriv ? field_eval_t<DIM, R, true>(P, F, x0, x1, x2) : field_eval_t<DIM, R, false>(P, F, x0, x1, x2);
 }
 
 // Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
@@ -395,17 +422,26 @@ struct MeshHit {
   R d, x, y, z;
 };
 
+// bound2: an upper bound of the squared distance (a known boundary point's), or
+// infinity.  The search starts from it, slightly enlarged for rounding, so only
+// boxes nearer than a known boundary point are opened; if rounding still hides
+// every triangle, the search restarts without the bound.  The result does not
+// depend on the bound.
 template <typename R>
-WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2) {
+WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2) {
   const R x[3] = {x0, x1, x2};
   const float* nodes = P.mesh_nodes;
   const float* tris = P.mesh_tris;
   int stk_n[kMeshStack];
   R stk_d[kMeshStack];
+  R best, bv = R(0), bw = R(0);
+  int best_t = -1;
+  const R slack = (sizeof(R) == 4) ? R(1e-5) : R(1e-12);
+  R start = (bound2 < R(INFINITY)) ? bound2 * (R(1) + slack) + R(1e-30) : R(INFINITY);
+  for (int attempt = 0; attempt < 2 && best_t < 0; ++attempt) {
+  best = (attempt == 0) ? start : R(INFINITY);
   int sp = 0;
   int node = 0;
-  R best = R(INFINITY), bv = R(0), bw = R(0);
-  int best_t = 0;
   for (;;) {
     F4 lo = ld4(nodes + 8 * node), hi = ld4(nodes + 8 * node + 4);
     int left = f_as_i(lo.w), count = f_as_i(hi.w);
@@ -437,6 +473,8 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2) {
     }
     if (!found) break;
   }
+  }
+  if (best_t < 0) best_t = 0;
   const float* t = tris + 12 * best_t;
   F4 A = ld4(t), B = ld4(t + 4), Cc = ld4(t + 8);
   MeshHit<R> h;
@@ -450,8 +488,10 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2) {
 // ---------------------------------------------------------------------------
 // distance to the boundary (positive inside) and closest boundary point
 // ---------------------------------------------------------------------------
-template <int DIM, typename R>
-WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb) {
+// bound2 (meshes only): an upper bound of the squared distance, see mesh_query.
+// MESH = false compiles the mesh case out (for kernels launched on analytic domains).
+template <int DIM, typename R, bool MESH = true>
+WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY)) {
   const R* p = P.dom;
 #pragma unroll
   for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
@@ -520,8 +560,8 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb) {
       return rc - qmax;
     }
     case D_MESH: {
-      if (DIM != 3) return R(-1);
-      MeshHit<R> h = mesh_query<R>(P, x[0], x[1], x[2]);
+      if (DIM != 3 || !MESH) return R(-1);
+      MeshHit<R> h = mesh_query<R>(P, x[0], x[1], x[2], bound2);
       xb[0] = h.x;
       xb[1] = h.y;
       xb[2] = h.z;

@@ -37,8 +37,10 @@ constexpr uint64_t kChunk = 128;
 template <int DIM, typename R>
 struct WalkState {
   R x[3];
+  R xbp[3];  // closest boundary point of the previous step (bounds the next mesh query)
   R W, acc;
   uint32_t p, w, k;
+  uint32_t prob;  // batched launches: the walk's problem
   uint64_t item;
 };
 
@@ -51,9 +53,8 @@ __device__ __forceinline__ double point_factor(const WalkLaunch& L, const DevPro
   return exp(-(double)gamma_at<DIM>(P, x0));
 }
 
-template <int DIM, typename R>
-__device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem<R>& P, uint64_t item,
-                                           WalkState<DIM, R>& s) {
+template <int DIM, typename R, bool BATCHED>
+__device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, WalkState<DIM, R>& s) {
   uint64_t p, j;
   if (L.walk_end == nullptr) {
     p = item / (uint64_t)L.walks_uniform;
@@ -71,6 +72,16 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem
   }
   s.item = item;
   s.p = (uint32_t)p;
+  s.prob = 0;
+  if (BATCHED) {
+    // the problem whose point range holds p: last offset <= p
+    int lo = 0, hi = L.nprob - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if ((uint64_t)__ldg(&L.prob_offsets[mid]) <= p) lo = mid; else hi = mid - 1;
+    }
+    s.prob = (uint32_t)lo;
+  }
   s.w = (uint32_t)(L.walk_offset + j);
   s.k = 0;
 #pragma unroll
@@ -82,23 +93,28 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, const DevProblem
 // FP32: at most 128 registers, so four 128-thread blocks (16 warps) fit an SM.  Left
 // alone the compiler takes 168 (12 warps); the cap spills ~80 bytes and measured 22%
 // faster on the 3D workload, the extra warps hiding the step's dependency chains.
-template <int DIM, typename R>
+// MESH: the domain is a triangle mesh; the walk then keeps its previous closest
+// point to bound the next BVH search (analytic domains carry none of this).
+// BATCHED: the launch walks many problems (each walk's problem description is
+// read from global memory through L1 instead of being staged in shared memory).
+template <int DIM, typename R, bool MESH, bool BATCHED>
 __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk_kernel(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
-  {
+  if (!BATCHED) {
     const int4* src = reinterpret_cast<const int4*>(L.problem);
     int4* dst = reinterpret_cast<int4*>(smem_raw);
     for (int i = threadIdx.x; i < L.problem_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
   }
-  __syncthreads();
-  const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
+  const DevProblem<R>* Pshared = reinterpret_cast<const DevProblem<R>*>(smem_raw);
+  const DevProblem<R>* Pall = reinterpret_cast<const DevProblem<R>*>(L.probs);
 
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
-  const R eps = R(L.eps), sb = R(L.sigma_bar), s_root = w_sqrt(R(L.sigma_bar));
-  const R inv_sb = R(1) / sb;
+  const R eps = R(L.eps);
+  R s_root = w_sqrt(R(L.sigma_bar)), inv_sb = R(1) / R(L.sigma_bar);
   const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
 
   // with per-point walk counts the total is the last inclusive prefix sum
@@ -112,7 +128,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
 
   // per-lane partial sums of the current point (points are < 2^32 per launch)
   const uint32_t kNoPoint = 0xffffffffu;
-  uint32_t acc_p = kNoPoint;
+  uint32_t acc_p = kNoPoint, acc_prob = 0;
   double s1 = 0.0, s2 = 0.0;
   uint32_t n_acc = 0;
   // per-lane statistics: a lane finishes far fewer than 2^32 walks in one launch
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
       unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
       unsigned rank = __popc(need & lt_mask);
       if (!active && rank < take) {
-        start_walk<DIM, R>(L, P, chunk_next + rank, s);
+        start_walk<DIM, R, BATCHED>(L, chunk_next + rank, s);
         active = true;
       }
       chunk_next += take;
@@ -147,10 +163,25 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
     }
     if (__ballot_sync(kFull, active) == 0u) break;
     if (!active) continue;
+    const DevProblem<R>& P = BATCHED ? Pall[s.prob] : *Pshared;
+    if (BATCHED) {
+      double sbp = __ldg(&L.sigma_bars[s.prob]);
+      s_root = w_sqrt(R(sbp));
+      inv_sb = R(1) / R(sbp);
+    }
 
     // ---- one step of the walk ----
     R xb[3];
-    R d = distance<DIM>(P, s.x, xb);
+    R bound2 = R(INFINITY);
+    if (MESH && s.k > 0) {
+      R e0 = s.x[0] - s.xbp[0], e1 = s.x[1] - s.xbp[1], e2 = s.x[2] - s.xbp[2];
+      bound2 = e0 * e0 + e1 * e1 + e2 * e2;
+    }
+    R d = distance<DIM, R, MESH>(P, s.x, xb, bound2);
+    if (MESH) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s.xbp[i] = xb[i];
+    }
     const bool ends = !(d >= eps) || s.k >= max_k;  // eps-shell (or outside, or NaN), or the step cap
     const R dd = w_fmax(d, R(0));
 
@@ -191,12 +222,13 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
       double acc_d = (double)s.acc;
       if (accumulate && s.p != acc_p) {
         if (acc_p != kNoPoint) {
-          double e0 = point_factor<DIM, R>(L, P, acc_p);
+          double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
           atomicAdd(&L.sum[acc_p], s1 * e0);
           atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
           atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
         }
         acc_p = s.p;
+        acc_prob = s.prob;
         s1 = 0.0;
         s2 = 0.0;
         n_acc = 0;
@@ -229,7 +261,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
   }
 
   if (accumulate && acc_p != kNoPoint) {
-    double e0 = point_factor<DIM, R>(L, P, acc_p);
+    double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
     atomicAdd(&L.sum[acc_p], s1 * e0);
     atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
     atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
@@ -252,25 +284,33 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
   }
 }
 
-template <int DIM, typename R>
-cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
-  size_t smem = (size_t)L.problem_bytes;
+template <int DIM, typename R, bool MESH, bool BATCHED>
+cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
+  size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R>, kWalkBlock, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED>,
+                                                                kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
   uint64_t warps_needed = (L.total_items + 31) / 32;
   uint64_t blocks_needed = (warps_needed + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R><<<grid, kWalkBlock, smem, stream>>>(L);
+  wos_walk_kernel<DIM, R, MESH, BATCHED><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
+}
+
+template <int DIM, typename R>
+cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
+  if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true>(L, num_sms, stream);
+  if (DIM == 3 && L.mesh) return launch_walks_m<DIM, R, true, false>(L, num_sms, stream);
+  return launch_walks_m<DIM, R, false, false>(L, num_sms, stream);
 }
 
 template <int DIM, typename R>
 int blocks_per_sm_t() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R>, kWalkBlock,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, false, false>, kWalkBlock,
                                                 sizeof(DevProblem<R>));
   return per_sm;
 }

@@ -1,0 +1,109 @@
+"""The path-replay sigma gradient (wos_adjoint_sigma) against the oracle's central
+finite differences with common random numbers: the oracle reruns the same walks
+(same seed and walk ids) with one sigma node moved by +-h; given sigma_bar the
+paths do not move, so the difference quotient has no Monte Carlo noise."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wos():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_13240_gb300 import build as B
+    B.build_lib()
+    import paper_2201_13240_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def setup(wos, orc):
+    sig = W.inverse_sigma_grid()
+    desc = W.inverse_problem(sig)
+    sb = orc.sigma_bar(desc, 48)[0]
+    pts = W.inverse_sensors(12, seed=5)
+    grad_u = np.random.default_rng(6).normal(size=pts.shape[1])
+    return sig, desc, sb, pts, grad_u
+
+
+def oracle_fd(orc, sig, pts, grad_u, node, walks, seed, sb, h):
+    """sum_p grad_u[p] d mean_p / d sigma_node by central differences on the same walks."""
+    vals, nodes = [], []
+    for s in (+1, -1):
+        g = sig.copy().reshape(-1)
+        g[node] += s * h
+        nodes.append(float(g[node]))  # the float32 grid rounds the step: divide by what was applied
+        desc = W.inverse_problem(g.reshape(sig.shape))
+        uh, _ = orc.walks(desc, pts, walks, seed=seed, eps=1e-4, sigma_bar=sb)
+        vals.append((grad_u * uh.mean(axis=1)).sum())
+    return (vals[0] - vals[1]) / (nodes[0] - nodes[1])
+
+
+def pick_nodes(sig, pts, k=6):
+    """Grid nodes next to the first sensors (their gradients are not zero)."""
+    n = sig.shape[0]
+    out = []
+    for i in range(k):
+        x = pts[:, i % pts.shape[1]]
+        ijk = np.clip(np.floor(x * (n - 1)).astype(int), 0, n - 2)
+        out.append(int(ijk[0] + n * (ijk[1] + n * ijk[2])))
+    return out
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32", 5e-2)])
+def test_adjoint_matches_crn_central_differences(wos, orc, setup, precision, rtol):
+    sig, desc, sb, pts, grad_u = setup
+    ctx = wos.Context(0)
+    sig_t = torch.from_numpy(sig).cuda()
+    d = dict(desc)
+    d["sigma"] = dict(desc["sigma"], data=sig_t)
+    prob = ctx.problem(d)
+    walks, seed = 32, 9
+    grad = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+    ctx.adjoint_sigma(prob, torch.from_numpy(pts).cuda(), walks, torch.from_numpy(grad_u).cuda(), grad, 1e-4, sb,
+                      seed=seed, precision=precision)
+    g = grad.cpu().numpy()
+    assert np.isfinite(g).all() and np.abs(g).sum() > 0
+    for node in pick_nodes(sig, pts):
+        fd = oracle_fd(orc, sig, pts, grad_u, node, walks, seed, sb, h=1e-3)
+        scale = max(abs(fd), 1e-3 * np.abs(g).max())
+        assert abs(g[node] - fd) <= rtol * scale, (precision, node, g[node], fd)
+
+
+def test_autograd_function_and_descent(wos, orc, setup):
+    """loss.backward() through SigmaSolve equals the adjoint, and gradient steps on the
+    sigma grid lower an L2 misfit to a target solved with the hidden sigma."""
+    from paper_2201_13240_gb300.autograd import SigmaSolve
+    sig_true, desc, sb, _, _ = setup
+    ctx = wos.Context(0)
+    pts = torch.from_numpy(W.inverse_sensors(256, seed=7)).cuda()
+    t_true = torch.from_numpy(sig_true).cuda()
+    dt = dict(desc)
+    dt["sigma"] = dict(desc["sigma"], data=t_true)
+    acc, _ = ctx.solve(ctx.problem(dt), pts, 4096, 1e-4, sb, seed=100)
+    target = ctx.finalize(acc)[0]
+    sigma = torch.full_like(t_true, 5.0).requires_grad_(True)
+    d = dict(desc)
+    d["sigma"] = dict(desc["sigma"], data=sigma.detach())
+    prob = ctx.problem(d)
+    losses = []
+    for it in range(4):
+        u = SigmaSolve.apply(sigma, ctx, prob, pts, 256, 1e-4, sb, 200 + it)
+        loss = ((u - target) ** 2).sum()
+        sigma.grad = None
+        loss.backward()
+        assert sigma.grad is not None and torch.isfinite(sigma.grad).all()
+        if it == 0:
+            ref = torch.zeros(sigma.numel(), dtype=torch.float64, device="cuda")
+            ctx.adjoint_sigma(prob, pts, 256, (2 * (u - target)).detach(), ref, 1e-4, sb, seed=200)
+            assert torch.allclose(sigma.grad.reshape(-1).double(), ref, rtol=1e-5, atol=1e-9)
+        losses.append(float(loss.detach()))
+        with torch.no_grad():
+            sigma -= 0.5 * sigma.grad / sigma.grad.abs().max()
+            sigma.clamp_(0.0, 20.0)
+    assert losses[-1] < losses[0]

@@ -397,3 +397,97 @@ def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3):
     p = cube3d_problem()
     p["domain"] = mesh_domain(verts, tris)
     return p
+
+
+# ---------------------------------------------------------------------------
+# Inverse problem: recover a 32^3 multilinear sigma grid on the unit cube from
+# the solution at seeded sensors.  alpha: 16^3 cubic B-spline noise in [0.5, 2]
+# (seed 2, fixed); hidden sigma: 32^3 noise in [0, 10] (seed 1); f = 1;
+# g = 1 + x y + z; sensors uniform in [0.05, 0.95]^3.
+# ---------------------------------------------------------------------------
+def inverse_alpha_grid(seed=2):
+    return value_noise_grid(3, 16, 0.5, 2.0, seed, cell=8)
+
+
+def inverse_sigma_grid(seed=1):
+    return value_noise_grid(3, 32, 0.0, 10.0, seed, cell=8)
+
+
+def inverse_problem(sigma_grid, alpha_grid=None):
+    lo, hi = [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]
+    alpha = inverse_alpha_grid() if alpha_grid is None else alpha_grid
+    g = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)), term(1.0, None, None, (LIN, 1.0, 0.0)))
+    return problem(3, box(lo, hi), grid_field("grid_bspline", alpha, lo, hi),
+                   grid_field("grid_linear", sigma_grid, lo, hi), const(1.0), g)
+
+
+def inverse_sensors(n=4096, seed=4):
+    return uniform_in_box(3, n, 0.05, 0.95, seed)
+
+
+# ---------------------------------------------------------------------------
+# Batched uneven solves: independent 2D problems (disks, annuli, rounded boxes,
+# seeded sizes 0.5 - 2), each with its own 64^2 noise grids: alpha in [0.5, 2]
+# (B-spline), sigma in [0, 10] and f in [-1, 1] (multilinear), a drift potential
+# Phi (B-spline) scaled so |omega| = |alpha grad Phi| <= 2 on its grid; g =
+# cos(pi x) y.  Points per problem log-uniform in [16, 4096], walks per point
+# log-uniform in [64, 1024].  The drift is conservative by construction (App. A).
+# ---------------------------------------------------------------------------
+def _inside_2d(dom, x, y, margin=0.0):
+    p = dom["p"]
+    if dom["kind"] == "ball":
+        return np.hypot(x - p[0], y - p[1]) < p[3] - margin
+    if dom["kind"] == "annulus":
+        r = np.hypot(x - p[0], y - p[1])
+        return (r > p[3] + margin) & (r < p[4] - margin)
+    # rounded box: inside when the distance to the inner box is below the corner radius
+    qx = np.abs(x - p[0]) - (p[3] - p[6])
+    qy = np.abs(y - p[1]) - (p[4] - p[6])
+    out = np.hypot(np.maximum(qx, 0), np.maximum(qy, 0)) + np.minimum(np.maximum(qx, qy), 0)
+    return out < p[6] - margin
+
+
+def batch_problems(nprob, seed=7, grid=64, max_points=4096, min_points=16, min_walks=64, max_walks=1024):
+    """(problems, points SoA float32 [2][N], offsets [nprob+1], walks int32 [N])."""
+    rng = np.random.default_rng(seed)
+    probs, pts, offs, walks = [], [], [0], []
+    g = sst(term(1.0, (COS, PI, 0.0), (LIN, 1.0, 0.0)))
+    for i in range(nprob):
+        kind = int(rng.integers(0, 3))
+        c = rng.uniform(-1.0, 1.0, size=2)
+        if kind == 0:
+            r = rng.uniform(0.5, 2.0)
+            dom = ball(c, r)
+            half = np.array([r, r])
+        elif kind == 1:
+            r = rng.uniform(0.5, 2.0)
+            dom = annulus(c, r * rng.uniform(0.3, 0.7), r)
+            half = np.array([r, r])
+        else:
+            half = rng.uniform(0.5, 2.0, size=2)
+            dom = rounded_box(c, half, rng.uniform(0.1, 0.4) * half.min())
+        lo, hi = list(c - half), list(c + half)
+        s = int(rng.integers(0, 2 ** 31))
+        a = value_noise_grid(2, grid, 0.5, 2.0, s, cell=8)
+        sg = value_noise_grid(2, grid, 0.0, 10.0, s + 1, cell=8)
+        f = value_noise_grid(2, grid, -1.0, 1.0, s + 2, cell=8)
+        ph = value_noise_grid(2, grid, -1.0, 1.0, s + 3, cell=8).astype(np.float64)
+        h = (np.array(hi) - np.array(lo)) / (grid - 1)
+        gy, gx = np.gradient(ph, h[1], h[0])
+        wmax = np.max(a * np.hypot(gx, gy))
+        ph = (ph * (2.0 / wmax)).astype(np.float32)
+        probs.append(problem(2, dom, grid_field("grid_bspline", a, lo, hi), grid_field("grid_linear", sg, lo, hi),
+                             grid_field("grid_linear", f, lo, hi), g, phi=grid_field("grid_bspline", ph, lo, hi)))
+        n = int(round(np.exp(rng.uniform(np.log(min_points), np.log(max_points)))))
+        got = []
+        while sum(len(q) for q in got) < n:
+            x = rng.uniform(lo[0], hi[0], size=4 * n)
+            y = rng.uniform(lo[1], hi[1], size=4 * n)
+            m = _inside_2d(dom, x, y, margin=1e-3)
+            got.append(np.stack([x[m], y[m]], 1))
+        q = np.concatenate(got)[:n]
+        pts.append(q)
+        offs.append(offs[-1] + n)
+        walks.append(np.round(np.exp(rng.uniform(np.log(min_walks), np.log(max_walks), size=n))).astype(np.int32))
+    P = np.ascontiguousarray(np.concatenate(pts).T.astype(np.float32))
+    return probs, P, np.array(offs, dtype=np.int64), np.concatenate(walks)
