@@ -321,6 +321,125 @@ def run_ours(args):
     return 0
 
 
+def run_other(args):
+    """Measurements of the other workloads (one GPU): walk-steps/s of each, and for the
+    inverse problem the adjoint (gradient) rate against the forward rate."""
+    import torch
+
+    import paper_2201_13240_gb300 as wos
+
+    ctx = wos.Context(0)
+    wl = args.workload
+    extra = {}
+
+    def timed(fn, reps):
+        fn(0)
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn(i + 1)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return out, sum(ms) / len(ms)
+
+    if wl == "square2d":
+        desc = W.square2d_problem()
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 256)[0]
+        pts_np = W.cell_centres(2, 32)
+        pts = torch.from_numpy(pts_np).cuda()
+        walks = args.walks if args.walks != WALKS else 256
+        (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-3, sb, seed=i), args.steps)
+        m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+        exact = W.square2d_exact(*pts_np.astype(np.float64))
+        extra["normalised_rms"] = float(np.linalg.norm(m - exact) / np.linalg.norm(exact))
+        cfg = {"workload": f"square2d_manufactured: 32^2 points x {walks} walks, eps 1e-3", "sigma_bar": sb}
+        npts = pts_np.shape[1]
+    elif wl == "mesh":
+        desc = W.mesh_noise_problem(level=7)
+        t0 = time.perf_counter()
+        prob = ctx.problem(desc)
+        extra["bvh_build_s"] = time.perf_counter() - t0
+        sb = ctx.sigma_bar(prob, 48)[0]
+        npts = args.points
+        pts = torch.from_numpy(W.mesh_interior_points(npts, seed=0)).cuda()
+        walks = args.walks if args.walks != WALKS else 512
+        (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
+        cfg = {"workload": f"displaced icosphere (327,680 triangles), 128^3 noise grids: {npts} interior points "
+                           f"x {walks} walks, eps 1e-4", "sigma_bar": sb}
+    elif wl == "batch":
+        probs, pts_np, offs, walks_np = W.batch_problems(args.problems, seed=7)
+        t0 = time.perf_counter()
+        hp = [ctx.problem(p) for p in probs]
+        sbs = [ctx.sigma_bar(h, 64)[0] for h in hp]
+        batch = ctx.batch(hp, offs, sbs)
+        extra["setup_s"] = time.perf_counter() - t0
+        pts = torch.from_numpy(pts_np).cuda()
+        wt = torch.from_numpy(walks_np).cuda()
+        acc = ctx.new_accum(pts.shape[1])
+        stt = ctx.new_stats()
+        graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            ctx.solve_batch(batch, pts, wt, 1e-3, seed=0, accum=acc, stats=stt, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            for t in acc:
+                t.zero_()
+            stt.zero_()
+            ctx.solve_batch(batch, pts, wt, 1e-3, seed=0, accum=acc, stats=stt, stream=s)
+
+        def run(i):
+            graph.replay()
+            return acc, stt
+        (acc, st), ms = timed(run, args.steps)
+        npts = pts.shape[1]
+        cfg = {"workload": f"{args.problems} 2D problems (disk/annulus/rounded box, 64^2 noise grids), "
+                           f"{npts} points, {int(walks_np.sum())} walks, one launch in a CUDA graph, eps 1e-3"}
+    elif wl == "inverse":
+        sig = W.inverse_sigma_grid()
+        sig_t = torch.from_numpy(sig).cuda()
+        desc = W.inverse_problem(sig)
+        desc["sigma"] = dict(desc["sigma"], data=sig_t)
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 48)[0]
+        npts = 4096
+        pts = torch.from_numpy(W.inverse_sensors(npts)).cuda()
+        walks = args.walks if args.walks != WALKS else 1024
+        gu = torch.ones(npts, dtype=torch.float64, device="cuda")
+        grad = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+        (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
+
+        def adj(i):
+            grad.zero_()
+            stt = ctx.new_stats()
+            ctx.adjoint_sigma(prob, pts, walks, gu, grad, 1e-4, sb, seed=i, stats=stt)
+            return grad, stt
+        (_, sta), ms_adj = timed(adj, args.steps)
+        extra["adjoint_ms"] = ms_adj
+        extra["forward_solves_per_s"] = 1e3 / ms
+        extra["adjoint_grads_per_s"] = 1e3 / ms_adj
+        extra["adjoint_grads_per_s_over_forward_solves_per_s"] = ms / ms_adj
+        cfg = {"workload": f"inverse sigma: 32^3 multilinear sigma, 16^3 B-spline alpha, {npts} sensors x {walks} "
+                           "walks, eps 1e-4", "sigma_bar": sb}
+    else:
+        raise SystemExit(f"unknown workload {wl}")
+    stv = wos.stats_dict(st)
+    line = {"metric": METRIC, "value": stv["steps"] / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "steps_per_walk": stv["steps"] / max(stv["walks"], 1),
+            "points_per_s": npts / (ms * 1e-3), "walks_per_s": stv["walks"] / (ms * 1e-3),
+            "capped_walks": stv["capped"], "nonfinite_walks": stv["nonfinite"]}
+    line.update(extra)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     global GRID, WALKS
     ap = argparse.ArgumentParser()
@@ -331,10 +450,16 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
     ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
+    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse"],
+                    help="cube3d is the benchmark; the others print supplementary measurements")
+    ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
+    ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     args = ap.parse_args()
     GRID, WALKS = args.grid, args.walks
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "cube3d":
+        return run_other(args)
     return run_ours(args)
 
 

@@ -139,7 +139,18 @@ enum { WOS_FP32 = 0, WOS_FP64 = 1 };
    walk_offset: walk id of the first walk of every point.
    max_steps:  step cap per walk (capped walks are counted, not hidden), >= 1.
    precision:  WOS_FP32 walk state (production) or WOS_FP64 (replays the FP64
-               reference arithmetic on the same random streams). */
+               reference arithmetic on the same random streams).
+   ww_lo, ww_hi, ww_depth: the weight window of Sec. 6 (the paper uses [0.5, 1.5]);
+               ww_lo = 0 turns it off.  After every null event the product W of null
+               weights is windowed: |W| < ww_lo plays Russian roulette (survive with
+               |W|/ww_lo, then |W| = ww_lo); |W| > ww_hi splits the walk into floor(m) or
+               floor(m)+1 copies (mean m = |W|/ww_hi) of weight W/m.  Copies run after
+               the branch that made them, in the same lane, so each walk's estimate is
+               still one sample; at most ww_depth (<= 8) copies wait at a time (m is
+               capped by the free room, which keeps the estimator unbiased).  Copy b of a
+               walk draws its randoms with block word (b << 2) | block; the window's own
+               uniform is block 1 word 2 (3D) or block 1 word 0 (2D).  Only wos_solve and
+               wos_walk_estimates support it. */
 typedef struct {
   double eps;
   double sigma_bar;
@@ -147,7 +158,9 @@ typedef struct {
   uint64_t walk_offset;
   int64_t max_steps;
   int32_t precision;
-  int32_t reserved;
+  int32_t ww_depth;
+  double ww_lo;
+  double ww_hi;
 } wos_params;
 
 typedef struct wos_ctx wos_ctx;

@@ -98,6 +98,13 @@ def _load():
                               C.c_double, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64),
                               C.c_int]
     lib.orc_sigma_bar.argtypes = [pp, C.c_int, dp, dp, dp]
+    lib.orc_walk_ww.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double,
+                                C.c_int64, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int32)]
+    lib.orc_walk_ww.restype = C.c_double
+    lib.orc_solve_ww.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
+                                 C.c_double, C.c_int64, C.c_double, C.c_double, C.c_int, dp, dp,
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]
     lib.orc_mesh_prepare.argtypes = [pp]
     lib.orc_mesh_release.argtypes = [pp]
     lib.orc_mesh_distance_brute.argtypes = [pp, dp, dp]
@@ -341,3 +348,34 @@ def finalize(accum):
     var = (s2 - n * mean * mean) / np.maximum(n - 1, 1)
     var = np.maximum(var, 0.0)
     return mean, var, np.sqrt(var / n)
+
+
+def walk_ww(prob, x0, point, walk_id, seed, eps, sigma_bar, ww_lo, ww_hi, depth=8, max_steps=1 << 20,
+            packed=None):
+    """One walk with the Sec. 6 weight window: (estimate, steps over all branches, flags)."""
+    pk = packed or pack(prob)
+    xx = np.zeros(3)
+    xx[: len(x0)] = x0
+    k = C.c_int64()
+    fl = C.c_int32()
+    u = _load().orc_walk_ww(pk.ptr, _dptr(xx), point, walk_id, seed, eps, sigma_bar, max_steps, ww_lo, ww_hi,
+                            depth, C.byref(k), C.byref(fl))
+    return u, k.value, fl.value
+
+
+def solve_ww(prob, pts, walks, seed, eps, sigma_bar, ww_lo, ww_hi, depth=8, walk_offset=0, max_steps=1 << 20,
+             nthreads=0):
+    lib = _load()
+    pk = pack(prob)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    npts = pts.shape[1]
+    acc = (np.zeros(npts), np.zeros(npts), np.zeros(npts, dtype=np.int64))
+    stats = np.zeros(4, dtype=np.int64)
+    rc = lib.orc_solve_ww(pk.ptr, _dptr(pts), npts, int(walks), walk_offset, seed, eps, sigma_bar, max_steps,
+                          ww_lo, ww_hi, depth, _dptr(acc[0]), _dptr(acc[1]),
+                          acc[2].ctypes.data_as(C.POINTER(C.c_int64)),
+                          stats.ctypes.data_as(C.POINTER(C.c_int64)), nthreads)
+    if rc != 0:
+        raise ValueError("orc_solve_ww rejected its inputs")
+    return acc, {"steps": int(stats[0]), "walks": int(stats[1]), "capped": int(stats[2]),
+                 "nonfinite": int(stats[3])}

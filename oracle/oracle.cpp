@@ -937,6 +937,158 @@ double orc_walk(const orc_problem* P, const double* x0, uint32_t point, uint32_t
   return u;
 }
 
+// Sec. 6 weight window on top of Supplemental Algorithm 1 (see oracle.h for the
+// random-number contract).  Branches of one walk share its estimate: every branch
+// adds its own weighted source terms and boundary value to the walk's sum.
+double orc_walk_ww(const orc_problem* P, const double* x0, uint32_t point, uint32_t walk,
+                   uint64_t seed, double eps, double sb, int64_t max_steps, double ww_lo,
+                   double ww_hi, int depth, int64_t* steps_out, int32_t* flags_out) {
+  int dim = P->dim;
+  struct Branch {
+    double x[3];
+    double W;
+    int64_t k;
+    uint32_t id;
+  };
+  std::vector<Branch> pending;
+  uint32_t next_id = 1;
+  double acc = 0.0;
+  double g0 = gamma_at(P, x0);
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  int64_t steps = 0;
+  int32_t flags = 0;
+  Branch b;
+  for (int d = 0; d < 3; ++d) b.x[d] = (d < dim) ? x0[d] : 0.0;
+  b.W = 1.0;
+  b.k = 0;
+  b.id = 0;
+  for (;;) {
+    // run branch b until it ends
+    for (;;) {
+      double xb[3];
+      double d = distance(P, b.x, xb);
+      if (d < eps) {
+        double gv, gg[3], gl;
+        field_eval(P, &P->g, xb, &gv, gg, &gl);
+        acc += b.W * std::exp(gamma_at(P, b.x)) * gv;
+        break;
+      }
+      if (b.k >= max_steps) {
+        flags |= 1;
+        break;
+      }
+      double R = d;
+      uint32_t blk0 = b.id << 2;
+      uint32_t ctr[4] = {point, walk, (uint32_t)b.k, blk0}, o0[4], o1[4];
+      philox(ctr, key, o0);
+      ctr[3] = blk0 | 1u;
+      philox(ctr, key, o1);
+      double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
+      double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+      double uww;
+      if (dim == 2) {
+        double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
+        dy[0] = std::cos(ty); dy[1] = std::sin(ty);
+        dz[0] = std::cos(tz); dz[1] = std::sin(tz);
+        uww = uniform01(o1[0]);
+      } else {
+        double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
+        double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
+        dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
+        double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
+        double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
+        dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
+        uww = uniform01(o1[2]);
+      }
+      double Gn = green_norm(dim, R, sb);
+      double r = orc_green_inv(dim, R, sb, ur);
+      double y[3] = {0, 0, 0};
+      for (int i = 0; i < dim; ++i) y[i] = b.x[i] + r * dy[i];
+      double gam_y, sp_y, fp_y, f_y, a_y;
+      coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+      acc += b.W * Gn * fp_y;
+      ++steps;
+      ++b.k;
+      if (mu <= sb * Gn) {
+        b.W *= 1.0 - sp_y / sb;
+        for (int i = 0; i < dim; ++i) b.x[i] = y[i];
+        double aw = std::fabs(b.W);
+        if (ww_lo > 0.0 && aw < ww_lo) {
+          if (uww < aw / ww_lo) {
+            b.W = (b.W < 0.0 ? -ww_lo : ww_lo);
+          } else {
+            break;  // the branch ends without a boundary value
+          }
+        } else if (ww_lo > 0.0 && aw > ww_hi) {
+          // expected-value splitting: N copies of weight W/m with E[N] = m, N in
+          // {floor(m), floor(m) + 1}; m is capped by the room for waiting copies
+          // (an integer m then gives exactly m copies, so the split stays unbiased)
+          double m = aw / ww_hi;
+          double room = (double)(depth - (int64_t)pending.size());
+          if (m > room + 1.0) m = room + 1.0;
+          double fl = std::floor(m);
+          int64_t n = (int64_t)fl + ((uww < fl + 1.0 - m) ? 0 : 1);
+          b.W /= m;
+          for (int64_t c = 1; c < n; ++c) {
+            Branch nb = b;
+            nb.id = next_id++;
+            pending.push_back(nb);
+          }
+        }
+      } else {
+        for (int i = 0; i < dim; ++i) b.x[i] = b.x[i] + R * dz[i];
+      }
+    }
+    if (pending.empty()) break;
+    b = pending.back();
+    pending.pop_back();
+  }
+  double u = acc * std::exp(-g0);
+  if (!std::isfinite(u)) flags |= 2;
+  if (steps_out) *steps_out = steps;
+  if (flags_out) *flags_out = flags;
+  return u;
+}
+
+int orc_solve_ww(const orc_problem* P, const double* pts, int64_t npts, int32_t walks_uniform,
+                 uint64_t walk_offset, uint64_t seed, double eps, double sb, int64_t max_steps,
+                 double ww_lo, double ww_hi, int depth, double* sum, double* sumsq, int64_t* count,
+                 int64_t* stats, int nthreads) {
+  if (!(sb > 0.0) || !(eps > 0.0) || !(ww_hi > ww_lo)) return -1;
+  int dim = P->dim;
+  int64_t st_steps = 0, st_walks = 0, st_capped = 0, st_nonfinite = 0;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) \
+    reduction(+ : st_steps, st_walks, st_capped, st_nonfinite)
+  for (int64_t p = 0; p < npts; ++p) {
+    double x0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) x0[d] = pts[d * npts + p];
+    double s1 = 0.0, s2 = 0.0;
+    for (int32_t j = 0; j < walks_uniform; ++j) {
+      int64_t k;
+      int32_t fl;
+      double u = orc_walk_ww(P, x0, (uint32_t)p, (uint32_t)(walk_offset + (uint64_t)j), seed, eps, sb,
+                             max_steps, ww_lo, ww_hi, depth, &k, &fl);
+      s1 += u;
+      s2 += u * u;
+      st_steps += k;
+      st_walks += 1;
+      st_capped += (fl & 1) ? 1 : 0;
+      st_nonfinite += (fl & 2) ? 1 : 0;
+    }
+    sum[p] += s1;
+    sumsq[p] += s2;
+    count[p] += walks_uniform;
+  }
+  if (stats) {
+    stats[0] += st_steps;
+    stats[1] += st_walks;
+    stats[2] += st_capped;
+    stats[3] += st_nonfinite;
+  }
+  return 0;
+}
+
 int orc_solve(const orc_problem* P, const double* pts, int64_t npts, const int32_t* walks,
               int32_t walks_uniform, uint64_t walk_offset, uint64_t seed, double eps, double sb,
               int64_t max_steps, double* sum, double* sumsq, int64_t* count, int64_t* stats,

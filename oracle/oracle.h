@@ -130,6 +130,21 @@ double orc_walk(const orc_problem* prob, const double* x0, uint32_t point, uint3
                 uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
                 int64_t* steps_out, int32_t* flags_out);
 
+/* Weight window (Sec. 6): after every null event, |W| < lo is Russian roulette
+   (survive with |W|/lo, then |W| = lo) and |W| > hi expected-value splitting into
+   floor(m) or floor(m)+1 copies (E = m = |W|/hi) of weight W/m.  Copies continue
+   depth-first within the walk (last created first); copy b draws its randoms with
+   Philox block word (b << 2) | block.  The window's own uniform: 3D block 1 word 2,
+   2D block 1 word 0.  At most `depth` copies wait at a time (fewer splits when full,
+   which stays unbiased).  lo <= 0 disables it. */
+double orc_walk_ww(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk,
+                   uint64_t seed, double eps, double sigma_bar, int64_t max_steps, double ww_lo,
+                   double ww_hi, int depth, int64_t* steps_out, int32_t* flags_out);
+int orc_solve_ww(const orc_problem* prob, const double* pts, int64_t npts, int32_t walks_uniform,
+                 uint64_t walk_offset, uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
+                 double ww_lo, double ww_hi, int depth, double* sum, double* sumsq, int64_t* count,
+                 int64_t* stats, int nthreads);
+
 /* Many walks: pts SoA [dim][npts].  walks[p] (or walks_uniform if walks == NULL)
    walks per point with ids walk_offset .. walk_offset + walks - 1, accumulated
    into sum / sumsq / count (FP64, caller-initialised).  stats: {steps, walks,

@@ -56,7 +56,8 @@ class ProblemDesc(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("sigma_bar", C.c_double), ("seed", C.c_uint64), ("walk_offset", C.c_uint64),
-                ("max_steps", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("max_steps", C.c_int64), ("precision", C.c_int32), ("ww_depth", C.c_int32), ("ww_lo", C.c_double),
+                ("ww_hi", C.c_double)]
 
 
 _lib = None
@@ -115,8 +116,12 @@ def _points(pts, dim, device):
     return pts.contiguous()
 
 
-def params(eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32"):
+def params(eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32", window=None):
+    """window: None, or (lo, hi) or (lo, hi, depth) for the Sec. 6 weight window."""
     p = Params()
+    if window is not None:
+        p.ww_lo, p.ww_hi = float(window[0]), float(window[1])
+        p.ww_depth = int(window[2]) if len(window) > 2 else 8
     p.eps = float(eps)
     p.sigma_bar = float(sigma_bar)
     p.seed = int(seed)
@@ -276,7 +281,7 @@ class Context:
         return torch.zeros(STATS_WORDS, dtype=torch.int64, device=f"cuda:{self.device}")
 
     def solve(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="fp32",
-              accum=None, stats=None, stream=None):
+              accum=None, stats=None, stream=None, window=None):
         """Add walks to the accumulators (sum, sumsq, count); pts: cuda float32 [dim, npts]."""
         import torch
         pts = _points(pts, prob.dim, self.device)
@@ -296,14 +301,14 @@ class Context:
                 raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
             walks = walks.contiguous()
             wp, wu = _ptr(walks), 0
-        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision, window)
         self._check(self.lib.wos_solve(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
                                        _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), _ptr(stats),
                                        _stream(stream)))
         return accum, stats
 
     def walk_estimates(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
-                       precision="fp32", stream=None):
+                       precision="fp32", stream=None, window=None):
         import torch
         pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
@@ -311,7 +316,7 @@ class Context:
         uhat = torch.empty((npts, walks_per_point), dtype=torch.float64, device=dev)
         steps = torch.empty((npts, walks_per_point), dtype=torch.int64, device=dev)
         stats = self.new_stats()
-        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision, window)
         self._check(self.lib.wos_walk_estimates(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
                                                 C.byref(p), _ptr(uhat), _ptr(steps), _ptr(stats), _stream(stream)))
         return uhat, steps, stats

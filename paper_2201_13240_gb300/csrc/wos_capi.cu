@@ -309,6 +309,16 @@ int validate_params(wos_ctx* ctx, const wos_params* prm) {
   if (prm->max_steps < 1) return fail(ctx, WOS_EINVAL, "max_steps must be >= 1");
   if (prm->precision != WOS_FP32 && prm->precision != WOS_FP64)
     return fail(ctx, WOS_EINVAL, "precision must be WOS_FP32 or WOS_FP64");
+  if (prm->ww_lo != 0.0) {
+    if (!finite_pos(prm->ww_lo) || !(std::isfinite(prm->ww_hi) && prm->ww_hi > prm->ww_lo))
+      return fail(ctx, WOS_EINVAL, "weight window needs 0 < ww_lo < ww_hi");
+    if (prm->ww_depth < 1 || prm->ww_depth > 8) return fail(ctx, WOS_EINVAL, "ww_depth must be in 1..8");
+  }
+  return WOS_OK;
+}
+
+int no_window(wos_ctx* ctx, const wos_params* prm) {
+  if (prm && prm->ww_lo != 0.0) return fail(ctx, WOS_EUNSUPPORTED, "this entry point has no weight window");
   return WOS_OK;
 }
 
@@ -345,6 +355,9 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.steps_out = steps;
   L.radial_tab = ctx->radial_tab[prob->dim - 2];
   L.mesh = prob->host64.domain_kind == wos::D_MESH;
+  L.ww_lo = prm->ww_lo;
+  L.ww_hi = prm->ww_hi;
+  L.ww_depth = prm->ww_depth;
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
@@ -704,6 +717,7 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
   if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
   int rc = validate_params(ctx, prm);
   if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
   if (npts < 0 || walks_uniform < 0) return fail(ctx, WOS_EINVAL, "negative size");
   if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
   if (npts == 0 || walks_uniform == 0) return WOS_OK;
@@ -815,6 +829,7 @@ extern "C" int wos_solve_batch(wos_ctx* ctx, const wos_batch* b, const float* pt
   if (!prm) return fail(ctx, WOS_EINVAL, "params is NULL");
   if (!finite_pos(prm->eps) || prm->max_steps < 1 || (prm->precision != WOS_FP32 && prm->precision != WOS_FP64))
     return fail(ctx, WOS_EINVAL, "eps must be > 0, max_steps >= 1, precision FP32 or FP64");
+  if (prm->ww_lo != 0.0) return fail(ctx, WOS_EUNSUPPORTED, "batches have no weight window");
   if (!walks && walks_uniform < 0) return fail(ctx, WOS_EINVAL, "walks_uniform < 0");
   if (b->npts == 0 || (!walks && walks_uniform == 0)) return WOS_OK;
   if (!pts || !sum || !sumsq || !count) return fail(ctx, WOS_EINVAL, "null device array");
@@ -970,6 +985,7 @@ extern "C" int wos_solve_noalloc(const wos_problem_desc* desc, const float* pts,
                                  const int32_t* walks, int32_t walks_uniform, const wos_params* prm,
                                  double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream) {
   if (!desc || !prm) return WOS_EINVAL;
+  if (prm->ww_lo != 0.0) return WOS_EUNSUPPORTED;
   if (!finite_pos(prm->eps) || !finite_pos(prm->sigma_bar) || prm->max_steps < 1 ||
       (prm->precision != WOS_FP32 && prm->precision != WOS_FP64))
     return WOS_EINVAL;

@@ -38,6 +38,9 @@ struct WalkLaunch {
   const int64_t* prob_offsets;    // [nprob + 1], device
   const double* sigma_bars;       // [nprob], device
   int32_t nprob;
+  // weight window (ww_lo > 0 enables it)
+  double ww_lo, ww_hi;
+  int32_t ww_depth;
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

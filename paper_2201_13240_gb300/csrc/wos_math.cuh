@@ -66,9 +66,21 @@ WOS_HD float w_rsqrt(float x) {
 #endif
 }
 WOS_HD double w_rsqrt(double x) { return 1.0 / sqrt(x); }
-WOS_HD float w_sin(float x) { return sinf(x); }
+WOS_HD float w_sin(float x) {
+#if defined(__CUDA_ARCH__)
+  return __sinf(x);
+#else
+  return sinf(x);
+#endif
+}
 WOS_HD double w_sin(double x) { return sin(x); }
-WOS_HD float w_cos(float x) { return cosf(x); }
+WOS_HD float w_cos(float x) {
+#if defined(__CUDA_ARCH__)
+  return __cosf(x);
+#else
+  return cosf(x);
+#endif
+}
 WOS_HD double w_cos(double x) { return cos(x); }
 WOS_HD void w_sincos(float x, float* s, float* c) {
 #if defined(__CUDA_ARCH__)

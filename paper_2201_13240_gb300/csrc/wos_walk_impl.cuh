@@ -42,7 +42,12 @@ struct WalkState {
   uint32_t p, w, k;
   uint32_t prob;  // batched launches: the walk's problem
   uint64_t item;
+  // weight window: current branch id, next id, branch ended by roulette, steps of the walk
+  uint32_t bid, next_bid, steps_walk;
+  bool dead;
 };
+
+constexpr int kWWDepth = 8;  // most split copies a lane keeps waiting
 
 // e^{-gamma(x_0)} of point p, in double (applied once per flush)
 template <int DIM, typename R>
@@ -88,17 +93,25 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, W
   for (int d = 0; d < 3; ++d) s.x[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
   s.W = R(1);
   s.acc = R(0);
+  s.bid = 0;
+  s.next_bid = 1;
+  s.steps_walk = 0;
+  s.dead = false;
 }
 
-// FP32: at most 128 registers, so four 128-thread blocks (16 warps) fit an SM.  Left
-// alone the compiler takes 168 (12 warps); the cap spills ~80 bytes and measured 22%
-// faster on the 3D workload, the extra warps hiding the step's dependency chains.
+// FP32: at most 96 registers, so five 128-thread blocks (20 warps) fit an SM.  Left
+// alone the compiler takes 168 (12 warps).  Measured on the 3D workload: 128 registers
+// (16 warps) 22% faster than 168, 96 registers another 3.5% -- the extra warps hide the
+// step's dependency chains better than the spilled bytes cost.
 // MESH: the domain is a triangle mesh; the walk then keeps its previous closest
 // point to bound the next BVH search (analytic domains carry none of this).
 // BATCHED: the launch walks many problems (each walk's problem description is
 // read from global memory through L1 instead of being staged in shared memory).
-template <int DIM, typename R, bool MESH, bool BATCHED>
-__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk_kernel(WalkLaunch L) {
+// WW: the Sec. 6 weight window (Russian roulette below ww_lo, expected-value
+// splitting above ww_hi); split copies wait on a per-lane stack and run after the
+// branch that made them, so a walk's estimate stays in one lane.
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW>
+__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk_kernel(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
   if (!BATCHED) {
@@ -114,7 +127,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
   const R eps = R(L.eps);
-  R s_root = w_sqrt(R(L.sigma_bar)), inv_sb = R(1) / R(L.sigma_bar);
+  const R s_root0 = w_sqrt(R(L.sigma_bar)), inv_sb0 = R(1) / R(L.sigma_bar);
   const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
 
   // with per-point walk counts the total is the last inclusive prefix sum
@@ -134,6 +147,12 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
   // per-lane statistics: a lane finishes far fewer than 2^32 walks in one launch
   unsigned long long st_steps = 0;
   uint32_t st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
+  // weight window: copies waiting to run (position, weight, step, branch id)
+  R stk_x[WW ? kWWDepth : 1][3], stk_W[WW ? kWWDepth : 1];
+  uint32_t stk_k[WW ? kWWDepth : 1], stk_id[WW ? kWWDepth : 1];
+  int sp = 0;
+  const int ww_depth = WW ? (L.ww_depth < kWWDepth ? L.ww_depth : kWWDepth) : 0;
+  const R ww_lo = R(L.ww_lo), ww_hi = R(L.ww_hi);
 
   for (;;) {
     // ---- regeneration: lanes without a walk claim the next items ----
@@ -164,6 +183,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
     if (__ballot_sync(kFull, active) == 0u) break;
     if (!active) continue;
     const DevProblem<R>& P = BATCHED ? Pall[s.prob] : *Pshared;
+    R s_root = s_root0, inv_sb = inv_sb0;
     if (BATCHED) {
       double sbp = __ldg(&L.sigma_bars[s.prob]);
       s_root = w_sqrt(R(sbp));
@@ -182,17 +202,21 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
 #pragma unroll
       for (int i = 0; i < 3; ++i) s.xbp[i] = xb[i];
     }
-    const bool ends = !(d >= eps) || s.k >= max_k;  // eps-shell (or outside, or NaN), or the step cap
+    // eps-shell (or outside, or NaN), the step cap, or (weight window) a branch lost at roulette
+    const bool ends = !(d >= eps) || s.k >= max_k || (WW && s.dead);
     const R dd = w_fmax(d, R(0));
+    const uint32_t blk0 = WW ? (s.bid << 2) : 0u;  // branch b of a split walk: block word (b << 2) | block
 
-    U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, 0u}, key0, key1);
+    U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, blk0}, key0, key1);
     R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
     R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
+    R uww3 = R(0);  // 3D: the weight window's uniform (block 1 word 2)
     if (DIM == 2) {
       w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
       w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
     } else {
-      U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, 1u}, key0, key1);
+      U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1);
+      uww3 = to_uniform<R>(r1.z);
       R cy = R(1) - R(2) * to_uniform<R>(r0.z);
       R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
       R sp_, cp_;
@@ -216,9 +240,24 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
     coeffs<DIM>(P, y, &spy, &fpy, &gam);
 
     if (ends) {
-      bool capped = (d >= eps);
-      if (!capped) s.acc += s.W * w_exp(gam) * g_at<DIM>(P, xb);   // Alg. 1: g at the closest point
+      const bool lost = WW && s.dead;
+      bool capped = (d >= eps) && !lost;
+      if (!capped && !lost) s.acc += s.W * w_exp(gam) * g_at<DIM>(P, xb);   // Alg. 1: g at the closest point
       if (s.k == 0 && !(d > R(0))) ++st_outside;
+      if (WW) {
+        if (capped) ++st_capped;
+        if (sp > 0) {  // the walk goes on with its last split copy
+          --sp;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) s.x[i] = stk_x[sp][i];
+          s.W = stk_W[sp];
+          s.k = stk_k[sp];
+          s.bid = stk_id[sp];
+          s.dead = false;
+          continue;
+        }
+        capped = false;  // already counted per branch
+      }
       double acc_d = (double)s.acc;
       if (accumulate && s.p != acc_p) {
         if (acc_p != kNoPoint) {
@@ -238,9 +277,9 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
       ++n_acc;
       if (L.uhat != nullptr) {
         L.uhat[s.item] = acc_d * point_factor<DIM, R>(L, P, s.p);
-        L.steps_out[s.item] = (int64_t)s.k;
+        L.steps_out[s.item] = WW ? (int64_t)s.steps_walk : (int64_t)s.k;
       }
-      st_steps += s.k;
+      if (!WW) st_steps += s.k;
       ++st_walks;
       if (capped) ++st_capped;
       if (!isfinite(acc_d)) ++st_nonfinite;
@@ -249,10 +288,39 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
     }
 
     s.acc += s.W * Gn * fpy;   // source term, every step
+    if (WW) {
+      ++st_steps;
+      ++s.steps_walk;
+    }
     if (mu <= PB) {            // volume term: null event at y
       s.W *= R(1) - spy * inv_sb;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) s.x[i] = y[i];
+      if (WW) {
+        R aw = w_fabs(s.W);
+        if (aw < ww_lo || aw > ww_hi) {
+          R uww = (DIM == 3) ? uww3 : to_uniform<R>(philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1).x);
+          if (aw < ww_lo) {  // Russian roulette: survive with |W| / lo, at weight lo
+            if (uww < aw / ww_lo) s.W = (s.W < R(0)) ? -ww_lo : ww_lo;
+            else s.dead = true;
+          } else {           // expected-value splitting into floor(m) or floor(m)+1 copies of W/m
+            R m = aw / ww_hi;
+            R room = R(ww_depth - sp);
+            if (m > room + R(1)) m = room + R(1);
+            R fl = floor(m);
+            int n = (int)fl + ((uww < fl + R(1) - m) ? 0 : 1);
+            s.W = s.W / m;
+            for (int c = 1; c < n; ++c) {
+#pragma unroll
+              for (int i = 0; i < 3; ++i) stk_x[sp][i] = s.x[i];
+              stk_W[sp] = s.W;
+              stk_k[sp] = s.k + 1;
+              stk_id[sp] = s.next_bid++;
+              ++sp;
+            }
+          }
+        }
+      }
     } else {                   // boundary term: uniform point on the sphere
 #pragma unroll
       for (int i = 0; i < DIM; ++i) s.x[i] = s.x[i] + dd * dz[i];
@@ -284,33 +352,37 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 4 : 1) wos_walk
   }
 }
 
-template <int DIM, typename R, bool MESH, bool BATCHED>
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED>,
-                                                                kWalkBlock, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW>, kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
   uint64_t warps_needed = (L.total_items + 31) / 32;
   uint64_t blocks_needed = (warps_needed + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R, MESH, BATCHED><<<grid, kWalkBlock, smem, stream>>>(L);
+  wos_walk_kernel<DIM, R, MESH, BATCHED, WW><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
-  if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true>(L, num_sms, stream);
-  if (DIM == 3 && L.mesh) return launch_walks_m<DIM, R, true, false>(L, num_sms, stream);
-  return launch_walks_m<DIM, R, false, false>(L, num_sms, stream);
+  if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true, false>(L, num_sms, stream);
+  const bool ww = L.ww_lo > 0.0;
+  if (DIM == 3 && L.mesh)
+    return ww ? launch_walks_m<DIM, R, true, false, true>(L, num_sms, stream)
+              : launch_walks_m<DIM, R, true, false, false>(L, num_sms, stream);
+  return ww ? launch_walks_m<DIM, R, false, false, true>(L, num_sms, stream)
+            : launch_walks_m<DIM, R, false, false, false>(L, num_sms, stream);
 }
 
 template <int DIM, typename R>
 int blocks_per_sm_t() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, false, false>, kWalkBlock,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, false, false, false>, kWalkBlock,
                                                 sizeof(DevProblem<R>));
   return per_sm;
 }

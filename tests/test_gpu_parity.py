@@ -263,3 +263,34 @@ def test_mesh_noise_workload_sampled_points(orc, ctx):
     exact = W.cube3d_exact(*pts.astype(np.float64))
     ok, nout, mz = four_se_rule((m - exact) / se)
     assert ok, (nout, mz)
+
+
+@pytest.mark.parametrize("name", ["square2d", "cube3d", "hifreq"])
+def test_weight_window_fp64_replay_and_fp32_parity(orc, ctx, name):
+    if name == "hifreq":
+        desc, pts, eps = W.hifreq_alpha_problem(), W.cell_centres(2, 8)[:, ::3], 1e-3
+    else:
+        mk, ptsf, eps = REPLAY_CASES[name]
+        desc, pts = mk(), ptsf()[:, :24]
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 64 if desc["dim"] == 3 else 128)[0]
+    win = (0.5, 1.5, 8)
+    uh, st, _ = ctx.walk_estimates(prob, dev(pts), 8, eps, sb, seed=17, precision="fp64", window=win)
+    uh = uh.cpu().numpy()
+    st = st.cpu().numpy()
+    pk = orc.pack(desc)
+    ok, steps_ok, n = 0, 0, 0
+    for i in range(pts.shape[1]):
+        for j in range(8):
+            u, k, _ = orc.walk_ww(desc, pts[:, i].astype(np.float64), i, j, 17, eps, sb, 0.5, 1.5, 8, packed=pk)
+            ok += abs(uh[i, j] - u) <= 1e-9 * max(1.0, abs(u))
+            steps_ok += st[i, j] == k
+            n += 1
+    assert ok >= 0.99 * n and steps_ok >= 0.99 * n, (ok, steps_ok, n)
+    m, se, s, _ = (lambda a: (ctx.finalize(a[0])[0].cpu().numpy(), ctx.finalize(a[0])[2].cpu().numpy(),
+                              [int(v) for v in a[1].cpu().tolist()], a[0]))(
+        ctx.solve(prob, dev(pts), 2048, eps, sb, seed=18, window=win))
+    oacc, _ = orc.solve_ww(desc, pts, 2048, seed=19, eps=eps, sigma_bar=sb, ww_lo=0.5, ww_hi=1.5)
+    om, ov, ose = orc.finalize(oacc)
+    good, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert good, (nout, mz)

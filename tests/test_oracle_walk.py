@@ -96,3 +96,44 @@ def test_step_cap_is_reported(orc):
     _, st = orc.solve(prob, pts, 50, seed=0, eps=1e-3, sigma_bar=sb, max_steps=2)
     assert st["capped"] > 0
     assert st["steps"] <= 2 * st["walks"]
+
+
+# ---------------------------------------------------------------------------
+# weight window (Sec. 6)
+# ---------------------------------------------------------------------------
+def test_window_off_equals_plain_walk(orc):
+    prob = W.cube3d_problem()
+    sb = orc.sigma_bar(prob)[0]
+    x = W.cell_centres(3, 64)[:, 1234].astype(np.float64)
+    for j in range(20):
+        u0, k0, _ = orc.walk(prob, x, 7, j, 5, 1e-4, sb)
+        u1, k1, _ = orc.walk_ww(prob, x, 7, j, 5, 1e-4, sb, 0.0, 1.0)
+        assert u0 == u1 and k0 == k1
+
+
+@pytest.mark.parametrize("depth", [8, 1])
+def test_window_unbiased_exact_solution(orc, depth):
+    prob = W.hifreq_alpha_problem()
+    sb = orc.sigma_bar(prob)[0]
+    pts = W.cell_centres(2, 8)[:, ::5]
+    acc, st = orc.solve_ww(prob, pts, 1500, seed=3, eps=1e-3, sigma_bar=sb, ww_lo=0.5, ww_hi=1.5, depth=depth)
+    m, v, se = orc.finalize(acc)
+    ok, _, _ = four_se_rule((m - W.hifreq_alpha_exact(*pts.astype(np.float64))) / se)
+    assert ok
+    assert st["capped"] == 0 and st["nonfinite"] == 0
+
+
+def test_window_reduces_variance_high_frequency_alpha(orc):
+    """Sec. 6 (weight-window figure): with a high-frequency alpha the plain estimator's
+    error is dominated by rare walks of huge weight; the window cuts the mean squared
+    error against the exact solution (here more than 3x) at fewer steps per walk."""
+    prob = W.hifreq_alpha_problem()
+    sb = orc.sigma_bar(prob)[0]
+    pts = W.cell_centres(2, 8)
+    exact = W.hifreq_alpha_exact(*pts.astype(np.float64))
+    a0, s0 = orc.solve(prob, pts, 1500, seed=5, eps=1e-3, sigma_bar=sb)
+    a1, s1 = orc.solve_ww(prob, pts, 1500, seed=5, eps=1e-3, sigma_bar=sb, ww_lo=0.5, ww_hi=1.5)
+    mse0 = np.mean((orc.finalize(a0)[0] - exact) ** 2)
+    mse1 = np.mean((orc.finalize(a1)[0] - exact) ** 2)
+    assert mse1 < mse0 / 3
+    assert s1["steps"] / s1["walks"] < s0["steps"] / s0["walks"]

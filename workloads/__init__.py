@@ -491,3 +491,16 @@ def batch_problems(nprob, seed=7, grid=64, max_points=4096, min_points=16, min_w
         walks.append(np.round(np.exp(rng.uniform(np.log(min_walks), np.log(max_walks), size=n))).astype(np.int32))
     P = np.ascontiguousarray(np.concatenate(pts).T.astype(np.float32))
     return probs, P, np.array(offs, dtype=np.int64), np.concatenate(walks)
+
+
+def hifreq_alpha_problem(freq=6.0, amp=0.8):
+    """div(alpha grad u) = -f on the unit square with a high-frequency diffusion
+    coefficient alpha = 1 + amp sin(freq pi x) sin(freq pi y), u = sin(pi x) sinh(y) / sinh(1) + 1
+    (the setting of the paper's weight-window experiment, Sec. 6)."""
+    u = sst(term(1.0), term(1.0 / math.sinh(1.0), (SIN, PI, 0.0), (SINH, 1.0, 0.0)))
+    alpha = sst(term(1.0), term(amp, (SIN, freq * PI, 0.0), (SIN, freq * PI, 0.0)))
+    return problem(2, box([0, 0], [1, 1]), alpha, zero(), manufactured(), u, um=u)
+
+
+def hifreq_alpha_exact(x, y):
+    return np.sin(np.pi * x) * np.sinh(y) / np.sinh(1.0) + 1.0
