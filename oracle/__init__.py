@@ -105,6 +105,12 @@ def _load():
     lib.orc_solve_ww.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
                                  C.c_double, C.c_int64, C.c_double, C.c_double, C.c_int, dp, dp,
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]
+    lib.orc_green_grad_ratios.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp]
+    lib.orc_walk_grad.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double,
+                                  C.c_int64, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.orc_walk_grad.restype = C.c_double
+    lib.orc_walks_grad.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
+                                   C.c_int64, dp, dp, C.POINTER(C.c_int64), C.c_int]
     lib.orc_mesh_prepare.argtypes = [pp]
     lib.orc_mesh_release.argtypes = [pp]
     lib.orc_mesh_distance_brute.argtypes = [pp, dp, dp]
@@ -379,3 +385,47 @@ def solve_ww(prob, pts, walks, seed, eps, sigma_bar, ww_lo, ww_hi, depth=8, walk
         raise ValueError("orc_solve_ww rejected its inputs")
     return acc, {"steps": int(stats[0]), "walks": int(stats[1]), "capped": int(stats[2]),
                  "nonfinite": int(stats[3])}
+
+
+def green_grad_ratios(dim, R, sb, r):
+    """(|grad_x G| / G at distance r, |grad_x P| / P) at the ball centre (Supplemental 1.3)."""
+    o = (C.c_double * 2)()
+    _load().orc_green_grad_ratios(dim, R, sb, r, o)
+    return o[0], o[1]
+
+
+def walk_grad(prob, x0, point, walk_id, seed, eps, sigma_bar, max_steps=1 << 20, packed=None):
+    """(u estimate, grad u estimate, steps, flags) of one walk (Supplemental Sec. 2)."""
+    pk = packed or pack(prob)
+    xx = np.zeros(3)
+    xx[: len(x0)] = x0
+    g = np.zeros(3)
+    k = C.c_int64()
+    fl = C.c_int32()
+    u = _load().orc_walk_grad(pk.ptr, _dptr(xx), point, walk_id, seed, eps, sigma_bar, max_steps, _dptr(g),
+                              C.byref(k), C.byref(fl))
+    return u, g[: prob["dim"]].copy(), k.value, fl.value
+
+
+def walks_grad(prob, pts, walks_per_point, seed, eps, sigma_bar, walk_offset=0, max_steps=1 << 20, nthreads=0):
+    """Per-walk u [npts, walks], grad u [dim, npts, walks] and step counts."""
+    lib = _load()
+    pk = pack(prob)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    dim, npts = pts.shape
+    uh = np.zeros((npts, walks_per_point))
+    gh = np.zeros((dim, npts, walks_per_point))
+    st = np.zeros((npts, walks_per_point), dtype=np.int64)
+    rc = lib.orc_walks_grad(pk.ptr, _dptr(pts), npts, walks_per_point, walk_offset, seed, eps, sigma_bar,
+                            max_steps, _dptr(uh), _dptr(gh), st.ctypes.data_as(C.POINTER(C.c_int64)), nthreads)
+    if rc != 0:
+        raise ValueError("orc_walks_grad rejected its inputs")
+    return uh, gh, st
+
+
+def solve_grad(prob, pts, walks, seed, eps, sigma_bar, walk_offset=0):
+    """Per point: mean u, its standard error, mean grad u [npts, dim] and their standard errors."""
+    uh, gh, _ = walks_grad(prob, pts, walks, seed, eps, sigma_bar, walk_offset)
+    n = float(walks)
+    gs = np.moveaxis(gh, 0, -1)  # [npts, walks, dim]
+    return (uh.mean(1), uh.std(1, ddof=1) / np.sqrt(n), gs.mean(1), gs.std(1, ddof=1) / np.sqrt(n))

@@ -937,6 +937,51 @@ double orc_walk(const orc_problem* P, const double* x0, uint32_t point, uint32_t
   return u;
 }
 
+// cosh z - sinh z / z; below z = 1 by its Taylor series sum_{n>=1} 2n z^{2n} / (2n+1)!,
+// where the two terms of the closed form cancel.
+double cosh_m_sinhc(double z) {
+  if (z >= 1.0) return std::cosh(z) - std::sinh(z) / z;
+  double z2 = z * z, term = z2 / 3.0, acc = term;
+  for (int n = 1; n < 30 && term > 1e-18 * acc; ++n) {
+    term *= z2 / ((2.0 * n) * (2.0 * n + 3.0));
+    acc += term;
+  }
+  return acc;
+}
+
+// Supplemental 1.3: grad_x G and grad_x P at the centre, as printed, over G and P.
+void grad_ratios(int dim, double R, double sb, double r, double* gG, double* gP) {
+  double s = std::sqrt(sb), a = s * R, t = s * r;
+  if (dim == 2) {
+    if (sb == 0.0) {
+      // harmonic: G = ln(R/r)/(2 pi), grad_x G = (y - x)(1/r^2 - 1/R^2)/(2 pi), P = 1/(2 pi R)
+      *gG = (1.0 / (r * r) - 1.0 / (R * R)) * r / std::log(R / r);
+      *gP = 2.0 / R;
+      return;
+    }
+    double G = bK0(t) - bK0(a) / bI0(a) * bI0(t);                     // 2 pi G
+    double dG = s / r * (bK1(t) - bK1(a) / bI1(a) * bI1(t));          // 2 pi |grad G| / |y - x|
+    *gG = dG * r / G;
+    double P = 1.0 / (R * bI0(a));                                     // 2 pi P
+    double dP = sb / R * (1.0 / (a * bI1(a)));                        // 2 pi |grad P| / |z - x|
+    *gP = dP * R / P;
+    return;
+  }
+  if (sb == 0.0) {
+    *gG = (1.0 / (r * r * r) - 1.0 / (R * R * R)) * r / (1.0 / r - 1.0 / R);
+    *gP = 3.0 / R;
+    return;
+  }
+  double G = std::exp(-t) / r - std::exp(-a) / R * (std::sinh(t) / t) * (a / std::sinh(a));   // 4 pi G
+  double br = std::exp(-t) * (1.0 + 1.0 / t) -
+              cosh_m_sinhc(t) * (std::exp(-a) * (1.0 + 1.0 / a)) / cosh_m_sinhc(a);
+  double dG = s / (r * r) * br;                                       // 4 pi |grad G| / |y - x|
+  *gG = dG * r / G;
+  double P = (a / std::sinh(a)) / (R * R);                            // 4 pi P
+  double dP = sb / (R * R) / cosh_m_sinhc(a);                          // 4 pi |grad P| / |z - x|
+  *gP = dP * R / P;
+}
+
 // Sec. 6 weight window on top of Supplemental Algorithm 1 (see oracle.h for the
 // random-number contract).  Branches of one walk share its estimate: every branch
 // adds its own weighted source terms and boundary value to the walk's sum.
@@ -1089,6 +1134,98 @@ int orc_solve_ww(const orc_problem* P, const double* pts, int64_t npts, int32_t 
   return 0;
 }
 
+void orc_green_grad_ratios(int dim, double R, double sb, double r, double out[2]) {
+  grad_ratios(dim, R, sb, r, &out[0], &out[1]);
+}
+
+// Supplemental Sec. 2 with the delta-tracking walk: the walk of orc_walk, plus the
+// first ball's gradient weights.
+double orc_walk_grad(const orc_problem* P, const double* x0, uint32_t point, uint32_t walk,
+                     uint64_t seed, double eps, double sb, int64_t max_steps, double* grad_out,
+                     int64_t* steps_out, int32_t* flags_out) {
+  int dim = P->dim;
+  double x[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) x[d] = x0[d];
+  double W = 1.0, acc = 0.0, S0 = 0.0;
+  double gradG[3] = {0, 0, 0}, gradB[3] = {0, 0, 0};
+  double g0 = gamma_at(P, x);
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  int64_t k = 0;
+  int32_t flags = 0;
+  for (;;) {
+    double xb[3];
+    double d = distance(P, x, xb);
+    if (d < eps) {
+      double gv, gg[3], gl;
+      field_eval(P, &P->g, xb, &gv, gg, &gl);
+      acc += W * std::exp(gamma_at(P, x)) * gv;
+      break;
+    }
+    if (k >= max_steps) {
+      flags |= 1;
+      break;
+    }
+    double R = d;
+    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4], o1[4];
+    philox(ctr, key, o0);
+    double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
+    double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+    if (dim == 2) {
+      double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
+      dy[0] = std::cos(ty); dy[1] = std::sin(ty);
+      dz[0] = std::cos(tz); dz[1] = std::sin(tz);
+    } else {
+      ctr[3] = 1u;
+      philox(ctr, key, o1);
+      double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
+      double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
+      dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
+      double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
+      double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
+      dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
+    }
+    double Gn = green_norm(dim, R, sb);
+    double r = orc_green_inv(dim, R, sb, ur);
+    double y[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) y[i] = x[i] + r * dy[i];
+    double gam_y, sp_y, fp_y, f_y, a_y;
+    coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+    acc += W * Gn * fp_y;
+    bool null_event = mu <= sb * Gn;
+    if (k == 0) {
+      double gG, gP;
+      grad_ratios(dim, R, sb, r, &gG, &gP);
+      S0 = Gn * fp_y;
+      for (int i = 0; i < dim; ++i) {
+        gradG[i] = gG * dy[i];
+        gradB[i] = null_event ? gG * dy[i] : gP * dz[i];
+      }
+    }
+    if (null_event) {
+      W *= 1.0 - sp_y / sb;
+      for (int i = 0; i < dim; ++i) x[i] = y[i];
+    } else {
+      for (int i = 0; i < dim; ++i) x[i] = x[i] + R * dz[i];
+    }
+    ++k;
+  }
+  double e0 = std::exp(-g0);
+  double u = acc * e0;
+  // grad gamma(x0) = (grad alpha / alpha + grad Phi) / 2
+  double av, ga[3], la, pv, gp[3], lp;
+  field_eval(P, &P->alpha, x0, &av, ga, &la);
+  field_eval(P, &P->phi, x0, &pv, gp, &lp);
+  for (int i = 0; i < dim; ++i) {
+    double gU = S0 * gradG[i] + (acc - S0) * gradB[i];
+    double ggam = 0.5 * (ga[i] / av + gp[i]);
+    grad_out[i] = (k == 0) ? NAN : e0 * (gU - acc * ggam);
+  }
+  if (!std::isfinite(u)) flags |= 2;
+  if (steps_out) *steps_out = k;
+  if (flags_out) *flags_out = flags;
+  return u;
+}
+
 int orc_solve(const orc_problem* P, const double* pts, int64_t npts, const int32_t* walks,
               int32_t walks_uniform, uint64_t walk_offset, uint64_t seed, double eps, double sb,
               int64_t max_steps, double* sum, double* sumsq, int64_t* count, int64_t* stats,
@@ -1126,6 +1263,30 @@ int orc_solve(const orc_problem* P, const double* pts, int64_t npts, const int32
     stats[1] += st_walks;
     stats[2] += st_capped;
     stats[3] += st_nonfinite;
+  }
+  return 0;
+}
+
+int orc_walks_grad(const orc_problem* P, const double* pts, int64_t npts, int32_t wpp,
+                   uint64_t walk_offset, uint64_t seed, double eps, double sb, int64_t max_steps,
+                   double* u, double* grad, int64_t* steps, int nthreads) {
+  if (!(sb > 0.0) || !(eps > 0.0)) return -1;
+  int dim = P->dim;
+  int64_t n = npts * (int64_t)wpp;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int64_t p = 0; p < npts; ++p) {
+    double x0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) x0[d] = pts[d * npts + p];
+    for (int32_t j = 0; j < wpp; ++j) {
+      int64_t k;
+      int32_t fl;
+      double g[3];
+      int64_t i = p * wpp + j;
+      u[i] = orc_walk_grad(P, x0, (uint32_t)p, (uint32_t)(walk_offset + j), seed, eps, sb, max_steps, g, &k, &fl);
+      for (int d = 0; d < dim; ++d) grad[d * n + i] = g[d];
+      steps[i] = k;
+    }
   }
   return 0;
 }

@@ -145,6 +145,26 @@ int orc_solve_ww(const orc_problem* prob, const double* pts, int64_t npts, int32
                  double ww_lo, double ww_hi, int depth, double* sum, double* sumsq, int64_t* count,
                  int64_t* stats, int nthreads);
 
+/* Gradient of the Green's function and Poisson kernel at the centre of the ball
+   (Supplemental 1.3, as printed), divided by the centred G(r) resp. P:
+   out[0] = |grad_x G| / G at distance r (the gradient points along y - x),
+   out[1] = |grad_x P| / P (along z - x). */
+void orc_green_grad_ratios(int dim, double R, double sigma_bar, double r, double out[2]);
+
+/* One walk estimating u(x0) and grad u(x0) (Supplemental Sec. 2): the first ball's
+   source sample and branch give grad U(x0) = S0 gG(y0) + (A - S0) g_branch, with
+   gG = grad_x G / G (y - x direction) and g_branch = gG on a null event or
+   grad_x P / P on a boundary step; grad u = e^{-gamma(x0)} (grad U - U grad gamma(x0)).
+   grad_out[dim]; NaN if x0 lies within eps of the boundary. */
+double orc_walk_grad(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk,
+                     uint64_t seed, double eps, double sigma_bar, int64_t max_steps, double* grad_out,
+                     int64_t* steps_out, int32_t* flags_out);
+
+/* Many gradient walks: u[npts * wpp], grad[dim][npts * wpp] (SoA), steps[npts * wpp]. */
+int orc_walks_grad(const orc_problem* prob, const double* pts, int64_t npts, int32_t wpp,
+                   uint64_t walk_offset, uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
+                   double* u, double* grad, int64_t* steps, int nthreads);
+
 /* Many walks: pts SoA [dim][npts].  walks[p] (or walks_uniform if walks == NULL)
    walks per point with ids walk_offset .. walk_offset + walks - 1, accumulated
    into sum / sumsq / count (FP64, caller-initialised).  stats: {steps, walks,

@@ -125,6 +125,11 @@ def square2d_exact(x, y):
     return np.sin(np.pi * x) * np.cosh(y)
 
 
+def square2d_exact_grad(x, y):
+    """grad u of square2d_exact, shape [2, ...]."""
+    return np.array([np.pi * np.cos(np.pi * x) * np.cosh(y), np.sin(np.pi * x) * np.sinh(y)])
+
+
 SQUARE2D = {"name": "square2d_manufactured", "eps": 1e-3, "grid": 32, "walks": 256,
             "seed": 0}
 
@@ -153,6 +158,14 @@ def cube3d_exact(x, y, z):
     return np.exp(0.5 * x) * np.sin(np.pi * y) * np.cos(np.pi * z)
 
 
+def cube3d_exact_grad(x, y, z):
+    """grad u of cube3d_exact, shape [3, ...]."""
+    e = np.exp(0.5 * x)
+    return np.array([0.5 * e * np.sin(np.pi * y) * np.cos(np.pi * z),
+                     np.pi * e * np.cos(np.pi * y) * np.cos(np.pi * z),
+                     -np.pi * e * np.sin(np.pi * y) * np.sin(np.pi * z)])
+
+
 CUBE3D = {"name": "cube3d_drift_manufactured", "eps": 1e-4, "grid": 64, "walks": 1024,
           "seed": 0}
 
@@ -171,6 +184,10 @@ def laplace_disk_exact(x, y):
     return x * x - y * y
 
 
+def laplace_disk_exact_grad(x, y):
+    return np.array([2.0 * x, -2.0 * y])
+
+
 def laplace_ball_problem():
     """Delta u = 0 on the unit ball, u = x y z + x^2 - z^2."""
     u = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)),
@@ -180,6 +197,10 @@ def laplace_ball_problem():
 
 def laplace_ball_exact(x, y, z):
     return x * y * z + x * x - z * z
+
+
+def laplace_ball_exact_grad(x, y, z):
+    return np.array([y * z + 2.0 * x, x * z, x * y - 2.0 * z])
 
 
 def screened_square_problem(sig=4.0):
@@ -201,6 +222,11 @@ def screened_ball_problem(sig=9.0):
 
 def screened_ball_exact(sig, x, y, z):
     return np.cosh(np.sqrt(sig) * x)
+
+
+def screened_ball_exact_grad(sig, x, y, z):
+    s = np.sqrt(sig)
+    return np.array([s * np.sinh(s * x), 0.0 * y, 0.0 * z])
 
 
 # ---------------------------------------------------------------------------
@@ -504,3 +530,8 @@ def hifreq_alpha_problem(freq=6.0, amp=0.8):
 
 def hifreq_alpha_exact(x, y):
     return np.sin(np.pi * x) * np.sinh(y) / np.sinh(1.0) + 1.0
+
+
+def hifreq_alpha_exact_grad(x, y):
+    k = 1.0 / np.sinh(1.0)
+    return np.array([np.pi * np.cos(np.pi * x) * np.sinh(y) * k, np.sin(np.pi * x) * np.cosh(y) * k])
