@@ -358,6 +358,22 @@ def run_other(args):
         extra["normalised_rms"] = float(np.linalg.norm(m - exact) / np.linalg.norm(exact))
         cfg = {"workload": f"square2d_manufactured: 32^2 points x {walks} walks, eps 1e-3", "sigma_bar": sb}
         npts = pts_np.shape[1]
+    elif wl == "grad":
+        desc = W.cube3d_problem()
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 64)[0]
+        pts_np = W.cell_centres(3, GRID)
+        pts = torch.from_numpy(pts_np).cuda()
+        npts = pts_np.shape[1]
+        (acc, gacc, st), ms = timed(lambda i: ctx.solve_grad(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        (acc0, st0), ms0 = timed(lambda i: ctx.solve(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        gm, gv, gse = (t.cpu().numpy() for t in ctx.finalize_grad(gacc, acc[2]))
+        exact = W.cube3d_exact_grad(*pts_np.astype(np.float64))
+        extra["grad_normalised_rms"] = float(np.linalg.norm(gm - exact) / np.linalg.norm(exact))
+        extra["value_only_ms"] = ms0
+        extra["grad_over_value_time"] = ms / ms0
+        cfg = {"workload": f"cube3d_drift_manufactured with grad u (Supplemental Sec. 2): {GRID}^3 points x "
+                           f"{WALKS} walks, eps 1e-4", "sigma_bar": sb}
     elif wl == "mesh":
         desc = W.mesh_noise_problem(level=7)
         t0 = time.perf_counter()
@@ -450,7 +466,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
     ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
-    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse"],
+    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad"],
                     help="cube3d is the benchmark; the others print supplementary measurements")
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")

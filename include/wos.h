@@ -212,6 +212,31 @@ int wos_walk_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, 
                        int32_t walks_per_point, const wos_params* params, double* uhat,
                        int64_t* steps, uint64_t* stats, void* stream);
 
+/* Spatial gradient (Supplemental Sec. 2, with the centre gradients of G and P of
+   Supplemental 1.3): as wos_solve, and also ADD every walk's estimate of grad u at
+   its point to grad_sum / grad_sumsq, device double SoA [dim][npts] (component d of
+   point p at d * npts + p; zero them to start; the count is `count`).  A walk weights
+   its first ball's source sample by grad_x G / G at y_0, and the rest of its estimate
+   by grad_x G / G (null event) or grad_x P / P at z_0 (boundary step); then
+   grad u = e^{-gamma(x_0)} (grad U - U grad gamma(x_0)) with gamma = (ln alpha + Phi)/2.
+   The value estimate is the one wos_solve returns for the same arguments (same walks).
+   A point within eps of the boundary has no first ball: its gradient sums are NaN.
+   wos_finalize(grad_sum + d * npts, grad_sumsq + d * npts, count, ...) gives
+   component d.  Errors: as wos_solve; WOS_EUNSUPPORTED with a weight window. */
+int wos_solve_grad(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                   const int32_t* walks, int32_t walks_uniform, const wos_params* params,
+                   double* sum, double* sumsq, int64_t* count, double* grad_sum, double* grad_sumsq,
+                   uint64_t* stats, void* stream);
+
+/* As wos_walk_estimates, also writing every walk's gradient estimate to grad_hat,
+   device double SoA [dim][npts * walks_per_point] (component d of walk
+   p * walks_per_point + j at d * npts * walks_per_point + p * walks_per_point + j).
+   For tests and custom estimators.  Errors: as wos_walk_estimates; WOS_EUNSUPPORTED
+   with a weight window. */
+int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                            int32_t walks_per_point, const wos_params* params, double* uhat,
+                            double* grad_hat, int64_t* steps, uint64_t* stats, void* stream);
+
 /* Per-point mean, unbiased sample variance of one walk's estimate, and standard
    error of the mean from the accumulators (Sec. 2.2: the estimate is the average
    of single-sample estimates).  All device arrays of npts; any output may be NULL. */

@@ -83,6 +83,8 @@ def load():
     lib.wos_solve.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_walk_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.wos_solve_grad.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
+    lib.wos_walk_grad_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_adjoint_sigma.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_batch_create.argtypes = [vp, C.POINTER(vp), i32, vp, vp, C.POINTER(vp)]
@@ -320,6 +322,63 @@ class Context:
         self._check(self.lib.wos_walk_estimates(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
                                                 C.byref(p), _ptr(uhat), _ptr(steps), _ptr(stats), _stream(stream)))
         return uhat, steps, stats
+
+    def solve_grad(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
+                   precision="fp32", accum=None, grad_accum=None, stats=None, stream=None):
+        """Add walks' estimates of u and grad u (Supplemental Sec. 2).  Returns (accum, grad_accum,
+        stats) with grad_accum = (sum, sumsq) of shape [dim, npts] float64; finalize_grad reads them."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        if accum is None:
+            accum = self.new_accum(npts)
+        if grad_accum is None:
+            dev = f"cuda:{self.device}"
+            grad_accum = tuple(torch.zeros((prob.dim, npts), dtype=torch.float64, device=dev) for _ in range(2))
+        if not all(t.is_cuda and t.is_contiguous() and t.dtype == torch.float64 and t.shape == (prob.dim, npts)
+                   for t in grad_accum):
+            raise TypeError("gradient accumulators must be contiguous CUDA float64 tensors of shape [dim, npts]")
+        if not (accum[0].dtype == torch.float64 and accum[1].dtype == torch.float64 and accum[2].dtype == torch.int64
+                and all(t.is_cuda and t.is_contiguous() and t.shape == (npts,) for t in accum)):
+            raise TypeError("accumulators must be contiguous CUDA (float64, float64, int64) tensors of length npts")
+        if stats is None:
+            stats = self.new_stats()
+        if isinstance(walks, int):
+            wp, wu = None, walks
+        else:
+            if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                    and walks.shape == (npts,)):
+                raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+            walks = walks.contiguous()
+            wp, wu = _ptr(walks), 0
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_grad(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
+                                            _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), _ptr(grad_accum[0]),
+                                            _ptr(grad_accum[1]), _ptr(stats), _stream(stream)))
+        return accum, grad_accum, stats
+
+    def finalize_grad(self, grad_accum, count, stream=None):
+        """Per-component mean, variance and standard error [dim, npts] of the gradient estimate."""
+        outs = [self.finalize((grad_accum[0][d], grad_accum[1][d], count), stream) for d in range(grad_accum[0].shape[0])]
+        import torch
+        return tuple(torch.stack([o[k] for o in outs]) for k in range(3))
+
+    def walk_grad_estimates(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0,
+                            max_steps=1 << 20, precision="fp32", stream=None):
+        """Per-walk (u, grad u [dim, npts, walks], steps, stats)."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        dev = f"cuda:{self.device}"
+        uhat = torch.empty((npts, walks_per_point), dtype=torch.float64, device=dev)
+        ghat = torch.empty((prob.dim, npts, walks_per_point), dtype=torch.float64, device=dev)
+        steps = torch.empty((npts, walks_per_point), dtype=torch.int64, device=dev)
+        stats = self.new_stats()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_walk_grad_estimates(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
+                                                     C.byref(p), _ptr(uhat), _ptr(ghat), _ptr(steps), _ptr(stats),
+                                                     _stream(stream)))
+        return uhat, ghat, steps, stats
 
     def finalize(self, accum, stream=None):
         import torch

@@ -324,7 +324,8 @@ int no_window(wos_ctx* ctx, const wos_params* prm) {
 
 int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, const int64_t* walk_end,
            int64_t walks_uniform, uint64_t total, const wos_params* prm, double* sum, double* sumsq,
-           int64_t* count, uint64_t* stats, double* uhat, int64_t* steps, cudaStream_t st) {
+           int64_t* count, uint64_t* stats, double* uhat, int64_t* steps, cudaStream_t st,
+           double* gsum = nullptr, double* gsumsq = nullptr, double* ghat = nullptr) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
   unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
@@ -358,6 +359,9 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.ww_lo = prm->ww_lo;
   L.ww_hi = prm->ww_hi;
   L.ww_depth = prm->ww_depth;
+  L.gsum = gsum;
+  L.gsumsq = gsumsq;
+  L.ghat = ghat;
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
@@ -624,6 +628,56 @@ int wos_solve(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npt
   }
   return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
                 nullptr, st);
+}
+
+int wos_solve_grad(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, const int32_t* walks,
+                   int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq, int64_t* count,
+                   double* grad_sum, double* grad_sumsq, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
+  if (npts < 0) return fail(ctx, WOS_EINVAL, "npts < 0");
+  if (npts == 0) return WOS_OK;
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
+  if (!pts || !sum || !sumsq || !count || !grad_sum || !grad_sumsq)
+    return fail(ctx, WOS_EINVAL, "null device array");
+  if (!walks && walks_uniform < 0) return fail(ctx, WOS_EINVAL, "walks_uniform < 0");
+  if (!walks && walks_uniform == 0) return WOS_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t* walk_end = nullptr;
+  uint64_t total;
+  if (walks) {
+    rc = grow(ctx, &ctx->walk_end, npts, &ctx->walk_end_cap, npts);
+    if (rc) return rc;
+    walk_prefix_kernel<<<1, 1024, 0, st>>>(walks, npts, ctx->walk_end);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "walk prefix kernel");
+    walk_end = ctx->walk_end;
+    total = ~0ull;
+  } else {
+    total = (uint64_t)npts * (uint64_t)walks_uniform;
+  }
+  return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
+                nullptr, st, grad_sum, grad_sumsq, nullptr);
+}
+
+int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,
+                            const wos_params* prm, double* uhat, double* grad_hat, int64_t* steps, uint64_t* stats,
+                            void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
+  if (npts < 0 || wpp < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts == 0 || wpp == 0) return WOS_OK;
+  if (!pts || !uhat || !steps || !grad_hat) return fail(ctx, WOS_EINVAL, "null device array");
+  DeviceGuard g(ctx->device);
+  return launch(ctx, pr, pts, npts, nullptr, wpp, (uint64_t)npts * (uint64_t)wpp, prm, nullptr, nullptr,
+                nullptr, stats, uhat, steps, static_cast<cudaStream_t>(stream), nullptr, nullptr, grad_hat);
 }
 
 int wos_walk_estimates(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,

@@ -121,4 +121,23 @@ void wos_hc_sample_f32(int dim, int use_table, double a, const double* u, int64_
   }
 }
 
+// gradient ratios at the ball centre, scaled by R: out[2i] = R gG, out[2i+1] = R gP
+void wos_hc_grad_ratios(int dim, int fp64, double a, const double* rho, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) {
+      double g, p;
+      if (dim == 2) wos::grad_ratios<2, double>(a, rho[i], &g, &p);
+      else wos::grad_ratios<3, double>(a, rho[i], &g, &p);
+      out[2 * i] = g;
+      out[2 * i + 1] = p;
+    } else {
+      float g, p;
+      if (dim == 2) wos::grad_ratios<2, float>((float)a, (float)rho[i], &g, &p);
+      else wos::grad_ratios<3, float>((float)a, (float)rho[i], &g, &p);
+      out[2 * i] = g;
+      out[2 * i + 1] = p;
+    }
+  }
+}
+
 }  // extern "C"

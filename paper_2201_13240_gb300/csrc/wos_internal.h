@@ -41,6 +41,10 @@ struct WalkLaunch {
   // weight window (ww_lo > 0 enables it)
   double ww_lo, ww_hi;
   int32_t ww_depth;
+  // spatial gradient (Supplemental Sec. 2): either pointer non-null enables it
+  double* gsum;                   // SoA [dim][npts], accumulated
+  double* gsumsq;                 // SoA [dim][npts], accumulated
+  double* ghat;                   // optional per-walk gradients SoA [dim][total_items]
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

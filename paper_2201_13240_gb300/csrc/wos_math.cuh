@@ -117,6 +117,8 @@ WOS_HD void w_sincospi2(double u, double* s, double* c) {
   *c = cos(6.283185307179586476925 * u);
 #endif
 }
+WOS_HD float w_expm1(float x) { return expm1f(x); }
+WOS_HD double w_expm1(double x) { return expm1(x); }
 WOS_HD float w_asin(float x) { return asinf(x); }
 WOS_HD double w_asin(double x) { return asin(x); }
 WOS_HD float w_fabs(float x) { return fabsf(x); }
@@ -373,6 +375,109 @@ WOS_HD double green_q2(double a) {
 template <int DIM, typename R>
 WOS_HD R green_q(R a) {
   return DIM == 2 ? green_q2(a) : green_q3(a);
+}
+
+// ---------------------------------------------------------------------------
+// Exponentially scaled I0, I1, K0, K1 at one argument:
+//   i0s = e^{-x} I0(x), i1s = e^{-x} I1(x), k0s = e^{x} K0(x), k1s = e^{x} K1(x).
+// ---------------------------------------------------------------------------
+WOS_HD void bessel_scaled(float x, float* i0s, float* i1s, float* k0s, float* k1s) {
+  float ex = w_exp(-x);
+  if (x < 3.75f) {
+    *i0s = as_i0_small(x) * ex;
+    *i1s = as_i1_small(x) * ex;
+  } else {
+    *i0s = as_i0s_large(x);
+    *i1s = as_i1s_large(x);
+  }
+  if (x <= 2.0f) {
+    float lt = w_log(0.5f * x);
+    float k0 = as_k0_poly(x) - lt * as_i0_small(x);
+    float k1 = (1.0f + as_k1_poly(x) + x * lt * as_i1_small(x)) / x;
+    *k0s = k0 / ex;
+    *k1s = k1 / ex;
+  } else {
+    *k0s = as_k0s_large(x);
+    *k1s = as_k1s_large(x);
+  }
+}
+WOS_HD void bessel_scaled(double x, double* i0s, double* i1s, double* k0s, double* k1s) {
+  *i0s = d_i0s(x);
+  *i1s = d_i1s(x);
+  if (x <= 2.0) {
+    double ex = exp(x);
+    *k0s = d_k0_small(x) * ex;
+    *k1s = (1.0 - d_1m_xk1_small(x)) / x * ex;
+  } else {
+    *k0s = trap_ks(0, x);
+    *k1s = trap_ks(1, x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradients at the centre of the ball (Supplemental 1.3) as ratios to the centred
+// densities:  grad_x G(x, y) = gG G(x, y) (y - x)/r,  grad_x P(x, z) = gP P(x, z) (z - x)/R.
+// Returned scaled by the radius, gGR = R gG and gPR = R gP, for a = sqrt(sb) R and
+// rho = r/R (t = a rho).  Supplemental Sec. 2 weights the first ball's samples by them.
+// 3D, with c(z) = cosh z - sinh z/z and kk(z) = e^{-z}(1 + 1/z), the printed
+// expressions give
+//   4 pi G = sinh(a - t)/(r sinh a),     4 pi |grad G| = (s/r)(kk(t) - c(t) kk(a)/c(a)),
+//   4 pi R^2 P = a/sinh a,               4 pi R^2 |grad P| = s a/c(a),
+// so gPR = a sinh(a)/c(a) and gGR = gPR (kk(t) c(a) - c(t) kk(a))/sinh(a - t), written
+// below with e^{-z}-scaled c^ = e^{-z} c, s^ = e^{-z} sinh (no overflow at large a):
+//   gGR = gPR [(1 + 1/t) c^(a) - e^{-2(a-t)} c^(t)(1 + 1/a)] / s^(a - t).
+// c(z) is summed as its series sum_{n>=1} 2n z^{2n}/(2n+1)! below z = 1/2, where
+// cosh z - sinh z/z cancels.  2D, from the printed K1/I1 forms:
+//   gPR = a I0(a)/I1(a),
+//   gGR = a [K1(t) - K1(a) I1(t)/I1(a)] / [K0(t) - K0(a) I0(t)/I0(a)].
+// For a -> 0 (Laplace ball) they tend to gPR = DIM and gGR = (1 + rho + rho^2)/rho (3D),
+// (1/rho - rho)/ln(1/rho) (2D); used below a = 1e-4.
+// ---------------------------------------------------------------------------
+template <typename R>
+WOS_HD R grad_chat(R z) {  // e^{-z} (cosh z - sinh z / z)
+  if (z < R(0.5)) {
+    R z2 = z * z, term = z2 * R(1.0 / 3.0), acc = term;
+#pragma unroll
+    for (int n = 1; n < 8; ++n) {
+      term *= z2 / R((2 * n) * (2 * n + 3));
+      acc += term;
+    }
+    return acc * w_exp(-z);
+  }
+  R e2 = w_exp(R(-2) * z);
+  return R(0.5) * (R(1) + e2) - R(0.5) * (R(1) - e2) / z;
+}
+
+template <int DIM, typename R>
+WOS_HD void grad_ratios(R a, R rho, R* gGR, R* gPR) {
+  if (DIM == 3) {
+    if (a < R(1e-4)) {
+      *gPR = R(3);
+      *gGR = (R(1) + rho + rho * rho) / rho;
+      return;
+    }
+    R t = a * rho;
+    R ca = grad_chat(a), ct = grad_chat(t);
+    R sa = R(-0.5) * w_expm1(R(-2) * a);
+    R sat = R(-0.5) * w_expm1(R(-2) * (a - t));
+    R gp = a * sa / ca;
+    R num = (R(1) + R(1) / t) * ca - w_exp(R(-2) * (a - t)) * ct * (R(1) + R(1) / a);
+    *gPR = gp;
+    *gGR = gp * num / sat;
+    return;
+  }
+  if (a < R(1e-4)) {
+    *gPR = R(2);
+    *gGR = (R(1) / rho - rho) / (-w_log(rho));
+    return;
+  }
+  R t = a * rho;
+  R i0a, i1a, k0a, k1a, i0t, i1t, k0t, k1t;
+  bessel_scaled(a, &i0a, &i1a, &k0a, &k1a);
+  bessel_scaled(t, &i0t, &i1t, &k0t, &k1t);
+  R e = w_exp(R(-2) * (a - t));
+  *gPR = a * i0a / i1a;
+  *gGR = a * (k1t - k1a * i1t / i1a * e) / (k0t - k0a * i0t / i0a * e);
 }
 
 // ---------------------------------------------------------------------------

@@ -316,6 +316,17 @@ WOS_HD R gamma_at(const DevProblem<R>& P, const R* x) {
   return R(0.5) * w_log(a) + R(0.5) * ph;
 }
 
+// grad gamma = (grad alpha / alpha + grad Phi) / 2 (Sec. 4.1, App. A)
+template <int DIM, typename R>
+WOS_HD void grad_gamma_at(const DevProblem<R>& P, const R* x, R* g) {
+  FieldVal<R> A = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], true);
+  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, x[0], x[1], x[2], true);
+  R ia = R(1) / A.v;
+  g[0] = R(0.5) * (A.gx * ia + Ph.gx);
+  g[1] = R(0.5) * (A.gy * ia + Ph.gy);
+  g[2] = R(0.5) * (A.gz * ia + Ph.gz);
+}
+
 template <int DIM, typename R>
 WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
   return field_eval<DIM>(P, P.g, x[0], x[1], x[2], false).v;

@@ -45,6 +45,8 @@ struct WalkState {
   // weight window: current branch id, next id, branch ended by roulette, steps of the walk
   uint32_t bid, next_bid, steps_walk;
   bool dead;
+  // spatial gradient: grad U of the walk = acc * gb + gc, set on the first step
+  R gb[3], gc[3];
 };
 
 constexpr int kWWDepth = 8;  // most split copies a lane keeps waiting
@@ -110,8 +112,15 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, W
 // WW: the Sec. 6 weight window (Russian roulette below ww_lo, expected-value
 // splitting above ww_hi); split copies wait on a per-lane stack and run after the
 // branch that made them, so a walk's estimate stays in one lane.
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW>
-__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk_kernel(WalkLaunch L) {
+// GRAD: also estimate grad u at the walk's start (Supplemental Sec. 2).  The first
+// ball weights its source sample by grad G / G at y_0 and the rest of the walk by
+// grad G / G (null event) or grad P / P at z_0 (boundary step): with S_0 the first
+// source term and A the walk's total, grad U = S_0 gG + (A - S_0) gB = A gB + gc.
+// Then grad u = e^{-gamma(x_0)} (grad U - U grad gamma(x_0)); e^{-gamma(x_0)} joins
+// the flush like the value's, grad gamma(x_0) is cached per lane and point.  The
+// extra FP64 partial sums take registers, so this variant runs 16 warps per SM.
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD>
+__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) : 1) wos_walk_kernel(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
   if (!BATCHED) {
@@ -144,6 +153,10 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
   uint32_t acc_p = kNoPoint, acc_prob = 0;
   double s1 = 0.0, s2 = 0.0;
   uint32_t n_acc = 0;
+  // spatial gradient: per-lane partial sums of (grad U - U grad gamma) and grad gamma(x_0)
+  double gs1[3] = {0.0, 0.0, 0.0}, gs2[3] = {0.0, 0.0, 0.0};
+  R ggam[3] = {R(0), R(0), R(0)};
+  uint32_t gg_p = kNoPoint;
   // per-lane statistics: a lane finishes far fewer than 2^32 walks in one launch
   unsigned long long st_steps = 0;
   uint32_t st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
@@ -231,7 +244,8 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
     R q = green_q<DIM, R>(a);
     R Gn = dd * dd * q;        // |G| on the ball of radius d
     R PB = a * a * q;          // sigma_bar |G|, probability of the volume term
-    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * dd;
+    R rho = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr);
+    R r = rho * dd;
     // coefficient point: y for a step; the walk's own point when it ends (gamma(x_n))
     R y[3];
 #pragma unroll
@@ -259,12 +273,34 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
         capped = false;  // already counted per branch
       }
       double acc_d = (double)s.acc;
+      R gv[3] = {R(0), R(0), R(0)};
+      if (GRAD) {
+        if (s.p != gg_p) {
+          gg_p = s.p;
+          R x0[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) x0[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)s.p])) : R(0);
+          grad_gamma_at<DIM>(P, x0, ggam);
+        }
+        // a walk that ends on its first step (start in the eps-shell) has no first ball
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) gv[i] = (s.k == 0) ? R(NAN) : s.acc * (s.gb[i] - ggam[i]) + s.gc[i];
+      }
       if (accumulate && s.p != acc_p) {
         if (acc_p != kNoPoint) {
           double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
           atomicAdd(&L.sum[acc_p], s1 * e0);
           atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
           atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+          if (GRAD) {
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+              atomicAdd(&L.gsum[(int64_t)i * L.npts + acc_p], gs1[i] * e0);
+              atomicAdd(&L.gsumsq[(int64_t)i * L.npts + acc_p], gs2[i] * e0 * e0);
+              gs1[i] = 0.0;
+              gs2[i] = 0.0;
+            }
+          }
         }
         acc_p = s.p;
         acc_prob = s.prob;
@@ -275,9 +311,21 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
       s1 += acc_d;
       s2 += acc_d * acc_d;
       ++n_acc;
+      if (GRAD) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          gs1[i] += (double)gv[i];
+          gs2[i] += (double)gv[i] * (double)gv[i];
+        }
+      }
       if (L.uhat != nullptr) {
-        L.uhat[s.item] = acc_d * point_factor<DIM, R>(L, P, s.p);
+        double e0 = point_factor<DIM, R>(L, P, s.p);
+        L.uhat[s.item] = acc_d * e0;
         L.steps_out[s.item] = WW ? (int64_t)s.steps_walk : (int64_t)s.k;
+        if (GRAD && L.ghat != nullptr) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) L.ghat[(uint64_t)i * L.total_items + s.item] = (double)gv[i] * e0;
+        }
       }
       if (!WW) st_steps += s.k;
       ++st_walks;
@@ -288,6 +336,19 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
     }
 
     s.acc += s.W * Gn * fpy;   // source term, every step
+    if (GRAD && s.k == 0) {    // first ball: gradient weights (W = 1 here)
+      R gGR, gPR;
+      grad_ratios<DIM, R>(a, rho, &gGR, &gPR);
+      const R inv_d = R(1) / dd, S0 = Gn * fpy;
+      const bool nul = mu <= PB;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        R vg = gGR * inv_d * dy[i];
+        R vb = nul ? vg : gPR * inv_d * dz[i];
+        s.gb[i] = vb;
+        s.gc[i] = S0 * (vg - vb);
+      }
+    }
     if (WW) {
       ++st_steps;
       ++s.steps_walk;
@@ -333,6 +394,13 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
     atomicAdd(&L.sum[acc_p], s1 * e0);
     atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
     atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+    if (GRAD) {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        atomicAdd(&L.gsum[(int64_t)i * L.npts + acc_p], gs1[i] * e0);
+        atomicAdd(&L.gsumsq[(int64_t)i * L.npts + acc_p], gs2[i] * e0 * e0);
+      }
+    }
   }
   // warp-reduce the statistics, one atomic per warp and word
 #pragma unroll
@@ -352,25 +420,28 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? 5 : 1) wos_walk
   }
 }
 
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW>
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW>, kWalkBlock, smem);
+      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD>, kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
   uint64_t warps_needed = (L.total_items + 31) / 32;
   uint64_t blocks_needed = (warps_needed + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R, MESH, BATCHED, WW><<<grid, kWalkBlock, smem, stream>>>(L);
+  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true, false>(L, num_sms, stream);
+  if (L.gsum != nullptr || L.ghat != nullptr)  // spatial gradient (no weight window)
+    return (DIM == 3 && L.mesh) ? launch_walks_m<DIM, R, true, false, false, true>(L, num_sms, stream)
+                                : launch_walks_m<DIM, R, false, false, false, true>(L, num_sms, stream);
   const bool ww = L.ww_lo > 0.0;
   if (DIM == 3 && L.mesh)
     return ww ? launch_walks_m<DIM, R, true, false, true>(L, num_sms, stream)
@@ -382,7 +453,7 @@ cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream
 template <int DIM, typename R>
 int blocks_per_sm_t() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, false, false, false>, kWalkBlock,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_walk_kernel<DIM, R, false, false, false, false>, kWalkBlock,
                                                 sizeof(DevProblem<R>));
   return per_sm;
 }

@@ -1,0 +1,132 @@
+"""GPU parity of the spatial-gradient walks (Supplemental Sec. 2) with the FP64 oracle.
+
+* FP64 replay: per walk, the kernel's u and grad u estimates equal the oracle's on
+  the same Philox streams (>= 99% of walks; grad to 1e-8 of the walk's scale).
+* FP32: per-point and per-component agreement with the oracle within 4 combined
+  standard errors, and with the exact gradient of the manufactured solution on
+  sampled points of the full 64^3 grid at 1024 walks per point.
+* The value estimate of wos_solve_grad matches wos_solve's (same walks).
+* Edge cases: a point in the epsilon shell has a NaN gradient; weight windows are
+  rejected; an empty call is a no-op.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.stats_util import combined_z, four_se_rule
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wos():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_13240_gb300 import build as B
+    B.build_lib()
+    import paper_2201_13240_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(wos):
+    return wos.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+CASES = {
+    "square2d": (W.square2d_problem, lambda: W.cell_centres(2, 32)[:, W.seeded_subset(1024, 48, 1)], 1e-3),
+    "cube3d": (W.cube3d_problem, lambda: W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 48, 2)], 1e-4),
+    "laplace_ball": (W.laplace_ball_problem, lambda: W.uniform_in_ball(3, 48, [0, 0, 0], 1.0, 4, 0.02), 1e-4),
+    "hifreq": (W.hifreq_alpha_problem, lambda: W.cell_centres(2, 16)[:, W.seeded_subset(256, 48, 8)], 1e-3),
+    "mesh": (lambda: W.mesh_manufactured_problem(level=5), lambda: W.mesh_interior_points(32, 7), 1e-4),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_replay_gradient_per_walk(orc, ctx, name):
+    mk, ptsf, eps = CASES[name]
+    desc = mk()
+    pts = ptsf()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 64 if desc["dim"] == 3 else 128)[0]
+    wpp = 16
+    uh, gh, st, stats = ctx.walk_grad_estimates(prob, dev(pts), wpp, eps, sb, seed=5, precision="fp64")
+    uo, go, so = orc.walks_grad(desc, pts, wpp, seed=5, eps=eps, sigma_bar=sb)
+    uh, gh, st = uh.cpu().numpy(), gh.cpu().numpy(), st.cpu().numpy()
+    ok_u = np.abs(uh - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
+    scale = np.maximum(1.0, np.sqrt(np.sum(go ** 2, axis=0)))  # per walk
+    ok_g = np.all(np.abs(gh - go) <= 1e-8 * scale[None], axis=0)
+    assert ok_u.mean() >= 0.99, (name, ok_u.mean())
+    assert (ok_u & ok_g).mean() >= 0.99, (name, ok_g.mean(), np.nanmax(np.abs(gh - go) / scale[None]))
+    assert (st == so).mean() >= 0.99
+
+
+@pytest.mark.parametrize("name", ["square2d", "cube3d", "hifreq", "mesh"])
+def test_fp32_gradient_parity_with_oracle(orc, ctx, name):
+    mk, ptsf, eps = CASES[name]
+    desc = mk()
+    pts = ptsf()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc, 64 if desc["dim"] == 3 else 128)[0]
+    walks = 4096
+    acc, gacc, stats = ctx.solve_grad(prob, dev(pts), walks, eps, sb, seed=1)
+    gm, gv, gse = (t.cpu().numpy() for t in ctx.finalize_grad(gacc, acc[2]))
+    om, ose, og, ogse = orc.solve_grad(desc, pts, walks, seed=2, eps=eps, sigma_bar=sb)
+    z = combined_z(gm.T.ravel(), gse.T.ravel(), og.ravel(), ogse.ravel())
+    ok, nout, mz = four_se_rule(z)
+    assert ok, (name, nout, mz)
+    m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (name, nout, mz)
+
+
+def test_fp32_gradient_full_grid_sampled_exact(ctx, orc):
+    """The 64^3 x 1024-walk workload through wos_solve_grad; sampled points against the exact
+    gradient of the manufactured solution."""
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)
+    sb = orc.sigma_bar(desc, 64)[0]
+    prob = ctx.problem(desc)
+    acc, gacc, stats = ctx.solve_grad(prob, dev(pts), 1024, 1e-4, sb, seed=0)
+    gm, gv, gse = (t.cpu().numpy() for t in ctx.finalize_grad(gacc, acc[2]))
+    idx = W.seeded_subset(64 ** 3, 4096, 12)
+    p = pts[:, idx].astype(np.float64)
+    want = W.cube3d_exact_grad(*p)
+    z = ((gm[:, idx] - want) / gse[:, idx]).ravel()
+    ok, nout, mz = four_se_rule(z)
+    assert ok, (nout, mz)
+    s = [int(x) for x in stats.cpu().tolist()]
+    assert s[1] == 64 ** 3 * 1024 and s[2] == 0 and s[3] == 0
+    # the same walks' value estimate as wos_solve
+    acc2, _ = ctx.solve(prob, dev(pts), 1024, 1e-4, sb, seed=0)
+    m1 = ctx.finalize(acc)[0].cpu().numpy()
+    m2 = ctx.finalize(acc2)[0].cpu().numpy()
+    assert np.allclose(m1, m2, rtol=1e-4, atol=1e-5)
+
+
+def test_gradient_edge_cases(ctx, orc, wos):
+    desc = W.square2d_problem()
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc)[0]
+    pts = np.array([[0.5, 0.5], [0.5, 1e-4]], dtype=np.float32)  # point 1 = (0.5, 1e-4) is in the shell
+    acc, gacc, _ = ctx.solve_grad(prob, dev(pts), 64, 1e-3, sb, seed=0)
+    gm = ctx.finalize_grad(gacc, acc[2])[0].cpu().numpy()
+    assert np.all(np.isfinite(gm[:, 0])) and np.all(np.isnan(gm[:, 1]))
+    # a weight window is rejected (WOS_EUNSUPPORTED) before any launch
+    import ctypes as C
+    p = wos.params(1e-3, sb, window=(0.5, 1.5, 4))
+    g = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    a = ctx.new_accum(2)
+    pd = dev(pts)
+    rc = ctx.lib.wos_solve_grad(ctx.handle, prob.handle, pd.data_ptr(), 2, None, 8, C.byref(p), a[0].data_ptr(),
+                                a[1].data_ptr(), a[2].data_ptr(), g[0].data_ptr(), g[1].data_ptr(), None, None)
+    assert rc == wos.WOS_EUNSUPPORTED
+    empty = torch.zeros((2, 0), dtype=torch.float32, device="cuda")
+    acc, gacc, st = ctx.solve_grad(prob, empty, 64, 1e-3, sb)
+    assert gacc[0].numel() == 0

@@ -112,3 +112,19 @@ def test_table_started_sampler(hc, orc, dim):
         assert np.max(np.abs(Fo - u[:400])) < 2e-6, a
         if a < 32:
             assert it.reshape(-1, 32).max(axis=1).mean() <= 3.5, a
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_centre_gradient_ratios(hc, orc, dim, fp64):
+    """The kernels' grad G / G and grad P / P at the ball centre (Supplemental 1.3) against the
+    oracle's printed forms, from the Laplace limit to large a.  FP32 cancels where G -> 0 at
+    the sphere, so rho is kept at or below 0.9 for the tight bound."""
+    R = 0.37
+    rho = np.array([1e-4, 0.01, 0.1, 0.3, 0.5, 0.7, 0.9])
+    tol = 1e-10 if fp64 else 1e-5
+    for a in (0.0, 1e-5, 1e-3, 0.05, 0.3, 0.49, 0.51, 1.0, 1.9, 2.1, 3.0, 3.8, 10.0, 40.0, 150.0):
+        out = np.zeros(2 * len(rho))
+        hc.wos_hc_grad_ratios(dim, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), out.ctypes.data_as(DP))
+        want = np.array([orc.green_grad_ratios(dim, R, (a / R) ** 2, r * R) for r in rho]) * R
+        assert np.allclose(out.reshape(-1, 2), want, rtol=tol, atol=0), (a, out.reshape(-1, 2), want)
