@@ -294,3 +294,19 @@ def test_weight_window_fp64_replay_and_fp32_parity(orc, ctx, name):
     om, ov, ose = orc.finalize(oacc)
     good, nout, mz = four_se_rule(combined_z(m, se, om, ose))
     assert good, (nout, mz)
+
+
+def test_fp32_matches_finite_difference_solve(ctx, orc):
+    """No closed-form solution: FP32 walks at 2^16 per point against a second-order
+    finite-difference solve of eq. 1 (N = 256) on 15^2 grid nodes."""
+    from tests.fd_reference import fd_reference_at
+    desc = W.fd_square_problem()
+    g = np.arange(1, 16) / 16.0
+    pts = np.array(np.meshgrid(g, g, indexing="ij")).reshape(2, -1)
+    want = fd_reference_at(W.fd_square_coefficients(), pts, n=256)
+    sb = orc.sigma_bar(desc)[0]
+    prob = ctx.problem(desc)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 1 << 16, 1e-4, sb, seed=3)
+    ok, nout, mz = four_se_rule((m - want) / se)
+    assert ok, (nout, mz)
+    assert normalised_rms(m, want) <= 1e-2

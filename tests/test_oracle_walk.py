@@ -137,3 +137,28 @@ def test_window_reduces_variance_high_frequency_alpha(orc):
     mse1 = np.mean((orc.finalize(a1)[0] - exact) ** 2)
     assert mse1 < mse0 / 3
     assert s1["steps"] / s1["walks"] < s0["steps"] / s0["walks"]
+
+
+# ---------------------------------------------------------------------------
+# a problem without a closed-form solution: fine finite-difference reference
+# ---------------------------------------------------------------------------
+def test_walk_matches_finite_difference_solve(orc):
+    """Variable alpha, conservative drift, variable sigma, a source and non-harmonic g on the
+    unit square (eq. 1): the walk's mean agrees with a second-order finite-difference solve
+    (N = 256, discretisation error ~1e-5, far below the standard errors)."""
+    from tests.fd_reference import fd_reference_at
+    prob = W.fd_square_problem()
+    c = W.fd_square_coefficients()
+    # the numpy coefficients are the problem's (checked at a few points)
+    for x in np.random.default_rng(0).uniform(0, 1, size=(5, 2)):
+        assert np.isclose(orc.field_eval(prob, "alpha", x)[0], c["alpha"](*x), rtol=1e-12)
+        assert np.allclose(orc.field_eval(prob, "phi", x)[1], c["grad_phi"](*x), rtol=1e-12)
+        assert np.isclose(orc.field_eval(prob, "sigma", x)[0], c["sigma"](*x), rtol=1e-12)
+        assert np.isclose(orc.field_eval(prob, "f", x)[0], c["f"](*x), rtol=1e-12)
+        assert np.isclose(orc.field_eval(prob, "g", x)[0], c["g"](*x), rtol=1e-12)
+    g = np.array([0.125, 0.375, 0.625, 0.875])
+    pts = np.array(np.meshgrid(g, g, indexing="ij")).reshape(2, -1)
+    want = fd_reference_at(c, pts, n=256)
+    m, se, st = _run(orc, prob, pts, 6000, 1e-4)
+    ok, nout, mz = four_se_rule((m - want) / se)
+    assert ok, ((m - want) / se)

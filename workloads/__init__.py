@@ -519,6 +519,31 @@ def batch_problems(nprob, seed=7, grid=64, max_points=4096, min_points=16, min_w
     return probs, P, np.array(offs, dtype=np.int64), np.concatenate(walks)
 
 
+def fd_square_problem():
+    """A unit-square problem with closed-form coefficients and no closed-form solution:
+    alpha = 1 + 0.5 sin(2 pi x) cos(2 pi y), omega = alpha grad(Phi) with Phi = 0.5 x y,
+    sigma = 2 + sin(3x + y), f = 1 + x, g = x^2 + y (reference: a fine finite-difference
+    solve)."""
+    alpha = sst(term(1.0), term(0.5, (SIN, 2 * PI, 0.0), (COS, 2 * PI, 0.0)))
+    phi = sst(term(0.5, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)))
+    sigma = sst(term(2.0), term(1.0, (SIN, 3.0, 0.0), (COS, 1.0, 0.0)),
+                term(1.0, (COS, 3.0, 0.0), (SIN, 1.0, 0.0)))
+    f = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0)))
+    g = sst(term(1.0, (QUAD, 1.0, 0.0)), term(1.0, None, (LIN, 1.0, 0.0)))
+    return problem(2, box([0, 0], [1, 1]), alpha, sigma, f, g, phi=phi)
+
+
+def fd_square_coefficients():
+    """The same coefficients as numpy functions of (x, y): alpha, grad Phi, sigma, f, g."""
+    return {
+        "alpha": lambda x, y: 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+        "grad_phi": lambda x, y: (0.5 * y, 0.5 * x),
+        "sigma": lambda x, y: 2.0 + np.sin(3.0 * x + y),
+        "f": lambda x, y: 1.0 + x,
+        "g": lambda x, y: x * x + y,
+    }
+
+
 def hifreq_alpha_problem(freq=6.0, amp=0.8):
     """div(alpha grad u) = -f on the unit square with a high-frequency diffusion
     coefficient alpha = 1 + amp sin(freq pi x) sin(freq pi y), u = sin(pi x) sinh(y) / sinh(1) + 1
