@@ -111,6 +111,15 @@ def _load():
     lib.orc_walk_grad.restype = C.c_double
     lib.orc_walks_grad.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
                                    C.c_int64, dp, dp, C.POINTER(C.c_int64), C.c_int]
+    lib.orc_offcentre_G.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp]
+    lib.orc_offcentre_G.restype = C.c_double
+    lib.orc_offcentre_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp]
+    lib.orc_offcentre_P.restype = C.c_double
+    lib.orc_walk_nf.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double, C.c_int64,
+                                C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.orc_walk_nf.restype = C.c_double
+    lib.orc_walks_nf.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
+                                 C.c_int64, C.c_int64, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]
     lib.orc_mesh_prepare.argtypes = [pp]
     lib.orc_mesh_release.argtypes = [pp]
     lib.orc_mesh_distance_brute.argtypes = [pp, dp, dp]
@@ -429,3 +438,46 @@ def solve_grad(prob, pts, walks, seed, eps, sigma_bar, walk_offset=0):
     n = float(walks)
     gs = np.moveaxis(gh, 0, -1)  # [npts, walks, dim]
     return (uh.mean(1), uh.std(1, ddof=1) / np.sqrt(n), gs.mean(1), gs.std(1, ddof=1) / np.sqrt(n))
+
+
+def offcentre_G(dim, R, sb, u, v):
+    """Approximate off-centred G(x, y) on the ball (Supplemental 1.2), u = x - c, v = y - c."""
+    uu, vv = np.zeros(3), np.zeros(3)
+    uu[:dim], vv[:dim] = u, v
+    return _load().orc_offcentre_G(dim, R, sb, _dptr(uu), _dptr(vv))
+
+
+def offcentre_P(dim, R, sb, u, v):
+    """Approximate off-centred P(x, z) on the sphere (Supplemental 1.2), u = x - c, v = z - c."""
+    uu, vv = np.zeros(3), np.zeros(3)
+    uu[:dim], vv[:dim] = u, v
+    return _load().orc_offcentre_P(dim, R, sb, _dptr(uu), _dptr(vv))
+
+
+def walk_nf(prob, x0, point, walk_id, seed, eps, sigma_bar, max_steps=1 << 20, max_inner=1 << 16, packed=None):
+    """(u estimate, outer steps, inner iterations, flags) of one next-flight walk."""
+    pk = packed or pack(prob)
+    xx = np.zeros(3)
+    xx[: len(x0)] = x0
+    k, m, fl = C.c_int64(), C.c_int64(), C.c_int32()
+    u = _load().orc_walk_nf(pk.ptr, _dptr(xx), point, walk_id, seed, eps, sigma_bar, max_steps, max_inner,
+                            C.byref(k), C.byref(m), C.byref(fl))
+    return u, k.value, m.value, fl.value
+
+
+def walks_nf(prob, pts, walks_per_point, seed, eps, sigma_bar, walk_offset=0, max_steps=1 << 20,
+             max_inner=1 << 16, nthreads=0):
+    """Per-walk next-flight estimates [npts, walks], outer steps and inner iterations."""
+    lib = _load()
+    pk = pack(prob)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    npts = pts.shape[1]
+    uh = np.zeros((npts, walks_per_point))
+    st = np.zeros((npts, walks_per_point), dtype=np.int64)
+    inn = np.zeros((npts, walks_per_point), dtype=np.int64)
+    rc = lib.orc_walks_nf(pk.ptr, _dptr(pts), npts, walks_per_point, walk_offset, seed, eps, sigma_bar, max_steps,
+                          max_inner, _dptr(uh), st.ctypes.data_as(C.POINTER(C.c_int64)),
+                          inn.ctypes.data_as(C.POINTER(C.c_int64)), nthreads)
+    if rc != 0:
+        raise ValueError("orc_walks_nf rejected its inputs")
+    return uh, st, inn

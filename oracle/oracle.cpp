@@ -1226,6 +1226,174 @@ double orc_walk_grad(const orc_problem* P, const double* x0, uint32_t point, uin
   return u;
 }
 
+// ---------------------------------------------------------------------------
+// Next-flight variant (Sec. 5.2; Supplemental 1.2 and Algorithm 2)
+// ---------------------------------------------------------------------------
+// Q(r): the bracket of the centred G of Supplemental 1.1 (G = Q / (2 pi) in 2D,
+// Q / (4 pi) in 3D) on a ball of radius R, taken at any r > 0; V(r) = -Q'(r), the
+// bracket of Supplemental 1.2's V.  sigma_bar = 0 gives the Laplace forms.
+double nf_Q(int dim, double R, double sb, double r) {
+  double s = std::sqrt(sb);
+  if (dim == 2) {
+    if (sb == 0.0) return std::log(R / r);
+    return bK0(r * s) - bK0(R * s) / bI0(R * s) * bI0(r * s);
+  }
+  if (sb == 0.0) return 1.0 / r - 1.0 / R;
+  double a = R * s, t = r * s;
+  // e^{-t}/r - e^{-a} sinh(t) / (r sinh(a)) = sinh(a - t) / (r sinh(a)), the form
+  // that does not cancel for r near R
+  if (a < 300.0) return std::sinh(a - t) / (r * std::sinh(a));
+  return std::exp(-t) * (1.0 - std::exp(-2.0 * (a - t))) / (r * (1.0 - std::exp(-2.0 * a)));
+}
+
+double nf_V(int dim, double R, double sb, double r) {
+  double s = std::sqrt(sb);
+  if (dim == 2) {
+    if (sb == 0.0) return 1.0 / r;
+    return s * (bK1(r * s) + bK0(R * s) / bI0(R * s) * bI1(r * s));
+  }
+  if (sb == 0.0) return 1.0 / (r * r);
+  double a = R * s, t = r * s;
+  double em = 2.0 * std::exp(-2.0 * a) / (1.0 - std::exp(-2.0 * a));
+  return s / r * (std::exp(-t) * (1.0 + 1.0 / t) + em * cosh_m_sinhc(t));
+}
+
+double dot3(const double* a, const double* b, int dim) {
+  double acc = 0.0;
+  for (int i = 0; i < dim; ++i) acc += a[i] * b[i];
+  return acc;
+}
+
+double orc_offcentre_G(int dim, double R, double sb, const double* u, const double* v) {
+  double w[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) w[i] = v[i] - u[i];
+  double nw = std::sqrt(dot3(w, w, dim));
+  double img = (R * R - dot3(u, v, dim)) / R;
+  double c = (dim == 2) ? 1.0 / (2.0 * kPi) : 1.0 / (4.0 * kPi);
+  return c * (nf_Q(dim, R, sb, nw) - nf_Q(dim, R, sb, img));
+}
+
+double orc_offcentre_P(int dim, double R, double sb, const double* u, const double* v) {
+  double w[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) w[i] = v[i] - u[i];
+  double nw = std::sqrt(dot3(w, w, dim)), nv = std::sqrt(dot3(v, v, dim));
+  double uv = dot3(u, v, dim);
+  double img = (R * R - uv) / R;
+  double c = (dim == 2) ? 1.0 / (2.0 * kPi) : 1.0 / (4.0 * kPi);
+  return c * (nf_V(dim, R, sb, nw) * (nv * nv - uv) / (nw * nv) + nf_V(dim, R, sb, img) * uv / (R * nv));
+}
+
+double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint32_t walk, uint64_t seed,
+                   double eps, double sb, int64_t max_steps, int64_t max_inner, int64_t* steps_out,
+                   int64_t* inner_out, int32_t* flags_out) {
+  int dim = P->dim;
+  double x[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) x[d] = x0[d];
+  double W = 1.0, acc = 0.0;
+  double g0 = gamma_at(P, x);
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  int64_t k = 0, inner = 0;
+  int32_t flags = 0;
+  for (;;) {
+    double xb[3];
+    double d = distance(P, x, xb);
+    if (d < eps) {
+      double gv, gg[3], gl;
+      field_eval(P, &P->g, xb, &gv, gg, &gl);
+      acc += W * std::exp(gamma_at(P, x)) * gv;
+      break;
+    }
+    if (k >= max_steps) {
+      flags |= 1;
+      break;
+    }
+    double R = d;
+    // exit point z, uniform on the sphere, shared by every term of the boundary series
+    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o[4];
+    philox(ctr, key, o);
+    double dz[3] = {0, 0, 0};
+    if (dim == 2) {
+      double tz = 2.0 * kPi * uniform01(o[0]);
+      dz[0] = std::cos(tz); dz[1] = std::sin(tz);
+    } else {
+      double cz = 1.0 - 2.0 * uniform01(o[0]), pz = 2.0 * kPi * uniform01(o[1]);
+      double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
+      dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
+    }
+    double vz[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) vz[i] = R * dz[i];
+    double area = (dim == 2) ? 2.0 * kPi * R : 4.0 * kPi * R * R;
+    double vol = (dim == 2) ? kPi * R * R : 4.0 / 3.0 * kPi * R * R * R;
+    double uc[3] = {0, 0, 0};  // current sample point minus the ball centre
+    double T = 1.0, Ttr = 0.0, Tsrc = 0.0;
+    for (int64_t j = 0;; ++j) {
+      Ttr += orc_offcentre_P(dim, R, sb, uc, vz) * area * T;  // P(x_c, z) / p(z)
+      ctr[3] = (uint32_t)(j + 1);
+      philox(ctr, key, o);
+      double pRR = std::fmin(1.0, std::fabs(T));
+      if (pRR < uniform01(o[0])) break;
+      T /= pRR;
+      if (j >= max_inner) {
+        flags |= 4;
+        break;
+      }
+      ++inner;
+      // next point uniform in the ball
+      double vn[3] = {0, 0, 0};
+      if (dim == 2) {
+        double rr = R * std::sqrt(uniform01(o[1])), th = 2.0 * kPi * uniform01(o[2]);
+        vn[0] = rr * std::cos(th); vn[1] = rr * std::sin(th);
+      } else {
+        double rr = R * std::cbrt(uniform01(o[1]));
+        double cn = 1.0 - 2.0 * uniform01(o[2]), pn = 2.0 * kPi * uniform01(o[3]);
+        double sn = std::sqrt(std::fmax(0.0, 1.0 - cn * cn));
+        vn[0] = rr * sn * std::cos(pn); vn[1] = rr * sn * std::sin(pn); vn[2] = rr * cn;
+      }
+      double y[3] = {0, 0, 0};
+      for (int i = 0; i < dim; ++i) y[i] = x[i] + vn[i];
+      double gam_y, sp_y, fp_y, f_y, a_y;
+      coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+      double Gv = orc_offcentre_G(dim, R, sb, uc, vn) * vol;  // G(x_c, x_n) / p(x_n)
+      // source: f'(x_n) / (sigma_bar - sigma'(x_n)) times the updated throughput
+      Tsrc += fp_y * Gv * T;
+      T *= Gv * (sb - sp_y);
+      for (int i = 0; i < dim; ++i) uc[i] = vn[i];
+    }
+    acc += W * Tsrc;
+    W *= Ttr;
+    for (int i = 0; i < dim; ++i) x[i] += vz[i];
+    ++k;
+  }
+  double u = acc * std::exp(-g0);
+  if (!std::isfinite(u)) flags |= 2;
+  if (steps_out) *steps_out = k;
+  if (inner_out) *inner_out = inner;
+  if (flags_out) *flags_out = flags;
+  return u;
+}
+
+int orc_walks_nf(const orc_problem* P, const double* pts, int64_t npts, int32_t wpp, uint64_t walk_offset,
+                 uint64_t seed, double eps, double sb, int64_t max_steps, int64_t max_inner, double* uhat,
+                 int64_t* steps, int64_t* inner, int nthreads) {
+  if (!(sb > 0.0) || !(eps > 0.0)) return -1;
+  int dim = P->dim;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int64_t p = 0; p < npts; ++p) {
+    double x0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) x0[d] = pts[d * npts + p];
+    for (int32_t j = 0; j < wpp; ++j) {
+      int64_t i = p * wpp + j, k, m;
+      int32_t fl;
+      uhat[i] = orc_walk_nf(P, x0, (uint32_t)p, (uint32_t)(walk_offset + j), seed, eps, sb, max_steps, max_inner,
+                            &k, &m, &fl);
+      steps[i] = k;
+      inner[i] = m;
+    }
+  }
+  return 0;
+}
+
 int orc_solve(const orc_problem* P, const double* pts, int64_t npts, const int32_t* walks,
               int32_t walks_uniform, uint64_t walk_offset, uint64_t seed, double eps, double sb,
               int64_t max_steps, double* sum, double* sumsq, int64_t* count, int64_t* stats,

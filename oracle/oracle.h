@@ -165,6 +165,25 @@ int orc_walks_grad(const orc_problem* prob, const double* pts, int64_t npts, int
                    uint64_t walk_offset, uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
                    double* u, double* grad, int64_t* steps, int nthreads);
 
+/* Next-flight variant (Sec. 5.2, Supplemental Algorithm 2) on the transformed
+   problem.  The approximate off-centred Green's function and Poisson kernel of
+   Supplemental 1.2 on a ball of radius R centred at c, with u = x - c, v = y - c
+   (v = z - c on the sphere for P); full G and P (not divided by 2 pi / 4 pi).
+   Exact at u = 0. */
+double orc_offcentre_G(int dim, double R, double sigma_bar, const double* u, const double* v);
+double orc_offcentre_P(int dim, double R, double sigma_bar, const double* u, const double* v);
+/* One next-flight walk.  Randoms: outer step k draws the exit point z from Philox
+   block (point, walk, k, 0); inner iteration j of that ball draws its roulette
+   uniform and its uniform in-ball point from block (point, walk, k, j + 1).
+   steps_out = outer steps (distance queries), inner_out = inner iterations; flags
+   bit 0 = outer step cap, bit 1 = non-finite, bit 2 = inner cap hit. */
+double orc_walk_nf(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk, uint64_t seed,
+                   double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, int64_t* steps_out,
+                   int64_t* inner_out, int32_t* flags_out);
+int orc_walks_nf(const orc_problem* prob, const double* pts, int64_t npts, int32_t wpp, uint64_t walk_offset,
+                 uint64_t seed, double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, double* uhat,
+                 int64_t* steps, int64_t* inner, int nthreads);
+
 /* Many walks: pts SoA [dim][npts].  walks[p] (or walks_uniform if walks == NULL)
    walks per point with ids walk_offset .. walk_offset + walks - 1, accumulated
    into sum / sumsq / count (FP64, caller-initialised).  stats: {steps, walks,

@@ -1,0 +1,158 @@
+"""Pins of the oracle's next-flight walk (Sec. 5.2, Supplemental Algorithm 2) and of
+the approximate off-centred Green's function and Poisson kernel it uses
+(Supplemental 1.2).
+
+What the paper fixes about the approximations, checked here:
+* they equal the centred G and P of Supplemental 1.1 when x is the ball centre;
+* P is the (negative) normal derivative of G on the sphere, as printed;
+* for the Laplacian along the ray through the centre (u parallel to v) they equal
+  the exact image-charge Green's function and Poisson kernel;
+* away from the centre they deviate from the exact kernels (the eigenfunction
+  series of Supplemental 1.2, summed with scipy), increasingly with |u|.
+The walk itself is pinned where its estimate is exact whatever the off-centre
+error: with sigma_bar = sigma' every null weight sigma_bar - sigma' is zero, so
+every ball uses only the centred kernels (screened ball; screened square with a
+source), and for a Laplace problem the off-centre terms carry a factor
+sigma_bar R^2 ~ 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.stats_util import four_se_rule
+from tests.test_oracle_grad import _g_harmonic, _g_series, _p_harmonic, _p_series
+
+
+def _vec(dim, r, ang):
+    v = np.zeros(dim)
+    v[0], v[1] = r * math.cos(ang), r * math.sin(ang)
+    return v
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("R,sb", [(0.5, 60.0), (0.2, 4.0), (1.0, 1e-3)])
+def test_offcentre_exact_at_centre(orc, dim, R, sb):
+    area = 2 * math.pi * R if dim == 2 else 4 * math.pi * R * R
+    u = np.zeros(dim)
+    for rho in (0.05, 0.4, 0.9):
+        v = _vec(dim, rho * R, 0.7)
+        g = orc.offcentre_G(dim, R, sb, u, v)
+        assert abs(g - orc.green_G(dim, R, sb, rho * R)) <= 1e-12 * abs(g)
+    z = _vec(dim, R, 2.1)
+    p = orc.offcentre_P(dim, R, sb, u, z)
+    assert abs(p - (1.0 - sb * orc.green_norm(dim, R, sb)) / area) <= 1e-12 * p
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("sb", [60.0, 1e-3])
+def test_offcentre_P_is_normal_derivative_of_G(orc, dim, sb):
+    """P(x, z) = -dG(x, y)/dn at y = z on the sphere, for the printed forms of both."""
+    R, h = 0.5, 1e-6
+    for fu, ang in ((0.2, 0.4), (0.5, 1.9), (0.7, 3.0)):
+        u = _vec(dim, fu * R, 0.3)
+        z = _vec(dim, R, ang)
+        n = z / R
+        dg = (orc.offcentre_G(dim, R, sb, u, z + h * n) - orc.offcentre_G(dim, R, sb, u, z - h * n)) / (2 * h)
+        p = orc.offcentre_P(dim, R, sb, u, z)
+        assert abs(p + dg) <= 1e-6 * abs(p), (fu, ang, p, -dg)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_offcentre_laplace_on_the_radial_line(orc, dim):
+    R = 0.8
+    for fu, fv in ((0.3, 0.6), (0.7, 0.2), (-0.5, 0.9)):
+        u = _vec(dim, fu * R, 0.0)
+        v = _vec(dim, fv * R, 0.0)
+        g = orc.offcentre_G(dim, R, 0.0, u, v)
+        assert abs(g - _g_harmonic(dim, R, u, v)) <= 1e-12 * abs(g)
+        z = _vec(dim, R, 0.0 if fu > 0 else math.pi)
+        p = orc.offcentre_P(dim, R, 0.0, u, z)
+        assert abs(p - _p_harmonic(dim, R, u, z)) <= 1e-12 * abs(p)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_offcentre_approximation_error_grows_from_the_centre(orc, dim):
+    """The approximations against the exact series: close near the centre, far off near the
+    sphere (a characterisation of Supplemental 1.2's approximation, not a bound the paper states)."""
+    R, sb = 0.5, 4.0
+
+    def worst(fu):
+        e = 0.0
+        u = _vec(dim, fu * R, 0.0)
+        for ang in (0.3, 1.2, 2.5):
+            for fr in (0.3, 0.8):
+                v = _vec(dim, fr * R, ang)
+                c = math.cos(ang)
+                gs = _g_series(dim, R, sb, fu * R, c, fr * R)
+                e = max(e, abs(orc.offcentre_G(dim, R, sb, u, v) - gs) / abs(gs))
+            z = _vec(dim, R, ang)
+            ps = _p_series(dim, R, sb, fu * R, math.cos(ang))
+            e = max(e, abs(orc.offcentre_P(dim, R, sb, u, z) - ps) / abs(ps))
+        return e
+    e1, e3, e6 = worst(0.1), worst(0.3), worst(0.6)
+    assert e1 < 0.05 and e1 < e3 < e6 and e6 > 0.3, (e1, e3, e6)
+
+
+NF_CASES = {
+    # sigma_bar = sigma' (constant): every inner series stops after its first term
+    "screened_ball": (W.screened_ball_problem, lambda p: W.screened_ball_exact(9.0, *p),
+                      lambda: W.uniform_in_ball(3, 8, [0, 0, 0], 1.0, seed=4, margin=0.05), 9.0, 3000),
+    "screened_square": (W.screened_square_problem, lambda p: W.screened_square_exact(*p),
+                        lambda: W.uniform_in_box(2, 8, 0.05, 0.95, seed=3), 4.0, 3000),
+    # Laplace with the sigma_bar floor: off-centre terms are O(sigma_bar R^2)
+    "laplace_disk": (W.laplace_disk_problem, lambda p: W.laplace_disk_exact(*p),
+                     lambda: W.uniform_in_ball(2, 8, [0, 0], 1.0, seed=1, margin=0.05), None, 3000),
+    "laplace_ball": (W.laplace_ball_problem, lambda p: W.laplace_ball_exact(*p),
+                     lambda: W.uniform_in_ball(3, 8, [0, 0, 0], 1.0, seed=2, margin=0.05), None, 3000),
+}
+
+
+@pytest.mark.parametrize("name", list(NF_CASES))
+def test_next_flight_exact_cases(orc, name):
+    mk, exact, ptsf, sb, walks = NF_CASES[name]
+    prob = mk()
+    pts = ptsf()
+    if sb is None:
+        sb = orc.sigma_bar(prob)[0]
+    uh, st, inner = orc.walks_nf(prob, pts, walks, seed=3, eps=1e-4, sigma_bar=sb)
+    m = uh.mean(1)
+    se = uh.std(1, ddof=1) / math.sqrt(walks)
+    ok, nout, mz = four_se_rule((m - exact(pts.astype(np.float64))) / se)
+    assert ok, (name, (m - exact(pts.astype(np.float64))) / se)
+    assert np.all(st > 0) and np.all(inner >= st)
+
+
+def test_next_flight_distance_queries_do_not_grow_with_sigma_bar(orc):
+    """Sec. 5.2, Fig. 12: raising sigma_bar multiplies the delta-tracking walk's distance
+    queries but leaves the next-flight walk's unchanged."""
+    prob = W.screened_square_problem()
+    pts = W.uniform_in_box(2, 6, 0.2, 0.8, seed=5)
+    counts = {}
+    for sb in (4.0, 400.0):
+        _, st_nf, _ = orc.walks_nf(prob, pts, 400, seed=1, eps=1e-3, sigma_bar=sb)
+        _, st_dt = orc.walks(prob, pts, 400, seed=1, eps=1e-3, sigma_bar=sb)
+        counts[sb] = (st_nf.mean(), st_dt.mean())
+    assert counts[400.0][1] > 2.5 * counts[4.0][1], counts
+    assert abs(counts[400.0][0] / counts[4.0][0] - 1.0) < 0.1
+
+
+def test_next_flight_stream_layout(orc):
+    """Walk ids continue streams; the walk at sigma_bar = sigma' uses one inner iteration per ball."""
+    prob = W.screened_ball_problem()
+    x = np.array([0.1, -0.2, 0.3])
+    for j in range(8):
+        u, k, m, fl = orc.walk_nf(prob, x, 2, j, 4, 1e-4, 9.0)
+        assert fl == 0 and m == k
+    a, sa, ia = orc.walks_nf(prob, x[:, None], 6, seed=4, eps=1e-4, sigma_bar=9.0)
+    b, sb_, ib = orc.walks_nf(prob, x[:, None], 3, seed=4, eps=1e-4, sigma_bar=9.0, walk_offset=3)
+    assert np.array_equal(a[:, 3:], b) and np.array_equal(sa[:, 3:], sb_)
+
+
+def test_next_flight_in_shell_returns_boundary_value(orc):
+    prob = W.square2d_problem()
+    sb = orc.sigma_bar(prob)[0]
+    u, k, m, fl = orc.walk_nf(prob, np.array([0.5, 1e-4]), 0, 0, 0, 1e-3, sb)
+    d, xb = orc.distance(prob, np.array([0.5, 1e-4]))
+    assert k == 0 and m == 0 and abs(u - W.square2d_exact(*xb)) <= 1e-12
