@@ -374,6 +374,30 @@ def run_other(args):
         extra["grad_over_value_time"] = ms / ms0
         cfg = {"workload": f"cube3d_drift_manufactured with grad u (Supplemental Sec. 2): {GRID}^3 points x "
                            f"{WALKS} walks, eps 1e-4", "sigma_bar": sb}
+    elif wl == "nf":
+        # next-flight (Sec. 5.2) against delta tracking on the 3D workload: balls (distance
+        # queries) and inner iterations per walk, and the time for the same walks
+        desc = W.cube3d_problem()
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 64)[0]
+        pts_np = W.cell_centres(3, GRID)
+        pts = torch.from_numpy(pts_np).cuda()
+        npts = pts_np.shape[1]
+        (acc, st), ms = timed(lambda i: ctx.solve_nf(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        (acc0, st0), ms0 = timed(lambda i: ctx.solve(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        sd, s0 = wos.stats_dict(st), wos.stats_dict(st0)
+        m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+        m0, v0, se0 = (t.cpu().numpy() for t in ctx.finalize(acc0))
+        exact = W.cube3d_exact(*pts_np.astype(np.float64))
+        extra["inner_per_walk"] = sd["inner"] / max(sd["walks"], 1)
+        extra["inner_per_s"] = sd["inner"] / (ms * 1e-3)
+        extra["delta_tracking_ms"] = ms0
+        extra["delta_tracking_steps_per_walk"] = s0["steps"] / max(s0["walks"], 1)
+        extra["normalised_rms"] = float(np.linalg.norm(m - exact) / np.linalg.norm(exact))
+        extra["delta_tracking_normalised_rms"] = float(np.linalg.norm(m0 - exact) / np.linalg.norm(exact))
+        extra["mean_stderr_over_delta_tracking"] = float(np.mean(se) / np.mean(se0))
+        cfg = {"workload": f"cube3d_drift_manufactured, next-flight walks (approximate off-centred G, P): "
+                           f"{GRID}^3 points x {WALKS} walks, eps 1e-4; steps count balls", "sigma_bar": sb}
     elif wl == "mesh":
         desc = W.mesh_noise_problem(level=7)
         t0 = time.perf_counter()
@@ -466,7 +490,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
     ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
-    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad"],
+    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad", "nf"],
                     help="cube3d is the benchmark; the others print supplementary measurements")
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")

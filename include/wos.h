@@ -55,7 +55,8 @@ extern "C" {
 #define WOS_STAT_CAPPED 2    /* walks stopped by max_steps (biased; should be 0) */
 #define WOS_STAT_NONFINITE 3 /* walks whose estimate is not finite */
 #define WOS_STAT_OUTSIDE 4   /* walks started at a point with distance <= 0 */
-#define WOS_STATS_WORDS 5
+#define WOS_STAT_INNER 5     /* next-flight walks: inner (in-ball) iterations; steps count balls */
+#define WOS_STATS_WORDS 6
 
 /* ---- problem description ---- */
 
@@ -236,6 +237,31 @@ int wos_solve_grad(wos_ctx* ctx, const wos_problem* prob, const float* pts, int6
 int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
                             int32_t walks_per_point, const wos_params* params, double* uhat,
                             double* grad_hat, int64_t* steps, uint64_t* stats, void* stream);
+
+/* Next-flight walk on spheres (Sec. 5.2, Supplemental Algorithm 2) with the
+   approximate off-centred Green's function and Poisson kernel of Supplemental 1.2.
+   One distance query per ball; in ball B(x) of radius R the walk draws one exit
+   point z uniform on the sphere and sums the boundary series
+   T_tr = sum_j P(x^j, z)|dB| prod_{l<j} theta_l and the source series
+   T_src = sum_{j>=1} f'(x^j) G(x^{j-1}, x^j)|B| prod_{l<j-1} theta_l over uniform
+   in-ball points x^j, theta_l = G(x^l, x^{l+1}) |B| (sigma_bar - sigma'(x^{l+1})),
+   with Russian roulette of probability min(1, |throughput|) ending the series; the
+   walk adds W T_src, sets W *= T_tr and moves to z.  The approximations are exact
+   at the ball centre only, so the estimate is biased where sigma' < sigma_bar;
+   exact when sigma' = sigma_bar everywhere.  Randoms: ball k of walk (p, w) uses
+   Philox block (p, w, k, 0) for z and block (p, w, k, j + 1) for inner iteration j.
+   max_inner (>= 1) caps a ball's iterations (the walk is then counted as capped).
+   Arguments and results as wos_solve (stats: steps = balls, WOS_STAT_INNER = inner
+   iterations).  Errors: as wos_solve; WOS_EINVAL if max_inner < 1;
+   WOS_EUNSUPPORTED with a weight window. */
+int wos_solve_nf(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                 const int32_t* walks, int32_t walks_uniform, const wos_params* params, int64_t max_inner,
+                 double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream);
+
+/* As wos_walk_estimates for next-flight walks (uhat, steps = balls per walk). */
+int wos_walk_estimates_nf(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                          int32_t walks_per_point, const wos_params* params, int64_t max_inner,
+                          double* uhat, int64_t* steps, uint64_t* stats, void* stream);
 
 /* Per-point mean, unbiased sample variance of one walk's estimate, and standard
    error of the mean from the accumulators (Sec. 2.2: the estimate is the average

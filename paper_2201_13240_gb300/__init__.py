@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libwos.so")
 WOS_OK, WOS_EINVAL, WOS_ENOMEM, WOS_ECUDA, WOS_ETIMEOUT, WOS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 WOS_FP32, WOS_FP64 = 0, 1
 STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
-STATS_WORDS = 5
+STATS_WORDS = 6
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
 _DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4}
 
@@ -83,6 +83,8 @@ def load():
     lib.wos_solve.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_walk_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.wos_solve_nf.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), i64, vp, vp, vp, vp, vp]
+    lib.wos_walk_estimates_nf.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), i64, vp, vp, vp, vp]
     lib.wos_solve_grad.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
     lib.wos_walk_grad_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
@@ -323,6 +325,49 @@ class Context:
                                                 C.byref(p), _ptr(uhat), _ptr(steps), _ptr(stats), _stream(stream)))
         return uhat, steps, stats
 
+    def solve_nf(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
+                 max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None):
+        """Next-flight walks (Sec. 5.2) added to the accumulators; stats 'steps' counts balls
+        (distance queries), 'inner' the in-ball iterations."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        if accum is None:
+            accum = self.new_accum(npts)
+        if not (accum[0].dtype == torch.float64 and accum[1].dtype == torch.float64 and accum[2].dtype == torch.int64
+                and all(t.is_cuda and t.is_contiguous() and t.shape == (npts,) for t in accum)):
+            raise TypeError("accumulators must be contiguous CUDA (float64, float64, int64) tensors of length npts")
+        if stats is None:
+            stats = self.new_stats()
+        if isinstance(walks, int):
+            wp, wu = None, walks
+        else:
+            if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                    and walks.shape == (npts,)):
+                raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+            walks = walks.contiguous()
+            wp, wu = _ptr(walks), 0
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_nf(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
+                                          int(max_inner), _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]),
+                                          _ptr(stats), _stream(stream)))
+        return accum, stats
+
+    def walk_estimates_nf(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0,
+                          max_steps=1 << 20, max_inner=1 << 16, precision="fp32", stream=None):
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        dev = f"cuda:{self.device}"
+        uhat = torch.empty((npts, walks_per_point), dtype=torch.float64, device=dev)
+        steps = torch.empty((npts, walks_per_point), dtype=torch.int64, device=dev)
+        stats = self.new_stats()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_walk_estimates_nf(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
+                                                   C.byref(p), int(max_inner), _ptr(uhat), _ptr(steps),
+                                                   _ptr(stats), _stream(stream)))
+        return uhat, steps, stats
+
     def solve_grad(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
                    precision="fp32", accum=None, grad_accum=None, stats=None, stream=None):
         """Add walks' estimates of u and grad u (Supplemental Sec. 2).  Returns (accum, grad_accum,
@@ -458,4 +503,4 @@ class Context:
 
 def stats_dict(stats):
     s = [int(v) for v in stats.cpu().tolist()]
-    return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4]}
+    return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4], "inner": s[5]}

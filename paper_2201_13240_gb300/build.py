@@ -21,9 +21,10 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libwos.so")
 HOSTCHECK = os.path.join(HERE, "libwos_hostcheck.so")
 
-CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_adjoint.cu", "wos_mesh.cpp"]
-HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_adjoint_impl.cuh", "wos_internal.h",
-           "wos_mesh.h"]
+CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_nf_f32.cu", "wos_nf_f64.cu",
+              "wos_adjoint.cu", "wos_mesh.cpp"]
+HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_nf_impl.cuh", "wos_adjoint_impl.cuh",
+           "wos_internal.h", "wos_mesh.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

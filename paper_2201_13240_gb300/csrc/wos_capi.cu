@@ -325,7 +325,7 @@ int no_window(wos_ctx* ctx, const wos_params* prm) {
 int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, const int64_t* walk_end,
            int64_t walks_uniform, uint64_t total, const wos_params* prm, double* sum, double* sumsq,
            int64_t* count, uint64_t* stats, double* uhat, int64_t* steps, cudaStream_t st,
-           double* gsum = nullptr, double* gsumsq = nullptr, double* ghat = nullptr) {
+           double* gsum = nullptr, double* gsumsq = nullptr, double* ghat = nullptr, int64_t nf_max_inner = 0) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
   unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
@@ -362,14 +362,16 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.gsum = gsum;
   L.gsumsq = gsumsq;
   L.ghat = ghat;
+  L.nf_max_inner = nf_max_inner;
+  const bool nf = nf_max_inner > 0;
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
-    e = wos::launch_walks_f64(L, ctx->num_sms, st);
+    e = nf ? wos::launch_nf_f64(L, ctx->num_sms, st) : wos::launch_walks_f64(L, ctx->num_sms, st);
   } else {
     L.problem = prob->d32;
     L.problem_bytes = (int)sizeof(DevProblem<float>);
-    e = wos::launch_walks_f32(L, ctx->num_sms, st);
+    e = nf ? wos::launch_nf_f32(L, ctx->num_sms, st) : wos::launch_walks_f32(L, ctx->num_sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "walk kernel launch");
   return WOS_OK;
@@ -662,6 +664,57 @@ int wos_solve_grad(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_
   }
   return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
                 nullptr, st, grad_sum, grad_sumsq, nullptr);
+}
+
+int wos_solve_nf(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, const int32_t* walks,
+                 int32_t walks_uniform, const wos_params* prm, int64_t max_inner, double* sum, double* sumsq,
+                 int64_t* count, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
+  if (max_inner < 1) return fail(ctx, WOS_EINVAL, "max_inner must be >= 1");
+  if (npts < 0) return fail(ctx, WOS_EINVAL, "npts < 0");
+  if (npts == 0) return WOS_OK;
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
+  if (!pts || !sum || !sumsq || !count) return fail(ctx, WOS_EINVAL, "null device array");
+  if (!walks && walks_uniform < 0) return fail(ctx, WOS_EINVAL, "walks_uniform < 0");
+  if (!walks && walks_uniform == 0) return WOS_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t* walk_end = nullptr;
+  uint64_t total;
+  if (walks) {
+    rc = grow(ctx, &ctx->walk_end, npts, &ctx->walk_end_cap, npts);
+    if (rc) return rc;
+    walk_prefix_kernel<<<1, 1024, 0, st>>>(walks, npts, ctx->walk_end);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "walk prefix kernel");
+    walk_end = ctx->walk_end;
+    total = ~0ull;
+  } else {
+    total = (uint64_t)npts * (uint64_t)walks_uniform;
+  }
+  return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
+                nullptr, st, nullptr, nullptr, nullptr, max_inner);
+}
+
+int wos_walk_estimates_nf(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,
+                          const wos_params* prm, int64_t max_inner, double* uhat, int64_t* steps, uint64_t* stats,
+                          void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
+  if (max_inner < 1) return fail(ctx, WOS_EINVAL, "max_inner must be >= 1");
+  if (npts < 0 || wpp < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts == 0 || wpp == 0) return WOS_OK;
+  if (!pts || !uhat || !steps) return fail(ctx, WOS_EINVAL, "null device array");
+  DeviceGuard g(ctx->device);
+  return launch(ctx, pr, pts, npts, nullptr, wpp, (uint64_t)npts * (uint64_t)wpp, prm, nullptr, nullptr, nullptr,
+                stats, uhat, steps, static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, max_inner);
 }
 
 int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,

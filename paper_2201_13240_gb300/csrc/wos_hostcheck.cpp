@@ -140,4 +140,41 @@ void wos_hc_grad_ratios(int dim, int fp64, double a, const double* rho, int64_t 
   }
 }
 
+// next-flight kernels: out[2i] = G(c + u_i, c + v_i), out[2i+1] = P(c + u_i, c + z_i) (|z_i| = R)
+void wos_hc_offcentre(int dim, int fp64, double Rb, double sb, const double* u, const double* v, const double* z,
+                      int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) {
+      double uu[3] = {u[3 * i], u[3 * i + 1], u[3 * i + 2]}, vv[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+      double zz[3] = {z[3 * i], z[3 * i + 1], z[3 * i + 2]};
+      if (dim == 2) {
+        wos::NfBall<2, double> b;
+        b.init(std::sqrt(sb), Rb);
+        out[2 * i] = b.G(uu, vv);
+        out[2 * i + 1] = b.P(uu, zz);
+      } else {
+        wos::NfBall<3, double> b;
+        b.init(std::sqrt(sb), Rb);
+        out[2 * i] = b.G(uu, vv);
+        out[2 * i + 1] = b.P(uu, zz);
+      }
+    } else {
+      float uu[3] = {(float)u[3 * i], (float)u[3 * i + 1], (float)u[3 * i + 2]};
+      float vv[3] = {(float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2]};
+      float zz[3] = {(float)z[3 * i], (float)z[3 * i + 1], (float)z[3 * i + 2]};
+      if (dim == 2) {
+        wos::NfBall<2, float> b;
+        b.init(std::sqrt((float)sb), (float)Rb);
+        out[2 * i] = b.G(uu, vv);
+        out[2 * i + 1] = b.P(uu, zz);
+      } else {
+        wos::NfBall<3, float> b;
+        b.init(std::sqrt((float)sb), (float)Rb);
+        out[2 * i] = b.G(uu, vv);
+        out[2 * i + 1] = b.P(uu, zz);
+      }
+    }
+  }
+}
+
 }  // extern "C"

@@ -8,7 +8,7 @@
 namespace wos {
 
 // statistics words written by the walk kernel (added atomically)
-enum { ST_STEPS = 0, ST_WALKS = 1, ST_CAPPED = 2, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_WORDS = 5 };
+enum { ST_STEPS = 0, ST_WALKS = 1, ST_CAPPED = 2, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_INNER = 5, ST_WORDS = 6 };
 
 struct WalkLaunch {
   const void* problem;            // DevProblem<R> in device memory
@@ -45,6 +45,8 @@ struct WalkLaunch {
   double* gsum;                   // SoA [dim][npts], accumulated
   double* gsumsq;                 // SoA [dim][npts], accumulated
   double* ghat;                   // optional per-walk gradients SoA [dim][total_items]
+  // next-flight launches: cap on the inner iterations of one ball
+  int64_t nf_max_inner;
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma
@@ -74,6 +76,10 @@ cudaError_t launch_adjoint_f64(const AdjLaunch& L, int num_sms, cudaStream_t str
 // launch the persistent walk kernel; returns a cudaError_t
 cudaError_t launch_walks_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
 cudaError_t launch_walks_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream);
+
+// next-flight walks (Sec. 5.2)
+cudaError_t launch_nf_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
+cudaError_t launch_nf_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream);
 
 // per-SM resident blocks of the walk kernel (for reporting)
 int walk_blocks_per_sm_f32(int dim);

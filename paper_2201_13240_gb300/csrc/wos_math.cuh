@@ -117,6 +117,8 @@ WOS_HD void w_sincospi2(double u, double* s, double* c) {
   *c = cos(6.283185307179586476925 * u);
 #endif
 }
+WOS_HD float w_cbrt(float x) { return cbrtf(x); }
+WOS_HD double w_cbrt(double x) { return cbrt(x); }
 WOS_HD float w_expm1(float x) { return expm1f(x); }
 WOS_HD double w_expm1(double x) { return expm1(x); }
 WOS_HD float w_asin(float x) { return asinf(x); }
@@ -479,6 +481,103 @@ WOS_HD void grad_ratios(R a, R rho, R* gGR, R* gPR) {
   *gPR = a * i0a / i1a;
   *gGR = a * (k1t - k1a * i1t / i1a * e) / (k0t - k0a * i0t / i0a * e);
 }
+
+// ---------------------------------------------------------------------------
+// Next-flight kernels (Sec. 5.2): the approximate off-centred Green's function and
+// Poisson kernel of Supplemental 1.2 on a ball of radius R (centre c), in terms of
+//   Q(r): the bracket of the centred G (G = Q/(2 pi) in 2D, Q/(4 pi) in 3D), any r > 0,
+//   V(r) = -Q'(r):
+//   G(x, y) = (Q(|w|) - Q(rho')) / (2 pi | 4 pi),
+//   P(x, z) = (V(|w|)(R^2 - u.v)/(|w| R) + V(rho') u.v / R^2) / (2 pi | 4 pi),
+// with u = x - c, v = y - c (|v| = R for P), w = v - u, rho' = (R^2 - u.v)/R.
+// Overflow-free forms (t = s r, a = s R):
+//   3D  Q = (e^{-t} - e^{t-2a}) / (r (1 - e^{-2a}))             [= sinh(a-t)/(r sinh a)]
+//       V = (s/r)(e^{-t}(1 + 1/t) + 2 e^{t-2a} c^(t) / (1 - e^{-2a})),  c^ = e^{-t}(cosh t - sinh t/t)
+//   2D  Q = e^{-t} k0s(t) - cK e^{t-2a} i0s(t),   V = s (e^{-t} k1s(t) + cK e^{t-2a} i1s(t)),
+//       cK = k0s(a)/i0s(a)  (e^{-x}-scaled I, e^{x}-scaled K)
+// and the Laplace forms (3D 1/r - 1/R, 1/r^2; 2D ln(R/r), 1/r) for a < 1e-7.
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+struct NfBall {
+  R s, a, Rb;
+  R inv_den;  // 3D: 1 / (1 - e^{-2a})
+  R cK;       // 2D: k0s(a) / i0s(a)
+  bool lap;
+  R pcentre;  // P^dB of the centred ball: P(c, z) |dB|
+
+  WOS_HD void init(R s_, R Rb_) {
+    s = s_;
+    Rb = Rb_;
+    a = s * Rb;
+    lap = !(a >= R(1e-7));
+    inv_den = R(0);
+    cK = R(0);
+    if (lap) {
+      pcentre = R(1);
+      return;
+    }
+    if (DIM == 3) {
+      inv_den = R(1) / (-w_expm1(R(-2) * a));
+      pcentre = R(2) * a * w_exp(-a) * inv_den;  // a / sinh a
+    } else {
+      R i0s, i1s, k0s, k1s;
+      bessel_scaled(a, &i0s, &i1s, &k0s, &k1s);
+      cK = k0s / i0s;
+      pcentre = w_exp(-a) / i0s;                 // 1 / I0(a)
+    }
+  }
+  WOS_HD R Q(R r) const {
+    if (DIM == 3) {
+      if (lap) return R(1) / r - R(1) / Rb;
+      R t = s * r;
+      // e^{-t} - e^{t-2a}, factored on the side that cannot overflow
+      R num = (t <= a) ? w_exp(-t) * (-w_expm1(R(-2) * (a - t))) : -w_exp(t - R(2) * a) * (-w_expm1(R(-2) * (t - a)));
+      return num * inv_den / r;
+    }
+    if (lap) return w_log(Rb / r);
+    R t = s * r;
+    R i0s, i1s, k0s, k1s;
+    bessel_scaled(t, &i0s, &i1s, &k0s, &k1s);
+    return w_exp(-t) * k0s - cK * w_exp(t - R(2) * a) * i0s;
+  }
+  WOS_HD R V(R r) const {
+    if (DIM == 3) {
+      if (lap) return R(1) / (r * r);
+      R t = s * r;
+      return s / r * (w_exp(-t) * (R(1) + R(1) / t) + R(2) * w_exp(t - R(2) * a) * grad_chat(t) * inv_den);
+    }
+    if (lap) return R(1) / r;
+    R t = s * r;
+    R i0s, i1s, k0s, k1s;
+    bessel_scaled(t, &i0s, &i1s, &k0s, &k1s);
+    return s * (w_exp(-t) * k1s + cK * w_exp(t - R(2) * a) * i1s);
+  }
+  // G(c + u, c + v)
+  WOS_HD R G(const R* u, const R* v) const {
+    R w2 = R(0), uv = R(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      R wi = v[i] - u[i];
+      w2 += wi * wi;
+      uv += u[i] * v[i];
+    }
+    const R cd = (DIM == 2) ? R(0.15915494309189533577) : R(0.07957747154594766788);
+    return cd * (Q(w_sqrt(w2)) - Q((Rb * Rb - uv) / Rb));
+  }
+  // P(c + u, c + v), |v| = R
+  WOS_HD R P(const R* u, const R* v) const {
+    R w2 = R(0), uv = R(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      R wi = v[i] - u[i];
+      w2 += wi * wi;
+      uv += u[i] * v[i];
+    }
+    const R cd = (DIM == 2) ? R(0.15915494309189533577) : R(0.07957747154594766788);
+    R nw = w_sqrt(w2), r2 = Rb * Rb;
+    return cd * (V(nw) * (r2 - uv) / (nw * Rb) + V((r2 - uv) / Rb) * uv / r2);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Radial CDF F(rho) of y ~ G/|G|, rho = r/R, and its density, 3D.

@@ -71,7 +71,7 @@ def test_fp64_replay_matches_oracle_per_walk(orc, ctx, name):
     ok = np.abs(uh - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
     assert ok.mean() >= 0.99, (name, ok.mean(), np.abs(uh - uo).max())
     assert (st == so).mean() >= 0.99
-    s = dict(zip(["steps", "walks", "capped", "nonfinite", "outside"], stats.cpu().tolist()))
+    s = dict(zip(["steps", "walks", "capped", "nonfinite", "outside", "inner"], stats.cpu().tolist()))
     assert s["walks"] == pts.shape[1] * wpp and s["steps"] == int(st.sum())
 
 

@@ -128,3 +128,34 @@ def test_centre_gradient_ratios(hc, orc, dim, fp64):
         hc.wos_hc_grad_ratios(dim, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), out.ctypes.data_as(DP))
         want = np.array([orc.green_grad_ratios(dim, R, (a / R) ** 2, r * R) for r in rho]) * R
         assert np.allclose(out.reshape(-1, 2), want, rtol=tol, atol=0), (a, out.reshape(-1, 2), want)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_offcentre_kernels(hc, orc, dim, fp64):
+    """The next-flight kernels' approximate off-centred G and P (Supplemental 1.2) against
+    the oracle's, at random interior and sphere points, from the Laplace limit to a = 126."""
+    rng = np.random.default_rng(0)
+    tol = 1e-12 if fp64 else 1e-4
+    for R, sb in ((0.3, 1e-3), (0.5, 4.0), (0.2, 787.0), (0.05, 1578.0), (1.0, 0.0), (0.4, 1e5)):
+        n = 100
+
+        def dirs():
+            d = rng.normal(size=(n, 3))
+            if dim == 2:
+                d[:, 2] = 0
+            return d / np.linalg.norm(d, axis=1)[:, None]
+        u = dirs() * (R * rng.uniform(size=n) ** (1 / dim))[:, None]
+        v = dirs() * (R * rng.uniform(size=n) ** (1 / dim))[:, None]
+        z = dirs() * R
+        out = np.zeros(2 * n)
+        hc.wos_hc_offcentre(dim, fp64, C.c_double(R), C.c_double(sb), np.ascontiguousarray(u).ctypes.data_as(DP),
+                            np.ascontiguousarray(v).ctypes.data_as(DP), np.ascontiguousarray(z).ctypes.data_as(DP),
+                            n, out.ctypes.data_as(DP))
+        scale = orc.green_G(dim, R, max(sb, 1e-12), 0.5 * R)
+        for i in range(n):
+            g = orc.offcentre_G(dim, R, sb, u[i, :dim], v[i, :dim])
+            p = orc.offcentre_P(dim, R, sb, u[i, :dim], z[i, :dim])
+            assert abs(out[2 * i] - g) <= tol * max(abs(g), scale), (R, sb, i)
+            if abs(p) > 1e-30:
+                assert abs(out[2 * i + 1] - p) <= tol * abs(p), (R, sb, i)
