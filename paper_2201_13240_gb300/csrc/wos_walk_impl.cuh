@@ -429,8 +429,9 @@ cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
-  uint64_t warps_needed = (L.total_items + 31) / 32;
-  uint64_t blocks_needed = (warps_needed + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
+  // total_items is ~0 when per-point walk counts give the total on the device: no cap then
+  uint64_t warps_needed = L.total_items / 32 + 1;
+  uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
   wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
