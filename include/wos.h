@@ -284,6 +284,20 @@ int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* prob, const float* pts, i
                       int32_t walks_uniform, const wos_params* params, const double* grad_u,
                       double* grad_sigma, uint64_t* stats, void* stream);
 
+/* Gradient of sum_p grad_u[p] * mean_p with respect to the control values of the cubic
+   B-spline alpha grid, by the same path replay as wos_adjoint_sigma (the walks do
+   not move with alpha either: sampling uses only the geometry, sigma_bar and the
+   randoms).  alpha enters through gamma = (ln alpha + Phi)/2, i.e. through
+   e^{-gamma(x_0)}, the sources f' = e^{gamma} f / alpha, the null weights via
+   sigma' = sigma/alpha + Lap gamma + |grad gamma|^2, and e^{gamma(x_n)} at the
+   boundary (Sec. 4.1, App. A).  grad_alpha: device double [alpha grid nodes], ADDED
+   to.  Grids of up to 8192 nodes are accumulated per CTA in shared memory first.
+   Errors: WOS_EUNSUPPORTED unless alpha is WOS_FIELD_GRID_BSPLINE and f is not
+   WOS_FIELD_MANUFACTURED; WOS_EINVAL as wos_solve. */
+int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
+                      int32_t walks_uniform, const wos_params* params, const double* grad_u,
+                      double* grad_alpha, uint64_t* stats, void* stream);
+
 /* ---- batches of independent problems (not in the paper; many small solves in one launch) ----
    wos_batch_create uploads nprob problems of one dimension (no mesh domains) with HOST
    point offsets [nprob + 1] (points of problem i are offsets[i] .. offsets[i+1]-1 of the

@@ -89,6 +89,7 @@ def load():
     lib.wos_walk_grad_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_adjoint_sigma.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
+    lib.wos_adjoint_alpha.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_batch_create.argtypes = [vp, C.POINTER(vp), i32, vp, vp, C.POINTER(vp)]
     lib.wos_batch_destroy.argtypes = [vp]
     lib.wos_solve_batch.argtypes = [vp, vp, vp, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
@@ -144,6 +145,7 @@ class Problem:
         self.dim = desc["dim"]
         self._keep = []
         self._sigma_ptr = 0
+        self._alpha_ptr = 0
         D = ProblemDesc()
         D.dim = desc["dim"]
         D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
@@ -182,6 +184,8 @@ class Problem:
                 F.data = data.data_ptr()
                 if name == "sigma":
                     self._sigma_ptr = data.data_ptr()
+                if name == "alpha":
+                    self._alpha_ptr = data.data_ptr()
         h = C.c_void_p()
         ctx._check(ctx.lib.wos_problem_create(ctx.handle, C.byref(D), C.byref(h)))
         self.handle = h
@@ -189,6 +193,10 @@ class Problem:
     def sigma_data_ptr(self):
         """Device address of the sigma grid the problem reads (0 if sigma is not a grid)."""
         return self._sigma_ptr
+
+    def alpha_data_ptr(self):
+        """Device address of the alpha grid the problem reads (0 if alpha is not a grid)."""
+        return self._alpha_ptr
 
     def close(self):
         if getattr(self, "handle", None):
@@ -478,6 +486,22 @@ class Context:
         self._check(self.lib.wos_adjoint_sigma(self.handle, prob.handle, _ptr(pts), npts, int(walks), C.byref(p),
                                                _ptr(grad_u), _ptr(grad_sigma), _ptr(stats), _stream(stream)))
         return grad_sigma
+
+    def adjoint_alpha(self, prob, pts, walks, grad_u, grad_alpha, eps, sigma_bar, seed=0, walk_offset=0,
+                      max_steps=1 << 20, precision="fp32", stats=None, stream=None):
+        """Add d(sum_p grad_u[p] mean_p)/d(alpha B-spline grid) to grad_alpha (CUDA float64, grid-sized)."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        if not (grad_u.is_cuda and grad_u.dtype == torch.float64 and grad_u.shape == (npts,)):
+            raise TypeError("grad_u must be a CUDA float64 tensor of shape [npts]")
+        if not (grad_alpha.is_cuda and grad_alpha.dtype == torch.float64 and grad_alpha.is_contiguous()):
+            raise TypeError("grad_alpha must be a contiguous CUDA float64 tensor")
+        grad_u = grad_u.contiguous()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_adjoint_alpha(self.handle, prob.handle, _ptr(pts), npts, int(walks), C.byref(p),
+                                               _ptr(grad_u), _ptr(grad_alpha), _ptr(stats), _stream(stream)))
+        return grad_alpha
 
     def solve_host(self, prob, pts_host, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
                    precision="fp32", out=None, stream=None):

@@ -18,6 +18,21 @@
 //     c * (A - P_{j+1}) / w_j * (-N_m(y_j) / (alpha(y_j) sigma_bar))
 // to the gradient of node m, c = grad_u[p] e^{-gamma(x_0)} / (walks of point p).
 // The estimator's paths are not stored (path replay).
+//
+// ALPHA: the gradient with respect to the control values alpha_m of a cubic
+// B-spline alpha grid.  alpha enters through gamma = (ln alpha + Phi)/2, so
+// through e^{-gamma(x_0)}, the sources f'(y) = e^{gamma} f / alpha, the null
+// weights through sigma' = sigma/alpha + Lap gamma + |grad gamma|^2, and the
+// boundary factor e^{gamma(x_n)} (Sec. 4.1, App. A).  With N_m the basis function
+// of node m, d gamma / d alpha_m = N_m / (2 alpha) and d ln f' / d alpha_m = -N_m/(2 alpha);
+// d sigma'/d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m with
+//   cN = -sigma/alpha^2 - Lap alpha/(2 alpha^2) + |grad alpha|^2/alpha^3 - grad gamma . grad alpha/alpha^2,
+//   cG = grad gamma/alpha - grad alpha/alpha^2,   cL = 1/(2 alpha).
+// So the replay scatters, per step k at y_k, c W_k |G_k| f'_k (-1/(2 alpha)) N_m plus,
+// at a null event, c (A - P_{k+1})/w_k (-1/sigma_bar) d sigma'/d alpha_m; at the end
+// c W_n e^{gamma(x_n)} g(xbar_n) / (2 alpha(x_n)) N_m(x_n); and once per walk
+// -c A / (2 alpha(x_0)) N_m(x_0).  Small grids are accumulated per CTA in shared
+// memory (FP64 shared atomics) and added to global memory once per CTA.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -59,7 +74,74 @@ __device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, d
   }
 }
 
+// add vN N_m + vG . grad N_m + vL Lap N_m at y to grad[m] over the 4^DIM nodes of
+// the cubic B-spline support (indices clamped as in grid_bspline)
 template <int DIM, typename R>
+__device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN, const double* vG, double vL,
+                                double* grad) {
+  int ib[3] = {0, 0, 0};
+  R B[3][4], B1[3][4], B2[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { B[d][a] = (a == 0) ? R(1) : R(0); B1[d][a] = R(0); B2[d][a] = R(0); }
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = (y[d] - F.lo[d]) * F.inv_h[d];
+    R fs = floor(s);
+    ib[d] = (int)fs - 1;
+    bspline_w(s - fs, B[d], B1[d], B2[d]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      B1[d][a] *= F.inv_h[d];
+      B2[d][a] *= F.inv_h[d] * F.inv_h[d];
+    }
+  }
+  const int n2 = (DIM == 3) ? 4 : 1;
+  for (int c2 = 0; c2 < n2; ++c2) {
+    int j2 = 0;
+    if (DIM == 3) j2 = min(max(ib[2] + c2, 0), F.res[2] - 1);
+#pragma unroll
+    for (int c1 = 0; c1 < 4; ++c1) {
+      int j1 = min(max(ib[1] + c1, 0), F.res[1] - 1);
+#pragma unroll
+      for (int c0 = 0; c0 < 4; ++c0) {
+        int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
+        double b0 = B[0][c0], b1 = B[1][c1], b2 = B[2][c2];
+        double n = b0 * b1 * b2;
+        double gx = (double)B1[0][c0] * b1 * b2, gy = b0 * (double)B1[1][c1] * b2, gz = b0 * b1 * (double)B1[2][c2];
+        double lap = (double)B2[0][c0] * b1 * b2 + b0 * (double)B2[1][c1] * b2 + b0 * b1 * (double)B2[2][c2];
+        double val = vN * n + vG[0] * gx + vG[1] * gy + vL * lap;
+        if (DIM == 3) val += vG[2] * gz;
+        if (val != 0.0) atomicAdd(&grad[(int64_t)j0 + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2)], val);
+      }
+    }
+  }
+}
+
+// d sigma' / d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m at y
+template <int DIM, typename R>
+__device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, double* cN, double* cG, double* cL) {
+  FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
+  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
+  FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
+  const double a = A.v, ia = 1.0 / a;
+  const double ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
+  double na2 = 0.0, gg_ga = 0.0, gg[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    gg[d] = 0.5 * (ga[d] * ia + gp[d]);
+    na2 += ga[d] * ga[d];
+    gg_ga += gg[d] * ga[d];
+  }
+  *cN = -(double)S.v * ia * ia - 0.5 * (double)A.lap * ia * ia + na2 * ia * ia * ia - gg_ga * ia * ia;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? gg[d] * ia - ga[d] * ia * ia : 0.0;
+  *cL = 0.5 * ia;
+}
+
+template <int DIM, typename R, bool ALPHA>
 __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
@@ -67,8 +149,12 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     int4* dst = reinterpret_cast<int4*>(smem_raw);
     for (int i = threadIdx.x; i < L.problem_bytes / 16; i += blockDim.x) dst[i] = src[i];
   }
+  double* gpriv = reinterpret_cast<double*>(smem_raw + L.problem_bytes);
+  if (ALPHA && L.priv_nodes > 0)
+    for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x) gpriv[i] = 0.0;
   __syncthreads();
   const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
+  double* gtarget = ALPHA ? ((L.priv_nodes > 0) ? gpriv : L.grad_alpha) : L.grad_sigma;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
@@ -166,16 +252,32 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
 
     if (ends) {
       bool capped = (d >= eps);
-      if (!capped) acc += W * w_exp(gam) * g_at<DIM>(P, xb);
+      R bterm = R(0);
+      if (!capped) {
+        bterm = W * w_exp(gam) * g_at<DIM>(P, xb);
+        acc += bterm;
+      }
+      if (ALPHA && phase == 1 && !capped) {
+        // boundary factor e^{gamma(x_n)}: d/d alpha_m = N_m(x_n) / (2 alpha(x_n)) times the term
+        const double vG[3] = {0.0, 0.0, 0.0};
+        double v = coef * (double)bterm * 0.5 / (double)al;
+        if (isfinite(v) && v != 0.0) bspline_scatter<DIM, R>(P.alpha, y, v, vG, 0.0, gtarget);
+      }
       if (phase == 0) {
         total = acc;
 #pragma unroll
         for (int dd2 = 0; dd2 < 3; ++dd2) x[dd2] = (dd2 < DIM) ? R(__ldg(&L.pts[(int64_t)dd2 * L.npts + (int64_t)p])) : R(0);
+        if (ALPHA) {
+          // e^{-gamma(x_0)}: -A N_m(x_0) / (2 alpha(x_0))
+          const double vG[3] = {0.0, 0.0, 0.0};
+          double a0 = (double)field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
+          double v = -coef * (double)total * 0.5 / a0;
+          if (isfinite(v) && v != 0.0) bspline_scatter<DIM, R>(P.alpha, x, v, vG, 0.0, gtarget);
+        }
         W = R(1);
         acc = R(0);
         k = 0;
         phase = 1;
-        st_steps += 0;
       } else {
         ++st_walks;
         if (capped) ++st_capped;
@@ -183,10 +285,29 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
       }
       continue;
     }
-    acc += W * Gn * fpy;
+    const R src = W * Gn * fpy;
+    acc += src;
+    if (ALPHA && phase == 1) {
+      // source f'(y): d/d alpha_m = -N_m(y) / (2 alpha(y)) times the term; null weight: see above
+      double vN = -coef * (double)src * 0.5 / (double)al, vG[3] = {0.0, 0.0, 0.0}, vL = 0.0;
+      if (mu <= PB) {
+        R wj = R(1) - spy * inv_sb;
+        double rem = ((double)total - (double)acc) / (double)wj;
+        double rj = -coef * rem / (double)L.sigma_bar;
+        double cN, cG[3], cL;
+        alpha_sensitivity<DIM, R>(P, y, &cN, cG, &cL);
+        if (isfinite(rj)) {
+          vN += rj * cN;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) vG[i] = rj * cG[i];
+          vL = rj * cL;
+        }
+      }
+      if (isfinite(vN)) bspline_scatter<DIM, R>(P.alpha, y, vN, vG, vL, gtarget);
+    }
     if (mu <= PB) {
       R wj = R(1) - spy * inv_sb;
-      if (phase == 1) {
+      if (!ALPHA && phase == 1) {
         // d total / d w_j = (A - P_{j+1}) / w_j ; d w_j / d sigma_m = -N_m(y) / (alpha(y) sigma_bar)
         double rem = ((double)total - (double)acc) / (double)wj;
         double val = -coef * rem / ((double)al * (double)L.sigma_bar);
@@ -213,20 +334,36 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     atomicAdd(&L.stats[ST_WALKS], (unsigned long long)st_walks);
     if (st_capped) atomicAdd(&L.stats[ST_CAPPED], (unsigned long long)st_capped);
   }
+  if (ALPHA && L.priv_nodes > 0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x)
+      if (gpriv[i] != 0.0) atomicAdd(&L.grad_alpha[i], gpriv[i]);
+  }
 }
 
-template <int DIM, typename R>
-cudaError_t launch_adjoint_t(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
-  size_t smem = (size_t)L.problem_bytes;
+template <int DIM, typename R, bool ALPHA>
+cudaError_t launch_adjoint_m(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
+  size_t smem = (size_t)L.problem_bytes + (ALPHA ? (size_t)L.priv_nodes * sizeof(double) : 0);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(wos_adjoint_kernel<DIM, R, ALPHA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_adjoint_kernel<DIM, R>, kAdjBlock, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_adjoint_kernel<DIM, R, ALPHA>, kAdjBlock,
+                                                                smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
   uint64_t blocks_needed = (L.total_items + kAdjBlock - 1) / kAdjBlock;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_adjoint_kernel<DIM, R><<<grid, kAdjBlock, smem, stream>>>(L);
+  wos_adjoint_kernel<DIM, R, ALPHA><<<grid, kAdjBlock, smem, stream>>>(L);
   return cudaGetLastError();
+}
+
+template <int DIM, typename R>
+cudaError_t launch_adjoint_t(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
+  return L.alpha ? launch_adjoint_m<DIM, R, true>(L, num_sms, stream) : launch_adjoint_m<DIM, R, false>(L, num_sms, stream);
 }
 
 }  // namespace wos

@@ -868,6 +868,61 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
   return WOS_OK;
 }
 
+extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts,
+                                 int32_t walks_uniform, const wos_params* prm, const double* grad_u,
+                                 double* grad_alpha, uint64_t* stats, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  int rc = validate_params(ctx, prm);
+  if (rc) return rc;
+  if ((rc = no_window(ctx, prm))) return rc;
+  if (npts < 0 || walks_uniform < 0) return fail(ctx, WOS_EINVAL, "negative size");
+  if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
+  if (npts == 0 || walks_uniform == 0) return WOS_OK;
+  if (!pts || !grad_u || !grad_alpha) return fail(ctx, WOS_EINVAL, "null device array");
+  const DevProblem<double>& H = pr->host64;
+  if (H.alpha.kind != wos::F_GRID_BSPLINE)
+    return fail(ctx, WOS_EUNSUPPORTED, "the alpha gradient needs alpha given as a B-spline grid");
+  if (H.f.kind == wos::F_MANUFACTURED)
+    return fail(ctx, WOS_EUNSUPPORTED, "a manufactured source depends on alpha; give f explicitly");
+  int64_t nodes = (int64_t)H.alpha.res[0] * H.alpha.res[1] * (pr->dim == 3 ? H.alpha.res[2] : 1);
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
+  wos::AdjLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.dim = pr->dim;
+  L.pts = pts;
+  L.npts = npts;
+  L.walks_uniform = walks_uniform;
+  L.total_items = (uint64_t)npts * (uint64_t)walks_uniform;
+  L.seed = prm->seed;
+  L.walk_offset = prm->walk_offset;
+  L.eps = prm->eps;
+  L.sigma_bar = prm->sigma_bar;
+  L.max_steps = prm->max_steps;
+  L.grad_u = grad_u;
+  L.grad_alpha = grad_alpha;
+  L.alpha = 1;
+  L.stats = reinterpret_cast<unsigned long long*>(stats);
+  L.work_counter = ctx->scratch;
+  L.radial_tab = ctx->radial_tab[pr->dim - 2];
+  // grids of up to 8192 nodes (64 KB of FP64) are accumulated per CTA in shared memory
+  L.priv_nodes = (nodes <= 8192) ? (int)nodes : 0;
+  if (prm->precision == WOS_FP64) {
+    L.problem = pr->d64;
+    L.problem_bytes = (int)sizeof(DevProblem<double>);
+    e = wos::launch_adjoint_f64(L, ctx->num_sms, st);
+  } else {
+    L.problem = pr->d32;
+    L.problem_bytes = (int)sizeof(DevProblem<float>);
+    e = wos::launch_adjoint_f32(L, ctx->num_sms, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+  return WOS_OK;
+}
+
 extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, int32_t nprob,
                                 const int64_t* pt_offsets, const double* sigma_bars, wos_batch** out) {
   if (!ctx) return WOS_EINVAL;

@@ -64,7 +64,10 @@ struct AdjLaunch {
   double sigma_bar;
   int64_t max_steps;
   const double* grad_u;           // [npts]
-  double* grad_sigma;             // [sigma grid nodes], accumulated
+  double* grad_sigma;             // [sigma grid nodes], accumulated (sigma launches)
+  double* grad_alpha;             // [alpha grid nodes], accumulated (alpha launches)
+  int alpha;                      // 1: gradient with respect to the alpha B-spline grid
+  int priv_nodes;                 // > 0: accumulate per CTA in shared memory over this many nodes
   unsigned long long* stats;      // optional
   unsigned long long* work_counter;
   const float* radial_tab;

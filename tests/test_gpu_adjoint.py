@@ -1,7 +1,8 @@
-"""The path-replay sigma gradient (wos_adjoint_sigma) against the oracle's central
-finite differences with common random numbers: the oracle reruns the same walks
-(same seed and walk ids) with one sigma node moved by +-h; given sigma_bar the
-paths do not move, so the difference quotient has no Monte Carlo noise."""
+"""The path-replay gradients (wos_adjoint_sigma, wos_adjoint_alpha) against the
+oracle's central finite differences with common random numbers: the oracle reruns
+the same walks (same seed and walk ids) with one sigma or alpha node moved by +-h;
+given sigma_bar the paths do not move, so the difference quotient has no Monte
+Carlo noise."""
 import numpy as np
 import pytest
 
@@ -107,3 +108,65 @@ def test_autograd_function_and_descent(wos, orc, setup):
             sigma -= 0.5 * sigma.grad / sigma.grad.abs().max()
             sigma.clamp_(0.0, 20.0)
     assert losses[-1] < losses[0]
+
+
+def oracle_fd_alpha(orc, sig, alpha, pts, grad_u, node, walks, seed, sb, h):
+    """sum_p grad_u[p] d mean_p / d alpha_node (B-spline control value) on the same walks."""
+    vals, nodes = [], []
+    for s in (+1, -1):
+        a = alpha.copy().reshape(-1)
+        a[node] += s * h
+        nodes.append(float(a[node]))
+        desc = W.inverse_problem(sig, a.reshape(alpha.shape))
+        uh, _ = orc.walks(desc, pts, walks, seed=seed, eps=1e-4, sigma_bar=sb)
+        vals.append((grad_u * uh.mean(axis=1)).sum())
+    return (vals[0] - vals[1]) / (nodes[0] - nodes[1])
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32", 5e-2)])
+def test_alpha_adjoint_matches_crn_central_differences(wos, orc, setup, precision, rtol):
+    """The alpha-grid gradient (e^{-gamma(x0)}, f', the null weights through sigma', and
+    e^{gamma(x_n)}) against central differences of the oracle on the same walks."""
+    sig, desc, sb, pts, grad_u = setup
+    alpha = W.inverse_alpha_grid()
+    ctx = wos.Context(0)
+    d = dict(desc)
+    d["sigma"] = dict(desc["sigma"], data=torch.from_numpy(sig).cuda())
+    d["alpha"] = dict(desc["alpha"], data=torch.from_numpy(alpha).cuda())
+    prob = ctx.problem(d)
+    walks, seed = 32, 11
+    grad = torch.zeros(alpha.size, dtype=torch.float64, device="cuda")
+    ctx.adjoint_alpha(prob, torch.from_numpy(pts).cuda(), walks, torch.from_numpy(grad_u).cuda(), grad, 1e-4, sb,
+                      seed=seed, precision=precision)
+    g = grad.cpu().numpy()
+    assert np.isfinite(g).all() and np.abs(g).sum() > 0
+    n = alpha.shape[0]
+    for i in range(6):
+        x = pts[:, i]
+        ijk = np.clip(np.floor(x * (n - 1)).astype(int) + (i % 2), 0, n - 1)
+        node = int(ijk[0] + n * (ijk[1] + n * ijk[2]))
+        fd = oracle_fd_alpha(orc, sig, alpha, pts, grad_u, node, walks, seed, sb, h=1e-3)
+        scale = max(abs(fd), 1e-3 * np.abs(g).max())
+        assert abs(g[node] - fd) <= rtol * scale, (precision, node, g[node], fd)
+
+
+def test_coefficient_solve_backward_matches_adjoints(wos, orc, setup):
+    from paper_2201_13240_gb300.autograd import CoefficientSolve
+    sig, desc, sb, _, _ = setup
+    ctx = wos.Context(0)
+    pts = torch.from_numpy(W.inverse_sensors(128, seed=8)).cuda()
+    s_t = torch.from_numpy(sig).cuda().requires_grad_(True)
+    a_t = torch.from_numpy(W.inverse_alpha_grid()).cuda().requires_grad_(True)
+    d = dict(desc)
+    d["sigma"] = dict(desc["sigma"], data=s_t.detach())
+    d["alpha"] = dict(desc["alpha"], data=a_t.detach())
+    prob = ctx.problem(d)
+    u = CoefficientSolve.apply(s_t, a_t, ctx, prob, pts, 64, 1e-4, sb, 5)
+    w = torch.linspace(-1, 1, u.numel(), device="cuda", dtype=torch.float64)
+    (u * w).sum().backward()
+    rs = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+    ra = torch.zeros(a_t.numel(), dtype=torch.float64, device="cuda")
+    ctx.adjoint_sigma(prob, pts, 64, w, rs, 1e-4, sb, seed=5)
+    ctx.adjoint_alpha(prob, pts, 64, w, ra, 1e-4, sb, seed=5)
+    assert torch.allclose(s_t.grad.reshape(-1).double(), rs, rtol=1e-5, atol=1e-9)
+    assert torch.allclose(a_t.grad.reshape(-1).double(), ra, rtol=1e-5, atol=1e-9)
