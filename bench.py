@@ -369,7 +369,13 @@ def run_other(args):
         (acc0, st0), ms0 = timed(lambda i: ctx.solve(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
         gm, gv, gse = (t.cpu().numpy() for t in ctx.finalize_grad(gacc, acc[2]))
         exact = W.cube3d_exact_grad(*pts_np.astype(np.float64))
+        # the first ball of a point at distance d weights by ~1/d: near the boundary the
+        # gradient estimate is far noisier, so the error is reported for d >= 0.1 too
+        dist = np.minimum(pts_np, 1.0 - pts_np).min(axis=0)
+        inner = dist >= 0.1
         extra["grad_normalised_rms"] = float(np.linalg.norm(gm - exact) / np.linalg.norm(exact))
+        extra["grad_normalised_rms_d_ge_0.1"] = float(np.linalg.norm((gm - exact)[:, inner]) /
+                                                      np.linalg.norm(exact[:, inner]))
         extra["value_only_ms"] = ms0
         extra["grad_over_value_time"] = ms / ms0
         cfg = {"workload": f"cube3d_drift_manufactured with grad u (Supplemental Sec. 2): {GRID}^3 points x "
