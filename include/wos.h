@@ -104,14 +104,40 @@ enum {
   WOS_DOMAIN_BALL = 1,        /* p[0..2] centre, p[3] radius (a disk in 2D) */
   WOS_DOMAIN_ANNULUS = 2,     /* p[0..2] centre, p[3] inner radius, p[4] outer radius */
   WOS_DOMAIN_ROUNDED_BOX = 3, /* p[0..2] centre, p[3..5] half extents, p[6] corner radius */
-  WOS_DOMAIN_MESH = 4         /* 3D closed triangle mesh: verts / tris below */
+  WOS_DOMAIN_MESH = 4,        /* 3D closed triangle mesh: verts / tris below */
+  WOS_DOMAIN_CSG = 5          /* signed-distance CSG list: csg / ncsg below; p[0..5] a bounding box */
 };
+
+/* CSG primitives (signed distance, negative inside) and operations for WOS_DOMAIN_CSG
+   (Sec. 7.2: domains given as a list of signed-distance CSG operations).  Node 0 starts
+   the list (its op is ignored); node i then combines d = op(d, prim_i):
+   UNION min(d, s), INTERSECT max(d, s), SUBTRACT max(d, -s). */
+enum {
+  WOS_CSG_SPHERE = 0,    /* p[0..2] centre, p[3] radius (a disk in 2D) */
+  WOS_CSG_BOX = 1,       /* p[0..2] centre, p[3..5] half extents, p[6] corner radius (0: sharp) */
+  WOS_CSG_CAPSULE = 2,   /* p[0..2] end a, p[3..5] end b, p[6] radius */
+  WOS_CSG_TORUS = 3,     /* p[0..2] centre, p[3] major radius, p[4] minor radius; axis z (2D: a ring) */
+  WOS_CSG_HALFSPACE = 4  /* p[0..2] a point on the plane, p[3..5] outward normal: the side it points away from */
+};
+enum { WOS_CSG_UNION = 0, WOS_CSG_INTERSECT = 1, WOS_CSG_SUBTRACT = 2 };
+typedef struct {
+  int32_t prim;
+  int32_t op;
+  double p[8];
+} wos_csg_node;
+#define WOS_CSG_MAX_NODES 16
 
 /* Domain.  For WOS_DOMAIN_MESH, verts (HOST float32 [nverts][3]) and tris (HOST int32
    [ntris][3], indices into verts) describe a closed surface; wos_problem_create builds
    a bounding volume hierarchy for closest-point queries (Sec. 7.1) and keeps its own
    copy, so the arrays may be freed afterwards.  Distances to a mesh are unsigned:
-   points must lie inside the surface (the library cannot tell). */
+   points must lie inside the surface (the library cannot tell).
+   For WOS_DOMAIN_CSG, csg (HOST, ncsg in 1..WOS_CSG_MAX_NODES nodes, copied) lists the
+   operations and p[0..2], p[3..5] the corners of a box containing the domain (used for the
+   sigma_bar lattice).  The walk's ball radius is -sdf(x): for a CSG of exact primitive
+   distances this is a lower bound of the distance to the boundary, so the ball lies in the
+   domain (any such ball keeps the estimator unbiased; a smaller one only costs steps).
+   The closest point is x - sdf(x) grad sdf(x) with the active primitive's gradient. */
 typedef struct {
   int32_t kind;
   double p[16];
@@ -119,6 +145,8 @@ typedef struct {
   int64_t nverts;
   const int32_t* tris;
   int64_t ntris;
+  const wos_csg_node* csg;
+  int32_t ncsg;
 } wos_domain_desc;
 
 /* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift

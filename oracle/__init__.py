@@ -26,7 +26,7 @@ _lib = None
 
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4,
                 "grid_bspline": 5}
-_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4}
+_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4, "csg": 5}
 
 
 def build(force: bool = False) -> str:
@@ -54,10 +54,14 @@ class Field(C.Structure):
                 ("hi", C.c_double * 3), ("data", C.POINTER(C.c_float))]
 
 
+class CsgNode(C.Structure):
+    _fields_ = [("prim", C.c_int32), ("op", C.c_int32), ("p", C.c_double * 8)]
+
+
 class Domain(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.POINTER(C.c_float)),
                 ("nverts", C.c_int64), ("tris", C.POINTER(C.c_int32)), ("ntris", C.c_int64),
-                ("bvh", C.c_void_p)]
+                ("bvh", C.c_void_p), ("csg", C.POINTER(CsgNode)), ("ncsg", C.c_int32)]
 
 
 class Problem(C.Structure):
@@ -149,6 +153,17 @@ class _Packed:
             P.domain.p[i] = v
         for name in ("alpha", "phi", "sigma", "f", "g", "um"):
             self._field(getattr(P, name), prob[name])
+        if dom["kind"] == "csg":
+            prims = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
+            ops = {"union": 0, "intersect": 1, "subtract": 2}
+            arr = (CsgNode * len(dom["nodes"]))()
+            for i, (prim, op, prm) in enumerate(dom["nodes"]):
+                arr[i].prim, arr[i].op = prims[prim], ops[op]
+                for k, v in enumerate(prm):
+                    arr[i].p[k] = v
+            self.keep.append(arr)
+            P.domain.csg = C.cast(arr, C.POINTER(CsgNode))
+            P.domain.ncsg = len(dom["nodes"])
         if dom["kind"] == "mesh":
             key = (id(dom["verts"]), id(dom["tris"]))
             if key not in _mesh_cache:

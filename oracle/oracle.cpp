@@ -617,6 +617,103 @@ double mesh_distance(const orc_domain& D, const double* x, double* xb) {
 // ---------------------------------------------------------------------------
 // Distance to the boundary (Alg. 1 "DistanceToBoundary"), analytic shapes.
 // ---------------------------------------------------------------------------
+// Signed distance of one CSG primitive and its gradient (standard exact distances).
+double csg_one(const orc_csg_node& n, int dim, const double* x, double* grad) {
+  const double* p = n.p;
+  for (int d = 0; d < 3; ++d) grad[d] = 0.0;
+  if (n.prim == 0 || n.prim == 2) {
+    // sphere: distance to the centre; capsule: distance to the segment a-b
+    double c[3] = {p[0], p[1], p[2]};
+    double rad = p[3];
+    if (n.prim == 2) {
+      double ab[3] = {0, 0, 0}, t = 0.0, l2 = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        ab[d] = p[3 + d] - p[d];
+        t += ab[d] * (x[d] - p[d]);
+        l2 += ab[d] * ab[d];
+      }
+      t = l2 > 0.0 ? std::min(1.0, std::max(0.0, t / l2)) : 0.0;
+      for (int d = 0; d < dim; ++d) c[d] = p[d] + t * ab[d];
+      rad = p[6];
+    }
+    double r2 = 0.0;
+    for (int d = 0; d < dim; ++d) r2 += (x[d] - c[d]) * (x[d] - c[d]);
+    double r = std::sqrt(r2);
+    if (r > 0.0) {
+      for (int d = 0; d < dim; ++d) grad[d] = (x[d] - c[d]) / r;
+    } else {
+      grad[0] = 1.0;
+    }
+    return r - rad;
+  }
+  if (n.prim == 1) {
+    // rounded box: the inner box (half extents - corner) grown by the corner radius
+    double rc = p[6], q[3] = {0, 0, 0}, out2 = 0.0, qmax = -INFINITY;
+    int imax = 0;
+    for (int d = 0; d < dim; ++d) {
+      q[d] = std::fabs(x[d] - p[d]) - (p[3 + d] - rc);
+      if (q[d] > 0.0) out2 += q[d] * q[d];
+      if (q[d] > qmax) { qmax = q[d]; imax = d; }
+    }
+    if (out2 > 0.0) {
+      double od = std::sqrt(out2);
+      for (int d = 0; d < dim; ++d)
+        grad[d] = q[d] > 0.0 ? ((x[d] >= p[d]) ? 1.0 : -1.0) * q[d] / od : 0.0;
+      return od - rc;
+    }
+    grad[imax] = (x[imax] >= p[imax]) ? 1.0 : -1.0;
+    return qmax - rc;
+  }
+  if (n.prim == 3) {
+    double v0 = x[0] - p[0], v1 = x[1] - p[1];
+    double rr = std::sqrt(v0 * v0 + v1 * v1);
+    if (dim == 2) {
+      double q = rr - p[3];
+      double sg = q >= 0.0 ? 1.0 : -1.0;
+      if (rr > 0.0) { grad[0] = sg * v0 / rr; grad[1] = sg * v1 / rr; } else { grad[0] = -1.0; }
+      return std::fabs(q) - p[4];
+    }
+    double q0 = rr - p[3], q1 = x[2] - p[2];
+    double ql = std::sqrt(q0 * q0 + q1 * q1);
+    if (ql > 0.0 && rr > 0.0) {
+      grad[0] = q0 / ql * v0 / rr;
+      grad[1] = q0 / ql * v1 / rr;
+      grad[2] = q1 / ql;
+    }
+    return ql - p[4];
+  }
+  // half-space with unit outward normal
+  double nn = 0.0;
+  for (int d = 0; d < dim; ++d) nn += p[3 + d] * p[3 + d];
+  nn = std::sqrt(nn);
+  double sd = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    grad[d] = p[3 + d] / nn;
+    sd += grad[d] * (x[d] - p[d]);
+  }
+  return sd;
+}
+
+double csg_eval(const orc_problem* P, const double* x, double* grad) {
+  const orc_domain& D = P->domain;
+  double d = csg_one(D.csg[0], P->dim, x, grad);
+  for (int i = 1; i < D.ncsg; ++i) {
+    double g[3];
+    double s = csg_one(D.csg[i], P->dim, x, g);
+    int op = D.csg[i].op;
+    if (op == 2) {
+      s = -s;
+      for (int k = 0; k < 3; ++k) g[k] = -g[k];
+    }
+    bool take = (op == 0) ? (s < d) : (s > d);
+    if (take) {
+      d = s;
+      for (int k = 0; k < 3; ++k) grad[k] = g[k];
+    }
+  }
+  return d;
+}
+
 double distance(const orc_problem* P, const double* x, double* xb) {
   int dim = P->dim;
   const double* p = P->domain.p;
@@ -651,6 +748,12 @@ double distance(const orc_problem* P, const double* x, double* xb) {
       if (r == 0.0) { v[0] = 1.0; r = 1.0; }
       for (int d = 0; d < dim; ++d) xb[d] = p[d] + v[d] / r * rad;
       return (din < dout) ? din : dout;
+    }
+    case ORC_DOM_CSG: {
+      double g[3];
+      double sd = csg_eval(P, x, g);
+      for (int d = 0; d < dim; ++d) xb[d] = x[d] - sd * g[d];
+      return -sd;
     }
     case ORC_DOM_ROUNDED_BOX: {
       // Minkowski sum of the inner box (half extents b - rc) and a ball of radius rc
@@ -690,7 +793,8 @@ void domain_bbox(const orc_problem* P, double lo[3], double hi[3]) {
   for (int d = 0; d < 3; ++d) { lo[d] = 0.0; hi[d] = 0.0; }
   for (int d = 0; d < P->dim; ++d) {
     switch (P->domain.kind) {
-      case ORC_DOM_BOX: lo[d] = p[d]; hi[d] = p[3 + d]; break;
+      case ORC_DOM_BOX:
+      case ORC_DOM_CSG: lo[d] = p[d]; hi[d] = p[3 + d]; break;
       case ORC_DOM_BALL: lo[d] = p[d] - p[3]; hi[d] = p[d] + p[3]; break;
       case ORC_DOM_ANNULUS: lo[d] = p[d] - p[4]; hi[d] = p[d] + p[4]; break;
       case ORC_DOM_ROUNDED_BOX: lo[d] = p[d] - p[3 + d]; hi[d] = p[d] + p[3 + d]; break;

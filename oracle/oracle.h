@@ -58,7 +58,17 @@ typedef struct {
 } orc_field;
 
 enum { ORC_DOM_BOX = 0, ORC_DOM_BALL = 1, ORC_DOM_ANNULUS = 2,
-       ORC_DOM_ROUNDED_BOX = 3, ORC_DOM_MESH = 4 };
+       ORC_DOM_ROUNDED_BOX = 3, ORC_DOM_MESH = 4, ORC_DOM_CSG = 5 };
+
+/* one signed-distance CSG node (Sec. 7.2): prim 0 sphere (centre, radius), 1 box
+   (centre, half extents, corner radius), 2 capsule (a, b, radius), 3 torus (centre,
+   major, minor radius; axis z; 2D: a ring), 4 half-space (point, outward normal);
+   op 0 union (min), 1 intersection (max), 2 subtraction (max(d, -s)). */
+typedef struct {
+  int32_t prim;
+  int32_t op;
+  double p[8];
+} orc_csg_node;
 
 typedef struct {
   int32_t kind;
@@ -74,6 +84,10 @@ typedef struct {
   const int32_t* tris;
   int64_t ntris;
   void* bvh;
+  /* CSG: nodes combined left to right; p[0..5] bound the domain.  The ball radius is
+     -sdf(x) and the closest point x - sdf(x) grad sdf(x). */
+  const orc_csg_node* csg;
+  int32_t ncsg;
 } orc_domain;
 
 typedef struct {

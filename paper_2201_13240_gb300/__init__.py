@@ -25,7 +25,9 @@ WOS_FP32, WOS_FP64 = 0, 1
 STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
 STATS_WORDS = 6
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
-_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4}
+_DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4, "csg": 5}
+_CSG_PRIMS = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
+_CSG_OPS = {"union": 0, "intersect": 1, "subtract": 2}
 
 
 class WosError(RuntimeError):
@@ -44,9 +46,13 @@ class FieldDesc(C.Structure):
                 ("data", C.c_void_p)]
 
 
+class CsgNode(C.Structure):
+    _fields_ = [("prim", C.c_int32), ("op", C.c_int32), ("p", C.c_double * 8)]
+
+
 class DomainDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.c_void_p), ("nverts", C.c_int64),
-                ("tris", C.c_void_p), ("ntris", C.c_int64)]
+                ("tris", C.c_void_p), ("ntris", C.c_int64), ("csg", C.c_void_p), ("ncsg", C.c_int32)]
 
 
 class ProblemDesc(C.Structure):
@@ -157,6 +163,17 @@ class Problem:
             self._keep += [verts, tris]
             D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
             D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
+        if desc["domain"]["kind"] == "csg":
+            nodes = desc["domain"]["nodes"]
+            arr = (CsgNode * max(1, len(nodes)))()
+            for i, (prim, op, prm) in enumerate(nodes):
+                arr[i].prim = _CSG_PRIMS[prim]
+                arr[i].op = _CSG_OPS[op]
+                for k, v in enumerate(prm):
+                    arr[i].p[k] = v
+            self._keep.append(arr)
+            D.domain.csg = C.cast(arr, C.c_void_p)
+            D.domain.ncsg = len(nodes)
         for name in ("alpha", "phi", "sigma", "f", "g", "um"):
             fd = desc[name]
             F = getattr(D, name)

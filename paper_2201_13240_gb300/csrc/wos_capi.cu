@@ -173,6 +173,23 @@ void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
   P.dim = d.dim;
   P.domain_kind = d.domain.kind;
   for (int i = 0; i < 16; ++i) P.dom[i] = R(d.domain.p[i]);
+  if (d.domain.kind == WOS_DOMAIN_CSG && d.domain.csg) {
+    P.ncsg = d.domain.ncsg;
+    for (int i = 0; i < d.domain.ncsg && i < wos::kMaxCsg; ++i) {
+      const wos_csg_node& n = d.domain.csg[i];
+      P.csg[i].prim = n.prim;
+      P.csg[i].op = n.op;
+      double q[8];
+      for (int k = 0; k < 8; ++k) q[k] = n.p[k];
+      if (n.prim == WOS_CSG_HALFSPACE) {  // unit normal
+        double nn = 0;
+        for (int k = 0; k < d.dim; ++k) nn += q[3 + k] * q[3 + k];
+        nn = std::sqrt(nn);
+        for (int k = 0; k < 3; ++k) q[3 + k] = (k < d.dim) ? q[3 + k] / nn : 0.0;
+      }
+      for (int k = 0; k < 8; ++k) P.csg[i].p[k] = R(q[k]);
+    }
+  }
   fill_field(P, P.alpha, d.alpha, d.dim);
   fill_field(P, P.phi, d.phi, d.dim);
   fill_field(P, P.sigma, d.sigma, d.dim);
@@ -191,7 +208,8 @@ void domain_bbox(const wos_problem* pr, double lo[3], double hi[3]) {
   for (int d = 0; d < 3; ++d) { lo[d] = 0.0; hi[d] = 0.0; }
   for (int d = 0; d < P.dim; ++d) {
     switch (P.domain_kind) {
-      case wos::D_BOX: lo[d] = p[d]; hi[d] = p[3 + d]; break;
+      case wos::D_BOX:
+      case wos::D_CSG: lo[d] = p[d]; hi[d] = p[3 + d]; break;
       case wos::D_BALL: lo[d] = p[d] - p[3]; hi[d] = p[d] + p[3]; break;
       case wos::D_ANNULUS: lo[d] = p[d] - p[4]; hi[d] = p[d] + p[4]; break;
       case wos::D_ROUNDED_BOX: lo[d] = p[d] - p[3 + d]; hi[d] = p[d] + p[3 + d]; break;
@@ -481,6 +499,36 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
       if (!d->domain.verts || !d->domain.tris || d->domain.nverts < 3 || d->domain.ntris < 1)
         return fail(ctx, WOS_EINVAL, "mesh: need vertices and triangles");
       break;
+    case WOS_DOMAIN_CSG: {
+      if (!d->domain.csg || d->domain.ncsg < 1 || d->domain.ncsg > WOS_CSG_MAX_NODES)
+        return fail(ctx, WOS_EINVAL, "csg: need 1..16 nodes");
+      for (int i = 0; i < d->dim; ++i)
+        if (!(p[3 + i] > p[i])) return fail(ctx, WOS_EINVAL, "csg: the bounding box needs hi > lo");
+      for (int i = 0; i < d->domain.ncsg; ++i) {
+        const wos_csg_node& n = d->domain.csg[i];
+        for (int k = 0; k < 8; ++k)
+          if (!std::isfinite(n.p[k])) return fail(ctx, WOS_EINVAL, "csg: non-finite parameter");
+        if (n.prim < WOS_CSG_SPHERE || n.prim > WOS_CSG_HALFSPACE) return fail(ctx, WOS_EINVAL, "csg: unknown primitive");
+        if (i > 0 && (n.op < WOS_CSG_UNION || n.op > WOS_CSG_SUBTRACT)) return fail(ctx, WOS_EINVAL, "csg: unknown operation");
+        bool ok = true;
+        switch (n.prim) {
+          case WOS_CSG_SPHERE: ok = n.p[3] > 0; break;
+          case WOS_CSG_BOX:
+            for (int k = 0; k < d->dim; ++k) ok = ok && n.p[3 + k] > 0 && n.p[6] >= 0 && n.p[6] <= n.p[3 + k];
+            break;
+          case WOS_CSG_CAPSULE: ok = n.p[6] > 0; break;
+          case WOS_CSG_TORUS: ok = n.p[3] > 0 && n.p[4] > 0; break;
+          case WOS_CSG_HALFSPACE: {
+            double nn = 0;
+            for (int k = 0; k < d->dim; ++k) nn += n.p[3 + k] * n.p[3 + k];
+            ok = nn > 0;
+            break;
+          }
+        }
+        if (!ok) return fail(ctx, WOS_EINVAL, "csg: invalid primitive parameters");
+      }
+      break;
+    }
     default:
       return fail(ctx, WOS_EINVAL, "unknown domain kind");
   }

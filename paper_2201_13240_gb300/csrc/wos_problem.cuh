@@ -25,7 +25,17 @@ namespace wos {
 
 enum AtomType { A_ONE = 0, A_SIN = 1, A_COS = 2, A_EXP = 3, A_SINH = 4, A_COSH = 5, A_LIN = 6, A_QUAD = 7 };
 enum FieldKind { F_ZERO = 0, F_CONST = 1, F_SST = 2, F_MANUFACTURED = 3, F_GRID_LINEAR = 4, F_GRID_BSPLINE = 5 };
-enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3, D_MESH = 4 };
+enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3, D_MESH = 4, D_CSG = 5 };
+enum CsgPrim { C_SPHERE = 0, C_BOX = 1, C_CAPSULE = 2, C_TORUS = 3, C_HALFSPACE = 4 };
+enum CsgOp { C_UNION = 0, C_INTERSECT = 1, C_SUBTRACT = 2 };
+constexpr int kMaxCsg = 16;
+
+template <typename R>
+struct CsgNode {
+  int32_t prim;
+  int32_t op;
+  R p[8];
+};
 
 constexpr int kMaxTerms = 96;  // separable terms over all fields of one problem
 
@@ -61,6 +71,9 @@ struct DevProblem {
   DevField<R> alpha, phi, sigma, f, g, um;
   const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
   const float* mesh_tris;   // 12 floats per triangle in leaf order, device
+  int32_t ncsg;
+  int32_t pad3[3];
+  CsgNode<R> csg[kMaxCsg];
   DevTerm<R> terms[kMaxTerms];
 };
 
@@ -477,6 +490,127 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
 // ---------------------------------------------------------------------------
 // distance to the boundary (positive inside) and closest boundary point
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// signed-distance CSG (Sec. 7.2): exact primitive distances combined by min / max.
+// Returns sdf(x) (negative inside) and the gradient of the active primitive.
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+WOS_HD R csg_prim(const CsgNode<R>& N, const R* x, R* g) {
+  const R* p = N.p;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[d] = R(0);
+  switch (N.prim) {
+    case C_SPHERE: {
+      R v[3] = {R(0), R(0), R(0)}, r2 = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) { v[d] = x[d] - p[d]; r2 += v[d] * v[d]; }
+      R r = w_sqrt(r2);
+      R inv = (r > R(0)) ? R(1) / r : R(0);
+      if (!(r > R(0))) g[0] = R(1);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) g[d] += v[d] * inv;
+      return r - p[3];
+    }
+    case C_BOX: {
+      R rc = p[6], q[3] = {R(0), R(0), R(0)}, sg[3] = {R(1), R(1), R(1)}, out2 = R(0), qmax = R(-1e30);
+      int imax = 0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        R rel = x[d] - p[d];
+        sg[d] = (rel >= R(0)) ? R(1) : R(-1);
+        q[d] = w_fabs(rel) - (p[3 + d] - rc);
+        if (q[d] > R(0)) out2 += q[d] * q[d];
+        if (q[d] > qmax) { qmax = q[d]; imax = d; }
+      }
+      if (out2 > R(0)) {
+        R od = w_sqrt(out2);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) g[d] = (q[d] > R(0)) ? sg[d] * q[d] / od : R(0);
+        return od - rc;
+      }
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) if (d == imax) g[d] = sg[d];
+      return qmax - rc;
+    }
+    case C_CAPSULE: {
+      R ab[3] = {R(0), R(0), R(0)}, ax[3] = {R(0), R(0), R(0)}, l2 = R(0), t = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        ab[d] = p[3 + d] - p[d];
+        ax[d] = x[d] - p[d];
+        l2 += ab[d] * ab[d];
+        t += ab[d] * ax[d];
+      }
+      t = (l2 > R(0)) ? w_fmin(w_fmax(t / l2, R(0)), R(1)) : R(0);
+      R v[3] = {R(0), R(0), R(0)}, r2 = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) { v[d] = ax[d] - t * ab[d]; r2 += v[d] * v[d]; }
+      R r = w_sqrt(r2);
+      R inv = (r > R(0)) ? R(1) / r : R(0);
+      if (!(r > R(0))) g[0] = R(1);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) g[d] += v[d] * inv;
+      return r - p[6];
+    }
+    case C_TORUS: {
+      if (DIM == 2) {  // a ring: distance to the circle of radius p[3], minus p[4]
+        R v0 = x[0] - p[0], v1 = x[1] - p[1];
+        R rr = w_sqrt(v0 * v0 + v1 * v1);
+        R q = rr - p[3];
+        R s = (q >= R(0)) ? R(1) : R(-1);
+        R inv = (rr > R(0)) ? R(1) / rr : R(0);
+        g[0] = s * v0 * inv;
+        g[1] = s * v1 * inv;
+        if (!(rr > R(0))) g[0] = R(-1);
+        return w_fabs(q) - p[4];
+      }
+      R v0 = x[0] - p[0], v1 = x[1] - p[1], v2 = x[2] - p[2];
+      R rr = w_sqrt(v0 * v0 + v1 * v1);
+      R q0 = rr - p[3], q1 = v2;
+      R ql = w_sqrt(q0 * q0 + q1 * q1);
+      R invr = (rr > R(0)) ? R(1) / rr : R(0);
+      R invq = (ql > R(0)) ? R(1) / ql : R(0);
+      g[0] = q0 * invq * v0 * invr;
+      g[1] = q0 * invq * v1 * invr;
+      g[2] = q1 * invq;
+      return ql - p[4];
+    }
+    case C_HALFSPACE: {
+      R s = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        s += p[3 + d] * (x[d] - p[d]);
+        g[d] = p[3 + d];
+      }
+      return s;
+    }
+    default:
+      return R(1e30);
+  }
+}
+
+template <int DIM, typename R>
+WOS_HD R csg_sdf(const DevProblem<R>& P, const R* x, R* g) {
+  R d = csg_prim<DIM, R>(P.csg[0], x, g);
+  for (int i = 1; i < P.ncsg; ++i) {
+    R gi[3];
+    R s = csg_prim<DIM, R>(P.csg[i], x, gi);
+    const int op = P.csg[i].op;
+    if (op == C_SUBTRACT) {
+      s = -s;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gi[k] = -gi[k];
+    }
+    const bool take = (op == C_UNION) ? (s < d) : (s > d);
+    if (take) {
+      d = s;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g[k] = gi[k];
+    }
+  }
+  return d;
+}
+
 // bound2 (meshes only): an upper bound of the squared distance, see mesh_query.
 // MESH = false compiles the mesh case out (for kernels launched on analytic domains).
 template <int DIM, typename R, bool MESH = true>
@@ -547,6 +681,14 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
       for (int d = 0; d < DIM; ++d)
         if (d == imax) xb[d] = p[d] + ((rel[d] >= R(0)) ? p[3 + d] : -p[3 + d]);
       return rc - qmax;
+    }
+    case D_CSG: {
+      // ball radius -sdf (a lower bound of the distance); closest point along the gradient
+      R g[3];
+      R sd = csg_sdf<DIM, R>(P, x, g);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) xb[d] = x[d] - sd * g[d];
+      return -sd;
     }
     case D_MESH: {
       if (DIM != 3 || !MESH) return R(-1);

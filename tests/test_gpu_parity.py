@@ -310,3 +310,33 @@ def test_fp32_matches_finite_difference_solve(ctx, orc):
     ok, nout, mz = four_se_rule((m - want) / se)
     assert ok, (nout, mz)
     assert normalised_rms(m, want) <= 1e-2
+
+
+def _csg_inside(orc, prob, n, seed, margin=0.02):
+    dim = prob["dim"]
+    lo = np.array(prob["domain"]["p"][:dim])
+    hi = np.array(prob["domain"]["p"][3:3 + dim])
+    X = lo + (hi - lo) * np.random.default_rng(seed).uniform(size=(8 * n + 4000, dim))
+    d = np.array([orc.distance(prob, x)[0] for x in X])
+    return np.ascontiguousarray(X[d > margin][:n].T.astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["csg2d", "csg3d", "csg_variable"])
+def test_csg_fp64_replay_and_fp32_parity(orc, ctx, name):
+    """Signed-distance CSG domains (Sec. 7.2): FP64 walks replay the oracle's per walk; FP32
+    estimates agree with the exact solution within 4 standard errors."""
+    desc = {"csg2d": lambda: W.csg_laplace_problem(2), "csg3d": lambda: W.csg_laplace_problem(3),
+            "csg_variable": W.csg_variable_problem}[name]()
+    pts = _csg_inside(orc, desc, 48, seed=11)
+    prob = ctx.problem(desc)
+    sb = orc.sigma_bar(desc)[0]
+    uh, st, _ = ctx.walk_estimates(prob, dev(pts), 16, 1e-4, sb, seed=3, precision="fp64")
+    uo, so = orc.walks(desc, pts, 16, seed=3, eps=1e-4, sigma_bar=sb)
+    ok = np.abs(uh.cpu().numpy() - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
+    assert ok.mean() >= 0.99 and (st.cpu().numpy() == so).mean() >= 0.99
+    m, se, s, _ = _gpu_solve(ctx, prob, pts, 8192, 1e-4, sb, seed=4)
+    p64 = pts.astype(np.float64)
+    exact = W.cube3d_exact(*p64) if name == "csg_variable" else W.csg_laplace_exact(desc["dim"], p64)
+    ok, nout, mz = four_se_rule((m - exact) / se)
+    assert ok, (nout, mz)
+    assert s[2] == 0 and s[4] == 0

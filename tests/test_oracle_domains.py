@@ -102,3 +102,88 @@ def test_distance_and_closest_point(orc, dim, dom):
         d2, _ = orc.distance(prob, xb)
         assert abs(d2) < 1e-12
     assert tested > 50
+
+
+# ---------------------------------------------------------------------------
+# signed-distance CSG domains (Sec. 7.2)
+# ---------------------------------------------------------------------------
+def _inside_points(orc, prob, n, seed, margin=0.0):
+    dim = prob["dim"]
+    lo = np.array(prob["domain"]["p"][:dim])
+    hi = np.array(prob["domain"]["p"][3:3 + dim])
+    X = lo + (hi - lo) * np.random.default_rng(seed).uniform(size=(n, dim))
+    d = np.array([orc.distance(prob, x)[0] for x in X])
+    return X[d > margin], X, d
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_csg_single_primitive_matches_analytic_domains(orc, dim):
+    """A one-node CSG list of a sphere / rounded box is the ball / rounded-box domain."""
+    c = [0.1, -0.2, 0.3][:dim]
+    cases = [(W.csg([-2] * dim, [2] * dim, ("sphere", "union", c + [0.0] * (3 - dim) + [0.8])), W.ball(c, 0.8)),
+             (W.csg([-2] * dim, [2] * dim, ("box", "union", c + [0.0] * (3 - dim) + [0.7, 0.5, 0.4][:dim] +
+                                            [0.0] * (3 - dim) + [0.1])),
+              W.rounded_box(c, [0.7, 0.5, 0.4][:dim], 0.1))]
+    rng = np.random.default_rng(dim)
+    for dom_csg, dom_ref in cases:
+        pa = W.problem(dim, dom_csg, W.const(1.0), W.zero(), W.zero(), W.zero())
+        pb = W.problem(dim, dom_ref, W.const(1.0), W.zero(), W.zero(), W.zero())
+        for x in np.array(c) + rng.uniform(-0.6, 0.6, size=(200, dim)):
+            da, xa = orc.distance(pa, x)
+            db, xb = orc.distance(pb, x)
+            if db > 1e-9:
+                assert abs(da - db) <= 1e-12 and np.allclose(xa, xb, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_csg_ball_stays_inside(orc, dim):
+    """The ball of radius -sdf(x) contains no outside point (min/max of exact primitive
+    distances bound the distance from below; the sign is exact)."""
+    prob = W.csg_laplace_problem(dim)
+    inside, X, d = _inside_points(orc, prob, 60000 if dim == 3 else 30000, seed=1)
+    outside = X[d < 0]
+    for x in inside[:300]:
+        R = orc.distance(prob, x)[0]
+        dist = np.linalg.norm(outside - x, axis=1)
+        assert dist.min() >= R * (1 - 1e-12), (x, R, dist.min())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_csg_closest_point_lies_on_the_boundary(orc, dim):
+    """Near the boundary (away from creases) x - sdf grad sdf lands on the zero set."""
+    prob = W.csg_laplace_problem(dim)
+    inside, X, d = _inside_points(orc, prob, 40000, seed=2)
+    near = X[(d > 0) & (d < 2e-3)]
+    assert len(near) > 20
+    on = 0
+    for x in near:
+        _, xb = orc.distance(prob, x)
+        if abs(orc.distance(prob, xb)[0]) <= 1e-9:
+            on += 1
+    assert on >= 0.95 * len(near)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_csg_walk_matches_harmonic_boundary_data(orc, dim):
+    """Laplace on a CSG scene with harmonic g: u = g (Kakutani), within 4 standard errors."""
+    from tests.stats_util import four_se_rule
+    prob = W.csg_laplace_problem(dim)
+    inside, _, _ = _inside_points(orc, prob, 20000, seed=3, margin=0.02)
+    pts = inside[:16].T.copy()
+    sb = orc.sigma_bar(prob)[0]
+    acc, st = orc.solve(prob, pts, 3000, seed=1, eps=1e-4, sigma_bar=sb)
+    m, v, se = orc.finalize(acc)
+    ok, nout, mz = four_se_rule((m - W.csg_laplace_exact(dim, pts)) / se)
+    assert ok and st["capped"] == 0
+
+
+def test_csg_variable_coefficients_manufactured(orc):
+    from tests.stats_util import four_se_rule
+    prob = W.csg_variable_problem()
+    inside, _, _ = _inside_points(orc, prob, 20000, seed=4, margin=0.02)
+    pts = inside[:12].T.copy()
+    sb = orc.sigma_bar(prob)[0]
+    acc, st = orc.solve(prob, pts, 3000, seed=2, eps=1e-4, sigma_bar=sb)
+    m, v, se = orc.finalize(acc)
+    ok, nout, mz = four_se_rule((m - W.cube3d_exact(*pts)) / se)
+    assert ok

@@ -94,6 +94,22 @@ def rounded_box(centre, half, corner):
     return {"kind": "rounded_box", "p": p}
 
 
+def csg(lo, hi, *nodes):
+    """Signed-distance CSG domain: nodes are (primitive, op, params) with primitive one of
+    sphere, box, capsule, torus, halfspace and op one of union, intersect, subtract (the
+    first node's op is ignored); lo, hi bound the domain."""
+    p = [0.0] * 16
+    for i, v in enumerate(lo):
+        p[i] = float(v)
+    for i, v in enumerate(hi):
+        p[3 + i] = float(v)
+    out = []
+    for prim, op, prm in nodes:
+        q = [float(v) for v in prm] + [0.0] * (8 - len(prm))
+        out.append((prim, op, q))
+    return {"kind": "csg", "p": p, "nodes": out}
+
+
 def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None):
     return {
         "dim": int(dim),
@@ -560,3 +576,51 @@ def hifreq_alpha_exact(x, y):
 def hifreq_alpha_exact_grad(x, y):
     k = 1.0 / np.sinh(1.0)
     return np.array([np.pi * np.cos(np.pi * x) * np.sinh(y) * k, np.sin(np.pi * x) * np.cosh(y) * k])
+
+
+
+# ---------------------------------------------------------------------------
+# Signed-distance CSG scenes (Sec. 7.2: domains edited as a list of SDF CSG
+# operations).  Harmonic boundary data make the exact solution the data itself.
+# ---------------------------------------------------------------------------
+def csg_scene_2d():
+    """Union of two disks minus a smaller disk and a box notch."""
+    return csg([-1.2, -1.0], [1.6, 1.0],
+               ("sphere", "union", [0.0, 0.0, 0.0, 0.9]),
+               ("sphere", "union", [0.8, 0.1, 0.0, 0.7]),
+               ("sphere", "subtract", [0.25, -0.15, 0.0, 0.3]),
+               ("box", "subtract", [-0.6, 0.7, 0.0, 0.25, 0.35, 0.0, 0.05]))
+
+
+def csg_scene_3d():
+    """A rounded box with a spherical cavity, a capsule added through it and a half-space cut."""
+    return csg([-1.3, -1.3, -1.3], [1.3, 1.3, 1.3],
+               ("box", "union", [0.0, 0.0, 0.0, 0.9, 0.7, 0.6, 0.15]),
+               ("capsule", "union", [-1.1, 0.0, 0.0, 1.1, 0.0, 0.0, 0.3]),
+               ("sphere", "subtract", [0.3, 0.2, 0.1, 0.35]),
+               ("torus", "subtract", [0.0, 0.0, 0.6, 0.45, 0.12]),
+               ("halfspace", "intersect", [0.0, -0.5, 0.0, 0.0, -1.0, 0.0]))
+
+
+def csg_laplace_problem(dim):
+    """Laplace's equation on a CSG scene with harmonic g (u = g): 2D x^2 - y^2 + x, 3D xyz + x^2 - z^2."""
+    if dim == 2:
+        u = sst(term(1.0, (QUAD, 1.0, 0.0)), term(-1.0, None, (QUAD, 1.0, 0.0)), term(1.0, (LIN, 1.0, 0.0)))
+        return problem(2, csg_scene_2d(), const(1.0), zero(), zero(), u, um=u)
+    u = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)),
+            term(1.0, (QUAD, 1.0, 0.0)), term(-1.0, None, None, (QUAD, 1.0, 0.0)))
+    return problem(3, csg_scene_3d(), const(1.0), zero(), zero(), u, um=u)
+
+
+def csg_laplace_exact(dim, x):
+    if dim == 2:
+        return x[0] ** 2 - x[1] ** 2 + x[0]
+    return x[0] * x[1] * x[2] + x[0] ** 2 - x[2] ** 2
+
+
+def csg_variable_problem():
+    """The 3D CSG scene with variable coefficients and a manufactured solution."""
+    u = sst(term(1.0, (EXP, 0.5, 0.0), (SIN, PI, 0.0), (COS, PI, 0.0)))
+    alpha = sst(term(1.0), term(0.3, (QUAD, 1.0, 0.0)), term(0.3, None, (QUAD, 1.0, 0.0)))
+    sigma = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)))
+    return problem(3, csg_scene_3d(), alpha, sigma, manufactured(), u, um=u)
