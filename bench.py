@@ -404,6 +404,39 @@ def run_other(args):
         extra["mean_stderr_over_delta_tracking"] = float(np.mean(se) / np.mean(se0))
         cfg = {"workload": f"cube3d_drift_manufactured, next-flight walks (approximate off-centred G, P): "
                            f"{GRID}^3 points x {WALKS} walks, eps 1e-4; steps count balls", "sigma_bar": sb}
+    elif wl == "slice":
+        # the interactive path (Sec. 7.2): one walk per slice point per frame plus the
+        # sphere-traced image of the CSG scene cut by the slice plane
+        desc = W.csg_variable_problem()
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 64)[0]
+        res = args.points if args.points != 16384 else 512
+        v = wos.view([-1.3, -1.3, 0.05], [2.6, 0, 0], [0, 2.6, 0], res, res, 1280, 720, (-3.0, 3.0),
+                     eye=(2.5, 2.0, 3.5), look=(0, 0, 0))
+        sv = wos.SliceView(ctx, prob, v, 1e-4, sb)
+        for _ in range(3):
+            sv.frame(1)
+        torch.cuda.synchronize()
+        nfr = max(args.steps, 1) * 10
+        stats0 = wos.stats_dict(sv.stats)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(nfr):
+            img = sv.frame(1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nfr
+        s1 = wos.stats_dict(sv.stats)
+        st = torch.tensor([s1[k] - stats0[k] for k in ("steps", "walks", "capped", "nonfinite", "outside", "inner")],
+                          dtype=torch.int64)
+        extra["frames_per_s"] = 1e3 / ms
+        extra["frames"] = nfr
+        npts = res * res
+        if args.write_image:
+            wos.write_ppm(args.write_image, img)
+        cfg = {"workload": f"CSG scene (rounded box, capsule, sphere and torus cuts, half-space) with variable "
+                           f"coefficients: {res}^2 slice points x 1 walk per frame + 1280x720 sphere-traced view, "
+                           "eps 1e-4", "sigma_bar": sb}
     elif wl == "mesh":
         desc = W.mesh_noise_problem(level=7)
         t0 = time.perf_counter()
@@ -467,6 +500,15 @@ def run_other(args):
             ctx.adjoint_sigma(prob, pts, walks, gu, grad, 1e-4, sb, seed=i, stats=stt)
             return grad, stt
         (_, sta), ms_adj = timed(adj, args.steps)
+        grad_a = torch.zeros(W.inverse_alpha_grid().size, dtype=torch.float64, device="cuda")
+
+        def adj_alpha(i):
+            grad_a.zero_()
+            ctx.adjoint_alpha(prob, pts, walks, gu, grad_a, 1e-4, sb, seed=i)
+            return grad_a
+        _, ms_adj_a = timed(adj_alpha, args.steps)
+        extra["adjoint_alpha_ms"] = ms_adj_a
+        extra["adjoint_alpha_grads_per_s_over_forward_solves_per_s"] = ms / ms_adj_a
         extra["adjoint_ms"] = ms_adj
         extra["forward_solves_per_s"] = 1e3 / ms
         extra["adjoint_grads_per_s"] = 1e3 / ms_adj
@@ -496,10 +538,11 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
     ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
-    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad", "nf"],
+    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad", "nf", "slice"],
                     help="cube3d is the benchmark; the others print supplementary measurements")
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
+    ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
     args = ap.parse_args()
     GRID, WALKS = args.grid, args.walks
     if args.impl == "reference":

@@ -352,6 +352,41 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host,
                    int32_t walks_uniform, const wos_params* params, double* mean_host,
                    double* var_host, double* stderr_host, uint64_t* stats_host, void* stream);
 
+/* ---- progressive slice view (Sec. 7.2) ----
+   The paper's interactive path: a solve on the points of a slice plane that adds one walk
+   per point per frame to the accumulators (discarding them when the problem is edited),
+   and a sphere-traced view of the domain cut by the plane.  Headless: the image goes to a
+   device buffer.  3D: a pinhole camera (eye, look-at point, up vector, vertical field of
+   view in degrees) and a slice rectangle plane_origin + a plane_u + b plane_v, a, b in
+   [0, 1), with plane_u orthogonal to plane_v.  2D: the rectangle is axis-aligned
+   (plane_u along x, plane_v along y) and fills the image; the camera is ignored.  The
+   slice grid is slice_nu x slice_nv cell centres, point index iv * slice_nu + iu.
+   Values are mapped linearly from [value_lo, value_hi] onto a blue-white-red scale. */
+typedef struct {
+  double eye[3], look[3], up[3];
+  double fov_y_deg;
+  double plane_origin[3], plane_u[3], plane_v[3];
+  int32_t slice_nu, slice_nv;
+  int32_t width, height;
+  double value_lo, value_hi;
+} wos_view;
+
+/* Write the slice grid's points, device float32 SoA [dim][slice_nu * slice_nv], for the
+   solve entry points.  Errors: WOS_EINVAL (degenerate rectangle or camera). */
+int wos_slice_points(wos_ctx* ctx, const wos_problem* prob, const wos_view* view, float* pts, void* stream);
+
+/* Render the view: per pixel a ray sphere-traced against the domain with the part on the
+   eye's side of the plane cut away (3D).  Where the ray meets the plane inside the domain
+   the pixel shows mean = sum / count of its slice cell (grey if count is 0); where it meets
+   the boundary it shows g there, Lambert-shaded by the normal of the signed distance.
+   rgba: device uint8 [height][width][4]; value: device float [height][width] with the
+   shown mean (NaN elsewhere), or NULL; depth: device float [height][width] ray parameter
+   of the hit (INFINITY on a miss; 3D only), or NULL.  sum, count: the slice points'
+   accumulators.  Errors: WOS_EINVAL (bad view, value_hi <= value_lo), WOS_EUNSUPPORTED
+   (mesh domains: their distance is unsigned). */
+int wos_render_slice(wos_ctx* ctx, const wos_problem* prob, const wos_view* view, const double* sum,
+                     const int64_t* count, uint8_t* rgba, float* value, float* depth, void* stream);
+
 /* ---- allocation-free solve ----
    The paper has no counterpart: this entry point exists for callers that cannot
    allocate device memory -- code running inside an allocator hook or a memory-pool

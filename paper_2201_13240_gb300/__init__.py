@@ -55,6 +55,30 @@ class DomainDesc(C.Structure):
                 ("tris", C.c_void_p), ("ntris", C.c_int64), ("csg", C.c_void_p), ("ncsg", C.c_int32)]
 
 
+class ViewDesc(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("look", C.c_double * 3), ("up", C.c_double * 3),
+                ("fov_y_deg", C.c_double), ("plane_origin", C.c_double * 3), ("plane_u", C.c_double * 3),
+                ("plane_v", C.c_double * 3), ("slice_nu", C.c_int32), ("slice_nv", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32), ("value_lo", C.c_double), ("value_hi", C.c_double)]
+
+
+def view(plane_origin, plane_u, plane_v, slice_nu, slice_nv, width, height, value_range, eye=(0, 0, 5),
+         look=(0, 0, 0), up=(0, 1, 0), fov_y_deg=40.0):
+    """A wos_view: slice rectangle plane_origin + a plane_u + b plane_v, its slice grid, the
+    image size, the colour range and (3D) a pinhole camera."""
+    v = ViewDesc()
+    for name, val in (("eye", eye), ("look", look), ("up", up), ("plane_origin", plane_origin),
+                      ("plane_u", plane_u), ("plane_v", plane_v)):
+        arr = getattr(v, name)
+        for k in range(3):
+            arr[k] = float(val[k]) if k < len(val) else 0.0
+    v.fov_y_deg = float(fov_y_deg)
+    v.slice_nu, v.slice_nv = int(slice_nu), int(slice_nv)
+    v.width, v.height = int(width), int(height)
+    v.value_lo, v.value_hi = float(value_range[0]), float(value_range[1])
+    return v
+
+
 class ProblemDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("domain", DomainDesc), ("alpha", FieldDesc), ("phi", FieldDesc),
                 ("sigma", FieldDesc), ("f", FieldDesc), ("g", FieldDesc), ("um", FieldDesc)]
@@ -89,6 +113,8 @@ def load():
     lib.wos_solve.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_walk_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp]
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.wos_slice_points.argtypes = [vp, vp, C.POINTER(ViewDesc), vp, vp]
+    lib.wos_render_slice.argtypes = [vp, vp, C.POINTER(ViewDesc), vp, vp, vp, vp, vp, vp]
     lib.wos_solve_nf.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), i64, vp, vp, vp, vp, vp]
     lib.wos_walk_estimates_nf.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), i64, vp, vp, vp, vp]
     lib.wos_solve_grad.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
@@ -350,6 +376,28 @@ class Context:
                                                 C.byref(p), _ptr(uhat), _ptr(steps), _ptr(stats), _stream(stream)))
         return uhat, steps, stats
 
+    def slice_points(self, prob, v, stream=None):
+        """The slice grid's points, CUDA float32 [dim, slice_nu * slice_nv]."""
+        import torch
+        pts = torch.empty((prob.dim, v.slice_nu * v.slice_nv), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.lib.wos_slice_points(self.handle, prob.handle, C.byref(v), _ptr(pts), _stream(stream)))
+        return pts
+
+    def render_slice(self, prob, v, accum, with_value=False, with_depth=False, stream=None):
+        """RGBA8 image [height, width, 4] (CUDA uint8) of the view, and optionally the per-pixel
+        value and depth buffers."""
+        import torch
+        dev = f"cuda:{self.device}"
+        n = v.slice_nu * v.slice_nv
+        if not (accum[0].shape == (n,) and accum[2].shape == (n,)):
+            raise ValueError("accumulators must have one entry per slice point")
+        img = torch.empty((v.height, v.width, 4), dtype=torch.uint8, device=dev)
+        val = torch.empty((v.height, v.width), dtype=torch.float32, device=dev) if with_value else None
+        dep = torch.empty((v.height, v.width), dtype=torch.float32, device=dev) if with_depth else None
+        self._check(self.lib.wos_render_slice(self.handle, prob.handle, C.byref(v), _ptr(accum[0]), _ptr(accum[2]),
+                                              _ptr(img), _ptr(val), _ptr(dep), _stream(stream)))
+        return img, val, dep
+
     def solve_nf(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
                  max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None):
         """Next-flight walks (Sec. 5.2) added to the accumulators; stats 'steps' counts balls
@@ -545,3 +593,40 @@ class Context:
 def stats_dict(stats):
     s = [int(v) for v in stats.cpu().tolist()]
     return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4], "inner": s[5]}
+
+
+class SliceView:
+    """Progressive solve on a slice plane (Sec. 7.2): each frame adds `walks` walks per slice
+    point (continuing the Philox streams through walk_offset) and renders the view; `edit`
+    swaps the problem and discards the accumulated walks."""
+
+    def __init__(self, ctx, prob, v, eps, sigma_bar, seed=0):
+        self.ctx, self.prob, self.view, self.eps, self.sigma_bar, self.seed = ctx, prob, v, eps, sigma_bar, seed
+        self.pts = ctx.slice_points(prob, v)
+        self.accum = ctx.new_accum(self.pts.shape[1])
+        self.stats = ctx.new_stats()
+        self.frames = 0
+
+    def frame(self, walks=1, render=True, stream=None):
+        self.ctx.solve(self.prob, self.pts, walks, self.eps, self.sigma_bar, seed=self.seed,
+                       walk_offset=self.frames, accum=self.accum, stats=self.stats, stream=stream)
+        self.frames += walks
+        return self.ctx.render_slice(self.prob, self.view, self.accum, stream=stream)[0] if render else None
+
+    def edit(self, prob, sigma_bar=None):
+        self.prob = prob
+        if sigma_bar is not None:
+            self.sigma_bar = sigma_bar
+        for t in self.accum:
+            t.zero_()
+        self.stats.zero_()
+        self.frames = 0
+
+
+def write_ppm(path, rgba):
+    """Write an RGBA8 image (array or tensor [h, w, 4]) as a binary PPM file."""
+    a = rgba.cpu().numpy() if hasattr(rgba, "cpu") else np.asarray(rgba)
+    h, w = a.shape[:2]
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (w, h))
+        f.write(np.ascontiguousarray(a[:, :, :3]).tobytes())

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libwos.so")
 HOSTCHECK = os.path.join(HERE, "libwos_hostcheck.so")
 
 CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_nf_f32.cu", "wos_nf_f64.cu",
-              "wos_adjoint.cu", "wos_mesh.cpp"]
+              "wos_adjoint.cu", "wos_render.cu", "wos_mesh.cpp"]
 HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_nf_impl.cuh", "wos_adjoint_impl.cuh",
            "wos_internal.h", "wos_mesh.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -32,7 +32,8 @@
 // at a null event, c (A - P_{k+1})/w_k (-1/sigma_bar) d sigma'/d alpha_m; at the end
 // c W_n e^{gamma(x_n)} g(xbar_n) / (2 alpha(x_n)) N_m(x_n); and once per walk
 // -c A / (2 alpha(x_0)) N_m(x_0).  Small grids are accumulated per CTA in shared
-// memory (FP64 shared atomics) and added to global memory once per CTA.
+// memory in the walk's precision (FP32 shared atomics are native; FP64 ones are not)
+// and added to the FP64 gradient once per CTA.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -76,9 +77,10 @@ __device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, d
 
 // add vN N_m + vG . grad N_m + vL Lap N_m at y to grad[m] over the 4^DIM nodes of
 // the cubic B-spline support (indices clamped as in grid_bspline)
-template <int DIM, typename R>
-__device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN, const double* vG, double vL,
-                                double* grad) {
+template <int DIM, typename R, typename A>
+__device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, const double* vG_, double vL_,
+                                A* grad) {
+  const R vN = R(vN_), vL = R(vL_), vG[3] = {R(vG_[0]), R(vG_[1]), R(vG_[2])};
   int ib[3] = {0, 0, 0};
   R B[3][4], B1[3][4], B2[3][4];
 #pragma unroll
@@ -108,13 +110,12 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN, con
 #pragma unroll
       for (int c0 = 0; c0 < 4; ++c0) {
         int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
-        double b0 = B[0][c0], b1 = B[1][c1], b2 = B[2][c2];
-        double n = b0 * b1 * b2;
-        double gx = (double)B1[0][c0] * b1 * b2, gy = b0 * (double)B1[1][c1] * b2, gz = b0 * b1 * (double)B1[2][c2];
-        double lap = (double)B2[0][c0] * b1 * b2 + b0 * (double)B2[1][c1] * b2 + b0 * b1 * (double)B2[2][c2];
-        double val = vN * n + vG[0] * gx + vG[1] * gy + vL * lap;
-        if (DIM == 3) val += vG[2] * gz;
-        if (val != 0.0) atomicAdd(&grad[(int64_t)j0 + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2)], val);
+        const R b0 = B[0][c0], b1 = B[1][c1], b2 = B[2][c2];
+        const R b12 = b1 * b2;
+        R val = vN * b0 * b12 + vG[0] * B1[0][c0] * b12 + vG[1] * b0 * B1[1][c1] * b2 +
+                vL * (B2[0][c0] * b12 + b0 * B2[1][c1] * b2 + b0 * b1 * B2[2][c2]);
+        if (DIM == 3) val += vG[2] * b0 * b1 * B1[2][c2];
+        if (val != R(0)) atomicAdd(&grad[(int64_t)j0 + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2)], A(val));
       }
     }
   }
@@ -149,12 +150,18 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     int4* dst = reinterpret_cast<int4*>(smem_raw);
     for (int i = threadIdx.x; i < L.problem_bytes / 16; i += blockDim.x) dst[i] = src[i];
   }
-  double* gpriv = reinterpret_cast<double*>(smem_raw + L.problem_bytes);
-  if (ALPHA && L.priv_nodes > 0)
-    for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x) gpriv[i] = 0.0;
+  // alpha: per-CTA accumulators in the walk's precision (FP32 shared atomics are native)
+  R* gpriv = reinterpret_cast<R*>(smem_raw + L.problem_bytes);
+  const bool priv = ALPHA && L.priv_nodes > 0;
+  if (priv)
+    for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x) gpriv[i] = R(0);
   __syncthreads();
   const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
-  double* gtarget = ALPHA ? ((L.priv_nodes > 0) ? gpriv : L.grad_alpha) : L.grad_sigma;
+#define WOS_ALPHA_SCATTER(pt, a, b, c)                                                   \
+  do {                                                                                   \
+    if (priv) bspline_scatter<DIM, R, R>(P.alpha, pt, a, b, c, gpriv);                   \
+    else bspline_scatter<DIM, R, double>(P.alpha, pt, a, b, c, L.grad_alpha);            \
+  } while (0)
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
@@ -261,7 +268,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
         // boundary factor e^{gamma(x_n)}: d/d alpha_m = N_m(x_n) / (2 alpha(x_n)) times the term
         const double vG[3] = {0.0, 0.0, 0.0};
         double v = coef * (double)bterm * 0.5 / (double)al;
-        if (isfinite(v) && v != 0.0) bspline_scatter<DIM, R>(P.alpha, y, v, vG, 0.0, gtarget);
+        if (isfinite(v) && v != 0.0) WOS_ALPHA_SCATTER(y, v, vG, 0.0);
       }
       if (phase == 0) {
         total = acc;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
           const double vG[3] = {0.0, 0.0, 0.0};
           double a0 = (double)field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
           double v = -coef * (double)total * 0.5 / a0;
-          if (isfinite(v) && v != 0.0) bspline_scatter<DIM, R>(P.alpha, x, v, vG, 0.0, gtarget);
+          if (isfinite(v) && v != 0.0) WOS_ALPHA_SCATTER(x, v, vG, 0.0);
         }
         W = R(1);
         acc = R(0);
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
           vL = rj * cL;
         }
       }
-      if (isfinite(vN)) bspline_scatter<DIM, R>(P.alpha, y, vN, vG, vL, gtarget);
+      if (isfinite(vN)) WOS_ALPHA_SCATTER(y, vN, vG, vL);
     }
     if (mu <= PB) {
       R wj = R(1) - spy * inv_sb;
@@ -334,16 +341,17 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     atomicAdd(&L.stats[ST_WALKS], (unsigned long long)st_walks);
     if (st_capped) atomicAdd(&L.stats[ST_CAPPED], (unsigned long long)st_capped);
   }
-  if (ALPHA && L.priv_nodes > 0) {
+  if (priv) {
     __syncthreads();
     for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x)
-      if (gpriv[i] != 0.0) atomicAdd(&L.grad_alpha[i], gpriv[i]);
+      if (gpriv[i] != R(0)) atomicAdd(&L.grad_alpha[i], (double)gpriv[i]);
   }
+#undef WOS_ALPHA_SCATTER
 }
 
 template <int DIM, typename R, bool ALPHA>
 cudaError_t launch_adjoint_m(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
-  size_t smem = (size_t)L.problem_bytes + (ALPHA ? (size_t)L.priv_nodes * sizeof(double) : 0);
+  size_t smem = (size_t)L.problem_bytes + (ALPHA ? (size_t)L.priv_nodes * sizeof(R) : 0);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(wos_adjoint_kernel<DIM, R, ALPHA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

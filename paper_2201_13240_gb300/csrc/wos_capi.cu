@@ -916,6 +916,39 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
   return WOS_OK;
 }
 
+namespace wos {
+int render_slice(const DevProblem<double>* dprob, const DevProblem<double>& host, int dim, const wos_view* view,
+                 const double* sum, const int64_t* count, uint8_t* rgba, float* value, float* depth, int num_sms,
+                 cudaStream_t st);
+int slice_points(int dim, const wos_view* view, float* pts, int num_sms, cudaStream_t st);
+}  // namespace wos
+
+extern "C" int wos_slice_points(wos_ctx* ctx, const wos_problem* pr, const wos_view* view, float* pts, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr || !view || !pts) return fail(ctx, WOS_EINVAL, "null argument");
+  if (view->slice_nu < 1 || view->slice_nv < 1) return fail(ctx, WOS_EINVAL, "empty slice grid");
+  DeviceGuard g(ctx->device);
+  int rc = wos::slice_points(pr->dim, view, pts, ctx->num_sms, static_cast<cudaStream_t>(stream));
+  if (rc != WOS_OK) return fail(ctx, rc, "slice points: degenerate plane rectangle");
+  return WOS_OK;
+}
+
+extern "C" int wos_render_slice(wos_ctx* ctx, const wos_problem* pr, const wos_view* view, const double* sum,
+                                const int64_t* count, uint8_t* rgba, float* value, float* depth, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr || !view || !sum || !count || !rgba) return fail(ctx, WOS_EINVAL, "null argument");
+  if (pr->host64.domain_kind == wos::D_MESH)
+    return fail(ctx, WOS_EUNSUPPORTED, "mesh distances are unsigned: no sphere tracing");
+  if (view->width < 1 || view->height < 1 || view->slice_nu < 1 || view->slice_nv < 1 ||
+      !(view->value_hi > view->value_lo))
+    return fail(ctx, WOS_EINVAL, "bad view size or value range");
+  DeviceGuard g(ctx->device);
+  int rc = wos::render_slice(pr->d64, pr->host64, pr->dim, view, sum, count, rgba, value, depth, ctx->num_sms,
+                             static_cast<cudaStream_t>(stream));
+  if (rc != WOS_OK) return fail(ctx, rc, "render: degenerate camera or plane, or launch failure");
+  return WOS_OK;
+}
+
 extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts,
                                  int32_t walks_uniform, const wos_params* prm, const double* grad_u,
                                  double* grad_alpha, uint64_t* stats, void* stream) {
