@@ -447,6 +447,22 @@ def run_other(args):
         pts = torch.from_numpy(W.mesh_interior_points(npts, seed=0)).cuda()
         walks = args.walks if args.walks != WALKS else 512
         (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
+        if args.dist_grid > 0:
+            # the same problem with a distance grid: conservative radii away from the boundary
+            dg = W.mesh_noise_problem(level=7, dist_grid=args.dist_grid)
+            t0 = time.perf_counter()
+            probg = ctx.problem(dg)
+            torch.cuda.synchronize()
+            build_g = time.perf_counter() - t0
+            (accg, stg), msg = timed(lambda i: ctx.solve(probg, pts, walks, 1e-4, sb, seed=i), args.steps)
+            sg = wos.stats_dict(stg)
+            mg = ctx.finalize(accg)[0].cpu().numpy()
+            m0, v0, se0 = (t.cpu().numpy() for t in ctx.finalize(acc))
+            extra[f"dist_grid_{args.dist_grid}"] = {
+                "ms": msg, "steps_per_walk": sg["steps"] / max(sg["walks"], 1),
+                "steps_per_s": sg["steps"] / (msg * 1e-3), "points_per_s": npts / (msg * 1e-3),
+                "build_s": build_g, "speedup_over_exact_radii": ms / msg,
+                "mean_abs_z_vs_exact_radii": float(np.mean(np.abs(mg - m0) / (np.sqrt(2.0) * se0)))}
         cfg = {"workload": f"displaced icosphere (327,680 triangles), 128^3 noise grids: {npts} interior points "
                            f"x {walks} walks, eps 1e-4", "sigma_bar": sb}
     elif wl == "batch":
@@ -543,6 +559,8 @@ def main():
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
+    ap.add_argument("--dist-grid", type=int, default=128,
+                    help="mesh workload: also time walks with an n^3 distance grid (0: exact radii only)")
     args = ap.parse_args()
     GRID, WALKS = args.grid, args.walks
     if args.impl == "reference":

@@ -147,6 +147,16 @@ typedef struct {
   int64_t ntris;
   const wos_csg_node* csg;
   int32_t ncsg;
+  /* WOS_DOMAIN_MESH only: 0 (default) takes every ball radius from an exact closest-point
+     query.  n >= 4 builds, at problem creation, an n^3 grid of exact distances to the
+     mesh over its bounding box (2% margin) and then takes the radius
+     L = max over the 8 corners c of the point's cell of (d(c) - |x - c|), a lower bound of
+     the distance (distances are 1-Lipschitz), whenever L >= 2 |cell diagonal|; nearer the
+     boundary the exact query runs, bounded by min over the corners of (d(c) + |x - c|).
+     A ball inside the domain keeps the estimator unbiased; interior steps then cost eight
+     loads instead of a BVH traversal.  Not in the paper (a distance acceleration structure
+     in the sense of Sec. 7.1). */
+  int32_t mesh_grid_res;
 } wos_domain_desc;
 
 /* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift

@@ -61,7 +61,7 @@ class CsgNode(C.Structure):
 class Domain(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.POINTER(C.c_float)),
                 ("nverts", C.c_int64), ("tris", C.POINTER(C.c_int32)), ("ntris", C.c_int64),
-                ("bvh", C.c_void_p), ("csg", C.POINTER(CsgNode)), ("ncsg", C.c_int32)]
+                ("bvh", C.c_void_p), ("csg", C.POINTER(CsgNode)), ("ncsg", C.c_int32), ("grid_res", C.c_int32)]
 
 
 class Problem(C.Structure):
@@ -165,7 +165,7 @@ class _Packed:
             P.domain.csg = C.cast(arr, C.POINTER(CsgNode))
             P.domain.ncsg = len(dom["nodes"])
         if dom["kind"] == "mesh":
-            key = (id(dom["verts"]), id(dom["tris"]))
+            key = (id(dom["verts"]), id(dom["tris"]), int(dom.get("grid_res", 0)))
             if key not in _mesh_cache:
                 verts = np.ascontiguousarray(dom["verts"], dtype=np.float32)
                 tris = np.ascontiguousarray(dom["tris"], dtype=np.int32)
@@ -176,6 +176,7 @@ class _Packed:
                 M.domain.nverts = len(verts)
                 M.domain.tris = tris.ctypes.data_as(C.POINTER(C.c_int32))
                 M.domain.ntris = len(tris)
+                M.domain.grid_res = int(dom.get("grid_res", 0))
                 if _load().orc_mesh_prepare(C.pointer(M)) != 0:
                     raise ValueError("orc_mesh_prepare failed")
                 _mesh_cache[key] = (verts, tris, M, dom["verts"], dom["tris"])
@@ -183,6 +184,7 @@ class _Packed:
             P.domain.verts, P.domain.nverts = M.domain.verts, M.domain.nverts
             P.domain.tris, P.domain.ntris = M.domain.tris, M.domain.ntris
             P.domain.bvh = M.domain.bvh
+            P.domain.grid_res = M.domain.grid_res
         self.P = P
         self.ptr = C.pointer(P)
 

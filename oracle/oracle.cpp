@@ -526,6 +526,10 @@ struct OrcNode {
 struct OrcBVH {
   std::vector<OrcNode> nodes;
   std::vector<int64_t> tri;  // permuted triangle indices
+  // optional distance grid
+  int n = 0;
+  double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0}, thresh = 0.0;
+  std::vector<double> dist;
 };
 
 int bvh_build(const orc_domain& D, OrcBVH& B, std::vector<V3>& cent, int first, int count) {
@@ -781,8 +785,27 @@ double distance(const orc_problem* P, const double* x, double* xb) {
       xb[imax] = p[imax] + ((rel[imax] >= 0.0) ? p[3 + imax] : -p[3 + imax]);
       return rc - qmax;
     }
-    case ORC_DOM_MESH:
+    case ORC_DOM_MESH: {
+      const OrcBVH* B = static_cast<const OrcBVH*>(P->domain.bvh);
+      if (B && B->n > 0) {
+        // 1-Lipschitz bound from the corners of the point's cell
+        int i0[3];
+        for (int d = 0; d < 3; ++d) {
+          double sg = std::floor((x[d] - B->lo[d]) / B->h[d]);
+          i0[d] = (int)std::min(std::max(sg, 0.0), (double)(B->n - 2));
+        }
+        double lb = -INFINITY;
+        for (int c = 0; c < 8; ++c) {
+          int ii = i0[0] + (c & 1), jj = i0[1] + ((c >> 1) & 1), kk = i0[2] + ((c >> 2) & 1);
+          double e[3] = {x[0] - (B->lo[0] + ii * B->h[0]), x[1] - (B->lo[1] + jj * B->h[1]),
+                         x[2] - (B->lo[2] + kk * B->h[2])};
+          double dc = B->dist[ii + (int64_t)B->n * (jj + (int64_t)B->n * kk)];
+          lb = std::max(lb, dc - std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
+        }
+        if (lb >= B->thresh) return lb;
+      }
       return mesh_distance(P->domain, x, xb);
+    }
     default:
       return NAN;
   }
@@ -945,6 +968,33 @@ int orc_mesh_prepare(orc_problem* prob) {
   }
   bvh_build(D, *B, cent, 0, (int)D.ntris);
   D.bvh = B;
+  if (D.grid_res > 0) {
+    int n = D.grid_res;
+    double vlo[3] = {INFINITY, INFINITY, INFINITY}, vhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < 3 * D.ntris; ++i) {
+      V3 v = mesh_vertex(D, D.tris[i]);
+      double c[3] = {v.x, v.y, v.z};
+      for (int k = 0; k < 3; ++k) { vlo[k] = std::min(vlo[k], c[k]); vhi[k] = std::max(vhi[k], c[k]); }
+    }
+    double ext = std::max(vhi[0] - vlo[0], std::max(vhi[1] - vlo[1], vhi[2] - vlo[2]));
+    double diag2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      B->lo[k] = vlo[k] - 0.02 * ext;
+      B->h[k] = (vhi[k] - vlo[k] + 0.04 * ext) / (n - 1);
+      diag2 += B->h[k] * B->h[k];
+    }
+    B->thresh = 2.0 * std::sqrt(diag2);
+    B->dist.resize((size_t)n * n * n);
+    int64_t total = (int64_t)n * n * n;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < total; ++i) {
+      double x[3] = {B->lo[0] + (double)(i % n) * B->h[0], B->lo[1] + (double)((i / n) % n) * B->h[1],
+                     B->lo[2] + (double)(i / ((int64_t)n * n)) * B->h[2]};
+      double xb[3];
+      B->dist[i] = mesh_distance(D, x, xb);
+    }
+    B->n = n;
+  }
   return 0;
 }
 

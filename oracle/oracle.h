@@ -88,6 +88,11 @@ typedef struct {
      -sdf(x) and the closest point x - sdf(x) grad sdf(x). */
   const orc_csg_node* csg;
   int32_t ncsg;
+  /* MESH: grid_res > 0 asks orc_mesh_prepare for a grid_res^3 grid of exact distances
+     over the triangles' vertex bounds plus 2% of the largest extent; the walk radius is
+     then L = max over the cell corners c of (d(c) - |x - c|) when L >= twice the cell
+     diagonal, else the exact distance. */
+  int32_t grid_res;
 } orc_domain;
 
 typedef struct {

@@ -52,7 +52,8 @@ class CsgNode(C.Structure):
 
 class DomainDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.c_void_p), ("nverts", C.c_int64),
-                ("tris", C.c_void_p), ("ntris", C.c_int64), ("csg", C.c_void_p), ("ncsg", C.c_int32)]
+                ("tris", C.c_void_p), ("ntris", C.c_int64), ("csg", C.c_void_p), ("ncsg", C.c_int32),
+                ("mesh_grid_res", C.c_int32)]
 
 
 class ViewDesc(C.Structure):
@@ -189,6 +190,7 @@ class Problem:
             self._keep += [verts, tris]
             D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
             D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
+            D.domain.mesh_grid_res = int(desc["domain"].get("grid_res", 0))
         if desc["domain"]["kind"] == "csg":
             nodes = desc["domain"]["nodes"]
             arr = (CsgNode * max(1, len(nodes)))()

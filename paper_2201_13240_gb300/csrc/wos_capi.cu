@@ -58,6 +58,8 @@ struct wos_problem {
   DevProblem<float> host32;   // host copy for batches
   float* mesh_nodes = nullptr;  // device BVH of a mesh boundary
   float* mesh_tris = nullptr;
+  float* mgrid32 = nullptr;     // mesh distance grid (FP32 walks)
+  double* mgrid64 = nullptr;    // the same grid in FP64 (replay walks)
   double mesh_lo[3] = {0, 0, 0}, mesh_hi[3] = {0, 0, 0};
   int mesh_depth = 0;
 };
@@ -236,6 +238,20 @@ __device__ void atomic_max_d(double* addr, double v) {
     unsigned long long prev = atomicCAS(p, old, __double_as_longlong(v));
     if (prev == old) break;
     old = prev;
+  }
+}
+
+// exact distances to the mesh at the nodes of an n^3 grid (FP64 queries)
+__global__ void mesh_grid_kernel(const DevProblem<double>* Pg, int n, double lo0, double lo1, double lo2, double h0,
+                                 double h1, double h2, double* out64, float* out32) {
+  const DevProblem<double>& P = *Pg;
+  int64_t total = (int64_t)n * n * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double x0 = lo0 + (double)(i % n) * h0, x1 = lo1 + (double)((i / n) % n) * h1,
+           x2 = lo2 + (double)(i / ((int64_t)n * n)) * h2;
+    wos::MeshHit<double> hit = wos::mesh_query<double>(P, x0, x1, x2, INFINITY);
+    out64[i] = hit.d;
+    out32[i] = (float)hit.d;
   }
 }
 
@@ -498,6 +514,8 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
       if (d->dim != 3) return fail(ctx, WOS_EINVAL, "mesh domains are 3D");
       if (!d->domain.verts || !d->domain.tris || d->domain.nverts < 3 || d->domain.ntris < 1)
         return fail(ctx, WOS_EINVAL, "mesh: need vertices and triangles");
+      if (d->domain.mesh_grid_res != 0 && (d->domain.mesh_grid_res < 4 || d->domain.mesh_grid_res > 512))
+        return fail(ctx, WOS_EINVAL, "mesh: grid resolution must be 0 or in 4..512");
       break;
     case WOS_DOMAIN_CSG: {
       if (!d->domain.csg || d->domain.ncsg < 1 || d->domain.ncsg > WOS_CSG_MAX_NODES)
@@ -578,15 +596,62 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   }
   if (e == cudaSuccess) e = cudaMalloc(&pr->d32, sizeof(DevProblem<float>));
   if (e == cudaSuccess) e = cudaMalloc(&pr->d64, sizeof(DevProblem<double>));
+  if (e == cudaSuccess) e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d->domain.kind == WOS_DOMAIN_MESH && d->domain.mesh_grid_res > 0) {
+    // distance grid over the vertex bounds of the triangles plus 2% of the largest extent
+    const int n = d->domain.mesh_grid_res;
+    double vlo[3] = {INFINITY, INFINITY, INFINITY}, vhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < 3 * d->domain.ntris; ++t) {
+      const float* v = d->domain.verts + 3 * (int64_t)d->domain.tris[t];
+      for (int k = 0; k < 3; ++k) {
+        vlo[k] = std::fmin(vlo[k], (double)v[k]);
+        vhi[k] = std::fmax(vhi[k], (double)v[k]);
+      }
+    }
+    double ext = std::fmax(vhi[0] - vlo[0], std::fmax(vhi[1] - vlo[1], vhi[2] - vlo[2]));
+    double glo[3], gh[3], diag2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      glo[k] = vlo[k] - 0.02 * ext;
+      gh[k] = (vhi[k] - vlo[k] + 0.04 * ext) / (n - 1);
+      diag2 += gh[k] * gh[k];
+    }
+    size_t nn = (size_t)n * n * n;
+    e = cudaMalloc(&pr->mgrid64, nn * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pr->mgrid32, nn * sizeof(float));
+    if (e == cudaSuccess) {
+      mesh_grid_kernel<<<ctx->num_sms * 8, 128>>>(pr->d64, n, glo[0], glo[1], glo[2], gh[0], gh[1], gh[2],
+                                                  pr->mgrid64, pr->mgrid32);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+      pr->host64.mg_res = n;
+      pr->host64.mgrid = pr->mgrid64;
+      h32->mg_res = n;
+      h32->mgrid = pr->mgrid32;
+      for (int k = 0; k < 3; ++k) {
+        pr->host64.mg_lo[k] = glo[k];
+        pr->host64.mg_h[k] = gh[k];
+        pr->host64.mg_inv_h[k] = 1.0 / gh[k];
+        h32->mg_lo[k] = (float)glo[k];
+        h32->mg_h[k] = (float)gh[k];
+        h32->mg_inv_h[k] = (float)(1.0 / gh[k]);
+      }
+      pr->host64.mg_thresh = 2.0 * std::sqrt(diag2);
+      h32->mg_thresh = (float)(2.0 * std::sqrt(diag2));
+      e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
+    }
+  }
   pr->host32 = *h32;
   if (e == cudaSuccess) e = cudaMemcpy(pr->d32, h32, sizeof(DevProblem<float>), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
   delete h32;
   if (e != cudaSuccess) {
     if (pr->d32) cudaFree(pr->d32);
     if (pr->d64) cudaFree(pr->d64);
     if (pr->mesh_nodes) cudaFree(pr->mesh_nodes);
     if (pr->mesh_tris) cudaFree(pr->mesh_tris);
+    if (pr->mgrid32) cudaFree(pr->mgrid32);
+    if (pr->mgrid64) cudaFree(pr->mgrid64);
     delete pr;
     return cuda_fail(ctx, e, "problem upload");
   }
@@ -602,6 +667,8 @@ int wos_problem_destroy(wos_problem* pr) {
     cudaFree(pr->d64);
     if (pr->mesh_nodes) cudaFree(pr->mesh_nodes);
     if (pr->mesh_tris) cudaFree(pr->mesh_tris);
+    if (pr->mgrid32) cudaFree(pr->mgrid32);
+    if (pr->mgrid64) cudaFree(pr->mgrid64);
   }
   delete pr;
   return WOS_OK;

@@ -72,7 +72,13 @@ struct DevProblem {
   const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
   const float* mesh_tris;   // 12 floats per triangle in leaf order, device
   int32_t ncsg;
-  int32_t pad3[3];
+  int32_t mg_res;           // mesh distance grid: nodes per axis (0: none)
+  int32_t pad3[2];
+  const R* mgrid;           // exact distances at the grid nodes, x fastest, device
+  const void* mg_pad_ptr;   // keeps the 16-byte layout
+  R mg_lo[3], mg_h[3], mg_inv_h[3];
+  R mg_thresh;              // use the grid's lower bound when it is at least this
+  R mg_pad[2];
   CsgNode<R> csg[kMaxCsg];
   DevTerm<R> terms[kMaxTerms];
 };
@@ -692,6 +698,30 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
     }
     case D_MESH: {
       if (DIM != 3 || !MESH) return R(-1);
+      if (P.mg_res > 0) {
+        // distance grid: lower bound max_c (d(c) - |x - c|), upper bound min_c (d(c) + |x - c|)
+        int i0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          R sg = floor((x[d] - P.mg_lo[d]) * P.mg_inv_h[d]);
+          int i = (int)w_fmin(w_fmax(sg, R(0)), R(P.mg_res - 2));
+          i0[d] = i;
+        }
+        R lo_b = R(-INFINITY), hi_b = R(INFINITY);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          int ii = i0[0] + (c & 1), jj = i0[1] + ((c >> 1) & 1), kk = i0[2] + ((c >> 2) & 1);
+          R e0 = x[0] - (P.mg_lo[0] + R(ii) * P.mg_h[0]);
+          R e1 = x[1] - (P.mg_lo[1] + R(jj) * P.mg_h[1]);
+          R e2 = x[2] - (P.mg_lo[2] + R(kk) * P.mg_h[2]);
+          R dist = w_sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+          R dc = P.mgrid[ii + (int64_t)P.mg_res * (jj + (int64_t)P.mg_res * kk)];
+          lo_b = w_fmax(lo_b, dc - dist);
+          hi_b = w_fmin(hi_b, dc + dist);
+        }
+        if (lo_b >= P.mg_thresh) return lo_b;  // xb unused: the walk is not in the shell
+        bound2 = hi_b * hi_b;
+      }
       MeshHit<R> h = mesh_query<R>(P, x[0], x[1], x[2], bound2);
       xb[0] = h.x;
       xb[1] = h.y;

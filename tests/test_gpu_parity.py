@@ -53,6 +53,8 @@ REPLAY_CASES = {
                                        dtype=np.float32), 1e-3),
     "noise_cube": (W.noise_cube_problem, lambda: W.uniform_in_box(3, 24, 0.1, 0.9, 6), 1e-3),
     "mesh": (lambda: W.mesh_manufactured_problem(level=5), lambda: W.mesh_interior_points(32, 7), 1e-4),
+    "mesh_grid": (lambda: W.mesh_manufactured_problem(level=5, dist_grid=48), lambda: W.mesh_interior_points(32, 7),
+                  1e-4),
 }
 
 
@@ -340,3 +342,20 @@ def test_csg_fp64_replay_and_fp32_parity(orc, ctx, name):
     ok, nout, mz = four_se_rule((m - exact) / se)
     assert ok, (nout, mz)
     assert s[2] == 0 and s[4] == 0
+
+
+def test_mesh_distance_grid_fp32_exact_solution(orc, ctx):
+    """Mesh walks with the distance grid (radius: the grid's Lipschitz lower bound away from
+    the boundary) against the manufactured solution, and their step count against exact radii."""
+    pts = W.mesh_interior_points(128, 13)
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    res = {}
+    for grid in (0, 64):
+        desc = W.mesh_manufactured_problem(level=6, dist_grid=grid)
+        prob = ctx.problem(desc)
+        sb = orc.sigma_bar(desc, 48)[0]
+        m, se, st, _ = _gpu_solve(ctx, prob, pts, 4096, 1e-4, sb, seed=8)
+        ok, nout, mz = four_se_rule((m - exact) / se)
+        assert ok, (grid, nout, mz)
+        res[grid] = st[0] / st[1]
+    assert res[64] < 1.2 * res[0]

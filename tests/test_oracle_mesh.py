@@ -60,3 +60,31 @@ def test_walk_on_mesh_matches_exact_solution(orc):
     ok, nout, mz = four_se_rule((m - exact) / se)
     assert ok, ((m - exact) / se)
     assert st["capped"] == 0 and st["nonfinite"] == 0
+
+
+def test_distance_grid_radius_is_a_lower_bound(orc):
+    """With a distance grid the radius is max_c (d(c) - |x - c|) over the cell corners (the
+    distance is 1-Lipschitz): never above the brute-force distance, exact below the threshold."""
+    pg = W.mesh_manufactured_problem(level=4, dist_grid=24)
+    pe = W.mesh_manufactured_problem(level=4)
+    X = W.mesh_interior_points(400, 9).T.astype(np.float64)
+    ratios = []
+    for x in X:
+        brute, _ = orc.mesh_distance_brute(pe, x)
+        dg, _ = orc.distance(pg, x)
+        assert dg <= brute * (1 + 1e-12) + 1e-15
+        ratios.append(dg / brute)
+    ratios = np.array(ratios)
+    assert ratios.mean() > 0.9 and (ratios == 1.0).any()
+
+
+def test_distance_grid_walk_matches_exact_solution(orc):
+    """Smaller balls leave the estimator unbiased: the manufactured solution within 4 SE."""
+    pg = W.mesh_manufactured_problem(level=5, dist_grid=48)
+    pts = W.mesh_interior_points(16, 7)
+    sb = orc.sigma_bar(pg)[0]
+    acc, st = orc.solve(pg, pts, 3000, seed=5, eps=1e-4, sigma_bar=sb)
+    m, v, se = orc.finalize(acc)
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    ok, nout, mz = four_se_rule((m - exact) / se)
+    assert ok and st["capped"] == 0

@@ -405,11 +405,12 @@ def displaced_icosphere(level=7, amplitude=0.1, seed=3):
     return (v * r[:, None]).astype(np.float32), f.astype(np.int32)
 
 
-def mesh_domain(verts, tris):
-    return {"kind": "mesh", "p": [0.0] * 16, "verts": verts, "tris": tris}
+def mesh_domain(verts, tris, grid_res=0):
+    """Closed triangle mesh; grid_res > 0 adds a grid_res^3 distance grid (conservative radii)."""
+    return {"kind": "mesh", "p": [0.0] * 16, "verts": verts, "tris": tris, "grid_res": int(grid_res)}
 
 
-def mesh_noise_problem(level=7, grid_res=128, seed=3):
+def mesh_noise_problem(level=7, grid_res=128, seed=3, dist_grid=0):
     """Displaced icosphere boundary; alpha in [0.5, 2] (cubic B-spline), sigma in [0, 20] and
     f in [-1, 1] (multilinear) from seeded 128^3 value-noise grids over the mesh box plus 5%;
     g = x y + z."""
@@ -422,7 +423,7 @@ def mesh_noise_problem(level=7, grid_res=128, seed=3):
     s = value_noise_grid(3, grid_res, 0.0, 20.0, seed + 2, cell=8)
     f = value_noise_grid(3, grid_res, -1.0, 1.0, seed + 3, cell=8)
     g = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)), term(1.0, None, None, (LIN, 1.0, 0.0)))
-    return problem(3, mesh_domain(verts, tris), grid_field("grid_bspline", a, lo, hi),
+    return problem(3, mesh_domain(verts, tris, dist_grid), grid_field("grid_bspline", a, lo, hi),
                    grid_field("grid_linear", s, lo, hi), grid_field("grid_linear", f, lo, hi), g)
 
 
@@ -432,12 +433,12 @@ def mesh_interior_points(n, seed, radius=0.88):
     return uniform_in_ball(3, n, [0.0, 0.0, 0.0], radius, seed)
 
 
-def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3):
+def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3, dist_grid=0):
     """The 3D manufactured problem (u, alpha, sigma, drift of the cube workload) on the
     displaced-icosphere domain: u is exact on any domain, so the mesh walk has an exact answer."""
     verts, tris = displaced_icosphere(level, amplitude, seed)
     p = cube3d_problem()
-    p["domain"] = mesh_domain(verts, tris)
+    p["domain"] = mesh_domain(verts, tris, dist_grid)
     return p
 
 
