@@ -427,8 +427,9 @@ def run_other(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / nfr
         s1 = wos.stats_dict(sv.stats)
-        st = torch.tensor([s1[k] - stats0[k] for k in ("steps", "walks", "capped", "nonfinite", "outside", "inner")],
-                          dtype=torch.int64)
+        # per-frame statistics (the line's rates are per frame time)
+        st = torch.tensor([(s1[k] - stats0[k]) // nfr for k in ("steps", "walks", "capped", "nonfinite", "outside",
+                                                                "inner")], dtype=torch.int64)
         extra["frames_per_s"] = 1e3 / ms
         extra["frames"] = nfr
         npts = res * res

@@ -234,6 +234,7 @@ class Problem:
         h = C.c_void_p()
         ctx._check(ctx.lib.wos_problem_create(ctx.handle, C.byref(D), C.byref(h)))
         self.handle = h
+        ctx._children.add(self)
 
     def sigma_data_ptr(self):
         """Device address of the sigma grid the problem reads (0 if sigma is not a grid)."""
@@ -272,6 +273,7 @@ class Batch:
         ctx._check(ctx.lib.wos_batch_create(ctx.handle, handles, len(self.problems), offs.ctypes.data,
                                             sbs.ctypes.data, C.byref(h)))
         self.handle = h
+        ctx._children.add(self)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -298,6 +300,8 @@ class Context:
         if rc != WOS_OK:
             raise WosError(rc, "wos_create failed")
         self.handle = h
+        import weakref
+        self._children = weakref.WeakSet()  # problems and batches: released before the context
 
     def _check(self, rc):
         if rc != WOS_OK:
@@ -305,6 +309,8 @@ class Context:
 
     def close(self):
         if getattr(self, "handle", None):
+            for c in list(getattr(self, "_children", ())):
+                c.close()
             self.lib.wos_destroy(self.handle)
             self.handle = None
 

@@ -124,22 +124,24 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, co
 // d sigma' / d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m at y
 template <int DIM, typename R>
 __device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, double* cN, double* cG, double* cL) {
+  // in the walk's precision (FP64 arithmetic is a small fraction of FP32's rate here)
   FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
   FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
   FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
-  const double a = A.v, ia = 1.0 / a;
-  const double ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
-  double na2 = 0.0, gg_ga = 0.0, gg[3] = {0.0, 0.0, 0.0};
+  const R ia = R(1) / A.v;
+  const R ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
+  R na2 = R(0), gg_ga = R(0), gg[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    gg[d] = 0.5 * (ga[d] * ia + gp[d]);
+    gg[d] = R(0.5) * (ga[d] * ia + gp[d]);
     na2 += ga[d] * ga[d];
     gg_ga += gg[d] * ga[d];
   }
-  *cN = -(double)S.v * ia * ia - 0.5 * (double)A.lap * ia * ia + na2 * ia * ia * ia - gg_ga * ia * ia;
+  const R ia2 = ia * ia;
+  *cN = (double)(-S.v * ia2 - R(0.5) * A.lap * ia2 + na2 * ia2 * ia - gg_ga * ia2);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? gg[d] * ia - ga[d] * ia * ia : 0.0;
-  *cL = 0.5 * ia;
+  for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? (double)(gg[d] * ia - ga[d] * ia2) : 0.0;
+  *cL = (double)(R(0.5) * ia);
 }
 
 template <int DIM, typename R, bool ALPHA>

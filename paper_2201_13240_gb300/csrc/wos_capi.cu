@@ -39,6 +39,7 @@ struct wos_ctx {
 
 struct wos_batch {
   wos_ctx* ctx = nullptr;
+  int device = 0;                     // kept here: destroy must not read a destroyed context
   int dim = 0;
   int32_t nprob = 0;
   int64_t npts = 0;
@@ -51,6 +52,7 @@ struct wos_batch {
 
 struct wos_problem {
   wos_ctx* ctx = nullptr;
+  int device = 0;  // kept here: destroy must not read a destroyed context
   int dim = 0;
   DevProblem<float>* d32 = nullptr;
   DevProblem<double>* d64 = nullptr;
@@ -81,13 +83,19 @@ int cuda_fail(wos_ctx* ctx, cudaError_t e, const char* what) {
 
 struct DeviceGuard {
   int prev = -1;
+  // errors of these calls are reported by the calls that follow; they are cleared here so
+  // that they do not surface later in the caller's own CUDA error checks
   explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      (void)cudaGetLastError();
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) (void)cudaGetLastError();
   }
   ~DeviceGuard() {
     int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev && cudaSetDevice(prev) != cudaSuccess)
+      (void)cudaGetLastError();
   }
 };
 
@@ -565,6 +573,7 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
 
   wos_problem* pr = new wos_problem();
   pr->ctx = ctx;
+  pr->device = ctx->device;
   pr->dim = d->dim;
   DevProblem<float>* h32 = new DevProblem<float>();
   fill_problem(*h32, *d);
@@ -662,7 +671,7 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
 int wos_problem_destroy(wos_problem* pr) {
   if (!pr) return WOS_EINVAL;
   {
-    DeviceGuard g(pr->ctx->device);
+    DeviceGuard g(pr->device);
     cudaFree(pr->d32);
     cudaFree(pr->d64);
     if (pr->mesh_nodes) cudaFree(pr->mesh_nodes);
@@ -1091,6 +1100,7 @@ extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, i
   DeviceGuard g(ctx->device);
   wos_batch* b = new wos_batch();
   b->ctx = ctx;
+  b->device = ctx->device;
   b->dim = dim;
   b->nprob = nprob;
   b->npts = npts;
@@ -1120,7 +1130,7 @@ extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, i
 extern "C" int wos_batch_destroy(wos_batch* b) {
   if (!b) return WOS_EINVAL;
   {
-    DeviceGuard g(b->ctx->device);
+    DeviceGuard g(b->device);
     if (b->d32) cudaFree(b->d32);
     if (b->d64) cudaFree(b->d64);
     if (b->offsets) cudaFree(b->offsets);

@@ -168,5 +168,6 @@ def test_coefficient_solve_backward_matches_adjoints(wos, orc, setup):
     ra = torch.zeros(a_t.numel(), dtype=torch.float64, device="cuda")
     ctx.adjoint_sigma(prob, pts, 64, w, rs, 1e-4, sb, seed=5)
     ctx.adjoint_alpha(prob, pts, 64, w, ra, 1e-4, sb, seed=5)
-    assert torch.allclose(s_t.grad.reshape(-1).double(), rs, rtol=1e-5, atol=1e-9)
-    assert torch.allclose(a_t.grad.reshape(-1).double(), ra, rtol=1e-5, atol=1e-9)
+    # the FP32 replay sums in nondeterministic order (per-CTA FP32 partial sums for alpha)
+    assert torch.allclose(s_t.grad.reshape(-1).double(), rs, rtol=1e-4, atol=1e-6 * float(rs.abs().max()))
+    assert torch.allclose(a_t.grad.reshape(-1).double(), ra, rtol=1e-3, atol=1e-4 * float(ra.abs().max()))
