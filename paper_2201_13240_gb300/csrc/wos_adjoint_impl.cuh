@@ -100,23 +100,30 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, co
       B2[d][a] *= F.inv_h[d] * F.inv_h[d];
     }
   }
-  const int n2 = (DIM == 3) ? 4 : 1;
-  for (int c2 = 0; c2 < n2; ++c2) {
-    int j2 = 0;
-    if (DIM == 3) j2 = min(max(ib[2] + c2, 0), F.res[2] - 1);
+  // Rows (c1, c2) of the support are visited in an order rotated by the lane, so lanes
+  // whose points share a cell (walks of one point start together) add to different
+  // addresses at the same time instead of serialising on one.
+  auto sel4 = [](const R* a, int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3])); };
+  const int nrows = (DIM == 3) ? 16 : 4;
+  const int rot = (int)(threadIdx.x & 31);
+  for (int k = 0; k < nrows; ++k) {
+    const int r = (k + rot) & (nrows - 1);
+    const int c1 = r & 3, c2 = (DIM == 3) ? (r >> 2) : 0;
+    const int j1 = min(max(ib[1] + c1, 0), F.res[1] - 1);
+    const int j2 = (DIM == 3) ? min(max(ib[2] + c2, 0), F.res[2] - 1) : 0;
+    const R b1 = sel4(B[1], c1), d1 = sel4(B1[1], c1), e1 = sel4(B2[1], c1);
+    const R b2 = (DIM == 3) ? sel4(B[2], c2) : R(1), d2 = (DIM == 3) ? sel4(B1[2], c2) : R(0);
+    const R e2 = (DIM == 3) ? sel4(B2[2], c2) : R(0);
+    const R b12 = b1 * b2;
+    A* row = grad + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2);
 #pragma unroll
-    for (int c1 = 0; c1 < 4; ++c1) {
-      int j1 = min(max(ib[1] + c1, 0), F.res[1] - 1);
-#pragma unroll
-      for (int c0 = 0; c0 < 4; ++c0) {
-        int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
-        const R b0 = B[0][c0], b1 = B[1][c1], b2 = B[2][c2];
-        const R b12 = b1 * b2;
-        R val = vN * b0 * b12 + vG[0] * B1[0][c0] * b12 + vG[1] * b0 * B1[1][c1] * b2 +
-                vL * (B2[0][c0] * b12 + b0 * B2[1][c1] * b2 + b0 * b1 * B2[2][c2]);
-        if (DIM == 3) val += vG[2] * b0 * b1 * B1[2][c2];
-        if (val != R(0)) atomicAdd(&grad[(int64_t)j0 + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2)], A(val));
-      }
+    for (int c0 = 0; c0 < 4; ++c0) {
+      const int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
+      const R b0 = B[0][c0];
+      R val = vN * b0 * b12 + vG[0] * B1[0][c0] * b12 + vG[1] * b0 * d1 * b2 +
+              vL * (B2[0][c0] * b12 + b0 * e1 * b2 + b0 * b1 * e2);
+      if (DIM == 3) val += vG[2] * b0 * b1 * d2;
+      if (val != R(0)) atomicAdd(&row[j0], A(val));
     }
   }
 }
