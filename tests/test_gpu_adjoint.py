@@ -194,8 +194,14 @@ def test_sigma_adjoint_matches_fd_grid_reference(wos, orc):
     acc, _ = ctx.solve(prob, p, 1 << 16, 1e-4, sb, seed=21)
     m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
     assert np.all(np.abs(m - u_fd) <= 4 * se + 2e-3)
-    grad = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
-    ctx.adjoint_sigma(prob, p, 1 << 16, torch.from_numpy(w).cuda(), grad, 1e-4, sb, seed=21)
-    g = grad.cpu().numpy()
-    rel = np.linalg.norm(g - g_fd) / np.linalg.norm(g_fd)
-    assert rel < 0.1, rel
+    gs = []
+    for seed in (21, 22):  # two independent halves give the Monte Carlo noise of their mean
+        grad = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+        ctx.adjoint_sigma(prob, p, 1 << 17, torch.from_numpy(w).cuda(), grad, 1e-4, sb, seed=seed)
+        gs.append(grad.cpu().numpy())
+    g = 0.5 * (gs[0] + gs[1])
+    noise = 0.5 * np.linalg.norm(gs[0] - gs[1])
+    err = np.linalg.norm(g - g_fd)
+    # Monte Carlo noise (2 sigma) plus the reference's discretisation error (5% allowance)
+    assert err <= 2.0 * noise + 0.05 * np.linalg.norm(g_fd), (err, noise, np.linalg.norm(g_fd))
+    assert err <= 0.15 * np.linalg.norm(g_fd)
