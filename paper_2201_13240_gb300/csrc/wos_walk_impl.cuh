@@ -10,8 +10,11 @@
 // Scheduling: the grid is persistent (resident blocks x SMs).  Walks are items
 // of a point-major index space claimed in chunks by one atomic per warp; a lane
 // whose walk ends takes the next item at the top of the step loop, so warps
-// stay full while walk lengths vary.  Each lane keeps FP64 partial sums of its
-// current point and flushes them with atomics when its point changes.
+// stay full while walk lengths vary.  Each lane keeps partial sums of its current
+// point, shifted by the first estimate it saw for that point (sums of u - c and
+// (u - c)^2 in the walk's precision: no FP64 arithmetic per walk, and no
+// cancellation when the estimates agree), and flushes them to the FP64
+// accumulators with atomics when its point changes.
 //
 // SIMT uniformity: in almost every iteration some lane of a warp ends its walk,
 // so the end of a walk must not run a separate instruction stream.  A lane that
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
   uint32_t acc_p = kNoPoint, acc_prob = 0;
   double s1 = 0.0, s2 = 0.0;
   uint32_t n_acc = 0;
+  R sh = R(0), d1 = R(0), d2 = R(0);  // FP32 partial sums shifted by the point's first value
   // spatial gradient: per-lane partial sums of (grad U - U grad gamma) and grad gamma(x_0)
   double gs1[3] = {0.0, 0.0, 0.0}, gs2[3] = {0.0, 0.0, 0.0};
   R ggam[3] = {R(0), R(0), R(0)};
@@ -289,6 +293,11 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
       if (accumulate && s.p != acc_p) {
         if (acc_p != kNoPoint) {
           double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
+          if (!GRAD) {
+            double c = (double)sh, n = (double)n_acc;
+            s1 = n * c + (double)d1;
+            s2 = n * c * c + 2.0 * c * (double)d1 + (double)d2;
+          }
           atomicAdd(&L.sum[acc_p], s1 * e0);
           atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
           atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
@@ -307,9 +316,18 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
         s1 = 0.0;
         s2 = 0.0;
         n_acc = 0;
+        sh = s.acc;
+        d1 = R(0);
+        d2 = R(0);
       }
-      s1 += acc_d;
-      s2 += acc_d * acc_d;
+      if (GRAD) {
+        s1 += acc_d;
+        s2 += acc_d * acc_d;
+      } else {
+        R dv = s.acc - sh;
+        d1 += dv;
+        d2 += dv * dv;
+      }
       ++n_acc;
       if (GRAD) {
 #pragma unroll
@@ -330,7 +348,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
       if (!WW) st_steps += s.k;
       ++st_walks;
       if (capped) ++st_capped;
-      if (!isfinite(acc_d)) ++st_nonfinite;
+      if (!isfinite(s.acc)) ++st_nonfinite;
       active = false;
       continue;
     }
@@ -391,6 +409,11 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
 
   if (accumulate && acc_p != kNoPoint) {
     double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
+    if (!GRAD) {
+      double c = (double)sh, n = (double)n_acc;
+      s1 = n * c + (double)d1;
+      s2 = n * c * c + 2.0 * c * (double)d1 + (double)d2;
+    }
     atomicAdd(&L.sum[acc_p], s1 * e0);
     atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
     atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
