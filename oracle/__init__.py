@@ -66,7 +66,7 @@ class Domain(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("domain", Domain), ("alpha", Field), ("phi", Field),
-                ("sigma", Field), ("f", Field), ("g", Field), ("um", Field)]
+                ("sigma", Field), ("f", Field), ("g", Field), ("um", Field), ("omega", Field * 3)]
 
 
 def _load():
@@ -109,6 +109,8 @@ def _load():
     lib.orc_solve_ww.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
                                  C.c_double, C.c_int64, C.c_double, C.c_double, C.c_int, dp, dp,
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]
+    lib.orc_green_dlog.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+    lib.orc_green_dlog.restype = C.c_double
     lib.orc_green_grad_ratios.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp]
     lib.orc_walk_grad.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double,
                                   C.c_int64, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
@@ -153,6 +155,8 @@ class _Packed:
             P.domain.p[i] = v
         for name in ("alpha", "phi", "sigma", "f", "g", "um"):
             self._field(getattr(P, name), prob[name])
+        for d, fd in enumerate(prob.get("omega", [{"kind": "zero"}] * 3)):
+            self._field(P.omega[d], fd)
         if dom["kind"] == "csg":
             prims = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
             ops = {"union": 0, "intersect": 1, "subtract": 2}
@@ -498,3 +502,8 @@ def walks_nf(prob, pts, walks_per_point, seed, eps, sigma_bar, walk_offset=0, ma
     if rc != 0:
         raise ValueError("orc_walks_nf rejected its inputs")
     return uh, st, inn
+
+
+def green_dlog(dim, R, sb, r):
+    """|G'(r)/G(r)| of the centred Green's function on a ball of radius R."""
+    return _load().orc_green_dlog(dim, R, sb, r)

@@ -423,12 +423,15 @@ int field_eval(const orc_problem* P, const orc_field* fl, const double* x, doubl
       if (field_eval(P, &P->alpha, x, &a, ga, &la)) return -1;
       if (field_eval(P, &P->phi, x, &ph, gp, &lp)) return -1;
       if (field_eval(P, &P->sigma, x, &s, gs, &ls)) return -1;
-      double dot_a = 0.0, dot_p = 0.0;
+      double dot_a = 0.0, dot_p = 0.0, dot_w = 0.0;
       for (int d = 0; d < dim; ++d) {
         dot_a += ga[d] * gu[d];
         dot_p += gp[d] * gu[d];
+        double w, gw[3], lw;
+        if (field_eval(P, &P->omega[d], x, &w, gw, &lw)) return -1;
+        dot_w += w * gu[d];
       }
-      *v = -(a * lu + dot_a) - a * dot_p + s * u;
+      *v = -(a * lu + dot_a) - a * dot_p - dot_w + s * u;
       *lap = NAN;
       g[0] = g[1] = g[2] = NAN;
       return 0;
@@ -440,8 +443,14 @@ int field_eval(const orc_problem* P, const orc_field* fl, const double* x, doubl
 
 // Sec. 4.1 (eq. 7-8) and App. A: gamma = 1/2 ln(alpha) + 1/2 Phi,
 // sigma' = sigma/alpha + Lap(gamma) + |grad gamma|^2, f' = e^gamma f / alpha.
+bool has_drift(const orc_problem* P) {
+  for (int d = 0; d < P->dim; ++d)
+    if (P->omega[d].kind != ORC_FIELD_ZERO) return true;
+  return false;
+}
+
 void coeffs(const orc_problem* P, const double* x, double* gamma, double* sp, double* fp,
-            double* fv, double* av) {
+            double* fv, double* av, double* bout = nullptr) {
   int dim = P->dim;
   double a, ga[3], la, ph, gp[3], lp, s, gs[3], ls, f, gf[3], lf;
   field_eval(P, &P->alpha, x, &a, ga, &la);
@@ -461,6 +470,36 @@ void coeffs(const orc_problem* P, const double* x, double* gamma, double* sp, do
   *fp = std::exp(*gamma) * f / a;
   *fv = f;
   *av = a;
+  if (bout) bout[0] = bout[1] = bout[2] = 0.0;
+  if (has_drift(P)) {
+    // b = omega_extra / alpha: sigma'' = sigma' + b . grad gamma, plus div b from the parts
+    double divw = 0.0, wga = 0.0, bg = 0.0, b[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      double w, gw[3], lw;
+      field_eval(P, &P->omega[d], x, &w, gw, &lw);
+      divw += gw[d];
+      wga += w * ga[d];
+      b[d] = w / a;
+      bg += b[d] * ggam[d];
+    }
+    double divb = divw / a - wga / (a * a);
+    *sp += bg + divb;
+    if (bout)
+      for (int d = 0; d < dim; ++d) bout[d] = b[d];
+  }
+}
+
+// |G'(r) / G(r)| of the centred Green's function on a ball of radius R (Supplemental 1.1):
+// 3D G ~ sinh(s(R - r)) / r, 2D G ~ K0(sr) - K0(sR) I0(sr) / I0(sR).
+double green_dlog(int dim, double R, double sb, double r) {
+  double s = std::sqrt(sb);
+  if (dim == 3) {
+    if (sb == 0.0) return 1.0 / r + 1.0 / (R - r);
+    return s / std::tanh(s * (R - r)) + 1.0 / r;
+  }
+  if (sb == 0.0) return 1.0 / (r * std::log(R / r));
+  double t = s * r, a = s * R;
+  return s * (bK1(t) + bK0(a) / bI0(a) * bI1(t)) / (bK0(t) - bK0(a) / bI0(a) * bI0(t));
 }
 
 double gamma_at(const orc_problem* P, const double* x) {
@@ -1073,11 +1112,17 @@ double orc_walk(const orc_problem* P, const double* x0, uint32_t point, uint32_t
     double r = orc_green_inv(dim, R, sb, ur);
     double y[3] = {0, 0, 0};
     for (int i = 0; i < dim; ++i) y[i] = x[i] + r * dy[i];
-    double gam_y, sp_y, fp_y, f_y, a_y;
-    coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+    double gam_y, sp_y, fp_y, f_y, a_y, b_y[3];
+    coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y, b_y);
     acc += W * Gn * fp_y;                       // source term, every step
     if (mu <= sb * Gn) {                        // volume term: null event at y
-      W *= 1.0 - sp_y / sb;
+      double wn = 1.0 - sp_y / sb;
+      if (has_drift(P)) {
+        double db = 0.0;
+        for (int i = 0; i < dim; ++i) db += dy[i] * b_y[i];
+        wn += green_dlog(dim, R, sb, r) * db / sb;
+      }
+      W *= wn;
       for (int i = 0; i < dim; ++i) x[i] = y[i];
     } else {                                    // boundary term: z uniform on the sphere
       for (int i = 0; i < dim; ++i) x[i] = x[i] + R * dz[i];
@@ -1203,13 +1248,19 @@ double orc_walk_ww(const orc_problem* P, const double* x0, uint32_t point, uint3
       double r = orc_green_inv(dim, R, sb, ur);
       double y[3] = {0, 0, 0};
       for (int i = 0; i < dim; ++i) y[i] = b.x[i] + r * dy[i];
-      double gam_y, sp_y, fp_y, f_y, a_y;
-      coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
+      double gam_y, sp_y, fp_y, f_y, a_y, b_y[3];
+      coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y, b_y);
       acc += b.W * Gn * fp_y;
       ++steps;
       ++b.k;
       if (mu <= sb * Gn) {
-        b.W *= 1.0 - sp_y / sb;
+        double wn = 1.0 - sp_y / sb;
+        if (has_drift(P)) {
+          double db = 0.0;
+          for (int i = 0; i < dim; ++i) db += dy[i] * b_y[i];
+          wn += green_dlog(dim, R, sb, r) * db / sb;
+        }
+        b.W *= wn;
         for (int i = 0; i < dim; ++i) b.x[i] = y[i];
         double aw = std::fabs(b.W);
         if (ww_lo > 0.0 && aw < ww_lo) {
@@ -1288,6 +1339,8 @@ int orc_solve_ww(const orc_problem* P, const double* pts, int64_t npts, int32_t 
   return 0;
 }
 
+double orc_green_dlog(int dim, double R, double sb, double r) { return green_dlog(dim, R, sb, r); }
+
 void orc_green_grad_ratios(int dim, double R, double sb, double r, double out[2]) {
   grad_ratios(dim, R, sb, r, &out[0], &out[1]);
 }
@@ -1298,6 +1351,7 @@ double orc_walk_grad(const orc_problem* P, const double* x0, uint32_t point, uin
                      uint64_t seed, double eps, double sb, int64_t max_steps, double* grad_out,
                      int64_t* steps_out, int32_t* flags_out) {
   int dim = P->dim;
+  if (has_drift(P)) return NAN;  // the first-ball gradient here has no extra-drift term
   double x[3] = {0, 0, 0};
   for (int d = 0; d < dim; ++d) x[d] = x0[d];
   double W = 1.0, acc = 0.0, S0 = 0.0;
@@ -1441,6 +1495,7 @@ double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint3
                    double eps, double sb, int64_t max_steps, int64_t max_inner, int64_t* steps_out,
                    int64_t* inner_out, int32_t* flags_out) {
   int dim = P->dim;
+  if (has_drift(P)) return NAN;  // the off-centred series here has no extra-drift term
   double x[3] = {0, 0, 0};
   for (int d = 0; d < dim; ++d) x[d] = x0[d];
   double W = 1.0, acc = 0.0;

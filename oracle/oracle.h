@@ -104,6 +104,13 @@ typedef struct {
   orc_field f;          /* source; MANUFACTURED: f = -div(alpha grad um) - omega.grad um + sigma um */
   orc_field g;          /* Dirichlet data, read at the closest boundary point */
   orc_field um;         /* manufactured solution used by f when f.kind == MANUFACTURED */
+  /* A further drift, any vector field (the non-conservative part): the PDE's drift is
+     omega = alpha grad(phi) + (omega_x, omega_y, omega_z).  Not in the paper: with
+     b = omega_extra / alpha the transformed equation gains b . grad U, which is moved
+     onto the Green's function by parts on each ball (G = 0 on the sphere), giving
+     null weights 1 - (sigma' + b . grad gamma + div b) / sigma_bar
+     + |G'(r)/G(r)| (dir_y . b(y)) / sigma_bar.  ZERO fields: no extra drift. */
+  orc_field omega[3];
 } orc_problem;
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */
@@ -163,6 +170,9 @@ int orc_solve_ww(const orc_problem* prob, const double* pts, int64_t npts, int32
                  uint64_t walk_offset, uint64_t seed, double eps, double sigma_bar, int64_t max_steps,
                  double ww_lo, double ww_hi, int depth, double* sum, double* sumsq, int64_t* count,
                  int64_t* stats, int nthreads);
+
+/* |G'(r)/G(r)| of the centred Green's function on a ball of radius R (Supplemental 1.1). */
+double orc_green_dlog(int dim, double R, double sigma_bar, double r);
 
 /* Gradient of the Green's function and Poisson kernel at the centre of the ball
    (Supplemental 1.3, as printed), divided by the centred G(r) resp. P:

@@ -110,7 +110,10 @@ def csg(lo, hi, *nodes):
     return {"kind": "csg", "p": p, "nodes": out}
 
 
-def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None):
+def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None, omega=None):
+    """omega: an extra drift vector field (a list of dim fields), added to alpha grad(phi)."""
+    om = list(omega) if omega is not None else []
+    om += [zero()] * (3 - len(om))
     return {
         "dim": int(dim),
         "domain": domain,
@@ -120,6 +123,7 @@ def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None):
         "f": f,
         "g": g,
         "um": um if um is not None else zero(),
+        "omega": om,
     }
 
 
@@ -168,6 +172,19 @@ def cube3d_problem():
               term(1.0 / (2 * PI), None, None, (SIN, 2 * PI, 0.0)),
               term(0.5, None, None, (LIN, 1.0, 0.0)))
     return problem(3, box([0, 0, 0], [1, 1, 1]), alpha, sigma, manufactured(), u, phi=phi, um=u)
+
+
+def cube3d_literal_problem():
+    """The 3D cube workload with its literal drift omega = (sin 2 pi y, cos 2 pi z, 0.5)
+    (non-zero curl: not alpha times a gradient), u, alpha, sigma as in cube3d_problem;
+    f from eq. 1.  Needs the extra-drift walk (the paper has no exact estimator for it)."""
+    u = sst(term(1.0, (EXP, 0.5, 0.0), (SIN, PI, 0.0), (COS, PI, 0.0)))
+    alpha = sst(term(1.0), term(0.3, (QUAD, 1.0, 0.0)), term(0.3, None, (QUAD, 1.0, 0.0)),
+                term(0.3, None, None, (QUAD, 1.0, 0.0)))
+    sigma = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)))
+    omega = [sst(term(1.0, None, (SIN, 2 * PI, 0.0))), sst(term(1.0, None, None, (COS, 2 * PI, 0.0))),
+             const(0.5)]
+    return problem(3, box([0, 0, 0], [1, 1, 1]), alpha, sigma, manufactured(), u, um=u, omega=omega)
 
 
 def cube3d_exact(x, y, z):
