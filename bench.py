@@ -404,6 +404,25 @@ def run_other(args):
         extra["mean_stderr_over_delta_tracking"] = float(np.mean(se) / np.mean(se0))
         cfg = {"workload": f"cube3d_drift_manufactured, next-flight walks (approximate off-centred G, P): "
                            f"{GRID}^3 points x {WALKS} walks, eps 1e-4; steps count balls", "sigma_bar": sb}
+    elif wl == "c2literal":
+        # config 2 with its literal, non-conservative drift (the extra-drift walk)
+        desc = W.cube3d_literal_problem()
+        prob = ctx.problem(desc)
+        sb = ctx.sigma_bar(prob, 64)[0]
+        pts_np = W.cell_centres(3, GRID)
+        pts = torch.from_numpy(pts_np).cuda()
+        npts = pts_np.shape[1]
+        (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+        exact = W.cube3d_exact(*pts_np.astype(np.float64))
+        rms = float(np.linalg.norm(m - exact) / np.linalg.norm(exact))
+        noise = float(np.sqrt(np.mean(se ** 2)) / np.sqrt(np.mean(exact ** 2)))
+        walks_1e2 = int(math.ceil(WALKS * (noise / 1e-2) ** 2))
+        extra["normalised_rms"] = rms
+        extra["walks_per_point_for_rms_1e-2"] = walks_1e2
+        extra["points_per_s_at_rms_1e-2"] = npts / (ms * 1e-3) * WALKS / max(walks_1e2, 1)
+        cfg = {"workload": f"cube3d with the literal drift omega = (sin 2 pi y, cos 2 pi z, 0.5): {GRID}^3 points x "
+                           f"{WALKS} walks, eps 1e-4 (extra-drift walk; not in the paper)", "sigma_bar": sb}
     elif wl == "slice":
         # the interactive path (Sec. 7.2): one walk per slice point per frame plus the
         # sphere-traced image of the CSG scene cut by the slice plane
@@ -555,7 +574,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID, help="points per axis (profiling runs use a smaller case)")
     ap.add_argument("--walks", type=int, default=WALKS, help="walks per point (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
-    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad", "nf", "slice"],
+    ap.add_argument("--workload", default="cube3d", choices=["cube3d", "square2d", "mesh", "batch", "inverse", "grad", "nf", "slice", "c2literal"],
                     help="cube3d is the benchmark; the others print supplementary measurements")
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")

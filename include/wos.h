@@ -162,11 +162,21 @@ typedef struct {
 /* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift
    potential (omega = alpha grad phi, App. A), sigma (screening), f (source),
    g (Dirichlet data, read at the closest boundary point), um (the manufactured
-   solution used when f.kind == WOS_FIELD_MANUFACTURED, else ignored). */
+   solution used when f.kind == WOS_FIELD_MANUFACTURED, else ignored).
+   omega[0..dim-1]: a further drift, any vector field (ZERO kinds: none), so the drift
+   of eq. 1 is alpha grad phi + omega.  Not in the paper, whose estimator needs
+   omega / alpha to be a gradient: with b = omega / alpha the transformed equation keeps
+   b . grad U, moved onto the Green's function by parts on each ball (G vanishes on the
+   sphere), so a null event at y = x + r dir_y carries the weight
+   1 - (sigma' + b . grad gamma + div b)/sigma_bar + |G'(r)/G(r)| (dir_y . b(y))/sigma_bar.
+   The components need first derivatives (not WOS_FIELD_GRID_LINEAR).  Supported by
+   wos_solve, wos_walk_estimates, wos_solve_host and wos_sigma_bar on analytic domains;
+   the other entry points return WOS_EUNSUPPORTED for such a problem. */
 typedef struct {
   int32_t dim; /* 2 or 3 */
   wos_domain_desc domain;
   wos_field_desc alpha, phi, sigma, f, g, um;
+  wos_field_desc omega[3];
 } wos_problem_desc;
 
 enum { WOS_FP32 = 0, WOS_FP64 = 1 };

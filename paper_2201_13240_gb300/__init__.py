@@ -82,7 +82,8 @@ def view(plane_origin, plane_u, plane_v, slice_nu, slice_nv, width, height, valu
 
 class ProblemDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("domain", DomainDesc), ("alpha", FieldDesc), ("phi", FieldDesc),
-                ("sigma", FieldDesc), ("f", FieldDesc), ("g", FieldDesc), ("um", FieldDesc)]
+                ("sigma", FieldDesc), ("f", FieldDesc), ("g", FieldDesc), ("um", FieldDesc),
+                ("omega", FieldDesc * 3)]
 
 
 class Params(C.Structure):
@@ -202,9 +203,11 @@ class Problem:
             self._keep.append(arr)
             D.domain.csg = C.cast(arr, C.c_void_p)
             D.domain.ncsg = len(nodes)
-        for name in ("alpha", "phi", "sigma", "f", "g", "um"):
-            fd = desc[name]
-            F = getattr(D, name)
+        omega = list(desc.get("omega", []))
+        omega += [{"kind": "zero"}] * (3 - len(omega))
+        slots = [(n, desc[n], getattr(D, n)) for n in ("alpha", "phi", "sigma", "f", "g", "um")]
+        slots += [(f"omega{k}", omega[k], D.omega[k]) for k in range(3)]
+        for name, fd, F in slots:
             F.kind = _FIELD_KINDS[fd["kind"]]
             F.value = fd.get("value", 0.0)
             if fd["kind"] == "sst":

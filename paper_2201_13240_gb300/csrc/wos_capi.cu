@@ -206,6 +206,15 @@ void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
   fill_field(P, P.f, d.f, d.dim);
   fill_field(P, P.g, d.g, d.dim);
   fill_field(P, P.um, d.um, d.dim);
+  P.has_drift = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (k < d.dim) {
+      fill_field(P, P.omega[k], d.omega[k], d.dim);
+      if (d.omega[k].kind != WOS_FIELD_ZERO) P.has_drift = 1;
+    } else {
+      P.omega[k].kind = wos::F_ZERO;
+    }
+  }
 }
 
 void domain_bbox(const wos_problem* pr, double lo[3], double hi[3]) {
@@ -275,7 +284,8 @@ __global__ void sigma_range_kernel(const DevProblem<double>* Pg, int m, double l
     double xb[3];
     if (!(wos::distance<DIM>(P, x, xb) > 0.0)) continue;
     double sp, fp;
-    wos::coeffs<DIM>(P, x, &sp, &fp);
+    if (P.has_drift) wos::coeffs<DIM, double, true>(P, x, &sp, &fp);
+    else wos::coeffs<DIM>(P, x, &sp, &fp);
     double a = wos::field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
     mn = fmin(mn, sp);
     mx = fmax(mx, sp);
@@ -405,7 +415,10 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.gsumsq = gsumsq;
   L.ghat = ghat;
   L.nf_max_inner = nf_max_inner;
+  L.drift = prob->host64.has_drift;
   const bool nf = nf_max_inner > 0;
+  if (L.drift && (nf || gsum || ghat || prm->ww_lo != 0.0))
+    return fail(ctx, WOS_EUNSUPPORTED, "an extra drift (omega) works with the plain solve only");
   if (prm->precision == WOS_FP64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
@@ -567,6 +580,14 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
     if (check_field(*x.f, d->dim, x.n, x.src, x.c2, &why) != WOS_OK) return fail(ctx, WOS_EINVAL, why);
     if (x.f->kind == WOS_FIELD_SST) total_terms += x.f->nterms;
   }
+  bool drift = false;
+  for (int k = 0; k < d->dim; ++k) {
+    if (check_field(d->omega[k], d->dim, "omega", false, true, &why) != WOS_OK) return fail(ctx, WOS_EINVAL, why);
+    if (d->omega[k].kind == WOS_FIELD_SST) total_terms += d->omega[k].nterms;
+    if (d->omega[k].kind != WOS_FIELD_ZERO) drift = true;
+  }
+  if (drift && d->domain.kind == WOS_DOMAIN_MESH)
+    return fail(ctx, WOS_EUNSUPPORTED, "an extra drift (omega) on a mesh domain is not supported");
   if (d->alpha.kind == WOS_FIELD_ZERO) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
   if (d->alpha.kind == WOS_FIELD_CONST && !(d->alpha.value > 0)) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
   if (total_terms > wos::kMaxTerms) return fail(ctx, WOS_EINVAL, "more than 96 separable terms in total");
@@ -954,6 +975,7 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
   if (npts == 0 || walks_uniform == 0) return WOS_OK;
   if (!pts || !grad_u || !grad_sigma) return fail(ctx, WOS_EINVAL, "null device array");
   const DevProblem<double>& H = pr->host64;
+  if (H.has_drift) return fail(ctx, WOS_EUNSUPPORTED, "the adjoint has no extra-drift (omega) term");
   if (H.sigma.kind != wos::F_GRID_LINEAR)
     return fail(ctx, WOS_EUNSUPPORTED, "the sigma gradient needs sigma given as a multilinear grid");
   if (H.f.kind == wos::F_MANUFACTURED)
@@ -1038,6 +1060,7 @@ extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const floa
   if (npts == 0 || walks_uniform == 0) return WOS_OK;
   if (!pts || !grad_u || !grad_alpha) return fail(ctx, WOS_EINVAL, "null device array");
   const DevProblem<double>& H = pr->host64;
+  if (H.has_drift) return fail(ctx, WOS_EUNSUPPORTED, "the adjoint has no extra-drift (omega) term");
   if (H.alpha.kind != wos::F_GRID_BSPLINE)
     return fail(ctx, WOS_EUNSUPPORTED, "the alpha gradient needs alpha given as a B-spline grid");
   if (H.f.kind == wos::F_MANUFACTURED)
@@ -1092,6 +1115,7 @@ extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, i
     if (probs[i]->ctx != ctx) return fail(ctx, WOS_EINVAL, "problem of another context in batch");
     if (probs[i]->dim != dim) return fail(ctx, WOS_EINVAL, "all problems of a batch must have one dimension");
     if (probs[i]->host64.domain_kind == wos::D_MESH) return fail(ctx, WOS_EUNSUPPORTED, "mesh domains in a batch");
+    if (probs[i]->host64.has_drift) return fail(ctx, WOS_EUNSUPPORTED, "extra-drift (omega) problems in a batch");
     if (pt_offsets[i + 1] < pt_offsets[i]) return fail(ctx, WOS_EINVAL, "point offsets must not decrease");
     if (!finite_pos(sigma_bars[i])) return fail(ctx, WOS_EINVAL, "sigma_bar of every problem must be > 0");
   }
@@ -1296,6 +1320,8 @@ bool na_desc_ok(const wos_problem_desc* d) {
   const wos_field_desc* fl[6] = {&d->alpha, &d->phi, &d->sigma, &d->f, &d->g, &d->um};
   for (auto* f : fl)
     if (f->kind == WOS_FIELD_SST) total += f->nterms;
+  for (int k = 0; k < 3; ++k)
+    if (k < d->dim && d->omega[k].kind != WOS_FIELD_ZERO) return false;  // the extra drift needs wos_solve
   return total <= wos::kMaxTerms;
 }
 

@@ -177,4 +177,13 @@ void wos_hc_offcentre(int dim, int fp64, double Rb, double sb, const double* u, 
   }
 }
 
+// R |G'/G| of the centred Green's function at rho = r/R
+void wos_hc_green_dlog(int dim, int fp64, double a, const double* rho, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) out[i] = (dim == 2) ? wos::green_dlog_r<2, double>(a, rho[i]) : wos::green_dlog_r<3, double>(a, rho[i]);
+    else out[i] = (dim == 2) ? wos::green_dlog_r<2, float>((float)a, (float)rho[i])
+                             : wos::green_dlog_r<3, float>((float)a, (float)rho[i]);
+  }
+}
+
 }  // extern "C"

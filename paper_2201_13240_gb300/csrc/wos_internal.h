@@ -47,6 +47,7 @@ struct WalkLaunch {
   double* ghat;                   // optional per-walk gradients SoA [dim][total_items]
   // next-flight launches: cap on the inner iterations of one ball
   int64_t nf_max_inner;
+  int drift;                      // the problem has an extra drift (omega fields)
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

@@ -483,6 +483,30 @@ WOS_HD void grad_ratios(R a, R rho, R* gGR, R* gPR) {
 }
 
 // ---------------------------------------------------------------------------
+// R |G'(r)/G(r)| of the centred Green's function (Supplemental 1.1), rho = r/R,
+// a = sqrt(sb) R, t = a rho: the weight of an extra drift (see coeffs).
+//   3D: G ~ sinh(a - t)/r          -> a / tanh(a - t) + 1/rho   (Laplace: 1/(1 - rho) + 1/rho)
+//   2D: G ~ K0(t) - cK I0(t) ...   -> a (k1s(t) + cK e^{2(t-a)} i1s(t)) / (k0s(t) - cK e^{2(t-a)} i0s(t))
+//                                      (Laplace: 1/(rho ln(1/rho)))
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+WOS_HD R green_dlog_r(R a, R rho) {
+  if (DIM == 3) {
+    if (a < R(1e-4)) return R(1) / (R(1) - rho) + R(1) / rho;
+    R dl = a * (R(1) - rho);
+    R th = (dl < R(20)) ? (-w_expm1(R(-2) * dl)) / (R(1) + w_exp(R(-2) * dl)) : R(1);  // tanh(dl)
+    return a / th + R(1) / rho;
+  }
+  if (a < R(1e-4)) return R(1) / (rho * (-w_log(rho)));
+  R t = a * rho;
+  R i0a, i1a, k0a, k1a, i0t, i1t, k0t, k1t;
+  bessel_scaled(a, &i0a, &i1a, &k0a, &k1a);
+  bessel_scaled(t, &i0t, &i1t, &k0t, &k1t);
+  R cK = k0a / i0a, e = w_exp(R(-2) * (a - t));
+  return a * (k1t + cK * e * i1t) / (k0t - cK * e * i0t);
+}
+
+// ---------------------------------------------------------------------------
 // Next-flight kernels (Sec. 5.2): the approximate off-centred Green's function and
 // Poisson kernel of Supplemental 1.2 on a ball of radius R (centre c), in terms of
 //   Q(r): the bracket of the centred G (G = Q/(2 pi) in 2D, Q/(4 pi) in 3D), any r > 0,

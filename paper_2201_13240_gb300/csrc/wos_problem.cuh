@@ -69,7 +69,10 @@ struct DevProblem {
   int32_t pad;
   R dom[16];
   DevField<R> alpha, phi, sigma, f, g, um;
-  const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
+  DevField<R> omega[3];     // extra drift (any vector field); has_drift when any is not ZERO
+  int32_t has_drift;
+  int32_t pad5;
+  alignas(16) const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
   const float* mesh_tris;   // 12 floats per triangle in leaf order, device
   int32_t ncsg;
   int32_t mg_res;           // mesh distance grid: nodes per axis (0: none)
@@ -289,9 +292,11 @@ WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F
 }
 
 // Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
-template <int DIM, typename R>
+// DRIFT: the problem has an extra drift omega; sp then also holds b . grad gamma + div b
+// (b = omega / alpha) and b_out receives b(y).
+template <int DIM, typename R, bool DRIFT = false>
 WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr,
-                   R* alpha_out = nullptr) {
+                   R* alpha_out = nullptr, R* b_out = nullptr) {
   FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
   FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
   FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
@@ -309,6 +314,10 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
       dp += gp[d] * gu[d];
     }
     f = -(A.v * U.lap + da) - A.v * dp + S.v * U.v;
+    if (DRIFT) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) f -= field_eval<DIM>(P, P.omega[d], y[0], y[1], y[2], false).v * gu[d];
+    }
   } else {
     f = field_eval<DIM>(P, P.f, y[0], y[1], y[2], false).v;
   }
@@ -326,6 +335,21 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
   *fp = w_exp(gam) * f * ia;
   if (gamma_out) *gamma_out = gam;
   if (alpha_out) *alpha_out = A.v;
+  if (DRIFT) {
+    // sigma'' = sigma' + b . grad gamma; div b = div omega / alpha - omega . grad alpha / alpha^2
+    R divw = R(0), wga = R(0), bg = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      FieldVal<R> Wd = field_eval<DIM>(P, P.omega[d], y[0], y[1], y[2], true);
+      const R gw[3] = {Wd.gx, Wd.gy, Wd.gz};
+      divw += gw[d];
+      wga += Wd.v * ga[d];
+      R bd = Wd.v * ia;
+      bg += bd * R(0.5) * (ga[d] * ia + gp[d]);
+      if (b_out) b_out[d] = bd;
+    }
+    *sp += bg + divw * ia - wga * ia * ia;
+  }
 }
 
 template <int DIM, typename R>

@@ -122,7 +122,10 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, W
 // Then grad u = e^{-gamma(x_0)} (grad U - U grad gamma(x_0)); e^{-gamma(x_0)} joins
 // the flush like the value's, grad gamma(x_0) is cached per lane and point.  The
 // extra FP64 partial sums take registers, so this variant runs 16 warps per SM.
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD>
+// DRIFT: the problem has an extra drift omega (not alpha times a gradient): coeffs adds
+// b . grad gamma + div b to sigma', and a null event also carries
+// |G'(r)/G(r)| (dir_y . b(y)) / sigma_bar (the drift term moved onto G by parts).
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD, bool DRIFT = false>
 __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) : 1) wos_walk_kernel(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
@@ -255,7 +258,8 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? (ends ? s.x[i] : s.x[i] + r * dy[i]) : R(0);
     R spy, fpy, gam;
-    coeffs<DIM>(P, y, &spy, &fpy, &gam);
+    R bvec[3] = {R(0), R(0), R(0)};
+    coeffs<DIM, R, DRIFT>(P, y, &spy, &fpy, &gam, nullptr, DRIFT ? bvec : nullptr);
 
     if (ends) {
       const bool lost = WW && s.dead;
@@ -372,7 +376,14 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
       ++s.steps_walk;
     }
     if (mu <= PB) {            // volume term: null event at y
-      s.W *= R(1) - spy * inv_sb;
+      R wn = R(1) - spy * inv_sb;
+      if (DRIFT) {
+        R db = R(0);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) db += dy[i] * bvec[i];
+        wn += green_dlog_r<DIM, R>(a, rho) / dd * db * inv_sb;
+      }
+      s.W *= wn;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) s.x[i] = y[i];
       if (WW) {
@@ -443,12 +454,12 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
   }
 }
 
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false>
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false, bool DRIFT = false>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD>, kWalkBlock, smem);
+      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>, kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
@@ -456,13 +467,14 @@ cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD><<<grid, kWalkBlock, smem, stream>>>(L);
+  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true, false>(L, num_sms, stream);
+  if (L.drift) return launch_walks_m<DIM, R, false, false, false, false, true>(L, num_sms, stream);
   if (L.gsum != nullptr || L.ghat != nullptr)  // spatial gradient (no weight window)
     return (DIM == 3 && L.mesh) ? launch_walks_m<DIM, R, true, false, false, true>(L, num_sms, stream)
                                 : launch_walks_m<DIM, R, false, false, false, true>(L, num_sms, stream);

@@ -159,3 +159,17 @@ def test_offcentre_kernels(hc, orc, dim, fp64):
             assert abs(out[2 * i] - g) <= tol * max(abs(g), scale), (R, sb, i)
             if abs(p) > 1e-30:
                 assert abs(out[2 * i + 1] - p) <= tol * abs(p), (R, sb, i)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_green_log_derivative(hc, orc, dim, fp64):
+    """R |G'/G| of the centred Green's function (the extra-drift weight) against the oracle."""
+    R = 0.37
+    rho = np.array([0.01, 0.1, 0.3, 0.5, 0.7, 0.9, 0.97])
+    tol = 1e-10 if fp64 else 2e-5
+    for a in (0.0, 1e-5, 1e-3, 0.05, 0.3, 1.0, 2.5, 8.0, 30.0):
+        out = np.zeros(len(rho))
+        hc.wos_hc_green_dlog(dim, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), out.ctypes.data_as(DP))
+        want = np.array([orc.green_dlog(dim, R, (a / R) ** 2, r * R) for r in rho]) * R
+        assert np.allclose(out, want, rtol=tol, atol=0), (a, out, want)
