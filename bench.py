@@ -34,6 +34,7 @@ METRIC = "walk-steps/s"
 UNIT = "steps/s"
 GRID = 64
 WALKS = 1024
+DEFAULT_WALKS = WALKS  # the other workloads use their own walk counts unless --walks is given
 EPS = 1e-4
 SEED = 0
 SIGMA_LATTICE = 64
@@ -351,7 +352,7 @@ def run_other(args):
         sb = ctx.sigma_bar(prob, 256)[0]
         pts_np = W.cell_centres(2, 32)
         pts = torch.from_numpy(pts_np).cuda()
-        walks = args.walks if args.walks != WALKS else 256
+        walks = args.walks if args.walks != DEFAULT_WALKS else 256
         (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-3, sb, seed=i), args.steps)
         m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
         exact = W.square2d_exact(*pts_np.astype(np.float64))
@@ -465,7 +466,7 @@ def run_other(args):
         sb = ctx.sigma_bar(prob, 48)[0]
         npts = args.points
         pts = torch.from_numpy(W.mesh_interior_points(npts, seed=0)).cuda()
-        walks = args.walks if args.walks != WALKS else 512
+        walks = args.walks if args.walks != DEFAULT_WALKS else 512
         (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
         if args.dist_grid > 0:
             # the same problem with a distance grid: conservative radii away from the boundary
@@ -525,7 +526,7 @@ def run_other(args):
         sb = ctx.sigma_bar(prob, 48)[0]
         npts = 4096
         pts = torch.from_numpy(W.inverse_sensors(npts)).cuda()
-        walks = args.walks if args.walks != WALKS else 1024
+        walks = args.walks if args.walks != DEFAULT_WALKS else 1024
         gu = torch.ones(npts, dtype=torch.float64, device="cuda")
         grad = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
         (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)

@@ -266,7 +266,7 @@ __global__ void mesh_grid_kernel(const DevProblem<double>* Pg, int n, double lo0
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     double x0 = lo0 + (double)(i % n) * h0, x1 = lo1 + (double)((i / n) % n) * h1,
            x2 = lo2 + (double)(i / ((int64_t)n * n)) * h2;
-    wos::MeshHit<double> hit = wos::mesh_query<double>(P, x0, x1, x2, INFINITY);
+    wos::MeshHit<double> hit = wos::mesh_query<double, false>(P, x0, x1, x2, INFINITY, nullptr, nullptr, 0);
     out64[i] = hit.d;
     out32[i] = (float)hit.d;
   }

@@ -62,7 +62,7 @@ struct Builder {
     MeshNode& N = nodes[node];
     std::memcpy(N.lo, nb.lo, sizeof(N.lo));
     std::memcpy(N.hi, nb.hi, sizeof(N.hi));
-    if (count <= kLeaf || depth >= 60) {
+    if (count <= kLeaf || depth >= 28) {  // depth <= 29: the traversal stack holds 32 entries
       N.left = first;
       N.count = count;
       return;

@@ -45,6 +45,12 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
     __syncthreads();
   }
   const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
+  int* stk_n = nullptr;
+  R* stk_d = nullptr;
+  if (MESH) {  // this thread's column of the BVH traversal stack, after the problem
+    stk_n = reinterpret_cast<int*>(smem_raw + L.problem_bytes) + threadIdx.x;
+    stk_d = reinterpret_cast<R*>(smem_raw + L.problem_bytes + sizeof(int) * kMeshStack * kNfBlock) + threadIdx.x;
+  }
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
         R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
         bound2 = e0 * e0 + e1 * e1 + e2 * e2;
       }
-      R d = distance<DIM, R, MESH>(P, x, xb, bound2);
+      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock);
       if (MESH) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
@@ -287,6 +293,12 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
 template <int DIM, typename R, bool MESH>
 cudaError_t launch_nf_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = (size_t)L.problem_bytes;
+  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kNfBlock;
+  if (smem > 48 * 1024) {
+    cudaError_t ea = cudaFuncSetAttribute(wos_nf_kernel<DIM, R, MESH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (ea != cudaSuccess) return ea;
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_nf_kernel<DIM, R, MESH>, kNfBlock, smem);
   if (e != cudaSuccess) return e;

@@ -382,7 +382,7 @@ WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
 // visits the nearer child first and skips every box farther than the best
 // triangle so far.
 // ---------------------------------------------------------------------------
-constexpr int kMeshStack = 64;  // the builder caps the tree depth at 61
+constexpr int kMeshStack = 32;  // the builder caps the tree depth at 29 (one push per level)
 
 struct F4 {
   float x, y, z, w;
@@ -459,13 +459,21 @@ struct MeshHit {
 // boxes nearer than a known boundary point are opened; if rounding still hides
 // every triangle, the search restarts without the bound.  The result does not
 // depend on the bound.
-template <typename R>
-WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2) {
+// SMEM: the stack lives in shared memory, entry k of this thread at sn[k * stride] and
+// sd[k * stride] (a column per thread: no bank conflicts); otherwise in local memory.
+// Kept in local memory by the walk kernels, the stack's divergent per-lane accesses
+// were the largest memory traffic of a mesh walk.
+template <typename R, bool SMEM>
+WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2, int* sn, R* sd,
+                                   int stride) {
   const R x[3] = {x0, x1, x2};
   const float* nodes = P.mesh_nodes;
   const float* tris = P.mesh_tris;
-  int stk_n[kMeshStack];
-  R stk_d[kMeshStack];
+  int loc_n[SMEM ? 1 : kMeshStack];
+  R loc_d[SMEM ? 1 : kMeshStack];
+  int* stk_n = SMEM ? sn : loc_n;
+  R* stk_d = SMEM ? sd : loc_d;
+  const int sst = SMEM ? stride : 1;
   R best, bv = R(0), bw = R(0);
   int best_t = -1;
   const R slack = (sizeof(R) == 4) ? R(1e-5) : R(1e-12);
@@ -491,7 +499,11 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
       int nn = (dl <= dr) ? left : left + 1;
       R dn = (dl <= dr) ? dl : dr, df = (dl <= dr) ? dr : dl;
       if (dn < best) {
-        if (df < best && sp < kMeshStack) { stk_n[sp] = (nn == left) ? left + 1 : left; stk_d[sp] = df; ++sp; }
+        if (df < best && sp < kMeshStack) {
+          stk_n[sp * sst] = (nn == left) ? left + 1 : left;
+          stk_d[sp * sst] = df;
+          ++sp;
+        }
         node = nn;
         descend = true;
       }
@@ -501,7 +513,7 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
     bool found = false;
     while (sp > 0) {
       --sp;
-      if (stk_d[sp] < best) { node = stk_n[sp]; found = true; break; }
+      if (stk_d[sp * sst] < best) { node = stk_n[sp * sst]; found = true; break; }
     }
     if (!found) break;
   }
@@ -644,7 +656,8 @@ WOS_HD R csg_sdf(const DevProblem<R>& P, const R* x, R* g) {
 // bound2 (meshes only): an upper bound of the squared distance, see mesh_query.
 // MESH = false compiles the mesh case out (for kernels launched on analytic domains).
 template <int DIM, typename R, bool MESH = true>
-WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY)) {
+WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY), int* stk_n = nullptr,
+                  R* stk_d = nullptr, int stk_stride = 0) {
   const R* p = P.dom;
 #pragma unroll
   for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
@@ -746,7 +759,8 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
         if (lo_b >= P.mg_thresh) return lo_b;  // xb unused: the walk is not in the shell
         bound2 = hi_b * hi_b;
       }
-      MeshHit<R> h = mesh_query<R>(P, x[0], x[1], x[2], bound2);
+      MeshHit<R> h = (stk_n != nullptr) ? mesh_query<R, true>(P, x[0], x[1], x[2], bound2, stk_n, stk_d, stk_stride)
+                                        : mesh_query<R, false>(P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0);
       xb[0] = h.x;
       xb[1] = h.y;
       xb[2] = h.z;

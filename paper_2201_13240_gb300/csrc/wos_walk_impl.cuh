@@ -137,6 +137,13 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
   }
   const DevProblem<R>* Pshared = reinterpret_cast<const DevProblem<R>*>(smem_raw);
   const DevProblem<R>* Pall = reinterpret_cast<const DevProblem<R>*>(L.probs);
+  // MESH: this thread's column of the BVH traversal stack, after the problem
+  int* stk_n = nullptr;
+  R* stk_d = nullptr;
+  if (MESH) {
+    stk_n = reinterpret_cast<int*>(smem_raw + L.problem_bytes) + threadIdx.x;
+    stk_d = reinterpret_cast<R*>(smem_raw + L.problem_bytes + sizeof(int) * kMeshStack * kWalkBlock) + threadIdx.x;
+  }
 
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
       R e0 = s.x[0] - s.xbp[0], e1 = s.x[1] - s.xbp[1], e2 = s.x[2] - s.xbp[2];
       bound2 = e0 * e0 + e1 * e1 + e2 * e2;
     }
-    R d = distance<DIM, R, MESH>(P, s.x, xb, bound2);
+    R d = distance<DIM, R, MESH>(P, s.x, xb, bound2, stk_n, stk_d, kWalkBlock);
     if (MESH) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) s.xbp[i] = xb[i];
@@ -457,6 +464,12 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
 template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false, bool DRIFT = false>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
+  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kWalkBlock;
+  if (smem > 48 * 1024) {
+    cudaError_t ea = cudaFuncSetAttribute(wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ea != cudaSuccess) return ea;
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>, kWalkBlock, smem);
