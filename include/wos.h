@@ -237,7 +237,9 @@ int wos_problem_destroy(wos_problem* prob);
 /* The delta-tracking bound (Sec. 5.1, Sec. 7.1: the paper's default is
    max sigma' - min sigma'): sigma' is sampled at the interior nodes of an
    m^dim lattice of cell centres over the domain's bounding box; returns (host)
-   sigma_bar = max(max - min, max, 1e-3 / diam^2), min sigma' and max sigma'.
+   sigma_bar = max(max - min, max, 1e-3 / diam^2), min sigma' and max sigma'.  With an extra
+   drift omega, sigma' includes b . grad gamma + div b (b = omega/alpha) and sigma_bar is
+   at least 50 max |b|^2 (the drift weight's variance falls like |b|^2 / sigma_bar).
    Synchronises `stream`.  Errors: WOS_EINVAL if m < 2 or alpha <= 0 at a node. */
 int wos_sigma_bar(wos_ctx* ctx, const wos_problem* prob, int32_t m, double* sigma_bar,
                   double* sigma_prime_min, double* sigma_prime_max, void* stream);

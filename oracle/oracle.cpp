@@ -1697,7 +1697,7 @@ int orc_sigma_bar(const orc_problem* P, int m, double* sigma_bar, double* smin, 
   int dim = P->dim;
   double lo[3], hi[3];
   domain_bbox(P, lo, hi);
-  double mn = INFINITY, mx = -INFINITY;
+  double mn = INFINITY, mx = -INFINITY, b2max = 0.0;
   int64_t total = 1;
   for (int d = 0; d < dim; ++d) total *= m;
   for (int64_t idx = 0; idx < total; ++idx) {
@@ -1708,16 +1708,21 @@ int orc_sigma_bar(const orc_problem* P, int m, double* sigma_bar, double* smin, 
       r /= m;
     }
     if (!(distance(P, x, xb) > 0.0)) continue;
-    double gm, sp, fp, fv, av;
-    coeffs(P, x, &gm, &sp, &fp, &fv, &av);
+    double gm, sp, fp, fv, av, b[3];
+    coeffs(P, x, &gm, &sp, &fp, &fv, &av, b);
     if (sp < mn) mn = sp;
     if (sp > mx) mx = sp;
+    double b2 = 0.0;
+    for (int d = 0; d < dim; ++d) b2 += b[d] * b[d];
+    if (b2 > b2max) b2max = b2;
   }
   double diam2 = 0.0;
   for (int d = 0; d < dim; ++d) diam2 += (hi[d] - lo[d]) * (hi[d] - lo[d]);
   double sbv = mx - mn;
   if (mx > sbv) sbv = mx;
   if (1e-3 / diam2 > sbv) sbv = 1e-3 / diam2;
+  // extra drift: the variance of its weight term falls like |b|^2 / sigma_bar
+  if (50.0 * b2max > sbv) sbv = 50.0 * b2max;
   *sigma_bar = sbv;
   *smin = mn;
   *smax = mx;

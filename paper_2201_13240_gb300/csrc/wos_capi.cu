@@ -274,10 +274,11 @@ __global__ void mesh_grid_kernel(const DevProblem<double>* Pg, int n, double lo0
 
 template <int DIM>
 __global__ void sigma_range_kernel(const DevProblem<double>* Pg, int m, double lo0, double lo1, double lo2,
-                                   double h0, double h1, double h2, double* out /* min, max, alpha_min, count */) {
+                                   double h0, double h1, double h2,
+                                   double* out /* min, max, alpha_min, count, max |omega/alpha|^2 */) {
   const DevProblem<double>& P = *Pg;
   int64_t total = (DIM == 3) ? (int64_t)m * m * m : (int64_t)m * m;
-  double mn = INFINITY, mx = -INFINITY, amin = INFINITY, cnt = 0.0;
+  double mn = INFINITY, mx = -INFINITY, amin = INFINITY, cnt = 0.0, b2max = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     double x[3] = {lo0 + (i % m + 0.5) * h0, lo1 + ((i / m) % m + 0.5) * h1,
                    DIM == 3 ? lo2 + (i / ((int64_t)m * m) + 0.5) * h2 : 0.0};
@@ -291,18 +292,28 @@ __global__ void sigma_range_kernel(const DevProblem<double>* Pg, int m, double l
     mx = fmax(mx, sp);
     amin = fmin(amin, a);
     cnt += 1.0;
+    if (P.has_drift) {
+      double b2 = 0.0;
+      for (int d = 0; d < DIM; ++d) {
+        double w = wos::field_eval<DIM>(P, P.omega[d], x[0], x[1], x[2], false).v / a;
+        b2 += w * w;
+      }
+      b2max = fmax(b2max, b2);
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, off));
     mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
     amin = fmin(amin, __shfl_down_sync(0xffffffffu, amin, off));
     cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    b2max = fmax(b2max, __shfl_down_sync(0xffffffffu, b2max, off));
   }
   if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
     atomic_min_d(&out[0], mn);
     atomic_max_d(&out[1], mx);
     atomic_min_d(&out[2], amin);
     atomicAdd(&out[3], cnt);
+    atomic_max_d(&out[4], b2max);
   }
 }
 
@@ -711,7 +722,7 @@ int wos_sigma_bar(wos_ctx* ctx, const wos_problem* pr, int32_t m, double* sb, do
   if (m < 2 || (pr->dim == 3 && m > 2048) || m > 1 << 16) return fail(ctx, WOS_EINVAL, "lattice size out of range");
   DeviceGuard g(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  double init[4] = {INFINITY, -INFINITY, INFINITY, 0.0};
+  double init[5] = {INFINITY, -INFINITY, INFINITY, 0.0, 0.0};
   double* out = reinterpret_cast<double*>(ctx->scratch + kScratchSigma);
   cudaError_t e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar init");
@@ -726,7 +737,7 @@ int wos_sigma_bar(wos_ctx* ctx, const wos_problem* pr, int32_t m, double* sb, do
     sigma_range_kernel<3><<<blocks, 256, 0, st>>>(pr->d64, m, lo[0], lo[1], lo[2], h[0], h[1], h[2], out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar kernel");
-  double res[4];
+  double res[5];
   e = cudaMemcpyAsync(res, out, sizeof(res), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sigma_bar readback");
@@ -738,6 +749,9 @@ int wos_sigma_bar(wos_ctx* ctx, const wos_problem* pr, int32_t m, double* sb, do
   double v = res[1] - res[0];
   if (res[1] > v) v = res[1];
   if (1e-3 / diam2 > v) v = 1e-3 / diam2;
+  // an extra drift's null weights carry |G'/G| (dir . b) / sigma_bar, whose second moment
+  // grows like |b|^2 / sigma_bar per null event: keep sigma_bar >= 50 max |b|^2
+  if (wos::kDriftSigmaBar * res[4] > v) v = wos::kDriftSigmaBar * res[4];
   *sb = v;
   if (smin) *smin = res[0];
   if (smax) *smax = res[1];

@@ -29,6 +29,7 @@ enum DomainKind { D_BOX = 0, D_BALL = 1, D_ANNULUS = 2, D_ROUNDED_BOX = 3, D_MES
 enum CsgPrim { C_SPHERE = 0, C_BOX = 1, C_CAPSULE = 2, C_TORUS = 3, C_HALFSPACE = 4 };
 enum CsgOp { C_UNION = 0, C_INTERSECT = 1, C_SUBTRACT = 2 };
 constexpr int kMaxCsg = 16;
+constexpr double kDriftSigmaBar = 50.0;  // sigma_bar >= this times max |omega/alpha|^2 (extra drift)
 
 template <typename R>
 struct CsgNode {

@@ -86,7 +86,8 @@ def test_progressive_frames_equal_one_solve_and_edit_resets(wos, ctx, orc):
     assert img.shape == (100, 140, 4)
     acc, _ = ctx.solve(prob, sv.pts, 8, 1e-4, sb, seed=3)
     assert torch.equal(sv.accum[2], acc[2])
-    assert torch.allclose(sv.accum[0], acc[0], rtol=1e-10, atol=1e-12)
+    # the same walks; per-lane partial sums are formed in FP32, so the order of the sums differs
+    assert torch.allclose(sv.accum[0], acc[0], rtol=1e-5, atol=1e-6)
     # slice points outside the CSG domain end at once (and are counted as such)
     st = wos.stats_dict(sv.stats)
     assert 0 < st["outside"] < st["walks"] and st["walks"] == 8 * 48 * 32

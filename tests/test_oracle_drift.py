@@ -51,7 +51,7 @@ def _expalpha_problem():
 
 CASES = {
     "square_exp_alpha": (_expalpha_problem, lambda p: W.square2d_exact(*p),
-                         lambda: W.cell_centres(2, 32)[:, W.seeded_subset(1024, 32, 4)], 20000),
+                         lambda: W.cell_centres(2, 32)[:, W.seeded_subset(1024, 32, 4)], 5000),
     "cube3d_literal": (W.cube3d_literal_problem, lambda p: W.cube3d_exact(*p),
                        lambda: W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 12, 6)], 3000),
     "square_rotational": (_rot2d_problem, lambda p: W.square2d_exact(*p),
