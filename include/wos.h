@@ -151,7 +151,7 @@ typedef struct {
      query.  n >= 4 builds, at problem creation, an n^3 grid of exact distances to the
      mesh over its bounding box (2% margin) and then takes the radius
      L = max over the 8 corners c of the point's cell of (d(c) - |x - c|), a lower bound of
-     the distance (distances are 1-Lipschitz), whenever L >= 2 |cell diagonal|; nearer the
+     the distance (distances are 1-Lipschitz), whenever L >= |cell diagonal| / 2; nearer the
      boundary the exact query runs, bounded by min over the corners of (d(c) + |x - c|).
      A ball inside the domain keeps the estimator unbiased; interior steps then cost eight
      loads instead of a BVH traversal.  Not in the paper (a distance acceleration structure

@@ -1022,7 +1022,7 @@ int orc_mesh_prepare(orc_problem* prob) {
       B->h[k] = (vhi[k] - vlo[k] + 0.04 * ext) / (n - 1);
       diag2 += B->h[k] * B->h[k];
     }
-    B->thresh = 2.0 * std::sqrt(diag2);
+    B->thresh = 0.5 * std::sqrt(diag2);
     B->dist.resize((size_t)n * n * n);
     int64_t total = (int64_t)n * n * n;
 #pragma omp parallel for schedule(dynamic, 256)

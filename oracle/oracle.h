@@ -90,7 +90,7 @@ typedef struct {
   int32_t ncsg;
   /* MESH: grid_res > 0 asks orc_mesh_prepare for a grid_res^3 grid of exact distances
      over the triangles' vertex bounds plus 2% of the largest extent; the walk radius is
-     then L = max over the cell corners c of (d(c) - |x - c|) when L >= twice the cell
+     then L = max over the cell corners c of (d(c) - |x - c|) when L >= half the cell
      diagonal, else the exact distance. */
   int32_t grid_res;
 } orc_domain;

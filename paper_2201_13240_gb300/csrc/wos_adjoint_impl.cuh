@@ -77,9 +77,12 @@ __device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, d
 
 // add vN N_m + vG . grad N_m + vL Lap N_m at y to grad[m] over the 4^DIM nodes of
 // the cubic B-spline support (indices clamped as in grid_bspline)
+// grad is indexed j0 + s1 j1 + s2 j2: the grid's own layout in global memory, a padded one
+// (s1 = res0 + 1, s2 = s1 res1 + 1) for the per-CTA copy in shared memory, which spreads the
+// rows of one support over different banks.
 template <int DIM, typename R, typename A>
 __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, const double* vG_, double vL_,
-                                A* grad) {
+                                A* grad, int64_t s1, int64_t s2) {
   const R vN = R(vN_), vL = R(vL_), vG[3] = {R(vG_[0]), R(vG_[1]), R(vG_[2])};
   int ib[3] = {0, 0, 0};
   R B[3][4], B1[3][4], B2[3][4];
@@ -115,7 +118,7 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, co
     const R b2 = (DIM == 3) ? sel4(B[2], c2) : R(1), d2 = (DIM == 3) ? sel4(B1[2], c2) : R(0);
     const R e2 = (DIM == 3) ? sel4(B2[2], c2) : R(0);
     const R b12 = b1 * b2;
-    A* row = grad + (int64_t)F.res[0] * (j1 + (int64_t)F.res[1] * j2);
+    A* row = grad + s1 * j1 + s2 * j2;
 #pragma unroll
     for (int c0 = 0; c0 < 4; ++c0) {
       const int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
@@ -162,14 +165,17 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   // alpha: per-CTA accumulators in the walk's precision (FP32 shared atomics are native)
   R* gpriv = reinterpret_cast<R*>(smem_raw + L.problem_bytes);
   const bool priv = ALPHA && L.priv_nodes > 0;
+  const DevProblem<R>& Pg0 = *reinterpret_cast<const DevProblem<R>*>(L.problem);
+  const int64_t ares0 = Pg0.alpha.res[0], ares1 = Pg0.alpha.res[1];
+  const int64_t ps1 = ares0 + 1, ps2 = ps1 * ares1 + 1;  // padded shared layout
   if (priv)
     for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x) gpriv[i] = R(0);
   __syncthreads();
   const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
 #define WOS_ALPHA_SCATTER(pt, a, b, c)                                                   \
   do {                                                                                   \
-    if (priv) bspline_scatter<DIM, R, R>(P.alpha, pt, a, b, c, gpriv);                   \
-    else bspline_scatter<DIM, R, double>(P.alpha, pt, a, b, c, L.grad_alpha);            \
+    if (priv) bspline_scatter<DIM, R, R>(P.alpha, pt, a, b, c, gpriv, ps1, ps2);         \
+    else bspline_scatter<DIM, R, double>(P.alpha, pt, a, b, c, L.grad_alpha, ares0, ares0 * ares1); \
   } while (0)
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -352,8 +358,12 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   }
   if (priv) {
     __syncthreads();
-    for (int i = threadIdx.x; i < L.priv_nodes; i += blockDim.x)
-      if (gpriv[i] != R(0)) atomicAdd(&L.grad_alpha[i], (double)gpriv[i]);
+    const int64_t ares2 = (DIM == 3) ? Pg0.alpha.res[2] : 1, nodes = ares0 * ares1 * ares2;
+    for (int64_t i = threadIdx.x; i < nodes; i += blockDim.x) {
+      const int64_t j0 = i % ares0, j1 = (i / ares0) % ares1, j2 = i / (ares0 * ares1);
+      const R v = gpriv[j0 + ps1 * j1 + ps2 * j2];
+      if (v != R(0)) atomicAdd(&L.grad_alpha[i], (double)v);
+    }
   }
 #undef WOS_ALPHA_SCATTER
 }

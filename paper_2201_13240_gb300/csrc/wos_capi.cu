@@ -678,8 +678,8 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
         h32->mg_h[k] = (float)gh[k];
         h32->mg_inv_h[k] = (float)(1.0 / gh[k]);
       }
-      pr->host64.mg_thresh = 2.0 * std::sqrt(diag2);
-      h32->mg_thresh = (float)(2.0 * std::sqrt(diag2));
+      pr->host64.mg_thresh = 0.5 * std::sqrt(diag2);
+      h32->mg_thresh = (float)(0.5 * std::sqrt(diag2));
       e = cudaMemcpy(pr->d64, &pr->host64, sizeof(DevProblem<double>), cudaMemcpyHostToDevice);
     }
   }
@@ -1103,7 +1103,9 @@ extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const floa
   L.work_counter = ctx->scratch;
   L.radial_tab = ctx->radial_tab[pr->dim - 2];
   // grids of up to 8192 nodes (64 KB of FP64) are accumulated per CTA in shared memory
-  L.priv_nodes = (nodes <= 8192) ? (int)nodes : 0;
+  // the per-CTA copy is padded (row stride res0 + 1, plane stride (res0 + 1) res1 + 1)
+  int64_t padded = ((int64_t)(H.alpha.res[0] + 1) * H.alpha.res[1] + 1) * (pr->dim == 3 ? H.alpha.res[2] : 1);
+  L.priv_nodes = (nodes <= 8192) ? (int)padded : 0;
   if (prm->precision == WOS_FP64) {
     L.problem = pr->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
