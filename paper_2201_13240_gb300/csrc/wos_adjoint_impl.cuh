@@ -47,7 +47,7 @@ namespace wos {
 constexpr int kAdjBlock = 128;
 
 template <int DIM, typename R>
-__device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, double val, double* grad) {
+__device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, R val, double* grad) {
   int i0[3] = {0, 0, 0};
   R t[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -62,16 +62,16 @@ __device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, d
   const int nc = (DIM == 3) ? 8 : 4;
 #pragma unroll
   for (int c = 0; c < nc; ++c) {
-    double w = val;
+    R w = val;
     int64_t idx = 0, stride = 1;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       int o = (c >> d) & 1;
-      w *= (double)(o ? t[d] : R(1) - t[d]);
+      w *= (o ? t[d] : R(1) - t[d]);
       idx += (int64_t)(i0[d] + o) * stride;
       stride *= F.res[d];
     }
-    if (w != 0.0) atomicAdd(&grad[idx], w);
+    if (w != R(0)) atomicAdd(&grad[idx], (double)w);
   }
 }
 
@@ -81,9 +81,8 @@ __device__ __forceinline__ void grid_scatter(const DevField<R>& F, const R* y, d
 // (s1 = res0 + 1, s2 = s1 res1 + 1) for the per-CTA copy in shared memory, which spreads the
 // rows of one support over different banks.
 template <int DIM, typename R, typename A>
-__device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, const double* vG_, double vL_,
-                                A* grad, int64_t s1, int64_t s2) {
-  const R vN = R(vN_), vL = R(vL_), vG[3] = {R(vG_[0]), R(vG_[1]), R(vG_[2])};
+__device__ void bspline_scatter(const DevField<R>& F, const R* y, R vN, const R* vG, R vL, A* grad, int64_t s1,
+                                int64_t s2) {
   int ib[3] = {0, 0, 0};
   R B[3][4], B1[3][4], B2[3][4];
 #pragma unroll
@@ -133,7 +132,7 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, double vN_, co
 
 // d sigma' / d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m at y
 template <int DIM, typename R>
-__device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, double* cN, double* cG, double* cL) {
+__device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, R* cN, R* cG, R* cL) {
   // in the walk's precision (FP64 arithmetic is a small fraction of FP32's rate here)
   FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
   FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
@@ -148,10 +147,10 @@ __device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, double* cN
     gg_ga += gg[d] * ga[d];
   }
   const R ia2 = ia * ia;
-  *cN = (double)(-S.v * ia2 - R(0.5) * A.lap * ia2 + na2 * ia2 * ia - gg_ga * ia2);
+  *cN = -S.v * ia2 - R(0.5) * A.lap * ia2 + na2 * ia2 * ia - gg_ga * ia2;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? (double)(gg[d] * ia - ga[d] * ia2) : 0.0;
-  *cL = (double)(R(0.5) * ia);
+  for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? gg[d] * ia - ga[d] * ia2 : R(0);
+  *cL = R(0.5) * ia;
 }
 
 template <int DIM, typename R, bool ALPHA>
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   R x[3] = {R(0), R(0), R(0)}, W = R(1), acc = R(0), total = R(0);
   R xbp[3] = {R(0), R(0), R(0)};  // previous closest boundary point (bounds the next mesh query)
   uint32_t p = 0, w = 0, k = 0, phase = 0;
-  double coef = 0.0;
+  R coef = R(0);  // grad_u e^{-gamma(x_0)} / walks of the walk's point (FP64 only when R is)
   unsigned long long st_steps = 0;
   uint32_t st_walks = 0, st_capped = 0;
 
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
         acc = R(0);
         k = 0;
         phase = 0;
-        coef = __ldg(&L.grad_u[p]) * inv_walks * exp(-(double)gamma_at<DIM>(P, x));
+        coef = R(__ldg(&L.grad_u[p]) * inv_walks * exp(-(double)gamma_at<DIM>(P, x)));
         active = true;
       }
       chunk_next += take;
@@ -281,9 +280,9 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
       }
       if (ALPHA && phase == 1 && !capped) {
         // boundary factor e^{gamma(x_n)}: d/d alpha_m = N_m(x_n) / (2 alpha(x_n)) times the term
-        const double vG[3] = {0.0, 0.0, 0.0};
-        double v = coef * (double)bterm * 0.5 / (double)al;
-        if (isfinite(v) && v != 0.0) WOS_ALPHA_SCATTER(y, v, vG, 0.0);
+        const R vG[3] = {R(0), R(0), R(0)};
+        R v = coef * bterm * R(0.5) / al;
+        if (isfinite(v) && v != R(0)) WOS_ALPHA_SCATTER(y, v, vG, R(0));
       }
       if (phase == 0) {
         total = acc;
@@ -291,10 +290,10 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
         for (int dd2 = 0; dd2 < 3; ++dd2) x[dd2] = (dd2 < DIM) ? R(__ldg(&L.pts[(int64_t)dd2 * L.npts + (int64_t)p])) : R(0);
         if (ALPHA) {
           // e^{-gamma(x_0)}: -A N_m(x_0) / (2 alpha(x_0))
-          const double vG[3] = {0.0, 0.0, 0.0};
-          double a0 = (double)field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
-          double v = -coef * (double)total * 0.5 / a0;
-          if (isfinite(v) && v != 0.0) WOS_ALPHA_SCATTER(x, v, vG, 0.0);
+          const R vG[3] = {R(0), R(0), R(0)};
+          R a0 = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
+          R v = -coef * total * R(0.5) / a0;
+          if (isfinite(v) && v != R(0)) WOS_ALPHA_SCATTER(x, v, vG, R(0));
         }
         W = R(1);
         acc = R(0);
@@ -311,12 +310,12 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     acc += src;
     if (ALPHA && phase == 1) {
       // source f'(y): d/d alpha_m = -N_m(y) / (2 alpha(y)) times the term; null weight: see above
-      double vN = -coef * (double)src * 0.5 / (double)al, vG[3] = {0.0, 0.0, 0.0}, vL = 0.0;
+      R vN = -coef * src * R(0.5) / al, vG[3] = {R(0), R(0), R(0)}, vL = R(0);
       if (mu <= PB) {
         R wj = R(1) - spy * inv_sb;
-        double rem = ((double)total - (double)acc) / (double)wj;
-        double rj = -coef * rem / (double)L.sigma_bar;
-        double cN, cG[3], cL;
+        R rem = (total - acc) / wj;
+        R rj = -coef * rem * inv_sb;
+        R cN, cG[3], cL;
         alpha_sensitivity<DIM, R>(P, y, &cN, cG, &cL);
         if (isfinite(rj)) {
           vN += rj * cN;
@@ -331,9 +330,9 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
       R wj = R(1) - spy * inv_sb;
       if (!ALPHA && phase == 1) {
         // d total / d w_j = (A - P_{j+1}) / w_j ; d w_j / d sigma_m = -N_m(y) / (alpha(y) sigma_bar)
-        double rem = ((double)total - (double)acc) / (double)wj;
-        double val = -coef * rem / ((double)al * (double)L.sigma_bar);
-        if (isfinite(val) && val != 0.0) grid_scatter<DIM, R>(P.sigma, y, val, L.grad_sigma);
+        R rem = (total - acc) / wj;
+        R val = -coef * rem * inv_sb / al;
+        if (isfinite(val) && val != R(0)) grid_scatter<DIM, R>(P.sigma, y, val, L.grad_sigma);
       }
       W *= wj;
 #pragma unroll
