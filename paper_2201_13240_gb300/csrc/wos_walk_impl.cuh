@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
         }
         capped = false;  // already counted per branch
       }
-      double acc_d = (double)s.acc;
+      // no FP64 arithmetic here unless a branch needs it: this block runs whenever a lane ends
       R gv[3] = {R(0), R(0), R(0)};
       if (GRAD) {
         if (s.p != gg_p) {
@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
         d2 = R(0);
       }
       if (GRAD) {
+        const double acc_d = (double)s.acc;
         s1 += acc_d;
         s2 += acc_d * acc_d;
       } else {
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
       }
       if (L.uhat != nullptr) {
         double e0 = point_factor<DIM, R>(L, P, s.p);
-        L.uhat[s.item] = acc_d * e0;
+        L.uhat[s.item] = (double)s.acc * e0;
         L.steps_out[s.item] = WW ? (int64_t)s.steps_walk : (int64_t)s.k;
         if (GRAD && L.ghat != nullptr) {
 #pragma unroll
