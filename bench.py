@@ -57,6 +57,24 @@ def workload_config(extra=None):
     return cfg
 
 
+JIT = {"compile_s": 0.0}
+
+
+def make_problem(ctx, desc, args, variants=("plain",)):
+    """Upload a problem; with --kernel specialised (the default) also compile and load the walk
+    kernels specialised to its fields (the compile time is reported, outside the timed region)."""
+    t0 = time.perf_counter()
+    prob = ctx.problem(desc, specialize=(("fp32",), variants) if args.kernel == "specialised" else None)
+    if args.kernel == "specialised":
+        JIT["compile_s"] += time.perf_counter() - t0
+    return prob
+
+
+def kernel_label(args):
+    return ("wos_walk_kernel<3,float> specialised to the problem's fields (NVRTC, sm_103a)"
+            if args.kernel == "specialised" else "wos_walk_kernel<3,float> (generic field interpreter)")
+
+
 def rank_info():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -186,7 +204,7 @@ def run_ours(args):
 
     ctx = wos.Context(local_rank)
     desc = W.cube3d_problem()
-    prob = ctx.problem(desc)
+    prob = make_problem(ctx, desc, args)
     sb, smin, smax = ctx.sigma_bar(prob, SIGMA_LATTICE)
     pts_np = W.cell_centres(3, GRID)
     npts = pts_np.shape[1]
@@ -226,6 +244,28 @@ def run_ours(args):
     times = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(times)
     st = wos.stats_dict(stats)
+    # the same steps through the generic kernel (field interpreter), for comparison
+    generic = None
+    if args.kernel == "specialised":
+        gprob = ctx.problem(desc)
+        gacc, gst = ctx.new_accum(npts), ctx.new_stats()
+        ctx.solve(gprob, pts, WALKS, EPS, sb, seed=SEED, walk_offset=offset, accum=gacc, stats=gst)
+        torch.cuda.synchronize()
+        gst.zero_()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gms = 0.0
+        for i in range(args.steps):
+            for t in gacc:
+                t.zero_()
+            flush.fill_(float(i))
+            g0.record(stream)
+            ctx.solve(gprob, pts, WALKS, EPS, sb, seed=SEED, walk_offset=offset, accum=gacc, stats=gst)
+            ctx.finalize(gacc)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            gms += g0.elapsed_time(g1)
+        generic = {"value": wos.stats_dict(gst)["steps"] / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms / args.steps}
+        gprob.close()
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -285,7 +325,7 @@ def run_ours(args):
     achieved = OPS_PER_STEP * (st["steps"] / args.steps) / (kernel_ms * 1e-3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_ops, "traffic": None,
-                "kernel": "wos_walk_kernel<3,float>", "ops_per_step": OPS_PER_STEP,
+                "kernel": kernel_label(args), "ops_per_step": OPS_PER_STEP,
                 "peak_basis": f"128 FP32/INT32 lanes x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                               "(sm_max_mhz of MEASURED_PEAKS.json)"}
 
@@ -307,7 +347,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"sigma_bar": sb, "parallelism": f"points replicated, disjoint walk ids, "
-                                                                        f"{world} GPU(s)"}),
+                                                                        f"{world} GPU(s)",
+                                       "kernel": args.kernel}),
+            "specialise_compile_s": JIT["compile_s"], "generic_kernel": generic,
             "points_per_s": world * npts / (ms_per_step * 1e-3),
             "walks_per_s": world * npts * WALKS / (ms_per_step * 1e-3),
             "steps_per_walk": steps_per_walk, "normalised_rms_at_1024_walks": rms,
@@ -348,7 +390,7 @@ def run_other(args):
 
     if wl == "square2d":
         desc = W.square2d_problem()
-        prob = ctx.problem(desc)
+        prob = make_problem(ctx, desc, args)
         sb = ctx.sigma_bar(prob, 256)[0]
         pts_np = W.cell_centres(2, 32)
         pts = torch.from_numpy(pts_np).cuda()
@@ -361,7 +403,7 @@ def run_other(args):
         npts = pts_np.shape[1]
     elif wl == "grad":
         desc = W.cube3d_problem()
-        prob = ctx.problem(desc)
+        prob = make_problem(ctx, desc, args, ("plain", "grad"))
         sb = ctx.sigma_bar(prob, 64)[0]
         pts_np = W.cell_centres(3, GRID)
         pts = torch.from_numpy(pts_np).cuda()
@@ -408,7 +450,7 @@ def run_other(args):
     elif wl == "c2literal":
         # config 2 with its literal, non-conservative drift (the extra-drift walk)
         desc = W.cube3d_literal_problem()
-        prob = ctx.problem(desc)
+        prob = make_problem(ctx, desc, args)
         sb = ctx.sigma_bar(prob, 64)[0]
         pts_np = W.cell_centres(3, GRID)
         pts = torch.from_numpy(pts_np).cuda()
@@ -435,7 +477,7 @@ def run_other(args):
         # the interactive path (Sec. 7.2): one walk per slice point per frame plus the
         # sphere-traced image of the CSG scene cut by the slice plane
         desc = W.csg_variable_problem()
-        prob = ctx.problem(desc)
+        prob = make_problem(ctx, desc, args)
         sb = ctx.sigma_bar(prob, 64)[0]
         res = args.points if args.points != 16384 else 512
         v = wos.view([-1.3, -1.3, 0.05], [2.6, 0, 0], [0, 2.6, 0], res, res, 1280, 720, (-3.0, 3.0),
@@ -470,6 +512,8 @@ def run_other(args):
         t0 = time.perf_counter()
         prob = ctx.problem(desc)
         extra["bvh_build_s"] = time.perf_counter() - t0
+        if args.kernel == "specialised":
+            prob.specialize(("fp32",), ("plain",))
         sb = ctx.sigma_bar(prob, 48)[0]
         npts = args.points
         pts = torch.from_numpy(W.mesh_interior_points(npts, seed=0)).cuda()
@@ -479,7 +523,7 @@ def run_other(args):
             # the same problem with a distance grid: conservative radii away from the boundary
             dg = W.mesh_noise_problem(level=7, dist_grid=args.dist_grid)
             t0 = time.perf_counter()
-            probg = ctx.problem(dg)
+            probg = make_problem(ctx, dg, args)
             torch.cuda.synchronize()
             build_g = time.perf_counter() - t0
             (accg, stg), msg = timed(lambda i: ctx.solve(probg, pts, walks, 1e-4, sb, seed=i), args.steps)
@@ -529,7 +573,7 @@ def run_other(args):
         sig_t = torch.from_numpy(sig).cuda()
         desc = W.inverse_problem(sig)
         desc["sigma"] = dict(desc["sigma"], data=sig_t)
-        prob = ctx.problem(desc)
+        prob = make_problem(ctx, desc, args)
         sb = ctx.sigma_bar(prob, 48)[0]
         npts = 4096
         pts = torch.from_numpy(W.inverse_sensors(npts)).cuda()
@@ -566,7 +610,8 @@ def run_other(args):
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": cfg, "steps_per_walk": stv["steps"] / max(stv["walks"], 1),
             "points_per_s": npts / (ms * 1e-3), "walks_per_s": stv["walks"] / (ms * 1e-3),
-            "capped_walks": stv["capped"], "nonfinite_walks": stv["nonfinite"]}
+            "capped_walks": stv["capped"], "nonfinite_walks": stv["nonfinite"],
+            "kernel": args.kernel if wl != "batch" else "generic", "specialise_compile_s": JIT["compile_s"]}
     line.update(extra)
     print(json.dumps(line))
     return 0
@@ -587,6 +632,8 @@ def main():
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
+    ap.add_argument("--kernel", default="specialised", choices=["specialised", "generic"],
+                    help="walk kernel: compiled for the problem's fields (default) or the generic field interpreter")
     ap.add_argument("--dist-grid", type=int, default=128,
                     help="mesh workload: also time walks with an n^3 distance grid (0: exact radii only)")
     args = ap.parse_args()

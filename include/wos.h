@@ -374,6 +374,49 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host,
                    int32_t walks_uniform, const wos_params* params, double* mean_host,
                    double* var_host, double* stderr_host, uint64_t* stats_host, void* stream);
 
+/* ---- problem-specialised walk kernels (runtime compilation) ----
+   The walk (Supplemental Alg. 1) evaluates alpha, Phi, sigma, f, g (and the
+   manufactured u, omega) with their gradients and Laplacians at every step
+   (Sec. 4.1, App. A).  wos_problem_specialize compiles, with NVRTC for sm_103a,
+   the walk kernel of this problem with those fields written out as code (the
+   problem's constants folded in); the domain, grids and every other part of the
+   walk are the same source as the generic kernel, and the estimates are the
+   same up to floating-point rounding.  It blocks for the compilation (seconds)
+   and loads the kernels on the problem's device.  Afterwards wos_solve,
+   wos_walk_estimates, wos_solve_grad, wos_walk_grad_estimates and
+   wos_solve_host on this problem launch the specialised kernel of the matching
+   precision and variant; every other variant, the next-flight walks, the
+   adjoints and batches keep the generic kernels.
+   flags: WOS_SPEC_FP32 and/or WOS_SPEC_FP64 (neither = FP32), and the variants
+   WOS_SPEC_PLAIN, WOS_SPEC_WINDOW (weight window), WOS_SPEC_GRAD (spatial
+   gradient) (none = PLAIN).  Calling it again adds variants; loaded kernels are
+   kept until wos_problem_destroy.
+   Errors: WOS_EINVAL (null handle, unknown flag); WOS_EUNSUPPORTED (libnvrtc
+   not found, a compilation error -- message in wos_last_error -- or a variant
+   the problem cannot run, e.g. a window with an extra drift); WOS_ECUDA (load). */
+#define WOS_SPEC_FP32 0x1
+#define WOS_SPEC_FP64 0x2
+#define WOS_SPEC_PLAIN 0x10
+#define WOS_SPEC_WINDOW 0x20
+#define WOS_SPEC_GRAD 0x40
+int wos_problem_specialize(wos_ctx* ctx, wos_problem* prob, int32_t flags);
+
+/* Which specialised kernels a problem holds: OR of the WOS_SPEC_* bits of the
+   loaded (precision, variant) pairs.  Host only. */
+int wos_problem_specialized(const wos_problem* prob, int32_t* flags_out);
+
+/* The generated program of a description (host only, no device): the field
+   code placed after the walk kernel's headers.  Writes up to cap-1 bytes and a
+   NUL to buf (may be NULL to query *len = full length).  WOS_EINVAL for an
+   invalid description (the reason is written to buf). */
+int wos_jit_source(const wos_problem_desc* desc, char* buf, int64_t cap, int64_t* len);
+
+/* Compile (no device, no load) the specialised kernels that flags select for a
+   description; *cubin_bytes = size of the sm_103a image.  The compiler log (or
+   the reason for a failure) is written to log (cap bytes, NUL-terminated). */
+int wos_jit_compile(const wos_problem_desc* desc, int32_t flags, char* log, int64_t log_cap,
+                    int64_t* cubin_bytes);
+
 /* ---- progressive slice view (Sec. 7.2) ----
    The paper's interactive path: a solve on the points of a slice plane that adds one walk
    per point per frame to the accumulators (discarding them when the problem is edited),

@@ -24,6 +24,7 @@ WOS_OK, WOS_EINVAL, WOS_ENOMEM, WOS_ECUDA, WOS_ETIMEOUT, WOS_EUNSUPPORTED = 0, -
 WOS_FP32, WOS_FP64 = 0, 1
 STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
 STATS_WORDS = 6
+WOS_SPEC_FP32, WOS_SPEC_FP64, WOS_SPEC_PLAIN, WOS_SPEC_WINDOW, WOS_SPEC_GRAD = 0x1, 0x2, 0x10, 0x20, 0x40
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
 _DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4, "csg": 5}
 _CSG_PRIMS = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
@@ -127,6 +128,10 @@ def load():
     lib.wos_batch_create.argtypes = [vp, C.POINTER(vp), i32, vp, vp, C.POINTER(vp)]
     lib.wos_batch_destroy.argtypes = [vp]
     lib.wos_solve_batch.argtypes = [vp, vp, vp, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_problem_specialize.argtypes = [vp, vp, i32]
+    lib.wos_problem_specialized.argtypes = [vp, C.POINTER(i32)]
+    lib.wos_jit_source.argtypes = [C.POINTER(ProblemDesc), C.c_char_p, i64, C.POINTER(i64)]
+    lib.wos_jit_compile.argtypes = [C.POINTER(ProblemDesc), i32, C.c_char_p, i64, C.POINTER(i64)]
     _lib = lib
     return lib
 
@@ -170,74 +175,140 @@ def params(eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20, precision="
     return p
 
 
+def describe(desc, device=None):
+    """The C description of a problem dict: (ProblemDesc, objects to keep alive, sigma grid
+    address, alpha grid address).  Grid data goes to cuda:device, or stays in host memory when
+    device is None (descriptions for wos_jit_source / wos_jit_compile, which never read it)."""
+    D = ProblemDesc()
+    keep = []
+    ptrs = {"sigma": 0, "alpha": 0}
+    D.dim = desc["dim"]
+    D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
+    for i, v in enumerate(desc["domain"]["p"]):
+        D.domain.p[i] = v
+    if desc["domain"]["kind"] == "mesh":
+        verts = np.ascontiguousarray(desc["domain"]["verts"], dtype=np.float32)
+        tris = np.ascontiguousarray(desc["domain"]["tris"], dtype=np.int32)
+        keep += [verts, tris]
+        D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
+        D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
+        D.domain.mesh_grid_res = int(desc["domain"].get("grid_res", 0))
+    if desc["domain"]["kind"] == "csg":
+        nodes = desc["domain"]["nodes"]
+        arr = (CsgNode * max(1, len(nodes)))()
+        for i, (prim, op, prm) in enumerate(nodes):
+            arr[i].prim = _CSG_PRIMS[prim]
+            arr[i].op = _CSG_OPS[op]
+            for k, v in enumerate(prm):
+                arr[i].p[k] = v
+        keep.append(arr)
+        D.domain.csg = C.cast(arr, C.c_void_p)
+        D.domain.ncsg = len(nodes)
+    omega = list(desc.get("omega", []))
+    omega += [{"kind": "zero"}] * (3 - len(omega))
+    slots = [(n, desc[n], getattr(D, n)) for n in ("alpha", "phi", "sigma", "f", "g", "um")]
+    slots += [(f"omega{k}", omega[k], D.omega[k]) for k in range(3)]
+    for name, fd, F in slots:
+        F.kind = _FIELD_KINDS[fd["kind"]]
+        F.value = fd.get("value", 0.0)
+        if fd["kind"] == "sst":
+            terms = (Term * max(1, len(fd["terms"])))()
+            for i, t in enumerate(fd["terms"]):
+                terms[i].c = t["c"]
+                for d, (ty, k, ph) in enumerate(t["atoms"]):
+                    terms[i].type[d], terms[i].k[d], terms[i].phi[d] = ty, k, ph
+            keep.append(terms)
+            F.nterms = len(fd["terms"])
+            F.terms = C.cast(terms, C.POINTER(Term))
+        if fd["kind"].startswith("grid"):
+            data = fd["data"]
+            if device is None:
+                if not isinstance(data, np.ndarray):
+                    data = data.detach().cpu().numpy()
+                data = np.ascontiguousarray(data, dtype=np.float32)
+                addr = data.ctypes.data
+            else:
+                import torch
+                if not isinstance(data, torch.Tensor):
+                    data = torch.as_tensor(np.ascontiguousarray(data, dtype=np.float32))
+                data = data.to(device=f"cuda:{device}", dtype=torch.float32).contiguous()
+                addr = data.data_ptr()
+            keep.append(data)
+            for d in range(3):
+                F.res[d] = fd["res"][d] if d < len(fd["res"]) else 1
+                F.lo[d] = fd["lo"][d] if d < len(fd["lo"]) else 0.0
+                F.hi[d] = fd["hi"][d] if d < len(fd["hi"]) else 0.0
+            F.data = addr
+            if name in ptrs:
+                ptrs[name] = addr
+    return D, keep, ptrs["sigma"], ptrs["alpha"]
+
+
+_SPEC_PRECISION = {"fp32": WOS_SPEC_FP32, "fp64": WOS_SPEC_FP64}
+_SPEC_VARIANT = {"plain": WOS_SPEC_PLAIN, "window": WOS_SPEC_WINDOW, "grad": WOS_SPEC_GRAD}
+
+
+def spec_flags(precisions=("fp32",), variants=("plain",)):
+    f = 0
+    for p in ([precisions] if isinstance(precisions, str) else precisions):
+        f |= _SPEC_PRECISION[p]
+    for v in ([variants] if isinstance(variants, str) else variants):
+        f |= _SPEC_VARIANT[v]
+    return f
+
+
+def jit_source(desc):
+    """The generated program of the problem-specialised walk kernel (host only)."""
+    lib = load()
+    D, keep, _, _ = describe(desc)
+    n = C.c_int64(0)
+    rc = lib.wos_jit_source(C.byref(D), None, 0, C.byref(n))
+    if rc != WOS_OK:
+        buf = C.create_string_buffer(512)
+        lib.wos_jit_source(C.byref(D), buf, 512, None)
+        raise WosError(rc, buf.value.decode(errors="replace"))
+    buf = C.create_string_buffer(n.value + 1)
+    lib.wos_jit_source(C.byref(D), buf, n.value + 1, C.byref(n))
+    return buf.value.decode()
+
+
+def jit_compile(desc, precision="fp32", variants=("plain",)):
+    """NVRTC compile of the specialised kernels (no device): (status, log, cubin bytes)."""
+    lib = load()
+    D, keep, _, _ = describe(desc)
+    log = C.create_string_buffer(1 << 16)
+    nbytes = C.c_int64(0)
+    rc = lib.wos_jit_compile(C.byref(D), spec_flags(precision, variants), log, 1 << 16, C.byref(nbytes))
+    return rc, log.value.decode(errors="replace"), nbytes.value
+
+
 class Problem:
     """A problem uploaded to the device (owns the library handle)."""
 
     def __init__(self, ctx, desc):
-        import torch
         self.ctx = ctx
         self.dim = desc["dim"]
-        self._keep = []
-        self._sigma_ptr = 0
-        self._alpha_ptr = 0
-        D = ProblemDesc()
-        D.dim = desc["dim"]
-        D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
-        for i, v in enumerate(desc["domain"]["p"]):
-            D.domain.p[i] = v
-        if desc["domain"]["kind"] == "mesh":
-            verts = np.ascontiguousarray(desc["domain"]["verts"], dtype=np.float32)
-            tris = np.ascontiguousarray(desc["domain"]["tris"], dtype=np.int32)
-            self._keep += [verts, tris]
-            D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
-            D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
-            D.domain.mesh_grid_res = int(desc["domain"].get("grid_res", 0))
-        if desc["domain"]["kind"] == "csg":
-            nodes = desc["domain"]["nodes"]
-            arr = (CsgNode * max(1, len(nodes)))()
-            for i, (prim, op, prm) in enumerate(nodes):
-                arr[i].prim = _CSG_PRIMS[prim]
-                arr[i].op = _CSG_OPS[op]
-                for k, v in enumerate(prm):
-                    arr[i].p[k] = v
-            self._keep.append(arr)
-            D.domain.csg = C.cast(arr, C.c_void_p)
-            D.domain.ncsg = len(nodes)
-        omega = list(desc.get("omega", []))
-        omega += [{"kind": "zero"}] * (3 - len(omega))
-        slots = [(n, desc[n], getattr(D, n)) for n in ("alpha", "phi", "sigma", "f", "g", "um")]
-        slots += [(f"omega{k}", omega[k], D.omega[k]) for k in range(3)]
-        for name, fd, F in slots:
-            F.kind = _FIELD_KINDS[fd["kind"]]
-            F.value = fd.get("value", 0.0)
-            if fd["kind"] == "sst":
-                terms = (Term * max(1, len(fd["terms"])))()
-                for i, t in enumerate(fd["terms"]):
-                    terms[i].c = t["c"]
-                    for d, (ty, k, ph) in enumerate(t["atoms"]):
-                        terms[i].type[d], terms[i].k[d], terms[i].phi[d] = ty, k, ph
-                self._keep.append(terms)
-                F.nterms = len(fd["terms"])
-                F.terms = C.cast(terms, C.POINTER(Term))
-            if fd["kind"].startswith("grid"):
-                data = fd["data"]
-                if not isinstance(data, torch.Tensor):
-                    data = torch.as_tensor(np.ascontiguousarray(data, dtype=np.float32))
-                data = data.to(device=f"cuda:{ctx.device}", dtype=torch.float32).contiguous()
-                self._keep.append(data)
-                for d in range(3):
-                    F.res[d] = fd["res"][d] if d < len(fd["res"]) else 1
-                    F.lo[d] = fd["lo"][d] if d < len(fd["lo"]) else 0.0
-                    F.hi[d] = fd["hi"][d] if d < len(fd["hi"]) else 0.0
-                F.data = data.data_ptr()
-                if name == "sigma":
-                    self._sigma_ptr = data.data_ptr()
-                if name == "alpha":
-                    self._alpha_ptr = data.data_ptr()
+        D, self._keep, self._sigma_ptr, self._alpha_ptr = describe(desc, ctx.device)
         h = C.c_void_p()
         ctx._check(ctx.lib.wos_problem_create(ctx.handle, C.byref(D), C.byref(h)))
         self.handle = h
         ctx._children.add(self)
+
+    def specialize(self, precisions=("fp32",), variants=("plain",)):
+        """Compile and load the walk kernels specialised to this problem's fields (NVRTC;
+        blocks for the compilation).  Later solves of the matching precision and variant
+        launch them."""
+        self.ctx._check(self.ctx.lib.wos_problem_specialize(self.ctx.handle, self.handle,
+                                                            spec_flags(precisions, variants)))
+        return self
+
+    def specialized(self):
+        """WOS_SPEC_* bits of the loaded specialised kernels."""
+        f = C.c_int32(0)
+        rc = self.ctx.lib.wos_problem_specialized(self.handle, C.byref(f))
+        if rc != WOS_OK:
+            raise WosError(rc, "wos_problem_specialized")
+        return f.value
 
     def sigma_data_ptr(self):
         """Device address of the sigma grid the problem reads (0 if sigma is not a grid)."""
@@ -324,8 +395,12 @@ class Context:
             pass
 
     # ---- calls ----
-    def problem(self, desc):
-        return Problem(self, desc)
+    def problem(self, desc, specialize=None):
+        """Upload a problem; specialize = None, or (precisions, variants) for Problem.specialize."""
+        p = Problem(self, desc)
+        if specialize:
+            p.specialize(*specialize)
+        return p
 
     def sigma_bar(self, prob, m=None, stream=None):
         if m is None:

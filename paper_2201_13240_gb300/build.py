@@ -22,11 +22,14 @@ LIB = os.path.join(HERE, "libwos.so")
 HOSTCHECK = os.path.join(HERE, "libwos_hostcheck.so")
 
 CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_nf_f32.cu", "wos_nf_f64.cu",
-              "wos_adjoint.cu", "wos_render.cu", "wos_mesh.cpp"]
+              "wos_adjoint.cu", "wos_render.cu", "wos_jit.cu", "wos_mesh.cpp"]
 HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_nf_impl.cuh", "wos_adjoint_impl.cuh",
-           "wos_internal.h", "wos_mesh.h"]
+           "wos_internal.h", "wos_mesh.h", "wos_jit.h"]
+# headers of the walk kernel, embedded in the library for the runtime-compiled (problem-
+# specialised) kernels
+JIT_HEADERS = ["wos_internal.h", "wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-I", BUILD_DIR]
 
 
 def _nvcc():
@@ -43,11 +46,37 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _write_jit_sources() -> None:
+    """_build/wos_jit_sources.inc: the walk kernel's headers as C++ raw string literals."""
+    delim = "WOSJIT"
+    names, texts = [], []
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h), encoding="utf-8") as f:
+            text = f.read()
+        if ")" + delim + '"' in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        names.append(f'"{h}"')
+        texts.append(f'R"{delim}({text}){delim}"')
+    body = ("// generated by build.py: headers of the walk kernel for runtime compilation\n"
+            f"static const int kJitHeaderCount = {len(JIT_HEADERS)};\n"
+            f"static const char* const kJitHeaderNames[] = {{{', '.join(names)}}};\n"
+            "static const char* const kJitHeaderTexts[] = {\n" + ",\n".join(texts) + "};\n")
+    out = os.path.join(BUILD_DIR, "wos_jit_sources.inc")
+    old = None
+    if os.path.exists(out):
+        with open(out, encoding="utf-8") as f:
+            old = f.read()
+    if old != body:
+        with open(out, "w", encoding="utf-8") as f:
+            f.write(body)
+
+
 def build_lib(force: bool = False, verbose: bool = False) -> str:
     deps = [os.path.join(CSRC, s) for s in CU_SOURCES + HEADERS] + [os.path.join(INCLUDE, "wos.h")]
     if not force and not _stale(LIB, deps):
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
+    _write_jit_sources()
     nvcc = _nvcc()
     procs = []
     objs = []
@@ -69,7 +98,7 @@ def build_lib(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(f"--- {s} ---\n{o}" for s, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

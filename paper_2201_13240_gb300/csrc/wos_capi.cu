@@ -4,15 +4,18 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "wos.h"
 #include "wos_internal.h"
 #include "wos_mesh.h"
+#include "wos_jit.h"
 #include "wos_problem.cuh"
 
 using wos::DevField;
@@ -64,6 +67,7 @@ struct wos_problem {
   double* mgrid64 = nullptr;    // the same grid in FP64 (replay walks)
   double mesh_lo[3] = {0, 0, 0}, mesh_hi[3] = {0, 0, 0};
   int mesh_depth = 0;
+  wos::JitState jit;  // walk kernels compiled for this problem (wos_problem_specialize)
 };
 
 namespace {
@@ -144,6 +148,33 @@ int check_field(const wos_field_desc& f, int dim, const char* name, bool is_sour
         return WOS_EINVAL;
       }
     }
+  }
+  return WOS_OK;
+}
+
+// every field of a description (the domain is checked by the caller)
+int check_fields(const wos_problem_desc& d, bool* drift, std::string* why) {
+  struct { const wos_field_desc* f; const char* n; bool src; bool c2; } fl[6] = {
+      {&d.alpha, "alpha", false, true}, {&d.phi, "phi", false, true}, {&d.sigma, "sigma", false, false},
+      {&d.f, "f", true, false},         {&d.g, "g", false, false},    {&d.um, "um", false, true}};
+  int total_terms = 0;
+  for (auto& x : fl) {
+    if (check_field(*x.f, d.dim, x.n, x.src, x.c2, why) != WOS_OK) return WOS_EINVAL;
+    if (x.f->kind == WOS_FIELD_SST) total_terms += x.f->nterms;
+  }
+  *drift = false;
+  for (int k = 0; k < d.dim; ++k) {
+    if (check_field(d.omega[k], d.dim, "omega", false, true, why) != WOS_OK) return WOS_EINVAL;
+    if (d.omega[k].kind == WOS_FIELD_SST) total_terms += d.omega[k].nterms;
+    if (d.omega[k].kind != WOS_FIELD_ZERO) *drift = true;
+  }
+  if (d.alpha.kind == WOS_FIELD_ZERO || (d.alpha.kind == WOS_FIELD_CONST && !(d.alpha.value > 0))) {
+    *why = "alpha must be > 0";
+    return WOS_EINVAL;
+  }
+  if (total_terms > wos::kMaxTerms) {
+    *why = "more than 96 separable terms in total";
+    return WOS_EINVAL;
   }
   return WOS_OK;
 }
@@ -430,7 +461,15 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   const bool nf = nf_max_inner > 0;
   if (L.drift && (nf || gsum || ghat || prm->ww_lo != 0.0))
     return fail(ctx, WOS_EUNSUPPORTED, "an extra drift (omega) works with the plain solve only");
-  if (prm->precision == WOS_FP64) {
+  const bool fp64 = prm->precision == WOS_FP64;
+  const int variant = (gsum || ghat) ? wos::kJitGrad : (prm->ww_lo != 0.0 ? wos::kJitWindow : wos::kJitPlain);
+  cudaKernel_t spec = nf ? nullptr : prob->jit.kernel[fp64 ? 1 : 0][variant];
+  if (spec != nullptr) {
+    // the walk kernel compiled for this problem's fields
+    L.problem = fp64 ? (const void*)prob->d64 : (const void*)prob->d32;
+    L.problem_bytes = fp64 ? (int)sizeof(DevProblem<double>) : (int)sizeof(DevProblem<float>);
+    e = wos::launch_walks_kernel(L, spec, fp64 ? 8 : 4, ctx->num_sms, st);
+  } else if (fp64) {
     L.problem = prob->d64;
     L.problem_bytes = (int)sizeof(DevProblem<double>);
     e = nf ? wos::launch_nf_f64(L, ctx->num_sms, st) : wos::launch_walks_f64(L, ctx->num_sms, st);
@@ -583,25 +622,11 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
       return fail(ctx, WOS_EINVAL, "unknown domain kind");
   }
   std::string why;
-  struct { const wos_field_desc* f; const char* n; bool src; bool c2; } fl[6] = {
-      {&d->alpha, "alpha", false, true}, {&d->phi, "phi", false, true}, {&d->sigma, "sigma", false, false},
-      {&d->f, "f", true, false},         {&d->g, "g", false, false},    {&d->um, "um", false, true}};
-  int total_terms = 0;
-  for (auto& x : fl) {
-    if (check_field(*x.f, d->dim, x.n, x.src, x.c2, &why) != WOS_OK) return fail(ctx, WOS_EINVAL, why);
-    if (x.f->kind == WOS_FIELD_SST) total_terms += x.f->nterms;
-  }
   bool drift = false;
-  for (int k = 0; k < d->dim; ++k) {
-    if (check_field(d->omega[k], d->dim, "omega", false, true, &why) != WOS_OK) return fail(ctx, WOS_EINVAL, why);
-    if (d->omega[k].kind == WOS_FIELD_SST) total_terms += d->omega[k].nterms;
-    if (d->omega[k].kind != WOS_FIELD_ZERO) drift = true;
-  }
+  int rc = check_fields(*d, &drift, &why);
+  if (rc != WOS_OK) return fail(ctx, rc, why);
   if (drift && d->domain.kind == WOS_DOMAIN_MESH)
     return fail(ctx, WOS_EUNSUPPORTED, "an extra drift (omega) on a mesh domain is not supported");
-  if (d->alpha.kind == WOS_FIELD_ZERO) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
-  if (d->alpha.kind == WOS_FIELD_CONST && !(d->alpha.value > 0)) return fail(ctx, WOS_EINVAL, "alpha must be > 0");
-  if (total_terms > wos::kMaxTerms) return fail(ctx, WOS_EINVAL, "more than 96 separable terms in total");
 
   wos_problem* pr = new wos_problem();
   pr->ctx = ctx;
@@ -710,6 +735,7 @@ int wos_problem_destroy(wos_problem* pr) {
     if (pr->mesh_tris) cudaFree(pr->mesh_tris);
     if (pr->mgrid32) cudaFree(pr->mgrid32);
     if (pr->mgrid64) cudaFree(pr->mgrid64);
+    wos::jit_release(&pr->jit);
   }
   delete pr;
   return WOS_OK;
@@ -972,6 +998,99 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* pr, const float* pts_host, i
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host solve readback");
   return WOS_OK;
+}
+
+// ---- problem-specialised walk kernels (runtime compilation) ----
+namespace {
+const int32_t kSpecFlags = WOS_SPEC_FP32 | WOS_SPEC_FP64 | WOS_SPEC_PLAIN | WOS_SPEC_WINDOW | WOS_SPEC_GRAD;
+
+int spec_variants(int32_t flags) {
+  int vm = 0;
+  if (flags & WOS_SPEC_PLAIN) vm |= 1 << wos::kJitPlain;
+  if (flags & WOS_SPEC_WINDOW) vm |= 1 << wos::kJitWindow;
+  if (flags & WOS_SPEC_GRAD) vm |= 1 << wos::kJitGrad;
+  return vm ? vm : 1 << wos::kJitPlain;
+}
+
+// the fields of a description, checked and filled as wos_problem_create does (no device)
+int host_problem(const wos_problem_desc* d, DevProblem<double>* P, std::string* why) {
+  if (d->dim != 2 && d->dim != 3) {
+    *why = "dim must be 2 or 3";
+    return WOS_EINVAL;
+  }
+  bool drift = false;
+  int rc = check_fields(*d, &drift, why);
+  if (rc != WOS_OK) return rc;
+  fill_problem(*P, *d);
+  return WOS_OK;
+}
+
+void copy_text(const std::string& t, char* buf, int64_t cap) {
+  if (!buf || cap <= 0) return;
+  size_t n = std::min((size_t)(cap - 1), t.size());
+  std::memcpy(buf, t.data(), n);
+  buf[n] = '\0';
+}
+}  // namespace
+
+int wos_problem_specialize(wos_ctx* ctx, wos_problem* pr, int32_t flags) {
+  if (!ctx) return WOS_EINVAL;
+  if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
+  if (flags & ~kSpecFlags) return fail(ctx, WOS_EINVAL, "unknown specialisation flag");
+  const int vm = spec_variants(flags);
+  const bool want32 = (flags & WOS_SPEC_FP32) || !(flags & WOS_SPEC_FP64);
+  const bool want64 = (flags & WOS_SPEC_FP64) != 0;
+  DeviceGuard g(pr->device);
+  std::string why;
+  for (int fp64 = 0; fp64 < 2; ++fp64) {
+    if (!(fp64 ? want64 : want32)) continue;
+    int rc = wos::jit_specialise(&pr->jit, pr->host64, fp64 != 0, vm, &why);
+    if (rc != WOS_OK) return fail(ctx, rc, "specialise: " + why);
+  }
+  return WOS_OK;
+}
+
+int wos_problem_specialized(const wos_problem* pr, int32_t* flags_out) {
+  if (!pr || !flags_out) return WOS_EINVAL;
+  int32_t f = 0;
+  static const int32_t vbit[wos::kJitVariants] = {WOS_SPEC_PLAIN, WOS_SPEC_WINDOW, WOS_SPEC_GRAD};
+  for (int p = 0; p < 2; ++p)
+    for (int v = 0; v < wos::kJitVariants; ++v)
+      if (pr->jit.kernel[p][v] != nullptr) f |= (p ? WOS_SPEC_FP64 : WOS_SPEC_FP32) | vbit[v];
+  *flags_out = f;
+  return WOS_OK;
+}
+
+int wos_jit_source(const wos_problem_desc* d, char* buf, int64_t cap, int64_t* len) {
+  if (!d) return WOS_EINVAL;
+  std::unique_ptr<DevProblem<double>> P(new DevProblem<double>());
+  std::string why;
+  int rc = host_problem(d, P.get(), &why);
+  if (rc != WOS_OK) {
+    copy_text(why, buf, cap);
+    return rc;
+  }
+  const std::string src = wos::jit_source(*P);
+  if (len) *len = (int64_t)src.size();
+  copy_text(src, buf, cap);
+  return WOS_OK;
+}
+
+int wos_jit_compile(const wos_problem_desc* d, int32_t flags, char* log, int64_t log_cap, int64_t* cubin_bytes) {
+  if (!d || (flags & ~kSpecFlags)) return WOS_EINVAL;
+  std::unique_ptr<DevProblem<double>> P(new DevProblem<double>());
+  std::string why;
+  int rc = host_problem(d, P.get(), &why);
+  if (rc != WOS_OK) {
+    copy_text(why, log, log_cap);
+    return rc;
+  }
+  std::vector<char> cubin;
+  std::vector<std::string> lowered;
+  rc = wos::jit_compile(*P, (flags & WOS_SPEC_FP64) != 0, spec_variants(flags), &cubin, &lowered, &why);
+  copy_text(why, log, log_cap);
+  if (cubin_bytes) *cubin_bytes = (int64_t)cubin.size();
+  return rc;
 }
 
 }  // extern "C"

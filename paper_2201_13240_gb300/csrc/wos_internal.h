@@ -2,8 +2,12 @@
 // walk-kernel translation units (not part of the public interface).
 #pragma once
 
+#if defined(__CUDACC_RTC__)
+#include "wos_math.cuh"  // fixed-width integer types of runtime compilation
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace wos {
 
@@ -74,12 +78,18 @@ struct AdjLaunch {
   const float* radial_tab;
 };
 
+#if !defined(__CUDACC_RTC__)
 cudaError_t launch_adjoint_f32(const AdjLaunch& L, int num_sms, cudaStream_t stream);
 cudaError_t launch_adjoint_f64(const AdjLaunch& L, int num_sms, cudaStream_t stream);
 
 // launch the persistent walk kernel; returns a cudaError_t
 cudaError_t launch_walks_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
 cudaError_t launch_walks_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream);
+
+// a walk kernel compiled at run time for one problem (same parameter block and launch
+// shape as wos_walk_kernel); real_bytes = sizeof the walk's real type
+cudaError_t launch_walks_kernel(const WalkLaunch& L, cudaKernel_t kernel, int real_bytes, int num_sms,
+                                cudaStream_t stream);
 
 // next-flight walks (Sec. 5.2)
 cudaError_t launch_nf_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);
@@ -88,5 +98,6 @@ cudaError_t launch_nf_f64(const WalkLaunch& L, int num_sms, cudaStream_t stream)
 // per-SM resident blocks of the walk kernel (for reporting)
 int walk_blocks_per_sm_f32(int dim);
 int walk_blocks_per_sm_f64(int dim);
+#endif
 
 }  // namespace wos

@@ -14,9 +14,19 @@
 // Everything is __host__ __device__ so the same code can be checked on a CPU.
 #pragma once
 
+#if defined(__CUDACC_RTC__)
+// runtime compilation (the problem-specialised walk kernel): device built-ins only
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#define INFINITY __int_as_float(0x7f800000)
+#define NAN __int_as_float(0x7fffffff)
+#else
 #include <stdint.h>
 
 #include <cmath>
+#endif
 
 #if defined(__CUDACC__)
 #define WOS_HD __host__ __device__ __forceinline__

@@ -10,8 +10,10 @@
 //     f' = e^gamma f / alpha,  g' = e^gamma g,  Lap U - sigma' U = -f'.
 #pragma once
 
+#if !defined(__CUDACC_RTC__)
 #include <stdint.h>
 #include <string.h>
+#endif
 
 #include "wos_math.cuh"
 
@@ -292,21 +294,36 @@ WOS_FIELD_FN FieldVal<R> field_eval(const DevProblem<R>& P, const DevField<R>& F
   return o;
 }
 
+// Fields as the walk kernel reads them.  A kernel compiled at run time for one
+// problem (WOS_JIT_FIELDS) evaluates each of its fields by generated straight-line
+// code with the problem's constants folded in (jit_field, emitted after this
+// header); every other kernel interprets the field descriptors.
+enum FieldId { FLD_ALPHA = 0, FLD_PHI = 1, FLD_SIGMA = 2, FLD_F = 3, FLD_G = 4, FLD_UM = 5, FLD_OMEGA0 = 6 };
+#if defined(WOS_JIT_FIELDS)
+template <int DIM, typename R>
+__device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id, R x0, R x1, R x2, bool deriv);
+#define WOS_FIELD(P, ID, F, x0, x1, x2, deriv) jit_field<DIM, R>(P, ID, x0, x1, x2, deriv)
+#define WOS_F_KIND(P) (WOS_JIT_F_KIND)
+#else
+#define WOS_FIELD(P, ID, F, x0, x1, x2, deriv) field_eval<DIM>(P, F, x0, x1, x2, deriv)
+#define WOS_F_KIND(P) ((P).f.kind)
+#endif
+
 // Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
 // DRIFT: the problem has an extra drift omega; sp then also holds b . grad gamma + div b
 // (b = omega / alpha) and b_out receives b(y).
 template <int DIM, typename R, bool DRIFT = false>
 WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr,
                    R* alpha_out = nullptr, R* b_out = nullptr) {
-  FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
-  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
-  FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
+  FieldVal<R> A = WOS_FIELD(P, FLD_ALPHA, P.alpha, y[0], y[1], y[2], true);
+  FieldVal<R> Ph = WOS_FIELD(P, FLD_PHI, P.phi, y[0], y[1], y[2], true);
+  FieldVal<R> S = WOS_FIELD(P, FLD_SIGMA, P.sigma, y[0], y[1], y[2], false);
   const R ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
   R f;
-  if (P.f.kind == F_MANUFACTURED) {
+  if (WOS_F_KIND(P) == F_MANUFACTURED) {
     // eq. 1 solved for f at the manufactured u: f = -(alpha Lap u + grad alpha . grad u)
     //                                              - alpha grad Phi . grad u + sigma u
-    FieldVal<R> U = field_eval<DIM>(P, P.um, y[0], y[1], y[2], true);
+    FieldVal<R> U = WOS_FIELD(P, FLD_UM, P.um, y[0], y[1], y[2], true);
     const R gu[3] = {U.gx, U.gy, U.gz};
     R da = R(0), dp = R(0);
 #pragma unroll
@@ -317,10 +334,10 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
     f = -(A.v * U.lap + da) - A.v * dp + S.v * U.v;
     if (DRIFT) {
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) f -= field_eval<DIM>(P, P.omega[d], y[0], y[1], y[2], false).v * gu[d];
+      for (int d = 0; d < DIM; ++d) f -= WOS_FIELD(P, FLD_OMEGA0 + d, P.omega[d], y[0], y[1], y[2], false).v * gu[d];
     }
   } else {
-    f = field_eval<DIM>(P, P.f, y[0], y[1], y[2], false).v;
+    f = WOS_FIELD(P, FLD_F, P.f, y[0], y[1], y[2], false).v;
   }
   R ia = w_div(R(1), A.v);
   R na2 = R(0), ng2 = R(0);
@@ -341,7 +358,7 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
     R divw = R(0), wga = R(0), bg = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      FieldVal<R> Wd = field_eval<DIM>(P, P.omega[d], y[0], y[1], y[2], true);
+      FieldVal<R> Wd = WOS_FIELD(P, FLD_OMEGA0 + d, P.omega[d], y[0], y[1], y[2], true);
       const R gw[3] = {Wd.gx, Wd.gy, Wd.gz};
       divw += gw[d];
       wga += Wd.v * ga[d];
@@ -355,16 +372,16 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
 
 template <int DIM, typename R>
 WOS_HD R gamma_at(const DevProblem<R>& P, const R* x) {
-  R a = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
-  R ph = field_eval<DIM>(P, P.phi, x[0], x[1], x[2], false).v;
+  R a = WOS_FIELD(P, FLD_ALPHA, P.alpha, x[0], x[1], x[2], false).v;
+  R ph = WOS_FIELD(P, FLD_PHI, P.phi, x[0], x[1], x[2], false).v;
   return R(0.5) * w_log(a) + R(0.5) * ph;
 }
 
 // grad gamma = (grad alpha / alpha + grad Phi) / 2 (Sec. 4.1, App. A)
 template <int DIM, typename R>
 WOS_HD void grad_gamma_at(const DevProblem<R>& P, const R* x, R* g) {
-  FieldVal<R> A = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], true);
-  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, x[0], x[1], x[2], true);
+  FieldVal<R> A = WOS_FIELD(P, FLD_ALPHA, P.alpha, x[0], x[1], x[2], true);
+  FieldVal<R> Ph = WOS_FIELD(P, FLD_PHI, P.phi, x[0], x[1], x[2], true);
   R ia = R(1) / A.v;
   g[0] = R(0.5) * (A.gx * ia + Ph.gx);
   g[1] = R(0.5) * (A.gy * ia + Ph.gy);
@@ -373,7 +390,7 @@ WOS_HD void grad_gamma_at(const DevProblem<R>& P, const R* x, R* g) {
 
 template <int DIM, typename R>
 WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
-  return field_eval<DIM>(P, P.g, x[0], x[1], x[2], false).v;
+  return WOS_FIELD(P, FLD_G, P.g, x[0], x[1], x[2], false).v;
 }
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,9 @@
 // all walks of a point, multiplies the partial sums when they are flushed.
 #pragma once
 
+#if !defined(__CUDACC_RTC__)
 #include <cuda_runtime.h>
+#endif
 
 #include "wos_internal.h"
 #include "wos_math.cuh"
@@ -462,6 +464,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
   }
 }
 
+#if !defined(__CUDACC_RTC__)
 template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false, bool DRIFT = false>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
@@ -507,5 +510,6 @@ int blocks_per_sm_t() {
                                                 sizeof(DevProblem<R>));
   return per_sm;
 }
+#endif  // !__CUDACC_RTC__
 
 }  // namespace wos
