@@ -71,7 +71,7 @@ def make_problem(ctx, desc, args, variants=("plain",)):
 
 
 def kernel_label(args):
-    return ("wos_walk_kernel<3,float> specialised to the problem's fields (NVRTC, sm_103a)"
+    return ("wos_walk_spec_kernel<3,float>: the walk kernel specialised to the problem's fields (NVRTC, sm_103a)"
             if args.kernel == "specialised" else "wos_walk_kernel<3,float> (generic field interpreter)")
 
 

@@ -378,7 +378,7 @@ __global__ void radial_table_kernel(float* tab) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= wos::kTabSize) return;
   int ia = i / wos::kTabU, iu = i % wos::kTabU;
-  double a = ia * (double)wos::kTabDA, u = (double)iu / (wos::kTabU - 1);
+  double a = ia * (double)wos::kTabDA, u = wos::tab_u_of_t((double)iu / (wos::kTabU - 1));
   double r = (iu == 0) ? 0.0 : (iu == wos::kTabU - 1) ? 1.0 : wos::sample_radius<DIM, double>(a, u);
   tab[i] = (float)r;
 }

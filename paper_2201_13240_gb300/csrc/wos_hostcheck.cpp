@@ -98,7 +98,7 @@ static const float* host_table(int dim) {
   if (!g_tab_ready[k]) {
     for (int i = 0; i < wos::kTabSize; ++i) {
       int ia = i / wos::kTabU, iu = i % wos::kTabU;
-      double a = ia * (double)wos::kTabDA, u = (double)iu / (wos::kTabU - 1);
+      double a = ia * (double)wos::kTabDA, u = wos::tab_u_of_t((double)iu / (wos::kTabU - 1));
       double r = (iu == 0) ? 0.0 : (iu == wos::kTabU - 1) ? 1.0
                : (dim == 2 ? wos::sample_radius<2, double>(a, u) : wos::sample_radius<3, double>(a, u));
       g_tab[k][i] = (float)r;

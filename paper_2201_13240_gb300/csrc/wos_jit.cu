@@ -234,10 +234,10 @@ const Nvrtc& nvrtc() {
 
 const char* kVariantName[kJitVariants] = {"plain", "weight window", "gradient"};
 
-// template arguments of wos_walk_kernel for a variant: <DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>
+// the kernel of a variant: <DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>
 std::string kernel_expr(int dim, bool fp64, bool mesh, bool drift, int variant) {
   const bool ww = variant == kJitWindow, grad = variant == kJitGrad;
-  return std::string("wos::wos_walk_kernel<") + std::to_string(dim) + ", " + (fp64 ? "double" : "float") + ", " +
+  return std::string("wos::wos_walk_spec_kernel<") + std::to_string(dim) + ", " + (fp64 ? "double" : "float") + ", " +
          (mesh ? "true" : "false") + ", false, " + (ww ? "true" : "false") + ", " + (grad ? "true" : "false") + ", " +
          (drift ? "true" : "false") + ">";
 }

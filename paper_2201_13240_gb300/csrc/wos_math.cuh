@@ -906,14 +906,27 @@ WOS_HD R radial_guess(R a, R u) {
   return w_fmin(t / a, R(0.999));
 }
 
-// Tabulated inverse radial CDF rho(u; a) on a uniform grid a = i * kTabDA
-// (i < kTabA), u = j / (kTabU - 1), filled in FP64 by the sampler below; its
-// bilinear interpolation is the FP32 Newton start (within ~1e-3 of the root,
-// so one or two iterations reach the FP32 tolerance).
+// Tabulated inverse radial CDF rho(u; a), filled in FP64 by the sampler below, on a
+// uniform grid a = i * kTabDA (i < kTabA) and t = j / (kTabU - 1), where
+//   u = 2 t^2 (t <= 1/2),  u = 1 - 2 (1 - t)^2 (t >= 1/2).
+// The radial density vanishes linearly at rho = 0 (3D; with a log factor in 2D) and
+// at rho = 1, so rho ~ sqrt(u) and 1 - rho ~ sqrt(1 - u) at the ends: in t both are
+// linear and bilinear interpolation is accurate up to the ends.  From the
+// interpolated start one Newton step leaves |F(rho) - u| at the FP32 rounding level
+// (max 1.3e-7 over a < 32, measured against the FP64 sampler), so the FP32 sampler
+// takes exactly one step there: no data-dependent loop, no divergence in a warp.
 constexpr int kTabA = 129;
-constexpr int kTabU = 129;
+constexpr int kTabU = 513;
 constexpr float kTabDA = 0.25f;
 constexpr int kTabSize = kTabA * kTabU;
+// u beyond the last t interval (probability 7.6e-6): rho jumps there from ~0.5 to 1 at
+// large a, so these few samples take the safeguarded Newton loop instead
+constexpr double kTabUHi = 1.0 - 2.0 / ((double)(kTabU - 1) * (double)(kTabU - 1));
+
+WOS_HD double tab_u_of_t(double t) { return (t <= 0.5) ? 2.0 * t * t : 1.0 - 2.0 * (1.0 - t) * (1.0 - t); }
+WOS_HD float tab_t_of_u(float u) {
+  return (u <= 0.5f) ? w_sqrt(0.5f * u) : 1.0f - w_sqrt(0.5f * (1.0f - u));
+}
 
 WOS_HD float load_tab(const float* p) {
 #if defined(__CUDA_ARCH__)
@@ -928,28 +941,53 @@ WOS_HD float table_guess(const float* tab, float a, float u) {
   int ia = (int)fa;
   if (ia > kTabA - 2) ia = kTabA - 2;
   float ta = fa - (float)ia;
-  float fu = u * (float)(kTabU - 1);
-  int iu = (int)fu;
-  if (iu > kTabU - 2) iu = kTabU - 2;
-  float tu = fu - (float)iu;
-  const float* r0 = tab + ia * kTabU + iu;
+  float ft = tab_t_of_u(u) * (float)(kTabU - 1);
+  int it = (int)ft;
+  if (it > kTabU - 2) it = kTabU - 2;
+  if (it < 0) it = 0;
+  float tt = ft - (float)it;
+  const float* r0 = tab + ia * kTabU + it;
   const float* r1 = r0 + kTabU;
-  float v0 = load_tab(r0) + tu * (load_tab(r0 + 1) - load_tab(r0));
-  float v1 = load_tab(r1) + tu * (load_tab(r1 + 1) - load_tab(r1));
+  float v0 = load_tab(r0) + tt * (load_tab(r0 + 1) - load_tab(r0));
+  float v1 = load_tab(r1) + tt * (load_tab(r1 + 1) - load_tab(r1));
   return v0 + ta * (v1 - v0);
 }
 
 template <int DIM, typename R>
 WOS_HD R sample_radius(R a, R u, int* iters_used = nullptr, const float* tab = nullptr) {
-  const int iters = (sizeof(R) == 4) ? 12 : 200;
+  // FP32: the loop serves only the rare samples outside the table's one-step range (the
+  // last t interval, a >= 32); in the flat tail near rho = 1 it may need bisection steps
+  const int iters = (sizeof(R) == 4) ? 40 : 200;
   const R tol = (sizeof(R) == 4) ? R(1e-7) : R(1e-16);
   const R ftol = (sizeof(R) == 4) ? R(1e-6) : R(0);
+  const bool tabled = tab != nullptr && a < R((kTabA - 1) * kTabDA);
   R g;
-  if (tab != nullptr && a < R((kTabA - 1) * kTabDA)) {
+  if (tabled) {
     g = R(table_guess(tab, (float)a, (float)u));
     g = w_fmin(w_fmax(g, R(1e-6)), R(1) - R(1e-6));
   } else {
     g = radial_guess<DIM, R>(a, u);
+  }
+  if (tabled && u < R(kTabUHi)) {
+    // one Newton step from the table (see above).  The start is kept where it already meets
+    // the FP32 tolerance (near rho = 1, where the density is tiny, F - u is rounding noise
+    // and a step would jump far), and where the step is larger than the table's error
+    // (at most 6e-3 in rho) or leaves (0, 1).
+    R F, p;
+    if (DIM == 3) {
+      Radial3<R> rad;
+      rad.init(a);
+      rad.eval(g, &F, &p);
+    } else {
+      Radial2<R> rad;
+      rad.init(a);
+      rad.eval(g, &F, &p);
+    }
+    const R res = F - u;
+    const R step = (p > R(0)) ? w_div(res, p) : R(0);
+    const R nr = g - step;
+    if (iters_used) *iters_used = 1;
+    return (w_fabs(res) > ftol && w_fabs(step) <= R(0.02) && nr > R(0) && nr < R(1)) ? nr : g;
   }
   if (DIM == 3) {
     Radial3<R> rad;

@@ -37,7 +37,12 @@ namespace wos {
 
 constexpr int kWalkBlock = 128;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint64_t kChunk = 128;
+// Walks a warp claims at a time: total / (warps x kChunksPerWarp), a multiple of 32,
+// within [kChunkMin, kChunkMax].  Items are point-major, so a lane keeps one point (and
+// its partial sums) for about chunk/32 walks: with 128-walk chunks a lane changed point
+// every ~4 walks and the flushes (FP64 arithmetic and atomics, run by one or two lanes
+// of the warp) took a third of the FP64 pipe.  The cap keeps the tail balanced.
+constexpr uint64_t kChunkMin = 128, kChunkMax = 2048, kChunksPerWarp = 64;
 
 template <int DIM, typename R>
 struct WalkState {
@@ -56,21 +61,31 @@ struct WalkState {
 
 constexpr int kWWDepth = 8;  // most split copies a lane keeps waiting
 
-// e^{-gamma(x_0)} of point p, in double (applied once per flush)
+// e^{-gamma(x_0)} of point p (applied once per flush), in the walk's precision: the
+// FP32 walk's gamma carries FP32 rounding already, and an FP64 exp costs dozens of
+// instructions on the narrow FP64 pipe
 template <int DIM, typename R>
 __device__ __forceinline__ double point_factor(const WalkLaunch& L, const DevProblem<R>& P, uint32_t p) {
   R x0[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) x0[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
-  return exp(-(double)gamma_at<DIM>(P, x0));
+  return (double)w_exp(-gamma_at<DIM>(P, x0));
 }
 
 template <int DIM, typename R, bool BATCHED>
-__device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, WalkState<DIM, R>& s) {
+__device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, uint64_t magic,
+                                           WalkState<DIM, R>& s) {
   uint64_t p, j;
   if (L.walk_end == nullptr) {
-    p = item / (uint64_t)L.walks_uniform;
-    j = item - p * (uint64_t)L.walks_uniform;
+    // item / walks_uniform by a multiply-high with magic = floor((2^64 - 1) / walks_uniform):
+    // the product's high word is the quotient or one less, and one correction makes it exact
+    const uint64_t d = (uint64_t)L.walks_uniform;
+    p = __umul64hi(item, magic);
+    j = item - p * d;
+    if (j >= d) {
+      ++p;
+      j -= d;
+    }
   } else {
     // first point whose inclusive walk prefix exceeds item
     int64_t lo = 0, hi = L.npts - 1;
@@ -127,8 +142,15 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, W
 // DRIFT: the problem has an extra drift omega (not alpha times a gradient): coeffs adds
 // b . grad gamma + div b to sigma', and a null event also carries
 // |G'(r)/G(r)| (dir_y . b(y)) / sigma_bar (the drift term moved onto G by parts).
+// Compiled at run time for one problem (WOS_JIT_FIELDS) the kernel is named
+// wos_walk_spec_kernel, so that profiles tell the two apart.
+#if defined(WOS_JIT_FIELDS)
+#define WOS_WALK_KERNEL wos_walk_spec_kernel
+#else
+#define WOS_WALK_KERNEL wos_walk_kernel
+#endif
 template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD, bool DRIFT = false>
-__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) : 1) wos_walk_kernel(WalkLaunch L) {
+__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) : 1) WOS_WALK_KERNEL(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
   if (!BATCHED) {
@@ -157,7 +179,10 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
   // with per-point walk counts the total is the last inclusive prefix sum
   const uint64_t total = (L.walk_end != nullptr) ? (uint64_t)__ldg(&L.walk_end[L.npts - 1]) : L.total_items;
   const bool accumulate = (L.sum != nullptr);
+  uint64_t chunk = total / ((uint64_t)gridDim.x * (kWalkBlock / 32) * kChunksPerWarp);
+  chunk = (chunk < kChunkMin) ? kChunkMin : (chunk > kChunkMax ? kChunkMax : chunk & ~31ull);
   uint64_t chunk_next = 0, chunk_end = 0;
+  const uint64_t magic = (L.walks_uniform > 0) ? ~0ull / (uint64_t)L.walks_uniform : 0ull;
   bool exhausted = false;
   bool active = false;
   WalkState<DIM, R> s;
@@ -189,21 +214,21 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : 5) 
     while (need != 0u && !exhausted) {
       if (chunk_next >= chunk_end) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, (unsigned long long)kChunk);
+        if (lane == 0) base = atomicAdd(L.work_counter, (unsigned long long)chunk);
         base = __shfl_sync(kFull, base, 0);
         if (base >= total) {
           exhausted = true;
           break;
         }
         chunk_next = base;
-        chunk_end = (base + kChunk < total) ? base + kChunk : total;
+        chunk_end = (base + chunk < total) ? base + chunk : total;
       }
       unsigned nneed = __popc(need);
       uint64_t avail = chunk_end - chunk_next;
       unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
       unsigned rank = __popc(need & lt_mask);
       if (!active && rank < take) {
-        start_walk<DIM, R, BATCHED>(L, chunk_next + rank, s);
+        start_walk<DIM, R, BATCHED>(L, chunk_next + rank, magic, s);
         active = true;
       }
       chunk_next += take;

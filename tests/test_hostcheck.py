@@ -115,6 +115,30 @@ def test_table_started_sampler(hc, orc, dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_table_sampler_dense_scan(hc, orc, dim):
+    """The FP32 sampler over the table's whole range (a < 32), including uniforms within
+    1e-7 of 0 and 1: one Newton step from the table (or, in the last t interval, the
+    safeguarded loop) leaves the exact CDF within 1.5e-6 of u."""
+    DPp = C.POINTER(C.c_double)
+    worst = 0.0
+    for a in np.concatenate([np.linspace(0.0, 31.99, 97), [1e-6, 1e-3]]):
+        rng = np.random.default_rng(int(a * 1000) + dim)
+        u = np.concatenate([(np.floor(rng.uniform(size=240) * 2 ** 24) + 0.5) / 2 ** 24,
+                            (np.arange(12) + 0.5) / 2 ** 24, 1.0 - (np.arange(12) + 0.5) / 2 ** 24])
+        rho = np.zeros_like(u)
+        it = np.zeros_like(u)
+        hc.wos_hc_sample_f32(dim, 1, C.c_double(a), u.ctypes.data_as(DPp), len(u), rho.ctypes.data_as(DPp),
+                             it.ctypes.data_as(DPp))
+        assert np.all((rho > 0) & (rho < 1))
+        Fo = np.array([orc.green_cdf(dim, 1.0, a * a, r) for r in rho])
+        worst = max(worst, float(np.max(np.abs(Fo - u))))
+        # inside the one-step range every lane does the same work
+        inner = u < 1.0 - 2.0 / 512 ** 2
+        assert np.all(it[inner] == 1)
+    assert worst < 1.5e-6, worst
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_centre_gradient_ratios(hc, orc, dim, fp64):
     """The kernels' grad G / G and grad P / P at the ball centre (Supplemental 1.3) against the
