@@ -81,7 +81,7 @@ void gen_atom(std::string& out, int n, int i, int type, double k, double ph, Ato
       return;
     case A_SINH:
     case A_COSH: {
-      out += "    const R x" + sfx + " = w_exp(" + t + "), y" + sfx + " = R(1) / x" + sfx + ";\n";
+      out += "    const R x" + sfx + " = w_exp(" + t + "), y" + sfx + " = w_div(R(1), x" + sfx + ");\n";
       out += "    const R sh" + sfx + " = R(0.5) * (x" + sfx + " - y" + sfx + "), ch" + sfx + " = R(0.5) * (x" + sfx +
              " + y" + sfx + ");\n";
       const std::string sh = "sh" + sfx, ch = "ch" + sfx;

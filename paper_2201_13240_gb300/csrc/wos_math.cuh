@@ -206,13 +206,13 @@ WOS_HD float as_i1_small(float x) {  // x <= 3.75
               t * (0.00301532f + t * 0.00032411f))))));
 }
 WOS_HD float as_i0s_large(float x) {  // x >= 3.75: e^{-x} I0(x)
-  float t = 3.75f / x;
+  float t = w_div(3.75f, x);
   float p = 0.39894228f + t * (0.01328592f + t * (0.00225319f + t * (-0.00157565f + t * (0.00916281f +
             t * (-0.02057706f + t * (0.02635537f + t * (-0.01647633f + t * 0.00392377f)))))));
   return p * w_rsqrt(x);
 }
 WOS_HD float as_i1s_large(float x) {  // x >= 3.75: e^{-x} I1(x)
-  float t = 3.75f / x;
+  float t = w_div(3.75f, x);
   float p = 0.39894228f + t * (-0.03988024f + t * (-0.00362018f + t * (0.00163801f + t * (-0.01031555f +
             t * (0.02282967f + t * (-0.02895312f + t * (0.01787654f - t * 0.00420059f)))))));
   return p * w_rsqrt(x);
@@ -230,13 +230,13 @@ WOS_HD float as_k1_poly(float x) {
          t * (-0.00110404f - t * 0.00004686f)))));
 }
 WOS_HD float as_k0s_large(float x) {  // x >= 2: e^{x} K0(x)
-  float t = 2.0f / x;
+  float t = w_div(2.0f, x);
   float p = 1.25331414f + t * (-0.07832358f + t * (0.02189568f + t * (-0.01062446f + t * (0.00587872f +
             t * (-0.00251540f + t * 0.00053208f)))));
   return p * w_rsqrt(x);
 }
 WOS_HD float as_k1s_large(float x) {  // x >= 2: e^{x} K1(x)
-  float t = 2.0f / x;
+  float t = w_div(2.0f, x);
   float p = 1.25331414f + t * (0.23498619f + t * (-0.03655620f + t * (0.01504268f + t * (-0.00780353f +
             t * (0.00325614f - t * 0.00068245f)))));
   return p * w_rsqrt(x);
@@ -338,8 +338,8 @@ WOS_HD float green_q3(float a) {
     return 0.16666667f + t * (-0.019444444f + t * (0.0020502645f - t * 0.00020998677f));
   }
   float e = w_exp(-a);
-  float ratio = 2.0f * a * e / (1.0f - e * e);  // a / sinh a
-  return (1.0f - ratio) / (a * a);
+  float ratio = w_div(2.0f * a * e, 1.0f - e * e);  // a / sinh a
+  return w_div(1.0f - ratio, a * a);
 }
 WOS_HD double green_q3(double a) {
   if (a < 1.0) {  // (sinh a - a)/(a^2 sinh a) by the series of sinh a - a
@@ -362,13 +362,13 @@ WOS_HD float green_q2(float a) {
     float s = 0.25f, term = 0.25f;  // (I0-1)/a^2 = 1/4 sum_{k>=1} q^(k-1)/(k!)^2
 #pragma unroll
     for (int k = 2; k < 12; ++k) {
-      term *= q / (float)(k * k);
+      term *= q * (1.0f / (float)(k * k));
       s += term;
     }
-    return s / (1.0f + a * a * s);
+    return w_div(s, 1.0f + a * a * s);
   }
-  float inv_i0 = w_exp(-a) / as_i0s_large(a);  // 1/I0(a)
-  return (1.0f - inv_i0) / (a * a);
+  float inv_i0 = w_div(w_exp(-a), as_i0s_large(a));  // 1/I0(a)
+  return w_div(1.0f - inv_i0, a * a);
 }
 WOS_HD double green_q2(double a) {
   if (a == 0.0) return 0.25;
@@ -405,9 +405,9 @@ WOS_HD void bessel_scaled(float x, float* i0s, float* i1s, float* k0s, float* k1
   if (x <= 2.0f) {
     float lt = w_log(0.5f * x);
     float k0 = as_k0_poly(x) - lt * as_i0_small(x);
-    float k1 = (1.0f + as_k1_poly(x) + x * lt * as_i1_small(x)) / x;
-    *k0s = k0 / ex;
-    *k1s = k1 / ex;
+    float k1 = w_div(1.0f + as_k1_poly(x) + x * lt * as_i1_small(x), x);
+    *k0s = w_div(k0, ex);
+    *k1s = w_div(k1, ex);
   } else {
     *k0s = as_k0s_large(x);
     *k1s = as_k1s_large(x);
@@ -639,16 +639,16 @@ struct Radial3 {
       R cj = R(1), T = R(0);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        R m = R(2 * j + 1);
-        c[j] = cj / ((m + R(1)) * (m + R(2)));
+        // divisors are constants of the unrolled loop: multiplies by folded reciprocals
+        c[j] = cj * (R(1) / R((2 * j + 2) * (2 * j + 3)));
         T += c[j];
-        cj *= a * a / (R(2 * j + 2) * R(2 * j + 3));
+        cj *= a * a * (R(1) / R((2 * j + 2) * (2 * j + 3)));
       }
-      invT = R(1) / T;
+      invT = w_div(R(1), T);
     } else {
       R ea = w_exp(-a);
       e2a = ea * ea;
-      invD = R(1) / (R(1) - R(2) * a * ea - e2a);
+      invD = w_div(R(1), R(1) - R(2) * a * ea - e2a);
     }
   }
   // h(x) = 1 - e^x (1 - x), series for |x| < 1/2
@@ -656,8 +656,9 @@ struct Radial3 {
     if (w_fabs(x) < R(0.5)) {
       const int nt = (sizeof(R) == 4) ? 9 : 20;
       R term = x, acc = R(0);
+#pragma unroll
       for (int m = 2; m < nt; ++m) {
-        term *= x / R(m);
+        term *= x * (R(1) / R(m));
         acc += term * R(m - 1);
       }
       return acc;
@@ -723,7 +724,7 @@ struct Radial2<float> {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (k > 0) {
-          b *= q / (float)(k * k);
+          b *= q * (1.0f / (float)(k * k));
           H += 1.0f / (float)k;
         }
         bk[k] = b;
@@ -731,25 +732,25 @@ struct Radial2<float> {
         I0 += b;
         S += H * b;
       }
-      float beta = S / I0;
+      float beta = w_div(S, I0);
       float N1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        float m = 2.0f * k + 2.0f;
-        A[k] = bk[k] / m;
-        B[k] = bk[k] * (1.0f / (m * m) + (Hk[k] - beta) / m);
+        const float im = 1.0f / (2.0f * k + 2.0f);  // a constant of the unrolled loop
+        A[k] = bk[k] * im;
+        B[k] = bk[k] * (im * im + (Hk[k] - beta) * im);
         Dd[k] = bk[k];
         Cc[k] = bk[k] * (Hk[k] - beta);
         N1 += B[k];
       }
-      invN1 = 1.0f / N1;  // N(1)/a^2 = B(1)
+      invN1 = w_div(1.0f, N1);  // N(1)/a^2 = B(1)
     } else {
       float ea = w_exp(-a);
       e2a = ea * ea;
       float i0s = (a < 3.75f) ? as_i0_small(a) * ea : as_i0s_large(a);
       float k0s = as_k0s_large(a);  // a >= 2
-      c_scaled = k0s / i0s;         // c = c_scaled e^{-2a}
-      invN1 = 1.0f / (1.0f - ea / i0s);
+      c_scaled = w_div(k0s, i0s);   // c = c_scaled e^{-2a}
+      invN1 = w_div(1.0f, 1.0f - w_div(ea, i0s));
     }
   }
   WOS_HD void eval(float rho, float* F, float* pdf) const {

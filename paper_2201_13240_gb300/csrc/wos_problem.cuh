@@ -115,7 +115,7 @@ WOS_HD void atom(int type, R k, R ph, R x, R* h, R* h1, R* h2) {
     }
     case A_SINH:
     case A_COSH: {
-      R e = w_exp(t), ei = R(1) / e;
+      R e = w_exp(t), ei = w_div(R(1), e);
       R sh = R(0.5) * (e - ei), ch = R(0.5) * (e + ei);
       if (type == A_SINH) { *h = sh; *h1 = k * ch; *h2 = k * k * sh; }
       else { *h = ch; *h1 = k * sh; *h2 = k * k * ch; }
@@ -710,7 +710,7 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
         rad = (din < dout) ? p[3] : p[4];
       }
       if (r == R(0)) { v[0] = R(1); r = R(1); }
-      R s = rad / r;
+      R s = w_div(rad, r);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) xb[d] = p[d] + v[d] * s;
       return dist;
@@ -730,7 +730,7 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
       }
       if (out2 > R(0)) {
         R od = w_sqrt(out2);
-        R s = rc / od;
+        R s = w_div(rc, od);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           R c = w_fmin(w_fmax(rel[d], -inner[d]), inner[d]);
