@@ -39,11 +39,13 @@ EPS = 1e-4
 SEED = 0
 SIGMA_LATTICE = 64
 # Algorithmic work of one walk step of this workload in ALU issue slots (FP32/INT32
-# lane operations; each special-function op counted as 8, the FP32:MUFU rate ratio):
-# Philox 2 blocks 160, uniforms 18, directions 16 + 6 MUFU, distance 17, Green's
-# norm 14 + 3 MUFU, radial inverse CDF 140 + 14 MUFU, coefficients 196 + 12 MUFU,
-# update 12  ->  573 ALU + 35 MUFU = 853.
-OPS_PER_STEP = 853
+# lane operations; each special-function op counted as 8, the FP32:MUFU rate ratio),
+# for a minimal implementation of the step with the fields as code: Philox 2 blocks
+# 160, uniforms 18, directions 16 + 6 MUFU, box distance 17, Green's norm 14 + 3 MUFU,
+# radius (table start + one Newton step of the radial CDF) 62 + 6 MUFU, coefficients
+# (alpha, Phi, sigma, u_m with value/gradient/Laplacian, f, the transform) 74 + 12 MUFU,
+# update 12  ->  373 ALU + 27 MUFU = 589.
+OPS_PER_STEP = 589
 L2_FLUSH_BYTES = 512 << 20
 
 

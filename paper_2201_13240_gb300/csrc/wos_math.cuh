@@ -860,6 +860,59 @@ struct Radial2<double> {
   }
 };
 
+// One evaluation of the 2D radial CDF and density (the one-step sampler).  For a < 2 the
+// series of Radial2<float> is summed in a single pass: with B_k = b_k/m^2 + b_k H_k/m
+// - beta b_k/m and C_k = b_k H_k - beta b_k, the beta terms factor out of the sums, so
+// no coefficient arrays are formed (they cost registers and spills in the walk kernel).
+WOS_HD void radial2_once(float a, float rho, float* F, float* pdf) {
+  if (a >= 2.0f) {
+    Radial2<float> rad;
+    rad.init(a);
+    rad.eval(rho, F, pdf);
+    return;
+  }
+  if (rho <= 0.0f) {
+    *F = 0.0f;
+    *pdf = 0.0f;
+    return;
+  }
+  const float q = 0.25f * a * a, r2 = rho * rho;
+  float b = 1.0f, H = 0.0f, rk = 1.0f;
+  float I0 = 0.0f, S = 0.0f, pa = 0.0f, pb1 = 0.0f, pb2 = 0.0f, pc1 = 0.0f, pd = 0.0f;
+  float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k > 0) {
+      b *= q * (1.0f / (float)(k * k));
+      H += 1.0f / (float)k;
+      rk *= r2;
+    }
+    const float im = 1.0f / (2.0f * k + 2.0f);
+    const float bi = b * im, bh = b * H;
+    I0 += b;
+    S += bh;
+    n1 += bi * im;
+    n2 += bh * im;
+    n3 += bi;
+    pa += bi * rk;
+    pb1 += bi * im * rk;
+    pb2 += bh * im * rk;
+    pc1 += bh * rk;
+    pd += b * rk;
+  }
+  const float beta = w_div(S, I0);
+  const float invN1 = w_div(1.0f, n1 + n2 - beta * n3);
+  const float pb = pb1 + pb2 - beta * pa, pc = pc1 - beta * pd;
+  const float lr = w_log(rho);
+  *F = r2 * (pb - lr * pa) * invN1;
+  *pdf = rho * (pc - lr * pd) * invN1;
+}
+WOS_HD void radial2_once(double a, double rho, double* F, double* pdf) {
+  Radial2<double> rad;
+  rad.init(a);
+  rad.eval(rho, F, pdf);
+}
+
 // ---------------------------------------------------------------------------
 // Radius of y ~ G/|G| on the centred ball: r = R F^{-1}(u), safeguarded Newton.
 // FP32 runs a fixed number of iterations from a closed-form starting point;
@@ -980,9 +1033,7 @@ WOS_HD R sample_radius(R a, R u, int* iters_used = nullptr, const float* tab = n
       rad.init(a);
       rad.eval(g, &F, &p);
     } else {
-      Radial2<R> rad;
-      rad.init(a);
-      rad.eval(g, &F, &p);
+      radial2_once(a, g, &F, &p);
     }
     const R res = F - u;
     const R step = (p > R(0)) ? w_div(res, p) : R(0);
