@@ -613,7 +613,7 @@ def run_other(args):
             "config": cfg, "steps_per_walk": stv["steps"] / max(stv["walks"], 1),
             "points_per_s": npts / (ms * 1e-3), "walks_per_s": stv["walks"] / (ms * 1e-3),
             "capped_walks": stv["capped"], "nonfinite_walks": stv["nonfinite"],
-            "kernel": args.kernel if wl != "batch" else "generic", "specialise_compile_s": JIT["compile_s"]}
+            "kernel": args.kernel if wl not in ("batch", "nf") else "generic", "specialise_compile_s": JIT["compile_s"]}
     line.update(extra)
     print(json.dumps(line))
     return 0
