@@ -550,6 +550,12 @@ def run_other(args):
         wt = torch.from_numpy(walks_np).cuda()
         acc = ctx.new_accum(pts.shape[1])
         stt = ctx.new_stats()
+        if not args.no_autotune:
+            # launch schedule (chunk, register cap) from trial launches at 1/16 of the walks
+            t0 = time.perf_counter()
+            sched, best_ms, default_ms = ctx.batch_autotune(batch, pts, wt, 1e-3, seed=1, trial_shift=4)
+            extra["autotune"] = {"schedule": sched, "trial_ms": best_ms, "default_trial_ms": default_ms,
+                                 "tune_s": time.perf_counter() - t0}
         graph = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -634,6 +640,7 @@ def main():
     ap.add_argument("--points", type=int, default=16384, help="mesh workload: interior points")
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
+    ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default launch schedule")
     ap.add_argument("--kernel", default="specialised", choices=["specialised", "generic"],
                     help="walk kernel: compiled for the problem's fields (default) or the generic field interpreter")
     ap.add_argument("--dist-grid", type=int, default=128,

@@ -366,6 +366,39 @@ int wos_solve_batch(wos_ctx* ctx, const wos_batch* batch, const float* pts, cons
                     int32_t walks_uniform, const wos_params* params, double* sum, double* sumsq, int64_t* count,
                     uint64_t* stats, void* stream);
 
+/* Launch schedule of a batch's persistent launch (not in the paper).  The work queue
+   hands each warp `chunk` consecutive (point, walk) items at a time: small chunks balance
+   the tail, large ones keep a lane on one point (fewer partial-sum flushes).
+     chunk          0 = the kernel's rule (total / (warps x 64), 128..2048), else a
+                    multiple of 32 in 32..65536
+     blocks_per_sm  0 = as many 128-thread blocks as fit, else 1..32 (capped by what fits)
+     regs_variant   0 = the default register cap, 1 = 64 registers (8 blocks per SM)
+     reserved       0
+   The schedule changes which lane runs which walk, not the walks: the same seed gives the
+   same walk estimates, and sums that differ only in the order of additions. */
+typedef struct {
+  int32_t chunk;
+  int32_t blocks_per_sm;
+  int32_t regs_variant;
+  int32_t reserved;
+} wos_schedule;
+
+/* Set (sched NULL = default) or read a batch's schedule; WOS_EINVAL for a value out of range. */
+int wos_batch_set_schedule(wos_batch* batch, const wos_schedule* sched);
+int wos_batch_get_schedule(const wos_batch* batch, wos_schedule* sched);
+
+/* Autotuner: times trial launches of this batch over candidate schedules (the kernel's
+   chunk rule and chunks 64..2048, at both register caps), each with walks per point
+   reduced to max(1, walks >> trial_shift) (0..16; 4 is a sixteenth), keeps the fastest in the
+   batch and returns it with its trial time (*best_ms) and the default schedule's
+   (*default_ms; either pointer may be NULL).  It allocates trial accumulators on the device,
+   synchronises `stream` after every trial and frees them before returning: call it before
+   capturing the batch's solve in a CUDA graph, not inside one.  Arguments as
+   wos_solve_batch; the trial sums are discarded. */
+int wos_batch_autotune(wos_ctx* ctx, wos_batch* batch, const float* pts, const int32_t* walks,
+                       int32_t walks_uniform, const wos_params* params, int32_t trial_shift,
+                       wos_schedule* best, double* best_ms, double* default_ms, void* stream);
+
 /* End-to-end convenience: HOST points in, HOST mean / variance / stderr out (and
    HOST stats if non-NULL).  Copies the inputs to device buffers owned by the
    context (grown as needed), runs wos_solve on fresh accumulators and

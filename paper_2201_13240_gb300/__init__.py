@@ -87,6 +87,14 @@ class ProblemDesc(C.Structure):
                 ("omega", FieldDesc * 3)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("regs_variant", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {"chunk": self.chunk, "blocks_per_sm": self.blocks_per_sm, "regs_variant": self.regs_variant}
+
+
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("sigma_bar", C.c_double), ("seed", C.c_uint64), ("walk_offset", C.c_uint64),
                 ("max_steps", C.c_int64), ("precision", C.c_int32), ("ww_depth", C.c_int32), ("ww_lo", C.c_double),
@@ -128,6 +136,9 @@ def load():
     lib.wos_batch_create.argtypes = [vp, C.POINTER(vp), i32, vp, vp, C.POINTER(vp)]
     lib.wos_batch_destroy.argtypes = [vp]
     lib.wos_solve_batch.argtypes = [vp, vp, vp, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_batch_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    lib.wos_batch_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    lib.wos_batch_autotune.argtypes = [vp, vp, vp, vp, i32, C.POINTER(Params), i32, C.POINTER(Schedule), dp, dp, vp]
     lib.wos_problem_specialize.argtypes = [vp, vp, i32]
     lib.wos_problem_specialized.argtypes = [vp, C.POINTER(i32)]
     lib.wos_jit_source.argtypes = [C.POINTER(ProblemDesc), C.c_char_p, i64, C.POINTER(i64)]
@@ -348,6 +359,20 @@ class Batch:
                                             sbs.ctypes.data, C.byref(h)))
         self.handle = h
         ctx._children.add(self)
+
+    def schedule(self):
+        """The batch's launch schedule (dict: chunk, blocks_per_sm, regs_variant)."""
+        sc = Schedule()
+        rc = self.ctx.lib.wos_batch_get_schedule(self.handle, C.byref(sc))
+        if rc != WOS_OK:
+            raise WosError(rc, "wos_batch_get_schedule")
+        return sc.as_dict()
+
+    def set_schedule(self, chunk=0, blocks_per_sm=0, regs_variant=0):
+        sc = Schedule(int(chunk), int(blocks_per_sm), int(regs_variant), 0)
+        rc = self.ctx.lib.wos_batch_set_schedule(self.handle, C.byref(sc))
+        if rc != WOS_OK:
+            raise WosError(rc, "invalid schedule")
 
     def close(self):
         if getattr(self, "handle", None):
@@ -621,6 +646,26 @@ class Context:
                                              _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]), _ptr(stats),
                                              _stream(stream)))
         return accum, stats
+
+    def batch_autotune(self, batch, pts, walks, eps, seed=0, trial_shift=4, precision="fp32", stream=None):
+        """Time candidate launch schedules of the batch on trial walks (walks >> trial_shift)
+        and keep the fastest in the batch: (schedule dict, best trial ms, default trial ms)."""
+        import torch
+        pts = _points(pts, batch.dim, self.device)
+        if isinstance(walks, int):
+            wp, wu = None, walks
+        else:
+            if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                    and walks.shape == (pts.shape[1],)):
+                raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+            wp, wu = _ptr(walks.contiguous()), 0
+        p = params(eps, 1.0, seed, 0, 1 << 20, precision)
+        sc = Schedule()
+        best, dflt = C.c_double(), C.c_double()
+        self._check(self.lib.wos_batch_autotune(self.handle, batch.handle, _ptr(pts), wp, wu, C.byref(p),
+                                                int(trial_shift), C.byref(sc), C.byref(best), C.byref(dflt),
+                                                _stream(stream)))
+        return sc.as_dict(), best.value, dflt.value
 
     def adjoint_sigma(self, prob, pts, walks, grad_u, grad_sigma, eps, sigma_bar, seed=0, walk_offset=0,
                       max_steps=1 << 20, precision="fp32", stats=None, stream=None):

@@ -51,6 +51,7 @@ struct wos_batch {
   int64_t* offsets = nullptr;         // [nprob + 1]
   double* sigma_bars = nullptr;       // [nprob]
   int64_t* walk_end = nullptr;        // [npts] prefix sums for per-point walk counts
+  wos_schedule sched = {0, 0, 0, 0};  // launch schedule (wos_batch_set_schedule / autotune)
 };
 
 struct wos_problem {
@@ -1300,10 +1301,130 @@ extern "C" int wos_batch_destroy(wos_batch* b) {
   return WOS_OK;
 }
 
+namespace {
+int solve_batch_impl(wos_ctx* ctx, const wos_batch* b, const wos_schedule& sched, const float* pts,
+                     const int32_t* walks, int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq,
+                     int64_t* count, uint64_t* stats, void* stream);
+
+bool valid_schedule(const wos_schedule& s) {
+  const bool chunk_ok = s.chunk == 0 || (s.chunk >= 32 && s.chunk <= 65536 && s.chunk % 32 == 0);
+  return chunk_ok && s.blocks_per_sm >= 0 && s.blocks_per_sm <= 32 && (s.regs_variant == 0 || s.regs_variant == 1) &&
+         s.reserved == 0;
+}
+
+__global__ void trial_walks_kernel(const int32_t* walks, int64_t n, int32_t uniform, int shift, int32_t* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t w = walks ? walks[i] : uniform;
+    out[i] = (w > 0) ? max(1, w >> shift) : 0;
+  }
+}
+}  // namespace
+
+extern "C" int wos_batch_set_schedule(wos_batch* b, const wos_schedule* sched) {
+  if (!b) return WOS_EINVAL;
+  wos_schedule s = sched ? *sched : wos_schedule{0, 0, 0, 0};
+  if (!valid_schedule(s)) return WOS_EINVAL;
+  b->sched = s;
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_get_schedule(const wos_batch* b, wos_schedule* out) {
+  if (!b || !out) return WOS_EINVAL;
+  *out = b->sched;
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_autotune(wos_ctx* ctx, wos_batch* b, const float* pts, const int32_t* walks,
+                                  int32_t walks_uniform, const wos_params* prm, int32_t trial_shift,
+                                  wos_schedule* best_out, double* best_ms, double* default_ms, void* stream) {
+  if (!ctx) return WOS_EINVAL;
+  if (!b || b->ctx != ctx) return fail(ctx, WOS_EINVAL, "null batch or batch of another context");
+  if (!prm || !pts) return fail(ctx, WOS_EINVAL, "null params or points");
+  if (trial_shift < 0 || trial_shift > 16) return fail(ctx, WOS_EINVAL, "trial_shift must be in 0..16");
+  if (!walks && walks_uniform <= 0) return fail(ctx, WOS_EINVAL, "walks_uniform must be > 0");
+  if (b->npts == 0) return fail(ctx, WOS_EINVAL, "empty batch");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // trial buffers: walks per point >> trial_shift (at least 1 where the walk count is > 0),
+  // and accumulators; freed before returning
+  const int64_t n = b->npts;
+  int32_t* tw = nullptr;
+  double* acc = nullptr;
+  int64_t* cnt = nullptr;
+  unsigned long long* stt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (tw) cudaFree(tw);
+    if (acc) cudaFree(acc);
+    if (cnt) cudaFree(cnt);
+    if (stt) cudaFree(stt);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&tw, sizeof(int32_t) * n) != cudaSuccess || cudaMalloc(&acc, 2 * sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(int64_t) * n) != cudaSuccess ||
+      cudaMalloc(&stt, wos::ST_WORDS * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, WOS_ENOMEM, "autotune trial buffers");
+  }
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, WOS_ECUDA, "autotune events");
+  }
+  trial_walks_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(walks, n, walks_uniform, trial_shift, tw);
+  // candidates: the kernel's own chunk rule and fixed chunks, at both register caps
+  std::vector<wos_schedule> cand;
+  const int32_t chunks[] = {0, 64, 128, 256, 512, 1024, 2048};
+  for (int rv = 0; rv < 2; ++rv)
+    for (int32_t c : chunks) cand.push_back(wos_schedule{c, 0, rv, 0});
+  double best = 1e300, dflt = -1.0;
+  wos_schedule best_s = cand[0];
+  int rc = WOS_OK;
+  for (size_t i = 0; i <= cand.size() && rc == WOS_OK; ++i) {
+    // i == 0 warms up with the first candidate (untimed)
+    const wos_schedule& sc = cand[i == 0 ? 0 : i - 1];
+    cudaMemsetAsync(acc, 0, 2 * sizeof(double) * n, st);
+    cudaMemsetAsync(cnt, 0, sizeof(int64_t) * n, st);
+    cudaEventRecord(e0, st);
+    rc = solve_batch_impl(ctx, b, sc, pts, tw, 0, prm, acc, acc + n, cnt, reinterpret_cast<uint64_t*>(stt), stream);
+    cudaEventRecord(e1, st);
+    if (rc != WOS_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = cuda_fail(ctx, cudaGetLastError(), "autotune trial");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (i == 0) continue;
+    if (i == 1) dflt = ms;
+    if (ms < best) {
+      best = ms;
+      best_s = sc;
+    }
+  }
+  cleanup();
+  if (rc != WOS_OK) return rc;
+  b->sched = best_s;
+  if (best_out) *best_out = best_s;
+  if (best_ms) *best_ms = best;
+  if (default_ms) *default_ms = dflt;
+  return WOS_OK;
+}
+
 extern "C" int wos_solve_batch(wos_ctx* ctx, const wos_batch* b, const float* pts, const int32_t* walks,
                                int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq,
                                int64_t* count, uint64_t* stats, void* stream) {
   if (!ctx) return WOS_EINVAL;
+  if (!b || b->ctx != ctx) return fail(ctx, WOS_EINVAL, "null batch or batch of another context");
+  return solve_batch_impl(ctx, b, b->sched, pts, walks, walks_uniform, prm, sum, sumsq, count, stats, stream);
+}
+
+namespace {
+int solve_batch_impl(wos_ctx* ctx, const wos_batch* b, const wos_schedule& sched, const float* pts,
+                     const int32_t* walks, int32_t walks_uniform, const wos_params* prm, double* sum, double* sumsq,
+                     int64_t* count, uint64_t* stats, void* stream) {
   if (!b || b->ctx != ctx) return fail(ctx, WOS_EINVAL, "null batch or batch of another context");
   if (!prm) return fail(ctx, WOS_EINVAL, "params is NULL");
   if (!finite_pos(prm->eps) || prm->max_steps < 1 || (prm->precision != WOS_FP32 && prm->precision != WOS_FP64))
@@ -1355,6 +1476,9 @@ extern "C" int wos_solve_batch(wos_ctx* ctx, const wos_batch* b, const float* pt
   L.prob_offsets = b->offsets;
   L.sigma_bars = b->sigma_bars;
   L.nprob = b->nprob;
+  L.chunk = (uint32_t)sched.chunk;
+  L.blocks_per_sm = sched.blocks_per_sm;
+  L.regs_variant = sched.regs_variant;
   if (prm->precision == WOS_FP64) {
     L.probs = b->d64;
     e = wos::launch_walks_f64(L, ctx->num_sms, st);
@@ -1365,6 +1489,7 @@ extern "C" int wos_solve_batch(wos_ctx* ctx, const wos_batch* b, const float* pt
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batched walk kernel launch");
   return WOS_OK;
 }
+}  // namespace
 
 // ===========================================================================
 // Allocation-free solve.

@@ -52,6 +52,11 @@ struct WalkLaunch {
   // next-flight launches: cap on the inner iterations of one ball
   int64_t nf_max_inner;
   int drift;                      // the problem has an extra drift (omega fields)
+  // launch schedule (0 = the kernel's own rule): walks claimed per warp at a time, resident
+  // blocks launched per SM, and the register-cap variant of batched launches (1: 8 blocks/SM)
+  uint32_t chunk;
+  int32_t blocks_per_sm;
+  int32_t regs_variant;
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

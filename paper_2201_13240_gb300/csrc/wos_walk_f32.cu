@@ -21,6 +21,7 @@ cudaError_t launch_walks_kernel(const WalkLaunch& L, cudaKernel_t kernel, int re
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
+  if (L.blocks_per_sm > 0 && L.blocks_per_sm < per_sm) per_sm = L.blocks_per_sm;
   int grid = per_sm * num_sms;
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;

@@ -154,8 +154,11 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, u
 #else
 #define WOS_WALK_KERNEL wos_walk_kernel
 #endif
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD, bool DRIFT = false>
-__global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : (MESH ? 5 : WOS_WALK_MIN_BLOCKS)) : 1)
+// MINB > 0 overrides the resident-block target (the batched launches' high-occupancy
+// variant, chosen by the schedule).
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD, bool DRIFT = false, int MINB = 0>
+__global__ void __launch_bounds__(kWalkBlock,
+                                  (sizeof(R) == 4) ? (GRAD ? 4 : (MESH ? 5 : (MINB > 0 ? MINB : WOS_WALK_MIN_BLOCKS))) : 1)
     WOS_WALK_KERNEL(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // stage the problem description (a few KB, read by every lane every step) in shared memory
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : (ME
   const bool accumulate = (L.sum != nullptr);
   uint64_t chunk = total / ((uint64_t)gridDim.x * (kWalkBlock / 32) * kChunksPerWarp);
   chunk = (chunk < kChunkMin) ? kChunkMin : (chunk > kChunkMax ? kChunkMax : chunk & ~31ull);
+  if (L.chunk != 0u) chunk = L.chunk;  // a schedule's choice (a multiple of 32, checked by the host)
   uint64_t chunk_next = 0, chunk_end = 0;
   const uint64_t magic = (L.walks_uniform > 0) ? ~0ull / (uint64_t)L.walks_uniform : 0ull;
   bool exhausted = false;
@@ -496,32 +500,36 @@ __global__ void __launch_bounds__(kWalkBlock, (sizeof(R) == 4) ? (GRAD ? 4 : (ME
 }
 
 #if !defined(__CUDACC_RTC__)
-template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false, bool DRIFT = false>
+template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = false, bool DRIFT = false,
+          int MINB = 0>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
   if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kWalkBlock;
   if (smem > 48 * 1024) {
-    cudaError_t ea = cudaFuncSetAttribute(wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>,
+    cudaError_t ea = cudaFuncSetAttribute(wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return ea;
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT>, kWalkBlock, smem);
+      &per_sm, wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB>, kWalkBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
+  if (L.blocks_per_sm > 0 && L.blocks_per_sm < per_sm) per_sm = L.blocks_per_sm;
   int grid = per_sm * num_sms;
   // total_items is ~0 when per-point walk counts give the total on the device: no cap then
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT><<<grid, kWalkBlock, smem, stream>>>(L);
+  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB><<<grid, kWalkBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_walks_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
-  if (L.probs != nullptr) return launch_walks_m<DIM, R, false, true, false>(L, num_sms, stream);
+  if (L.probs != nullptr)
+    return (L.regs_variant == 1) ? launch_walks_m<DIM, R, false, true, false, false, false, 8>(L, num_sms, stream)
+                                 : launch_walks_m<DIM, R, false, true, false>(L, num_sms, stream);
   if (L.drift) return launch_walks_m<DIM, R, false, false, false, false, true>(L, num_sms, stream);
   if (L.gsum != nullptr || L.ghat != nullptr)  // spatial gradient (no weight window)
     return (DIM == 3 && L.mesh) ? launch_walks_m<DIM, R, true, false, false, true>(L, num_sms, stream)

@@ -98,3 +98,43 @@ def test_per_point_walks_and_graph_replay(wos, orc, setup):
         assert torch.equal(acc[2], ref[2])
         assert torch.allclose(acc[0], ref[0], rtol=1e-9, atol=1e-12)
         assert torch.allclose(acc[1], ref[1], rtol=1e-9, atol=1e-12)
+
+
+def test_schedules_change_the_lanes_not_the_walks(wos, setup):
+    """Any schedule runs the same walks: FP64 sums equal the default schedule's to rounding,
+    counts exactly; invalid schedules are refused."""
+    ctx, probs, pts, offs, walks, sbs, batch = setup
+    dpts = torch.from_numpy(pts).cuda()
+    wt = torch.from_numpy(walks).cuda()
+    batch.set_schedule()
+    ref, _ = ctx.solve_batch(batch, dpts, wt, 1e-3, seed=5, precision="fp64")
+    for sched in ({"chunk": 32}, {"chunk": 64, "blocks_per_sm": 1}, {"chunk": 2048, "regs_variant": 1},
+                  {"chunk": 0, "blocks_per_sm": 3, "regs_variant": 1}):
+        batch.set_schedule(**sched)
+        assert {k: v for k, v in batch.schedule().items() if k in sched} == sched
+        acc, st = ctx.solve_batch(batch, dpts, wt, 1e-3, seed=5, precision="fp64")
+        assert torch.equal(acc[2], ref[2])
+        assert torch.allclose(acc[0], ref[0], rtol=1e-12, atol=1e-12), sched
+        acc32, _ = ctx.solve_batch(batch, dpts, wt, 1e-3, seed=5)
+        assert torch.equal(acc32[2], ref[2])
+    for bad in ({"chunk": 33}, {"chunk": 16}, {"blocks_per_sm": -1}, {"regs_variant": 2}, {"blocks_per_sm": 33}):
+        with pytest.raises(wos.WosError):
+            batch.set_schedule(**bad)
+    batch.set_schedule()
+    assert batch.schedule() == {"chunk": 0, "blocks_per_sm": 0, "regs_variant": 0}
+
+
+def test_autotune_keeps_a_candidate_and_the_results(wos, setup):
+    ctx, probs, pts, offs, walks, sbs, batch = setup
+    dpts = torch.from_numpy(pts).cuda()
+    wt = torch.from_numpy(walks).cuda()
+    sched, best_ms, default_ms = ctx.batch_autotune(batch, dpts, wt, 1e-3, seed=1, trial_shift=2)
+    assert sched["chunk"] in (0, 64, 128, 256, 512, 1024, 2048) and sched["regs_variant"] in (0, 1)
+    assert 0 < best_ms <= default_ms
+    assert batch.schedule() == sched
+    acc, st = ctx.solve_batch(batch, dpts, wt, 1e-3, seed=9)
+    assert torch.equal(acc[2].cpu(), torch.from_numpy(walks.astype(np.int64)))
+    assert wos.stats_dict(st)["walks"] == int(walks.sum())
+    with pytest.raises(wos.WosError):
+        ctx.batch_autotune(batch, dpts, wt, 1e-3, trial_shift=17)
+    batch.set_schedule()
