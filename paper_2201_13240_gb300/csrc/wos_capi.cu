@@ -651,10 +651,13 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
       pr->mesh_lo[k] = nodes[0].lo[k];
       pr->mesh_hi[k] = nodes[0].hi[k];
     }
-    e = cudaMalloc(&pr->mesh_nodes, nodes.size() * sizeof(wos::MeshNode));
+    std::vector<wos::MeshNode4> wide;  // the device traverses 4-wide nodes
+    int wide_depth = 0;
+    wos::mesh_collapse4(nodes, &wide, &wide_depth);
+    e = cudaMalloc(&pr->mesh_nodes, wide.size() * sizeof(wos::MeshNode4));
     if (e == cudaSuccess) e = cudaMalloc(&pr->mesh_tris, tri.size() * sizeof(float));
     if (e == cudaSuccess)
-      e = cudaMemcpy(pr->mesh_nodes, nodes.data(), nodes.size() * sizeof(wos::MeshNode), cudaMemcpyHostToDevice);
+      e = cudaMemcpy(pr->mesh_nodes, wide.data(), wide.size() * sizeof(wos::MeshNode4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pr->mesh_tris, tri.data(), tri.size() * sizeof(float), cudaMemcpyHostToDevice);
     h32->mesh_nodes = pr->mesh_nodes;
     h32->mesh_tris = pr->mesh_tris;

@@ -9,7 +9,8 @@
 //           whose children are nodes `left` and `left + 1`; a leaf holds
 //           triangles first = left .. left + count - 1 of the reordered list.
 //   tris:   3 x float4 per triangle in leaf order: (v0, v1, v2), w unused.
-// Node 0 is the root.  The build is deterministic.
+// Node 0 is the root.  The build is deterministic.  mesh_collapse4 turns the binary
+// tree into the 4-wide nodes the device traverses.
 #include "wos_mesh.h"
 
 #include <algorithm>
@@ -130,7 +131,61 @@ struct Builder {
   }
 };
 
+int collapse(const std::vector<MeshNode>& bin, int64_t n, std::vector<MeshNode4>* wide, int level, int* depth) {
+  const int idx = (int)wide->size();
+  wide->emplace_back();
+  *depth = std::max(*depth, level);
+  int64_t slot[4];
+  int ns = 0;
+  if (bin[n].count > 0) {
+    slot[ns++] = n;  // a root that is a leaf
+  } else {
+    for (int64_t c = bin[n].left; c < bin[n].left + 2; ++c) {
+      if (bin[c].count == 0) {
+        slot[ns++] = bin[c].left;
+        slot[ns++] = bin[c].left + 1;
+      } else {
+        slot[ns++] = c;
+      }
+    }
+  }
+  int32_t child[4], count[4];
+  for (int i = 0; i < 4; ++i) {
+    if (i >= ns) {
+      child[i] = 0;
+      count[i] = -1;
+    } else if (bin[slot[i]].count > 0) {
+      child[i] = bin[slot[i]].left;
+      count[i] = bin[slot[i]].count;
+    } else {
+      child[i] = collapse(bin, slot[i], wide, level + 1, depth);
+      count[i] = 0;
+    }
+  }
+  MeshNode4& w = (*wide)[idx];  // after the recursion: the vector may have moved
+  for (int i = 0; i < 4; ++i) {
+    const bool on = i < ns;
+    w.lox[i] = on ? bin[slot[i]].lo[0] : INFINITY;
+    w.loy[i] = on ? bin[slot[i]].lo[1] : INFINITY;
+    w.loz[i] = on ? bin[slot[i]].lo[2] : INFINITY;
+    w.hix[i] = on ? bin[slot[i]].hi[0] : -INFINITY;
+    w.hiy[i] = on ? bin[slot[i]].hi[1] : -INFINITY;
+    w.hiz[i] = on ? bin[slot[i]].hi[2] : -INFINITY;
+    w.child[i] = child[i];
+    w.count[i] = count[i];
+  }
+  return idx;
+}
+
 }  // namespace
+
+void mesh_collapse4(const std::vector<MeshNode>& bin, std::vector<MeshNode4>* wide, int* depth) {
+  wide->clear();
+  wide->reserve(bin.size() / 2 + 1);
+  int d = 0;
+  collapse(bin, 0, wide, 1, &d);
+  if (depth) *depth = d;
+}
 
 int mesh_build_bvh(const float* verts, int64_t nverts, const int32_t* tris, int64_t ntris,
                    std::vector<MeshNode>* nodes, std::vector<float>* tri_data, int* depth_out) {

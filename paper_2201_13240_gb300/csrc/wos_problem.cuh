@@ -400,7 +400,7 @@ WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
 // visits the nearer child first and skips every box farther than the best
 // triangle so far.
 // ---------------------------------------------------------------------------
-constexpr int kMeshStack = 32;  // the builder caps the tree depth at 29 (one push per level)
+constexpr int kMeshStack = 32;  // entries of the traversal stack (a full stack repeats the pass: mesh_query)
 
 struct F4 {
   float x, y, z, w;
@@ -451,13 +451,13 @@ WOS_HD void tri_closest(const R* p, const float* t, R* v_out, R* w_out, R* d2_ou
   if (d1 <= R(0) && d2 <= R(0)) { v = R(0); w = R(0); }                       // vertex a
   else if (d3 >= R(0) && d4 <= d3) { v = R(1); w = R(0); }                    // vertex b
   else if (d6 >= R(0) && d5 <= d6) { v = R(0); w = R(1); }                    // vertex c
-  else if (vc <= R(0) && d1 >= R(0) && d3 <= R(0)) { v = d1 / (d1 - d3); w = R(0); }   // edge ab
-  else if (vb <= R(0) && d2 >= R(0) && d6 <= R(0)) { v = R(0); w = d2 / (d2 - d6); }   // edge ac
+  else if (vc <= R(0) && d1 >= R(0) && d3 <= R(0)) { v = w_div(d1, d1 - d3); w = R(0); }   // edge ab
+  else if (vb <= R(0) && d2 >= R(0) && d6 <= R(0)) { v = R(0); w = w_div(d2, d2 - d6); }   // edge ac
   else if (va <= R(0) && (d4 - d3) >= R(0) && (d5 - d6) >= R(0)) {                    // edge bc
-    w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    w = w_div(d4 - d3, (d4 - d3) + (d5 - d6));
     v = R(1) - w;
   } else {                                                                              // interior
-    R den = R(1) / (va + vb + vc);
+    R den = w_div(R(1), va + vb + vc);
     v = vb * den;
     w = vc * den;
   }
@@ -477,10 +477,38 @@ struct MeshHit {
 // boxes nearer than a known boundary point are opened; if rounding still hides
 // every triangle, the search restarts without the bound.  The result does not
 // depend on the bound.
+// The tree has 4-wide nodes of one 128-byte line (MeshNode4 in wos_mesh.h: child boxes
+// as structure of arrays): a visit loads one line and tests four boxes, so a query
+// follows half as many dependent loads as in the binary tree.  Leaf children nearer
+// than the best triangle are tested at once; the nearest interior child is visited
+// next and the others are pushed, farther first.  A full stack drops the entry and
+// marks the pass; a marked pass is repeated from the root with the best distance found
+// (still exact: every dropped node is seen again).
 // SMEM: the stack lives in shared memory, entry k of this thread at sn[k * stride] and
 // sd[k * stride] (a column per thread: no bank conflicts); otherwise in local memory.
 // Kept in local memory by the walk kernels, the stack's divergent per-lane accesses
 // were the largest memory traffic of a mesh walk.
+struct I4 {
+  int x, y, z, w;
+};
+WOS_HD I4 ld4i(const float* p) {
+#if defined(__CUDA_ARCH__)
+  int4 v = __ldg(reinterpret_cast<const int4*>(p));
+  return I4{v.x, v.y, v.z, v.w};
+#else
+  I4 v;
+  memcpy(&v, p, 16);
+  return v;
+#endif
+}
+template <typename R>
+WOS_HD R box_d2_1(const R* x, float lx, float ly, float lz, float hx, float hy, float hz) {
+  R dx = w_fmax(w_fmax(R(lx) - x[0], x[0] - R(hx)), R(0));
+  R dy = w_fmax(w_fmax(R(ly) - x[1], x[1] - R(hy)), R(0));
+  R dz = w_fmax(w_fmax(R(lz) - x[2], x[2] - R(hz)), R(0));
+  return dx * dx + dy * dy + dz * dz;
+}
+
 template <typename R, bool SMEM>
 WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2, int* sn, R* sd,
                                    int stride) {
@@ -492,49 +520,79 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
   int* stk_n = SMEM ? sn : loc_n;
   R* stk_d = SMEM ? sd : loc_d;
   const int sst = SMEM ? stride : 1;
-  R best, bv = R(0), bw = R(0);
+  R best = R(INFINITY), bv = R(0), bw = R(0);
   int best_t = -1;
   const R slack = (sizeof(R) == 4) ? R(1e-5) : R(1e-12);
-  R start = (bound2 < R(INFINITY)) ? bound2 * (R(1) + slack) + R(1e-30) : R(INFINITY);
-  for (int attempt = 0; attempt < 2 && best_t < 0; ++attempt) {
-  best = (attempt == 0) ? start : R(INFINITY);
-  int sp = 0;
-  int node = 0;
-  for (;;) {
-    F4 lo = ld4(nodes + 8 * node), hi = ld4(nodes + 8 * node + 4);
-    int left = f_as_i(lo.w), count = f_as_i(hi.w);
-    bool descend = false;
-    if (count > 0) {
-      for (int i = 0; i < count; ++i) {
-        R v, w, d2;
-        tri_closest(x, tris + 12 * (left + i), &v, &w, &d2);
-        if (d2 < best) { best = d2; best_t = left + i; bv = v; bw = w; }
-      }
-    } else {
-      F4 l0 = ld4(nodes + 8 * left), l1 = ld4(nodes + 8 * left + 4);
-      F4 r0 = ld4(nodes + 8 * (left + 1)), r1 = ld4(nodes + 8 * (left + 1) + 4);
-      R dl = box_d2(x, l0, l1), dr = box_d2(x, r0, r1);
-      int nn = (dl <= dr) ? left : left + 1;
-      R dn = (dl <= dr) ? dl : dr, df = (dl <= dr) ? dr : dl;
-      if (dn < best) {
-        if (df < best && sp < kMeshStack) {
-          stk_n[sp * sst] = (nn == left) ? left + 1 : left;
-          stk_d[sp * sst] = df;
-          ++sp;
+  const R start = (bound2 < R(INFINITY)) ? bound2 * (R(1) + slack) + R(1e-30) : R(INFINITY);
+  bool again = true;
+  for (int pass = 0; pass < 8 && again; ++pass) {
+    // pass 0 starts from the bound; a pass that found nothing within it, or dropped
+    // stack entries, is followed by one from the root with the best so far
+    if (pass == 0) best = start;
+    else if (best_t < 0) best = R(INFINITY);
+    again = false;
+    int sp = 0;
+    int node = 0;
+    for (;;) {
+      const float* nd = nodes + 32 * node;
+      const F4 lx = ld4(nd), ly = ld4(nd + 4), lz = ld4(nd + 8), hx = ld4(nd + 12), hy = ld4(nd + 16),
+               hz = ld4(nd + 20);
+      const I4 ch = ld4i(nd + 24), cn = ld4i(nd + 28);
+      R d[4] = {box_d2_1(x, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x), box_d2_1(x, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y),
+                box_d2_1(x, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z), box_d2_1(x, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w)};
+      const int cc[4] = {ch.x, ch.y, ch.z, ch.w}, nc[4] = {cn.x, cn.y, cn.z, cn.w};
+      // leaf children nearer than the best triangle: test them now (lowers best)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (nc[i] > 0 && d[i] < best) {
+          for (int j = 0; j < nc[i]; ++j) {
+            R v, w, d2;
+            tri_closest(x, tris + 12 * (cc[i] + j), &v, &w, &d2);
+            if (d2 < best) { best = d2; best_t = cc[i] + j; bv = v; bw = w; }
+          }
         }
-        node = nn;
-        descend = true;
       }
-    }
-    if (descend) continue;
-    // pop the next node still closer than the best triangle
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (stk_d[sp * sst] < best) { node = stk_n[sp * sst]; found = true; break; }
-    }
-    if (!found) break;
+      // interior children nearer than the best: sort by distance (others at infinity)
+      R k[4];
+      int c[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        k[i] = (nc[i] == 0 && d[i] < best) ? d[i] : R(INFINITY);
+        c[i] = cc[i];
+      }
+#define WOS_CSWAP(a, b)                                   \
+  if (k[b] < k[a]) {                                      \
+    R tk = k[a]; k[a] = k[b]; k[b] = tk;                  \
+    int tc = c[a]; c[a] = c[b]; c[b] = tc;                \
   }
+      WOS_CSWAP(0, 1) WOS_CSWAP(2, 3) WOS_CSWAP(0, 2) WOS_CSWAP(1, 3) WOS_CSWAP(1, 2)
+#undef WOS_CSWAP
+      // push the farther ones (farthest first, so the nearer are popped first)
+#pragma unroll
+      for (int i = 3; i >= 1; --i) {
+        if (k[i] < best) {
+          if (sp < kMeshStack) {
+            stk_n[sp * sst] = c[i];
+            stk_d[sp * sst] = k[i];
+            ++sp;
+          } else {
+            again = true;
+          }
+        }
+      }
+      if (k[0] < best) {
+        node = c[0];
+        continue;
+      }
+      // pop the next node still nearer than the best triangle
+      bool found = false;
+      while (sp > 0) {
+        --sp;
+        if (stk_d[sp * sst] < best) { node = stk_n[sp * sst]; found = true; break; }
+      }
+      if (!found) break;
+    }
+    if (best_t < 0) again = true;
   }
   if (best_t < 0) best_t = 0;
   const float* t = tris + 12 * best_t;
