@@ -47,7 +47,7 @@ extern "C" {
 #define WOS_ENOMEM (-2)       /* device or host allocation failed */
 #define WOS_ECUDA (-3)        /* a CUDA runtime call failed (message has details) */
 #define WOS_ETIMEOUT (-4)     /* reserved: a bounded device wait gave up */
-#define WOS_EUNSUPPORTED (-5) /* valid request this build does not handle */
+#define WOS_EUNSUPPORTED (-5) /* valid request the library does not handle */
 
 /* ---- statistics words (device uint64 array of WOS_STATS_WORDS, added to) ---- */
 #define WOS_STAT_STEPS 0     /* walk steps: distance query + Green's sample */
