@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   const double inv_walks = 1.0 / (double)L.walks_uniform;
 
   uint64_t chunk_next = 0, chunk_end = 0;
+  const uint64_t magic = (L.walks_uniform > 0) ? ~0ull / (uint64_t)L.walks_uniform : 0ull;
   bool exhausted = false, active = false;
   // walk state; phase 0 computes the total A, phase 1 replays and scatters
   R x[3] = {R(0), R(0), R(0)}, W = R(1), acc = R(0), total = R(0);
@@ -213,17 +214,24 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
       unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
       unsigned rank = __popc(need & lt_mask);
       if (!active && rank < take) {
-        uint64_t item = chunk_next + rank;
-        uint64_t pp = item / (uint64_t)L.walks_uniform;
+        // item / walks_uniform by a multiply-high and one correction (as in the walk kernel)
+        const uint64_t item = chunk_next + rank, dw = (uint64_t)L.walks_uniform;
+        uint64_t pp = __umul64hi(item, magic), jj = item - pp * dw;
+        if (jj >= dw) {
+          ++pp;
+          jj -= dw;
+        }
         p = (uint32_t)pp;
-        w = (uint32_t)(L.walk_offset + (item - pp * (uint64_t)L.walks_uniform));
+        w = (uint32_t)(L.walk_offset + jj);
 #pragma unroll
         for (int d = 0; d < 3; ++d) x[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)p])) : R(0);
         W = R(1);
         acc = R(0);
         k = 0;
         phase = 0;
-        coef = R(__ldg(&L.grad_u[p]) * inv_walks * exp(-(double)gamma_at<DIM>(P, x)));
+        // e^{-gamma(x_0)} in the walk's precision (an FP64 exp per walk start, run by the one
+        // or two lanes that start, occupied the narrow FP64 pipe)
+        coef = R(__ldg(&L.grad_u[p]) * inv_walks) * w_exp(-gamma_at<DIM>(P, x));
         active = true;
       }
       chunk_next += take;
