@@ -250,7 +250,8 @@ std::string jit_source(const DevProblem<double>& P) {
   s += "// walk kernel specialised to one problem (" + std::to_string(dim) + "D): generated field code\n";
   s += "#define WOS_JIT_FIELDS 1\n";
   s += "#define WOS_JIT_F_KIND " + std::to_string(P.f.kind) + "\n";
-  if (dim == 3) s += "#define WOS_WALK_MIN_BLOCKS 7\n";  // 3D: 72 registers without spills
+  // resident blocks per SM: 3D 7 (72 registers), 2D 8 (64 registers), neither spills
+  s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 7\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
   s += "#include \"wos_walk_impl.cuh\"\n\nnamespace wos {\n\n";
   s += "template <int DIM, typename R>\n";
   s += "__device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id, R x0, R x1, R x2, "

@@ -710,40 +710,34 @@ template <>
 struct Radial2<float> {
   float a;
   int small;
-  float A[8], B[8], Cc[8], Dd[8];
-  float invN1;
-  float c_scaled;  // K0(a)/I0(a) times e^{2a}: k0s(a)/i0s(a)
+  float q, beta, invN1;  // a < 2: the series' parameters (coefficients are formed as summed)
+  float c_scaled;        // K0(a)/I0(a) times e^{2a}: k0s(a)/i0s(a)
   float e2a;
 
+  // For a < 2 no coefficient arrays are kept (they cost registers and a stack frame in the
+  // walk kernels): init sums N(1) and beta in one pass, eval the four series at rho in
+  // another, with the beta terms factored out as in radial2_once below.
   WOS_HD void init(float a_) {
     a = a_;
     small = (a < 2.0f);
     if (small) {
-      float q = 0.25f * a * a, b = 1.0f, H = 0.0f, I0 = 0.0f, S = 0.0f;
-      float bk[8], Hk[8];
+      q = 0.25f * a * a;
+      float b = 1.0f, H = 0.0f, I0 = 0.0f, S = 0.0f, n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (k > 0) {
           b *= q * (1.0f / (float)(k * k));
           H += 1.0f / (float)k;
         }
-        bk[k] = b;
-        Hk[k] = H;
+        const float im = 1.0f / (2.0f * k + 2.0f);
         I0 += b;
         S += H * b;
+        n1 += b * im * im;
+        n2 += b * H * im;
+        n3 += b * im;
       }
-      float beta = w_div(S, I0);
-      float N1 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float im = 1.0f / (2.0f * k + 2.0f);  // a constant of the unrolled loop
-        A[k] = bk[k] * im;
-        B[k] = bk[k] * (im * im + (Hk[k] - beta) * im);
-        Dd[k] = bk[k];
-        Cc[k] = bk[k] * (Hk[k] - beta);
-        N1 += B[k];
-      }
-      invN1 = w_div(1.0f, N1);  // N(1)/a^2 = B(1)
+      beta = w_div(S, I0);
+      invN1 = w_div(1.0f, n1 + n2 - beta * n3);  // N(1)/a^2 = B(1)
     } else {
       float ea = w_exp(-a);
       e2a = ea * ea;
@@ -756,15 +750,23 @@ struct Radial2<float> {
   WOS_HD void eval(float rho, float* F, float* pdf) const {
     if (small) {
       if (rho <= 0.0f) { *F = 0.0f; *pdf = 0.0f; return; }
-      float r2 = rho * rho, lr = w_log(rho);
-      float pa = A[7], pb = B[7], pc = Cc[7], pd = Dd[7];
+      const float r2 = rho * rho, lr = w_log(rho);
+      float b = 1.0f, H = 0.0f, rk = 1.0f, pa = 0.0f, pb1 = 0.0f, pb2 = 0.0f, pc1 = 0.0f, pd = 0.0f;
 #pragma unroll
-      for (int k = 6; k >= 0; --k) {
-        pa = pa * r2 + A[k];
-        pb = pb * r2 + B[k];
-        pc = pc * r2 + Cc[k];
-        pd = pd * r2 + Dd[k];
+      for (int k = 0; k < 8; ++k) {
+        if (k > 0) {
+          b *= q * (1.0f / (float)(k * k));
+          H += 1.0f / (float)k;
+          rk *= r2;
+        }
+        const float im = 1.0f / (2.0f * k + 2.0f), brk = b * rk;
+        pa += brk * im;
+        pb1 += brk * im * im;
+        pb2 += brk * H * im;
+        pc1 += brk * H;
+        pd += brk;
       }
+      const float pb = pb1 + pb2 - beta * pa, pc = pc1 - beta * pd;
       *F = r2 * (pb - lr * pa) * invN1;
       *pdf = rho * (pc - lr * pd) * invN1;
       return;
