@@ -47,6 +47,11 @@ SIGMA_LATTICE = 64
 # update 12  ->  373 ALU + 27 MUFU = 589.
 OPS_PER_STEP = 589
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one launch of the specialised walk kernel on this workload,
+# from the ncu capture summarised in profiles/wos_walk_spec_kernel_cube3d.md (9.53 MB read,
+# 0 written: the points and the radial table; walk state stays in registers).  Reported only
+# for the configuration that capture measured; re-take it whenever the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 9.528320e6
 
 
 def workload_config(extra=None):
@@ -325,8 +330,10 @@ def run_ours(args):
     finalize_ms = fe0.elapsed_time(fe1) / 5
     kernel_ms = ms_per_step - finalize_ms
     achieved = OPS_PER_STEP * (st["steps"] / args.steps) / (kernel_ms * 1e-3)
+    captured = args.kernel == "specialised" and GRID == 64 and WALKS == 1024
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": None,
+                "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if captured else None,
+                "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "kernel": kernel_label(args), "ops_per_step": OPS_PER_STEP,
                 "peak_basis": f"128 FP32/INT32 lanes x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                               "(sm_max_mhz of MEASURED_PEAKS.json)"}
