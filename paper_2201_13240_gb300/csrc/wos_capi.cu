@@ -1377,6 +1377,10 @@ extern "C" int wos_batch_autotune(wos_ctx* ctx, wos_batch* b, const float* pts, 
     return fail(ctx, WOS_ECUDA, "autotune events");
   }
   trial_walks_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(walks, n, walks_uniform, trial_shift, tw);
+  if (cudaError_t el = cudaGetLastError(); el != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ctx, el, "autotune trial walks");
+  }
   // candidates: the kernel's own chunk rule and fixed chunks, at both register caps
   std::vector<wos_schedule> cand;
   const int32_t chunks[] = {0, 64, 128, 256, 512, 1024, 2048};
@@ -1388,8 +1392,12 @@ extern "C" int wos_batch_autotune(wos_ctx* ctx, wos_batch* b, const float* pts, 
   for (size_t i = 0; i <= cand.size() && rc == WOS_OK; ++i) {
     // i == 0 warms up with the first candidate (untimed)
     const wos_schedule& sc = cand[i == 0 ? 0 : i - 1];
-    cudaMemsetAsync(acc, 0, 2 * sizeof(double) * n, st);
-    cudaMemsetAsync(cnt, 0, sizeof(int64_t) * n, st);
+    cudaError_t em = cudaMemsetAsync(acc, 0, 2 * sizeof(double) * n, st);
+    if (em == cudaSuccess) em = cudaMemsetAsync(cnt, 0, sizeof(int64_t) * n, st);
+    if (em != cudaSuccess) {
+      rc = cuda_fail(ctx, em, "autotune accumulators");
+      break;
+    }
     cudaEventRecord(e0, st);
     rc = solve_batch_impl(ctx, b, sc, pts, tw, 0, prm, acc, acc + n, cnt, reinterpret_cast<uint64_t*>(stt), stream);
     cudaEventRecord(e1, st);

@@ -291,7 +291,12 @@ int jit_compile(const DevProblem<double>& P, bool fp64, int variant_mask, std::v
   for (int v = 0; v < kJitVariants; ++v) {
     if (!(variant_mask & (1 << v))) continue;
     exprs[v] = kernel_expr(P.dim, fp64, mesh, drift, v);
-    api.AddNameExpression(prog, exprs[v].c_str());
+    r = api.AddNameExpression(prog, exprs[v].c_str());
+    if (r != NVRTC_SUCCESS) {
+      *log = std::string("nvrtcAddNameExpression: ") + api.GetErrorString(r);
+      api.DestroyProgram(&prog);
+      return WOS_EUNSUPPORTED;
+    }
   }
   const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
   r = api.CompileProgram(prog, 3, opts);
@@ -346,18 +351,20 @@ int jit_specialise(JitState* js, const DevProblem<double>& P, bool fp64, int var
     cudaGetLastError();
     return WOS_ECUDA;
   }
+  // every requested kernel is found before any is published: a failure leaves the state as it was
+  cudaKernel_t found[kJitVariants] = {nullptr, nullptr, nullptr};
   for (int v = 0; v < kJitVariants; ++v) {
     if (!(need & (1 << v))) continue;
-    cudaKernel_t k = nullptr;
-    e = lowered[v].empty() ? cudaErrorSymbolNotFound : cudaLibraryGetKernel(&k, lib, lowered[v].c_str());
+    e = lowered[v].empty() ? cudaErrorSymbolNotFound : cudaLibraryGetKernel(&found[v], lib, lowered[v].c_str());
     if (e != cudaSuccess) {
       *why = std::string("cudaLibraryGetKernel(") + kVariantName[v] + "): " + cudaGetErrorString(e);
       cudaGetLastError();
       cudaLibraryUnload(lib);
       return WOS_ECUDA;
     }
-    js->kernel[p][v] = k;
   }
+  for (int v = 0; v < kJitVariants; ++v)
+    if (need & (1 << v)) js->kernel[p][v] = found[v];
   js->libs.push_back(lib);
   return WOS_OK;
 }
