@@ -173,3 +173,81 @@ def test_bspline_derivatives_match_differences(orc):
             assert g[d] == pytest.approx((vp - vm) / (2 * h), rel=1e-5, abs=1e-6)
             lap_fd += (vp - 2 * v + vm) / (h * h)
         assert l_ == pytest.approx(lap_fd, rel=1e-3, abs=1e-3)
+
+
+def _cardinal_bspline_field(data, lo, hi, x):
+    """Value, gradient and Laplacian of sum_j c_j N(s - j + 2) per axis, N the cubic
+    basis element on the knots 0..4 from scipy's Cox-de Boor recursion, s the point in
+    node units, control indices clamped to the grid (array index [z, y, x])."""
+    from scipy.interpolate import BSpline
+    N = BSpline.basis_element(np.arange(5.0), extrapolate=False)
+    dN, d2N = N.derivative(1), N.derivative(2)
+    res = data.shape[::-1]
+    h = [(hi[d] - lo[d]) / (res[d] - 1) for d in range(3)]
+    s = [(x[d] - lo[d]) / h[d] for d in range(3)]
+    base = [int(np.floor(s[d])) - 1 for d in range(3)]
+    w = [[], [], []]
+    for d in range(3):
+        for a in range(4):
+            t = s[d] - (base[d] + a) + 2.0
+            w[d].append((float(N(t)), float(dN(t)) / h[d], float(d2N(t)) / h[d] ** 2))
+    v, g, lap = 0.0, np.zeros(3), 0.0
+    for c in range(4):
+        for b in range(4):
+            for a in range(4):
+                i = [min(max(base[0] + a, 0), res[0] - 1), min(max(base[1] + b, 0), res[1] - 1),
+                     min(max(base[2] + c, 0), res[2] - 1)]
+                cv = float(data[i[2], i[1], i[0]])
+                wx, wy, wz = w[0][a], w[1][b], w[2][c]
+                v += cv * wx[0] * wy[0] * wz[0]
+                g += cv * np.array([wx[1] * wy[0] * wz[0], wx[0] * wy[1] * wz[0], wx[0] * wy[0] * wz[1]])
+                lap += cv * (wx[2] * wy[0] * wz[0] + wx[0] * wy[2] * wz[0] + wx[0] * wy[0] * wz[2])
+    return v, g, lap
+
+
+def test_bspline_grid_is_the_cardinal_cubic_bspline(orc):
+    """The B-spline grid field (reading R6: node values as control points of a uniform
+    cubic B-spline, C^2) equals the textbook cardinal cubic B-spline built from scipy's
+    Cox-de Boor basis element: value, gradient and Laplacian, inside the grid and near
+    its faces (clamped control indices).  An interpolating cubic (Catmull-Rom) or a
+    wrong basis that still sums to one fails this."""
+    rng = np.random.default_rng(11)
+    res = (7, 6, 5)
+    lo, hi = (-0.5, 0.0, 1.0), (1.0, 2.0, 2.0)
+    data = rng.uniform(0.5, 2.0, size=res[::-1]).astype(np.float32)
+    fd = {"kind": "grid_bspline", "res": res, "lo": lo, "hi": hi, "data": data}
+    prob = W.problem(3, W.box(lo, hi), fd, W.zero(), W.zero(), W.zero())
+    for _ in range(40):
+        x = np.array([rng.uniform(lo[d], hi[d]) for d in range(3)])
+        v, g, l_ = orc.field_eval(prob, "alpha", x)
+        rv, rg, rl = _cardinal_bspline_field(data, lo, hi, x)
+        assert v == pytest.approx(rv, rel=1e-12, abs=1e-12)
+        assert np.asarray(g) == pytest.approx(rg, rel=1e-10, abs=1e-10)
+        assert l_ == pytest.approx(rl, rel=1e-9, abs=1e-9)
+
+
+def test_bspline_grid_node_identity_and_c2_faces(orc):
+    """At an interior node the cubic B-spline takes (c_{i-1} + 4 c_i + c_{i+1}) / 6 along
+    each axis (a tensor product of that stencil), not the node value; across a cell face
+    the value, gradient and Laplacian are continuous (C^2, which sigma' needs)."""
+    rng = np.random.default_rng(12)
+    res = (6, 6, 6)
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    data = rng.uniform(0.5, 2.0, size=res).astype(np.float64)
+    fd = {"kind": "grid_bspline", "res": res, "lo": lo, "hi": hi, "data": data.astype(np.float32)}
+    prob = W.problem(3, W.box(lo, hi), fd, W.zero(), W.zero(), W.zero())
+    c = data.astype(np.float32).astype(np.float64)
+    st = np.array([1.0, 4.0, 1.0]) / 6.0
+    for (i, j, k) in [(1, 1, 1), (2, 3, 4), (4, 2, 3)]:
+        x = np.array([i, j, k], dtype=np.float64) / 5.0
+        want = np.einsum("a,b,c,cba->", st, st, st, c[k - 1:k + 2, j - 1:j + 2, i - 1:i + 2])
+        assert orc.field_eval(prob, "alpha", x)[0] == pytest.approx(want, rel=1e-12)
+    # continuity across the face x = 0.4 (a node plane) at random (y, z)
+    delta = 1e-7
+    for _ in range(10):
+        y, z = rng.uniform(0.05, 0.95, size=2)
+        a = orc.field_eval(prob, "alpha", np.array([0.4 - delta, y, z]))
+        b = orc.field_eval(prob, "alpha", np.array([0.4 + delta, y, z]))
+        assert a[0] == pytest.approx(b[0], abs=1e-5)
+        assert np.asarray(a[1]) == pytest.approx(np.asarray(b[1]), abs=1e-4)
+        assert a[2] == pytest.approx(b[2], abs=2e-3)
