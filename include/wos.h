@@ -488,29 +488,35 @@ int wos_render_slice(wos_ctx* ctx, const wos_problem* prob, const wos_view* view
 /* ---- allocation-free solve ----
    The paper has no counterpart: this entry point exists for callers that cannot
    allocate device memory -- code running inside an allocator hook or a memory-pool
-   callback, plugins whose host program owns every allocation and forbids
-   cudaMalloc/cudaFree, and programs that must not synchronise the device (cudaFree
-   does).  It needs no context and no wos_problem: the problem description is passed
-   directly, and the walk kernel's scratch (work counter, default statistics, the
-   uploaded description and the per-point walk prefix sums) lives in one static
-   device array of WOS_NOALLOC_SCRATCH_BYTES that the library's module image carries,
-   so every GPU that loads this library holds it until the process exits.  The call
-   performs no cudaMalloc, cudaFree or other allocating routine.
+   callback (allocating there would re-enter the allocator), plugins whose host program
+   owns every allocation and forbids cudaMalloc/cudaFree, and programs that must not
+   synchronise the device (cudaFree does).  It needs no context and no wos_problem: the
+   problem description is passed directly, and the walk kernel's scratch (work counter,
+   default statistics, the problem description and the per-point walk prefix sums)
+   lives in one static device array of WOS_NOALLOC_SCRATCH_BYTES that the library's
+   module image carries, so every GPU that loads this library holds it until the process
+   exits.  The call performs no cudaMalloc, cudaFree or other allocating routine, and
+   it does not block the host: the description reaches the device as a kernel argument.
 
    Same arguments and results as wos_solve, on the CURRENT CUDA device, except:
      - desc: host problem description (validated on every call; grid data are device
-       pointers owned by the caller);
+       pointers owned by the caller).  Only analytic domains (box, ball, annulus,
+       rounded box) without an extra drift: mesh domains need a BVH built and stored at
+       problem creation, CSG lists do not fit the static description, and both return
+       WOS_EINVAL here, as does a non-ZERO omega;
      - walks (per-point counts) is limited to npts <= WOS_NOALLOC_MAX_VAR_POINTS, the
        capacity of the static prefix-sum buffer; larger npts with walks != NULL returns
        WOS_EINVAL (uniform walk counts have no point limit);
+     - no weight window (WOS_EUNSUPPORTED when ww_lo != 0);
      - errors are reported by the return code only (WOS_EINVAL, WOS_ECUDA);
      - FP32 walks start Newton from the closed-form guess instead of the context's
        inverse-CDF table: same distribution, somewhat slower.
-   The first call on a device resolves the address of the static array
-   (cudaGetSymbolAddress) for that device; make that first call outside any CUDA
-   stream capture.  Every call on a device shares the one array and the call resets
-   what must start at zero; calls whose work overlaps on the GPU (other streams, other
-   host threads) race on it and must be serialised by the caller. */
+   Every call asks the runtime for the static array's address on the current device
+   (cudaGetSymbolAddress); the first call on a device also loads the library's module
+   there, so make that first call before any CUDA stream capture.  Every call on a
+   device shares the one array and resets what must start at zero; the array keeps the
+   last call's contents otherwise.  Calls whose work overlaps on the GPU (other streams,
+   other host threads) race on it and must be serialised by the caller. */
 #define WOS_NOALLOC_MAX_VAR_POINTS 65536
 #define WOS_NOALLOC_SCRATCH_BYTES (16640 + 8 * WOS_NOALLOC_MAX_VAR_POINTS)
 int wos_solve_noalloc(const wos_problem_desc* desc, const float* pts, int64_t npts, const int32_t* walks,

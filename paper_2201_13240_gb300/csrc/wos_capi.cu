@@ -18,58 +18,7 @@
 #include "wos_jit.h"
 #include "wos_problem.cuh"
 
-using wos::DevField;
-using wos::DevProblem;
-using wos::DevTerm;
-
-struct wos_ctx {
-  int device = 0;
-  int num_sms = 0;
-  std::string err;
-  // scratch: [0] work counter, [8..8+ST_WORDS) default stats, [16..20) sigma-bar reduction
-  unsigned long long* scratch = nullptr;
-  // walks-per-point prefix sums
-  int64_t* walk_end = nullptr;
-  int64_t walk_end_cap = 0;
-  // FP32 inverse radial CDF start tables for 2D and 3D (wos::kTabSize floats each)
-  float* radial_tab[2] = {nullptr, nullptr};
-  // buffers of wos_solve_host
-  float* h_pts = nullptr;
-  double* h_acc = nullptr;  // sum, sumsq, mean, var, se: 5 * cap doubles
-  int64_t* h_count = nullptr;
-  int64_t host_cap = 0;
-};
-
-struct wos_batch {
-  wos_ctx* ctx = nullptr;
-  int device = 0;                     // kept here: destroy must not read a destroyed context
-  int dim = 0;
-  int32_t nprob = 0;
-  int64_t npts = 0;
-  DevProblem<float>* d32 = nullptr;   // [nprob]
-  DevProblem<double>* d64 = nullptr;  // [nprob]
-  int64_t* offsets = nullptr;         // [nprob + 1]
-  double* sigma_bars = nullptr;       // [nprob]
-  int64_t* walk_end = nullptr;        // [npts] prefix sums for per-point walk counts
-  wos_schedule sched = {0, 0, 0, 0};  // launch schedule (wos_batch_set_schedule / autotune)
-};
-
-struct wos_problem {
-  wos_ctx* ctx = nullptr;
-  int device = 0;  // kept here: destroy must not read a destroyed context
-  int dim = 0;
-  DevProblem<float>* d32 = nullptr;
-  DevProblem<double>* d64 = nullptr;
-  DevProblem<double> host64;  // host copy for the sigma_bar lattice bounds
-  DevProblem<float> host32;   // host copy for batches
-  float* mesh_nodes = nullptr;  // device BVH of a mesh boundary
-  float* mesh_tris = nullptr;
-  float* mgrid32 = nullptr;     // mesh distance grid (FP32 walks)
-  double* mgrid64 = nullptr;    // the same grid in FP64 (replay walks)
-  double mesh_lo[3] = {0, 0, 0}, mesh_hi[3] = {0, 0, 0};
-  int mesh_depth = 0;
-  wos::JitState jit;  // walk kernels compiled for this problem (wos_problem_specialize)
-};
+#include "wos_capi_state.h"
 
 namespace {
 
@@ -397,6 +346,29 @@ __global__ void finalize_kernel(const double* sum, const double* sumsq, const in
   }
 }
 
+// The FP32 Newton start table of one dimension, built (in FP64, tens of ms) when the
+// first problem of that dimension is created, so that a context used for 3D problems
+// only never pays for the 2D table.  Problem creation allocates and synchronises anyway;
+// every later launch on any stream finds the table complete.
+int ensure_radial_table(wos_ctx* ctx, int dim) {
+  float*& tab = ctx->radial_tab[dim - 2];
+  if (tab != nullptr) return WOS_OK;
+  float* t = nullptr;
+  cudaError_t e = cudaMalloc(&t, wos::kTabSize * sizeof(float));
+  if (e != cudaSuccess) return fail(ctx, WOS_ENOMEM, std::string("cudaMalloc(radial table): ") + cudaGetErrorString(e));
+  const int blocks = (wos::kTabSize + 127) / 128;
+  if (dim == 2) radial_table_kernel<2><<<blocks, 128>>>(t);
+  else radial_table_kernel<3><<<blocks, 128>>>(t);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(t);
+    return cuda_fail(ctx, e, "radial table kernel");
+  }
+  tab = t;
+  return WOS_OK;
+}
+
 int validate_params(wos_ctx* ctx, const wos_params* prm) {
   if (!prm) return fail(ctx, WOS_EINVAL, "params is NULL");
   if (!finite_pos(prm->eps)) return fail(ctx, WOS_EINVAL, "eps must be finite and > 0");
@@ -522,20 +494,12 @@ int wos_create(wos_ctx** out, int device) {
     delete ctx;
     return WOS_ENOMEM;
   }
-  cudaMemset(ctx->scratch, 0, kScratchWords * sizeof(unsigned long long));
-  for (int k = 0; k < 2; ++k) {
-    if (cudaMalloc(&ctx->radial_tab[k], wos::kTabSize * sizeof(float)) != cudaSuccess) {
-      wos_destroy(ctx);
-      return WOS_ENOMEM;
-    }
-  }
-  int blocks = (wos::kTabSize + 127) / 128;
-  radial_table_kernel<2><<<blocks, 128>>>(ctx->radial_tab[0]);
-  radial_table_kernel<3><<<blocks, 128>>>(ctx->radial_tab[1]);
-  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaMemset(ctx->scratch, 0, kScratchWords * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     wos_destroy(ctx);
     return WOS_ECUDA;
   }
+  // the FP32 radial start tables are built by the first problem of each dimension
   *out = ctx;
   return WOS_OK;
 }
@@ -551,6 +515,9 @@ int wos_destroy(wos_ctx* ctx) {
     if (ctx->h_pts) cudaFree(ctx->h_pts);
     if (ctx->h_acc) cudaFree(ctx->h_acc);
     if (ctx->h_count) cudaFree(ctx->h_count);
+    if (ctx->mv_sum) cudaFree(ctx->mv_sum);
+    if (ctx->mv_count) cudaFree(ctx->mv_count);
+    if (ctx->adj_buf) cudaFree(ctx->adj_buf);
   }
   delete ctx;
   return WOS_OK;
@@ -637,6 +604,12 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   fill_problem(*h32, *d);
   fill_problem(pr->host64, *d);
   DeviceGuard g(ctx->device);
+  rc = ensure_radial_table(ctx, d->dim);
+  if (rc != WOS_OK) {
+    delete h32;
+    delete pr;
+    return rc;
+  }
   cudaError_t e = cudaSuccess;
   if (d->domain.kind == WOS_DOMAIN_MESH) {
     std::vector<wos::MeshNode> nodes;
@@ -1530,9 +1503,40 @@ static_assert(kNaProblem % 256 == 0 && kNaPrefix % 256 == 0, "scratch regions mu
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// device address of g_noalloc_scratch for each device, resolved on first use
-constexpr int kNaMaxDevices = 64;
-unsigned char* g_noalloc_ptr[kNaMaxDevices] = {nullptr};
+// The problem description reaches the scratch as a kernel argument: a by-value
+// parameter is copied by the launch itself, so the host neither blocks (a pageable
+// cudaMemcpyAsync waits for the stream) nor leaves a pointer to its own stack behind.
+// One thread copies it with compile-time offsets (a dynamic index into the parameter
+// block would make a per-thread local copy); it also zeroes the work counter and, when
+// the caller passes no statistics array, the default statistics.
+static_assert(sizeof(DevProblem<double>) + 64 <= 32764, "problem must fit the kernel parameter block");
+template <typename Prob>
+struct NaBlob {
+  int4 w[sizeof(Prob) / 16];
+};
+template <typename Prob>
+__global__ void noalloc_setup_kernel(const NaBlob<Prob> blob, int4* dst, unsigned long long* counter,
+                                     unsigned long long* stats_zero) {
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(Prob) / 16); ++i) dst[i] = blob.w[i];
+  *counter = 0ull;
+  if (stats_zero != nullptr) {
+#pragma unroll
+    for (int i = 0; i < WOS_STATS_WORDS; ++i) stats_zero[i] = 0ull;
+  }
+}
+
+template <typename Prob>
+cudaError_t noalloc_setup(const wos_problem_desc& d, unsigned char* base, unsigned long long* stats_zero,
+                          cudaStream_t st) {
+  Prob h;
+  fill_problem(h, d);
+  NaBlob<Prob> blob;
+  std::memcpy(&blob, &h, sizeof(Prob));
+  noalloc_setup_kernel<Prob><<<1, 1, 0, st>>>(blob, reinterpret_cast<int4*>(base + kNaProblem),
+                                              reinterpret_cast<unsigned long long*>(base + kNaCounter), stats_zero);
+  return cudaGetLastError();
+}
 
 // validation without host allocation (no message strings)
 bool na_field_ok(const wos_field_desc& f, int dim, bool is_source, bool needs_c2) {
@@ -1613,42 +1617,29 @@ extern "C" int wos_solve_noalloc(const wos_problem_desc* desc, const float* pts,
   if (npts == 0 || (walks == nullptr && walks_uniform == 0)) return WOS_OK;
   if (!pts || !sum || !sumsq || !count) return WOS_EINVAL;
 
-  // one-time set-up on this device: resolve the scratch array's device address
+  // The array's address on the current device.  In host code the name
+  // g_noalloc_scratch is only a host-side stand-in, so the kernels get the address the
+  // runtime reports.  It is resolved on every call (no allocation, not a stream
+  // operation): a cached address would go stale if the host program reset the device
+  // and the module were loaded again elsewhere.  The first call on a device also loads
+  // the module there.
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return WOS_ECUDA;
-  if (g_noalloc_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return WOS_ECUDA;
-    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  unsigned char* base = g_noalloc_ptr[dev];
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return WOS_ECUDA;
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || sym == nullptr) return WOS_ECUDA;
+  unsigned char* base = static_cast<unsigned char*>(sym);
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WOS_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-  // the problem description, filled on the host stack and copied into the scratch
+  // problem description into the scratch, work counter (and default statistics) to zero
   const bool fp64 = prm->precision == WOS_FP64;
-  DevProblem<double> h64;
-  DevProblem<float> h32;
-  const void* hsrc;
-  size_t pbytes;
-  if (fp64) {
-    fill_problem(h64, *desc);
-    hsrc = &h64;
-    pbytes = sizeof(h64);
-  } else {
-    fill_problem(h32, *desc);
-    hsrc = &h32;
-    pbytes = sizeof(h32);
-  }
-  cudaError_t e = cudaMemcpyAsync(base + kNaProblem, hsrc, pbytes, cudaMemcpyHostToDevice, st);
-  // the work counter (and the default statistics) must start at zero on every call
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + kNaCounter, 0, 8, st);
+  const size_t pbytes = fp64 ? sizeof(DevProblem<double>) : sizeof(DevProblem<float>);
   unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
-  if (e == cudaSuccess && st_ptr == nullptr) {
-    st_ptr = reinterpret_cast<unsigned long long*>(base + kNaStats);
-    e = cudaMemsetAsync(st_ptr, 0, WOS_STATS_WORDS * sizeof(unsigned long long), st);
-  }
+  unsigned long long* st_zero = nullptr;
+  if (st_ptr == nullptr) st_ptr = st_zero = reinterpret_cast<unsigned long long*>(base + kNaStats);
+  cudaError_t e = fp64 ? noalloc_setup<DevProblem<double>>(*desc, base, st_zero, st)
+                       : noalloc_setup<DevProblem<float>>(*desc, base, st_zero, st);
   if (e != cudaSuccess) return WOS_ECUDA;
 
   const int64_t* walk_end = nullptr;

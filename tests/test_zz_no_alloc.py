@@ -11,7 +11,9 @@ calls in a row (the static scratch keeps the previous call's contents):
   agree to summation-order rounding (1e-9 relative), counts exactly;
 * FP32 walks start Newton differently, so the means agree within 4 combined
   standard errors;
-* per-point walk counts up to the static limit, and the limit itself.
+* per-point walk counts up to the static limit, the limit itself, and a call
+  that fills the static prefix-sum buffer exactly;
+* a call on a stream other than the current one.
 """
 import ctypes as C
 
@@ -76,7 +78,8 @@ def pack(wos, desc, keep):
     return D
 
 
-def noalloc(wos, D, pts, walks, prm, acc, stats=None):
+def noalloc(wos, D, pts, walks, prm, acc, stats=None, stream=None):
+    st = torch.cuda.current_stream() if stream is None else stream
     if isinstance(walks, int):
         wp, wu = None, walks
     else:
@@ -85,7 +88,7 @@ def noalloc(wos, D, pts, walks, prm, acc, stats=None):
                                       C.c_void_p(acc[0].data_ptr()), C.c_void_p(acc[1].data_ptr()),
                                       C.c_void_p(acc[2].data_ptr()),
                                       None if stats is None else C.c_void_p(stats.data_ptr()),
-                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                      C.c_void_p(st.cuda_stream))
     return rc
 
 
@@ -171,3 +174,33 @@ def test_per_point_walks_and_the_static_limit(wos, orc):
     Db = pack(wos, bad, keep)
     assert noalloc(wos, Db, p, 4, wos.params(1e-4, sb), ctx.new_accum(3000)) == wos.WOS_EINVAL
     assert noalloc(wos, D, p, 4, wos.params(0.0, sb), ctx.new_accum(3000)) == wos.WOS_EINVAL
+
+
+def test_full_prefix_buffer_and_a_side_stream(wos, orc):
+    """npts equal to the static limit fills the prefix-sum buffer to its last entry."""
+    desc = W.cube3d_problem()
+    sb = orc.sigma_bar(desc, 64)[0]
+    ctx = wos.Context(0)
+    prob = ctx.problem(desc)
+    keep = []
+    D = pack(wos, desc, keep)
+    n = 65536  # WOS_NOALLOC_MAX_VAR_POINTS
+    pts = W.uniform_in_box(3, n, 0.02, 0.98, 33)
+    walks = torch.from_numpy(np.random.default_rng(4).integers(0, 3, size=n).astype(np.int32)).cuda()
+    p = dev(pts)
+    ref, _ = ctx.solve(prob, p, walks, 1e-4, sb, seed=61, precision="fp64")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        got = ctx.new_accum(n)
+    prm = wos.params(1e-4, sb, seed=61, precision="fp64")
+    for call in range(2):
+        with torch.cuda.stream(side):
+            for t in got:
+                t.zero_()
+        assert noalloc(wos, D, p, walks, prm, got, stream=side) == wos.WOS_OK
+        side.synchronize()
+        assert torch.equal(ref[2], got[2]), call
+        assert torch.equal(got[2].cpu().to(torch.int32), walks.cpu()), call
+        assert torch.allclose(ref[0], got[0], rtol=1e-9, atol=1e-12), call
+        assert torch.allclose(ref[1], got[1], rtol=1e-9, atol=1e-12), call
