@@ -38,20 +38,62 @@ DEFAULT_WALKS = WALKS  # the other workloads use their own walk counts unless --
 EPS = 1e-4
 SEED = 0
 SIGMA_LATTICE = 64
-# Algorithmic work of one walk step of this workload in ALU issue slots (FP32/INT32
-# lane operations; each special-function op counted as 8, the FP32:MUFU rate ratio),
-# for a minimal implementation of the step with the fields as code: Philox 2 blocks
-# 160, uniforms 18, directions 16 + 6 MUFU, box distance 17, Green's norm 14 + 3 MUFU,
-# radius (table start + one Newton step of the radial CDF) 62 + 6 MUFU, coefficients
-# (alpha, Phi, sigma, u_m with value/gradient/Laplacian, f, the transform) 74 + 12 MUFU,
-# update 12  ->  373 ALU + 27 MUFU = 589.
-OPS_PER_STEP = 589
+# Algorithmic work of one walk step of this workload, for a minimal implementation of the
+# step with the fields as code: FP32/INT32 lane operations -- Philox 2 blocks 160, uniforms
+# 18, directions 16, box distance 17, Green's norm 14, radius (table start + one Newton
+# step of the radial CDF) 62, coefficients (alpha, Phi, sigma, u_m with value / gradient /
+# Laplacian, f, the transform) 74, update 12 -> 373; special-function (MUFU) operations --
+# directions 6, Green's norm 3, radius 6, coefficients 12 -> 27.  Every warp instruction
+# takes one issue slot whatever its pipe, and the lanes issue at the FP32 lane rate, so the
+# step needs 400 issue slots; the MUFU pipe (its own rate) is a separate, looser bound.
+LANE_OPS_PER_STEP = 373
+MUFU_OPS_PER_STEP = 27
+ISSUE_OPS_PER_STEP = LANE_OPS_PER_STEP + MUFU_OPS_PER_STEP
+RMS_TARGET = 1e-2
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one launch of the specialised walk kernel on this workload,
 # from the ncu capture summarised in profiles/wos_walk_spec_kernel_cube3d.md (9.53 MB read,
 # 0 written: the points and the radial table; walk state stays in registers).  Reported only
 # for the configuration that capture measured; re-take it whenever the kernel changes.
 TRAFFIC_BYTES_PER_LAUNCH = 9.528320e6
+
+
+def measure_unit_peaks(ctx):
+    """Measured rates of the units the walk kernel uses (library micro-benchmarks, CUDA events)."""
+    lanes, lanes_ms = ctx.measure_peak("fp32_lanes")
+    mufu, mufu_ms = ctx.measure_peak("mufu")
+    l2, l2_ms = ctx.measure_peak("l2_read", 32 << 20)
+    return {"fp32_lanes_per_s": lanes, "mufu_ops_per_s": mufu, "l2_read_bytes_per_s": l2,
+            "how": "wos_measure_peak: FFMA / rsqrt.approx chains at 32 warps per SM; 16-byte cache-global "
+                   "loads of a 32 MiB buffer; 5 launches after one warm-up, CUDA events"}
+
+
+def walks_for_rms(ctx, prob, pts, exact, sb, n_guess, stream, seed):
+    """The smallest tried walks-per-point whose normalised RMS against the exact solution is at
+    most RMS_TARGET: geometric steps of 10% up from 0.8 x the noise-model guess; each try is one
+    solve (fresh accumulators, device-timed with CUDA events)."""
+    import torch
+    npts = pts.shape[1]
+    acc = ctx.new_accum(npts)
+    n = max(256, int(math.ceil(0.8 * n_guess / 256.0)) * 256)
+    tries = []
+    for _ in range(8):
+        for t in acc:
+            t.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve(prob, pts, n, EPS, sb, seed=seed, accum=acc)
+        m, _, _ = ctx.finalize(acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rms = float(np.linalg.norm(m.cpu().numpy() - exact) / np.linalg.norm(exact))
+        tries.append([n, rms, ms])
+        if rms <= RMS_TARGET:
+            return {"walks_per_point": n, "normalised_rms": rms, "solve_ms": ms,
+                    "points_per_s": npts / (ms * 1e-3), "tries": tries, "seed": seed}
+        n = int(math.ceil(1.1 * n / 256.0)) * 256
+    return {"walks_per_point": None, "tries": tries, "seed": seed}
 
 
 def workload_config(extra=None):
@@ -143,13 +185,6 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
-
-
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        return {}
 
 
 # ---------------------------------------------------------------------------
@@ -298,7 +333,8 @@ def run_ours(args):
     # end to end through the C interface with HOST buffers (copies inside the timed region)
     pin_pts = torch.from_numpy(pts_np).pin_memory()
     out = (torch.empty(npts, dtype=torch.float64).pin_memory(), torch.empty(npts, dtype=torch.float64).pin_memory(),
-           torch.empty(npts, dtype=torch.float64).pin_memory(), torch.zeros(5, dtype=torch.int64).pin_memory())
+           torch.empty(npts, dtype=torch.float64).pin_memory(),
+           torch.zeros(wos.STATS_WORDS, dtype=torch.int64).pin_memory())
     e2e_steps = 0
     ctx.solve_host(prob, pin_pts, WALKS, EPS, sb, seed=SEED, walk_offset=offset, out=out)
     torch.cuda.synchronize()
@@ -313,13 +349,11 @@ def run_ours(args):
         e2e_t = float(t.item())
         e2e_steps *= world
     e2e = {"value": e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * npts,
-           "d2h_bytes_per_step": 3 * 8 * npts + 5 * 8}
+           "d2h_bytes_per_step": 3 * 8 * npts + 8 * wos.STATS_WORDS}
 
-    # roofline of the walk kernel (ALU bound): algorithmic issue slots / kernel time
-    props = torch.cuda.get_device_properties(local_rank)
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = 128 * props.multi_processor_count * sm_max * 1e6
+    # roofline of the walk kernel (ALU bound): algorithmic issue slots / kernel time, against
+    # the lane rate measured in this run (and each pipe against its own measured rate)
+    peaks = measure_unit_peaks(ctx)
     # kernel time: the solve dominates the step; finalize and memsets are timed separately below
     fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fe0.record(stream)
@@ -329,14 +363,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     finalize_ms = fe0.elapsed_time(fe1) / 5
     kernel_ms = ms_per_step - finalize_ms
-    achieved = OPS_PER_STEP * (st["steps"] / args.steps) / (kernel_ms * 1e-3)
+    steps_per_s_kernel = (st["steps"] / args.steps) / (kernel_ms * 1e-3)
+    achieved = ISSUE_OPS_PER_STEP * steps_per_s_kernel
+    peak_lanes = peaks["fp32_lanes_per_s"]
     captured = args.kernel == "specialised" and GRID == 64 and WALKS == 1024
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if captured else None,
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lanes / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak_lanes, "traffic": TRAFFIC_BYTES_PER_LAUNCH if captured else None,
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
-                "kernel": kernel_label(args), "ops_per_step": OPS_PER_STEP,
-                "peak_basis": f"128 FP32/INT32 lanes x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
-                              "(sm_max_mhz of MEASURED_PEAKS.json)"}
+                "kernel": kernel_label(args), "ops_per_step": ISSUE_OPS_PER_STEP,
+                "peak_basis": "measured in this run: FP32 FMA lane operations per second (wos_measure_peak); "
+                              "one issue slot per lane operation",
+                "pipes": {"fp32_int_lanes": {"ops_per_step": LANE_OPS_PER_STEP,
+                                             "frac": LANE_OPS_PER_STEP * steps_per_s_kernel / peak_lanes},
+                          "mufu": {"ops_per_step": MUFU_OPS_PER_STEP,
+                                   "frac": MUFU_OPS_PER_STEP * steps_per_s_kernel / peaks["mufu_ops_per_s"]}},
+                "measured_peaks": peaks}
+
+    # points/s at normalised RMS 1e-2, measured: the smallest tried walk count that reaches it
+    rms_run = walks_for_rms(ctx, prob, pts, exact, sb, walks_for_1e2, stream, SEED + 1000) if rank == 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -362,8 +406,8 @@ def run_ours(args):
             "points_per_s": world * npts / (ms_per_step * 1e-3),
             "walks_per_s": world * npts * WALKS / (ms_per_step * 1e-3),
             "steps_per_walk": steps_per_walk, "normalised_rms_at_1024_walks": rms,
-            "walks_per_point_for_rms_1e-2": walks_for_1e2,
-            "points_per_s_at_rms_1e-2": world * npts / (ms_per_step * 1e-3) * WALKS / max(walks_for_1e2, 1),
+            "noise_model_walks_for_rms_1e-2": walks_for_1e2,
+            "points_per_s_at_rms_1e-2": rms_run.get("points_per_s"), "rms_1e-2_run": rms_run,
             "capped_walks": st["capped"], "nonfinite_walks": st["nonfinite"],
             "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks}
@@ -517,17 +561,50 @@ def run_other(args):
                            f"coefficients: {res}^2 slice points x 1 walk per frame + 1280x720 sphere-traced view, "
                            "eps 1e-4", "sigma_bar": sb}
     elif wl == "mesh":
-        desc = W.mesh_noise_problem(level=7)
-        t0 = time.perf_counter()
-        prob = ctx.problem(desc)
-        extra["bvh_build_s"] = time.perf_counter() - t0
-        if args.kernel == "specialised":
-            prob.specialize(("fp32",), ("plain",))
-        sb = ctx.sigma_bar(prob, 48)[0]
+        # distance queries with a certified-radius tolerance (the default walk of this line) and
+        # with exact radii, on the same points, walks and seed; query work read from the
+        # kernel's node and triangle counters
+        l2_peak = ctx.measure_peak("l2_read", 32 << 20)[0]
         npts = args.points
         pts = torch.from_numpy(W.mesh_interior_points(npts, seed=0)).cuda()
         walks = args.walks if args.walks != DEFAULT_WALKS else 512
-        (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
+        sb = None
+        runs, head_ms_st = {}, {}
+        for tol in (args.mesh_tol, 0.0) if args.mesh_tol > 0 else (0.0,):
+            desc = W.mesh_noise_problem(level=7, tol=tol)
+            t0 = time.perf_counter()
+            prob = ctx.problem(desc)
+            build_s = time.perf_counter() - t0
+            if args.kernel == "specialised":
+                prob.specialize(("fp32",), ("plain",))
+            if sb is None:
+                sb = ctx.sigma_bar(prob, 48)[0]
+            (acc, st), ms = timed(lambda i: ctx.solve(prob, pts, walks, 1e-4, sb, seed=i), args.steps)
+            sd = wos.stats_dict(st)  # statistics of the last timed solve
+            steps, walks_n = sd["steps"], sd["walks"]
+            nodes, tris = sd["mesh_nodes"] / sd["steps"], sd["mesh_tris"] / sd["steps"]
+            # bytes one step reads from L2: BVH nodes (128 B), triangles (3 x 16 B), and the
+            # coefficient taps at y (alpha B-spline 64 x 4 B, sigma and f multilinear 8 x 4 B each)
+            bps = 128.0 * nodes + 48.0 * tris + 4.0 * (64 + 8 + 8)
+            m, v, se = ctx.finalize(acc)
+            head_ms_st[tol] = (ms, st)
+            runs[tol] = {"ms": ms, "steps_per_s": steps / (ms * 1e-3), "points_per_s": npts / (ms * 1e-3),
+                         "steps_per_walk": steps / walks_n, "nodes_per_step": nodes, "triangles_per_step": tris,
+                         "exhausted": sd["exhausted"], "bvh_build_s": build_s,
+                         "l2": {"bytes_per_step": bps, "gb_per_s": bps * steps / (ms * 1e-3) / 1e9,
+                                "peak_gb_per_s": l2_peak / 1e9, "frac": bps * steps / (ms * 1e-3) / l2_peak,
+                                "basis": "algorithmic bytes of the visited nodes, tested triangles and field taps "
+                                         "per step (kernel counters) / kernel time; peak: wos_measure_peak L2 read"},
+                         "_mean": m.cpu().numpy(), "_se": se.cpu().numpy()}
+        ms, st = head_ms_st[args.mesh_tol if args.mesh_tol > 0 else 0.0]
+        extra["mesh_tol"] = args.mesh_tol
+        for tol, r in runs.items():
+            extra[f"tol_{tol}"] = {k: v for k, v in r.items() if not k.startswith("_")}
+        if args.mesh_tol > 0:
+            a, b = runs[args.mesh_tol], runs[0.0]
+            extra["speedup_over_exact_radii"] = b["ms"] / a["ms"]
+            extra["mean_abs_z_vs_exact_radii"] = float(np.mean(np.abs(a["_mean"] - b["_mean"]) /
+                                                               np.sqrt(a["_se"] ** 2 + b["_se"] ** 2)))
         if args.dist_grid > 0:
             # the same problem with a distance grid: conservative radii away from the boundary
             dg = W.mesh_noise_problem(level=7, dist_grid=args.dist_grid)
@@ -537,15 +614,12 @@ def run_other(args):
             build_g = time.perf_counter() - t0
             (accg, stg), msg = timed(lambda i: ctx.solve(probg, pts, walks, 1e-4, sb, seed=i), args.steps)
             sg = wos.stats_dict(stg)
-            mg = ctx.finalize(accg)[0].cpu().numpy()
-            m0, v0, se0 = (t.cpu().numpy() for t in ctx.finalize(acc))
             extra[f"dist_grid_{args.dist_grid}"] = {
                 "ms": msg, "steps_per_walk": sg["steps"] / max(sg["walks"], 1),
                 "steps_per_s": sg["steps"] / (msg * 1e-3), "points_per_s": npts / (msg * 1e-3),
-                "build_s": build_g, "speedup_over_exact_radii": ms / msg,
-                "mean_abs_z_vs_exact_radii": float(np.mean(np.abs(mg - m0) / (np.sqrt(2.0) * se0)))}
+                "build_s": build_g, "speedup_over_exact_radii": runs[0.0]["ms"] / msg if 0.0 in runs else None}
         cfg = {"workload": f"displaced icosphere (327,680 triangles), 128^3 noise grids: {npts} interior points "
-                           f"x {walks} walks, eps 1e-4", "sigma_bar": sb}
+                           f"x {walks} walks, eps 1e-4, distance-query tolerance {args.mesh_tol}", "sigma_bar": sb}
     elif wl == "batch":
         probs, pts_np, offs, walks_np = W.batch_problems(args.problems, seed=7)
         t0 = time.perf_counter()
@@ -650,6 +724,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default launch schedule")
     ap.add_argument("--kernel", default="specialised", choices=["specialised", "generic"],
                     help="walk kernel: compiled for the problem's fields (default) or the generic field interpreter")
+    ap.add_argument("--mesh-tol", type=float, default=0.1,
+                    help="mesh workload: certified-radius tolerance of the distance queries (0: exact radii only)")
     ap.add_argument("--dist-grid", type=int, default=128,
                     help="mesh workload: also time walks with an n^3 distance grid (0: exact radii only)")
     args = ap.parse_args()

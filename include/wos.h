@@ -56,7 +56,11 @@ extern "C" {
 #define WOS_STAT_NONFINITE 3 /* walks whose estimate is not finite */
 #define WOS_STAT_OUTSIDE 4   /* walks started at a point with distance <= 0 */
 #define WOS_STAT_INNER 5     /* next-flight walks: inner (in-ball) iterations; steps count balls */
-#define WOS_STATS_WORDS 6
+#define WOS_STAT_MESH_NODES 6 /* mesh walks: BVH nodes visited by the distance queries */
+#define WOS_STAT_MESH_TRIS 7  /* mesh walks: triangles tested by the distance queries */
+#define WOS_STAT_EXHAUSTED 8  /* mesh walks: queries that found no boundary point (the walk ends
+                                 there, at distance 0; should be 0) */
+#define WOS_STATS_WORDS 9
 
 /* ---- problem description ---- */
 
@@ -157,6 +161,15 @@ typedef struct {
      loads instead of a BVH traversal.  Not in the paper (a distance acceleration structure
      in the sense of Sec. 7.1). */
   int32_t mesh_grid_res;
+  /* WOS_DOMAIN_MESH only: 0 (default) makes every ball radius the exact distance.  tol in
+     (0, 0.5] lets a query stop once it has certified a radius between (1 - tol) d and d (d the
+     exact distance): a box is opened only while its distance is below (1 - tol) times the
+     best triangle's, and the radius is (1 - tol) times that triangle's distance, a lower
+     bound of d.  Any ball inside the domain keeps the estimator unbiased (Sec. 2.2); smaller
+     balls cost steps only.  Where the radius falls below eps the exact query runs, so the
+     eps-shell test and the closest point for g are those of the exact walk.  Not in the paper
+     (Sec. 5.2 names distance queries as the main cost; this bounds their work). */
+  double mesh_tol;
 } wos_domain_desc;
 
 /* The PDE of Sec. 3 eq. 1 on a domain.  alpha > 0 (diffusion), phi the drift
@@ -177,6 +190,13 @@ typedef struct {
   wos_domain_desc domain;
   wos_field_desc alpha, phi, sigma, f, g, um;
   wos_field_desc omega[3];
+  /* With an extra drift: 0, or B >= max |omega / alpha| over the domain.  The extra drift's
+     null weight then uses a mixture sample (half of the radius uniform's range draws from
+     G/|G|, half a uniform radius; the source and null weights carry the density ratio),
+     which bounds the |G'/G| factor, and each ball of radius R delta-tracks with its own
+     bound max(sigma_bar, 10 B / R), which bounds the drift weight of small balls near the
+     boundary.  Both keep the expectation (any positive bound per ball is unbiased). */
+  double drift_bound;
 } wos_problem_desc;
 
 enum { WOS_FP32 = 0, WOS_FP64 = 1 };
@@ -270,7 +290,11 @@ int wos_walk_estimates(wos_ctx* ctx, const wos_problem* prob, const float* pts, 
    its first ball's source sample by grad_x G / G at y_0, and the rest of its estimate
    by grad_x G / G (null event) or grad_x P / P at z_0 (boundary step); then
    grad u = e^{-gamma(x_0)} (grad U - U grad gamma(x_0)) with gamma = (ln alpha + Phi)/2.
-   The value estimate is the one wos_solve returns for the same arguments (same walks).
+   The first ball's radius comes from a mixture (half of the radius uniform's range draws
+   from G/|G|, half a uniform radius) and its source and null weights carry the density
+   ratio of G/|G| to the mixture: this bounds the grad G / G factor, whose second moment
+   under G/|G| is infinite, and keeps the expectation of the value and the gradient.  The
+   value estimate therefore has wos_solve's expectation, not its walks.
    A point within eps of the boundary has no first ball: its gradient sums are NaN.
    wos_finalize(grad_sum + d * npts, grad_sumsq + d * npts, count, ...) gives
    component d.  Errors: as wos_solve; WOS_EUNSUPPORTED with a weight window. */
@@ -484,6 +508,115 @@ int wos_slice_points(wos_ctx* ctx, const wos_problem* prob, const wos_view* view
    (mesh domains: their distance is unsigned). */
 int wos_render_slice(wos_ctx* ctx, const wos_problem* prob, const wos_view* view, const double* sum,
                      const int64_t* count, uint8_t* rgba, float* value, float* depth, void* stream);
+
+/* ---- problem handles: the problem statement of Sec. 3 piece by piece ----
+   The calls below build a problem from separate handles for the domain Omega and the
+   scalar fields of eq. 1 (alpha > 0, sigma, the drift potential Phi with
+   omega = alpha grad Phi, the source f and the Dirichlet data g), and return per-point
+   means and variances directly.  They are layered on wos_problem_desc / wos_solve and
+   give the same estimates for the same problem, seed and walks.  A handle is owned by
+   the library until its destroy call; a problem keeps no reference to the handles it
+   was assembled from (grid data stay with the caller and must outlive the problem).
+   ctx may be NULL for the domain and field constructors (errors are then reported by
+   the return code only). */
+typedef struct wos_domain wos_domain;
+typedef struct wos_field wos_field;
+
+/* Axis-aligned box [lo, hi] (dim = 2 or 3; host arrays of dim values).  WOS_EINVAL
+   unless hi > lo in every axis and all values are finite. */
+int wos_domain_box(wos_ctx* ctx, int32_t dim, const double* lo, const double* hi, wos_domain** out);
+/* Analytic signed-distance domain: kind WOS_DOMAIN_BALL (a disk in 2D), WOS_DOMAIN_ANNULUS
+   or WOS_DOMAIN_ROUNDED_BOX, params (host) laid out as wos_domain_desc.p for that kind
+   (ball 4 values, annulus 5, rounded box 7).  WOS_EINVAL for another kind, a non-positive
+   radius or extent, or a corner radius beyond a half extent. */
+int wos_domain_sdf(wos_ctx* ctx, int32_t dim, int32_t kind, const double* params, wos_domain** out);
+/* Closed triangle mesh (3D, Sec. 7.1): verts DEVICE float32 [nverts][3], tris DEVICE int32
+   [ntris][3].  The arrays are copied to the host here (this call synchronises the legacy
+   default stream); the bounding volume hierarchy is built when a problem is assembled on
+   the domain.  WOS_EINVAL for an index out of range, a non-finite vertex, or a surface that
+   is not closed (some edge not shared by exactly two triangles).  Points must lie inside. */
+int wos_domain_mesh(wos_ctx* ctx, const float* verts, int64_t nverts, const int32_t* tris, int64_t ntris,
+                    wos_domain** out);
+int wos_domain_destroy(wos_domain* dom);
+
+/* Analytic field of a family:
+     WOS_FIELD_ZERO          nparams 0;
+     WOS_FIELD_CONST         params[0] = the value (nparams 1);
+     WOS_FIELD_SST           a sum of nparams / 10 separable terms, each packed as 10
+                             doubles (c, type[0..2], k[0..2], phi[0..2]; see wos_term);
+     WOS_FIELD_MANUFACTURED  the manufactured solution u_m packed as for SST: used as the
+                             source f, it stands for f = -div(alpha grad u_m) - omega.grad u_m
+                             + sigma u_m with the problem's own alpha, Phi and sigma.
+   WOS_EINVAL for another family, a bad term count or atom type, or non-finite values. */
+int wos_field_analytic(wos_ctx* ctx, int32_t family_id, const double* params, int32_t nparams, wos_field** out);
+/* Grid field: res[i] >= 2 nodes on [lo[i], hi[i]] (host arrays of dim values), DEVICE
+   float32 node values (x fastest) owned by the caller, interp WOS_FIELD_GRID_LINEAR
+   (multilinear) or WOS_FIELD_GRID_BSPLINE (node values as cubic B-spline control points;
+   alpha and Phi need this one). */
+int wos_field_grid(wos_ctx* ctx, int32_t dim, const int32_t* res, const double* lo, const double* hi,
+                   const float* data, int32_t interp, wos_field** out);
+int wos_field_destroy(wos_field* field);
+
+/* Assemble the problem of eq. 1 on a domain: alpha, sigma, f and g are required, Phi may
+   be NULL (no drift).  The fields' dimension must match the domain's.  Then as
+   wos_problem_create (validation, upload, BVH of a mesh domain). */
+int wos_problem_assemble(wos_ctx* ctx, const wos_domain* dom, const wos_field* alpha, const wos_field* sigma,
+                         const wos_field* phi, const wos_field* f, const wos_field* g, wos_problem** prob);
+
+/* The paper's default delta-tracking bound (Sec. 5.1, Sec. 7.1) with the library's lattice:
+   wos_sigma_bar with m = 256 in 2D and 128 in 3D, on the legacy default stream
+   (synchronised).  Any output pointer but sigma_bar may be NULL. */
+int wos_problem_sigma_bar(wos_ctx* ctx, const wos_problem* prob, double* sigma_bar, double* sigma_prime_min,
+                          double* sigma_prime_max);
+
+/* Run walks and return per-point estimates (Sec. 2.2: the mean of single-walk estimates):
+   mean, var (unbiased sample variance of one walk's estimate) and count, DEVICE arrays of
+   npts.  If count[p] > 0 on entry, the new walks are merged with (mean[p], var[p],
+   count[p]) by the pairwise update of Chan, Golub and LeVeque, so a call with a later
+   walk_offset continues an estimate (pass zeroed counts to start).  Walks go to
+   context-owned FP64 accumulators first (grown with cudaMalloc when npts exceeds their
+   size; otherwise nothing is allocated).  Other arguments and errors as wos_solve. */
+int wos_solve_mean(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, const int32_t* walks,
+                   int32_t walks_uniform, const wos_params* params, double* mean, double* var, int64_t* count,
+                   uint64_t* stats, void* stream);
+
+/* Solve many problems of one dimension in one persistent launch and return per-point
+   estimates as wos_solve_mean.  pt_offsets: HOST [nprob + 1] (points of problem i are
+   pt_offsets[i] .. pt_offsets[i+1]-1 of pts); sigma_bars: HOST [nprob] or NULL (then each
+   problem's wos_problem_sigma_bar).  A batch is created, run and freed inside the call,
+   which therefore allocates and synchronises `stream`; for repeated solves of one batch
+   (and CUDA graphs) use wos_batch_create and wos_solve_batch. */
+int wos_solve_batched(wos_ctx* ctx, const wos_problem* const* probs, int32_t nprob, const int64_t* pt_offsets,
+                      const double* sigma_bars, const float* pts, const int32_t* walks, int32_t walks_uniform,
+                      const wos_params* params, double* mean, double* var, int64_t* count, uint64_t* stats,
+                      void* stream);
+
+/* Gradient of sum_p grad_u[p] * mean_p with respect to the sigma grid's node values
+   (grad_sigma, DEVICE float32 [sigma nodes]) and to the alpha B-spline grid's control
+   values (grad_alpha, DEVICE float32 [alpha nodes]), WRITTEN (not added), by the path
+   replay of wos_adjoint_sigma and wos_adjoint_alpha (FP64 accumulation, then rounded).
+   Either output may be NULL; a non-NULL one needs that field to be a grid of the kind
+   those calls accept (else WOS_EUNSUPPORTED).  Uses context-owned FP64 buffers (grown
+   with cudaMalloc as needed). */
+int wos_adjoint(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, int32_t walks_uniform,
+                const wos_params* params, const double* grad_u, float* grad_sigma, float* grad_alpha,
+                uint64_t* stats, void* stream);
+
+/* ---- measurement utilities (not part of the method) ----
+   Sustained rates of the units the walk kernels use, measured on the context's device
+   (which must be current) with CUDA events around five launches after one warm-up:
+     WOS_PEAK_FP32_LANES  FP32 fused multiply-add lane operations per second (independent
+                          chains; the lanes' rate also bounds the issue of every instruction);
+     WOS_PEAK_MUFU        special-function lane operations per second (approximate
+                          reciprocal square roots, independent chains);
+     WOS_PEAK_L2_READ     bytes per second read by 16-byte cache-global loads (L1 bypassed)
+                          from buf, a zero-filled 16-byte aligned DEVICE buffer of `bytes`
+                          (>= 1 MiB) small enough to stay in L2, read about 40 GB per launch.
+   *rate receives the rate, *ms (may be NULL) one launch's duration.  Synchronises `stream`. */
+#define WOS_PEAK_FP32_LANES 0
+#define WOS_PEAK_MUFU 1
+#define WOS_PEAK_L2_READ 2
+int wos_measure_peak(wos_ctx* ctx, int32_t which, void* buf, int64_t bytes, double* rate, double* ms, void* stream);
 
 /* ---- allocation-free solve ----
    The paper has no counterpart: this entry point exists for callers that cannot

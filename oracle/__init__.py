@@ -66,7 +66,8 @@ class Domain(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("domain", Domain), ("alpha", Field), ("phi", Field),
-                ("sigma", Field), ("f", Field), ("g", Field), ("um", Field), ("omega", Field * 3)]
+                ("sigma", Field), ("f", Field), ("g", Field), ("um", Field), ("omega", Field * 3),
+                ("drift_bound", C.c_double)]
 
 
 def _load():
@@ -84,6 +85,8 @@ def _load():
     for n in ("orc_green_G", "orc_green_cdf", "orc_green_pdf", "orc_green_inv"):
         getattr(lib, n).argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
         getattr(lib, n).restype = C.c_double
+    lib.orc_mix_radius.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp]
+    lib.orc_mix_radius.restype = C.c_double
     for n in ("orc_green_norm", "orc_green_poisson"):
         getattr(lib, n).argtypes = [C.c_int, C.c_double, C.c_double]
         getattr(lib, n).restype = C.c_double
@@ -157,6 +160,7 @@ class _Packed:
             self._field(getattr(P, name), prob[name])
         for d, fd in enumerate(prob.get("omega", [{"kind": "zero"}] * 3)):
             self._field(P.omega[d], fd)
+        P.drift_bound = float(prob.get("drift_bound", 0.0))
         if dom["kind"] == "csg":
             prims = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
             ops = {"union": 0, "intersect": 1, "subtract": 2}
@@ -264,6 +268,13 @@ def green_pdf(dim, R, sb, r):
 
 def green_inv(dim, R, sb, u):
     return _load().orc_green_inv(dim, R, sb, u)
+
+
+def mix_radius(dim, R, sb, ur, lam):
+    """(r, weight) of the mixture ball sample with G/|G| weight lam (reading R22)."""
+    w = C.c_double()
+    r = _load().orc_mix_radius(dim, R, sb, ur, lam, C.byref(w))
+    return r, w.value
 
 
 def field_eval(prob, name, x, packed=None):

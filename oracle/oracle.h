@@ -111,6 +111,9 @@ typedef struct {
      null weights 1 - (sigma' + b . grad gamma + div b) / sigma_bar
      + |G'(r)/G(r)| (dir_y . b(y)) / sigma_bar.  ZERO fields: no extra drift. */
   orc_field omega[3];
+  /* With an extra drift: B >= max |omega_extra / alpha| over the domain, or 0.  B > 0 gives
+     each ball its own bound sigma_B = max(sigma_bar, 10 B / R) (reading R23). */
+  double drift_bound;
 } orc_problem;
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */
@@ -130,6 +133,9 @@ double orc_green_poisson(int dim, double R, double sigma_bar);
 double orc_green_cdf(int dim, double R, double sigma_bar, double r);
 double orc_green_pdf(int dim, double R, double sigma_bar, double r);
 double orc_green_inv(int dim, double R, double sigma_bar, double u);
+/* Reading R22: radius r from the uniform ur under the mixture lam G/|G| (ur < lam, rescaled)
+   + (1 - lam) uniform radius (ur >= lam, rescaled); *mixw = (G/|G|)/mixture density at r. */
+double orc_mix_radius(int dim, double R, double sigma_bar, double ur, double lam, double* mixw);
 
 /* Field value, gradient and Laplacian at x (MANUFACTURED needs the problem). */
 int orc_field_eval(const orc_problem* prob, const orc_field* fld, const double* x,

@@ -22,8 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libwos.so")
 
 WOS_OK, WOS_EINVAL, WOS_ENOMEM, WOS_ECUDA, WOS_ETIMEOUT, WOS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 WOS_FP32, WOS_FP64 = 0, 1
-STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE = range(5)
-STATS_WORDS = 6
+STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE, STAT_INNER = range(6)
+STAT_MESH_NODES, STAT_MESH_TRIS, STAT_EXHAUSTED = 6, 7, 8
+STATS_WORDS = 9
 WOS_SPEC_FP32, WOS_SPEC_FP64, WOS_SPEC_PLAIN, WOS_SPEC_WINDOW, WOS_SPEC_GRAD = 0x1, 0x2, 0x10, 0x20, 0x40
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
 _DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4, "csg": 5}
@@ -54,7 +55,7 @@ class CsgNode(C.Structure):
 class DomainDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_double * 16), ("verts", C.c_void_p), ("nverts", C.c_int64),
                 ("tris", C.c_void_p), ("ntris", C.c_int64), ("csg", C.c_void_p), ("ncsg", C.c_int32),
-                ("mesh_grid_res", C.c_int32)]
+                ("mesh_grid_res", C.c_int32), ("mesh_tol", C.c_double)]
 
 
 class ViewDesc(C.Structure):
@@ -84,7 +85,7 @@ def view(plane_origin, plane_u, plane_v, slice_nu, slice_nv, width, height, valu
 class ProblemDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("domain", DomainDesc), ("alpha", FieldDesc), ("phi", FieldDesc),
                 ("sigma", FieldDesc), ("f", FieldDesc), ("g", FieldDesc), ("um", FieldDesc),
-                ("omega", FieldDesc * 3)]
+                ("omega", FieldDesc * 3), ("drift_bound", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -143,6 +144,21 @@ def load():
     lib.wos_problem_specialized.argtypes = [vp, C.POINTER(i32)]
     lib.wos_jit_source.argtypes = [C.POINTER(ProblemDesc), C.c_char_p, i64, C.POINTER(i64)]
     lib.wos_jit_compile.argtypes = [C.POINTER(ProblemDesc), i32, C.c_char_p, i64, C.POINTER(i64)]
+    # problem-statement calls: domain and field handles, assembly, mean / variance solves
+    lib.wos_domain_box.argtypes = [vp, i32, dp, dp, C.POINTER(vp)]
+    lib.wos_domain_sdf.argtypes = [vp, i32, i32, dp, C.POINTER(vp)]
+    lib.wos_domain_mesh.argtypes = [vp, vp, i64, vp, i64, C.POINTER(vp)]
+    lib.wos_domain_destroy.argtypes = [vp]
+    lib.wos_field_analytic.argtypes = [vp, i32, dp, i32, C.POINTER(vp)]
+    lib.wos_field_grid.argtypes = [vp, i32, C.POINTER(i32), dp, dp, vp, i32, C.POINTER(vp)]
+    lib.wos_field_destroy.argtypes = [vp]
+    lib.wos_problem_assemble.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
+    lib.wos_problem_sigma_bar.argtypes = [vp, vp, dp, dp, dp]
+    lib.wos_solve_mean.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_solve_batched.argtypes = [vp, C.POINTER(vp), i32, vp, vp, vp, vp, i32, C.POINTER(Params), vp, vp, vp,
+                                      vp, vp]
+    lib.wos_adjoint.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
+    lib.wos_measure_peak.argtypes = [vp, i32, vp, i64, dp, dp, vp]
     _lib = lib
     return lib
 
@@ -194,6 +210,7 @@ def describe(desc, device=None):
     keep = []
     ptrs = {"sigma": 0, "alpha": 0}
     D.dim = desc["dim"]
+    D.drift_bound = float(desc.get("drift_bound", 0.0))
     D.domain.kind = _DOM_KINDS[desc["domain"]["kind"]]
     for i, v in enumerate(desc["domain"]["p"]):
         D.domain.p[i] = v
@@ -204,6 +221,7 @@ def describe(desc, device=None):
         D.domain.verts, D.domain.nverts = verts.ctypes.data, len(verts)
         D.domain.tris, D.domain.ntris = tris.ctypes.data, len(tris)
         D.domain.mesh_grid_res = int(desc["domain"].get("grid_res", 0))
+        D.domain.mesh_tol = float(desc["domain"].get("tol", 0.0))
     if desc["domain"]["kind"] == "csg":
         nodes = desc["domain"]["nodes"]
         arr = (CsgNode * max(1, len(nodes)))()
@@ -341,6 +359,38 @@ class Problem:
             pass
 
 
+def _dvec(vals):
+    arr = (C.c_double * max(1, len(vals)))(*[float(v) for v in vals])
+    return arr
+
+
+def pack_terms(terms):
+    """Separable terms (workloads format) as the 10-double packing of wos_field_analytic."""
+    out = []
+    for t in terms:
+        atoms = list(t["atoms"]) + [(0, 0.0, 0.0)] * (3 - len(t["atoms"]))
+        out += [t["c"]] + [a[0] for a in atoms] + [a[1] for a in atoms] + [a[2] for a in atoms]
+    return out
+
+
+class Handle:
+    """A domain or field handle of the problem-statement calls (owns it)."""
+
+    def __init__(self, lib, h, destroy, keep=None, dim=0):
+        self.lib, self.handle, self._destroy, self._keep, self.dim = lib, h, destroy, keep, dim
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Many independent problems solved by one launch (owns the library handle)."""
 
@@ -418,6 +468,163 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    # ---- measurement utilities ----
+    def measure_peak(self, unit, l2_bytes=32 << 20, stream=None):
+        """Measured rate of 'fp32_lanes' (lane ops/s), 'mufu' (ops/s) or 'l2_read' (bytes/s, from
+        a zero-filled l2_bytes buffer); returns (rate, ms per launch)."""
+        import torch
+        which = {"fp32_lanes": 0, "mufu": 1, "l2_read": 2}[unit]
+        buf = torch.zeros(l2_bytes // 4, dtype=torch.float32, device=f"cuda:{self.device}") if which == 2 else None
+        r, ms = C.c_double(), C.c_double()
+        self._check(self.lib.wos_measure_peak(self.handle, which, _ptr(buf), l2_bytes if buf is not None else 0,
+                                              C.byref(r), C.byref(ms), _stream(stream)))
+        return r.value, ms.value
+
+    # ---- problem-statement calls (handles) ----
+    def _handle(self, rc, h, destroy, keep=None, dim=0):
+        self._check(rc)
+        return Handle(self.lib, h, destroy, keep, dim)
+
+    def domain_box(self, dim, lo, hi):
+        h = C.c_void_p()
+        return self._handle(self.lib.wos_domain_box(self.handle, int(dim), _dvec(lo), _dvec(hi), C.byref(h)), h,
+                            self.lib.wos_domain_destroy, dim=dim)
+
+    def domain_sdf(self, dim, kind, p):
+        """kind: 'ball', 'annulus' or 'rounded_box'; p as wos_domain_desc.p for that kind."""
+        h = C.c_void_p()
+        return self._handle(self.lib.wos_domain_sdf(self.handle, int(dim), _DOM_KINDS[kind], _dvec(p), C.byref(h)),
+                            h, self.lib.wos_domain_destroy, dim=dim)
+
+    def domain_mesh(self, verts, tris):
+        """verts: CUDA float32 [nv, 3], tris: CUDA int32 [nt, 3] (copied by the call)."""
+        verts, tris = verts.contiguous(), tris.contiguous()
+        h = C.c_void_p()
+        return self._handle(self.lib.wos_domain_mesh(self.handle, _ptr(verts), verts.shape[0], _ptr(tris),
+                                                     tris.shape[0], C.byref(h)), h, self.lib.wos_domain_destroy,
+                            dim=3)
+
+    def field_analytic(self, family, p=()):
+        """family: 'zero', 'const' (p = [value]), 'sst' or 'manufactured' (p = pack_terms(...))."""
+        h = C.c_void_p()
+        return self._handle(self.lib.wos_field_analytic(self.handle, _FIELD_KINDS[family], _dvec(p), len(p),
+                                                        C.byref(h)), h, self.lib.wos_field_destroy)
+
+    def field_grid(self, dim, res, lo, hi, data, interp="grid_linear"):
+        """data: CUDA float32 node values (x fastest), kept alive by the handle."""
+        data = data.contiguous()
+        r = (C.c_int32 * 3)(*[int(v) for v in list(res) + [1] * (3 - len(res))])
+        h = C.c_void_p()
+        return self._handle(self.lib.wos_field_grid(self.handle, int(dim), r, _dvec(lo), _dvec(hi), _ptr(data),
+                                                    _FIELD_KINDS[interp], C.byref(h)), h,
+                            self.lib.wos_field_destroy, keep=data, dim=dim)
+
+    def field(self, fd, dim):
+        """A handle for a workloads field dict (grid data uploaded to this context's device)."""
+        import torch
+        k = fd["kind"]
+        if k in ("zero",):
+            return self.field_analytic("zero")
+        if k == "const":
+            return self.field_analytic("const", [fd["value"]])
+        if k == "sst":
+            return self.field_analytic("sst", pack_terms(fd["terms"]))
+        if k.startswith("grid"):
+            data = fd["data"]
+            if not isinstance(data, torch.Tensor):
+                data = torch.as_tensor(np.ascontiguousarray(data, dtype=np.float32))
+            data = data.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+            return self.field_grid(dim, fd["res"][:dim], fd["lo"][:dim], fd["hi"][:dim], data, k)
+        raise ValueError(f"field kind {k} has no handle of its own")
+
+    def problem_assemble(self, domain, alpha, sigma, phi, f, g):
+        """A Problem from handles (phi may be None)."""
+        h = C.c_void_p()
+        self._check(self.lib.wos_problem_assemble(self.handle, domain.handle, alpha.handle, sigma.handle,
+                                                  phi.handle if phi is not None else None, f.handle, g.handle,
+                                                  C.byref(h)))
+        p = Problem.__new__(Problem)
+        p.ctx, p.dim, p.handle = self, domain.dim, h
+        p._keep = [domain, alpha, sigma, phi, f, g]
+        p._sigma_ptr = sigma._keep.data_ptr() if sigma._keep is not None else 0
+        p._alpha_ptr = alpha._keep.data_ptr() if alpha._keep is not None else 0
+        self._children.add(p)
+        return p
+
+    def problem_sigma_bar(self, prob):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.wos_problem_sigma_bar(self.handle, prob.handle, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def new_moments(self, npts):
+        """Zeroed (mean, var, count) for solve_mean."""
+        import torch
+        dev = f"cuda:{self.device}"
+        return (torch.zeros(npts, dtype=torch.float64, device=dev), torch.zeros(npts, dtype=torch.float64, device=dev),
+                torch.zeros(npts, dtype=torch.int64, device=dev))
+
+    def _walks(self, walks, npts):
+        import torch
+        if isinstance(walks, int):
+            return None, walks, None
+        if not (isinstance(walks, torch.Tensor) and walks.is_cuda and walks.dtype == torch.int32
+                and walks.shape == (npts,)):
+            raise TypeError("walks must be an int or a CUDA int32 tensor of shape [npts]")
+        walks = walks.contiguous()
+        return _ptr(walks), 0, walks
+
+    def solve_mean(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
+                   precision="fp32", moments=None, stats=None, stream=None):
+        """Per-point (mean, var, count), merged into `moments` when its counts are non-zero."""
+        pts = _points(pts, prob.dim, self.device)
+        npts = pts.shape[1]
+        if moments is None:
+            moments = self.new_moments(npts)
+        if stats is None:
+            stats = self.new_stats()
+        wp, wu, _w = self._walks(walks, npts)
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_mean(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
+                                            _ptr(moments[0]), _ptr(moments[1]), _ptr(moments[2]), _ptr(stats),
+                                            _stream(stream)))
+        return moments, stats
+
+    def solve_batched(self, problems, pt_offsets, sigma_bars, pts, walks, eps, seed=0, walk_offset=0,
+                      max_steps=1 << 20, precision="fp32", moments=None, stats=None, stream=None):
+        """One-call batch (creates, runs and frees a batch): per-point (mean, var, count)."""
+        offs = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+        sbs = None if sigma_bars is None else np.ascontiguousarray(sigma_bars, dtype=np.float64)
+        dim = problems[0].dim
+        pts = _points(pts, dim, self.device)
+        npts = pts.shape[1]
+        if moments is None:
+            moments = self.new_moments(npts)
+        if stats is None:
+            stats = self.new_stats()
+        wp, wu, _w = self._walks(walks, npts)
+        handles = (C.c_void_p * len(problems))(*[q.handle.value for q in problems])
+        p = params(eps, 1.0, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_solve_batched(self.handle, handles, len(problems), offs.ctypes.data,
+                                               None if sbs is None else sbs.ctypes.data, _ptr(pts), wp, wu,
+                                               C.byref(p), _ptr(moments[0]), _ptr(moments[1]), _ptr(moments[2]),
+                                               _ptr(stats), _stream(stream)))
+        return moments, stats
+
+    def adjoint(self, prob, pts, walks_uniform, eps, sigma_bar, grad_u, sigma_nodes=0, alpha_nodes=0, seed=0,
+                walk_offset=0, max_steps=1 << 20, precision="fp32", stats=None, stream=None):
+        """wos_adjoint: float32 gradients with respect to the sigma grid (sigma_nodes > 0) and the
+        alpha grid (alpha_nodes > 0); either is None when not asked for."""
+        import torch
+        pts = _points(pts, prob.dim, self.device)
+        dev = f"cuda:{self.device}"
+        gs = torch.empty(sigma_nodes, dtype=torch.float32, device=dev) if sigma_nodes else None
+        ga = torch.empty(alpha_nodes, dtype=torch.float32, device=dev) if alpha_nodes else None
+        gu = grad_u.to(device=dev, dtype=torch.float64).contiguous()
+        p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
+        self._check(self.lib.wos_adjoint(self.handle, prob.handle, _ptr(pts), pts.shape[1], int(walks_uniform),
+                                         C.byref(p), _ptr(gu), _ptr(gs), _ptr(ga), _ptr(stats), _stream(stream)))
+        return gs, ga
 
     # ---- calls ----
     def problem(self, desc, specialize=None):
@@ -713,6 +920,8 @@ class Context:
         if out is None:
             out = (torch.empty(npts, dtype=torch.float64), torch.empty(npts, dtype=torch.float64),
                    torch.empty(npts, dtype=torch.float64), torch.zeros(STATS_WORDS, dtype=torch.int64))
+        if not all(t.numel() >= n for t, n in zip(out, (npts, npts, npts, STATS_WORDS))):
+            raise ValueError("host output buffers are too small")
         p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
         self._check(self.lib.wos_solve_host(self.handle, prob.handle, C.c_void_p(pts_host.data_ptr()), npts,
                                             int(walks), C.byref(p), C.c_void_p(out[0].data_ptr()),
@@ -723,7 +932,8 @@ class Context:
 
 def stats_dict(stats):
     s = [int(v) for v in stats.cpu().tolist()]
-    return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4], "inner": s[5]}
+    return {"steps": s[0], "walks": s[1], "capped": s[2], "nonfinite": s[3], "outside": s[4], "inner": s[5],
+            "mesh_nodes": s[6], "mesh_tris": s[7], "exhausted": s[8]}
 
 
 class SliceView:

@@ -22,9 +22,9 @@ LIB = os.path.join(HERE, "libwos.so")
 HOSTCHECK = os.path.join(HERE, "libwos_hostcheck.so")
 
 CU_SOURCES = ["wos_capi.cu", "wos_walk_f32.cu", "wos_walk_f64.cu", "wos_nf_f32.cu", "wos_nf_f64.cu",
-              "wos_adjoint.cu", "wos_render.cu", "wos_jit.cu", "wos_mesh.cpp"]
+              "wos_adjoint.cu", "wos_render.cu", "wos_jit.cu", "wos_mesh.cpp", "wos_handles.cu", "wos_peaks.cu"]
 HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_nf_impl.cuh", "wos_adjoint_impl.cuh",
-           "wos_internal.h", "wos_mesh.h", "wos_jit.h"]
+           "wos_internal.h", "wos_mesh.h", "wos_jit.h", "wos_capi_state.h"]
 # headers of the walk kernel, embedded in the library for the runtime-compiled (problem-
 # specialised) kernels
 JIT_HEADERS = ["wos_internal.h", "wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh"]

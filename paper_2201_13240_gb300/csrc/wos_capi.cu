@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kScratchWords = 64;
 constexpr int kScratchStats = 8;
-constexpr int kScratchSigma = 16;
+constexpr int kScratchSigma = 24;
 
 int fail(wos_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -181,6 +181,8 @@ void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
       for (int k = 0; k < 8; ++k) P.csg[i].p[k] = R(q[k]);
     }
   }
+  P.mesh_tau = R(1);
+  if (d.domain.kind == WOS_DOMAIN_MESH) P.mesh_tau = R((1.0 - d.domain.mesh_tol) * (1.0 - d.domain.mesh_tol));
   fill_field(P, P.alpha, d.alpha, d.dim);
   fill_field(P, P.phi, d.phi, d.dim);
   fill_field(P, P.sigma, d.sigma, d.dim);
@@ -188,6 +190,7 @@ void fill_problem(DevProblem<R>& P, const wos_problem_desc& d) {
   fill_field(P, P.g, d.g, d.dim);
   fill_field(P, P.um, d.um, d.dim);
   P.has_drift = 0;
+  P.drift_bound = R(d.drift_bound);
   for (int k = 0; k < 3; ++k) {
     if (k < d.dim) {
       fill_field(P, P.omega[k], d.omega[k], d.dim);
@@ -555,6 +558,8 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
         return fail(ctx, WOS_EINVAL, "mesh: need vertices and triangles");
       if (d->domain.mesh_grid_res != 0 && (d->domain.mesh_grid_res < 4 || d->domain.mesh_grid_res > 512))
         return fail(ctx, WOS_EINVAL, "mesh: grid resolution must be 0 or in 4..512");
+      if (!(d->domain.mesh_tol >= 0.0 && d->domain.mesh_tol <= 0.5))
+        return fail(ctx, WOS_EINVAL, "mesh: tolerance must be in [0, 0.5]");
       break;
     case WOS_DOMAIN_CSG: {
       if (!d->domain.csg || d->domain.ncsg < 1 || d->domain.ncsg > WOS_CSG_MAX_NODES)
@@ -593,6 +598,8 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
   bool drift = false;
   int rc = check_fields(*d, &drift, &why);
   if (rc != WOS_OK) return fail(ctx, rc, why);
+  if (!(d->drift_bound >= 0.0) || !std::isfinite(d->drift_bound))
+    return fail(ctx, WOS_EINVAL, "drift_bound must be finite and >= 0");
   if (drift && d->domain.kind == WOS_DOMAIN_MESH)
     return fail(ctx, WOS_EUNSUPPORTED, "an extra drift (omega) on a mesh domain is not supported");
 

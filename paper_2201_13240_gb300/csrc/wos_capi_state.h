@@ -19,7 +19,7 @@ struct wos_ctx {
   int device = 0;
   int num_sms = 0;
   std::string err;
-  // scratch: [0] work counter, [8..8+ST_WORDS) default stats, [16..20) sigma-bar reduction
+  // scratch: [0] work counter, [8..8+ST_WORDS) default stats, [24..29) sigma-bar reduction
   unsigned long long* scratch = nullptr;
   // walks-per-point prefix sums
   int64_t* walk_end = nullptr;

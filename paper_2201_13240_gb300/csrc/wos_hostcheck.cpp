@@ -186,4 +186,23 @@ void wos_hc_green_dlog(int dim, int fp64, double a, const double* rho, int64_t n
   }
 }
 
+// the mixture ball sample: out[2i] = rho, out[2i+1] = its weight, for radius uniforms u
+void wos_hc_mix_radius(int dim, int fp64, double a, double lam, const double* u, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (fp64) {
+      double w = 0.0;
+      double rho = (dim == 2) ? wos::mix_sample_radius<2, double>(a, u[i], nullptr, lam, &w)
+                              : wos::mix_sample_radius<3, double>(a, u[i], nullptr, lam, &w);
+      out[2 * i] = rho;
+      out[2 * i + 1] = w;
+    } else {
+      float w = 0.0f;
+      float rho = (dim == 2) ? wos::mix_sample_radius<2, float>((float)a, (float)u[i], nullptr, (float)lam, &w)
+                             : wos::mix_sample_radius<3, float>((float)a, (float)u[i], nullptr, (float)lam, &w);
+      out[2 * i] = rho;
+      out[2 * i + 1] = w;
+    }
+  }
+}
+
 }  // extern "C"

@@ -12,7 +12,10 @@
 namespace wos {
 
 // statistics words written by the walk kernel (added atomically)
-enum { ST_STEPS = 0, ST_WALKS = 1, ST_CAPPED = 2, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_INNER = 5, ST_WORDS = 6 };
+enum {
+  ST_STEPS = 0, ST_WALKS = 1, ST_CAPPED = 2, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_INNER = 5,
+  ST_MESH_NODES = 6, ST_MESH_TRIS = 7, ST_EXHAUSTED = 8, ST_WORDS = 9
+};
 
 struct WalkLaunch {
   const void* problem;            // DevProblem<R> in device memory

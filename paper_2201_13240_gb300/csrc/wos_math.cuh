@@ -1054,4 +1054,34 @@ WOS_HD R sample_radius(R a, R u, int* iters_used = nullptr, const float* tab = n
   }
 }
 
+// density f(rho) = dF/drho of rho = r/R under y ~ G/|G|
+template <int DIM, typename R>
+WOS_HD R radial_pdf(R a, R rho) {
+  R F, p;
+  if (DIM == 3) {
+    Radial3<R> rad;
+    rad.init(a);
+    rad.eval(rho, &F, &p);
+  } else {
+    radial2_once(a, rho, &F, &p);
+  }
+  return p;
+}
+
+// Mixture ball sample for weights that carry |G'(r)/G(r)| (the extra drift's null weight,
+// the gradient's first ball), which has an infinite second moment under G/|G|: a fraction
+// lam of the radius uniform's range draws from G/|G| (u < lam, rescaled to u / lam), the
+// rest a uniform radius (rho = (u - lam) / (1 - lam)).  The source term and the null
+// weight are then multiplied by *mixw = f / (lam f + 1 - lam), the density ratio of G/|G|
+// to the mixture, which keeps their expectations and bounds the weight at both ends.
+template <int DIM, typename R>
+WOS_HD R mix_sample_radius(R a, R u, const float* tab, R lam, R* mixw) {
+  R rho;
+  if (u < lam) rho = sample_radius<DIM, R>(a, u / lam, nullptr, tab);
+  else rho = (u - lam) / (R(1) - lam);
+  const R f = radial_pdf<DIM, R>(a, rho);
+  *mixw = f / (lam * f + (R(1) - lam));
+  return rho;
+}
+
 }  // namespace wos

@@ -84,7 +84,8 @@ struct DevProblem {
   const void* mg_pad_ptr;   // keeps the 16-byte layout
   R mg_lo[3], mg_h[3], mg_inv_h[3];
   R mg_thresh;              // use the grid's lower bound when it is at least this
-  R mg_pad[2];
+  R mesh_tau;               // mesh queries: squared radius factor (1 - tol)^2 (1: exact radii)
+  R drift_bound;            // extra drift: B >= max |omega / alpha| (0: none), for per-ball bounds
   CsgNode<R> csg[kMaxCsg];
   DevTerm<R> terms[kMaxTerms];
 };
@@ -469,14 +470,32 @@ WOS_HD void tri_closest(const R* p, const float* t, R* v_out, R* w_out, R* d2_ou
 
 template <typename R>
 struct MeshHit {
-  R d, x, y, z;
+  R d;        // a certified lower bound of the distance: the exact distance when tau = 1
+  R x, y, z;  // the best boundary point found (NaN when none is known)
+};
+
+// Counters of one lane's mesh queries (BVH nodes visited, triangles tested, searches that
+// found no boundary point), added to the walk statistics.
+struct MeshVisits {
+  unsigned long long nodes, tris;
+  uint32_t exhausted;
 };
 
 // bound2: an upper bound of the squared distance (a known boundary point's), or
 // infinity.  The search starts from it, slightly enlarged for rounding, so only
-// boxes nearer than a known boundary point are opened; if rounding still hides
-// every triangle, the search restarts without the bound.  The result does not
-// depend on the bound.
+// boxes nearer than a known boundary point are opened.
+// tau = 1 (exact): if rounding still hides every triangle, the search restarts
+// without the bound, and the result does not depend on the bound.
+// tau < 1 (a radius within a factor sqrt(tau) of the distance): a box is opened only
+// if its squared distance is below tau times the best squared distance so far, and
+// the query returns sqrt(tau * best).  Every box left closed then holds only triangles
+// at squared distance >= tau * best, and every tested triangle is at >= best, so the
+// returned value is a lower bound of the distance (the ball it spans lies in the
+// domain, which keeps the walk's estimator unbiased) and at least sqrt(tau) times the
+// distance.  When nothing is found inside the bound, the bound's own boundary point pb
+// (if given) is the best point.  Deep inside a near-spherical surface almost every
+// leaf lies within the exact search's bound; with tau < 1 the query stops at boxes
+// that are small enough to be certified.
 // The tree has 4-wide nodes of one 128-byte line (MeshNode4 in wos_mesh.h: child boxes
 // as structure of arrays): a visit loads one line and tests four boxes, so a query
 // follows half as many dependent loads as in the binary tree.  Leaf children nearer
@@ -511,7 +530,7 @@ WOS_HD R box_d2_1(const R* x, float lx, float ly, float lz, float hx, float hy, 
 
 template <typename R, bool SMEM>
 WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2, int* sn, R* sd,
-                                   int stride) {
+                                   int stride, R tau = R(1), const R* pb = nullptr, MeshVisits* vis = nullptr) {
   const R x[3] = {x0, x1, x2};
   const float* nodes = P.mesh_nodes;
   const float* tris = P.mesh_tris;
@@ -520,16 +539,19 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
   int* stk_n = SMEM ? sn : loc_n;
   R* stk_d = SMEM ? sd : loc_d;
   const int sst = SMEM ? stride : 1;
+  const bool exact = !(tau < R(1));
   R best = R(INFINITY), bv = R(0), bw = R(0);
   int best_t = -1;
   const R slack = (sizeof(R) == 4) ? R(1e-5) : R(1e-12);
   const R start = (bound2 < R(INFINITY)) ? bound2 * (R(1) + slack) + R(1e-30) : R(INFINITY);
+  unsigned long long n_nodes = 0, n_tris = 0;
   bool again = true;
   for (int pass = 0; pass < 8 && again; ++pass) {
-    // pass 0 starts from the bound; a pass that found nothing within it, or dropped
-    // stack entries, is followed by one from the root with the best so far
+    // pass 0 starts from the bound.  Exact: a pass that found nothing within it, or
+    // dropped stack entries, is followed by one from the root with the best so far (or
+    // none).  tau < 1: only a pass that dropped entries is repeated, from the best so far.
     if (pass == 0) best = start;
-    else if (best_t < 0) best = R(INFINITY);
+    else if (best_t < 0 && exact) best = R(INFINITY);
     again = false;
     int sp = 0;
     int node = 0;
@@ -538,26 +560,29 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
       const F4 lx = ld4(nd), ly = ld4(nd + 4), lz = ld4(nd + 8), hx = ld4(nd + 12), hy = ld4(nd + 16),
                hz = ld4(nd + 20);
       const I4 ch = ld4i(nd + 24), cn = ld4i(nd + 28);
+      ++n_nodes;
       R d[4] = {box_d2_1(x, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x), box_d2_1(x, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y),
                 box_d2_1(x, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z), box_d2_1(x, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w)};
       const int cc[4] = {ch.x, ch.y, ch.z, ch.w}, nc[4] = {cn.x, cn.y, cn.z, cn.w};
-      // leaf children nearer than the best triangle: test them now (lowers best)
+      // leaf children within the opening threshold: test them now (lowers best)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (nc[i] > 0 && d[i] < best) {
+        if (nc[i] > 0 && d[i] < tau * best) {
           for (int j = 0; j < nc[i]; ++j) {
             R v, w, d2;
             tri_closest(x, tris + 12 * (cc[i] + j), &v, &w, &d2);
             if (d2 < best) { best = d2; best_t = cc[i] + j; bv = v; bw = w; }
           }
+          n_tris += (unsigned long long)nc[i];
         }
       }
-      // interior children nearer than the best: sort by distance (others at infinity)
+      const R thr = tau * best;
+      // interior children within the threshold: sort by distance (others at infinity)
       R k[4];
       int c[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        k[i] = (nc[i] == 0 && d[i] < best) ? d[i] : R(INFINITY);
+        k[i] = (nc[i] == 0 && d[i] < thr) ? d[i] : R(INFINITY);
         c[i] = cc[i];
       }
 #define WOS_CSWAP(a, b)                                   \
@@ -570,7 +595,7 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
       // push the farther ones (farthest first, so the nearer are popped first)
 #pragma unroll
       for (int i = 3; i >= 1; --i) {
-        if (k[i] < best) {
+        if (k[i] < thr) {
           if (sp < kMeshStack) {
             stk_n[sp * sst] = c[i];
             stk_d[sp * sst] = k[i];
@@ -580,28 +605,47 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
           }
         }
       }
-      if (k[0] < best) {
+      if (k[0] < thr) {
         node = c[0];
         continue;
       }
-      // pop the next node still nearer than the best triangle
+      // pop the next node still within the threshold of the best triangle
       bool found = false;
       while (sp > 0) {
         --sp;
-        if (stk_d[sp * sst] < best) { node = stk_n[sp * sst]; found = true; break; }
+        if (stk_d[sp * sst] < tau * best) { node = stk_n[sp * sst]; found = true; break; }
       }
       if (!found) break;
     }
-    if (best_t < 0) again = true;
+    if (best_t < 0 && exact) again = true;
   }
-  if (best_t < 0) best_t = 0;
-  const float* t = tris + 12 * best_t;
-  F4 A = ld4(t), B = ld4(t + 4), Cc = ld4(t + 8);
   MeshHit<R> h;
-  h.x = R(A.x) + (R(B.x) - R(A.x)) * bv + (R(Cc.x) - R(A.x)) * bw;
-  h.y = R(A.y) + (R(B.y) - R(A.y)) * bv + (R(Cc.y) - R(A.y)) * bw;
-  h.z = R(A.z) + (R(B.z) - R(A.z)) * bv + (R(Cc.z) - R(A.z)) * bw;
-  h.d = w_sqrt(best);
+  if (vis != nullptr) {
+    vis->nodes += n_nodes;
+    vis->tris += n_tris;
+  }
+  if (best_t >= 0) {
+    const float* t = tris + 12 * best_t;
+    F4 A = ld4(t), B = ld4(t + 4), Cc = ld4(t + 8);
+    h.x = R(A.x) + (R(B.x) - R(A.x)) * bv + (R(Cc.x) - R(A.x)) * bw;
+    h.y = R(A.y) + (R(B.y) - R(A.y)) * bv + (R(Cc.y) - R(A.y)) * bw;
+    h.z = R(A.z) + (R(B.z) - R(A.z)) * bv + (R(Cc.z) - R(A.z)) * bw;
+    h.d = exact ? w_sqrt(best) : w_sqrt(tau * best);
+  } else if (!exact && best < R(INFINITY)) {
+    // nothing inside the bound: its own boundary point (when known) is the best point
+    h.x = pb ? pb[0] : R(NAN);
+    h.y = pb ? pb[1] : R(NAN);
+    h.z = pb ? pb[2] : R(NAN);
+    h.d = w_sqrt(tau * best);
+  } else {
+    // no boundary point found at all (eight passes of overflowing stacks, or a non-finite
+    // point): counted, and the walk ends here (distance 0, closest point x)
+    if (vis != nullptr) ++vis->exhausted;
+    h.x = x0;
+    h.y = x1;
+    h.z = x2;
+    h.d = R(0);
+  }
   return h;
 }
 
@@ -731,9 +775,11 @@ WOS_HD R csg_sdf(const DevProblem<R>& P, const R* x, R* g) {
 
 // bound2 (meshes only): an upper bound of the squared distance, see mesh_query.
 // MESH = false compiles the mesh case out (for kernels launched on analytic domains).
+// tau, pb, vis (meshes only): see mesh_query; tau = 1 returns the exact distance.
 template <int DIM, typename R, bool MESH = true>
 WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY), int* stk_n = nullptr,
-                  R* stk_d = nullptr, int stk_stride = 0) {
+                  R* stk_d = nullptr, int stk_stride = 0, R tau = R(1), const R* pb = nullptr,
+                  MeshVisits* vis = nullptr) {
   const R* p = P.dom;
 #pragma unroll
   for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
@@ -832,11 +878,20 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
           lo_b = w_fmax(lo_b, dc - dist);
           hi_b = w_fmin(hi_b, dc + dist);
         }
-        if (lo_b >= P.mg_thresh) return lo_b;  // xb unused: the walk is not in the shell
-        bound2 = hi_b * hi_b;
+        if (lo_b >= P.mg_thresh) {
+          // the walk is not in the shell; no boundary point is known (NaN: the next step's
+          // query starts without a bound)
+          xb[0] = xb[1] = xb[2] = R(NAN);
+          return lo_b;
+        }
+        if (hi_b * hi_b < bound2) {
+          bound2 = hi_b * hi_b;
+          pb = nullptr;  // the grid's bound has no boundary point of its own
+        }
       }
-      MeshHit<R> h = (stk_n != nullptr) ? mesh_query<R, true>(P, x[0], x[1], x[2], bound2, stk_n, stk_d, stk_stride)
-                                        : mesh_query<R, false>(P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0);
+      MeshHit<R> h = (stk_n != nullptr)
+                         ? mesh_query<R, true>(P, x[0], x[1], x[2], bound2, stk_n, stk_d, stk_stride, tau, pb, vis)
+                         : mesh_query<R, false>(P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0, tau, pb, vis);
       xb[0] = h.x;
       xb[1] = h.y;
       xb[2] = h.z;

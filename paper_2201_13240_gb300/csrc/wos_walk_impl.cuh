@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(kWalkBlock,
   // per-lane statistics: a lane finishes far fewer than 2^32 walks in one launch
   unsigned long long st_steps = 0;
   uint32_t st_walks = 0, st_capped = 0, st_nonfinite = 0, st_outside = 0;
+  MeshVisits mvis = {0ull, 0ull, 0u};  // mesh queries: nodes, triangles, exhausted searches
   // weight window: copies waiting to run (position, weight, step, branch id)
   R stk_x[WW ? kWWDepth : 1][3], stk_W[WW ? kWWDepth : 1];
   uint32_t stk_k[WW ? kWWDepth : 1], stk_id[WW ? kWWDepth : 1];
@@ -257,15 +258,33 @@ __global__ void __launch_bounds__(kWalkBlock,
 
     // ---- one step of the walk ----
     R xb[3];
-    R bound2 = R(INFINITY);
-    if (MESH && s.k > 0) {
-      R e0 = s.x[0] - s.xbp[0], e1 = s.x[1] - s.xbp[1], e2 = s.x[2] - s.xbp[2];
-      bound2 = e0 * e0 + e1 * e1 + e2 * e2;
-    }
-    R d = distance<DIM, R, MESH>(P, s.x, xb, bound2, stk_n, stk_d, kWalkBlock);
+    R d;
     if (MESH) {
+      // the previous step's boundary point bounds the query (NaN when none is known)
+      R bound2 = R(INFINITY);
+      if (s.k > 0) {
+        R e0 = s.x[0] - s.xbp[0], e1 = s.x[1] - s.xbp[1], e2 = s.x[2] - s.xbp[2];
+        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (b2 < R(INFINITY)) bound2 = b2;
+      }
+      const R tau = P.mesh_tau;
+      d = distance<DIM, R, MESH>(P, s.x, xb, bound2, stk_n, stk_d, kWalkBlock, tau,
+                                 (bound2 < R(INFINITY)) ? s.xbp : nullptr, &mvis);
+      if (tau < R(1) && !(d >= eps)) {
+        // a certified radius below eps: the exact distance decides the eps-shell test and
+        // gives the closest point for g (a step or two per walk, near the boundary)
+        R e0 = s.x[0] - xb[0], e1 = s.x[1] - xb[1], e2 = s.x[2] - xb[2];
+        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+        R xe[3];
+        d = distance<DIM, R, MESH>(P, s.x, xe, (b2 < R(INFINITY)) ? b2 : R(INFINITY), stk_n, stk_d, kWalkBlock,
+                                   R(1), nullptr, &mvis);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xb[i] = xe[i];
+      }
 #pragma unroll
       for (int i = 0; i < 3; ++i) s.xbp[i] = xb[i];
+    } else {
+      d = distance<DIM, R, MESH>(P, s.x, xb);
     }
     // eps-shell (or outside, or NaN), the step cap, or (weight window) a branch lost at roulette
     const bool ends = !(d >= eps) || s.k >= max_k || (WW && s.dead);
@@ -292,11 +311,27 @@ __global__ void __launch_bounds__(kWalkBlock,
       w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
       dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
     }
+    // DRIFT: the ball's own bound max(sigma_bar, 10 B / d) with B the problem's drift bound
+    // (any positive bound per ball keeps the ball's identity; this one keeps the drift
+    // weight of small balls near the boundary bounded)
+    if (DRIFT && P.drift_bound > R(0)) {
+      const R sb_ball = (R(10) * P.drift_bound) / dd;
+      if (sb_ball > R(L.sigma_bar)) {
+        s_root = w_sqrt(sb_ball);
+        inv_sb = R(1) / sb_ball;
+      }
+    }
     R a = s_root * dd;
     R q = green_q<DIM, R>(a);
     R Gn = dd * dd * q;        // |G| on the ball of radius d
     R PB = a * a * q;          // sigma_bar |G|, probability of the volume term
-    R rho = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr);
+    // DRIFT (every ball, G/|G| weight 0.97: the weight ratios multiply along the walk) and
+    // GRAD (the first ball only, weight 1/2) draw the mixture sample whose weight mixw
+    // bounds the |G'/G| and grad G / G factors; the others draw from G/|G|
+    R mixw = R(1);
+    const float* tab = (sizeof(R) == 4) ? L.radial_tab : nullptr;
+    R rho = (DRIFT || (GRAD && s.k == 0)) ? mix_sample_radius<DIM, R>(a, ur, tab, DRIFT ? R(0.97) : R(0.5), &mixw)
+                                          : sample_radius<DIM, R>(a, ur, nullptr, tab);
     R r = rho * dd;
     // coefficient point: y for a step; the walk's own point when it ends (gamma(x_n))
     R y[3];
@@ -403,11 +438,11 @@ __global__ void __launch_bounds__(kWalkBlock,
       continue;
     }
 
-    s.acc += s.W * Gn * fpy;   // source term, every step
+    s.acc += s.W * Gn * fpy * mixw;   // source term, every step
     if (GRAD && s.k == 0) {    // first ball: gradient weights (W = 1 here)
       R gGR, gPR;
       grad_ratios<DIM, R>(a, rho, &gGR, &gPR);
-      const R inv_d = R(1) / dd, S0 = Gn * fpy;
+      const R inv_d = R(1) / dd, S0 = Gn * fpy * mixw;
       const bool nul = mu <= PB;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(kWalkBlock,
         for (int i = 0; i < DIM; ++i) db += dy[i] * bvec[i];
         wn += green_dlog_r<DIM, R>(a, rho) / dd * db * inv_sb;
       }
-      s.W *= wn;
+      s.W *= wn * mixw;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) s.x[i] = y[i];
       if (WW) {
@@ -490,6 +525,11 @@ __global__ void __launch_bounds__(kWalkBlock,
     st_capped += __shfl_down_sync(kFull, st_capped, off);
     st_nonfinite += __shfl_down_sync(kFull, st_nonfinite, off);
     st_outside += __shfl_down_sync(kFull, st_outside, off);
+    if (MESH) {
+      mvis.nodes += __shfl_down_sync(kFull, mvis.nodes, off);
+      mvis.tris += __shfl_down_sync(kFull, mvis.tris, off);
+      mvis.exhausted += __shfl_down_sync(kFull, mvis.exhausted, off);
+    }
   }
   if (lane == 0) {
     atomicAdd(&L.stats[ST_STEPS], st_steps);
@@ -497,6 +537,11 @@ __global__ void __launch_bounds__(kWalkBlock,
     if (st_capped) atomicAdd(&L.stats[ST_CAPPED], (unsigned long long)st_capped);
     if (st_nonfinite) atomicAdd(&L.stats[ST_NONFINITE], (unsigned long long)st_nonfinite);
     if (st_outside) atomicAdd(&L.stats[ST_OUTSIDE], (unsigned long long)st_outside);
+    if (MESH) {
+      atomicAdd(&L.stats[ST_MESH_NODES], mvis.nodes);
+      atomicAdd(&L.stats[ST_MESH_TRIS], mvis.tris);
+      if (mvis.exhausted) atomicAdd(&L.stats[ST_EXHAUSTED], (unsigned long long)mvis.exhausted);
+    }
   }
 }
 

@@ -5,7 +5,8 @@
 * FP32: per-point and per-component agreement with the oracle within 4 combined
   standard errors, and with the exact gradient of the manufactured solution on
   sampled points of the full 64^3 grid at 1024 walks per point.
-* The value estimate of wos_solve_grad matches wos_solve's (same walks).
+* The value estimate of wos_solve_grad keeps wos_solve's expectation (its first ball draws
+  the mixture sample that bounds the gradient weight).
 * Edge cases: a point in the epsilon shell has a NaN gradient; weight windows are
   rejected; an empty call is a no-op.
 """
@@ -103,16 +104,14 @@ def test_fp32_gradient_full_grid_sampled_exact(ctx, orc):
     assert ok, (nout, mz)
     s = [int(x) for x in stats.cpu().tolist()]
     assert s[1] == 64 ** 3 * 1024 and s[2] == 0 and s[3] == 0
-    # the same walks' value estimate as wos_solve.  The two kernels are compiled differently
-    # (registers, contraction), so FP32 rounding can flip a rare walk's shell test or
-    # null-event comparison; such a point differs by about one walk's share, well inside
-    # its standard error, and every other point agrees to rounding.
+    # the value estimate keeps wos_solve's expectation: the first ball's mixture sample (same
+    # randoms, a different radius for half of them) makes the two estimates correlated but
+    # not equal, so they are compared as independent estimates (a conservative rule)
     acc2, _ = ctx.solve(prob, dev(pts), 1024, 1e-4, sb, seed=0)
     m1, _, se1 = (t.cpu().numpy() for t in ctx.finalize(acc))
-    m2 = ctx.finalize(acc2)[0].cpu().numpy()
-    close = np.isclose(m1, m2, rtol=1e-4, atol=1e-5)
-    zdiff = np.abs(m1 - m2) / se1
-    assert close.mean() >= 0.99 and zdiff.max() <= 4.0, (close.mean(), zdiff.max())
+    m2, _, se2 = (t.cpu().numpy() for t in ctx.finalize(acc2))
+    ok, nout, mz = four_se_rule(combined_z(m1, se1, m2, se2))
+    assert ok, (nout, mz)
 
 
 def test_gradient_edge_cases(ctx, orc, wos):

@@ -359,3 +359,49 @@ def test_mesh_distance_grid_fp32_exact_solution(orc, ctx):
         assert ok, (grid, nout, mz)
         res[grid] = st[0] / st[1]
     assert res[64] < 1.2 * res[0]
+
+
+@pytest.mark.parametrize("tol", [0.1, 0.25])
+def test_mesh_tolerance_walk_matches_the_exact_walk(orc, ctx, tol):
+    """Distance queries that stop at a certified radius (1 - tol) d <= r <= d: FP32 GPU walks on
+    the 327,680-triangle noise workload against the oracle's exact-radius walks (4 combined
+    standard errors; any ball inside the domain keeps the estimator unbiased), and against
+    the manufactured solution on the same mesh; the query counters are reported and no
+    search is exhausted."""
+    desc = W.mesh_noise_problem(level=7, tol=tol)
+    prob = ctx.problem(desc)
+    exact_desc = W.mesh_noise_problem(level=7)
+    sb = orc.sigma_bar(exact_desc, 48)[0]
+    pts = W.mesh_interior_points(12, seed=18)
+    m, se, st, _ = _gpu_solve(ctx, prob, pts, 1024, 1e-4, sb, seed=13)
+    oacc, _ = orc.solve(exact_desc, pts, 512, seed=14, eps=1e-4, sigma_bar=sb)
+    om, ov, ose = orc.finalize(oacc)
+    ok, nout, mz = four_se_rule(combined_z(m, se, om, ose))
+    assert ok, (nout, mz)
+    assert st[2] == 0 and st[3] == 0 and st[8] == 0
+    assert st[6] > 0 and st[7] > 0  # nodes and triangles of the queries
+    man = W.mesh_manufactured_problem(level=7, tol=tol)
+    mp = ctx.problem(man)
+    sbm = orc.sigma_bar(W.mesh_manufactured_problem(level=7), 48)[0]
+    pts = W.mesh_interior_points(2048, seed=19)
+    m, se, st, _ = _gpu_solve(ctx, mp, pts, 1 << 14, 1e-4, sbm, seed=15)
+    exact = W.cube3d_exact(*pts.astype(np.float64))
+    ok, nout, mz = four_se_rule((m - exact) / se)
+    assert ok, (nout, mz)
+    assert st[8] == 0
+
+
+def test_mesh_tolerance_cuts_query_work(wos, orc, ctx):
+    """The same walks' distance queries open fewer BVH nodes and test far fewer triangles per
+    step with tol = 0.1 than with exact radii."""
+    pts = dev(W.mesh_interior_points(4096, seed=20))
+    per = {}
+    for tol in (0.0, 0.1):
+        desc = W.mesh_noise_problem(level=7, tol=tol)
+        prob = ctx.problem(desc)
+        acc, stats = ctx.solve(prob, pts, 16, 1e-4, 787.0, seed=21)
+        s = wos.stats_dict(stats)
+        per[tol] = (s["mesh_nodes"] / s["steps"], s["mesh_tris"] / s["steps"], s["steps"] / s["walks"])
+        assert s["exhausted"] == 0
+    assert per[0.1][0] < 0.5 * per[0.0][0] and per[0.1][1] < 0.2 * per[0.0][1], per
+    assert per[0.1][2] < 1.5 * per[0.0][2], per  # balls at least 0.9 d: a few more steps per walk

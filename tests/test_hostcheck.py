@@ -197,3 +197,43 @@ def test_green_log_derivative(hc, orc, dim, fp64):
         hc.wos_hc_green_dlog(dim, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), out.ctypes.data_as(DP))
         want = np.array([orc.green_dlog(dim, R, (a / R) ** 2, r * R) for r in rho]) * R
         assert np.allclose(out, want, rtol=tol, atol=0), (a, out, want)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("lam", [0.97, 0.5])
+def test_mixture_sample_matches_oracle(hc, orc, dim, lam):
+    """The kernels' mixture ball sample (reading R22) equals the oracle's: FP64 radius and
+    weight to rounding, FP32 within its sampler's tolerance."""
+    R, sb = 0.35, 60.0
+    a = np.sqrt(sb) * R
+    u = np.ascontiguousarray(np.concatenate([np.linspace(0.001, 0.999, 401), [1e-7, 0.5 - 1e-9, lam, 1 - 1e-7]]))
+    for fp64 in (1, 0):
+        out = np.zeros(2 * len(u))
+        hc.wos_hc_mix_radius(dim, fp64, C.c_double(a), C.c_double(lam), u.ctypes.data_as(DP), len(u),
+                             out.ctypes.data_as(DP))
+        for i, x in enumerate(u):
+            r, w = orc.mix_radius(dim, R, sb, float(x), lam)
+            if fp64:
+                # the radius to rounding (in CDF terms where F is flat near rho = 1)
+                r64 = out[2 * i] * R
+                if x < lam:
+                    assert abs(orc.green_cdf(dim, R, sb, r64) - x / lam) <= 1e-13
+                    assert r64 == pytest.approx(r, rel=1e-7)
+                else:
+                    assert r64 == pytest.approx(r, rel=1e-13, abs=1e-15)
+                # the weight at the radius drawn (the density vanishes like 1 - rho at the sphere)
+                f = orc.green_pdf(dim, R, sb, r64) * R
+                assert out[2 * i + 1] == pytest.approx(f / (lam * f + 1 - lam), rel=1e-8, abs=1e-13)
+            else:
+                # FP32: the radius within the sampler's CDF tolerance, the weight at that radius
+                r32 = out[2 * i] * R
+                if np.float32(x) < np.float32(lam):  # the branch as float32 compares it
+                    assert abs(orc.green_cdf(dim, R, sb, r32) - float(np.float32(x)) / lam) <= 2e-6
+                else:
+                    # the uniform part in float32 arithmetic (u - lam cancels bits when lam ~ 1;
+                    # the weight is taken at the radius actually drawn)
+                    f32 = np.float32
+                    want = (f32(x) - f32(lam)) / (f32(1) - f32(lam))
+                    assert out[2 * i] == pytest.approx(float(want), rel=1e-6, abs=1e-7)
+                f = orc.green_pdf(dim, R, sb, r32) * R
+                assert out[2 * i + 1] == pytest.approx(f / (lam * f + 1 - lam), rel=1e-4, abs=1e-5)

@@ -82,3 +82,100 @@ def test_extra_drift_sigma_bar_invariance(orc):
     m2, _, se2 = orc.finalize(b)
     ok, nout, mz = four_se_rule(combined_z(m1, se1, m2, se2))
     assert ok
+
+
+def _p1_moment(dim, R, sb, k):
+    """E[r^k] under y ~ G/|G| on the centred ball, by scipy quadrature of the printed G."""
+    from scipy import integrate, special
+    s = math.sqrt(sb)
+    if dim == 3:
+        def G(r):
+            return math.sinh(s * (R - r)) / (4 * math.pi * r * math.sinh(s * R)) if sb > 0 else \
+                (1 / r - 1 / R) / (4 * math.pi)
+        w = lambda r: 4 * math.pi * r * r * G(r)
+    else:
+        def G(r):
+            return (special.k0(s * r) - special.k0(s * R) / special.i0(s * R) * special.i0(s * r)) / (2 * math.pi)
+        w = lambda r: 2 * math.pi * r * G(r)
+    num = integrate.quad(lambda r: r ** k * w(r), 0, R, limit=200)[0]
+    den = integrate.quad(w, 0, R, limit=200)[0]
+    return num / den
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("lam", [0.97, 0.5])
+@pytest.mark.parametrize("R,sb", [(0.3, 1.0), (0.1, 1000.0), (0.5, 50.0)])
+def test_mixture_sample_keeps_expectations(orc, dim, lam, R, sb):
+    """Reading R22: over the radius uniform u, E[mixw] = 1 and E[mixw r^k] = E_{G/|G|}[r^k]
+    (the density ratio undoes the mixture), by midpoint quadrature in u against scipy
+    quadrature of the printed G."""
+    n = 40000
+    u = (np.arange(n) + 0.5) / n
+    rw = np.array([orc.mix_radius(dim, R, sb, x, lam) for x in u])
+    r, w = rw[:, 0], rw[:, 1]
+    assert w.mean() == pytest.approx(1.0, abs=2e-5)
+    for k in (1, 2):
+        assert (w * r ** k).mean() == pytest.approx(_p1_moment(dim, R, sb, k), rel=1e-4)
+    # the part u >= lam is a uniform radius
+    j = np.searchsorted(u, lam)
+    assert np.allclose(r[j:], R * (u[j:] - lam) / (1 - lam), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixture_bounds_the_log_derivative_factor(orc, dim):
+    """Reading R22: mixw |G'/G| R stays bounded over the whole radius range (both ends
+    included), while |G'/G| R under the plain sample G/|G| is unbounded (it grows without
+    limit as u -> 0 and u -> 1)."""
+    R, sb = 0.4, 30.0
+    u = np.concatenate([np.logspace(-12, -2, 60), np.linspace(0.01, 0.99, 99), 1 - np.logspace(-2, -12, 60)])
+    for lam in (0.97, 0.5):
+        worst = max(orc.mix_radius(dim, R, sb, x, lam)[1] * orc.green_dlog(dim, R, sb,
+                                                                           orc.mix_radius(dim, R, sb, x, lam)[0]) * R
+                    for x in u)
+        assert worst < 60.0 / (1.0 - lam), (lam, worst)
+    plain = max(orc.green_dlog(dim, R, sb, orc.green_inv(dim, R, sb, x)) * R for x in u)
+    assert plain > 1e4
+
+
+def test_per_ball_bound_keeps_the_mean(orc):
+    """Reading R23: the drift bound B only changes each ball's delta-tracking bound
+    (max(sigma_bar, 10 B / R)); the estimate's expectation does not move (B = 0, the exact
+    bound 1.5, and 6)."""
+    base = W.cube3d_literal_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 16, 8)]
+    sb = orc.sigma_bar(base, 64)[0]
+    res = []
+    for j, B in enumerate((0.0, 1.5, 6.0)):
+        p = dict(base)
+        p["drift_bound"] = B
+        acc, _ = orc.solve(p, pts, 2048, seed=30 + j, eps=1e-4, sigma_bar=sb)
+        res.append(orc.finalize(acc))
+    for k in (1, 2):
+        ok, nout, mz = four_se_rule(combined_z(res[0][0], res[0][2], res[k][0], res[k][2]))
+        assert ok, (k, nout, mz)
+
+
+def _spread_ratio(u):
+    """Per point: sample standard deviation of one walk's estimate over all walks divided by
+    the one over the first 1024 (SE * sqrt(N) at N = 2^14 against N = 2^10)."""
+    return np.array([np.std(x) / np.std(x[:1024]) for x in u])
+
+
+@pytest.mark.parametrize("which", ["plain", "extra_drift", "gradient"])
+def test_walk_spread_is_constant_in_n(orc, which):
+    """SE * sqrt(N) constant over N = 2^10 .. 2^14 (a finite variance): the plain walk on the
+    3D workload, the extra-drift walk on its literal drift (readings R22, R23), and the
+    gradient walk's components (reading R22 on the first ball)."""
+    n = 1 << 14
+    if which == "gradient":
+        prob = W.cube3d_problem()
+        pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 8, 51)]
+        _, g, _ = orc.walks_grad(prob, pts, n, seed=52, eps=1e-4, sigma_bar=orc.sigma_bar(prob, 64)[0])
+        r = _spread_ratio(g.reshape(-1, n))
+        assert 0.85 < np.median(r) < 1.15, r
+        return
+    prob = W.cube3d_problem() if which == "plain" else W.cube3d_literal_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 12, 53)]
+    u, _ = orc.walks(prob, pts, n, seed=54, eps=1e-4, sigma_bar=orc.sigma_bar(prob, 64)[0])
+    r = _spread_ratio(u)
+    assert 0.85 < np.median(r) < 1.15 and r.max() < 1.5, r

@@ -110,11 +110,13 @@ def csg(lo, hi, *nodes):
     return {"kind": "csg", "p": p, "nodes": out}
 
 
-def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None, omega=None):
-    """omega: an extra drift vector field (a list of dim fields), added to alpha grad(phi)."""
+def problem(dim, domain, alpha, sigma, f, g, phi=None, um=None, omega=None, drift_bound=0.0):
+    """omega: an extra drift vector field (a list of dim fields), added to alpha grad(phi);
+    drift_bound: 0 or an upper bound of |omega / alpha| over the domain."""
     om = list(omega) if omega is not None else []
     om += [zero()] * (3 - len(om))
     return {
+        "drift_bound": float(drift_bound),
         "dim": int(dim),
         "domain": domain,
         "alpha": alpha,
@@ -184,7 +186,9 @@ def cube3d_literal_problem():
     sigma = sst(term(1.0), term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)))
     omega = [sst(term(1.0, None, (SIN, 2 * PI, 0.0))), sst(term(1.0, None, None, (COS, 2 * PI, 0.0))),
              const(0.5)]
-    return problem(3, box([0, 0, 0], [1, 1, 1]), alpha, sigma, manufactured(), u, um=u, omega=omega)
+    # |omega| <= (1 + 1 + 0.25)^(1/2) = 1.5 and alpha >= 1 on the cube: |omega / alpha| <= 1.5
+    return problem(3, box([0, 0, 0], [1, 1, 1]), alpha, sigma, manufactured(), u, um=u, omega=omega,
+                   drift_bound=1.5)
 
 
 def cube3d_exact(x, y, z):
@@ -422,12 +426,14 @@ def displaced_icosphere(level=7, amplitude=0.1, seed=3):
     return (v * r[:, None]).astype(np.float32), f.astype(np.int32)
 
 
-def mesh_domain(verts, tris, grid_res=0):
-    """Closed triangle mesh; grid_res > 0 adds a grid_res^3 distance grid (conservative radii)."""
-    return {"kind": "mesh", "p": [0.0] * 16, "verts": verts, "tris": tris, "grid_res": int(grid_res)}
+def mesh_domain(verts, tris, grid_res=0, tol=0.0):
+    """Closed triangle mesh; grid_res > 0 adds a grid_res^3 distance grid (conservative radii);
+    tol > 0 lets distance queries stop at a certified radius >= (1 - tol) x the distance."""
+    return {"kind": "mesh", "p": [0.0] * 16, "verts": verts, "tris": tris, "grid_res": int(grid_res),
+            "tol": float(tol)}
 
 
-def mesh_noise_problem(level=7, grid_res=128, seed=3, dist_grid=0):
+def mesh_noise_problem(level=7, grid_res=128, seed=3, dist_grid=0, tol=0.0):
     """Displaced icosphere boundary; alpha in [0.5, 2] (cubic B-spline), sigma in [0, 20] and
     f in [-1, 1] (multilinear) from seeded 128^3 value-noise grids over the mesh box plus 5%;
     g = x y + z."""
@@ -440,7 +446,7 @@ def mesh_noise_problem(level=7, grid_res=128, seed=3, dist_grid=0):
     s = value_noise_grid(3, grid_res, 0.0, 20.0, seed + 2, cell=8)
     f = value_noise_grid(3, grid_res, -1.0, 1.0, seed + 3, cell=8)
     g = sst(term(1.0, (LIN, 1.0, 0.0), (LIN, 1.0, 0.0)), term(1.0, None, None, (LIN, 1.0, 0.0)))
-    return problem(3, mesh_domain(verts, tris, dist_grid), grid_field("grid_bspline", a, lo, hi),
+    return problem(3, mesh_domain(verts, tris, dist_grid, tol), grid_field("grid_bspline", a, lo, hi),
                    grid_field("grid_linear", s, lo, hi), grid_field("grid_linear", f, lo, hi), g)
 
 
@@ -450,12 +456,12 @@ def mesh_interior_points(n, seed, radius=0.88):
     return uniform_in_ball(3, n, [0.0, 0.0, 0.0], radius, seed)
 
 
-def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3, dist_grid=0):
+def mesh_manufactured_problem(level=5, amplitude=0.1, seed=3, dist_grid=0, tol=0.0):
     """The 3D manufactured problem (u, alpha, sigma, drift of the cube workload) on the
     displaced-icosphere domain: u is exact on any domain, so the mesh walk has an exact answer."""
     verts, tris = displaced_icosphere(level, amplitude, seed)
     p = cube3d_problem()
-    p["domain"] = mesh_domain(verts, tris, dist_grid)
+    p["domain"] = mesh_domain(verts, tris, dist_grid, tol)
     return p
 
 
