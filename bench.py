@@ -325,6 +325,14 @@ def run_ours(args):
     exact = W.cube3d_exact(*pts_np.astype(np.float64))
     m_np = m.cpu().numpy()
     rms = float(np.linalg.norm(m_np - exact) / np.linalg.norm(exact))
+    # the ranks walked disjoint walk ids of the same points: their accumulators merge into
+    # one estimate with world x WALKS walks per point (one all-reduce of sum, sumsq, count)
+    rms_merged = rms
+    if dist is not None:
+        from paper_2201_13240_gb300 import multi
+        multi.merge_accumulators(acc)
+        mm = ctx.finalize(acc)[0].cpu().numpy()
+        rms_merged = float(np.linalg.norm(mm - exact) / np.linalg.norm(exact))
     se_np = se.cpu().numpy()
     # walks per point for normalised RMS 1e-2 (noise part scales as 1/sqrt(N))
     noise = float(np.sqrt(np.mean(se_np ** 2)) / np.sqrt(np.mean(exact ** 2)))
@@ -406,6 +414,7 @@ def run_ours(args):
             "points_per_s": world * npts / (ms_per_step * 1e-3),
             "walks_per_s": world * npts * WALKS / (ms_per_step * 1e-3),
             "steps_per_walk": steps_per_walk, "normalised_rms_at_1024_walks": rms,
+            "normalised_rms_merged_over_ranks": rms_merged,
             "noise_model_walks_for_rms_1e-2": walks_for_1e2,
             "points_per_s_at_rms_1e-2": rms_run.get("points_per_s"), "rms_1e-2_run": rms_run,
             "capped_walks": st["capped"], "nonfinite_walks": st["nonfinite"],
@@ -512,12 +521,14 @@ def run_other(args):
         m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
         exact = W.cube3d_exact(*pts_np.astype(np.float64))
         rms = float(np.linalg.norm(m - exact) / np.linalg.norm(exact))
-        # the drift weight's second moment diverges logarithmically (|G'/G| ~ 1/r): rare walks
-        # carry very large weights, so the RMS over all points is dominated by a few points
+        # a heavy tail of the walk's weights shows as a few points with large errors: the RMS
+        # over all points against the RMS without the worst 0.1% measures it (the mixture ball
+        # sample and the per-ball bounds of the drift walk bound its weights)
         err = np.abs(m - exact)
         keep = err <= np.quantile(err, 0.999)
-        extra["normalised_rms_without_worst_0.1pct_points"] = float(np.linalg.norm((m - exact)[keep]) /
-                                                                   np.linalg.norm(exact[keep]))
+        trimmed = float(np.linalg.norm((m - exact)[keep]) / np.linalg.norm(exact[keep]))
+        extra["normalised_rms_without_worst_0.1pct_points"] = trimmed
+        extra["rms_all_over_trimmed"] = rms / trimmed
         extra["median_abs_z"] = float(np.median(err / se))
         noise = float(np.sqrt(np.median(se ** 2)) / np.sqrt(np.mean(exact ** 2)))
         walks_1e2 = int(math.ceil(WALKS * (noise / 1e-2) ** 2))

@@ -1074,14 +1074,24 @@ WOS_HD R radial_pdf(R a, R rho) {
 // rest a uniform radius (rho = (u - lam) / (1 - lam)).  The source term and the null
 // weight are then multiplied by *mixw = f / (lam f + 1 - lam), the density ratio of G/|G|
 // to the mixture, which keeps their expectations and bounds the weight at both ends.
+// The radius of a mixture lane from the inverse-CDF radius rho_g (drawn with u / lam when
+// u < lam, the part of G/|G|) and the uniform u; sets *mixw.  FP32 uniforms are rounded
+// to 24 bits, so u can equal lam and u / lam can round to 1: rho is kept inside the
+// uniform's resolution, where the weight and the |G'/G| factor are finite (at rho = 0 or
+// 1 the weight vanishes and the factor is infinite; their product has a finite limit).
 template <int DIM, typename R>
-WOS_HD R mix_sample_radius(R a, R u, const float* tab, R lam, R* mixw) {
-  R rho;
-  if (u < lam) rho = sample_radius<DIM, R>(a, u / lam, nullptr, tab);
-  else rho = (u - lam) / (R(1) - lam);
+WOS_HD R mix_radius_weight(R a, R u, R rho_g, R lam, R* mixw) {
+  R rho = (u < lam) ? rho_g : (u - lam) / (R(1) - lam);
+  if (sizeof(R) == 4) rho = w_fmin(w_fmax(rho, R(1e-7)), R(1) - R(6e-8));
   const R f = radial_pdf<DIM, R>(a, rho);
   *mixw = f / (lam * f + (R(1) - lam));
   return rho;
+}
+
+template <int DIM, typename R>
+WOS_HD R mix_sample_radius(R a, R u, const float* tab, R lam, R* mixw) {
+  const R rho_g = sample_radius<DIM, R>(a, (u < lam) ? u / lam : R(0.5), nullptr, tab);
+  return mix_radius_weight<DIM, R>(a, u, rho_g, lam, mixw);
 }
 
 }  // namespace wos

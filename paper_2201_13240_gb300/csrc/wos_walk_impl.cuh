@@ -328,10 +328,14 @@ __global__ void __launch_bounds__(kWalkBlock,
     // DRIFT (every ball, G/|G| weight 0.97: the weight ratios multiply along the walk) and
     // GRAD (the first ball only, weight 1/2) draw the mixture sample whose weight mixw
     // bounds the |G'/G| and grad G / G factors; the others draw from G/|G|
+    // (one radius solve for every lane, its argument chosen per lane: a mixture lane whose
+    // uniform falls in the uniform-radius part solves a dummy and discards it)
     R mixw = R(1);
     const float* tab = (sizeof(R) == 4) ? L.radial_tab : nullptr;
-    R rho = (DRIFT || (GRAD && s.k == 0)) ? mix_sample_radius<DIM, R>(a, ur, tab, DRIFT ? R(0.97) : R(0.5), &mixw)
-                                          : sample_radius<DIM, R>(a, ur, nullptr, tab);
+    const bool mix = DRIFT || (GRAD && s.k == 0);
+    const R lam = DRIFT ? R(0.97) : R(0.5);
+    R rho = sample_radius<DIM, R>(a, mix ? ((ur < lam) ? ur / lam : R(0.5)) : ur, nullptr, tab);
+    if (mix) rho = mix_radius_weight<DIM, R>(a, ur, rho, lam, &mixw);
     R r = rho * dd;
     // coefficient point: y for a step; the walk's own point when it ends (gamma(x_n))
     R y[3];

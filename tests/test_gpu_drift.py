@@ -78,6 +78,10 @@ def test_drift_full_cube_literal_rms(orc, ctx):
     z = (m[idx] - W.cube3d_exact(*pts[:, idx].astype(np.float64))) / se[idx]
     ok, nout, mz = four_se_rule(z)
     assert ok, (nout, mz)
+    # FP32 uniforms can equal the mixture's split point: every walk must stay finite
+    s = [int(x) for x in stats.cpu().tolist()]
+    assert s[1] == 64 ** 3 * 1024 and s[2] == 0 and s[3] == 0, s
+    assert np.all(np.isfinite(m))
 
 
 def test_drift_refused_where_the_term_is_missing(orc, ctx, wos):

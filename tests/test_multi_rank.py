@@ -1,5 +1,7 @@
 """World-size-2 CPU (gloo) checks of the multi-rank host logic: disjoint shards that
-cover every walk once, and the accumulator merge equals the single-process sums."""
+cover every walk once, the accumulator merge equals the single-process sums, and walks
+sharded over ranks -- by disjoint walk-id ranges or by point blocks -- merge into the
+estimate of one process running every walk (the oracle walks on each rank)."""
 import os
 import socket
 
@@ -61,3 +63,56 @@ def test_merge_two_ranks_gloo(tmp_path):
     for r in range(world):
         got = np.load(tmp_path / f"out{r}.npy")
         assert np.allclose(got, want, rtol=0, atol=1e-12)
+
+
+def _walk_worker(rank, world, port, mode, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    import workloads as W
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 24, 61)]
+    npts, walks, seed = pts.shape[1], 96, 17
+    sb = oracle.sigma_bar(desc, 64)[0]
+    acc = (torch.zeros(npts, dtype=torch.float64), torch.zeros(npts, dtype=torch.float64),
+           torch.zeros(npts, dtype=torch.int64))
+    if mode == "walks":
+        off, cnt = multi.walk_range(rank, world, walks)
+        if cnt > 0:
+            o, _ = oracle.solve(desc, pts, cnt, seed=seed, eps=1e-4, sigma_bar=sb, walk_offset=off)
+            for t, v in zip(acc, o):
+                t += torch.from_numpy(np.asarray(v))
+    else:
+        a, b = multi.point_range(rank, world, npts)
+        # the block's points keep their global indices (the Philox counter's point word):
+        # per-point walk counts, zero outside the block
+        w = np.zeros(npts, dtype=np.int32)
+        w[a:b] = walks
+        o, _ = oracle.solve(desc, pts, w, seed=seed, eps=1e-4, sigma_bar=sb)
+        for t, v in zip(acc, o):
+            t += torch.from_numpy(np.asarray(v))
+    multi.merge_accumulators(acc)
+    if rank == 0:
+        np.save(os.path.join(out_dir, f"merged_{mode}.npy"), np.stack([t.numpy().astype(np.float64) for t in acc]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["walks", "points"])
+def test_sharded_walks_merge_to_one_process(tmp_path, orc, mode):
+    """Two ranks walk disjoint walk-id ranges of every point (or disjoint point blocks);
+    after the all-reduce the counts equal one process's exactly and the sums agree to
+    summation-order rounding."""
+    import workloads as W
+    world = 2
+    mp.start_processes(_walk_worker, args=(world, _free_port(), mode, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    got = np.load(tmp_path / f"merged_{mode}.npy")
+    desc = W.cube3d_problem()
+    pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 24, 61)]
+    sb = orc.sigma_bar(desc, 64)[0]
+    ref, _ = orc.solve(desc, pts, 96, seed=17, eps=1e-4, sigma_bar=sb)
+    assert np.array_equal(got[2], np.asarray(ref[2], dtype=np.float64))
+    assert np.allclose(got[0], ref[0], rtol=1e-12, atol=1e-12)
+    assert np.allclose(got[1], ref[1], rtol=1e-12, atol=1e-12)
