@@ -68,6 +68,42 @@ def measure_unit_peaks(ctx):
                    "loads of a 32 MiB buffer; 5 launches after one warm-up, CUDA events"}
 
 
+def mesh_l2_record(ctx, args, l2_peak):
+    """L2 roofline of the mesh walk (the displaced icosphere with 128^3 noise grids, distance
+    queries with tolerance 0.1): algorithmic L2 bytes per step from the kernel's node and
+    triangle counters plus the field taps, over the kernel time, against the measured L2
+    read rate.  16,384 interior points x 64 walks, three timed solves."""
+    import torch
+    desc = W.mesh_noise_problem(level=7, tol=0.1)
+    prob = make_problem(ctx, desc, args)
+    sb = ctx.sigma_bar(prob, 48)[0]
+    pts = torch.from_numpy(W.mesh_interior_points(16384, seed=0)).cuda()
+    ctx.solve(prob, pts, 64, 1e-4, sb, seed=0)
+    torch.cuda.synchronize()
+    ms, st = [], None
+    for i in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, st = ctx.solve(prob, pts, 64, 1e-4, sb, seed=1 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    import paper_2201_13240_gb300 as wos
+    sd = wos.stats_dict(st)
+    t = sum(ms) / len(ms)
+    nodes, tris = sd["mesh_nodes"] / sd["steps"], sd["mesh_tris"] / sd["steps"]
+    bps = 128.0 * nodes + 48.0 * tris + 4.0 * (64 + 8 + 8)
+    rate = bps * sd["steps"] / (t * 1e-3)
+    prob.close()
+    return {"workload": "displaced icosphere (327,680 triangles), 128^3 noise grids, 16384 interior points x 64 "
+                        "walks, eps 1e-4, distance-query tolerance 0.1",
+            "steps_per_s": sd["steps"] / (t * 1e-3), "steps_per_walk": sd["steps"] / sd["walks"],
+            "nodes_per_step": nodes, "triangles_per_step": tris, "bytes_per_step": bps,
+            "gb_per_s": rate / 1e9, "peak_gb_per_s": l2_peak / 1e9, "frac": rate / l2_peak,
+            "basis": "BVH nodes x 128 B + triangles x 48 B (kernel counters) + alpha B-spline 64 and sigma, f "
+                     "multilinear 8 taps x 4 B per step; peak: wos_measure_peak L2 read (32 MiB buffer)"}
+
+
 def walks_for_rms(ctx, prob, pts, exact, sb, n_guess, stream, seed):
     """The smallest tried walks-per-point whose normalised RMS against the exact solution is at
     most RMS_TARGET: geometric steps of 10% up from 0.8 x the noise-model guess; each try is one
@@ -389,6 +425,7 @@ def run_ours(args):
 
     # points/s at normalised RMS 1e-2, measured: the smallest tried walk count that reaches it
     rms_run = walks_for_rms(ctx, prob, pts, exact, sb, walks_for_1e2, stream, SEED + 1000) if rank == 0 else None
+    mesh_l2 = mesh_l2_record(ctx, args, peaks["l2_read_bytes_per_s"]) if rank == 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -418,7 +455,8 @@ def run_ours(args):
             "noise_model_walks_for_rms_1e-2": walks_for_1e2,
             "points_per_s_at_rms_1e-2": rms_run.get("points_per_s"), "rms_1e-2_run": rms_run,
             "capped_walks": st["capped"], "nonfinite_walks": st["nonfinite"],
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "mesh_l2": mesh_l2,
+            "cpu_baseline": cpu,
             "clocks": clocks}
     print(json.dumps(line))
     if dist is not None:
@@ -581,7 +619,10 @@ def run_other(args):
         walks = args.walks if args.walks != DEFAULT_WALKS else 512
         sb = None
         runs, head_ms_st = {}, {}
-        for tol in (args.mesh_tol, 0.0) if args.mesh_tol > 0 else (0.0,):
+        tols = (args.mesh_tol, 0.0) if args.mesh_tol > 0 else (0.0,)
+        if args.no_mesh_exact and args.mesh_tol > 0:
+            tols = (args.mesh_tol,)
+        for tol in tols:
             desc = W.mesh_noise_problem(level=7, tol=tol)
             t0 = time.perf_counter()
             prob = ctx.problem(desc)
@@ -611,7 +652,7 @@ def run_other(args):
         extra["mesh_tol"] = args.mesh_tol
         for tol, r in runs.items():
             extra[f"tol_{tol}"] = {k: v for k, v in r.items() if not k.startswith("_")}
-        if args.mesh_tol > 0:
+        if args.mesh_tol > 0 and 0.0 in runs:
             a, b = runs[args.mesh_tol], runs[0.0]
             extra["speedup_over_exact_radii"] = b["ms"] / a["ms"]
             extra["mean_abs_z_vs_exact_radii"] = float(np.mean(np.abs(a["_mean"] - b["_mean"]) /
@@ -638,6 +679,13 @@ def run_other(args):
         sbs = [ctx.sigma_bar(h, 64)[0] for h in hp]
         batch = ctx.batch(hp, offs, sbs)
         extra["setup_s"] = time.perf_counter() - t0
+        if args.kernel == "specialised":
+            # the batched kernel with the fields every problem shares compiled in (before the
+            # autotuner, whose trials then run it)
+            t0 = time.perf_counter()
+            batch.specialize(("fp32",))
+            JIT["compile_s"] += time.perf_counter() - t0
+            extra["shared_fields_mask"] = batch.specialized()[1]
         pts = torch.from_numpy(pts_np).cuda()
         wt = torch.from_numpy(walks_np).cuda()
         acc = ctx.new_accum(pts.shape[1])
@@ -666,6 +714,12 @@ def run_other(args):
             return acc, stt
         (acc, st), ms = timed(run, args.steps)
         npts = pts.shape[1]
+        if args.kernel == "specialised":
+            # the same launch through the generic (field-interpreting) batched kernel
+            gb = ctx.batch(hp, offs, sbs)
+            gb.set_schedule(**batch.schedule())
+            (_, gst), gms = timed(lambda i: ctx.solve_batch(gb, pts, wt, 1e-3, seed=0), args.steps)
+            extra["generic_kernel"] = {"ms": gms, "steps_per_s": wos.stats_dict(gst)["steps"] / (gms * 1e-3)}
         cfg = {"workload": f"{args.problems} 2D problems (disk/annulus/rounded box, 64^2 noise grids), "
                            f"{npts} points, {int(walks_np.sum())} walks, one launch in a CUDA graph, eps 1e-3"}
     elif wl == "inverse":
@@ -673,7 +727,8 @@ def run_other(args):
         sig_t = torch.from_numpy(sig).cuda()
         desc = W.inverse_problem(sig)
         desc["sigma"] = dict(desc["sigma"], data=sig_t)
-        prob = make_problem(ctx, desc, args)
+        # the forward walk and both replay adjoints compiled for the problem's fields
+        prob = make_problem(ctx, desc, args, ("plain", "adjoint"))
         sb = ctx.sigma_bar(prob, 48)[0]
         npts = 4096
         pts = torch.from_numpy(W.inverse_sensors(npts)).cuda()
@@ -697,6 +752,14 @@ def run_other(args):
         _, ms_adj_a = timed(adj_alpha, args.steps)
         extra["adjoint_alpha_ms"] = ms_adj_a
         extra["adjoint_alpha_grads_per_s_over_forward_solves_per_s"] = ms / ms_adj_a
+        if args.kernel == "specialised":
+            # the generic (field-interpreting) adjoint kernels on the same walks, for comparison
+            gprob = ctx.problem(desc)
+            _, ms_g = timed(lambda i: (grad.zero_(), ctx.adjoint_sigma(gprob, pts, walks, gu, grad, 1e-4, sb,
+                                                                       seed=i)), args.steps)
+            _, ms_ga = timed(lambda i: (grad_a.zero_(), ctx.adjoint_alpha(gprob, pts, walks, gu, grad_a, 1e-4, sb,
+                                                                          seed=i)), args.steps)
+            extra["generic_adjoint_ms"] = {"sigma": ms_g, "alpha": ms_ga}
         extra["adjoint_ms"] = ms_adj
         extra["forward_solves_per_s"] = 1e3 / ms
         extra["adjoint_grads_per_s"] = 1e3 / ms_adj
@@ -737,6 +800,8 @@ def main():
                     help="walk kernel: compiled for the problem's fields (default) or the generic field interpreter")
     ap.add_argument("--mesh-tol", type=float, default=0.1,
                     help="mesh workload: certified-radius tolerance of the distance queries (0: exact radii only)")
+    ap.add_argument("--no-mesh-exact", action="store_true",
+                    help="mesh workload: skip the exact-radius comparison (sweeps)")
     ap.add_argument("--dist-grid", type=int, default=128,
                     help="mesh workload: also time walks with an n^3 distance grid (0: exact radii only)")
     args = ap.parse_args()

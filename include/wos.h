@@ -350,7 +350,11 @@ int wos_finalize(wos_ctx* ctx, const double* sum, const double* sumsq, const int
    Given sigma_bar, a walk's path does not depend on sigma; sigma enters only the
    null weights w = 1 - sigma'(y)/sigma_bar with d sigma'/d sigma_m = N_m(y)/alpha(y)
    (Sec. 4.1, Sec. 5.1), so each walk runs twice: once for its total, once adding
-   (total - prefix)/w * dw/dsigma_m at every null event.
+   (total - prefix)/w * dw/dsigma_m at every null event.  The two runs are two kernel
+   launches on `stream` (per 2^24 walks); the totals between them live in a
+   context-owned buffer of 4 (FP32) or 8 (FP64) bytes per walk, grown with cudaMalloc
+   when a call needs more (after a device synchronisation), so calls on one context
+   are not concurrent.
    grad_u: device double [npts]; grad_sigma: device double [sigma grid nodes], ADDED to.
    Errors: WOS_EUNSUPPORTED unless sigma is WOS_FIELD_GRID_LINEAR and f is not
    WOS_FIELD_MANUFACTURED; WOS_EINVAL as wos_solve. */
@@ -366,6 +370,7 @@ int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* prob, const float* pts, i
    sigma' = sigma/alpha + Lap gamma + |grad gamma|^2, and e^{gamma(x_n)} at the
    boundary (Sec. 4.1, App. A).  grad_alpha: device double [alpha grid nodes], ADDED
    to.  Grids of up to 8192 nodes are accumulated per CTA in shared memory first.
+   Launches and the totals buffer as wos_adjoint_sigma.
    Errors: WOS_EUNSUPPORTED unless alpha is WOS_FIELD_GRID_BSPLINE and f is not
    WOS_FIELD_MANUFACTURED; WOS_EINVAL as wos_solve. */
 int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
@@ -423,6 +428,21 @@ int wos_batch_autotune(wos_ctx* ctx, wos_batch* batch, const float* pts, const i
                        int32_t walks_uniform, const wos_params* params, int32_t trial_shift,
                        wos_schedule* best, double* best_ms, double* default_ms, void* stream);
 
+/* Batch specialisation (not in the paper): compile, with NVRTC for sm_103a, the batched walk
+   kernel with every field that all problems of the batch share (the same kind and, for
+   CONST and SST fields, the same value or terms) written out as code; grid fields read the
+   walk's own problem's grid as before, and fields that differ between problems keep the
+   field interpreter.  Both register caps of wos_schedule are compiled, so schedules and
+   the autotuner apply unchanged; later wos_solve_batch calls launch these kernels.
+   flags: WOS_SPEC_FP32 and/or WOS_SPEC_FP64 (neither = FP32), optionally WOS_SPEC_PLAIN.
+   Blocks for the compilation.  Errors: WOS_EINVAL (unknown flag), WOS_EUNSUPPORTED (no
+   libnvrtc, a compile error, or problems whose sources differ in being manufactured),
+   WOS_ECUDA.  wos_batch_specialized: WOS_SPEC_* bits of the loaded kernels and (if
+   uniform_fields is not NULL) the shared fields as bits alpha 1, Phi 2, sigma 4, f 8,
+   g 16, u_m 32. */
+int wos_batch_specialize(wos_ctx* ctx, wos_batch* batch, int32_t flags);
+int wos_batch_specialized(const wos_batch* batch, int32_t* flags_out, int32_t* uniform_fields);
+
 /* End-to-end convenience: HOST points in, HOST mean / variance / stderr out (and
    HOST stats if non-NULL).  Copies the inputs to device buffers owned by the
    context (grown as needed), runs wos_solve on fresh accumulators and
@@ -442,11 +462,12 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host,
    and loads the kernels on the problem's device.  Afterwards wos_solve,
    wos_walk_estimates, wos_solve_grad, wos_walk_grad_estimates and
    wos_solve_host on this problem launch the specialised kernel of the matching
-   precision and variant; every other variant, the next-flight walks, the
-   adjoints and batches keep the generic kernels.
+   precision and variant, and wos_adjoint_sigma, wos_adjoint_alpha and wos_adjoint
+   the specialised adjoint kernels once WOS_SPEC_ADJOINT was asked for; the
+   next-flight walks keep the generic kernels (batches: wos_batch_specialize).
    flags: WOS_SPEC_FP32 and/or WOS_SPEC_FP64 (neither = FP32), and the variants
    WOS_SPEC_PLAIN, WOS_SPEC_WINDOW (weight window), WOS_SPEC_GRAD (spatial
-   gradient) (none = PLAIN).  Calling it again adds variants; loaded kernels are
+   gradient), WOS_SPEC_ADJOINT (both replay adjoints; analytic domains) (none = PLAIN).  Calling it again adds variants; loaded kernels are
    kept until wos_problem_destroy.
    Errors: WOS_EINVAL (null handle, unknown flag); WOS_EUNSUPPORTED (libnvrtc
    not found, a compilation error -- message in wos_last_error -- or a variant
@@ -456,6 +477,7 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* prob, const float* pts_host,
 #define WOS_SPEC_PLAIN 0x10
 #define WOS_SPEC_WINDOW 0x20
 #define WOS_SPEC_GRAD 0x40
+#define WOS_SPEC_ADJOINT 0x80 /* the path-replay adjoint kernels of wos_adjoint_sigma / _alpha / wos_adjoint */
 int wos_problem_specialize(wos_ctx* ctx, wos_problem* prob, int32_t flags);
 
 /* Which specialised kernels a problem holds: OR of the WOS_SPEC_* bits of the
@@ -473,6 +495,12 @@ int wos_jit_source(const wos_problem_desc* desc, char* buf, int64_t cap, int64_t
    the reason for a failure) is written to log (cap bytes, NUL-terminated). */
 int wos_jit_compile(const wos_problem_desc* desc, int32_t flags, char* log, int64_t log_cap,
                     int64_t* cubin_bytes);
+
+/* The same two for a batch of n descriptions (host only): the generated program of
+   wos_batch_specialize, and its NVRTC compile of one precision (both register caps). */
+int wos_jit_batch_source(const wos_problem_desc* descs, int32_t n, char* buf, int64_t cap, int64_t* len);
+int wos_jit_batch_compile(const wos_problem_desc* descs, int32_t n, int32_t flags, char* log, int64_t log_cap,
+                          int64_t* cubin_bytes);
 
 /* ---- progressive slice view (Sec. 7.2) ----
    The paper's interactive path: a solve on the points of a slice plane that adds one walk

@@ -26,6 +26,7 @@ STAT_STEPS, STAT_WALKS, STAT_CAPPED, STAT_NONFINITE, STAT_OUTSIDE, STAT_INNER = 
 STAT_MESH_NODES, STAT_MESH_TRIS, STAT_EXHAUSTED = 6, 7, 8
 STATS_WORDS = 9
 WOS_SPEC_FP32, WOS_SPEC_FP64, WOS_SPEC_PLAIN, WOS_SPEC_WINDOW, WOS_SPEC_GRAD = 0x1, 0x2, 0x10, 0x20, 0x40
+WOS_SPEC_ADJOINT = 0x80
 _FIELD_KINDS = {"zero": 0, "const": 1, "sst": 2, "manufactured": 3, "grid_linear": 4, "grid_bspline": 5}
 _DOM_KINDS = {"box": 0, "ball": 1, "annulus": 2, "rounded_box": 3, "mesh": 4, "csg": 5}
 _CSG_PRIMS = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "halfspace": 4}
@@ -159,6 +160,10 @@ def load():
                                       vp, vp]
     lib.wos_adjoint.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_measure_peak.argtypes = [vp, i32, vp, i64, dp, dp, vp]
+    lib.wos_batch_specialize.argtypes = [vp, vp, i32]
+    lib.wos_batch_specialized.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.wos_jit_batch_source.argtypes = [C.POINTER(ProblemDesc), i32, C.c_char_p, i64, C.POINTER(i64)]
+    lib.wos_jit_batch_compile.argtypes = [C.POINTER(ProblemDesc), i32, i32, C.c_char_p, i64, C.POINTER(i64)]
     _lib = lib
     return lib
 
@@ -274,7 +279,8 @@ def describe(desc, device=None):
 
 
 _SPEC_PRECISION = {"fp32": WOS_SPEC_FP32, "fp64": WOS_SPEC_FP64}
-_SPEC_VARIANT = {"plain": WOS_SPEC_PLAIN, "window": WOS_SPEC_WINDOW, "grad": WOS_SPEC_GRAD}
+_SPEC_VARIANT = {"plain": WOS_SPEC_PLAIN, "window": WOS_SPEC_WINDOW, "grad": WOS_SPEC_GRAD,
+                 "adjoint": WOS_SPEC_ADJOINT}
 
 
 def spec_flags(precisions=("fp32",), variants=("plain",)):
@@ -308,6 +314,41 @@ def jit_compile(desc, precision="fp32", variants=("plain",)):
     log = C.create_string_buffer(1 << 16)
     nbytes = C.c_int64(0)
     rc = lib.wos_jit_compile(C.byref(D), spec_flags(precision, variants), log, 1 << 16, C.byref(nbytes))
+    return rc, log.value.decode(errors="replace"), nbytes.value
+
+
+def _describe_many(descs):
+    arr = (ProblemDesc * len(descs))()
+    keep = []
+    for i, d in enumerate(descs):
+        D, k, _, _ = describe(d)
+        arr[i] = D
+        keep.append(k)
+    return arr, keep
+
+
+def jit_batch_source(descs):
+    """The generated program of wos_batch_specialize for a list of problem dicts (host only)."""
+    lib = load()
+    arr, keep = _describe_many(descs)
+    n = C.c_int64(0)
+    rc = lib.wos_jit_batch_source(arr, len(descs), None, 0, C.byref(n))
+    if rc != WOS_OK:
+        buf = C.create_string_buffer(512)
+        lib.wos_jit_batch_source(arr, len(descs), buf, 512, None)
+        raise WosError(rc, buf.value.decode(errors="replace"))
+    buf = C.create_string_buffer(n.value + 1)
+    lib.wos_jit_batch_source(arr, len(descs), buf, n.value + 1, C.byref(n))
+    return buf.value.decode()
+
+
+def jit_batch_compile(descs, precision="fp32"):
+    """NVRTC compile of a batch's specialised kernels (no device): (status, log, cubin bytes)."""
+    lib = load()
+    arr, keep = _describe_many(descs)
+    log = C.create_string_buffer(1 << 16)
+    nbytes = C.c_int64(0)
+    rc = lib.wos_jit_batch_compile(arr, len(descs), spec_flags(precision), log, 1 << 16, C.byref(nbytes))
     return rc, log.value.decode(errors="replace"), nbytes.value
 
 
@@ -417,6 +458,20 @@ class Batch:
         if rc != WOS_OK:
             raise WosError(rc, "wos_batch_get_schedule")
         return sc.as_dict()
+
+    def specialize(self, precisions=("fp32",)):
+        """Compile the batched walk kernel with the fields every problem shares as code
+        (NVRTC; blocks for the compilation); later solves launch it."""
+        self.ctx._check(self.ctx.lib.wos_batch_specialize(self.ctx.handle, self.handle, spec_flags(precisions)))
+        return self
+
+    def specialized(self):
+        """(WOS_SPEC_* bits of the loaded kernels, bits of the fields all problems share)."""
+        f, u = C.c_int32(0), C.c_int32(0)
+        rc = self.ctx.lib.wos_batch_specialized(self.handle, C.byref(f), C.byref(u))
+        if rc != WOS_OK:
+            raise WosError(rc, "wos_batch_specialized")
+        return f.value, u.value
 
     def set_schedule(self, chunk=0, blocks_per_sm=0, regs_variant=0):
         sc = Schedule(int(chunk), int(blocks_per_sm), int(regs_variant), 0)

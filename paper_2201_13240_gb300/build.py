@@ -27,7 +27,7 @@ HEADERS = ["wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_nf_impl.
            "wos_internal.h", "wos_mesh.h", "wos_jit.h", "wos_capi_state.h"]
 # headers of the walk kernel, embedded in the library for the runtime-compiled (problem-
 # specialised) kernels
-JIT_HEADERS = ["wos_internal.h", "wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh"]
+JIT_HEADERS = ["wos_internal.h", "wos_math.cuh", "wos_problem.cuh", "wos_walk_impl.cuh", "wos_adjoint_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-I", BUILD_DIR]
 

@@ -36,7 +36,9 @@
 // and added to the FP64 gradient once per CTA.
 #pragma once
 
+#if !defined(__CUDACC_RTC__)
 #include <cuda_runtime.h>
+#endif
 
 #include "wos_internal.h"
 #include "wos_math.cuh"
@@ -102,41 +104,52 @@ __device__ void bspline_scatter(const DevField<R>& F, const R* y, R vN, const R*
       B2[d][a] *= F.inv_h[d] * F.inv_h[d];
     }
   }
+  // clamped control indices per axis, once: x offsets and the row / plane offsets (32-bit:
+  // grids stay far below 2^31 nodes)
+  const int t1 = (int)s1, t2 = (int)s2;
+  int o0[4], o1[4], o2[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    o0[a] = min(max(ib[0] + a, 0), F.res[0] - 1);
+    o1[a] = t1 * min(max(ib[1] + a, 0), F.res[1] - 1);
+    o2[a] = (DIM == 3) ? t2 * min(max(ib[2] + a, 0), F.res[2] - 1) : 0;
+  }
   // Rows (c1, c2) of the support are visited in an order rotated by the lane, so lanes
   // whose points share a cell (walks of one point start together) add to different
   // addresses at the same time instead of serialising on one.
-  auto sel4 = [](const R* a, int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3])); };
+  auto sel4 = [](const R* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3])); };
+  auto sel4i = [](const int* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3])); };
   const int nrows = (DIM == 3) ? 16 : 4;
   const int rot = (int)(threadIdx.x & 31);
   for (int k = 0; k < nrows; ++k) {
     const int r = (k + rot) & (nrows - 1);
     const int c1 = r & 3, c2 = (DIM == 3) ? (r >> 2) : 0;
-    const int j1 = min(max(ib[1] + c1, 0), F.res[1] - 1);
-    const int j2 = (DIM == 3) ? min(max(ib[2] + c2, 0), F.res[2] - 1) : 0;
     const R b1 = sel4(B[1], c1), d1 = sel4(B1[1], c1), e1 = sel4(B2[1], c1);
     const R b2 = (DIM == 3) ? sel4(B[2], c2) : R(1), d2 = (DIM == 3) ? sel4(B1[2], c2) : R(0);
     const R e2 = (DIM == 3) ? sel4(B2[2], c2) : R(0);
     const R b12 = b1 * b2;
-    A* row = grad + s1 * j1 + s2 * j2;
+    // the tap (c0, c1, c2) is b0 P + B1_0 Q + B2_0 T with the row's P, Q, T: the value,
+    // gradient and Laplacian weights factored along x
+    R Prow = vN * b12 + vG[1] * d1 * b2 + vL * (e1 * b2 + b1 * e2);
+    if (DIM == 3) Prow += vG[2] * b1 * d2;
+    const R Qrow = vG[0] * b12, Trow = vL * b12;
+    A* row = grad + (sel4i(o1, c1) + sel4i(o2, c2));
 #pragma unroll
     for (int c0 = 0; c0 < 4; ++c0) {
-      const int j0 = min(max(ib[0] + c0, 0), F.res[0] - 1);
-      const R b0 = B[0][c0];
-      R val = vN * b0 * b12 + vG[0] * B1[0][c0] * b12 + vG[1] * b0 * d1 * b2 +
-              vL * (B2[0][c0] * b12 + b0 * e1 * b2 + b0 * b1 * e2);
-      if (DIM == 3) val += vG[2] * b0 * b1 * d2;
-      if (val != R(0)) atomicAdd(&row[j0], A(val));
+      const R val = B[0][c0] * Prow + B1[0][c0] * Qrow + B2[0][c0] * Trow;
+      if (val != R(0)) atomicAdd(&row[o0[c0]], A(val));
     }
   }
 }
 
-// d sigma' / d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m at y
+// d sigma' / d alpha_m = cN N_m + cG . grad N_m + cL Lap N_m at y, from the fields coeffs
+// evaluated there (in the walk's precision: FP64 arithmetic is a small fraction of FP32's
+// rate here)
 template <int DIM, typename R>
-__device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, R* cN, R* cG, R* cL) {
-  // in the walk's precision (FP64 arithmetic is a small fraction of FP32's rate here)
-  FieldVal<R> A = field_eval<DIM>(P, P.alpha, y[0], y[1], y[2], true);
-  FieldVal<R> Ph = field_eval<DIM>(P, P.phi, y[0], y[1], y[2], true);
-  FieldVal<R> S = field_eval<DIM>(P, P.sigma, y[0], y[1], y[2], false);
+__device__ void alpha_sensitivity(const FieldsAt<R>& F, R* cN, R* cG, R* cL) {
+  const FieldVal<R>& A = F.A;
+  const FieldVal<R>& Ph = F.Ph;
+  const R Sv = F.S;
   const R ia = R(1) / A.v;
   const R ga[3] = {A.gx, A.gy, A.gz}, gp[3] = {Ph.gx, Ph.gy, Ph.gz};
   R na2 = R(0), gg_ga = R(0), gg[3] = {R(0), R(0), R(0)};
@@ -147,14 +160,27 @@ __device__ void alpha_sensitivity(const DevProblem<R>& P, const R* y, R* cN, R* 
     gg_ga += gg[d] * ga[d];
   }
   const R ia2 = ia * ia;
-  *cN = -S.v * ia2 - R(0.5) * A.lap * ia2 + na2 * ia2 * ia - gg_ga * ia2;
+  *cN = -Sv * ia2 - R(0.5) * A.lap * ia2 + na2 * ia2 * ia - gg_ga * ia2;
 #pragma unroll
   for (int d = 0; d < 3; ++d) cG[d] = (d < DIM) ? gg[d] * ia - ga[d] * ia2 : R(0);
   *cL = R(0.5) * ia;
 }
 
-template <int DIM, typename R, bool ALPHA>
-__global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
+// Compiled at run time for one problem (WOS_JIT_FIELDS, wos_problem_specialize with the
+// adjoint variant) the fields are the problem's generated code and the kernel is named
+// wos_adjoint_spec_kernel, so that profiles tell the two apart.
+#if defined(WOS_JIT_FIELDS)
+#define WOS_ADJOINT_KERNEL wos_adjoint_spec_kernel
+#else
+#define WOS_ADJOINT_KERNEL wos_adjoint_kernel
+#endif
+// PASS 1 runs every walk's first replay only and stores its total A in L.totals (indexed by
+// the walk's place in the launch); PASS 2 starts every walk in the second replay from that
+// total and scatters.  The walks of one launch are items L.item_base .. + L.total_items.  Two
+// launches instead of one keep the lanes of a warp in one phase: in a single launch, lanes
+// whose walks were still in their first replay idled through the others' scatters.
+template <int DIM, typename R, bool ALPHA, int PASS>
+__global__ void __launch_bounds__(kAdjBlock, 4) WOS_ADJOINT_KERNEL(AdjLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
     const int4* src = reinterpret_cast<const int4*>(L.problem);
@@ -163,7 +189,8 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   }
   // alpha: per-CTA accumulators in the walk's precision (FP32 shared atomics are native)
   R* gpriv = reinterpret_cast<R*>(smem_raw + L.problem_bytes);
-  const bool priv = ALPHA && L.priv_nodes > 0;
+  const bool priv = ALPHA && PASS == 2 && L.priv_nodes > 0;
+  R* totals = reinterpret_cast<R*>(L.totals);
   const DevProblem<R>& Pg0 = *reinterpret_cast<const DevProblem<R>*>(L.problem);
   const int64_t ares0 = Pg0.alpha.res[0], ares1 = Pg0.alpha.res[1];
   const int64_t ps1 = ares0 + 1, ps2 = ps1 * ares1 + 1;  // padded shared layout
@@ -187,10 +214,12 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
   uint64_t chunk_next = 0, chunk_end = 0;
   const uint64_t magic = (L.walks_uniform > 0) ? ~0ull / (uint64_t)L.walks_uniform : 0ull;
   bool exhausted = false, active = false;
-  // walk state; phase 0 computes the total A, phase 1 replays and scatters
+  // walk state; pass 1 computes the total A, pass 2 replays and scatters
   R x[3] = {R(0), R(0), R(0)}, W = R(1), acc = R(0), total = R(0);
   R xbp[3] = {R(0), R(0), R(0)};  // previous closest boundary point (bounds the next mesh query)
-  uint32_t p = 0, w = 0, k = 0, phase = 0;
+  uint32_t p = 0, w = 0, k = 0;
+  uint64_t slot = 0;  // the walk's place in the launch (index into L.totals)
+  bool fresh = false;  // pass 2: the walk's first iteration (at x_0) is next
   R coef = R(0);  // grad_u e^{-gamma(x_0)} / walks of the walk's point (FP64 only when R is)
   unsigned long long st_steps = 0;
   uint32_t st_walks = 0, st_capped = 0;
@@ -215,7 +244,7 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
       unsigned rank = __popc(need & lt_mask);
       if (!active && rank < take) {
         // item / walks_uniform by a multiply-high and one correction (as in the walk kernel)
-        const uint64_t item = chunk_next + rank, dw = (uint64_t)L.walks_uniform;
+        const uint64_t item = L.item_base + chunk_next + rank, dw = (uint64_t)L.walks_uniform;
         uint64_t pp = __umul64hi(item, magic), jj = item - pp * dw;
         if (jj >= dw) {
           ++pp;
@@ -228,10 +257,11 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
         W = R(1);
         acc = R(0);
         k = 0;
-        phase = 0;
-        // e^{-gamma(x_0)} in the walk's precision (an FP64 exp per walk start, run by the one
-        // or two lanes that start, occupied the narrow FP64 pipe)
-        coef = R(__ldg(&L.grad_u[p]) * inv_walks) * w_exp(-gamma_at<DIM>(P, x));
+        slot = chunk_next + rank;
+        if (PASS == 2) {
+          total = totals[slot];
+          fresh = true;
+        }
         active = true;
       }
       chunk_next += take;
@@ -240,117 +270,117 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
     if (__ballot_sync(0xffffffffu, active) == 0u) break;
     if (!active) continue;
 
-    R xb[3];
-    R bound2 = R(INFINITY);
-    if (P.domain_kind == D_MESH && k > 0) {
-      R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
-      bound2 = e0 * e0 + e1 * e1 + e2 * e2;
-    }
-    R d = distance<DIM>(P, x, xb, bound2);
+    // pass 2 gives each walk one iteration of its own at x_0 first: the fields there give
+    // e^{-gamma(x_0)} and the alpha term of x_0, which then goes through the same scatter
+    // call as the steps' and the boundary's (lanes that start, step or end a walk in one
+    // iteration scatter together instead of one after another)
+    const bool first = (PASS == 2) && fresh;
+    R y[3] = {x[0], x[1], x[2]};
+    R xb[3] = {R(0), R(0), R(0)};
+    R d = R(0), dd = R(0), mu = R(1), Gn = R(0), PB = R(0);
+    R dz[3] = {R(0), R(0), R(0)};
+    bool ends = false;
+    if (!first) {
+      R bound2 = R(INFINITY);
+      if (P.domain_kind == D_MESH && k > 0) {
+        R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
+        bound2 = e0 * e0 + e1 * e1 + e2 * e2;
+      }
+      d = distance<DIM>(P, x, xb, bound2);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
-    const bool ends = !(d >= eps) || k >= max_k;
-    const R dd = w_fmax(d, R(0));
-    U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
-    R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
-    R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
-    if (DIM == 2) {
-      w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
-      w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
-    } else {
-      U4 r1 = philox4x32_10(U4{p, w, k, 1u}, key0, key1);
-      R cy = R(1) - R(2) * to_uniform<R>(r0.z);
-      R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
-      R sp_, cp_;
-      w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
-      dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
-      R cz = R(1) - R(2) * to_uniform<R>(r1.x);
-      R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
-      w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
-      dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
-    }
-    R a = s_root * dd;
-    R q = green_q<DIM, R>(a);
-    R Gn = dd * dd * q, PB = a * a * q;
-    R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * dd;
-    R y[3];
+      for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
+      ends = !(d >= eps) || k >= max_k;
+      dd = w_fmax(d, R(0));
+      U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
+      mu = to_uniform<R>(r0.x);
+      const R ur = to_uniform<R>(r0.y);
+      R dy[3] = {R(0), R(0), R(0)};
+      if (DIM == 2) {
+        w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
+        w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
+      } else {
+        U4 r1 = philox4x32_10(U4{p, w, k, 1u}, key0, key1);
+        R cy = R(1) - R(2) * to_uniform<R>(r0.z);
+        R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
+        R sp_, cp_;
+        w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
+        dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
+        R cz = R(1) - R(2) * to_uniform<R>(r1.x);
+        R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+        w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
+        dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
+      }
+      R a = s_root * dd;
+      R q = green_q<DIM, R>(a);
+      Gn = dd * dd * q;
+      PB = a * a * q;
+      R r = sample_radius<DIM, R>(a, ur, nullptr, (sizeof(R) == 4) ? L.radial_tab : nullptr) * dd;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) y[i] = (i < DIM) ? (ends ? x[i] : x[i] + r * dy[i]) : R(0);
+      for (int i = 0; i < DIM; ++i) y[i] = ends ? x[i] : x[i] + r * dy[i];
+    }
     R spy, fpy, gam, al;
-    coeffs<DIM>(P, y, &spy, &fpy, &gam, &al);
-
-    if (ends) {
+    FieldsAt<R> fat;
+    coeffs<DIM, R, false>(P, y, &spy, &fpy, &gam, &al, nullptr, (ALPHA && PASS == 2) ? &fat : nullptr);
+    // alpha scatter of this iteration: vN N_m + vG . grad N_m + vL Lap N_m at y
+    R vN = R(0), vG[3] = {R(0), R(0), R(0)}, vL = R(0);
+    if (first) {
+      // grad_u e^{-gamma(x_0)} / walks; alpha: -A N_m(x_0) / (2 alpha(x_0))
+      coef = R(__ldg(&L.grad_u[p]) * inv_walks) * w_exp(-gam);
+      if (ALPHA) vN = -coef * total * R(0.5) / al;
+      fresh = false;
+    } else if (ends) {
       bool capped = (d >= eps);
-      R bterm = R(0);
       if (!capped) {
-        bterm = W * w_exp(gam) * g_at<DIM>(P, xb);
+        const R bterm = W * w_exp(gam) * g_at<DIM>(P, xb);
         acc += bterm;
-      }
-      if (ALPHA && phase == 1 && !capped) {
         // boundary factor e^{gamma(x_n)}: d/d alpha_m = N_m(x_n) / (2 alpha(x_n)) times the term
-        const R vG[3] = {R(0), R(0), R(0)};
-        R v = coef * bterm * R(0.5) / al;
-        if (isfinite(v) && v != R(0)) WOS_ALPHA_SCATTER(y, v, vG, R(0));
+        if (ALPHA && PASS == 2) vN = coef * bterm * R(0.5) / al;
       }
-      if (phase == 0) {
-        total = acc;
-#pragma unroll
-        for (int dd2 = 0; dd2 < 3; ++dd2) x[dd2] = (dd2 < DIM) ? R(__ldg(&L.pts[(int64_t)dd2 * L.npts + (int64_t)p])) : R(0);
-        if (ALPHA) {
-          // e^{-gamma(x_0)}: -A N_m(x_0) / (2 alpha(x_0))
-          const R vG[3] = {R(0), R(0), R(0)};
-          R a0 = field_eval<DIM>(P, P.alpha, x[0], x[1], x[2], false).v;
-          R v = -coef * total * R(0.5) / a0;
-          if (isfinite(v) && v != R(0)) WOS_ALPHA_SCATTER(x, v, vG, R(0));
-        }
-        W = R(1);
-        acc = R(0);
-        k = 0;
-        phase = 1;
+      if (PASS == 1) {
+        totals[slot] = acc;  // the walk's total; the second pass replays it
       } else {
         ++st_walks;
         if (capped) ++st_capped;
-        active = false;
       }
-      continue;
-    }
-    const R src = W * Gn * fpy;
-    acc += src;
-    if (ALPHA && phase == 1) {
-      // source f'(y): d/d alpha_m = -N_m(y) / (2 alpha(y)) times the term; null weight: see above
-      R vN = -coef * src * R(0.5) / al, vG[3] = {R(0), R(0), R(0)}, vL = R(0);
-      if (mu <= PB) {
-        R wj = R(1) - spy * inv_sb;
-        R rem = (total - acc) / wj;
-        R rj = -coef * rem * inv_sb;
-        R cN, cG[3], cL;
-        alpha_sensitivity<DIM, R>(P, y, &cN, cG, &cL);
-        if (isfinite(rj)) {
-          vN += rj * cN;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) vG[i] = rj * cG[i];
-          vL = rj * cL;
-        }
-      }
-      if (isfinite(vN)) WOS_ALPHA_SCATTER(y, vN, vG, vL);
-    }
-    if (mu <= PB) {
-      R wj = R(1) - spy * inv_sb;
-      if (!ALPHA && phase == 1) {
-        // d total / d w_j = (A - P_{j+1}) / w_j ; d w_j / d sigma_m = -N_m(y) / (alpha(y) sigma_bar)
-        R rem = (total - acc) / wj;
-        R val = -coef * rem * inv_sb / al;
-        if (isfinite(val) && val != R(0)) grid_scatter<DIM, R>(P.sigma, y, val, L.grad_sigma);
-      }
-      W *= wj;
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) x[i] = y[i];
+      active = false;
     } else {
+      const R src = W * Gn * fpy;
+      acc += src;
+      // source f'(y): d/d alpha_m = -N_m(y) / (2 alpha(y)) times the term
+      if (ALPHA && PASS == 2) vN = -coef * src * R(0.5) / al;
+      if (mu <= PB) {
+        const R wj = R(1) - spy * inv_sb;
+        if (PASS == 2) {
+          // d total / d w_j = (A - P_{j+1}) / w_j
+          const R rem = (total - acc) / wj;
+          if (ALPHA) {
+            // d w_j / d alpha_m = -(1/sigma_bar) d sigma'/d alpha_m
+            const R rj = -coef * rem * inv_sb;
+            R cN, cG[3], cL;
+            alpha_sensitivity<DIM, R>(fat, &cN, cG, &cL);
+            if (isfinite(rj)) {
+              vN += rj * cN;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) x[i] = x[i] + dd * dz[i];
+              for (int i = 0; i < 3; ++i) vG[i] = rj * cG[i];
+              vL = rj * cL;
+            }
+          } else {
+            // d w_j / d sigma_m = -N_m(y) / (alpha(y) sigma_bar)
+            const R val = -coef * rem * inv_sb / al;
+            if (isfinite(val) && val != R(0)) grid_scatter<DIM, R>(P.sigma, y, val, L.grad_sigma);
+          }
+        }
+        W *= wj;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) x[i] = y[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) x[i] = x[i] + dd * dz[i];
+      }
+      if (PASS == 2) ++st_steps;
+      ++k;
     }
-    if (phase == 1) ++st_steps;
-    ++k;
+    if (ALPHA && PASS == 2 && isfinite(vN) && (vN != R(0) || vL != R(0))) WOS_ALPHA_SCATTER(y, vN, vG, vL);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -375,29 +405,36 @@ __global__ void __launch_bounds__(kAdjBlock) wos_adjoint_kernel(AdjLaunch L) {
 #undef WOS_ALPHA_SCATTER
 }
 
-template <int DIM, typename R, bool ALPHA>
+#if !defined(__CUDACC_RTC__)
+// one pass (L.pass 1 or 2) of the adjoint; the caller zeroes the work counter before each
+template <int DIM, typename R, bool ALPHA, int PASS>
 cudaError_t launch_adjoint_m(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
-  size_t smem = (size_t)L.problem_bytes + (ALPHA ? (size_t)L.priv_nodes * sizeof(R) : 0);
+  size_t smem = (size_t)L.problem_bytes + ((ALPHA && PASS == 2) ? (size_t)L.priv_nodes * sizeof(R) : 0);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(wos_adjoint_kernel<DIM, R, ALPHA>,
+    cudaError_t e = cudaFuncSetAttribute(wos_adjoint_kernel<DIM, R, ALPHA, PASS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_adjoint_kernel<DIM, R, ALPHA>, kAdjBlock,
-                                                                smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_adjoint_kernel<DIM, R, ALPHA, PASS>,
+                                                                kAdjBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
   uint64_t blocks_needed = (L.total_items + kAdjBlock - 1) / kAdjBlock;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_adjoint_kernel<DIM, R, ALPHA><<<grid, kAdjBlock, smem, stream>>>(L);
+  wos_adjoint_kernel<DIM, R, ALPHA, PASS><<<grid, kAdjBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_adjoint_t(const AdjLaunch& L, int num_sms, cudaStream_t stream) {
-  return L.alpha ? launch_adjoint_m<DIM, R, true>(L, num_sms, stream) : launch_adjoint_m<DIM, R, false>(L, num_sms, stream);
+  if (L.pass == 1)
+    return L.alpha ? launch_adjoint_m<DIM, R, true, 1>(L, num_sms, stream)
+                   : launch_adjoint_m<DIM, R, false, 1>(L, num_sms, stream);
+  return L.alpha ? launch_adjoint_m<DIM, R, true, 2>(L, num_sms, stream)
+                 : launch_adjoint_m<DIM, R, false, 2>(L, num_sms, stream);
 }
+#endif  // !__CUDACC_RTC__
 
 }  // namespace wos

@@ -521,6 +521,7 @@ int wos_destroy(wos_ctx* ctx) {
     if (ctx->mv_sum) cudaFree(ctx->mv_sum);
     if (ctx->mv_count) cudaFree(ctx->mv_count);
     if (ctx->adj_buf) cudaFree(ctx->adj_buf);
+    if (ctx->adj_totals) cudaFree(ctx->adj_totals);
   }
   delete ctx;
   return WOS_OK;
@@ -986,13 +987,15 @@ int wos_solve_host(wos_ctx* ctx, const wos_problem* pr, const float* pts_host, i
 
 // ---- problem-specialised walk kernels (runtime compilation) ----
 namespace {
-const int32_t kSpecFlags = WOS_SPEC_FP32 | WOS_SPEC_FP64 | WOS_SPEC_PLAIN | WOS_SPEC_WINDOW | WOS_SPEC_GRAD;
+const int32_t kSpecFlags =
+    WOS_SPEC_FP32 | WOS_SPEC_FP64 | WOS_SPEC_PLAIN | WOS_SPEC_WINDOW | WOS_SPEC_GRAD | WOS_SPEC_ADJOINT;
 
 int spec_variants(int32_t flags) {
   int vm = 0;
   if (flags & WOS_SPEC_PLAIN) vm |= 1 << wos::kJitPlain;
   if (flags & WOS_SPEC_WINDOW) vm |= 1 << wos::kJitWindow;
   if (flags & WOS_SPEC_GRAD) vm |= 1 << wos::kJitGrad;
+  if (flags & WOS_SPEC_ADJOINT) vm |= 1 << wos::kJitAdjoint;
   return vm ? vm : 1 << wos::kJitPlain;
 }
 
@@ -1041,6 +1044,8 @@ int wos_problem_specialized(const wos_problem* pr, int32_t* flags_out) {
   for (int p = 0; p < 2; ++p)
     for (int v = 0; v < wos::kJitVariants; ++v)
       if (pr->jit.kernel[p][v] != nullptr) f |= (p ? WOS_SPEC_FP64 : WOS_SPEC_FP32) | vbit[v];
+  for (int p = 0; p < 2; ++p)
+    if (pr->jit.adjoint[p][0][0] != nullptr) f |= (p ? WOS_SPEC_FP64 : WOS_SPEC_FP32) | WOS_SPEC_ADJOINT;
   *flags_out = f;
   return WOS_OK;
 }
@@ -1058,6 +1063,56 @@ int wos_jit_source(const wos_problem_desc* d, char* buf, int64_t cap, int64_t* l
   if (len) *len = (int64_t)src.size();
   copy_text(src, buf, cap);
   return WOS_OK;
+}
+
+static int batch_info_of(const wos_problem_desc* descs, int32_t n, wos::BatchJitInfo* info, std::string* why) {
+  if (!descs || n < 1) {
+    *why = "need at least one description";
+    return WOS_EINVAL;
+  }
+  std::vector<DevProblem<double>> h(n);
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = host_problem(&descs[i], &h[i], why);
+    if (rc != WOS_OK) return rc;
+    if (descs[i].dim != descs[0].dim) {
+      *why = "all problems of a batch must have one dimension";
+      return WOS_EINVAL;
+    }
+  }
+  wos::batch_jit_info(h.data(), n, info);
+  return WOS_OK;
+}
+
+int wos_jit_batch_source(const wos_problem_desc* descs, int32_t n, char* buf, int64_t cap, int64_t* len) {
+  std::unique_ptr<wos::BatchJitInfo> info(new wos::BatchJitInfo());
+  std::string why;
+  int rc = batch_info_of(descs, n, info.get(), &why);
+  if (rc != WOS_OK) {
+    copy_text(why, buf, cap);
+    return rc;
+  }
+  const std::string src = wos::jit_source_batch(*info);
+  if (len) *len = (int64_t)src.size();
+  copy_text(src, buf, cap);
+  return WOS_OK;
+}
+
+int wos_jit_batch_compile(const wos_problem_desc* descs, int32_t n, int32_t flags, char* log, int64_t log_cap,
+                          int64_t* cubin_bytes) {
+  if (flags & ~(WOS_SPEC_FP32 | WOS_SPEC_FP64 | WOS_SPEC_PLAIN)) return WOS_EINVAL;
+  std::unique_ptr<wos::BatchJitInfo> info(new wos::BatchJitInfo());
+  std::string why;
+  int rc = batch_info_of(descs, n, info.get(), &why);
+  if (rc != WOS_OK) {
+    copy_text(why, log, log_cap);
+    return rc;
+  }
+  std::vector<char> cubin;
+  std::vector<std::string> lowered;
+  rc = wos::jit_compile_batch(*info, (flags & WOS_SPEC_FP64) != 0, &cubin, &lowered, &why);
+  copy_text(why, log, log_cap);
+  if (cubin_bytes) *cubin_bytes = (int64_t)cubin.size();
+  return rc;
 }
 
 int wos_jit_compile(const wos_problem_desc* d, int32_t flags, char* log, int64_t log_cap, int64_t* cubin_bytes) {
@@ -1079,6 +1134,57 @@ int wos_jit_compile(const wos_problem_desc* d, int32_t flags, char* log, int64_t
 
 }  // extern "C"
 
+namespace {
+constexpr uint64_t kAdjChunkItems = 1ull << 24;  // walks per pair of passes (their totals: 64 or 128 MB)
+
+// the context's buffer of walk totals, at least `bytes` long
+int ensure_adj_totals(wos_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->adj_totals_bytes) return WOS_OK;
+  // an earlier adjoint may still be reading the old buffer on some stream
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing the adjoint totals");
+  if (ctx->adj_totals) cudaFree(ctx->adj_totals);
+  ctx->adj_totals = nullptr;
+  ctx->adj_totals_bytes = 0;
+  e = cudaMalloc(&ctx->adj_totals, bytes);
+  if (e != cudaSuccess) {
+    ctx->adj_totals = nullptr;
+    return fail(ctx, WOS_ENOMEM, std::string("cudaMalloc(adjoint totals): ") + cudaGetErrorString(e));
+  }
+  ctx->adj_totals_bytes = bytes;
+  return WOS_OK;
+}
+
+// the two passes of the path-replay adjoint over chunks of at most kAdjChunkItems walks: pass 1
+// stores each walk's total, pass 2 replays the walk from it and scatters.  The
+// problem-specialised kernels run when loaded (WOS_SPEC_ADJOINT), else the generic ones.
+int adjoint_run(wos_ctx* ctx, const wos_problem* pr, wos::AdjLaunch& L, bool fp64, cudaStream_t st) {
+  L.problem = fp64 ? (const void*)pr->d64 : (const void*)pr->d32;
+  L.problem_bytes = fp64 ? (int)sizeof(DevProblem<double>) : (int)sizeof(DevProblem<float>);
+  L.work_counter = ctx->scratch;
+  const uint64_t all = L.total_items;
+  const size_t rb = fp64 ? sizeof(double) : sizeof(float);
+  int rc = ensure_adj_totals(ctx, rb * (size_t)std::min<uint64_t>(all, kAdjChunkItems));
+  if (rc) return rc;
+  L.totals = ctx->adj_totals;
+  for (uint64_t base = 0; base < all; base += kAdjChunkItems) {
+    L.item_base = base;
+    L.total_items = std::min<uint64_t>(all - base, kAdjChunkItems);
+    for (int pass = 1; pass <= 2; ++pass) {
+      L.pass = pass;
+      cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
+      cudaKernel_t spec = pr->jit.adjoint[fp64 ? 1 : 0][L.alpha ? 1 : 0][pass - 1];
+      if (spec != nullptr) e = wos::launch_adjoint_kernel(L, spec, (int)rb, ctx->num_sms, st);
+      else e = fp64 ? wos::launch_adjoint_f64(L, ctx->num_sms, st) : wos::launch_adjoint_f32(L, ctx->num_sms, st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+    }
+  }
+  L.total_items = all;
+  return WOS_OK;
+}
+}  // namespace
+
 extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts,
                                  int32_t walks_uniform, const wos_params* prm, const double* grad_u,
                                  double* grad_sigma, uint64_t* stats, void* stream) {
@@ -1099,8 +1205,6 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
     return fail(ctx, WOS_EUNSUPPORTED, "a manufactured source depends on sigma; give f explicitly");
   DeviceGuard g(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
   wos::AdjLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.dim = pr->dim;
@@ -1116,19 +1220,8 @@ extern "C" int wos_adjoint_sigma(wos_ctx* ctx, const wos_problem* pr, const floa
   L.grad_u = grad_u;
   L.grad_sigma = grad_sigma;
   L.stats = reinterpret_cast<unsigned long long*>(stats);
-  L.work_counter = ctx->scratch;
   L.radial_tab = ctx->radial_tab[pr->dim - 2];
-  if (prm->precision == WOS_FP64) {
-    L.problem = pr->d64;
-    L.problem_bytes = (int)sizeof(DevProblem<double>);
-    e = wos::launch_adjoint_f64(L, ctx->num_sms, st);
-  } else {
-    L.problem = pr->d32;
-    L.problem_bytes = (int)sizeof(DevProblem<float>);
-    e = wos::launch_adjoint_f32(L, ctx->num_sms, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
-  return WOS_OK;
+  return adjoint_run(ctx, pr, L, prm->precision == WOS_FP64, st);
 }
 
 namespace wos {
@@ -1185,8 +1278,6 @@ extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const floa
   int64_t nodes = (int64_t)H.alpha.res[0] * H.alpha.res[1] * (pr->dim == 3 ? H.alpha.res[2] : 1);
   DeviceGuard g(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
   wos::AdjLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.dim = pr->dim;
@@ -1203,23 +1294,12 @@ extern "C" int wos_adjoint_alpha(wos_ctx* ctx, const wos_problem* pr, const floa
   L.grad_alpha = grad_alpha;
   L.alpha = 1;
   L.stats = reinterpret_cast<unsigned long long*>(stats);
-  L.work_counter = ctx->scratch;
   L.radial_tab = ctx->radial_tab[pr->dim - 2];
   // grids of up to 8192 nodes (64 KB of FP64) are accumulated per CTA in shared memory
   // the per-CTA copy is padded (row stride res0 + 1, plane stride (res0 + 1) res1 + 1)
   int64_t padded = ((int64_t)(H.alpha.res[0] + 1) * H.alpha.res[1] + 1) * (pr->dim == 3 ? H.alpha.res[2] : 1);
   L.priv_nodes = (nodes <= 8192) ? (int)padded : 0;
-  if (prm->precision == WOS_FP64) {
-    L.problem = pr->d64;
-    L.problem_bytes = (int)sizeof(DevProblem<double>);
-    e = wos::launch_adjoint_f64(L, ctx->num_sms, st);
-  } else {
-    L.problem = pr->d32;
-    L.problem_bytes = (int)sizeof(DevProblem<float>);
-    e = wos::launch_adjoint_f32(L, ctx->num_sms, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
-  return WOS_OK;
+  return adjoint_run(ctx, pr, L, prm->precision == WOS_FP64, st);
 }
 
 extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, int32_t nprob,
@@ -1253,6 +1333,8 @@ extern "C" int wos_batch_create(wos_ctx* ctx, const wos_problem* const* probs, i
     h32[i] = probs[i]->host32;
     h64[i] = probs[i]->host64;
   }
+  // which fields every problem shares (the code wos_batch_specialize can compile in)
+  wos::batch_jit_info(h64.data(), nprob, &b->jit_info);
   cudaError_t e = cudaMalloc(&b->d32, sizeof(DevProblem<float>) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d64, sizeof(DevProblem<double>) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->offsets, sizeof(int64_t) * (nprob + 1));
@@ -1279,8 +1361,36 @@ extern "C" int wos_batch_destroy(wos_batch* b) {
     if (b->offsets) cudaFree(b->offsets);
     if (b->sigma_bars) cudaFree(b->sigma_bars);
     if (b->walk_end) cudaFree(b->walk_end);
+    wos::jit_release(&b->jit);
   }
   delete b;
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_specialize(wos_ctx* ctx, wos_batch* b, int32_t flags) {
+  if (!ctx) return WOS_EINVAL;
+  if (!b || b->ctx != ctx) return fail(ctx, WOS_EINVAL, "null batch or batch of another context");
+  if (flags & ~(WOS_SPEC_FP32 | WOS_SPEC_FP64 | WOS_SPEC_PLAIN))
+    return fail(ctx, WOS_EINVAL, "batches specialise the plain walk in FP32 and/or FP64 only");
+  const bool f32 = (flags & WOS_SPEC_FP32) || !(flags & WOS_SPEC_FP64);
+  const bool f64 = (flags & WOS_SPEC_FP64) != 0;
+  DeviceGuard g(b->device);
+  std::string why;
+  for (int p = 0; p < 2; ++p) {
+    if ((p == 0 && !f32) || (p == 1 && !f64)) continue;
+    int rc = wos::jit_specialise_batch(&b->jit, b->jit_info, p == 1, &why);
+    if (rc != WOS_OK) return fail(ctx, rc, why);
+  }
+  return WOS_OK;
+}
+
+extern "C" int wos_batch_specialized(const wos_batch* b, int32_t* flags_out, int32_t* uniform_fields) {
+  if (!b || !flags_out) return WOS_EINVAL;
+  int32_t f = 0;
+  if (b->jit.kernel[0][0]) f |= WOS_SPEC_FP32 | WOS_SPEC_PLAIN;
+  if (b->jit.kernel[1][0]) f |= WOS_SPEC_FP64 | WOS_SPEC_PLAIN;
+  *flags_out = f;
+  if (uniform_fields) *uniform_fields = (int32_t)b->jit_info.uniform;
   return WOS_OK;
 }
 
@@ -1470,13 +1580,11 @@ int solve_batch_impl(wos_ctx* ctx, const wos_batch* b, const wos_schedule& sched
   L.chunk = (uint32_t)sched.chunk;
   L.blocks_per_sm = sched.blocks_per_sm;
   L.regs_variant = sched.regs_variant;
-  if (prm->precision == WOS_FP64) {
-    L.probs = b->d64;
-    e = wos::launch_walks_f64(L, ctx->num_sms, st);
-  } else {
-    L.probs = b->d32;
-    e = wos::launch_walks_f32(L, ctx->num_sms, st);
-  }
+  const bool fp64 = prm->precision == WOS_FP64;
+  L.probs = fp64 ? (const void*)b->d64 : (const void*)b->d32;
+  cudaKernel_t spec = b->jit.kernel[fp64 ? 1 : 0][sched.regs_variant == 1 ? 1 : 0];
+  if (spec != nullptr) e = wos::launch_walks_kernel(L, spec, fp64 ? 8 : 4, ctx->num_sms, st);  // wos_batch_specialize
+  else e = fp64 ? wos::launch_walks_f64(L, ctx->num_sms, st) : wos::launch_walks_f32(L, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batched walk kernel launch");
   return WOS_OK;
 }

@@ -38,6 +38,9 @@ struct wos_ctx {
   // FP64 gradient buffer of wos_adjoint (sigma nodes + alpha nodes)
   double* adj_buf = nullptr;
   int64_t adj_cap = 0;
+  // per-walk totals between the two passes of the path-replay adjoint
+  void* adj_totals = nullptr;
+  size_t adj_totals_bytes = 0;
 };
 
 struct wos_batch {
@@ -52,6 +55,8 @@ struct wos_batch {
   double* sigma_bars = nullptr;       // [nprob]
   int64_t* walk_end = nullptr;        // [npts] prefix sums for per-point walk counts
   wos_schedule sched = {0, 0, 0, 0};  // launch schedule (wos_batch_set_schedule / autotune)
+  wos::BatchJitInfo jit_info;         // fields shared by every problem (wos_batch_specialize)
+  wos::JitState jit;                  // batched kernels compiled for them: [fp64][regs variant]
 };
 
 struct wos_problem {

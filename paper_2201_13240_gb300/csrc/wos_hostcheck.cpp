@@ -205,4 +205,9 @@ void wos_hc_mix_radius(int dim, int fp64, double a, double lam, const double* u,
   }
 }
 
+// FP32 uniforms of the walk kernels from Philox words
+void wos_hc_uniform_f32(const uint32_t* x, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = (double)wos::to_uniform<float>(x[i]);
+}
+
 }  // extern "C"

@@ -70,7 +70,8 @@ struct AdjLaunch {
   const float* pts;
   int64_t npts;
   int64_t walks_uniform;
-  uint64_t total_items;
+  uint64_t total_items;           // walks of this launch: items item_base .. item_base + total_items - 1
+  uint64_t item_base;             // item = point * walks_uniform + walk
   uint64_t seed;
   uint64_t walk_offset;
   double eps;
@@ -84,11 +85,16 @@ struct AdjLaunch {
   unsigned long long* stats;      // optional
   unsigned long long* work_counter;
   const float* radial_tab;
+  void* totals;                   // [total_items] walk totals in the walk's precision (pass 1 writes them)
+  int pass;                       // 1: the walks' totals, 2: the replay that scatters
 };
 
 #if !defined(__CUDACC_RTC__)
 cudaError_t launch_adjoint_f32(const AdjLaunch& L, int num_sms, cudaStream_t stream);
 cudaError_t launch_adjoint_f64(const AdjLaunch& L, int num_sms, cudaStream_t stream);
+// an adjoint kernel compiled at run time for one problem (same parameter block and launch shape)
+cudaError_t launch_adjoint_kernel(const AdjLaunch& L, cudaKernel_t kernel, int real_bytes, int num_sms,
+                                  cudaStream_t stream);
 
 // launch the persistent walk kernel; returns a cudaError_t
 cudaError_t launch_walks_f32(const WalkLaunch& L, int num_sms, cudaStream_t stream);

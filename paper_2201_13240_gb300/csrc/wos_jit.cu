@@ -252,7 +252,7 @@ std::string jit_source(const DevProblem<double>& P) {
   s += "#define WOS_JIT_F_KIND " + std::to_string(P.f.kind) + "\n";
   // resident blocks per SM: 3D 7 (72 registers), 2D 8 (64 registers), neither spills
   s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 7\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
-  s += "#include \"wos_walk_impl.cuh\"\n\nnamespace wos {\n\n";
+  s += "#include \"wos_walk_impl.cuh\"\n#include \"wos_adjoint_impl.cuh\"\n\nnamespace wos {\n\n";
   s += "template <int DIM, typename R>\n";
   s += "__device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id, R x0, R x1, R x2, "
        "bool deriv) {\n";
@@ -271,6 +271,168 @@ std::string jit_source(const DevProblem<double>& P) {
   return s;
 }
 
+bool same_field(const DevProblem<double>& A, const DevField<double>& F, const DevProblem<double>& B,
+                const DevField<double>& G) {
+  if (F.kind != G.kind) return false;
+  if (F.kind == F_CONST) return F.value == G.value;
+  if (F.kind != F_SST) return true;  // ZERO; grids read the walk's own descriptor
+  if (F.nterms != G.nterms) return false;
+  for (int n = 0; n < F.nterms; ++n) {
+    const DevTerm<double>& s = A.terms[F.first + n];
+    const DevTerm<double>& t = B.terms[G.first + n];
+    if (s.c != t.c) return false;
+    for (int i = 0; i < 3; ++i)
+      if (s.type[i] != t.type[i] || s.k[i] != t.k[i] || s.phi[i] != t.phi[i]) return false;
+  }
+  return true;
+}
+
+std::string jit_source_batch(const BatchJitInfo& info) {
+  const DevProblem<double>& P = info.rep;
+  const int dim = P.dim;
+  std::string s;
+  s += "// walk kernel specialised to a batch of problems (" + std::to_string(dim) +
+       "D): fields shared by every problem are generated code, the others are interpreted\n";
+  s += "#define WOS_JIT_FIELDS 1\n";
+  s += "#define WOS_JIT_F_KIND " + std::to_string(P.f.kind) + "\n";
+  s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 7\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
+  s += "#include \"wos_walk_impl.cuh\"\n\nnamespace wos {\n\n";
+  s += "template <int DIM, typename R>\n";
+  s += "__device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id, R x0, R x1, R x2, "
+       "bool deriv) {\n";
+  s += "  FieldVal<R> o = {R(0), R(0), R(0), R(0), R(0)};\n";
+  s += "  switch (id) {\n";
+  const DevField<double>* fields[6] = {&P.alpha, &P.phi, &P.sigma, &P.f, &P.g, &P.um};
+  static const char* ids[6] = {"FLD_ALPHA", "FLD_PHI", "FLD_SIGMA", "FLD_F", "FLD_G", "FLD_UM"};
+  static const char* mem[6] = {"alpha", "phi", "sigma", "f", "g", "um"};
+  for (int f = 0; f < 6; ++f) {
+    if (info.uniform & (1u << f)) {
+      gen_field(s, P, *fields[f], ids[f], mem[f], dim);
+    } else {
+      s += std::string("  case ") + ids[f] + ":\n    return field_eval<DIM>(P, P." + mem[f] +
+           ", x0, x1, x2, deriv);\n";
+    }
+  }
+  s += "  default:\n    return o;\n  }\n}\n\n}  // namespace wos\n";
+  return s;
+}
+
+namespace {
+std::string batch_kernel_expr(int dim, bool fp64, int minb) {
+  return std::string("wos::wos_walk_spec_kernel<") + std::to_string(dim) + ", " + (fp64 ? "double" : "float") +
+         ", false, true, false, false, false, " + std::to_string(minb) + ">";
+}
+
+// NVRTC compile of a source with the given kernel name expressions
+int compile_exprs(const std::string& src, const std::vector<std::string>& exprs, std::vector<char>* cubin,
+                  std::vector<std::string>* lowered, std::string* log) {
+  const Nvrtc& api = nvrtc();
+  if (!api.ok) {
+    *log = api.why;
+    return WOS_EUNSUPPORTED;
+  }
+  nvrtcProgram prog = nullptr;
+  nvrtcResult r = api.CreateProgram(&prog, src.c_str(), "wos_walk_specialised.cu", kJitHeaderCount, kJitHeaderTexts,
+                                    kJitHeaderNames);
+  if (r != NVRTC_SUCCESS) {
+    *log = std::string("nvrtcCreateProgram: ") + api.GetErrorString(r);
+    return WOS_EUNSUPPORTED;
+  }
+  for (const std::string& e : exprs) {
+    r = api.AddNameExpression(prog, e.c_str());
+    if (r != NVRTC_SUCCESS) {
+      *log = std::string("nvrtcAddNameExpression: ") + api.GetErrorString(r);
+      api.DestroyProgram(&prog);
+      return WOS_EUNSUPPORTED;
+    }
+  }
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
+  r = api.CompileProgram(prog, 3, opts);
+  size_t ls = 0;
+  api.GetProgramLogSize(prog, &ls);
+  std::string plog(ls, '\0');
+  if (ls > 0) api.GetProgramLog(prog, &plog[0]);
+  while (!plog.empty() && plog.back() == '\0') plog.pop_back();
+  if (r != NVRTC_SUCCESS) {
+    *log = std::string("nvrtcCompileProgram: ") + api.GetErrorString(r) + "\n" + plog;
+    api.DestroyProgram(&prog);
+    return WOS_EUNSUPPORTED;
+  }
+  size_t n = 0;
+  api.GetCUBINSize(prog, &n);
+  cubin->assign(n, 0);
+  api.GetCUBIN(prog, cubin->data());
+  lowered->assign(exprs.size(), std::string());
+  for (size_t v = 0; v < exprs.size(); ++v) {
+    const char* ln = nullptr;
+    if (api.GetLoweredName(prog, exprs[v].c_str(), &ln) == NVRTC_SUCCESS && ln) (*lowered)[v] = ln;
+  }
+  api.DestroyProgram(&prog);
+  *log = plog;
+  return WOS_OK;
+}
+}  // namespace
+
+void batch_jit_info(const DevProblem<double>* probs, int n, BatchJitInfo* info) {
+  info->rep = probs[0];
+  info->uniform = 0x3fu;
+  info->f_kind_uniform = true;
+  const DevProblem<double>& A = probs[0];
+  const DevField<double>* fa[6] = {&A.alpha, &A.phi, &A.sigma, &A.f, &A.g, &A.um};
+  for (int i = 1; i < n; ++i) {
+    const DevProblem<double>& B = probs[i];
+    const DevField<double>* fb[6] = {&B.alpha, &B.phi, &B.sigma, &B.f, &B.g, &B.um};
+    for (int f = 0; f < 6; ++f)
+      if (!same_field(A, *fa[f], B, *fb[f])) info->uniform &= ~(1u << f);
+    if ((A.f.kind == F_MANUFACTURED) != (B.f.kind == F_MANUFACTURED)) info->f_kind_uniform = false;
+  }
+}
+
+int jit_compile_batch(const BatchJitInfo& info, bool fp64, std::vector<char>* cubin, std::vector<std::string>* lowered,
+                      std::string* log) {
+  if (!info.f_kind_uniform) {
+    *log = "the problems of the batch differ in the kind of their source (manufactured or not)";
+    return WOS_EUNSUPPORTED;
+  }
+  const std::vector<std::string> exprs = {batch_kernel_expr(info.rep.dim, fp64, 0),
+                                          batch_kernel_expr(info.rep.dim, fp64, 8)};
+  return compile_exprs(jit_source_batch(info), exprs, cubin, lowered, log);
+}
+
+int jit_specialise_batch(JitState* js, const BatchJitInfo& info, bool fp64, std::string* why) {
+  const int p = fp64 ? 1 : 0;
+  if (js->kernel[p][0] != nullptr && js->kernel[p][1] != nullptr) return WOS_OK;
+  std::vector<char> cubin;
+  std::vector<std::string> lowered;
+  std::string log;
+  int rc = jit_compile_batch(info, fp64, &cubin, &lowered, &log);
+  if (rc != WOS_OK) {
+    *why = log;
+    return rc;
+  }
+  cudaLibrary_t lib = nullptr;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) {
+    *why = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return WOS_ECUDA;
+  }
+  cudaKernel_t found[2] = {nullptr, nullptr};
+  for (int v = 0; v < 2; ++v) {
+    e = lowered[v].empty() ? cudaErrorSymbolNotFound : cudaLibraryGetKernel(&found[v], lib, lowered[v].c_str());
+    if (e != cudaSuccess) {
+      *why = std::string("cudaLibraryGetKernel(batch): ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      cudaLibraryUnload(lib);
+      return WOS_ECUDA;
+    }
+  }
+  js->kernel[p][0] = found[0];
+  js->kernel[p][1] = found[1];
+  js->libs.push_back(lib);
+  return WOS_OK;
+}
+
 int jit_compile(const DevProblem<double>& P, bool fp64, int variant_mask, std::vector<char>* cubin,
                 std::vector<std::string>* lowered, std::string* log) {
   const Nvrtc& api = nvrtc();
@@ -287,10 +449,22 @@ int jit_compile(const DevProblem<double>& P, bool fp64, int variant_mask, std::v
     *log = std::string("nvrtcCreateProgram: ") + api.GetErrorString(r);
     return WOS_EUNSUPPORTED;
   }
-  std::vector<std::string> exprs(kJitVariants);
-  for (int v = 0; v < kJitVariants; ++v) {
-    if (!(variant_mask & (1 << v))) continue;
-    exprs[v] = kernel_expr(P.dim, fp64, mesh, drift, v);
+  // walk variants at 0..kJitVariants-1, then the adjoint kernels (sigma pass 1, 2, alpha pass 1, 2)
+  std::vector<std::string> exprs(kJitExprs);
+  if (variant_mask & (1 << kJitAdjoint)) {
+    const std::string t = std::to_string(P.dim) + ", " + (fp64 ? "double" : "float");
+    for (int a = 0; a < 2; ++a)
+      for (int pass = 1; pass <= 2; ++pass)
+        exprs[kJitVariants + 2 * a + pass - 1] = "wos::wos_adjoint_spec_kernel<" + t + (a ? ", true, " : ", false, ") +
+                                                 std::to_string(pass) + ">";
+  }
+  for (int v = 0; v < kJitExprs; ++v) {
+    if (v < kJitVariants) {
+      if (!(variant_mask & (1 << v))) continue;
+      exprs[v] = kernel_expr(P.dim, fp64, mesh, drift, v);
+    } else if (exprs[v].empty()) {
+      continue;
+    }
     r = api.AddNameExpression(prog, exprs[v].c_str());
     if (r != NVRTC_SUCCESS) {
       *log = std::string("nvrtcAddNameExpression: ") + api.GetErrorString(r);
@@ -314,8 +488,8 @@ int jit_compile(const DevProblem<double>& P, bool fp64, int variant_mask, std::v
   api.GetCUBINSize(prog, &n);
   cubin->assign(n, 0);
   api.GetCUBIN(prog, cubin->data());
-  lowered->assign(kJitVariants, std::string());
-  for (int v = 0; v < kJitVariants; ++v) {
+  lowered->assign(kJitExprs, std::string());
+  for (int v = 0; v < kJitExprs; ++v) {
     if (exprs[v].empty()) continue;
     const char* ln = nullptr;
     if (api.GetLoweredName(prog, exprs[v].c_str(), &ln) == NVRTC_SUCCESS && ln) (*lowered)[v] = ln;
@@ -326,15 +500,20 @@ int jit_compile(const DevProblem<double>& P, bool fp64, int variant_mask, std::v
 }
 
 int jit_specialise(JitState* js, const DevProblem<double>& P, bool fp64, int variant_mask, std::string* why) {
-  // a drift problem walks with the plain variant only (no window, no gradient)
+  // a drift problem walks with the plain variant only (no window, no gradient, no adjoint)
   if (P.has_drift && (variant_mask & ~(1 << kJitPlain))) {
     *why = "an extra drift (omega) works with the plain walk only";
+    return WOS_EUNSUPPORTED;
+  }
+  if ((variant_mask & (1 << kJitAdjoint)) && P.domain_kind == D_MESH) {
+    *why = "the adjoint kernels run on analytic domains";
     return WOS_EUNSUPPORTED;
   }
   const int p = fp64 ? 1 : 0;
   int need = 0;
   for (int v = 0; v < kJitVariants; ++v)
     if ((variant_mask & (1 << v)) && js->kernel[p][v] == nullptr) need |= 1 << v;
+  if ((variant_mask & (1 << kJitAdjoint)) && js->adjoint[p][0][0] == nullptr) need |= 1 << kJitAdjoint;
   if (need == 0) return WOS_OK;
   std::vector<char> cubin;
   std::vector<std::string> lowered;
@@ -352,12 +531,13 @@ int jit_specialise(JitState* js, const DevProblem<double>& P, bool fp64, int var
     return WOS_ECUDA;
   }
   // every requested kernel is found before any is published: a failure leaves the state as it was
-  cudaKernel_t found[kJitVariants] = {nullptr, nullptr, nullptr};
-  for (int v = 0; v < kJitVariants; ++v) {
-    if (!(need & (1 << v))) continue;
+  cudaKernel_t found[kJitExprs] = {};
+  for (int v = 0; v < kJitExprs; ++v) {
+    if (!(need & (1 << (v < kJitVariants ? v : kJitAdjoint)))) continue;
     e = lowered[v].empty() ? cudaErrorSymbolNotFound : cudaLibraryGetKernel(&found[v], lib, lowered[v].c_str());
     if (e != cudaSuccess) {
-      *why = std::string("cudaLibraryGetKernel(") + kVariantName[v] + "): " + cudaGetErrorString(e);
+      *why = std::string("cudaLibraryGetKernel(") + (v < kJitVariants ? kVariantName[v] : "adjoint") +
+             "): " + cudaGetErrorString(e);
       cudaGetLastError();
       cudaLibraryUnload(lib);
       return WOS_ECUDA;
@@ -365,6 +545,10 @@ int jit_specialise(JitState* js, const DevProblem<double>& P, bool fp64, int var
   }
   for (int v = 0; v < kJitVariants; ++v)
     if (need & (1 << v)) js->kernel[p][v] = found[v];
+  if (need & (1 << kJitAdjoint)) {
+    for (int a = 0; a < 2; ++a)
+      for (int q = 0; q < 2; ++q) js->adjoint[p][a][q] = found[kJitVariants + 2 * a + q];
+  }
   js->libs.push_back(lib);
   return WOS_OK;
 }
@@ -374,6 +558,9 @@ void jit_release(JitState* js) {
   js->libs.clear();
   for (auto& row : js->kernel)
     for (auto& k : row) k = nullptr;
+  for (auto& plane : js->adjoint)
+    for (auto& row : plane)
+      for (auto& k : row) k = nullptr;
 }
 
 }  // namespace wos

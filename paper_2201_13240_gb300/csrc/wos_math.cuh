@@ -26,6 +26,7 @@ typedef unsigned long long uint64_t;
 #include <stdint.h>
 
 #include <cmath>
+#include <cstring>
 #endif
 
 #if defined(__CUDACC__)
@@ -179,9 +180,31 @@ WOS_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 // uniforms in (0,1): FP32 keeps the top 24 bits, FP64 all 32
 template <typename R>
 WOS_HD R to_uniform(uint32_t x);
+// FP32: ((x >> 9) + 1/2) 2^-23, built from the bits -- the 23 high bits as the mantissa of
+// a float in [1, 2), minus (1 - 2^-24), both exact -- with an OR and a subtraction instead
+// of an integer-to-float conversion.  The FP32 walks' parity with the oracle is
+// statistical, so their uniforms need not be the FP64 ones rounded.
+WOS_HD float u32_bits_as_float(uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+WOS_HD int32_t f_as_i_bits(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_int(f);
+#else
+  int32_t i;
+  memcpy(&i, &f, 4);
+  return i;
+#endif
+}
 template <>
 WOS_HD float to_uniform<float>(uint32_t x) {
-  return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+  return u32_bits_as_float(0x3f800000u | (x >> 9)) - 0.99999994039535522461f;
 }
 template <>
 WOS_HD double to_uniform<double>(uint32_t x) {
@@ -992,16 +1015,30 @@ WOS_HD float load_tab(const float* p) {
 #endif
 }
 
+// floor of v in [0, 2^22) as (index, v - index) by the float magic number 1.5 * 2^23: adding
+// it rounds v - 1/2 to an integer held in the mantissa (at an integer v a tie may round one
+// down, leaving a fraction of exactly 1: the interpolation is continuous there).  No
+// float-integer conversion instruction.
+WOS_HD int floor_split(float v, float* frac) {
+  const float m = (v - 0.5f) + 12582912.0f;
+  const float fl = m - 12582912.0f;
+  *frac = v - fl;
+  return (int)(f_as_i_bits(m) - f_as_i_bits(12582912.0f));
+}
 WOS_HD float table_guess(const float* tab, float a, float u) {
-  float fa = a * (1.0f / kTabDA);
-  int ia = (int)fa;
-  if (ia > kTabA - 2) ia = kTabA - 2;
-  float ta = fa - (float)ia;
-  float ft = tab_t_of_u(u) * (float)(kTabU - 1);
-  int it = (int)ft;
-  if (it > kTabU - 2) it = kTabU - 2;
-  if (it < 0) it = 0;
-  float tt = ft - (float)it;
+  const float fa = a * (1.0f / kTabDA);  // a < (kTabA - 1) kTabDA when the table is used
+  float ta;
+  int ia = floor_split(fa, &ta);
+  if (ia > kTabA - 2) {  // a at the table's upper edge
+    ta += (float)(ia - (kTabA - 2));
+    ia = kTabA - 2;
+  }
+  float tt;
+  int it = floor_split(tab_t_of_u(u) * (float)(kTabU - 1), &tt);
+  if (it > kTabU - 2) {  // t = 1
+    tt += 1.0f;
+    it = kTabU - 2;
+  }
   const float* r0 = tab + ia * kTabU + it;
   const float* r1 = r0 + kTabU;
   float v0 = load_tab(r0) + tt * (load_tab(r0 + 1) - load_tab(r0));

@@ -313,9 +313,17 @@ __device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id,
 // Transformed coefficients at y: sigma'(y), f'(y) and gamma(y) (Sec. 4.1, App. A).
 // DRIFT: the problem has an extra drift omega; sp then also holds b . grad gamma + div b
 // (b = omega / alpha) and b_out receives b(y).
+// The fields coeffs evaluated (alpha and Phi with gradient and Laplacian, sigma's value):
+// the alpha adjoint reuses them for d sigma' / d alpha instead of evaluating them again.
+template <typename R>
+struct FieldsAt {
+  FieldVal<R> A, Ph;
+  R S;
+};
+
 template <int DIM, typename R, bool DRIFT = false>
 WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_out = nullptr,
-                   R* alpha_out = nullptr, R* b_out = nullptr) {
+                   R* alpha_out = nullptr, R* b_out = nullptr, FieldsAt<R>* raw = nullptr) {
   FieldVal<R> A = WOS_FIELD(P, FLD_ALPHA, P.alpha, y[0], y[1], y[2], true);
   FieldVal<R> Ph = WOS_FIELD(P, FLD_PHI, P.phi, y[0], y[1], y[2], true);
   FieldVal<R> S = WOS_FIELD(P, FLD_SIGMA, P.sigma, y[0], y[1], y[2], false);
@@ -354,6 +362,11 @@ WOS_HD void coeffs(const DevProblem<R>& P, const R* y, R* sp, R* fp, R* gamma_ou
   *fp = w_exp(gam) * f * ia;
   if (gamma_out) *gamma_out = gam;
   if (alpha_out) *alpha_out = A.v;
+  if (raw) {
+    raw->A = A;
+    raw->Ph = Ph;
+    raw->S = S.v;
+  }
   if (DRIFT) {
     // sigma'' = sigma' + b . grad gamma; div b = div omega / alpha - omega . grad alpha / alpha^2
     R divw = R(0), wga = R(0), bg = R(0);

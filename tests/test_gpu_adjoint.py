@@ -205,3 +205,36 @@ def test_sigma_adjoint_matches_fd_grid_reference(wos, orc):
     # Monte Carlo noise (2 sigma) plus the reference's discretisation error (5% allowance)
     assert err <= 2.0 * noise + 0.05 * np.linalg.norm(g_fd), (err, noise, np.linalg.norm(g_fd))
     assert err <= 0.15 * np.linalg.norm(g_fd)
+
+
+def test_specialised_adjoints_equal_the_generic_ones(wos, orc, setup):
+    """WOS_SPEC_ADJOINT: the replay kernels compiled for the problem's fields give the
+    generic kernels' gradients (FP64 to summation-order rounding; FP32 to its rounding) and,
+    in FP64, the oracle's common-random-number central differences."""
+    sig, desc, sb, pts, grad_u = setup
+    ctx = wos.Context(0)
+    d = dict(desc)
+    d["sigma"] = dict(desc["sigma"], data=torch.from_numpy(sig).cuda())
+    gen = ctx.problem(d)
+    spec = ctx.problem(d, specialize=(("fp32", "fp64"), ("plain", "adjoint")))
+    assert spec.specialized() & wos.WOS_SPEC_ADJOINT
+    p = torch.from_numpy(pts).cuda()
+    gu = torch.from_numpy(grad_u).cuda()
+    na = W.inverse_alpha_grid().size
+    for precision, rtol in (("fp64", 1e-10), ("fp32", 2e-4)):
+        out = {}
+        for name, prob in (("gen", gen), ("spec", spec)):
+            gs = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+            ga = torch.zeros(na, dtype=torch.float64, device="cuda")
+            ctx.adjoint_sigma(prob, p, 32, gu, gs, 1e-4, sb, seed=9, precision=precision)
+            ctx.adjoint_alpha(prob, p, 32, gu, ga, 1e-4, sb, seed=9, precision=precision)
+            out[name] = (gs.cpu().numpy(), ga.cpu().numpy())
+        for k in range(2):
+            a, b = out["gen"][k], out["spec"][k]
+            assert np.allclose(b, a, rtol=rtol, atol=rtol * np.abs(a).max()), (precision, k)
+    gs = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+    ctx.adjoint_sigma(spec, p, 32, gu, gs, 1e-4, sb, seed=9, precision="fp64")
+    g = gs.cpu().numpy()
+    for node in pick_nodes(sig, pts, k=3):
+        fd = oracle_fd(orc, sig, pts, grad_u, node, 32, 9, sb, h=1e-3)
+        assert g[node] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(g).max())

@@ -138,3 +138,34 @@ def test_autotune_keeps_a_candidate_and_the_results(wos, setup):
     with pytest.raises(wos.WosError):
         ctx.batch_autotune(batch, dpts, wt, 1e-3, trial_shift=17)
     batch.set_schedule()
+
+
+def test_specialised_batch_runs_the_same_walks(wos, orc, setup):
+    """wos_batch_specialize: the batched kernel with the shared fields compiled in gives the
+    generic batched kernel's walks (FP64 sums to rounding, counts exact, both register caps)
+    and the oracle's statistics in FP32."""
+    ctx, probs, pts, offs, walks, sbs, batch = setup
+    hp = [ctx.problem(p) for p in probs]
+    spec = ctx.batch(hp, offs, sbs).specialize(("fp32", "fp64"))
+    flags, uniform = spec.specialized()
+    assert flags & wos.WOS_SPEC_FP32 and flags & wos.WOS_SPEC_FP64 and uniform == 0x3f
+    p = torch.from_numpy(pts).cuda()
+    w = torch.from_numpy(walks).cuda()
+    ref, _ = ctx.solve_batch(batch, p, w, 1e-3, seed=41, precision="fp64")
+    for regs in (0, 1):
+        spec.set_schedule(regs_variant=regs)
+        got, _ = ctx.solve_batch(spec, p, w, 1e-3, seed=41, precision="fp64")
+        assert torch.equal(got[2], ref[2])
+        assert torch.allclose(got[0], ref[0], rtol=1e-9, atol=1e-10)
+    acc, st = ctx.solve_batch(spec, p, 512, 1e-3, seed=42)
+    mean, var, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+    s = wos.stats_dict(st)
+    assert s["walks"] == 512 * pts.shape[1] and s["capped"] == 0 and s["nonfinite"] == 0
+    zs = []
+    for k in range(len(probs)):
+        a, b = offs[k], offs[k + 1]
+        oacc, _ = orc.solve(probs[k], pts[:, a:b], 512, seed=43, eps=1e-3, sigma_bar=sbs[k])
+        om, ov, ose = orc.finalize(oacc)
+        zs.append(combined_z(mean[a:b], se[a:b], om, ose))
+    ok, nout, mz = four_se_rule(np.concatenate(zs))
+    assert ok, (nout, mz)

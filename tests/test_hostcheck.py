@@ -239,3 +239,15 @@ def test_mixture_sample_matches_oracle(hc, orc, dim, lam):
                     assert out[2 * i] == pytest.approx(want, rel=1e-6, abs=1e-7)
                 f = orc.green_pdf(dim, R, sb, r32) * R
                 assert out[2 * i + 1] == pytest.approx(f / (lam * f + 1 - lam), rel=1e-4, abs=1e-5)
+
+
+def test_fp32_uniform_from_bits(hc):
+    """The FP32 uniform is ((x >> 9) + 1/2) 2^-23 exactly: inside (0, 1), symmetric about 1/2,
+    and equal to the conversion formula it replaces."""
+    x = np.concatenate([np.array([0, 1, 511, 512, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 513, 2 ** 32 - 1], dtype=np.uint64),
+                        np.random.default_rng(3).integers(0, 2 ** 32, size=4096, dtype=np.uint64)]).astype(np.uint32)
+    out = np.zeros(len(x))
+    hc.wos_hc_uniform_f32(x.ctypes.data_as(C.POINTER(C.c_uint32)), len(x), out.ctypes.data_as(DP))
+    want = ((x.astype(np.float64) // 512) + 0.5) / 2 ** 23
+    assert np.array_equal(out, want)
+    assert out.min() == 2.0 ** -24 and out.max() == 1 - 2.0 ** -24

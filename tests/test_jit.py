@@ -70,7 +70,8 @@ extern "C" void eval_field(int id, const double* x, double* out) {
 
 def _host_fields(wos, desc, tmp_path, name):
     """The generated field code of desc compiled by g++ (FP64), as a callable."""
-    src = wos.jit_source(desc).replace('#include "wos_walk_impl.cuh"', '#include "wos_problem.cuh"')
+    src = (wos.jit_source(desc).replace('#include "wos_walk_impl.cuh"', '#include "wos_problem.cuh"')
+           .replace('#include "wos_adjoint_impl.cuh"', ''))
     cpp = tmp_path / f"jit_{name}.cpp"
     so = tmp_path / f"jit_{name}.so"
     cpp.write_text(HARNESS % {"source": src, "dim": desc["dim"]})
@@ -181,3 +182,38 @@ def test_invalid_descriptions_are_refused(wos):
     assert rc == wos.WOS_EINVAL and "dim" in log
     with pytest.raises(KeyError):
         wos.spec_flags("fp16")
+
+
+def test_batch_source_shares_uniform_fields_and_compiles(wos):
+    """A batch's specialised program: fields that every problem shares are generated code
+    (grids read the walk's own problem's grid), a field that differs between problems calls
+    the field interpreter; both precisions compile for sm_103a (no device)."""
+    probs, pts, offs, walks = W.batch_problems(6, seed=5, max_points=8, min_points=4, min_walks=8, max_walks=16)
+    src = wos.jit_batch_source(probs)
+    assert "field_eval<DIM>(P, P." not in src                       # all six fields shared
+    assert "grid_bspline<DIM>(P.alpha" in src and "grid_linear<DIM>(P.sigma" in src
+    assert "R(0x1.921fb54442d18p+1)" in src                         # g = cos(pi x) y folded in
+    for prec in ("fp32", "fp64"):
+        rc, log, nbytes = wos.jit_batch_compile(probs, prec)
+        assert rc == 0 and nbytes > 0, log
+    # a g that differs between problems keeps the interpreter for g only
+    other = [dict(p) for p in probs]
+    other[3]["g"] = W.sst(W.term(2.0, (COS, 3.0, 0.0), (LIN, 1.0, 0.0)))
+    src = wos.jit_batch_source(other)
+    assert "case FLD_G:\n    return field_eval<DIM>(P, P.g" in src
+    assert "field_eval<DIM>(P, P.alpha" not in src
+    rc, log, nbytes = wos.jit_batch_compile(other, "fp32")
+    assert rc == 0, log
+    # sources that differ in being manufactured cannot share one kernel
+    mixed = [W.rounded_box_problem(), W.noise_annulus_problem()]
+    rc, log, _ = wos.jit_batch_compile(mixed, "fp32")
+    assert rc == wos.WOS_EUNSUPPORTED and "manufactured" in log
+
+
+def test_adjoint_kernels_compile_for_the_inverse_problem(wos):
+    """WOS_SPEC_ADJOINT compiles the sigma and alpha replay kernels with the problem's fields
+    (both precisions, sm_103a, no device)."""
+    desc = W.inverse_problem(W.inverse_sigma_grid())
+    for prec in ("fp32", "fp64"):
+        rc, log, nbytes = wos.jit_compile(desc, prec, ("plain", "adjoint"))
+        assert rc == 0 and nbytes > 0, log

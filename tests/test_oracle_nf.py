@@ -156,3 +156,4 @@ def test_next_flight_in_shell_returns_boundary_value(orc):
     u, k, m, fl = orc.walk_nf(prob, np.array([0.5, 1e-4]), 0, 0, 0, 1e-3, sb)
     d, xb = orc.distance(prob, np.array([0.5, 1e-4]))
     assert k == 0 and m == 0 and abs(u - W.square2d_exact(*xb)) <= 1e-12
+
