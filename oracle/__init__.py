@@ -124,11 +124,17 @@ def _load():
     lib.orc_offcentre_G.restype = C.c_double
     lib.orc_offcentre_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp]
     lib.orc_offcentre_P.restype = C.c_double
+    lib.orc_series_G.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_int]
+    lib.orc_series_G.restype = C.c_double
+    lib.orc_series_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_int]
+    lib.orc_series_P.restype = C.c_double
     lib.orc_walk_nf.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double, C.c_int64,
-                                C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+                                C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int32)]
     lib.orc_walk_nf.restype = C.c_double
     lib.orc_walks_nf.argtypes = [pp, dp, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_double, C.c_double,
-                                 C.c_int64, C.c_int64, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]
+                                 C.c_int64, C.c_int64, C.c_int32, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.c_int]
     lib.orc_mesh_prepare.argtypes = [pp]
     lib.orc_mesh_release.argtypes = [pp]
     lib.orc_mesh_distance_brute.argtypes = [pp, dp, dp]
@@ -486,19 +492,35 @@ def offcentre_P(dim, R, sb, u, v):
     return _load().orc_offcentre_P(dim, R, sb, _dptr(uu), _dptr(vv))
 
 
-def walk_nf(prob, x0, point, walk_id, seed, eps, sigma_bar, max_steps=1 << 20, max_inner=1 << 16, packed=None):
-    """(u estimate, outer steps, inner iterations, flags) of one next-flight walk."""
+def series_G(dim, R, sb, u, v, nterms=0):
+    """Off-centred G(x, y) on the ball as the series of Supplemental 1.2 (nterms = 0: to rounding)."""
+    uu, vv = np.zeros(3), np.zeros(3)
+    uu[:dim], vv[:dim] = u, v
+    return _load().orc_series_G(dim, R, sb, _dptr(uu), _dptr(vv), nterms)
+
+
+def series_P(dim, R, sb, u, v, nterms=0):
+    """Off-centred P(x, z) on the sphere as the series of Supplemental 1.2 (nterms = 0: to rounding)."""
+    uu, vv = np.zeros(3), np.zeros(3)
+    uu[:dim], vv[:dim] = u, v
+    return _load().orc_series_P(dim, R, sb, _dptr(uu), _dptr(vv), nterms)
+
+
+def walk_nf(prob, x0, point, walk_id, seed, eps, sigma_bar, max_steps=1 << 20, max_inner=1 << 16, packed=None,
+            series_terms=0):
+    """(u estimate, outer steps, inner iterations, flags) of one next-flight walk; series_terms > 0
+    takes the series G and P with that many terms instead of the printed approximations."""
     pk = packed or pack(prob)
     xx = np.zeros(3)
     xx[: len(x0)] = x0
     k, m, fl = C.c_int64(), C.c_int64(), C.c_int32()
     u = _load().orc_walk_nf(pk.ptr, _dptr(xx), point, walk_id, seed, eps, sigma_bar, max_steps, max_inner,
-                            C.byref(k), C.byref(m), C.byref(fl))
+                            series_terms, C.byref(k), C.byref(m), C.byref(fl))
     return u, k.value, m.value, fl.value
 
 
 def walks_nf(prob, pts, walks_per_point, seed, eps, sigma_bar, walk_offset=0, max_steps=1 << 20,
-             max_inner=1 << 16, nthreads=0):
+             max_inner=1 << 16, nthreads=0, series_terms=0):
     """Per-walk next-flight estimates [npts, walks], outer steps and inner iterations."""
     lib = _load()
     pk = pack(prob)
@@ -508,7 +530,7 @@ def walks_nf(prob, pts, walks_per_point, seed, eps, sigma_bar, walk_offset=0, ma
     st = np.zeros((npts, walks_per_point), dtype=np.int64)
     inn = np.zeros((npts, walks_per_point), dtype=np.int64)
     rc = lib.orc_walks_nf(pk.ptr, _dptr(pts), npts, walks_per_point, walk_offset, seed, eps, sigma_bar, max_steps,
-                          max_inner, _dptr(uh), st.ctypes.data_as(C.POINTER(C.c_int64)),
+                          max_inner, series_terms, _dptr(uh), st.ctypes.data_as(C.POINTER(C.c_int64)),
                           inn.ctypes.data_as(C.POINTER(C.c_int64)), nthreads)
     if rc != 0:
         raise ValueError("orc_walks_nf rejected its inputs")

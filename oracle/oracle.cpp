@@ -1545,9 +1545,162 @@ double orc_offcentre_P(int dim, double R, double sb, const double* u, const doub
   return c * (nf_V(dim, R, sb, nw) * (nv * nv - uv) / (nw * nv) + nf_V(dim, R, sb, img) * uv / (R * nv));
 }
 
+// ---------------------------------------------------------------------------
+// Supplemental Sec. 1.2, the off-centred Green's function and Poisson kernel as the
+// printed infinite series (Legendre polynomials in 3D, cosines in 2D, with modified
+// Bessel functions of the two distances and of R sqrt(sigma_bar)).  Written here in
+// the form G = Phi(|x - y|) - H(x, y): the free-space kernel Phi (its addition
+// theorem is the part of the printed series in I(r<) K(r>)) in closed form, and the
+// regular part H (the part in K(R)/I(R)) as the series, whose terms shrink like
+// (r1 r2 / R^2)^n.  With k = sqrt(sigma_bar), a = kR, z = k r:
+//   3D: Phi = e^{-kd} / (4 pi d),  H = 1/(4 pi R) sum_n (2n+1) P_n(cos theta) p_n t_n(z1) t_n(z2),
+//   2D: Phi = K_0(kd) / (2 pi),    H = 1/(2 pi) sum_{n in Z} cos(n theta) p_n t_n(z1) t_n(z2),
+// t_n(z) = i_n(z)/i_n(a) (3D, modified spherical Bessel) or I_n(z)/I_n(a) (2D), and
+// p_n = a k_n(a) i_n(a) (3D) or I_n(a) K_n(a) (2D).  The Poisson kernel is the inward
+// normal derivative of G at |y - c| = R; term by term the Wronskians
+// i_n k_n' - i_n' k_n = -1/z^2 and I_n K_n' - I_n' K_n = -1/z leave
+//   3D: P = 1/(4 pi R^2) sum_n (2n+1) P_n(cos theta) t_n(k |x - c|),
+//   2D: P = 1/(2 pi R) sum_{n in Z} cos(n theta) t_n(k |x - c|).
+// nterms > 0 keeps n = 0 .. nterms - 1 (2D: |n| < nterms); nterms = 0 sums until
+// the terms are below rounding.  sigma_bar = 0 takes the Laplace coefficients
+// (t_n = (r/R)^n, 3D p_n = 1/(2n+1); 2D: Phi = -ln(d)/(2 pi), the n = 0 term of H
+// -ln(R)/(2 pi), p_n = 1/(2|n|)).
+// Every Bessel value comes from its defining power series, summed in logarithms
+// (no cancellation: all terms are positive), except K_n of 2D, which runs the
+// three-term recurrence upwards from the library's K_0 and K_1 (the stable
+// direction for K).
+namespace {
+
+// ln I_n(z) (2D) or ln i_n(z) (3D), z > 0:
+//   I_n(z) = (z/2)^n sum_m (z^2/4)^m / (m! (n+m)!),
+//   i_n(z) = z^n / (2n+1)!! sum_m (z^2/2)^m / (m! (2n+3)(2n+5)...(2n+2m+1)).
+double ln_bessel_i(int dim, int n, double z) {
+  double sum = 1.0, term = 1.0;
+  for (int m = 1; m < 1000000; ++m) {
+    if (dim == 2) term *= (z * z / 4.0) / ((double)m * (double)(n + m));
+    else term *= (z * z / 2.0) / ((double)m * (double)(2 * n + 2 * m + 1));
+    sum += term;
+    if ((double)m > z && term < 1e-18 * sum) break;
+  }
+  if (dim == 2) return n * std::log(z / 2.0) - std::lgamma(n + 1.0) + std::log(sum);
+  const double ln_dfact = std::lgamma(2.0 * n + 2.0) - n * std::log(2.0) - std::lgamma(n + 1.0);  // (2n+1)!!
+  return n * std::log(z) - ln_dfact + std::log(sum);
+}
+
+// ln k_n(z), 3D: k_n(z) = e^{-z}/z sum_{j=0}^{n} (n+j)! / (j! (n-j)!) (2z)^{-j}
+double ln_sph_k(int n, double z) {
+  std::vector<double> lt(n + 1);
+  double mx = -INFINITY;
+  for (int j = 0; j <= n; ++j) {
+    lt[j] = std::lgamma(n + j + 1.0) - std::lgamma(j + 1.0) - std::lgamma(n - j + 1.0) - j * std::log(2.0 * z);
+    mx = std::max(mx, lt[j]);
+  }
+  double s = 0.0;
+  for (int j = 0; j <= n; ++j) s += std::exp(lt[j] - mx);
+  return -z - std::log(z) + mx + std::log(s);
+}
+
+// ln p_n for n = 0 .. N-1 on a ball with a = k R
+std::vector<double> series_ln_p(int dim, double a, int N) {
+  std::vector<double> lp(N);
+  if (dim == 3) {
+    for (int n = 0; n < N; ++n) lp[n] = std::log(a) + ln_sph_k(n, a) + ln_bessel_i(3, n, a);
+    return lp;
+  }
+  // K_{n+1} = K_{n-1} + (2n/a) K_n, carried as the ratio K_{n+1}/K_n and ln K_n
+  double lnK = std::log(bK0(a)), ratio = bK1(a) / bK0(a);
+  for (int n = 0; n < N; ++n) {
+    lp[n] = ln_bessel_i(2, n, a) + lnK;
+    lnK += std::log(ratio);
+    ratio = 2.0 * (n + 1) / a + 1.0 / ratio;
+  }
+  return lp;
+}
+
+struct SeriesGeom {
+  double r1, r2, d, mu;
+};
+SeriesGeom series_geom(int dim, const double* u, const double* v) {
+  SeriesGeom g;
+  double w[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) w[i] = v[i] - u[i];
+  g.r1 = std::sqrt(dot3(u, u, dim));
+  g.r2 = std::sqrt(dot3(v, v, dim));
+  g.d = std::sqrt(dot3(w, w, dim));
+  g.mu = (g.r1 > 0.0 && g.r2 > 0.0) ? std::fmax(-1.0, std::fmin(1.0, dot3(u, v, dim) / (g.r1 * g.r2))) : 1.0;
+  return g;
+}
+
+// angular factor of term n: 3D (2n+1) P_n(mu); 2D cos(n theta), doubled for n >= 1 (n and -n)
+double series_angle(int dim, int n, double mu) {
+  if (dim == 3) return (2.0 * n + 1.0) * std::legendre((unsigned)n, mu);
+  return (n == 0 ? 1.0 : 2.0) * std::cos(n * std::acos(mu));
+}
+
+// t_n(z) = i_n(z)/i_n(a) (or I_n), with t_n(0) = 0 for n >= 1
+double series_t(int dim, int n, double z, double ln_ia) {
+  if (z <= 0.0) return (n == 0) ? std::exp(-ln_ia) : 0.0;  // i_0(0) = I_0(0) = 1
+  return std::exp(ln_bessel_i(dim, n, z) - ln_ia);
+}
+
+const int kSeriesMaxTerms = 100000;
+}  // namespace
+
+double orc_series_G(int dim, double R, double sb, const double* u, const double* v, int nterms) {
+  const SeriesGeom g = series_geom(dim, u, v);
+  const double cd = (dim == 2) ? 1.0 / (2.0 * kPi) : 1.0 / (4.0 * kPi);
+  const int N = (nterms > 0) ? nterms : kSeriesMaxTerms;
+  double H = 0.0, phi;
+  if (sb == 0.0) {
+    const double t = g.r1 * g.r2 / (R * R);
+    phi = (dim == 2) ? -cd * std::log(g.d) : cd / g.d;
+    for (int n = 0; n < N; ++n) {
+      double c;
+      if (dim == 3) c = std::legendre((unsigned)n, g.mu) * std::pow(t, n) / R;
+      else c = (n == 0) ? -std::log(R) : std::cos(n * std::acos(g.mu)) * std::pow(t, n) / n;
+      H += cd * c;
+      if (nterms == 0 && n > 8 && std::pow(t, n) < 1e-18) break;
+    }
+    return phi - H;
+  }
+  const double k = std::sqrt(sb), a = k * R, z1 = k * g.r1, z2 = k * g.r2;
+  phi = (dim == 2) ? cd * bK0(k * g.d) : cd * std::exp(-k * g.d) / g.d;
+  int n_lp = std::min(N, 4096);
+  std::vector<double> lp = series_ln_p(dim, a, n_lp);
+  for (int n = 0; n < N; ++n) {
+    if (n >= n_lp) {  // long sums (nterms = 0 near the sphere): extend p_n
+      n_lp = std::min(N, 2 * n_lp);
+      lp = series_ln_p(dim, a, n_lp);
+    }
+    const double ln_ia = ln_bessel_i(dim, n, a);
+    const double tt = series_t(dim, n, z1, ln_ia) * series_t(dim, n, z2, ln_ia);
+    const double term = series_angle(dim, n, g.mu) * std::exp(lp[n]) * tt;
+    H += term * ((dim == 3) ? cd / R : cd);
+    if (nterms == 0 && n > 8 && std::fabs(term) * (2.0 * n + 1.0) < 1e-18 * std::fabs(H)) break;
+    if (tt == 0.0 && n > 0) break;
+  }
+  return phi - H;
+}
+
+double orc_series_P(int dim, double R, double sb, const double* u, const double* v, int nterms) {
+  const SeriesGeom g = series_geom(dim, u, v);
+  const double cd = (dim == 2) ? 1.0 / (2.0 * kPi * R) : 1.0 / (4.0 * kPi * R * R);
+  const int N = (nterms > 0) ? nterms : kSeriesMaxTerms;
+  const double k = std::sqrt(sb), a = k * R, z1 = k * g.r1, s = g.r1 / R;
+  double P = 0.0;
+  for (int n = 0; n < N; ++n) {
+    const double t = (sb == 0.0) ? std::pow(s, n) : series_t(dim, n, z1, ln_bessel_i(dim, n, a));
+    const double term = series_angle(dim, n, g.mu) * t;
+    P += cd * term;
+    if (nterms == 0 && n > 8 && std::fabs(term) < 1e-18 * std::fabs(P / cd)) break;
+    if (t == 0.0 && n > 0) break;
+  }
+  return P;
+}
+
 double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint32_t walk, uint64_t seed,
-                   double eps, double sb, int64_t max_steps, int64_t max_inner, int64_t* steps_out,
-                   int64_t* inner_out, int32_t* flags_out) {
+                   double eps, double sb, int64_t max_steps, int64_t max_inner, int32_t series_terms,
+                   int64_t* steps_out, int64_t* inner_out, int32_t* flags_out) {
   int dim = P->dim;
   if (has_drift(P)) return NAN;  // the off-centred series here has no extra-drift term
   double x[3] = {0, 0, 0};
@@ -1590,7 +1743,10 @@ double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint3
     double uc[3] = {0, 0, 0};  // current sample point minus the ball centre
     double T = 1.0, Ttr = 0.0, Tsrc = 0.0;
     for (int64_t j = 0;; ++j) {
-      Ttr += orc_offcentre_P(dim, R, sb, uc, vz) * area * T;  // P(x_c, z) / p(z)
+      // P(x_c, z) / p(z): the printed approximation, or the series of series_terms terms
+      const double Pv = (series_terms > 0) ? orc_series_P(dim, R, sb, uc, vz, series_terms)
+                                           : orc_offcentre_P(dim, R, sb, uc, vz);
+      Ttr += Pv * area * T;
       ctr[3] = (uint32_t)(j + 1);
       philox(ctr, key, o);
       double pRR = std::fmin(1.0, std::fabs(T));
@@ -1616,7 +1772,9 @@ double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint3
       for (int i = 0; i < dim; ++i) y[i] = x[i] + vn[i];
       double gam_y, sp_y, fp_y, f_y, a_y;
       coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
-      double Gv = orc_offcentre_G(dim, R, sb, uc, vn) * vol;  // G(x_c, x_n) / p(x_n)
+      // G(x_c, x_n) / p(x_n)
+      double Gv = ((series_terms > 0) ? orc_series_G(dim, R, sb, uc, vn, series_terms)
+                                      : orc_offcentre_G(dim, R, sb, uc, vn)) * vol;
       // source: f'(x_n) / (sigma_bar - sigma'(x_n)) times the updated throughput
       Tsrc += fp_y * Gv * T;
       T *= Gv * (sb - sp_y);
@@ -1636,9 +1794,9 @@ double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint3
 }
 
 int orc_walks_nf(const orc_problem* P, const double* pts, int64_t npts, int32_t wpp, uint64_t walk_offset,
-                 uint64_t seed, double eps, double sb, int64_t max_steps, int64_t max_inner, double* uhat,
-                 int64_t* steps, int64_t* inner, int nthreads) {
-  if (!(sb > 0.0) || !(eps > 0.0)) return -1;
+                 uint64_t seed, double eps, double sb, int64_t max_steps, int64_t max_inner, int32_t series_terms,
+                 double* uhat, int64_t* steps, int64_t* inner, int nthreads) {
+  if (!(sb > 0.0) || !(eps > 0.0) || series_terms < 0) return -1;
   int dim = P->dim;
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
@@ -1649,7 +1807,7 @@ int orc_walks_nf(const orc_problem* P, const double* pts, int64_t npts, int32_t 
       int64_t i = p * wpp + j, k, m;
       int32_t fl;
       uhat[i] = orc_walk_nf(P, x0, (uint32_t)p, (uint32_t)(walk_offset + j), seed, eps, sb, max_steps, max_inner,
-                            &k, &m, &fl);
+                            series_terms, &k, &m, &fl);
       steps[i] = k;
       inner[i] = m;
     }

@@ -207,17 +207,26 @@ int orc_walks_grad(const orc_problem* prob, const double* pts, int64_t npts, int
    Exact at u = 0. */
 double orc_offcentre_G(int dim, double R, double sigma_bar, const double* u, const double* v);
 double orc_offcentre_P(int dim, double R, double sigma_bar, const double* u, const double* v);
+/* The off-centred G and P as the series of Supplemental 1.2 (Legendre polynomials in
+   3D, cosines in 2D, modified Bessel functions), G written as the closed-form
+   free-space kernel minus the series of its regular part; nterms > 0 keeps the
+   terms n < nterms (2D: |n| < nterms), nterms = 0 sums to rounding.  Same
+   arguments and scaling as orc_offcentre_G / _P; sigma_bar = 0 gives Laplace's. */
+double orc_series_G(int dim, double R, double sigma_bar, const double* u, const double* v, int nterms);
+double orc_series_P(int dim, double R, double sigma_bar, const double* u, const double* v, int nterms);
 /* One next-flight walk.  Randoms: outer step k draws the exit point z from Philox
    block (point, walk, k, 0); inner iteration j of that ball draws its roulette
    uniform and its uniform in-ball point from block (point, walk, k, j + 1).
    steps_out = outer steps (distance queries), inner_out = inner iterations; flags
-   bit 0 = outer step cap, bit 1 = non-finite, bit 2 = inner cap hit. */
+   bit 0 = outer step cap, bit 1 = non-finite, bit 2 = inner cap hit.
+   series_terms = 0: the printed approximate G and P; > 0: the series with that
+   many terms (orc_series_G / _P). */
 double orc_walk_nf(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk, uint64_t seed,
-                   double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, int64_t* steps_out,
-                   int64_t* inner_out, int32_t* flags_out);
+                   double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, int32_t series_terms,
+                   int64_t* steps_out, int64_t* inner_out, int32_t* flags_out);
 int orc_walks_nf(const orc_problem* prob, const double* pts, int64_t npts, int32_t wpp, uint64_t walk_offset,
-                 uint64_t seed, double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, double* uhat,
-                 int64_t* steps, int64_t* inner, int nthreads);
+                 uint64_t seed, double eps, double sigma_bar, int64_t max_steps, int64_t max_inner,
+                 int32_t series_terms, double* uhat, int64_t* steps, int64_t* inner, int nthreads);
 
 /* Many walks: pts SoA [dim][npts].  walks[p] (or walks_uniform if walks == NULL)
    walks per point with ids walk_offset .. walk_offset + walks - 1, accumulated
