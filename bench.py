@@ -51,11 +51,12 @@ MUFU_OPS_PER_STEP = 27
 ISSUE_OPS_PER_STEP = LANE_OPS_PER_STEP + MUFU_OPS_PER_STEP
 RMS_TARGET = 1e-2
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one launch of the specialised walk kernel on this workload,
-# from the ncu capture summarised in profiles/wos_walk_spec_kernel_cube3d.md (9.53 MB read,
-# 0 written: the points and the radial table; walk state stays in registers).  Reported only
-# for the configuration that capture measured; re-take it whenever the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 9.528320e6
+# DRAM bytes (read + write) of one launch of the specialised walk kernel on the 64^3-point
+# workload, from the ncu capture summarised in profiles/wos_walk_spec_kernel_cube3d.md:
+# 9.85 MB read, 0 written, at 64 walks per point.  The bytes are per point (the points, the
+# accumulators, the radial table); walk state stays in registers, so the 1024-walk launch
+# moves the same bytes.  Reported for 64^3 points only; re-take it whenever the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 9.853440e6
 
 
 def measure_unit_peaks(ctx):
@@ -410,7 +411,7 @@ def run_ours(args):
     steps_per_s_kernel = (st["steps"] / args.steps) / (kernel_ms * 1e-3)
     achieved = ISSUE_OPS_PER_STEP * steps_per_s_kernel
     peak_lanes = peaks["fp32_lanes_per_s"]
-    captured = args.kernel == "specialised" and GRID == 64 and WALKS == 1024
+    captured = args.kernel == "specialised" and GRID == 64
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lanes / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_lanes, "traffic": TRAFFIC_BYTES_PER_LAUNCH if captured else None,
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
@@ -774,7 +775,7 @@ def run_other(args):
             "config": cfg, "steps_per_walk": stv["steps"] / max(stv["walks"], 1),
             "points_per_s": npts / (ms * 1e-3), "walks_per_s": stv["walks"] / (ms * 1e-3),
             "capped_walks": stv["capped"], "nonfinite_walks": stv["nonfinite"],
-            "kernel": args.kernel if wl not in ("batch", "nf") else "generic", "specialise_compile_s": JIT["compile_s"]}
+            "kernel": args.kernel if wl != "nf" else "generic", "specialise_compile_s": JIT["compile_s"]}
     line.update(extra)
     print(json.dumps(line))
     return 0
