@@ -312,30 +312,42 @@ int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* prob, const float* 
                             int32_t walks_per_point, const wos_params* params, double* uhat,
                             double* grad_hat, int64_t* steps, uint64_t* stats, void* stream);
 
-/* Next-flight walk on spheres (Sec. 5.2, Supplemental Algorithm 2) with the
-   approximate off-centred Green's function and Poisson kernel of Supplemental 1.2.
+/* Next-flight walk on spheres (Sec. 5.2, Supplemental Algorithm 2).
    One distance query per ball; in ball B(x) of radius R the walk draws one exit
    point z uniform on the sphere and sums the boundary series
    T_tr = sum_j P(x^j, z)|dB| prod_{l<j} theta_l and the source series
    T_src = sum_{j>=1} f'(x^j) G(x^{j-1}, x^j)|B| prod_{l<j-1} theta_l over uniform
    in-ball points x^j, theta_l = G(x^l, x^{l+1}) |B| (sigma_bar - sigma'(x^{l+1})),
    with Russian roulette of probability min(1, |throughput|) ending the series; the
-   walk adds W T_src, sets W *= T_tr and moves to z.  The approximations are exact
-   at the ball centre only, so the estimate is biased where sigma' < sigma_bar;
-   exact when sigma' = sigma_bar everywhere.  Randoms: ball k of walk (p, w) uses
-   Philox block (p, w, k, 0) for z and block (p, w, k, j + 1) for inner iteration j.
-   max_inner (>= 1) caps a ball's iterations (the walk is then counted as capped).
+   walk adds W T_src, sets W *= T_tr and moves to z.  Randoms: ball k of walk (p, w)
+   uses Philox block (p, w, k, 0) for z and block (p, w, k, j + 1) for inner
+   iteration j.  max_inner (>= 1) caps a ball's iterations (the walk is then counted
+   as capped).
+   series_terms selects the off-centred G and P (Supplemental 1.2):
+     0      the printed approximations: exact at the ball centre only, so the estimate
+            is biased where sigma' < sigma_bar (exact when sigma' = sigma_bar
+            everywhere), and the approximate P is not integrable near the exit point;
+     1..WOS_NF_SERIES_MAX  the printed series with that many terms (n < N in 3D,
+            |n| < N in 2D), G as the closed-form free-space kernel minus its regular
+            part's series: the exact kernels projected on angular harmonics of degree
+            < N, so the estimate's mean is exact for boundary values and sources
+            without higher harmonics on the balls' spheres, and P stays bounded
+            (about N^2 / |dB|), which keeps the variance finite.  Each inner iteration
+            then sums both series in one sweep of about N + 12 + sqrt(sigma_bar) R
+            terms.
    Arguments and results as wos_solve (stats: steps = balls, WOS_STAT_INNER = inner
-   iterations).  Errors: as wos_solve; WOS_EINVAL if max_inner < 1;
-   WOS_EUNSUPPORTED with a weight window. */
+   iterations).  Errors: as wos_solve; WOS_EINVAL if max_inner < 1 or series_terms
+   is outside [0, WOS_NF_SERIES_MAX]; WOS_EUNSUPPORTED with a weight window. */
+#define WOS_NF_SERIES_MAX 64
 int wos_solve_nf(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
                  const int32_t* walks, int32_t walks_uniform, const wos_params* params, int64_t max_inner,
-                 double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream);
+                 int32_t series_terms, double* sum, double* sumsq, int64_t* count, uint64_t* stats,
+                 void* stream);
 
 /* As wos_walk_estimates for next-flight walks (uhat, steps = balls per walk). */
 int wos_walk_estimates_nf(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts,
                           int32_t walks_per_point, const wos_params* params, int64_t max_inner,
-                          double* uhat, int64_t* steps, uint64_t* stats, void* stream);
+                          int32_t series_terms, double* uhat, int64_t* steps, uint64_t* stats, void* stream);
 
 /* Per-point mean, unbiased sample variance of one walk's estimate, and standard
    error of the mean from the accumulators (Sec. 2.2: the estimate is the average

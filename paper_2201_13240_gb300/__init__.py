@@ -128,8 +128,8 @@ def load():
     lib.wos_finalize.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
     lib.wos_slice_points.argtypes = [vp, vp, C.POINTER(ViewDesc), vp, vp]
     lib.wos_render_slice.argtypes = [vp, vp, C.POINTER(ViewDesc), vp, vp, vp, vp, vp, vp]
-    lib.wos_solve_nf.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), i64, vp, vp, vp, vp, vp]
-    lib.wos_walk_estimates_nf.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), i64, vp, vp, vp, vp]
+    lib.wos_solve_nf.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), i64, i32, vp, vp, vp, vp, vp]
+    lib.wos_walk_estimates_nf.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), i64, i32, vp, vp, vp, vp]
     lib.wos_solve_grad.argtypes = [vp, vp, vp, i64, vp, i32, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
     lib.wos_walk_grad_estimates.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
     lib.wos_solve_host.argtypes = [vp, vp, vp, i64, i32, C.POINTER(Params), vp, vp, vp, vp, vp]
@@ -772,9 +772,10 @@ class Context:
         return img, val, dep
 
     def solve_nf(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
-                 max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None):
+                 max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None, series_terms=0):
         """Next-flight walks (Sec. 5.2) added to the accumulators; stats 'steps' counts balls
-        (distance queries), 'inner' the in-ball iterations."""
+        (distance queries), 'inner' the in-ball iterations.  series_terms = 0 takes the printed
+        approximate off-centred kernels, N in 1..64 their series with N terms."""
         import torch
         pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
@@ -795,12 +796,13 @@ class Context:
             wp, wu = _ptr(walks), 0
         p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
         self._check(self.lib.wos_solve_nf(self.handle, prob.handle, _ptr(pts), npts, wp, wu, C.byref(p),
-                                          int(max_inner), _ptr(accum[0]), _ptr(accum[1]), _ptr(accum[2]),
+                                          int(max_inner), int(series_terms), _ptr(accum[0]), _ptr(accum[1]),
+                                          _ptr(accum[2]),
                                           _ptr(stats), _stream(stream)))
         return accum, stats
 
     def walk_estimates_nf(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0,
-                          max_steps=1 << 20, max_inner=1 << 16, precision="fp32", stream=None):
+                          max_steps=1 << 20, max_inner=1 << 16, precision="fp32", stream=None, series_terms=0):
         import torch
         pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
@@ -810,7 +812,8 @@ class Context:
         stats = self.new_stats()
         p = params(eps, sigma_bar, seed, walk_offset, max_steps, precision)
         self._check(self.lib.wos_walk_estimates_nf(self.handle, prob.handle, _ptr(pts), npts, int(walks_per_point),
-                                                   C.byref(p), int(max_inner), _ptr(uhat), _ptr(steps),
+                                                   C.byref(p), int(max_inner), int(series_terms), _ptr(uhat),
+                                                   _ptr(steps),
                                                    _ptr(stats), _stream(stream)))
         return uhat, steps, stats
 

@@ -395,7 +395,8 @@ int no_window(wos_ctx* ctx, const wos_params* prm) {
 int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts, const int64_t* walk_end,
            int64_t walks_uniform, uint64_t total, const wos_params* prm, double* sum, double* sumsq,
            int64_t* count, uint64_t* stats, double* uhat, int64_t* steps, cudaStream_t st,
-           double* gsum = nullptr, double* gsumsq = nullptr, double* ghat = nullptr, int64_t nf_max_inner = 0) {
+           double* gsum = nullptr, double* gsumsq = nullptr, double* ghat = nullptr, int64_t nf_max_inner = 0,
+           int32_t nf_series = 0) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(work counter)");
   unsigned long long* st_ptr = reinterpret_cast<unsigned long long*>(stats);
@@ -433,6 +434,7 @@ int launch(wos_ctx* ctx, const wos_problem* prob, const float* pts, int64_t npts
   L.gsumsq = gsumsq;
   L.ghat = ghat;
   L.nf_max_inner = nf_max_inner;
+  L.nf_series = nf_series;
   L.drift = prob->host64.has_drift;
   const bool nf = nf_max_inner > 0;
   if (L.drift && (nf || gsum || ghat || prm->ww_lo != 0.0))
@@ -836,15 +838,19 @@ int wos_solve_grad(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_
                 nullptr, st, grad_sum, grad_sumsq, nullptr);
 }
 
+static_assert(WOS_NF_SERIES_MAX == wos::kNfSeriesMax, "series table size");
+
 int wos_solve_nf(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, const int32_t* walks,
-                 int32_t walks_uniform, const wos_params* prm, int64_t max_inner, double* sum, double* sumsq,
-                 int64_t* count, uint64_t* stats, void* stream) {
+                 int32_t walks_uniform, const wos_params* prm, int64_t max_inner, int32_t series_terms,
+                 double* sum, double* sumsq, int64_t* count, uint64_t* stats, void* stream) {
   if (!ctx) return WOS_EINVAL;
   if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
   int rc = validate_params(ctx, prm);
   if (rc) return rc;
   if ((rc = no_window(ctx, prm))) return rc;
   if (max_inner < 1) return fail(ctx, WOS_EINVAL, "max_inner must be >= 1");
+  if (series_terms < 0 || series_terms > WOS_NF_SERIES_MAX)
+    return fail(ctx, WOS_EINVAL, "series_terms must be in [0, WOS_NF_SERIES_MAX]");
   if (npts < 0) return fail(ctx, WOS_EINVAL, "npts < 0");
   if (npts == 0) return WOS_OK;
   if (npts > 0xffffffffll) return fail(ctx, WOS_EINVAL, "more than 2^32 points in one call");
@@ -867,24 +873,27 @@ int wos_solve_nf(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t 
     total = (uint64_t)npts * (uint64_t)walks_uniform;
   }
   return launch(ctx, pr, pts, npts, walk_end, walks_uniform, total, prm, sum, sumsq, count, stats, nullptr,
-                nullptr, st, nullptr, nullptr, nullptr, max_inner);
+                nullptr, st, nullptr, nullptr, nullptr, max_inner, series_terms);
 }
 
 int wos_walk_estimates_nf(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,
-                          const wos_params* prm, int64_t max_inner, double* uhat, int64_t* steps, uint64_t* stats,
-                          void* stream) {
+                          const wos_params* prm, int64_t max_inner, int32_t series_terms, double* uhat,
+                          int64_t* steps, uint64_t* stats, void* stream) {
   if (!ctx) return WOS_EINVAL;
   if (!pr) return fail(ctx, WOS_EINVAL, "null problem");
   int rc = validate_params(ctx, prm);
   if (rc) return rc;
   if ((rc = no_window(ctx, prm))) return rc;
   if (max_inner < 1) return fail(ctx, WOS_EINVAL, "max_inner must be >= 1");
+  if (series_terms < 0 || series_terms > WOS_NF_SERIES_MAX)
+    return fail(ctx, WOS_EINVAL, "series_terms must be in [0, WOS_NF_SERIES_MAX]");
   if (npts < 0 || wpp < 0) return fail(ctx, WOS_EINVAL, "negative size");
   if (npts == 0 || wpp == 0) return WOS_OK;
   if (!pts || !uhat || !steps) return fail(ctx, WOS_EINVAL, "null device array");
   DeviceGuard g(ctx->device);
   return launch(ctx, pr, pts, npts, nullptr, wpp, (uint64_t)npts * (uint64_t)wpp, prm, nullptr, nullptr, nullptr,
-                stats, uhat, steps, static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, max_inner);
+                stats, uhat, steps, static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, max_inner,
+                series_terms);
 }
 
 int wos_walk_grad_estimates(wos_ctx* ctx, const wos_problem* pr, const float* pts, int64_t npts, int32_t wpp,

@@ -177,6 +177,45 @@ void wos_hc_offcentre(int dim, int fp64, double Rb, double sb, const double* u, 
   }
 }
 
+}  // extern "C"
+
+// next-flight series kernels (N terms): out[2i] = G(c + u_i, c + v_i), out[2i+1] = P(c + v_i, c + z_i)
+template <int DIM, typename R>
+static void hc_nf_series(double Rb, double sb, int N, const double* u, const double* v, const double* z, int64_t n,
+                         double* out) {
+  const R k = (R)std::sqrt(sb), rb = (R)Rb, a = k * rb;
+  R pn[wos::kNfSeriesMax], ra[wos::kNfSeriesMax];
+  wos::nf_series_ball<DIM, R>(a, N, pn, ra);
+  const int n0 = N + 12 + (int)std::fmin((double)a, 4096.0);
+  for (int64_t i = 0; i < n; ++i) {
+    R uu[3], vv[3], zz[3];
+    for (int d = 0; d < 3; ++d) {
+      uu[d] = (R)u[3 * i + d];
+      vv[d] = (R)v[3 * i + d];
+      zz[d] = (R)z[3 * i + d];
+    }
+    R G, P;
+    wos::nf_series_eval<DIM, R>(k, a, rb, N, n0, pn, ra, uu, vv, zz, &G, &P);
+    out[2 * i] = (double)G;
+    out[2 * i + 1] = (double)P;
+  }
+}
+
+extern "C" {
+
+int wos_hc_nf_series(int dim, int fp64, double Rb, double sb, int N, const double* u, const double* v,
+                     const double* z, int64_t n, double* out) {
+  if (N < 1 || N > wos::kNfSeriesMax) return -1;
+  if (dim == 2) {
+    if (fp64) hc_nf_series<2, double>(Rb, sb, N, u, v, z, n, out);
+    else hc_nf_series<2, float>(Rb, sb, N, u, v, z, n, out);
+  } else {
+    if (fp64) hc_nf_series<3, double>(Rb, sb, N, u, v, z, n, out);
+    else hc_nf_series<3, float>(Rb, sb, N, u, v, z, n, out);
+  }
+  return 0;
+}
+
 // R |G'/G| of the centred Green's function at rho = r/R
 void wos_hc_green_dlog(int dim, int fp64, double a, const double* rho, int64_t n, double* out) {
   for (int64_t i = 0; i < n; ++i) {

@@ -52,8 +52,10 @@ struct WalkLaunch {
   double* gsum;                   // SoA [dim][npts], accumulated
   double* gsumsq;                 // SoA [dim][npts], accumulated
   double* ghat;                   // optional per-walk gradients SoA [dim][total_items]
-  // next-flight launches: cap on the inner iterations of one ball
+  // next-flight launches: cap on the inner iterations of one ball, and the kernels: 0 the
+  // printed approximations, N > 0 the series with N terms
   int64_t nf_max_inner;
+  int32_t nf_series;
   int drift;                      // the problem has an extra drift (omega fields)
   // launch schedule (0 = the kernel's own rule): walks claimed per warp at a time, resident
   // blocks launched per SM, and the register-cap variant of batched launches (1: 8 blocks/SM)

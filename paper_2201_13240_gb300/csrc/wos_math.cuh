@@ -637,6 +637,173 @@ struct NfBall {
 };
 
 // ---------------------------------------------------------------------------
+// Next-flight kernels as the series of Supplemental 1.2 (the exact off-centred kernels,
+// truncated at N terms), for a ball of radius R centred at c, k = sqrt(sigma_bar),
+// a = kR, u = x - c, v = y - c:
+//   G(x, y) = Phi(|v - u|) - H(u, v),  Phi = e^{-kd}/(4 pi d) (3D), K_0(kd)/(2 pi) (2D),
+//   H = 1/(4 pi R) sum_{n<N} (2n+1) P_n(cos) p_n t_n(k|u|) t_n(k|v|)            (3D)
+//     = 1/(2 pi)   sum_{|n|<N} cos(n th) p_n t_n(k|u|) t_n(k|v|)                 (2D)
+//   P(y, z) = 1/(4 pi R^2) sum_{n<N} (2n+1) P_n(cos) t_n(k|v|)                   (3D)
+//           = 1/(2 pi R)   sum_{|n|<N} cos(n th) t_n(k|v|)                        (2D)
+// with t_n(z) = i_n(z)/i_n(a) (modified spherical Bessel; 2D I_n(z)/I_n(a)) and
+// p_n = a k_n(a) i_n(a) (2D I_n(a) K_n(a)).  The free-space kernel in closed form keeps
+// G's singularity exact; the regular part H and the whole P are truncated, i.e. projected
+// on the angular harmonics of degree < N.
+// Evaluation:
+//  * the ratios rho_n(z) = i_n(z)/i_{n-1}(z) by the backward recurrence
+//    rho_n = 1 / ((2n+1)/z + rho_{n+1}) (2D: 2n/z), the stable direction for i_n, started
+//    with rho = 0 at n0 = N + 12 + a or above (the error shrinks by rho_n^2 per step);
+//  * t_{n-1} = t_n rho_n(a) / rho_n(z), run downwards from an arbitrary t at the top and
+//    rescaled at the end by the closed form t_0 (3D (a/z) sinh z / sinh a, 2D I_0(z)/I_0(a));
+//  * p_n upwards from p_0 (3D (1 - e^{-2a})/(2a), 2D I_0(a) K_0(a)) by
+//    p_n = rho_n(a) (1/a - rho_n(a) p_{n-1}), which follows from the cross products
+//    i_{n-1} k_n + i_n k_{n-1} = 1/a^2 (2D: I_{n-1} K_n + I_n K_{n-1} = 1/a) and damps
+//    errors (factor rho_n^2 per step);
+//  * the Legendre / cosine sums by Clenshaw's recurrence, downwards with the t's.
+// p_n and rho_n(a) depend on the ball only: nf_series_ball fills them once per ball.
+// ---------------------------------------------------------------------------
+constexpr int kNfSeriesMax = 64;  // largest N
+
+// (2n+1) in 3D, 2n in 2D: the recurrence coefficient of the ratios
+template <int DIM, typename R>
+WOS_HD R nf_rec_coef(int n) {
+  return (DIM == 3) ? R(2 * n + 1) : R(2 * n);
+}
+
+// rho_n(a) for 1 <= n < N into ra[n], p_n for 0 <= n < N into pn[n]
+template <int DIM, typename R>
+WOS_HD void nf_series_ball(R a, int N, R* pn, R* ra) {
+  const R inv_a = w_div(R(1), a);
+  const int n0 = N + 12 + (int)w_fmin(a, R(4096));
+  R rho = R(0);
+  for (int n = n0; n >= 1; --n) {
+    rho = w_div(R(1), nf_rec_coef<DIM, R>(n) * inv_a + rho);
+    if (n < N) ra[n] = rho;
+  }
+  if (DIM == 3) {
+    pn[0] = R(-0.5) * w_expm1(R(-2) * a) * inv_a;
+  } else {
+    R i0s, i1s, k0s, k1s;
+    bessel_scaled(a, &i0s, &i1s, &k0s, &k1s);
+    pn[0] = i0s * k0s;
+  }
+  for (int n = 1; n < N; ++n) pn[n] = ra[n] * (inv_a - ra[n] * pn[n - 1]);
+}
+
+// t_0(z) = i_0(z)/i_0(a) (2D I_0(z)/I_0(a)), 0 <= z <= a
+template <int DIM, typename R>
+WOS_HD R nf_series_t0(R z, R a) {
+  if (DIM == 3) {
+    // (a/z) sinh z / sinh a = (a/z) e^{z-a} (1 - e^{-2z}) / (1 - e^{-2a}); a/sinh a at z = 0
+    const R den = -w_expm1(R(-2) * a);
+    if (!(z > R(0))) return R(2) * a * w_exp(-a) / den;
+    return a / z * w_exp(z - a) * (-w_expm1(R(-2) * z)) / den;
+  }
+  R i0z, i1z, k0z, k1z, i0a, i1a, k0a, k1a;
+  bessel_scaled(z, &i0z, &i1z, &k0z, &k1z);
+  bessel_scaled(a, &i0a, &i1a, &k0a, &k1a);
+  return i0z / i0a * w_exp(z - a);
+}
+
+// the last index whose terms matter at geometric rate q (terms shrink like q^n; below
+// 2^-40 relative (2^-64 for FP64) they are dropped), capped at N - 1
+template <typename R>
+WOS_HD int nf_series_last(R q, int N) {
+  if (!(q > R(0))) return 0;
+  if (q > R(0.5)) return N - 1;
+  const R bits = (sizeof(R) == 4) ? R(40) : R(64);
+  const R m = bits / (-w_log(q) * R(1.44269504088896340736));  // bits / -log2(q)
+  return (m < R(N - 1)) ? (int)m + 1 : N - 1;
+}
+
+// G(c + u, c + v) and P(c + v, c + zp) (|zp| = R) from one downward sweep.  n0 >= the
+// ball's N + 12 + a (the caller may pass a larger one, e.g. the largest of its warp, so
+// that the sweep's index is the same on every lane).
+template <int DIM, typename R>
+WOS_HD void nf_series_eval(R k, R a, R Rb, int N, int n0, const R* pn, const R* ra, const R* u, const R* v,
+                           const R* zp, R* G, R* P) {
+  R r1s = R(0), r2s = R(0), uv = R(0), vz = R(0), d2 = R(0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    r1s += u[i] * u[i];
+    r2s += v[i] * v[i];
+    uv += u[i] * v[i];
+    vz += v[i] * zp[i];
+    const R w = v[i] - u[i];
+    d2 += w * w;
+  }
+  const R r1 = w_sqrt(r1s), r2 = w_sqrt(r2s), d = w_sqrt(d2);
+  const R muH = (r1 > R(0) && r2 > R(0)) ? w_fmax(R(-1), w_fmin(R(1), uv / (r1 * r2))) : R(0);
+  const R muP = (r2 > R(0)) ? w_fmax(R(-1), w_fmin(R(1), vz / (r2 * Rb))) : R(0);
+  const R z1 = k * r1, z2 = k * r2;
+  // 1/z, 0 at the centre (only the n = 0 terms remain there: the sweep leaves t alone)
+  const R iz1 = (z1 > R(0)) ? w_div(R(1), z1) : R(0), iz2 = (z2 > R(0)) ? w_div(R(1), z2) : R(0);
+  const int lastH = nf_series_last<R>(r1 * r2 / (Rb * Rb), N);
+  const int lastP = nf_series_last<R>(r2 / Rb, N);
+  const R big = R(1073741824.0), small = R(1.0 / 1073741824.0);  // 2^30, 2^-30
+  R rho1 = R(0), rho2 = R(0), t1 = R(1), t2 = R(1);
+  R bH1 = R(0), bH2 = R(0), bP1 = R(0), bP2 = R(0);
+  R inv_n2 = w_div(R(1), R(n0 + 2));  // 1/(n+2) of the first step
+  for (int n = n0; n >= 1; --n) {
+    const R c = nf_rec_coef<DIM, R>(n);
+    const R s1 = (z1 > R(0)) ? c * iz1 + rho1 : R(1), s2 = (z2 > R(0)) ? c * iz2 + rho2 : R(1);
+    rho1 = w_div(R(1), s1);
+    rho2 = w_div(R(1), s2);
+    const R inv_n1 = w_div(R(1), R(n + 1));
+    // Clenshaw coefficients of term n: 3D Legendre alpha_n = (2n+1) mu/(n+1), beta_{n+1} =
+    // -(n+1)/(n+2); 2D cosines alpha_n = 2 mu, beta = -1
+    const R aH = (DIM == 3) ? R(2 * n + 1) * muH * inv_n1 : R(2) * muH;
+    const R aP = (DIM == 3) ? R(2 * n + 1) * muP * inv_n1 : R(2) * muP;
+    const R bt = (DIM == 3) ? -R(n + 1) * inv_n2 : R(-1);
+    const R wn = (DIM == 3) ? R(2 * n + 1) : R(2);  // weight of term n (2D: n and -n)
+    if (n <= lastP) {
+      const R b0 = wn * t2 + aP * bP1 + bt * bP2;
+      bP2 = bP1;
+      bP1 = b0;
+    }
+    if (n <= lastH) {
+      const R b0 = wn * pn[n] * t1 * t2 + aH * bH1 + bt * bH2;
+      bH2 = bH1;
+      bH1 = b0;
+      t1 *= ra[n] * s1;  // t_{n-1}(z1)
+      if (t1 > big) {
+        t1 *= small;
+        bH1 *= small;
+        bH2 *= small;
+      }
+    }
+    if (n <= lastP) {
+      t2 *= ra[n] * s2;  // t_{n-1}(z2)
+      if (t2 > big) {
+        t2 *= small;
+        bP1 *= small;
+        bP2 *= small;
+        bH1 *= small;
+        bH2 *= small;
+      }
+    }
+    inv_n2 = inv_n1;
+  }
+  // n = 0: alpha_0 = mu (both), beta_1 = -1/2 (3D) or -1 (2D)
+  const R b1 = (DIM == 3) ? R(-0.5) : R(-1);
+  const R SP = t2 + muP * bP1 + b1 * bP2;
+  const R SH = pn[0] * t1 * t2 + muH * bH1 + b1 * bH2;
+  const R n2 = nf_series_t0<DIM, R>(z2, a) / t2;
+  const R n1 = nf_series_t0<DIM, R>(z1, a) / t1;
+  if (DIM == 3) {
+    const R c4 = R(0.07957747154594766788);  // 1/(4 pi)
+    *P = c4 * SP * n2 / (Rb * Rb);
+    *G = c4 * (w_exp(-k * d) / d - SH * n1 * n2 / Rb);
+  } else {
+    const R c2 = R(0.15915494309189533577);  // 1/(2 pi)
+    R i0s, i1s, k0s, k1s;
+    bessel_scaled(k * d, &i0s, &i1s, &k0s, &k1s);
+    *P = c2 * SP * n2 / Rb;
+    *G = c2 * (k0s * w_exp(-k * d) - SH * n1 * n2);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Radial CDF F(rho) of y ~ G/|G|, rho = r/R, and its density, 3D.
 //   N(rho) = a^2 int_0^rho t sinh(a(1-t)) dt, F = N(rho)/N(1).
 //   a >= 1:  with h(x) = 1 - e^x (1-x),

@@ -9,8 +9,10 @@
 //   theta_l = G(x^l, x^{l+1}) |B| (sigma_bar - sigma'(x^{l+1})),
 // stopping by Russian roulette with probability min(1, |throughput|).  The walk
 // then adds W T_src, multiplies its weight W by T_tr and moves to z.  G and P are
-// the approximate off-centred forms of Supplemental 1.2 (NfBall); the first term
-// of each ball is the centred P.
+// the approximate off-centred forms of Supplemental 1.2 (NfBall), or (SERIES) its
+// series truncated at L.nf_series terms (nf_series_ball / nf_series_eval, with the
+// ball's coefficient tables in per-lane local memory); the first term of each ball is
+// the centred P.
 //
 // Lanes run a two-phase state machine.  A lane at the start of a ball runs the
 // distance query (phase 0, a divergent branch) and then, in the same iteration,
@@ -35,7 +37,7 @@ namespace wos {
 constexpr int kNfBlock = 128;
 constexpr uint64_t kNfChunk = 128;
 
-template <int DIM, typename R, bool MESH>
+template <int DIM, typename R, bool MESH, bool SERIES>
 __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_kernel(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
@@ -78,6 +80,10 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
   R W = R(1), acc = R(0), T = R(1), Ttr = R(0), Tsrc = R(0), Rb = R(0);
   NfBall<DIM, R> ball;
   ball.init(R(1), R(1));
+  // series tables of the current ball: p_n and rho_n(a) (indices < nser)
+  const int nser = SERIES ? L.nf_series : 1;
+  R ser_p[SERIES ? kNfSeriesMax : 1], ser_ra[SERIES ? kNfSeriesMax : 1];
+  int ser_n0 = 0;  // the ball's start index of the downward sweep
 
   const uint32_t kNoPoint = 0xffffffffu;
   uint32_t acc_p = kNoPoint;
@@ -190,6 +196,10 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
       }
       Rb = d;
       ball.init(s_root, Rb);
+      if (SERIES) {
+        nf_series_ball<DIM, R>(s_root * Rb, nser, ser_p, ser_ra);
+        ser_n0 = nser + 12 + (int)w_fmin(s_root * Rb, R(4096));
+      }
       U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
       R dz[3] = {R(0), R(0), R(0)};
       if (DIM == 2) {
@@ -251,13 +261,23 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
     R spy, fpy;
     coeffs<DIM>(P, y, &spy, &fpy);
     R vol = cvol * Rb * Rb * ((DIM == 3) ? Rb : R(1));
-    R Gv = ball.G(uc, vn) * vol;          // G(x_c, x_n) / p(x_n)
+    R area = carea * Rb * ((DIM == 3) ? Rb : R(1));
+    R Gxy, Pyz;  // G(x_c, x_n) and P(x_n, z)
+    if (SERIES) {
+      // one downward sweep for both; its start index is the largest of the lanes here,
+      // so that the sweep's index (and the tables' local-memory rows) agree across the warp
+      const int n0w = __reduce_max_sync(__activemask(), ser_n0);
+      nf_series_eval<DIM, R>(s_root, s_root * Rb, Rb, nser, n0w, ser_p, ser_ra, uc, vn, vz, &Gxy, &Pyz);
+    } else {
+      Gxy = ball.G(uc, vn);
+      Pyz = ball.P(vn, vz);
+    }
+    R Gv = Gxy * vol;                     // G(x_c, x_n) / p(x_n)
     Tsrc += fpy * Gv * T;
     T *= Gv * (sbar - spy);
 #pragma unroll
     for (int i = 0; i < 3; ++i) uc[i] = vn[i];
-    R area = carea * Rb * ((DIM == 3) ? Rb : R(1));
-    Ttr += ball.P(uc, vz) * area * T;     // next term of the boundary series
+    Ttr += Pyz * area * T;                // next term of the boundary series
     ++j;
     ++st_inner;
   }
@@ -290,17 +310,18 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
   }
 }
 
-template <int DIM, typename R, bool MESH>
+template <int DIM, typename R, bool MESH, bool SERIES>
 cudaError_t launch_nf_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = (size_t)L.problem_bytes;
   if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kNfBlock;
   if (smem > 48 * 1024) {
-    cudaError_t ea = cudaFuncSetAttribute(wos_nf_kernel<DIM, R, MESH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem);
+    cudaError_t ea = cudaFuncSetAttribute(wos_nf_kernel<DIM, R, MESH, SERIES>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return ea;
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_nf_kernel<DIM, R, MESH>, kNfBlock, smem);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wos_nf_kernel<DIM, R, MESH, SERIES>, kNfBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = per_sm * num_sms;
@@ -308,14 +329,18 @@ cudaError_t launch_nf_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kNfBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_nf_kernel<DIM, R, MESH><<<grid, kNfBlock, smem, stream>>>(L);
+  wos_nf_kernel<DIM, R, MESH, SERIES><<<grid, kNfBlock, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
 template <int DIM, typename R>
 cudaError_t launch_nf_t(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
-  if (DIM == 3 && L.mesh) return launch_nf_m<DIM, R, true>(L, num_sms, stream);
-  return launch_nf_m<DIM, R, false>(L, num_sms, stream);
+  const bool series = L.nf_series > 0;
+  if (DIM == 3 && L.mesh)
+    return series ? launch_nf_m<DIM, R, true, true>(L, num_sms, stream)
+                  : launch_nf_m<DIM, R, true, false>(L, num_sms, stream);
+  return series ? launch_nf_m<DIM, R, false, true>(L, num_sms, stream)
+                : launch_nf_m<DIM, R, false, false>(L, num_sms, stream);
 }
 
 }  // namespace wos

@@ -6,6 +6,9 @@
   shell decisions agree except for rare rounding flips), and against the exact
   solution where the next-flight estimate is exact (sigma_bar = sigma').
 * Counters: balls (distance queries) and inner iterations.
+* The series kernels (series_terms > 0): the same FP64 per-walk replay against the
+  oracle's series walk, and the FP32 estimate against the exact solution where sigma'
+  varies (the printed approximations are biased there).
 """
 import numpy as np
 import pytest
@@ -104,6 +107,41 @@ def test_fp32_next_flight_exact_when_sigma_bar_is_sigma(ctx, name, sb):
     assert ok, (nout, mz)
 
 
+@pytest.mark.parametrize("name", ["square2d", "cube3d", "hifreq", "screened_ball", "mesh"])
+def test_fp64_replay_next_flight_series_per_walk(orc, ctx, wos, name):
+    mk, ptsf, eps, sb = CASES[name]
+    desc = mk()
+    pts = ptsf()
+    prob = ctx.problem(desc)
+    sb = _sb(orc, desc, sb)
+    wpp, nser = 8, 12
+    uh, st, stats = ctx.walk_estimates_nf(prob, dev(pts), wpp, eps, sb, seed=5, precision="fp64", series_terms=nser)
+    uo, so, io = orc.walks_nf(desc, pts, wpp, seed=5, eps=eps, sigma_bar=sb, series_terms=nser)
+    uh, st = uh.cpu().numpy(), st.cpu().numpy()
+    ok = np.abs(uh - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
+    assert ok.mean() >= 0.99, (name, ok.mean())
+    assert (st == so).mean() >= 0.99
+
+
+@pytest.mark.parametrize("name", ["cube3d"])
+def test_fp32_next_flight_series_is_unbiased_where_sigma_varies(orc, ctx, wos, name):
+    if name == "cube3d":
+        desc, exact = W.cube3d_problem(), W.cube3d_exact
+        pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 256, 3)]
+        sb = orc.sigma_bar(desc, 64)[0]
+    else:
+        desc, exact = W.square2d_problem(), W.square2d_exact
+        pts = W.cell_centres(2, 32)[:, W.seeded_subset(1024, 256, 4)]
+        sb = orc.sigma_bar(desc)[0]
+    prob = ctx.problem(desc)
+    acc, stats = ctx.solve_nf(prob, dev(pts), 16384, 1e-4, sb, seed=3, series_terms=16)
+    m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+    ex = np.array([exact(*pts[:, i].astype(np.float64)) for i in range(pts.shape[1])])
+    ok, nout, mz = four_se_rule((m - ex) / se)
+    assert ok, (name, nout, mz)
+    assert wos.stats_dict(stats)["nonfinite"] == 0
+
+
 def test_next_flight_arguments(ctx, orc, wos):
     desc = W.square2d_problem()
     prob = ctx.problem(desc)
@@ -111,6 +149,9 @@ def test_next_flight_arguments(ctx, orc, wos):
     pts = dev(W.cell_centres(2, 4))
     with pytest.raises(wos.WosError):
         ctx.solve_nf(prob, pts, 8, 1e-3, sb, max_inner=0)
+    for bad in (-1, 65):
+        with pytest.raises(wos.WosError):
+            ctx.solve_nf(prob, pts, 8, 1e-3, sb, series_terms=bad)
     acc, st = ctx.solve_nf(prob, pts, 8, 1e-3, sb, max_inner=1)  # every ball cut after one iteration
     s = wos.stats_dict(st)
     assert s["walks"] == 16 * 8 and s["inner"] <= s["steps"]

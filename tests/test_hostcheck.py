@@ -187,6 +187,45 @@ def test_offcentre_kernels(hc, orc, dim, fp64):
 
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("fp64", [0, 1])
+@pytest.mark.parametrize("N", [1, 8, 32, 64])
+def test_series_offcentre_kernels(hc, orc, dim, fp64, N):
+    """The next-flight kernels' series G and P (Supplemental 1.2, N terms: ratio recurrences,
+    Clenshaw sums) against the oracle's (power series, log-scaled), at random interior and
+    sphere points including the ball centre, from a = 1e-3 to a = 100."""
+    rng = np.random.default_rng(N)
+    hc.wos_hc_nf_series.restype = C.c_int
+    for R, sb in ((0.3, 1e-5), (0.5, 45.0), (0.2, 787.0), (1.0, 4.0), (0.1, 1e6)):
+        n = 40
+
+        def dirs():
+            d = rng.normal(size=(n, 3))
+            if dim == 2:
+                d[:, 2] = 0
+            return d / np.linalg.norm(d, axis=1)[:, None]
+        u = dirs() * (R * rng.uniform(size=n) ** (1 / dim))[:, None]
+        v = dirs() * (R * rng.uniform(size=n) ** (1 / dim))[:, None]
+        z = dirs() * R
+        u[0] = 0.0
+        out = np.zeros(2 * n)
+        rc = hc.wos_hc_nf_series(dim, fp64, C.c_double(R), C.c_double(sb), N,
+                                 np.ascontiguousarray(u).ctypes.data_as(DP), np.ascontiguousarray(v).ctypes.data_as(DP),
+                                 np.ascontiguousarray(z).ctypes.data_as(DP), n, out.ctypes.data_as(DP))
+        assert rc == 0
+        g = np.array([orc.series_G(dim, R, sb, u[i, :dim], v[i, :dim], N) for i in range(n)])
+        p = np.array([orc.series_P(dim, R, sb, v[i, :dim], z[i, :dim], N) for i in range(n)])
+        # G near the sphere is a difference of two larger terms: errors relative to the kernel's scale
+        gs, ps = np.abs(g).max(), np.abs(p).max()
+        tol = 1e-10 if fp64 else 2e-3
+        assert np.all(np.abs(out[0::2] - g) <= tol * np.maximum(np.abs(g), 1e-2 * gs)), (R, sb)
+        assert np.all(np.abs(out[1::2] - p) <= tol * np.maximum(np.abs(p), 1e-2 * ps)), (R, sb)
+    bad = np.zeros(2)
+    z3 = np.zeros(3)
+    assert hc.wos_hc_nf_series(dim, fp64, C.c_double(1.0), C.c_double(1.0), 65, z3.ctypes.data_as(DP),
+                               z3.ctypes.data_as(DP), z3.ctypes.data_as(DP), 1, bad.ctypes.data_as(DP)) == -1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
 def test_green_log_derivative(hc, orc, dim, fp64):
     """R |G'/G| of the centred Green's function (the extra-drift weight) against the oracle."""
     R = 0.37
