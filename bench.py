@@ -810,7 +810,7 @@ def main():
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default launch schedule")
-    ap.add_argument("--nf-series", type=int, default=16,
+    ap.add_argument("--nf-series", type=int, default=8,
                     help="nf workload: terms of the off-centred kernels' series (1..64)")
     ap.add_argument("--kernel", default="specialised", choices=["specialised", "generic"],
                     help="walk kernel: compiled for the problem's fields (default) or the generic field interpreter")

@@ -128,6 +128,10 @@ def _load():
     lib.orc_series_G.restype = C.c_double
     lib.orc_series_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_int]
     lib.orc_series_P.restype = C.c_double
+    lib.orc_nf_h.argtypes = [C.c_int, C.c_double]
+    lib.orc_nf_h.restype = C.c_double
+    lib.orc_nf_free_radius.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+    lib.orc_nf_free_radius.restype = C.c_double
     lib.orc_walk_nf.argtypes = [pp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, C.c_double, C.c_int64,
                                 C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int32)]
@@ -504,6 +508,16 @@ def series_P(dim, R, sb, u, v, nterms=0):
     uu, vv = np.zeros(3), np.zeros(3)
     uu[:dim], vv[:dim] = u, v
     return _load().orc_series_P(dim, R, sb, _dptr(uu), _dptr(vv), nterms)
+
+
+def nf_h(dim, t):
+    """h(t) of the series walk's in-ball sampling: 1 - e^{-t}(1 + t) (3D), 1 - t K_1(t) (2D)."""
+    return _load().orc_nf_h(dim, t)
+
+
+def nf_free_radius(dim, sb, rm, u):
+    """Distance r in [0, rm] with h(sqrt(sb) r) = u h(sqrt(sb) rm)."""
+    return _load().orc_nf_free_radius(dim, sb, rm, u)
 
 
 def walk_nf(prob, x0, point, walk_id, seed, eps, sigma_bar, max_steps=1 << 20, max_inner=1 << 16, packed=None,

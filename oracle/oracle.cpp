@@ -1644,9 +1644,85 @@ double series_t(int dim, int n, double z, double ln_ia) {
 }
 
 const int kSeriesMaxTerms = 100000;
+
+// The regular part H of the series G (G = Phi - H), for the in-ball sampling below.
+double series_H(int dim, double R, double sb, const double* u, const double* v, int nterms, double* phi_out);
+
+// ---------------------------------------------------------------------------
+// In-ball points of the series walk (reading R24, not in the paper).  Sec. 5.2 leaves the
+// in-ball density p^B free (Supplemental 1.4: uniform suffices).  Uniform points make the
+// throughput factor theta = G |B| (sigma_bar - sigma') unbounded near the current point
+// (G ~ Phi there), and the series' variance infinite once (sigma_bar - sigma')^2 R^4 is of
+// order one.  The series walk draws y = x + r w instead: w uniform on the unit sphere
+// (circle), r in [0, r_m(w)] (r_m the distance from x to the sphere along w) with density
+// proportional to Phi(r) r^{d-1}, Phi the free-space kernel.  With k = sqrt(sigma_bar),
+//   p(y) = Phi(r) k^2 / h(k r_m),  h(t) = 1 - e^{-t}(1 + t) (3D),  1 - t K_1(t) (2D)
+// (k^2 times the free-space kernel's mass within radius t/k), and since 0 <= G <= Phi,
+//   G(x, y) / p(y) = (1 - H/Phi) h(k r_m) / sigma_bar <= 1 / sigma_bar,
+// so theta <= 1 - sigma'/sigma_bar: the throughput no longer grows.
+// ---------------------------------------------------------------------------
+// h and h' = t e^{-t} (3D), t K_0(t) (2D)
+double nf_h(int dim, double t) {
+  if (dim == 3) {
+    if (t < 0.5) {  // sum_{n>=2} (-1)^n (n-1) t^n / n!
+      double term = t * t / 2.0, sum = 0.0;
+      for (int n = 2; n < 60 && std::fabs(term) > 1e-300; ++n) {
+        sum += (n - 1) * term;
+        term *= -t / (n + 1);
+      }
+      return sum;
+    }
+    return 1.0 - std::exp(-t) * (1.0 + t);
+  }
+  if (t < 2.0) {
+    // DLMF 10.31.1 (n = 1): 1 - t K_1(t) = -t ln(t/2) I_1(t)
+    //   + (t^2/4) sum_k (psi(k+1) + psi(k+2)) (t^2/4)^k / (k! (k+1)!)
+    if (t == 0.0) return 0.0;
+    const double q = t * t / 4.0;
+    double c = 1.0, i1 = 0.0, ps = 0.0;  // c = q^k / (k! (k+1)!)
+    double psi1 = -kEulerGamma, psi2 = 1.0 - kEulerGamma;  // psi(k+1), psi(k+2)
+    for (int k = 0; k < 60; ++k) {
+      i1 += c;
+      ps += (psi1 + psi2) * c;
+      psi1 += 1.0 / (k + 1);
+      psi2 += 1.0 / (k + 2);
+      c *= q / ((k + 1.0) * (k + 2.0));
+      if (c < 1e-20) break;
+    }
+    i1 *= t / 2.0;
+    return -t * std::log(t / 2.0) * i1 + q * ps;
+  }
+  return 1.0 - t * bK1(t);
+}
+double nf_hprime(int dim, double t) { return (dim == 3) ? t * std::exp(-t) : t * bK0(t); }
+
+// r in [0, rm] with h(k r) = U h(k rm): safeguarded Newton on t = k r, run to convergence
+double nf_free_radius(int dim, double k, double rm, double U) {
+  const double tm = k * rm, c = U * nf_h(dim, tm);
+  double lo = 0.0, hi = tm, t = tm * std::sqrt(U);
+  for (int it = 0; it < 200; ++it) {
+    const double f = nf_h(dim, t) - c;
+    if (f == 0.0) break;
+    if (f > 0.0) hi = t; else lo = t;
+    const double d = nf_hprime(dim, t);
+    double nt = (d > 0.0) ? t - f / d : 0.5 * (lo + hi);
+    if (!(nt >= lo && nt <= hi)) nt = 0.5 * (lo + hi);
+    const double step = std::fabs(nt - t);
+    t = nt;
+    if (step <= 1e-16 * tm || hi - lo <= 1e-16 * tm) break;
+  }
+  return t / k;
+}
 }  // namespace
 
 double orc_series_G(int dim, double R, double sb, const double* u, const double* v, int nterms) {
+  double phi;
+  const double H = series_H(dim, R, sb, u, v, nterms, &phi);
+  return phi - H;
+}
+
+namespace {
+double series_H(int dim, double R, double sb, const double* u, const double* v, int nterms, double* phi_out) {
   const SeriesGeom g = series_geom(dim, u, v);
   const double cd = (dim == 2) ? 1.0 / (2.0 * kPi) : 1.0 / (4.0 * kPi);
   const int N = (nterms > 0) ? nterms : kSeriesMaxTerms;
@@ -1661,7 +1737,8 @@ double orc_series_G(int dim, double R, double sb, const double* u, const double*
       H += cd * c;
       if (nterms == 0 && n > 8 && std::pow(t, n) < 1e-18) break;
     }
-    return phi - H;
+    *phi_out = phi;
+    return H;
   }
   const double k = std::sqrt(sb), a = k * R, z1 = k * g.r1, z2 = k * g.r2;
   phi = (dim == 2) ? cd * bK0(k * g.d) : cd * std::exp(-k * g.d) / g.d;
@@ -1679,8 +1756,13 @@ double orc_series_G(int dim, double R, double sb, const double* u, const double*
     if (nterms == 0 && n > 8 && std::fabs(term) * (2.0 * n + 1.0) < 1e-18 * std::fabs(H)) break;
     if (tt == 0.0 && n > 0) break;
   }
-  return phi - H;
+  *phi_out = phi;
+  return H;
 }
+}  // namespace
+
+double orc_nf_h(int dim, double t) { return nf_h(dim, t); }
+double orc_nf_free_radius(int dim, double sb, double rm, double U) { return nf_free_radius(dim, std::sqrt(sb), rm, U); }
 
 double orc_series_P(int dim, double R, double sb, const double* u, const double* v, int nterms) {
   const SeriesGeom g = series_geom(dim, u, v);
@@ -1757,24 +1839,34 @@ double orc_walk_nf(const orc_problem* P, const double* x0, uint32_t point, uint3
         break;
       }
       ++inner;
-      // next point uniform in the ball
-      double vn[3] = {0, 0, 0};
+      // next in-ball point: uniform (printed approximations), or along a uniform direction
+      // w at a free-space-kernel distance from the current point (series, reading R24)
+      double vn[3] = {0, 0, 0}, w[3] = {0, 0, 0}, Gv;
       if (dim == 2) {
-        double rr = R * std::sqrt(uniform01(o[1])), th = 2.0 * kPi * uniform01(o[2]);
-        vn[0] = rr * std::cos(th); vn[1] = rr * std::sin(th);
+        double th = 2.0 * kPi * uniform01(o[2]);
+        w[0] = std::cos(th); w[1] = std::sin(th);
       } else {
-        double rr = R * std::cbrt(uniform01(o[1]));
         double cn = 1.0 - 2.0 * uniform01(o[2]), pn = 2.0 * kPi * uniform01(o[3]);
         double sn = std::sqrt(std::fmax(0.0, 1.0 - cn * cn));
-        vn[0] = rr * sn * std::cos(pn); vn[1] = rr * sn * std::sin(pn); vn[2] = rr * cn;
+        w[0] = sn * std::cos(pn); w[1] = sn * std::sin(pn); w[2] = cn;
+      }
+      if (series_terms > 0) {
+        const double k = std::sqrt(sb), uw = dot3(uc, w, dim);
+        const double rm = -uw + std::sqrt(std::fmax(0.0, uw * uw + R * R - dot3(uc, uc, dim)));
+        const double r = nf_free_radius(dim, k, rm, uniform01(o[1]));
+        for (int i = 0; i < dim; ++i) vn[i] = uc[i] + r * w[i];
+        double phi;
+        const double H = series_H(dim, R, sb, uc, vn, series_terms, &phi);
+        Gv = (1.0 - H / phi) * nf_h(dim, k * rm) / sb;  // G(x_c, x_n) / p(x_n)
+      } else {
+        double rr = (dim == 2) ? R * std::sqrt(uniform01(o[1])) : R * std::cbrt(uniform01(o[1]));
+        for (int i = 0; i < dim; ++i) vn[i] = rr * w[i];
+        Gv = orc_offcentre_G(dim, R, sb, uc, vn) * vol;  // G(x_c, x_n) / p(x_n)
       }
       double y[3] = {0, 0, 0};
       for (int i = 0; i < dim; ++i) y[i] = x[i] + vn[i];
       double gam_y, sp_y, fp_y, f_y, a_y;
       coeffs(P, y, &gam_y, &sp_y, &fp_y, &f_y, &a_y);
-      // G(x_c, x_n) / p(x_n)
-      double Gv = ((series_terms > 0) ? orc_series_G(dim, R, sb, uc, vn, series_terms)
-                                      : orc_offcentre_G(dim, R, sb, uc, vn)) * vol;
       // source: f'(x_n) / (sigma_bar - sigma'(x_n)) times the updated throughput
       Tsrc += fp_y * Gv * T;
       T *= Gv * (sb - sp_y);

@@ -214,13 +214,21 @@ double orc_offcentre_P(int dim, double R, double sigma_bar, const double* u, con
    arguments and scaling as orc_offcentre_G / _P; sigma_bar = 0 gives Laplace's. */
 double orc_series_G(int dim, double R, double sigma_bar, const double* u, const double* v, int nterms);
 double orc_series_P(int dim, double R, double sigma_bar, const double* u, const double* v, int nterms);
+/* The series walk's in-ball sampling (reading R24): h(t) = 1 - e^{-t}(1 + t) (3D) or
+   1 - t K_1(t) (2D), and the distance r in [0, rm] with h(sqrt(sigma_bar) r) =
+   U h(sqrt(sigma_bar) rm) (density proportional to the free-space kernel times r^{d-1}). */
+double orc_nf_h(int dim, double t);
+double orc_nf_free_radius(int dim, double sigma_bar, double rm, double U);
 /* One next-flight walk.  Randoms: outer step k draws the exit point z from Philox
    block (point, walk, k, 0); inner iteration j of that ball draws its roulette
    uniform and its uniform in-ball point from block (point, walk, k, j + 1).
    steps_out = outer steps (distance queries), inner_out = inner iterations; flags
    bit 0 = outer step cap, bit 1 = non-finite, bit 2 = inner cap hit.
-   series_terms = 0: the printed approximate G and P; > 0: the series with that
-   many terms (orc_series_G / _P). */
+   series_terms = 0: the printed approximate G and P with uniform in-ball points; > 0:
+   the series with that many terms (orc_series_G / _P), in-ball points drawn along a
+   uniform direction at a distance from the current point with density proportional to
+   the free-space kernel (orc_nf_free_radius; the uniforms of the uniform point: word 1
+   the distance, words 2, 3 the direction). */
 double orc_walk_nf(const orc_problem* prob, const double* x0, uint32_t point, uint32_t walk, uint64_t seed,
                    double eps, double sigma_bar, int64_t max_steps, int64_t max_inner, int32_t series_terms,
                    int64_t* steps_out, int64_t* inner_out, int32_t* flags_out);

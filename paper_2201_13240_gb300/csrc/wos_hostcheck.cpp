@@ -194,9 +194,9 @@ static void hc_nf_series(double Rb, double sb, int N, const double* u, const dou
       vv[d] = (R)v[3 * i + d];
       zz[d] = (R)z[3 * i + d];
     }
-    R G, P;
-    wos::nf_series_eval<DIM, R>(k, a, rb, N, n0, pn, ra, uu, vv, zz, &G, &P);
-    out[2 * i] = (double)G;
+    R H, Phi, P;
+    wos::nf_series_eval<DIM, R>(k, a, rb, N, n0, pn, ra, uu, vv, zz, &H, &Phi, &P);
+    out[2 * i] = (double)(Phi - H);
     out[2 * i + 1] = (double)P;
   }
 }
@@ -212,6 +212,24 @@ int wos_hc_nf_series(int dim, int fp64, double Rb, double sb, int N, const doubl
   } else {
     if (fp64) hc_nf_series<3, double>(Rb, sb, N, u, v, z, n, out);
     else hc_nf_series<3, float>(Rb, sb, N, u, v, z, n, out);
+  }
+  return 0;
+}
+
+// series walk sampling: out[i] = h(t_i) (which = 0) or the radius r with h(k r) = U_i h(k rm) (which = 1)
+int wos_hc_nf_free(int dim, int fp64, int which, double sb, double rm, const double* x, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (which == 0) {
+      out[i] = (dim == 2) ? (fp64 ? wos::nf_free_h<2, double>(x[i]) : (double)wos::nf_free_h<2, float>((float)x[i]))
+                          : (fp64 ? wos::nf_free_h<3, double>(x[i]) : (double)wos::nf_free_h<3, float>((float)x[i]));
+    } else {
+      const double k = std::sqrt(sb);
+      out[i] = (dim == 2)
+                   ? (fp64 ? wos::nf_free_radius<2, double>(k, rm, x[i])
+                           : (double)wos::nf_free_radius<2, float>((float)k, (float)rm, (float)x[i]))
+                   : (fp64 ? wos::nf_free_radius<3, double>(k, rm, x[i])
+                           : (double)wos::nf_free_radius<3, float>((float)k, (float)rm, (float)x[i]));
+    }
   }
   return 0;
 }

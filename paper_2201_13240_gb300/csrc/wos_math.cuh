@@ -716,12 +716,13 @@ WOS_HD int nf_series_last(R q, int N) {
   return (m < R(N - 1)) ? (int)m + 1 : N - 1;
 }
 
-// G(c + u, c + v) and P(c + v, c + zp) (|zp| = R) from one downward sweep.  n0 >= the
-// ball's N + 12 + a (the caller may pass a larger one, e.g. the largest of its warp, so
-// that the sweep's index is the same on every lane).
+// For G(c + u, c + v) = Phi - H: its regular part H and the free-space kernel Phi(|v - u|);
+// and P(c + v, c + zp) (|zp| = R); from one downward sweep.  n0 >= the ball's N + 12 + a
+// (the caller may pass a larger one, e.g. the largest of its warp, so that the sweep's
+// index is the same on every lane).
 template <int DIM, typename R>
 WOS_HD void nf_series_eval(R k, R a, R Rb, int N, int n0, const R* pn, const R* ra, const R* u, const R* v,
-                           const R* zp, R* G, R* P) {
+                           const R* zp, R* H, R* Phi, R* P) {
   R r1s = R(0), r2s = R(0), uv = R(0), vz = R(0), d2 = R(0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
@@ -793,14 +794,86 @@ WOS_HD void nf_series_eval(R k, R a, R Rb, int N, int n0, const R* pn, const R* 
   if (DIM == 3) {
     const R c4 = R(0.07957747154594766788);  // 1/(4 pi)
     *P = c4 * SP * n2 / (Rb * Rb);
-    *G = c4 * (w_exp(-k * d) / d - SH * n1 * n2 / Rb);
+    *H = c4 * SH * n1 * n2 / Rb;
+    *Phi = c4 * w_exp(-k * d) / d;
   } else {
     const R c2 = R(0.15915494309189533577);  // 1/(2 pi)
     R i0s, i1s, k0s, k1s;
     bessel_scaled(k * d, &i0s, &i1s, &k0s, &k1s);
     *P = c2 * SP * n2 / Rb;
-    *G = c2 * (k0s * w_exp(-k * d) - SH * n1 * n2);
+    *H = c2 * SH * n1 * n2;
+    *Phi = c2 * k0s * w_exp(-k * d);
   }
+}
+
+// In-ball points of the series walk: y = x + r w, w uniform on the unit sphere (circle),
+// r in [0, r_m] (r_m the distance from x to the sphere along w) with density proportional
+// to Phi(r) r^{d-1}.  Then p(y) = Phi(r) k^2 / h(k r_m) with
+//   h(t) = 1 - e^{-t}(1 + t) (3D),  1 - t K_1(t) (2D),   h'(t) = t e^{-t},  t K_0(t),
+// and G(x, y)/p(y) = (1 - H/Phi) h(k r_m) / sigma_bar <= 1/sigma_bar (0 <= G <= Phi): the
+// throughput factor G/p (sigma_bar - sigma') stays at most 1 - sigma'/sigma_bar.
+// Small t: 3D sum_{n>=2} (-1)^n (n-1) t^n / n!; 2D (DLMF 10.31.1 at n = 1)
+//   1 - t K_1(t) = -t ln(t/2) I_1(t) + (t^2/4) sum_k (psi(k+1) + psi(k+2)) (t^2/4)^k / (k! (k+1)!).
+template <int DIM, typename R>
+WOS_HD R nf_free_h(R t) {
+  if (DIM == 3) {
+    if (t < R(0.5)) {
+      R term = R(0.5) * t * t, sum = R(0);
+      const int nmax = (sizeof(R) == 4) ? 12 : 24;
+      for (int n = 2; n <= nmax; ++n) {
+        sum += R(n - 1) * term;
+        term *= -t / R(n + 1);
+      }
+      return sum;
+    }
+    return -w_expm1(-t) - t * w_exp(-t);
+  }
+  if (t < R(2)) {
+    if (!(t > R(0))) return R(0);
+    const R q = R(0.25) * t * t;
+    R c = R(1), i1 = R(0), ps = R(0);
+    R psi1 = R(-0.57721566490153286061), psi2 = R(0.42278433509846713939);  // psi(1), psi(2)
+    const int kmax = (sizeof(R) == 4) ? 9 : 18;
+    for (int kk = 0; kk <= kmax; ++kk) {
+      i1 += c;
+      ps += (psi1 + psi2) * c;
+      psi1 += R(1) / R(kk + 1);
+      psi2 += R(1) / R(kk + 2);
+      c *= q / (R(kk + 1) * R(kk + 2));
+    }
+    return -t * w_log(R(0.5) * t) * (R(0.5) * t * i1) + q * ps;
+  }
+  R i0s, i1s, k0s, k1s;
+  bessel_scaled(t, &i0s, &i1s, &k0s, &k1s);
+  return R(1) - t * k1s * w_exp(-t);
+}
+template <int DIM, typename R>
+WOS_HD R nf_free_hp(R t) {
+  if (DIM == 3) return t * w_exp(-t);
+  R i0s, i1s, k0s, k1s;
+  bessel_scaled(t, &i0s, &i1s, &k0s, &k1s);
+  return t * k0s * w_exp(-t);
+}
+// r in [0, rm] with h(k r) = U h(k rm): safeguarded Newton on t = k r (bracketed;
+// FP64 runs to convergence, FP32 to a step of 1e-6 of t)
+template <int DIM, typename R>
+WOS_HD R nf_free_radius(R k, R rm, R U) {
+  const R tm = k * rm, c = U * nf_free_h<DIM, R>(tm);
+  const R tol = (sizeof(R) == 4) ? R(1e-6) : R(4e-16);
+  const int itmax = (sizeof(R) == 4) ? 30 : 200;
+  R lo = R(0), hi = tm, t = tm * w_sqrt(U);
+  for (int it = 0; it < itmax; ++it) {
+    const R f = nf_free_h<DIM, R>(t) - c;
+    if (f == R(0)) break;
+    if (f > R(0)) hi = t; else lo = t;
+    const R dh = nf_free_hp<DIM, R>(t);
+    R nt = (dh > R(0)) ? t - f / dh : R(0.5) * (lo + hi);
+    if (!(nt >= lo && nt <= hi)) nt = R(0.5) * (lo + hi);
+    const R step = w_fabs(nt - t);
+    t = nt;
+    if (step <= tol * t || hi - lo <= tol * t) break;
+  }
+  return t / k;
 }
 
 // ---------------------------------------------------------------------------

@@ -241,19 +241,36 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
       continue;
     }
     T /= pRR;
-    R vn[3] = {R(0), R(0), R(0)};
+    // next in-ball point: a uniform direction w (words z, w) and a distance (word y), uniform
+    // in the ball (printed approximations) or from the free-space kernel (series)
+    R wd[3] = {R(0), R(0), R(0)};
     if (DIM == 2) {
-      R rr = Rb * w_sqrt(to_uniform<R>(r1.y));
-      R sn, cn;
-      w_sincospi2(to_uniform<R>(r1.z), &sn, &cn);
-      vn[0] = rr * cn; vn[1] = rr * sn;
+      w_sincospi2(to_uniform<R>(r1.z), &wd[1], &wd[0]);
     } else {
-      R rr = Rb * w_cbrt(to_uniform<R>(r1.y));
       R cn = R(1) - R(2) * to_uniform<R>(r1.z);
       R sn = w_sqrt(w_fmax(R(0), R(1) - cn * cn));
       R sp_, cp_;
       w_sincospi2(to_uniform<R>(r1.w), &sp_, &cp_);
-      vn[0] = rr * sn * cp_; vn[1] = rr * sn * sp_; vn[2] = rr * cn;
+      wd[0] = sn * cp_; wd[1] = sn * sp_; wd[2] = cn;
+    }
+    R vn[3] = {R(0), R(0), R(0)};
+    R hm = R(0);  // series: h(k r_m)
+    if (SERIES) {
+      R uw = R(0), uu = R(0);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        uw += uc[i] * wd[i];
+        uu += uc[i] * uc[i];
+      }
+      const R rm = -uw + w_sqrt(w_fmax(R(0), uw * uw + Rb * Rb - uu));
+      const R rr = nf_free_radius<DIM, R>(s_root, rm, to_uniform<R>(r1.y));
+      hm = nf_free_h<DIM, R>(s_root * rm);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) vn[i] = uc[i] + rr * wd[i];
+    } else {
+      const R rr = (DIM == 2) ? Rb * w_sqrt(to_uniform<R>(r1.y)) : Rb * w_cbrt(to_uniform<R>(r1.y));
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) vn[i] = rr * wd[i];
     }
     R y[3];
 #pragma unroll
@@ -262,17 +279,18 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
     coeffs<DIM>(P, y, &spy, &fpy);
     R vol = cvol * Rb * Rb * ((DIM == 3) ? Rb : R(1));
     R area = carea * Rb * ((DIM == 3) ? Rb : R(1));
-    R Gxy, Pyz;  // G(x_c, x_n) and P(x_n, z)
+    R Gv, Pyz;  // G(x_c, x_n) / p(x_n) and P(x_n, z)
     if (SERIES) {
       // one downward sweep for both; its start index is the largest of the lanes here,
       // so that the sweep's index (and the tables' local-memory rows) agree across the warp
       const int n0w = __reduce_max_sync(__activemask(), ser_n0);
-      nf_series_eval<DIM, R>(s_root, s_root * Rb, Rb, nser, n0w, ser_p, ser_ra, uc, vn, vz, &Gxy, &Pyz);
+      R Hxy, Phi;
+      nf_series_eval<DIM, R>(s_root, s_root * Rb, Rb, nser, n0w, ser_p, ser_ra, uc, vn, vz, &Hxy, &Phi, &Pyz);
+      Gv = (R(1) - Hxy / Phi) * hm / sbar;
     } else {
-      Gxy = ball.G(uc, vn);
+      Gv = ball.G(uc, vn) * vol;
       Pyz = ball.P(vn, vz);
     }
-    R Gv = Gxy * vol;                     // G(x_c, x_n) / p(x_n)
     Tsrc += fpy * Gv * T;
     T *= Gv * (sbar - spy);
 #pragma unroll

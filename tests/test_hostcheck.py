@@ -226,6 +226,26 @@ def test_series_offcentre_kernels(hc, orc, dim, fp64, N):
 
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("fp64", [0, 1])
+def test_series_walk_sampling(hc, orc, dim, fp64):
+    """The series walk's in-ball distance (h and its inverse, reading R24) against the oracle."""
+    hc.wos_hc_nf_free.restype = C.c_int
+    t = np.array([1e-6, 1e-3, 0.2, 0.499, 0.501, 1.0, 1.999, 2.001, 5.0, 30.0])
+    out = np.zeros_like(t)
+    hc.wos_hc_nf_free(dim, fp64, 0, C.c_double(0.0), C.c_double(0.0), t.ctypes.data_as(DP), len(t),
+                      out.ctypes.data_as(DP))
+    want = np.array([orc.nf_h(dim, x) for x in t])
+    assert np.allclose(out, want, rtol=1e-13 if fp64 else 3e-6, atol=0), (out, want)
+    u = np.array([1e-7, 1e-3, 0.1, 0.5, 0.9, 0.999])
+    for sb, rm in ((45.0, 0.3), (4.0, 0.8), (900.0, 0.5), (1e-4, 0.2)):
+        out = np.zeros_like(u)
+        hc.wos_hc_nf_free(dim, fp64, 1, C.c_double(sb), C.c_double(rm), u.ctypes.data_as(DP), len(u),
+                          out.ctypes.data_as(DP))
+        want = np.array([orc.nf_free_radius(dim, sb, rm, x) for x in u])
+        assert np.allclose(out, want, rtol=1e-12 if fp64 else 2e-5, atol=0), (sb, rm, out, want)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [0, 1])
 def test_green_log_derivative(hc, orc, dim, fp64):
     """R |G'/G| of the centred Green's function (the extra-drift weight) against the oracle."""
     R = 0.37

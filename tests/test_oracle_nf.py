@@ -242,6 +242,25 @@ def test_series_P_integrates_to_the_boundary_solution(orc, dim, nterms):
         assert abs(tot - exact) <= 1e-9 * exact, (fu, tot, exact)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_series_walk_radius_follows_the_free_space_kernel(orc, dim):
+    """The series walk's in-ball distance r (reading R24) has density proportional to
+    Phi(r) r^{d-1} on [0, r_m] (Phi: e^{-kr}/(4 pi r) in 3D, K_0(kr)/(2 pi) in 2D): its CDF,
+    integrated with scipy, equals the uniform it was drawn from; h(t) is that mass."""
+    from scipy import integrate
+    from scipy import special as sp
+    dens = (lambda r, k: r * math.exp(-k * r)) if dim == 3 else (lambda r, k: r * sp.k0(k * r))
+    for sb, rm in ((45.0, 0.3), (4.0, 0.8), (900.0, 0.5), (1e-4, 0.2)):
+        k = math.sqrt(sb)
+        tot = integrate.quad(dens, 0, rm, args=(k,), epsabs=0, epsrel=1e-12, limit=200)[0]
+        assert abs(orc.nf_h(dim, k * rm) - k * k * tot) <= 1e-10 * k * k * tot
+        for u in (1e-6, 0.1, 0.5, 0.9, 0.999999):
+            r = orc.nf_free_radius(dim, sb, rm, u)
+            assert 0.0 <= r <= rm
+            F = integrate.quad(dens, 0, r, args=(k,), epsabs=0, epsrel=1e-12, limit=200)[0] / tot
+            assert abs(F - u) <= 1e-9, (sb, rm, u, F)
+
+
 NF_CASES = {
     # sigma_bar = sigma' (constant): every inner series stops after its first term
     "screened_ball": (W.screened_ball_problem, lambda p: W.screened_ball_exact(9.0, *p),
@@ -308,11 +327,11 @@ def test_next_flight_in_shell_returns_boundary_value(orc):
 
 @pytest.mark.parametrize("name", ["cube3d", "square2d"])
 def test_next_flight_with_series_is_unbiased_where_sigma_varies(orc, name):
-    """With the series kernels (truncated at 8 terms) the next-flight walk's mean agrees
-    with the exact solution where sigma' varies and the null weights do not vanish;
-    truncation keeps the kernels' low harmonics, and the smooth boundary data and
-    sources carry almost nothing above them.  (The printed approximations are checked
-    only where they are exact.)"""
+    """With the series kernels (truncated at 8 terms) and free-space-kernel in-ball points
+    the next-flight walk's mean agrees with the exact solution where sigma' varies and the
+    null weights do not vanish; truncation keeps the kernels' low harmonics, and the smooth
+    boundary data and sources carry almost nothing above them.  (The printed
+    approximations are checked only where they are exact.)"""
     if name == "cube3d":
         prob, exact = W.cube3d_problem(), W.cube3d_exact
         pts = W.cell_centres(3, 64)[:, W.seeded_subset(64 ** 3, 12, 2)]
@@ -321,7 +340,7 @@ def test_next_flight_with_series_is_unbiased_where_sigma_varies(orc, name):
         prob, exact = W.square2d_problem(), W.square2d_exact
         pts = W.cell_centres(2, 32)[:, W.seeded_subset(1024, 12, 1)]
         sb = orc.sigma_bar(prob)[0]
-    walks = 8192  # the estimates are heavy-tailed: a few thousand walks leave single points at 5 SE
+    walks = 8192
     uh, st, inner = orc.walks_nf(prob, pts, walks, seed=7, eps=1e-4, sigma_bar=sb, series_terms=8)
     m = uh.mean(1)
     se = uh.std(1, ddof=1) / math.sqrt(walks)
