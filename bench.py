@@ -543,7 +543,8 @@ def run_other(args):
         (acc, st), ms = timed(lambda i: ctx.solve_nf(prob, pts, WALKS, 1e-4, sb, seed=i, series_terms=nser),
                               args.steps)
         rms, mse = rms_of(acc)
-        (acc_a, st_a), ms_a = timed(lambda i: ctx.solve_nf(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
+        (acc_a, st_a), ms_a = timed(lambda i: ctx.solve_nf(prob, pts, WALKS, 1e-4, sb, seed=i, series_terms=0),
+                                    args.steps)
         rms_a, mse_a = rms_of(acc_a)
         (acc0, st0), ms0 = timed(lambda i: ctx.solve(prob, pts, WALKS, 1e-4, sb, seed=i), args.steps)
         rms0, mse0 = rms_of(acc0)

@@ -772,10 +772,11 @@ class Context:
         return img, val, dep
 
     def solve_nf(self, prob, pts, walks, eps, sigma_bar, seed=0, walk_offset=0, max_steps=1 << 20,
-                 max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None, series_terms=0):
+                 max_inner=1 << 16, precision="fp32", accum=None, stats=None, stream=None, series_terms=8):
         """Next-flight walks (Sec. 5.2) added to the accumulators; stats 'steps' counts balls
-        (distance queries), 'inner' the in-ball iterations.  series_terms = 0 takes the printed
-        approximate off-centred kernels, N in 1..64 their series with N terms."""
+        (distance queries), 'inner' the in-ball iterations.  series_terms = N in 1..64 takes the
+        off-centred kernels as their series with N terms (in-ball points from the free-space
+        kernel); 0 the printed approximations with uniform in-ball points."""
         import torch
         pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]
@@ -802,7 +803,7 @@ class Context:
         return accum, stats
 
     def walk_estimates_nf(self, prob, pts, walks_per_point, eps, sigma_bar, seed=0, walk_offset=0,
-                          max_steps=1 << 20, max_inner=1 << 16, precision="fp32", stream=None, series_terms=0):
+                          max_steps=1 << 20, max_inner=1 << 16, precision="fp32", stream=None, series_terms=8):
         import torch
         pts = _points(pts, prob.dim, self.device)
         npts = pts.shape[1]

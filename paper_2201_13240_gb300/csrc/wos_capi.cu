@@ -637,6 +637,10 @@ int wos_problem_create(wos_ctx* ctx, const wos_problem_desc* d, wos_problem** ou
     std::vector<wos::MeshNode4> wide;  // the device traverses 4-wide nodes
     int wide_depth = 0;
     wos::mesh_collapse4(nodes, &wide, &wide_depth);
+    static_assert(1 + 4 + 16 <= wos::kMeshTopMax, "top levels staged in shared memory");
+    const int ntop = std::min(wos::mesh_top_first(&wide, wos::kMeshTopLevels), wos::kMeshTopMax);
+    h32->mesh_top = ntop;
+    pr->host64.mesh_top = ntop;
     e = cudaMalloc(&pr->mesh_nodes, wide.size() * sizeof(wos::MeshNode4));
     if (e == cudaSuccess) e = cudaMalloc(&pr->mesh_tris, tri.size() * sizeof(float));
     if (e == cudaSuccess)

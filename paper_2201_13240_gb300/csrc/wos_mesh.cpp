@@ -187,6 +187,42 @@ void mesh_collapse4(const std::vector<MeshNode>& bin, std::vector<MeshNode4>* wi
   if (depth) *depth = d;
 }
 
+int mesh_top_first(std::vector<MeshNode4>* wide, int levels) {
+  std::vector<MeshNode4>& w = *wide;
+  const int n = (int)w.size();
+  std::vector<int> order;  // new position -> old index
+  std::vector<int> level_of(n, 0);
+  std::vector<char> top(n, 0);
+  order.reserve(n);
+  // breadth-first over the interior children down to `levels`
+  std::vector<int> queue = {0};
+  level_of[0] = 1;
+  for (size_t q = 0; q < queue.size(); ++q) {
+    const int v = queue[q];
+    top[v] = 1;
+    order.push_back(v);
+    if (level_of[v] >= levels) continue;
+    for (int i = 0; i < 4; ++i)
+      if (w[v].count[i] == 0) {
+        level_of[w[v].child[i]] = level_of[v] + 1;
+        queue.push_back(w[v].child[i]);
+      }
+  }
+  const int ntop = (int)order.size();
+  for (int v = 0; v < n; ++v)
+    if (!top[v]) order.push_back(v);
+  std::vector<int> pos(n);
+  for (int i = 0; i < n; ++i) pos[order[i]] = i;
+  std::vector<MeshNode4> out(n);
+  for (int i = 0; i < n; ++i) {
+    out[i] = w[order[i]];
+    for (int c = 0; c < 4; ++c)
+      if (out[i].count[c] == 0) out[i].child[c] = pos[out[i].child[c]];
+  }
+  w.swap(out);
+  return ntop;
+}
+
 int mesh_build_bvh(const float* verts, int64_t nverts, const int32_t* tris, int64_t ntris,
                    std::vector<MeshNode>* nodes, std::vector<float>* tri_data, int* depth_out) {
   if (!verts || !tris || nverts < 3 || ntris < 1 || ntris > (int64_t)1 << 30) return -1;

@@ -34,6 +34,13 @@ static_assert(sizeof(MeshNode4) == 128, "MeshNode4 must be one 128-byte line");
 // wide tree.  Wide node 0 is the root.
 void mesh_collapse4(const std::vector<MeshNode>& bin, std::vector<MeshNode4>* wide, int* depth);
 
+// Nodes of the wide tree's top `levels` levels (the root is level 1), placed first in
+// breadth-first order; the other nodes keep their order after them and every child index
+// is renumbered.  Returns how many nodes come first (the kernels stage them in shared
+// memory: every query starts at the root).
+constexpr int kMeshTopLevels = 3;  // at most 1 + 4 + 16 = 21 nodes, 2.7 KB
+int mesh_top_first(std::vector<MeshNode4>* wide, int levels);
+
 // Build the BVH of a closed triangle mesh (host arrays).  tri_data receives 12
 // floats per triangle in leaf order: v0.xyz, -, v1.xyz, -, v2.xyz, -.
 // Returns 0, or -1 for invalid input (out-of-range index, non-finite vertex).

@@ -49,9 +49,16 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
   const DevProblem<R>& P = *reinterpret_cast<const DevProblem<R>*>(smem_raw);
   int* stk_n = nullptr;
   R* stk_d = nullptr;
+  const float* mtop = nullptr;  // the tree's top nodes, staged after the stacks
   if (MESH) {  // this thread's column of the BVH traversal stack, after the problem
     stk_n = reinterpret_cast<int*>(smem_raw + L.problem_bytes) + threadIdx.x;
     stk_d = reinterpret_cast<R*>(smem_raw + L.problem_bytes + sizeof(int) * kMeshStack * kNfBlock) + threadIdx.x;
+    float* top = reinterpret_cast<float*>(smem_raw + L.problem_bytes + (sizeof(int) + sizeof(R)) * kMeshStack * kNfBlock);
+    const int n4 = 8 * min(P.mesh_top, kMeshTopMax);
+    const float4* src = reinterpret_cast<const float4*>(P.mesh_nodes);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) reinterpret_cast<float4*>(top)[i] = __ldg(src + i);
+    __syncthreads();
+    mtop = top;
   }
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
         R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
         bound2 = e0 * e0 + e1 * e1 + e2 * e2;
       }
-      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock);
+      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock, R(1), nullptr, nullptr, mtop);
       if (MESH) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
 template <int DIM, typename R, bool MESH, bool SERIES>
 cudaError_t launch_nf_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = (size_t)L.problem_bytes;
-  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kNfBlock;
+  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kNfBlock + 128 * kMeshTopMax;
   if (smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(wos_nf_kernel<DIM, R, MESH, SERIES>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

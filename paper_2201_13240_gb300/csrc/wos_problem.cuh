@@ -75,11 +75,12 @@ struct DevProblem {
   DevField<R> omega[3];     // extra drift (any vector field); has_drift when any is not ZERO
   int32_t has_drift;
   int32_t pad5;
-  alignas(16) const float* mesh_nodes;  // BVH: 8 floats per node (see wos_mesh.h), device
+  alignas(16) const float* mesh_nodes;  // BVH: 32 floats per 4-wide node (see wos_mesh.h), device
   const float* mesh_tris;   // 12 floats per triangle in leaf order, device
   int32_t ncsg;
   int32_t mg_res;           // mesh distance grid: nodes per axis (0: none)
-  int32_t pad3[2];
+  int32_t mesh_top;         // the first mesh_top nodes are the tree's top levels (staged in shared memory)
+  int32_t pad3;
   const R* mgrid;           // exact distances at the grid nodes, x fastest, device
   const void* mg_pad_ptr;   // keeps the 16-byte layout
   R mg_lo[3], mg_h[3], mg_inv_h[3];
@@ -415,6 +416,7 @@ WOS_HD R g_at(const DevProblem<R>& P, const R* x) {
 // triangle so far.
 // ---------------------------------------------------------------------------
 constexpr int kMeshStack = 32;  // entries of the traversal stack (a full stack repeats the pass: mesh_query)
+constexpr int kMeshTopMax = 21;  // nodes of the BVH's top levels staged in shared memory (1 + 4 + 16)
 
 struct F4 {
   float x, y, z, w;
@@ -533,6 +535,25 @@ WOS_HD I4 ld4i(const float* p) {
   return v;
 #endif
 }
+// 16 bytes of a node staged in shared memory (plain loads: the address is a shared one)
+WOS_HD F4 lds4(const float* p) {
+#if defined(__CUDA_ARCH__)
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return F4{v.x, v.y, v.z, v.w};
+#else
+  return F4{p[0], p[1], p[2], p[3]};
+#endif
+}
+WOS_HD I4 lds4i(const float* p) {
+#if defined(__CUDA_ARCH__)
+  const int4 v = *reinterpret_cast<const int4*>(p);
+  return I4{v.x, v.y, v.z, v.w};
+#else
+  I4 v;
+  memcpy(&v, p, 16);
+  return v;
+#endif
+}
 template <typename R>
 WOS_HD R box_d2_1(const R* x, float lx, float ly, float lz, float hx, float hy, float hz) {
   R dx = w_fmax(w_fmax(R(lx) - x[0], x[0] - R(hx)), R(0));
@@ -543,7 +564,8 @@ WOS_HD R box_d2_1(const R* x, float lx, float ly, float lz, float hx, float hy, 
 
 template <typename R, bool SMEM>
 WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R bound2, int* sn, R* sd,
-                                   int stride, R tau = R(1), const R* pb = nullptr, MeshVisits* vis = nullptr) {
+                                   int stride, R tau = R(1), const R* pb = nullptr, MeshVisits* vis = nullptr,
+                                   const float* top = nullptr) {
   const R x[3] = {x0, x1, x2};
   const float* nodes = P.mesh_nodes;
   const float* tris = P.mesh_tris;
@@ -569,10 +591,20 @@ WOS_FIELD_FN MeshHit<R> mesh_query(const DevProblem<R>& P, R x0, R x1, R x2, R b
     int sp = 0;
     int node = 0;
     for (;;) {
-      const float* nd = nodes + 32 * node;
-      const F4 lx = ld4(nd), ly = ld4(nd + 4), lz = ld4(nd + 8), hx = ld4(nd + 12), hy = ld4(nd + 16),
-               hz = ld4(nd + 20);
-      const I4 ch = ld4i(nd + 24), cn = ld4i(nd + 28);
+      F4 lx, ly, lz, hx, hy, hz;
+      I4 ch, cn;
+      if (top != nullptr && node < P.mesh_top) {
+        // one of the tree's top nodes, staged in shared memory by the kernel
+        const float* nd = top + 32 * node;
+        lx = lds4(nd); ly = lds4(nd + 4); lz = lds4(nd + 8);
+        hx = lds4(nd + 12); hy = lds4(nd + 16); hz = lds4(nd + 20);
+        ch = lds4i(nd + 24); cn = lds4i(nd + 28);
+      } else {
+        const float* nd = nodes + 32 * node;
+        lx = ld4(nd); ly = ld4(nd + 4); lz = ld4(nd + 8);
+        hx = ld4(nd + 12); hy = ld4(nd + 16); hz = ld4(nd + 20);
+        ch = ld4i(nd + 24); cn = ld4i(nd + 28);
+      }
       ++n_nodes;
       R d[4] = {box_d2_1(x, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x), box_d2_1(x, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y),
                 box_d2_1(x, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z), box_d2_1(x, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w)};
@@ -792,7 +824,7 @@ WOS_HD R csg_sdf(const DevProblem<R>& P, const R* x, R* g) {
 template <int DIM, typename R, bool MESH = true>
 WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY), int* stk_n = nullptr,
                   R* stk_d = nullptr, int stk_stride = 0, R tau = R(1), const R* pb = nullptr,
-                  MeshVisits* vis = nullptr) {
+                  MeshVisits* vis = nullptr, const float* top = nullptr) {
   const R* p = P.dom;
 #pragma unroll
   for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
@@ -903,8 +935,9 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
         }
       }
       MeshHit<R> h = (stk_n != nullptr)
-                         ? mesh_query<R, true>(P, x[0], x[1], x[2], bound2, stk_n, stk_d, stk_stride, tau, pb, vis)
-                         : mesh_query<R, false>(P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0, tau, pb, vis);
+                         ? mesh_query<R, true>(P, x[0], x[1], x[2], bound2, stk_n, stk_d, stk_stride, tau, pb, vis,
+                                               top)
+                         : mesh_query<R, false>(P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0, tau, pb, vis, top);
       xb[0] = h.x;
       xb[1] = h.y;
       xb[2] = h.z;

@@ -12,7 +12,7 @@ cudaError_t launch_walks_kernel(const WalkLaunch& L, cudaKernel_t kernel, int re
                                 cudaStream_t stream) {
   const void* fn = reinterpret_cast<const void*>(kernel);
   size_t smem = (size_t)L.problem_bytes;
-  if (L.mesh) smem += (sizeof(int) + (size_t)real_bytes) * kMeshStack * kWalkBlock;
+  if (L.mesh) smem += (sizeof(int) + (size_t)real_bytes) * kMeshStack * kWalkBlock + 128 * kMeshTopMax;
   if (smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return ea;

@@ -174,9 +174,17 @@ __global__ void __launch_bounds__(kWalkBlock,
   // MESH: this thread's column of the BVH traversal stack, after the problem
   int* stk_n = nullptr;
   R* stk_d = nullptr;
+  // and the tree's top nodes (every query starts at the root), staged after the stacks
+  const float* mtop = nullptr;
   if (MESH) {
     stk_n = reinterpret_cast<int*>(smem_raw + L.problem_bytes) + threadIdx.x;
     stk_d = reinterpret_cast<R*>(smem_raw + L.problem_bytes + sizeof(int) * kMeshStack * kWalkBlock) + threadIdx.x;
+    float* top = reinterpret_cast<float*>(smem_raw + L.problem_bytes + (sizeof(int) + sizeof(R)) * kMeshStack * kWalkBlock);
+    const int n4 = 8 * min(Pshared->mesh_top, kMeshTopMax);  // 8 x 16 bytes per node
+    const float4* src = reinterpret_cast<const float4*>(Pshared->mesh_nodes);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) reinterpret_cast<float4*>(top)[i] = __ldg(src + i);
+    __syncthreads();
+    mtop = top;
   }
 
   const int lane = threadIdx.x & 31;
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kWalkBlock,
       }
       const R tau = P.mesh_tau;
       d = distance<DIM, R, MESH>(P, s.x, xb, bound2, stk_n, stk_d, kWalkBlock, tau,
-                                 (bound2 < R(INFINITY)) ? s.xbp : nullptr, &mvis);
+                                 (bound2 < R(INFINITY)) ? s.xbp : nullptr, &mvis, mtop);
       if (tau < R(1) && !(d >= eps)) {
         // a certified radius below eps: the exact distance decides the eps-shell test and
         // gives the closest point for g (a step or two per walk, near the boundary)
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(kWalkBlock,
         R b2 = e0 * e0 + e1 * e1 + e2 * e2;
         R xe[3];
         d = distance<DIM, R, MESH>(P, s.x, xe, (b2 < R(INFINITY)) ? b2 : R(INFINITY), stk_n, stk_d, kWalkBlock,
-                                   R(1), nullptr, &mvis);
+                                   R(1), nullptr, &mvis, mtop);
 #pragma unroll
         for (int i = 0; i < 3; ++i) xb[i] = xe[i];
       }
@@ -554,7 +562,7 @@ template <int DIM, typename R, bool MESH, bool BATCHED, bool WW, bool GRAD = fal
           int MINB = 0>
 cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   size_t smem = BATCHED ? 0 : (size_t)L.problem_bytes;
-  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kWalkBlock;
+  if (MESH) smem += (sizeof(int) + sizeof(R)) * kMeshStack * kWalkBlock + 128 * kMeshTopMax;
   if (smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

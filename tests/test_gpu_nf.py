@@ -63,7 +63,7 @@ def test_fp64_replay_next_flight_per_walk(orc, ctx, wos, name):
     prob = ctx.problem(desc)
     sb = _sb(orc, desc, sb)
     wpp = 16
-    uh, st, stats = ctx.walk_estimates_nf(prob, dev(pts), wpp, eps, sb, seed=9, precision="fp64")
+    uh, st, stats = ctx.walk_estimates_nf(prob, dev(pts), wpp, eps, sb, seed=9, precision="fp64", series_terms=0)
     uo, so, io = orc.walks_nf(desc, pts, wpp, seed=9, eps=eps, sigma_bar=sb)
     uh, st = uh.cpu().numpy(), st.cpu().numpy()
     ok = np.abs(uh - uo) <= 1e-9 * np.maximum(1.0, np.abs(uo))
@@ -76,15 +76,16 @@ def test_fp64_replay_next_flight_per_walk(orc, ctx, wos, name):
         assert s["inner"] == int(io.sum())
 
 
+@pytest.mark.parametrize("nser", [0, 8])
 @pytest.mark.parametrize("name", ["square2d", "cube3d", "screened_ball", "mesh"])
-def test_fp32_next_flight_matches_fp64_per_walk(orc, ctx, name):
+def test_fp32_next_flight_matches_fp64_per_walk(orc, ctx, name, nser):
     mk, ptsf, eps, sb = CASES[name]
     desc = mk()
     pts = ptsf()
     prob = ctx.problem(desc)
     sb = _sb(orc, desc, sb)
-    u64, s64, _ = ctx.walk_estimates_nf(prob, dev(pts), 32, eps, sb, seed=2, precision="fp64")
-    u32, s32, _ = ctx.walk_estimates_nf(prob, dev(pts), 32, eps, sb, seed=2, precision="fp32")
+    u64, s64, _ = ctx.walk_estimates_nf(prob, dev(pts), 32, eps, sb, seed=2, precision="fp64", series_terms=nser)
+    u32, s32, _ = ctx.walk_estimates_nf(prob, dev(pts), 32, eps, sb, seed=2, precision="fp32", series_terms=nser)
     u64, u32 = u64.cpu().numpy(), u32.cpu().numpy()
     ok = np.abs(u32 - u64) <= 1e-3 * np.maximum(1.0, np.abs(u64))
     assert ok.mean() >= 0.95, (name, ok.mean())
@@ -101,10 +102,11 @@ def test_fp32_next_flight_exact_when_sigma_bar_is_sigma(ctx, name, sb):
         pts = W.uniform_in_box(2, 256, 0.02, 0.98, 7)
         exact = W.screened_square_exact(*pts.astype(np.float64))
     prob = ctx.problem(desc)
-    acc, stats = ctx.solve_nf(prob, dev(pts), 4096, 1e-4, sb, seed=1)
-    m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
-    ok, nout, mz = four_se_rule((m - exact) / se)
-    assert ok, (nout, mz)
+    for nser in (0, 8):
+        acc, stats = ctx.solve_nf(prob, dev(pts), 4096, 1e-4, sb, seed=1, series_terms=nser)
+        m, v, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+        ok, nout, mz = four_se_rule((m - exact) / se)
+        assert ok, (nser, nout, mz)
 
 
 @pytest.mark.parametrize("name", ["square2d", "cube3d", "hifreq", "screened_ball", "mesh"])

@@ -27,19 +27,24 @@ extern "C" int build(const float* v, long long nv, const int* t, long long nt, i
   int depth = 0;
   if (wos::mesh_build_bvh(v, nv, t, nt, &bin, &g_tris, &depth) != 0) return -1;
   wos::mesh_collapse4(bin, &g_wide, wdepth);
+  // the top levels first, as the library uploads them; the queries read those nodes through
+  // the staged-node path (here the same host array)
+  g_P.mesh_top = wos::mesh_top_first(&g_wide, wos::kMeshTopLevels);
   *nwide = (int)g_wide.size();
   g_P.mesh_nodes = reinterpret_cast<const float*>(g_wide.data());
   g_P.mesh_tris = g_tris.data();
   return 0;
 }
+extern "C" int top_count() { return g_P.mesh_top; }
 extern "C" void query(const double* x, double bound2, double* out) {
-  wos::MeshHit<double> h = wos::mesh_query<double, false>(g_P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0);
+  wos::MeshHit<double> h = wos::mesh_query<double, false>(g_P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0, 1.0,
+                                                          nullptr, nullptr, g_P.mesh_nodes);
   out[0] = h.d; out[1] = h.x; out[2] = h.y; out[3] = h.z;
 }
 extern "C" void query_tol(const double* x, double bound2, const double* pb, double tau, double* out) {
   wos::MeshVisits v = {0ull, 0ull, 0u};
   wos::MeshHit<double> h = wos::mesh_query<double, false>(g_P, x[0], x[1], x[2], bound2, nullptr, nullptr, 0, tau,
-                                                          pb, &v);
+                                                          pb, &v, g_P.mesh_nodes);
   out[0] = h.d; out[1] = h.x; out[2] = h.y; out[3] = h.z;
   out[4] = (double)v.nodes; out[5] = (double)v.tris; out[6] = (double)v.exhausted;
 }
@@ -68,6 +73,7 @@ def test_wide_bvh_query_equals_brute_force(lib, orc, level):
     nw, wd = C.c_int(), C.c_int()
     assert lib.build(verts.ctypes.data, len(verts), tris.ctypes.data, len(tris), C.byref(nw), C.byref(wd)) == 0
     assert nw.value >= 1 and 1 <= wd.value <= 15
+    assert 1 <= lib.top_count() <= min(21, nw.value)
     pk = orc.pack(desc)
     rng = np.random.default_rng(level)
     pts = np.concatenate([W.uniform_in_ball(3, 120, [0, 0, 0], 0.95, level, 0.0).T.astype(np.float64),
