@@ -39,14 +39,15 @@ EPS = 1e-4
 SEED = 0
 SIGMA_LATTICE = 64
 # Algorithmic work of one walk step of this workload, for a minimal implementation of the
-# step with the fields as code: FP32/INT32 lane operations -- Philox 2 blocks 160, uniforms
-# 18, directions 16, box distance 17, Green's norm 14, radius (table start + one Newton
-# step of the radial CDF) 62, coefficients (alpha, Phi, sigma, u_m with value / gradient /
-# Laplacian, f, the transform) 74, update 12 -> 373; special-function (MUFU) operations --
-# directions 6, Green's norm 3, radius 6, coefficients 12 -> 27.  Every warp instruction
-# takes one issue slot whatever its pipe, and the lanes issue at the FP32 lane rate, so the
-# step needs 400 issue slots; the MUFU pipe (its own rate) is a separate, looser bound.
-LANE_OPS_PER_STEP = 373
+# step with the fields as code: FP32/INT32 lane operations -- one Philox block 80, the six
+# 21-bit uniforms (split 12, conversions 18) 30, directions 16, box distance 17, Green's
+# norm 14, radius (table start + one Newton step of the radial CDF) 62, coefficients
+# (alpha, Phi, sigma, u_m with value / gradient / Laplacian, f, the transform) 74, update
+# 12 -> 305; special-function (MUFU) operations -- directions 6, Green's norm 3, radius 6,
+# coefficients 12 -> 27.  Every warp instruction takes one issue slot whatever its pipe, and
+# the lanes issue at the FP32 lane rate, so the step needs 332 issue slots; the MUFU pipe
+# (its own rate) is a separate, looser bound.
+LANE_OPS_PER_STEP = 305
 MUFU_OPS_PER_STEP = 27
 ISSUE_OPS_PER_STEP = LANE_OPS_PER_STEP + MUFU_OPS_PER_STEP
 RMS_TARGET = 1e-2

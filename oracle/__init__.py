@@ -124,6 +124,7 @@ def _load():
     lib.orc_offcentre_G.restype = C.c_double
     lib.orc_offcentre_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp]
     lib.orc_offcentre_P.restype = C.c_double
+    lib.orc_uniforms21.argtypes = [C.POINTER(C.c_uint32), dp]
     lib.orc_series_G.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_int]
     lib.orc_series_G.restype = C.c_double
     lib.orc_series_P.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_int]
@@ -494,6 +495,14 @@ def offcentre_P(dim, R, sb, u, v):
     uu, vv = np.zeros(3), np.zeros(3)
     uu[:dim], vv[:dim] = u, v
     return _load().orc_offcentre_P(dim, R, sb, _dptr(uu), _dptr(vv))
+
+
+def uniforms21(words):
+    """The six 21-bit uniforms of a 3D step from one Philox block (four uint32 words)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    out = np.zeros(6)
+    _load().orc_uniforms21(w.ctypes.data_as(C.POINTER(C.c_uint32)), _dptr(out))
+    return out
 
 
 def series_G(dim, R, sb, u, v, nterms=0):

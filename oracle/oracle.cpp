@@ -267,6 +267,38 @@ void philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 
 double uniform01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
 
+// Reading R12: a 3D step takes its six uniforms (mu, the radius uniform, two per direction)
+// from one Philox block: 21-bit fields -- each word's top 21 bits, then the low 11 bits of
+// words 0 and 1 each followed by the low 10 bits of words 2 and 3 -- as (f + 1/2) / 2^21.
+void uniforms21(const uint32_t* o, double* u) {
+  const uint32_t f[6] = {o[0] >> 11, o[1] >> 11, o[2] >> 11, o[3] >> 11,
+                         ((o[0] & 0x7ffu) << 10) | (o[2] & 0x3ffu), ((o[1] & 0x7ffu) << 10) | (o[3] & 0x3ffu)};
+  for (int i = 0; i < 6; ++i) u[i] = ((double)f[i] + 0.5) / 2097152.0;
+}
+
+// The step's mu, radius uniform and the two directions (y's and z's), dim 2 or 3
+void step_randoms(int dim, const uint32_t* o0, double* mu, double* ur, double* dy, double* dz) {
+  if (dim == 2) {
+    *mu = uniform01(o0[0]);
+    *ur = uniform01(o0[1]);
+    double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
+    dy[0] = std::cos(ty); dy[1] = std::sin(ty);
+    dz[0] = std::cos(tz); dz[1] = std::sin(tz);
+    return;
+  }
+  double u6[6];
+  uniforms21(o0, u6);
+  *mu = u6[0];
+  *ur = u6[1];
+  // uniform direction on the sphere from two uniforms (Archimedes' projection)
+  double cy = 1.0 - 2.0 * u6[2], py = 2.0 * kPi * u6[3];
+  double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
+  dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
+  double cz = 1.0 - 2.0 * u6[4], pz = 2.0 * kPi * u6[5];
+  double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
+  dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
+}
+
 // ---------------------------------------------------------------------------
 // Fields: sum of separable terms, grids, manufactured source.
 // ---------------------------------------------------------------------------
@@ -918,6 +950,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 double orc_uniform(uint32_t x) { return uniform01(x); }
+void orc_uniforms21(const uint32_t* o, double* u) { uniforms21(o, u); }
 
 void orc_bessel(double x, double out[4]) {
   out[0] = bI0(x);
@@ -1131,25 +1164,10 @@ double orc_walk(const orc_problem* P, const double* x0, uint32_t point, uint32_t
       break;
     }
     double R = d;
-    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4], o1[4];
+    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4];
     philox(ctr, key, o0);
-    double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
-    double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
-    if (dim == 2) {
-      double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
-      dy[0] = std::cos(ty); dy[1] = std::sin(ty);
-      dz[0] = std::cos(tz); dz[1] = std::sin(tz);
-    } else {
-      ctr[3] = 1u;
-      philox(ctr, key, o1);
-      // uniform direction on the sphere from two uniforms (Archimedes' projection)
-      double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
-      double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
-      dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
-      double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
-      double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
-      dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
-    }
+    double mu, ur, dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+    step_randoms(dim, o0, &mu, &ur, dy, dz);
     // the extra drift: the ball's own bound (reading R23) and the mixture sample (R22)
     const bool drift = has_drift(P);
     const double sbk = drift ? ball_bound(P, sb, R) : sb;
@@ -1274,23 +1292,9 @@ double orc_walk_ww(const orc_problem* P, const double* x0, uint32_t point, uint3
       philox(ctr, key, o0);
       ctr[3] = blk0 | 1u;
       philox(ctr, key, o1);
-      double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
-      double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
-      double uww;
-      if (dim == 2) {
-        double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
-        dy[0] = std::cos(ty); dy[1] = std::sin(ty);
-        dz[0] = std::cos(tz); dz[1] = std::sin(tz);
-        uww = uniform01(o1[0]);
-      } else {
-        double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
-        double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
-        dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
-        double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
-        double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
-        dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
-        uww = uniform01(o1[2]);
-      }
+      double mu, ur, dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+      step_randoms(dim, o0, &mu, &ur, dy, dz);
+      const double uww = uniform01(o1[(dim == 2) ? 0 : 2]);  // the window's: block 1, word 0 (2D) or 2 (3D)
       const bool drift = has_drift(P);
       const double sbk = drift ? ball_bound(P, sb, R) : sb;  // readings R22, R23
       double Gn = green_norm(dim, R, sbk);
@@ -1425,24 +1429,10 @@ double orc_walk_grad(const orc_problem* P, const double* x0, uint32_t point, uin
       break;
     }
     double R = d;
-    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4], o1[4];
+    uint32_t ctr[4] = {point, walk, (uint32_t)k, 0u}, o0[4];
     philox(ctr, key, o0);
-    double mu = uniform01(o0[0]), ur = uniform01(o0[1]);
-    double dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
-    if (dim == 2) {
-      double ty = 2.0 * kPi * uniform01(o0[2]), tz = 2.0 * kPi * uniform01(o0[3]);
-      dy[0] = std::cos(ty); dy[1] = std::sin(ty);
-      dz[0] = std::cos(tz); dz[1] = std::sin(tz);
-    } else {
-      ctr[3] = 1u;
-      philox(ctr, key, o1);
-      double cy = 1.0 - 2.0 * uniform01(o0[2]), py = 2.0 * kPi * uniform01(o0[3]);
-      double sy = std::sqrt(std::fmax(0.0, 1.0 - cy * cy));
-      dy[0] = sy * std::cos(py); dy[1] = sy * std::sin(py); dy[2] = cy;
-      double cz = 1.0 - 2.0 * uniform01(o1[0]), pz = 2.0 * kPi * uniform01(o1[1]);
-      double sz = std::sqrt(std::fmax(0.0, 1.0 - cz * cz));
-      dz[0] = sz * std::cos(pz); dz[1] = sz * std::sin(pz); dz[2] = cz;
-    }
+    double mu, ur, dy[3] = {0, 0, 0}, dz[3] = {0, 0, 0};
+    step_randoms(dim, o0, &mu, &ur, dy, dz);
     double Gn = green_norm(dim, R, sb);
     // the first ball's sample weights grad G / G (~ 1/r at the centre): the mixture sample
     // of reading R22 bounds it (mixw = 1 on the later balls)

@@ -120,6 +120,9 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* uniform in (0,1): (x + 1/2) 2^-32 */
 double orc_uniform(uint32_t x);
+/* Reading R12, 3D steps: the six uniforms (mu, radius, two per direction) of one Philox
+   block o[4] as 21-bit fields (see oracle.cpp). */
+void orc_uniforms21(const uint32_t* o, double* u);
 
 /* Bessel I0, I1, K0, K1 as used by the oracle (C++17 special functions). */
 void orc_bessel(double x, double out[4]);

@@ -292,22 +292,27 @@ __global__ void __launch_bounds__(kAdjBlock, 4) WOS_ADJOINT_KERNEL(AdjLaunch L) 
       ends = !(d >= eps) || k >= max_k;
       dd = w_fmax(d, R(0));
       U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
-      mu = to_uniform<R>(r0.x);
-      const R ur = to_uniform<R>(r0.y);
+      R ur;
       R dy[3] = {R(0), R(0), R(0)};
       if (DIM == 2) {
+        mu = to_uniform<R>(r0.x);
+        ur = to_uniform<R>(r0.y);
         w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
         w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
       } else {
-        U4 r1 = philox4x32_10(U4{p, w, k, 1u}, key0, key1);
-        R cy = R(1) - R(2) * to_uniform<R>(r0.z);
+        // the walk kernel's six 21-bit uniforms of one block
+        uint32_t f[6];
+        split21(r0, f);
+        mu = u21<R>(f[0]);
+        ur = u21<R>(f[1]);
+        R cy = R(1) - R(2) * u21<R>(f[2]);
         R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
         R sp_, cp_;
-        w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
+        w_sincospi2(u21<R>(f[3]), &sp_, &cp_);
         dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
-        R cz = R(1) - R(2) * to_uniform<R>(r1.x);
+        R cz = R(1) - R(2) * u21<R>(f[4]);
         R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
-        w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
+        w_sincospi2(u21<R>(f[5]), &sp_, &cp_);
         dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
       }
       R a = s_root * dd;

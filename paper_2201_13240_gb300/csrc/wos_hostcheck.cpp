@@ -234,6 +234,15 @@ int wos_hc_nf_free(int dim, int fp64, int which, double sb, double rm, const dou
   return 0;
 }
 
+// the 3D step's six 21-bit uniforms of Philox blocks w[4 i .. 4 i + 3] (out[6 i + j])
+void wos_hc_uniforms21(int fp64, const uint32_t* w, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t f[6];
+    wos::split21(wos::U4{w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]}, f);
+    for (int j = 0; j < 6; ++j) out[6 * i + j] = fp64 ? wos::u21<double>(f[j]) : (double)wos::u21<float>(f[j]);
+  }
+}
+
 // R |G'/G| of the centred Green's function at rho = r/R
 void wos_hc_green_dlog(int dim, int fp64, double a, const double* rho, int64_t n, double* out) {
   for (int64_t i = 0; i < n; ++i) {

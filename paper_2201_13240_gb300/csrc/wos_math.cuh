@@ -211,6 +211,29 @@ WOS_HD double to_uniform<double>(uint32_t x) {
   return ((double)x + 0.5) * 2.3283064365386962890625e-10;
 }
 
+// 3D steps draw six uniforms from one Philox block: the top 21 bits of each word, and two
+// more fields of 21 bits from the words' low bits, ((w0 & 0x7ff) << 10) | (w2 & 0x3ff) and
+// ((w1 & 0x7ff) << 10) | (w3 & 0x3ff) -- disjoint bits, so the six are independent.  A
+// field f gives (f + 1/2) 2^-21 in (0, 1), exact and equal in FP32 and FP64.
+template <typename R>
+WOS_HD R u21(uint32_t f);
+template <>
+WOS_HD float u21<float>(uint32_t f) {
+  return u32_bits_as_float(0x3f800000u | (f << 2)) - 0.99999976158142089844f;  // 1 + f 2^-21, minus 1 - 2^-22
+}
+template <>
+WOS_HD double u21<double>(uint32_t f) {
+  return ((double)f + 0.5) * 4.76837158203125e-07;
+}
+WOS_HD void split21(U4 r, uint32_t* f) {
+  f[0] = r.x >> 11;
+  f[1] = r.y >> 11;
+  f[2] = r.z >> 11;
+  f[3] = r.w >> 11;
+  f[4] = ((r.x & 0x7ffu) << 10) | (r.z & 0x3ffu);
+  f[5] = ((r.y & 0x7ffu) << 10) | (r.w & 0x3ffu);
+}
+
 // ---------------------------------------------------------------------------
 // Bessel functions, FP32: Abramowitz & Stegun 9.8.1-9.8.8 (|error| <~ 2e-7 on
 // the scaled quantities).  *_s are exponentially scaled: i0s(x) = e^{-x} I0(x),

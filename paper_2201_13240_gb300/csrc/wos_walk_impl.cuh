@@ -300,23 +300,27 @@ __global__ void __launch_bounds__(kWalkBlock,
     const uint32_t blk0 = WW ? (s.bid << 2) : 0u;  // branch b of a split walk: block word (b << 2) | block
 
     U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, blk0}, key0, key1);
-    R mu = to_uniform<R>(r0.x), ur = to_uniform<R>(r0.y);
+    R mu, ur;
     R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
-    R uww3 = R(0);  // 3D: the weight window's uniform (block 1 word 2)
     if (DIM == 2) {
+      mu = to_uniform<R>(r0.x);
+      ur = to_uniform<R>(r0.y);
       w_sincospi2(to_uniform<R>(r0.z), &dy[1], &dy[0]);
       w_sincospi2(to_uniform<R>(r0.w), &dz[1], &dz[0]);
     } else {
-      U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1);
-      uww3 = to_uniform<R>(r1.z);
-      R cy = R(1) - R(2) * to_uniform<R>(r0.z);
+      // six 21-bit uniforms of the one block: mu, ur, the two directions
+      uint32_t f[6];
+      split21(r0, f);
+      mu = u21<R>(f[0]);
+      ur = u21<R>(f[1]);
+      R cy = R(1) - R(2) * u21<R>(f[2]);
       R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
       R sp_, cp_;
-      w_sincospi2(to_uniform<R>(r0.w), &sp_, &cp_);
+      w_sincospi2(u21<R>(f[3]), &sp_, &cp_);
       dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
-      R cz = R(1) - R(2) * to_uniform<R>(r1.x);
+      R cz = R(1) - R(2) * u21<R>(f[4]);
       R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
-      w_sincospi2(to_uniform<R>(r1.y), &sp_, &cp_);
+      w_sincospi2(u21<R>(f[5]), &sp_, &cp_);
       dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
     }
     // DRIFT: the ball's own bound max(sigma_bar, 10 B / d) with B the problem's drift bound
@@ -482,7 +486,9 @@ __global__ void __launch_bounds__(kWalkBlock,
       if (WW) {
         R aw = w_fabs(s.W);
         if (aw < ww_lo || aw > ww_hi) {
-          R uww = (DIM == 3) ? uww3 : to_uniform<R>(philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1).x);
+          // the window's own uniform: block 1, word 0 (2D) or word 2 (3D)
+          const U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1);
+          R uww = to_uniform<R>((DIM == 3) ? r1.z : r1.x);
           if (aw < ww_lo) {  // Russian roulette: survive with |W| / lo, at weight lo
             if (uww < aw / ww_lo) s.W = (s.W < R(0)) ? -ww_lo : ww_lo;
             else s.dead = true;

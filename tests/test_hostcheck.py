@@ -244,6 +244,21 @@ def test_series_walk_sampling(hc, orc, dim, fp64):
         assert np.allclose(out, want, rtol=1e-12 if fp64 else 2e-5, atol=0), (sb, rm, out, want)
 
 
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_uniforms21_equal_the_oracle(hc, orc, fp64):
+    """The 3D step's six 21-bit uniforms (split and conversion) equal the oracle's exactly, in
+    both precisions (the FP32 and FP64 walks draw identical values)."""
+    rng = np.random.default_rng(3)
+    w = rng.integers(0, 2 ** 32, size=(500, 4), dtype=np.uint64).astype(np.uint32)
+    w[0] = 0
+    w[1] = 0xFFFFFFFF
+    out = np.zeros(6 * len(w))
+    hc.wos_hc_uniforms21(fp64, np.ascontiguousarray(w).ctypes.data_as(C.POINTER(C.c_uint32)), len(w),
+                         out.ctypes.data_as(DP))
+    want = np.array([orc.uniforms21(x) for x in w]).ravel()
+    assert np.array_equal(out, want)
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_green_log_derivative(hc, orc, dim, fp64):

@@ -29,3 +29,40 @@ def test_philox_counter_words_uniform_chi2(orc):
         hist = np.bincount((words[:, w] >> np.uint64(26)).astype(np.int64), minlength=64)
         chi2 = ((hist - n / 64) ** 2 / (n / 64)).sum()
         assert chi2 < 63 + 5 * np.sqrt(2 * 63)
+
+
+def test_six_uniforms_of_a_3d_step_use_every_bit_once(orc):
+    """The 3D step's six 21-bit uniforms (reading R12) read disjoint bits of the block: a
+    single set bit moves at most one of them, each takes 21 bits, and 126 of the 128 bits are
+    used.  Each is (f + 1/2)/2^21 for a 21-bit integer f, on that grid inside (0, 1)."""
+    base = orc.uniforms21([0, 0, 0, 0])
+    assert np.all(base == 0.5 / 2 ** 21)
+    hits = np.zeros(6, dtype=int)
+    unused = 0
+    for word in range(4):
+        for bit in range(32):
+            w = [0, 0, 0, 0]
+            w[word] = 1 << bit
+            moved = np.flatnonzero(orc.uniforms21(w) != base)
+            assert len(moved) <= 1, (word, bit, moved)
+            if len(moved):
+                hits[moved[0]] += 1
+            else:
+                unused += 1
+    assert list(hits) == [21] * 6 and unused == 2
+    u = orc.uniforms21([0xFFFFFFFF] * 4)
+    assert np.all(u == (2 ** 21 - 0.5) / 2 ** 21)
+
+
+def test_six_uniforms_are_uniform_and_uncorrelated(orc):
+    """Over consecutive Philox counters each of the six is uniform (chi^2, 64 bins) and the
+    pairwise correlations vanish (|r| < 4 / sqrt(n))."""
+    n = 20000
+    u = np.array([orc.uniforms21(orc.philox4x32_10([i, 5, 2, 0], [3, 9])) for i in range(n)])
+    for j in range(6):
+        hist = np.bincount(np.minimum((u[:, j] * 64).astype(int), 63), minlength=64)
+        chi2 = ((hist - n / 64) ** 2 / (n / 64)).sum()
+        assert chi2 < 120, (j, chi2)  # 63 dof: p < 1e-5 beyond ~120
+    r = np.corrcoef(u.T)
+    off = r[~np.eye(6, dtype=bool)]
+    assert np.all(np.abs(off) < 4 / np.sqrt(n)), off
