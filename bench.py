@@ -560,6 +560,36 @@ def run_other(args):
         extra["delta_tracking_ms"] = ms0
         extra["delta_tracking_steps_per_walk"] = s0["steps"] / max(s0["walks"], 1)
         extra["delta_tracking_normalised_rms"] = rms0
+        # Sec. 5.2's point: next-flight walks take one distance query per ball, flat in
+        # sigma_bar, where delta tracking takes one per step.  On the triangle mesh (the
+        # manufactured problem on the displaced icosphere, certified radii) at the problem's
+        # sigma_bar and at 8 times it
+        if not args.no_nf_mesh:
+            dm = W.mesh_manufactured_problem(level=7, tol=args.mesh_tol)
+            pm = ctx.problem(dm)
+            pm.specialize(("fp32",), ("plain",))
+            sbm = ctx.sigma_bar(pm, 48)[0]
+            pts_m_np = W.mesh_interior_points(16384, seed=0)
+            pts_m = torch.from_numpy(pts_m_np).cuda()
+            exm = W.cube3d_exact(*pts_m_np.astype(np.float64))
+            wm = 256
+            mesh_leg = {"points": 16384, "walks": wm, "mesh_tol": args.mesh_tol}
+            for fac in (1, 8):
+                (a_nf, s_nf), ms_nf = timed(lambda i: ctx.solve_nf(prob=pm, pts=pts_m, walks=wm, eps=1e-4,
+                                                                   sigma_bar=fac * sbm, seed=i, series_terms=nser),
+                                            args.steps)
+                (a_dt, s_dt), ms_dt = timed(lambda i: ctx.solve(pm, pts_m, wm, 1e-4, fac * sbm, seed=i), args.steps)
+                dn, dd_ = wos.stats_dict(s_nf), wos.stats_dict(s_dt)
+                mn = ctx.finalize(a_nf)[0].cpu().numpy()
+                md = ctx.finalize(a_dt)[0].cpu().numpy()
+                mesh_leg[f"sigma_bar_x{fac}"] = {
+                    "sigma_bar": fac * sbm,
+                    "next_flight": {"ms": ms_nf, "balls_per_walk": dn["steps"] / max(dn["walks"], 1),
+                                    "inner_per_walk": dn["inner"] / max(dn["walks"], 1),
+                                    "normalised_rms": float(np.linalg.norm(mn - exm) / np.linalg.norm(exm))},
+                    "delta_tracking": {"ms": ms_dt, "steps_per_walk": dd_["steps"] / max(dd_["walks"], 1),
+                                       "normalised_rms": float(np.linalg.norm(md - exm) / np.linalg.norm(exm))}}
+            extra["mesh"] = mesh_leg
         cfg = {"workload": f"cube3d_drift_manufactured, next-flight walks (off-centred G, P as the series of "
                            f"{nser} terms): {GRID}^3 points x {WALKS} walks, eps 1e-4; steps count balls",
                "sigma_bar": sb}
@@ -736,6 +766,16 @@ def run_other(args):
             gb.set_schedule(**batch.schedule())
             (_, gst), gms = timed(lambda i: ctx.solve_batch(gb, pts, wt, 1e-3, seed=0), args.steps)
             extra["generic_kernel"] = {"ms": gms, "steps_per_s": wos.stats_dict(gst)["steps"] / (gms * 1e-3)}
+        # L2 roofline of the batched step: the grid taps it reads per step (alpha and Phi cubic
+        # B-splines with derivatives, 16 taps each; sigma and f bilinear, 4 each; 4 B a tap)
+        # over the kernel time, against the L2 read rate measured here
+        l2_peak = ctx.measure_peak("l2_read", 32 << 20)[0]
+        bps = 4.0 * (16 + 16 + 4 + 4)
+        steps_b = wos.stats_dict(st)["steps"]
+        extra["l2"] = {"bytes_per_step": bps, "gb_per_s": bps * steps_b / (ms * 1e-3) / 1e9,
+                       "peak_gb_per_s": l2_peak / 1e9, "frac": bps * steps_b / (ms * 1e-3) / l2_peak,
+                       "basis": "algorithmic bytes of the grid taps per step / kernel time; peak: "
+                                "wos_measure_peak L2 read (ncu reads ~625 B per step of 32-byte sectors)"}
         cfg = {"workload": f"{args.problems} 2D problems (disk/annulus/rounded box, 64^2 noise grids), "
                            f"{npts} points, {int(walks_np.sum())} walks, one launch in a CUDA graph, eps 1e-3"}
     elif wl == "inverse":
@@ -812,6 +852,7 @@ def main():
     ap.add_argument("--problems", type=int, default=4096, help="batch workload: problems")
     ap.add_argument("--write-image", default="", help="slice workload: write the last frame as a PPM file")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default launch schedule")
+    ap.add_argument("--no-nf-mesh", action="store_true", help="nf workload: skip the triangle-mesh leg")
     ap.add_argument("--nf-series", type=int, default=8,
                     help="nf workload: terms of the off-centred kernels' series (1..64)")
     ap.add_argument("--kernel", default="specialised", choices=["specialised", "generic"],

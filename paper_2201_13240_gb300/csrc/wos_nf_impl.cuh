@@ -154,10 +154,25 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
       R xb[3];
       R bound2 = R(INFINITY);
       if (MESH && k > 0) {
+        // the previous ball's boundary point bounds the query (NaN when none is known)
         R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
-        bound2 = e0 * e0 + e1 * e1 + e2 * e2;
+        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (b2 < R(INFINITY)) bound2 = b2;
       }
-      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock, R(1), nullptr, nullptr, mtop);
+      // meshes: the ball takes the problem's certified radius (any ball inside the domain
+      // keeps the series' identities), and the exact distance decides the eps-shell test
+      const R tau = MESH ? P.mesh_tau : R(1);
+      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock, tau,
+                                   (bound2 < R(INFINITY)) ? xbp : nullptr, nullptr, mtop);
+      if (MESH && tau < R(1) && !(d >= eps)) {
+        R e0 = x[0] - xb[0], e1 = x[1] - xb[1], e2 = x[2] - xb[2];
+        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+        R xe[3];
+        d = distance<DIM, R, MESH>(P, x, xe, (b2 < R(INFINITY)) ? b2 : R(INFINITY), stk_n, stk_d, kNfBlock, R(1),
+                                   nullptr, nullptr, mtop);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xb[i] = xe[i];
+      }
       if (MESH) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
