@@ -346,19 +346,22 @@ def test_csg_fp64_replay_and_fp32_parity(orc, ctx, name):
 
 def test_mesh_distance_grid_fp32_exact_solution(orc, ctx):
     """Mesh walks with the distance grid (radius: the grid's Lipschitz lower bound away from
-    the boundary) against the manufactured solution, and their step count against exact radii."""
+    the boundary), alone and with certified radii near the boundary, against the manufactured
+    solution, and their step count against exact radii."""
     pts = W.mesh_interior_points(128, 13)
     exact = W.cube3d_exact(*pts.astype(np.float64))
     res = {}
-    for grid in (0, 64):
-        desc = W.mesh_manufactured_problem(level=6, dist_grid=grid)
+    for grid, tol in ((0, 0.0), (64, 0.0), (64, 0.1)):
+        desc = W.mesh_manufactured_problem(level=6, dist_grid=grid, tol=tol)
         prob = ctx.problem(desc)
         sb = orc.sigma_bar(desc, 48)[0]
         m, se, st, _ = _gpu_solve(ctx, prob, pts, 4096, 1e-4, sb, seed=8)
         ok, nout, mz = four_se_rule((m - exact) / se)
-        assert ok, (grid, nout, mz)
-        res[grid] = st[0] / st[1]
-    assert res[64] < 1.2 * res[0]
+        assert ok, (grid, tol, nout, mz)
+        res[(grid, tol)] = st[0] / st[1]
+    assert res[(64, 0.0)] < 1.2 * res[(0, 0.0)]
+    # the grid with certified radii near the boundary (both lower bounds of the distance)
+    assert res[(64, 0.1)] < 1.4 * res[(0, 0.0)]
 
 
 @pytest.mark.parametrize("tol", [0.1, 0.25])
