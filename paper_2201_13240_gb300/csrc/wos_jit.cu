@@ -250,6 +250,15 @@ std::string jit_source(const DevProblem<double>& P) {
   s += "// walk kernel specialised to one problem (" + std::to_string(dim) + "D): generated field code\n";
   s += "#define WOS_JIT_FIELDS 1\n";
   s += "#define WOS_JIT_F_KIND " + std::to_string(P.f.kind) + "\n";
+  // analytic domains: the kind and its parameters as constants (meshes and CSG lists keep
+  // their descriptors)
+  if (P.domain_kind == D_BOX || P.domain_kind == D_BALL || P.domain_kind == D_ANNULUS ||
+      P.domain_kind == D_ROUNDED_BOX) {
+    s += "#define WOS_JIT_DOMAIN_KIND " + std::to_string(P.domain_kind) + "\n";
+    s += "#define WOS_JIT_DOMAIN_PARAMS {";
+    for (int i = 0; i < 16; ++i) s += (i ? ", " : "") + lit(P.dom[i]);
+    s += "}\n";
+  }
   // resident blocks per SM: 3D 7 (72 registers), 2D 8 (64 registers), neither spills
   s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 7\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
   s += "#include \"wos_walk_impl.cuh\"\n#include \"wos_adjoint_impl.cuh\"\n\nnamespace wos {\n\n";

@@ -825,10 +825,18 @@ template <int DIM, typename R, bool MESH = true>
 WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINITY), int* stk_n = nullptr,
                   R* stk_d = nullptr, int stk_stride = 0, R tau = R(1), const R* pb = nullptr,
                   MeshVisits* vis = nullptr, const float* top = nullptr) {
+#if defined(WOS_JIT_DOMAIN_KIND)
+  // a kernel compiled for one problem with an analytic domain: its kind and parameters are
+  // constants of the generated source
+  const R p[16] = WOS_JIT_DOMAIN_PARAMS;
+  constexpr int kind = WOS_JIT_DOMAIN_KIND;
+#else
   const R* p = P.dom;
+  const int kind = P.domain_kind;
+#endif
 #pragma unroll
   for (int d = 0; d < 3; ++d) xb[d] = (d < DIM) ? x[d] : R(0);
-  switch (P.domain_kind) {
+  switch (kind) {
     case D_BOX: {
       R best = x[0] - p[0];
       int bd = 0;
@@ -850,7 +858,7 @@ WOS_HD R distance(const DevProblem<R>& P, const R* x, R* xb, R bound2 = R(INFINI
       for (int d = 0; d < DIM; ++d) { v[d] = x[d] - p[d]; r2 += v[d] * v[d]; }
       R r = w_sqrt(r2);
       R dist, rad;
-      if (P.domain_kind == D_BALL) {
+      if (kind == D_BALL) {
         dist = p[3] - r;
         rad = p[3];
       } else {
