@@ -149,119 +149,133 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
     if (__ballot_sync(kAll, active) == 0u) break;
     if (!active) continue;
 
-    if (phase == 0) {
-      // ---- a new ball: distance query, exit point, first boundary term ----
-      R xb[3];
-      R bound2 = R(INFINITY);
-      if (MESH && k > 0) {
-        // the previous ball's boundary point bounds the query (NaN when none is known)
-        R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
-        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
-        if (b2 < R(INFINITY)) bound2 = b2;
-      }
-      // meshes: the ball takes the problem's certified radius (any ball inside the domain
-      // keeps the series' identities), and the exact distance decides the eps-shell test
-      const R tau = MESH ? P.mesh_tau : R(1);
-      R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock, tau,
-                                   (bound2 < R(INFINITY)) ? xbp : nullptr, nullptr, mtop);
-      if (MESH && tau < R(1) && !(d >= eps)) {
-        R e0 = x[0] - xb[0], e1 = x[1] - xb[1], e2 = x[2] - xb[2];
-        R b2 = e0 * e0 + e1 * e1 + e2 * e2;
-        R xe[3];
-        d = distance<DIM, R, MESH>(P, x, xe, (b2 < R(INFINITY)) ? b2 : R(INFINITY), stk_n, stk_d, kNfBlock, R(1),
-                                   nullptr, nullptr, mtop);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) xb[i] = xe[i];
-      }
-      if (MESH) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
-      }
-      const bool shell = !(d >= eps);
-      if (shell || k >= max_k) {
-        if (shell) acc += W * w_exp(gamma_at<DIM>(P, x)) * g_at<DIM>(P, xb);
-        else capped = true;
-        if (k == 0 && !(d > R(0))) ++st_outside;
-        double acc_d = (double)acc;
-        if (accumulate && p != acc_p) {
-          if (acc_p != kNoPoint) {
-            R x0[3];
-#pragma unroll
-            for (int dd = 0; dd < 3; ++dd)
-              x0[dd] = (dd < DIM) ? R(__ldg(&L.pts[(int64_t)dd * L.npts + (int64_t)acc_p])) : R(0);
-            double e0 = exp(-(double)gamma_at<DIM>(P, x0));
-            atomicAdd(&L.sum[acc_p], s1 * e0);
-            atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
-            atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+    // A lane whose ball's series stops sets up its next ball in the same iteration: with
+    // about one inner iteration per ball, every lane then runs the same sequence in an
+    // iteration (the roulette that ends a ball, the next ball's query and set-up, its first
+    // inner iteration) instead of half the lanes idling through the others' set-ups.  A new
+    // ball's first roulette never stops (T = 1), so two passes suffice.
+    U4 r1 = U4{0u, 0u, 0u, 0u};
+    R pRR = R(1);
+    bool ended = false;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (phase == 0) {
+        // ---- a new ball: distance query, exit point, first boundary term ----
+        R xb[3];
+        R bound2 = R(INFINITY);
+        if (MESH && k > 0) {
+          // the previous ball's boundary point bounds the query (NaN when none is known)
+          R e0 = x[0] - xbp[0], e1 = x[1] - xbp[1], e2 = x[2] - xbp[2];
+          R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+          if (b2 < R(INFINITY)) bound2 = b2;
+        }
+        // meshes: the ball takes the problem's certified radius (any ball inside the domain
+        // keeps the series' identities), and the exact distance decides the eps-shell test
+        const R tau = MESH ? P.mesh_tau : R(1);
+        R d = distance<DIM, R, MESH>(P, x, xb, bound2, stk_n, stk_d, kNfBlock, tau,
+                                     (bound2 < R(INFINITY)) ? xbp : nullptr, nullptr, mtop);
+        if (MESH && tau < R(1) && !(d >= eps)) {
+          R e0 = x[0] - xb[0], e1 = x[1] - xb[1], e2 = x[2] - xb[2];
+          R b2 = e0 * e0 + e1 * e1 + e2 * e2;
+          R xe[3];
+          d = distance<DIM, R, MESH>(P, x, xe, (b2 < R(INFINITY)) ? b2 : R(INFINITY), stk_n, stk_d, kNfBlock, R(1),
+                                     nullptr, nullptr, mtop);
+  #pragma unroll
+          for (int i = 0; i < 3; ++i) xb[i] = xe[i];
+        }
+        if (MESH) {
+  #pragma unroll
+          for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
+        }
+        const bool shell = !(d >= eps);
+        if (shell || k >= max_k) {
+          if (shell) acc += W * w_exp(gamma_at<DIM>(P, x)) * g_at<DIM>(P, xb);
+          else capped = true;
+          if (k == 0 && !(d > R(0))) ++st_outside;
+          double acc_d = (double)acc;
+          if (accumulate && p != acc_p) {
+            if (acc_p != kNoPoint) {
+              R x0[3];
+  #pragma unroll
+              for (int dd = 0; dd < 3; ++dd)
+                x0[dd] = (dd < DIM) ? R(__ldg(&L.pts[(int64_t)dd * L.npts + (int64_t)acc_p])) : R(0);
+              double e0 = exp(-(double)gamma_at<DIM>(P, x0));
+              atomicAdd(&L.sum[acc_p], s1 * e0);
+              atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
+              atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+            }
+            acc_p = p;
+            s1 = 0.0;
+            s2 = 0.0;
+            n_acc = 0;
           }
-          acc_p = p;
-          s1 = 0.0;
-          s2 = 0.0;
-          n_acc = 0;
+          s1 += acc_d;
+          s2 += acc_d * acc_d;
+          ++n_acc;
+          if (L.uhat != nullptr) {
+            R x0[3];
+  #pragma unroll
+            for (int dd = 0; dd < 3; ++dd) x0[dd] = (dd < DIM) ? R(__ldg(&L.pts[(int64_t)dd * L.npts + (int64_t)p])) : R(0);
+            L.uhat[item] = acc_d * exp(-(double)gamma_at<DIM>(P, x0));
+            L.steps_out[item] = (int64_t)k;
+          }
+          st_steps += k;
+          ++st_walks;
+          if (capped) ++st_capped;
+          if (!isfinite(acc_d)) ++st_nonfinite;
+          active = false;
+          ended = true;
+          break;
         }
-        s1 += acc_d;
-        s2 += acc_d * acc_d;
-        ++n_acc;
-        if (L.uhat != nullptr) {
-          R x0[3];
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) x0[dd] = (dd < DIM) ? R(__ldg(&L.pts[(int64_t)dd * L.npts + (int64_t)p])) : R(0);
-          L.uhat[item] = acc_d * exp(-(double)gamma_at<DIM>(P, x0));
-          L.steps_out[item] = (int64_t)k;
+        Rb = d;
+        ball.init(s_root, Rb);
+        if (SERIES) {
+          nf_series_ball<DIM, R>(s_root * Rb, nser, ser_p, ser_ra);
+          ser_n0 = nser + 12 + (int)w_fmin(s_root * Rb, R(4096));
         }
-        st_steps += k;
-        ++st_walks;
-        if (capped) ++st_capped;
-        if (!isfinite(acc_d)) ++st_nonfinite;
-        active = false;
-        continue;
+        U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
+        R dz[3] = {R(0), R(0), R(0)};
+        if (DIM == 2) {
+          w_sincospi2(to_uniform<R>(r0.x), &dz[1], &dz[0]);
+        } else {
+          R cz = R(1) - R(2) * to_uniform<R>(r0.x);
+          R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+          R sp_, cp_;
+          w_sincospi2(to_uniform<R>(r0.y), &sp_, &cp_);
+          dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
+        }
+  #pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          vz[i] = Rb * dz[i];
+          uc[i] = R(0);
+        }
+        T = R(1);
+        Ttr = ball.pcentre;  // P(x, z) |dB| at the centre
+        Tsrc = R(0);
+        j = 0;
+        phase = 1;
       }
-      Rb = d;
-      ball.init(s_root, Rb);
-      if (SERIES) {
-        nf_series_ball<DIM, R>(s_root * Rb, nser, ser_p, ser_ra);
-        ser_n0 = nser + 12 + (int)w_fmin(s_root * Rb, R(4096));
+      // ---- the roulette of the ball's series ----
+      r1 = philox4x32_10(U4{p, w, k, j + 1u}, key0, key1);
+      pRR = w_fmin(R(1), w_fabs(T));
+      bool stop = pRR < to_uniform<R>(r1.x);
+      if (!stop && j >= max_j) {
+        stop = true;
+        capped = true;
       }
-      U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
-      R dz[3] = {R(0), R(0), R(0)};
-      if (DIM == 2) {
-        w_sincospi2(to_uniform<R>(r0.x), &dz[1], &dz[0]);
-      } else {
-        R cz = R(1) - R(2) * to_uniform<R>(r0.x);
-        R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
-        R sp_, cp_;
-        w_sincospi2(to_uniform<R>(r0.y), &sp_, &cp_);
-        dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
-      }
+      if (stop) {
+        acc += W * Tsrc;
+        W *= Ttr;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        vz[i] = Rb * dz[i];
-        uc[i] = R(0);
+        for (int i = 0; i < DIM; ++i) x[i] += vz[i];
+        ++k;
+        phase = 0;
+        continue;  // the next pass sets up the next ball
       }
-      T = R(1);
-      Ttr = ball.pcentre;  // P(x, z) |dB| at the centre
-      Tsrc = R(0);
-      j = 0;
-      phase = 1;
+      break;
     }
+    if (ended || phase == 0) continue;
 
     // ---- one inner iteration of the ball's series ----
-    U4 r1 = philox4x32_10(U4{p, w, k, j + 1u}, key0, key1);
-    R pRR = w_fmin(R(1), w_fabs(T));
-    bool stop = pRR < to_uniform<R>(r1.x);
-    if (!stop && j >= max_j) {
-      stop = true;
-      capped = true;
-    }
-    if (stop) {
-      acc += W * Tsrc;
-      W *= Ttr;
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) x[i] += vz[i];
-      ++k;
-      phase = 0;
-      continue;
-    }
     T /= pRR;
     // next in-ball point: a uniform direction w (words z, w) and a distance (word y), uniform
     // in the ball (printed approximations) or from the free-space kernel (series)
