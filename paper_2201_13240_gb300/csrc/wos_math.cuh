@@ -972,9 +972,11 @@ struct Radial3 {
     R x = a * rho;
     R e1 = w_exp(-x);             // e^{-a rho}
     R e2 = w_exp(-a * (R(2) - rho));  // e^{-a(2 - rho)} = e^{-2a} e^{a rho}
-    R hm = h(-x, e1);
-    // e^{-2a} h(a rho) = e^{-2a} - e2 (1 - x); series branch for small x
-    R hp = (x < R(0.5)) ? e2a * h(x, R(0)) : e2a - e2 * (R(1) - x);
+    // h(-x) = 1 - e^{-x}(1 + x) = -expm1(-x) - x e^{-x} and e^{-2a} h(x) = e^{-2a} - e2 (1 - x),
+    // without a branch on x: both differences lose about x eps of F's absolute accuracy (F is
+    // divided by D >= 1 - 2/e - e^{-2} for a >= 1), far inside the sampler's tolerance
+    R hm = -w_expm1(-x) - x * e1;
+    R hp = e2a - e2 * (R(1) - x);
     *F = (hm - hp) * invD;
     *pdf = a * x * (e1 - e2) * invD;
   }
