@@ -238,3 +238,47 @@ def test_specialised_adjoints_equal_the_generic_ones(wos, orc, setup):
     for node in pick_nodes(sig, pts, k=3):
         fd = oracle_fd(orc, sig, pts, grad_u, node, 32, 9, sb, h=1e-3)
         assert g[node] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(g).max())
+
+
+def test_full_size_adjoints_match_gpu_crn_differences(wos, orc):
+    """The inverse workload at its full size (4096 sensors x 1024 walks, the benchmark's
+    sensors, grad_u = 1): both replay gradients in FP64 at sampled grid nodes against central
+    differences of FP64 forward solves on the same walks (common random numbers: given
+    sigma_bar the paths do not move, so the quotient has no Monte Carlo noise)."""
+    sig, alpha = W.inverse_sigma_grid(), W.inverse_alpha_grid()
+    desc = W.inverse_problem(sig)
+    sb = orc.sigma_bar(desc, 48)[0]
+    ctx = wos.Context(0)
+    pts = torch.from_numpy(W.inverse_sensors(4096)).cuda()
+    walks, seed = 1024, 4
+    gu = torch.ones(4096, dtype=torch.float64, device="cuda")
+
+    def loss(sig_np, alpha_np):
+        prob = ctx.problem(W.inverse_problem(sig_np, alpha_np))
+        acc, _ = ctx.solve(prob, pts, walks, 1e-4, sb, seed=seed, precision="fp64")
+        mean = ctx.finalize(acc)[0]
+        prob.close()
+        return float(mean.sum())
+
+    prob = ctx.problem(desc)
+    gs = torch.zeros(sig.size, dtype=torch.float64, device="cuda")
+    ga = torch.zeros(alpha.size, dtype=torch.float64, device="cuda")
+    ctx.adjoint_sigma(prob, pts, walks, gu, gs, 1e-4, sb, seed=seed, precision="fp64")
+    ctx.adjoint_alpha(prob, pts, walks, gu, ga, 1e-4, sb, seed=seed, precision="fp64")
+    gs, ga = gs.cpu().numpy(), ga.cpu().numpy()
+    assert np.isfinite(gs).all() and np.isfinite(ga).all()
+    for grid, g, which in ((sig, gs, "sigma"), (alpha, ga, "alpha")):
+        # the nodes with the largest gradients, and one in the middle of the ranking
+        order = np.argsort(-np.abs(g))
+        for node in (int(order[0]), int(order[1]), int(order[len(order) // 4])):
+            vals, steps = [], []
+            for sgn in (+1, -1):
+                m = grid.copy().reshape(-1)
+                h = 1e-3 * max(abs(float(m[node])), 1.0)
+                m[node] += sgn * h
+                steps.append(float(m[node]))
+                m = m.reshape(grid.shape)
+                vals.append(loss(m, alpha) if which == "sigma" else loss(sig, m))
+            fd = (vals[0] - vals[1]) / (steps[0] - steps[1])
+            scale = max(abs(fd), 1e-3 * np.abs(g).max())
+            assert abs(g[node] - fd) <= 1e-5 * scale, (which, node, g[node], fd)

@@ -169,3 +169,32 @@ def test_specialised_batch_runs_the_same_walks(wos, orc, setup):
         zs.append(combined_z(mean[a:b], se[a:b], om, ose))
     ok, nout, mz = four_se_rule(np.concatenate(zs))
     assert ok, (nout, mz)
+
+
+def test_full_size_batch_sampled_points(wos, orc):
+    """The 4096-problem batch at its full size and in the benchmark's launch configuration
+    (the batch kernel specialised to the shared fields, the autotuned schedule, per-point walk
+    counts, one launch): 24 sampled points, each against the oracle's walks of its own problem
+    at the same walk count, within 4 combined standard errors."""
+    probs, pts, offs, walks = W.batch_problems(4096, seed=7)
+    ctx = wos.Context(0)
+    hp = [ctx.problem(p) for p in probs]
+    sbs = [ctx.sigma_bar(h, 64)[0] for h in hp]
+    batch = ctx.batch(hp, offs, sbs)
+    batch.specialize(("fp32",))
+    pts_t, wt = torch.from_numpy(pts).cuda(), torch.from_numpy(walks).cuda()
+    ctx.batch_autotune(batch, pts_t, wt, 1e-3, seed=1, trial_shift=4)
+    acc, st = ctx.solve_batch(batch, pts_t, wt, 1e-3, seed=0)
+    mean, var, se = (t.cpu().numpy() for t in ctx.finalize(acc))
+    s = wos.stats_dict(st)
+    assert s["walks"] == int(walks.sum()) and s["capped"] == 0 and s["nonfinite"] == 0
+    assert np.array_equal(acc[2].cpu().numpy(), walks.astype(np.int64))
+    rng = np.random.default_rng(5)
+    zs = []
+    for i in rng.choice(pts.shape[1], size=24, replace=False):
+        k = prob_of(offs, i)
+        oacc, _ = orc.solve(probs[k], pts[:, i:i + 1], int(walks[i]), seed=3, eps=1e-3, sigma_bar=sbs[k])
+        om, ov, ose = orc.finalize(oacc)
+        zs.append(combined_z(mean[i:i + 1], se[i:i + 1], om, ose))
+    ok, nout, mz = four_se_rule(np.concatenate(zs))
+    assert ok, (nout, mz)
