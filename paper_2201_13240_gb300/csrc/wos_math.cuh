@@ -937,20 +937,6 @@ struct Radial3 {
       invD = w_div(R(1), R(1) - R(2) * a * ea - e2a);
     }
   }
-  // h(x) = 1 - e^x (1 - x), series for |x| < 1/2
-  WOS_HD static R h(R x, R ex) {
-    if (w_fabs(x) < R(0.5)) {
-      const int nt = (sizeof(R) == 4) ? 9 : 20;
-      R term = x, acc = R(0);
-#pragma unroll
-      for (int m = 2; m < nt; ++m) {
-        term *= x * (R(1) / R(m));
-        acc += term * R(m - 1);
-      }
-      return acc;
-    }
-    return R(1) - ex * (R(1) - x);
-  }
   // F(rho) and dF/drho
   WOS_HD void eval(R rho, R* F, R* pdf) const {
     if (small) {
