@@ -900,71 +900,83 @@ WOS_HD R nf_free_radius(R k, R rm, R U) {
 }
 
 // ---------------------------------------------------------------------------
+// 1/n! as a compile-time constant, and sum_{k<NT} t^k / (2k + OFF)! by Horner's rule with
+// the coefficients folded in (one FMA per term).
+// ---------------------------------------------------------------------------
+template <int N>
+struct RFact {
+  static constexpr double v = RFact<N - 1>::v / N;
+};
+template <>
+struct RFact<0> {
+  static constexpr double v = 1.0;
+};
+template <typename R, int OFF, int K, int NT, bool LAST = (K + 1 >= NT)>
+struct FactPoly {
+  static WOS_HD R eval(R t) { return R(RFact<2 * K + OFF>::v) + t * FactPoly<R, OFF, K + 1, NT>::eval(t); }
+};
+template <typename R, int OFF, int K, int NT>
+struct FactPoly<R, OFF, K, NT, true> {
+  static WOS_HD R eval(R) { return R(RFact<2 * K + OFF>::v); }
+};
+
+// ---------------------------------------------------------------------------
 // Radial CDF F(rho) of y ~ G/|G|, rho = r/R, and its density, 3D.
-//   N(rho) = a^2 int_0^rho t sinh(a(1-t)) dt, F = N(rho)/N(1).
-//   a >= 1:  with h(x) = 1 - e^x (1-x),
-//            F = [h(-a rho) - e^{-2a} h(a rho)] / [1 - 2a e^{-a} - e^{-2a}]
-//   a < 1:   N/a^3 = sum_j c_j J_{2j+1}(rho), c_j = a^{2j}/(2j+1)!,
-//            J_m(rho) = [1 - v^{m+1} ((m+2) - (m+1) v)] / ((m+1)(m+2)), v = 1 - rho,
-//            so F = 1 - Q(v)/T with T = sum_j c_j/((m+1)(m+2)) and
-//            Q(v) = sum_j c_j v^{m+1} ((m+2) - (m+1) v) / ((m+1)(m+2)).
+//   N(rho) = a^2 int_0^rho s sinh(a(1-s)) ds, F = N(rho)/N(1).
+// Integrating by parts, with v = 1 - rho, y = a v, x = a rho and S(y) = sinh y - y:
+//   1 - F = [S(y) + x (cosh y - 1)] / S(a),   dF/drho = a x sinh(y) / S(a).
+// Both terms of the numerator are >= 0, so 1 - F carries the relative accuracy of its
+// parts at every a and rho.  Each part has two forms, and a select on its own argument
+// (not a branch: every lane of a warp runs the same instructions) picks one:
+//   y < 1:  Taylor series of positive terms, S(y) = y^3 P(t), cosh y - 1 = y^2 C(t),
+//           sinh y = y (1 + t P(t)), t = y^2, P(t) = sum t^k/(2k+3)!, C(t) = sum t^k/(2k+2)!
+//           (NC terms: the first one left out is below the type's rounding for t < 1);
+//   y >= 1: exponentials, everything scaled by 2e^{-a} (no overflow at any a), with
+//           e1 = e^{-x}, e2 = e^{-a(1+v)}:  2e^{-a} S(y) = e1 - e2 - 2y e^{-a},
+//           2e^{-a} (cosh y - 1) = e1 + e2 - 2e^{-a},  2e^{-a} sinh y = e1 - e2.
+// The denominator takes the same choice on a: P(a^2) for a < 1 (the a^3 common to the
+// numerator and S(a) cancels, so a -> 0 needs no care), 1 - e^{-2a} - 2a e^{-a} for a >= 1.
+// The numerator's series form is multiplied by K = 1 (a < 1) or 2e^{-a} a^3 (a >= 1) to
+// put it in the denominator's units.  At a = 0 this is the Beta(2,2) law,
+// 1 - F = v^2 (3 - 2v).
 // ---------------------------------------------------------------------------
 template <typename R>
 struct Radial3 {
   static constexpr int NC = (sizeof(R) == 4) ? 5 : 10;  // series terms
   R a;
-  int small;
-  R c[NC];  // series: c_j / ((m+1)(m+2)) with m = 2j+1
-  R invT;
-  R invD, e2a;  // closed form
+  R ea;    // e^{-a}
+  R K;     // units of the series form of the numerator
+  R invD;  // 1 / denominator
 
   WOS_HD void init(R a_) {
     a = a_;
-    small = (a < R(1));
-    if (small) {
-      R cj = R(1), T = R(0);
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        // divisors are constants of the unrolled loop: multiplies by folded reciprocals
-        c[j] = cj * (R(1) / R((2 * j + 2) * (2 * j + 3)));
-        T += c[j];
-        cj *= a * a * (R(1) / R((2 * j + 2) * (2 * j + 3)));
-      }
-      invT = w_div(R(1), T);
-    } else {
-      R ea = w_exp(-a);
-      e2a = ea * ea;
-      invD = w_div(R(1), R(1) - R(2) * a * ea - e2a);
-    }
+    ea = w_exp(-a);
+    const R a2 = a * a;
+    const bool sm = a < R(1);
+    const R dsm = FactPoly<R, 3, 0, NC>::eval(a2);
+    const R dlg = (R(1) - ea * ea) - R(2) * a * ea;
+    K = sm ? R(1) : R(2) * ea * a2 * a;
+    invD = w_div(R(1), sm ? dsm : dlg);
   }
   // F(rho) and dF/drho
   WOS_HD void eval(R rho, R* F, R* pdf) const {
-    if (small) {
-      R v = R(1) - rho;
-      R v2 = v * v;
-      R Q = R(0), dQ = R(0), vm = v;  // vm = v^m, m = 2j+1
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        R m = R(2 * j + 1);
-        Q += c[j] * vm * v * ((m + R(2)) - (m + R(1)) * v);
-        // d/dv [v^{m+1}((m+2) - (m+1) v)] = (m+1)(m+2) v^m (1 - v)
-        dQ += c[j] * (m + R(1)) * (m + R(2)) * vm * rho;
-        vm *= v2;
-      }
-      *F = R(1) - Q * invT;
-      *pdf = dQ * invT;  // dF/drho = dQ/dv / T
-      return;
-    }
-    R x = a * rho;
-    R e1 = w_exp(-x);             // e^{-a rho}
-    R e2 = w_exp(-a * (R(2) - rho));  // e^{-a(2 - rho)} = e^{-2a} e^{a rho}
-    // h(-x) = 1 - e^{-x}(1 + x) = -expm1(-x) - x e^{-x} and e^{-2a} h(x) = e^{-2a} - e2 (1 - x),
-    // without a branch on x: both differences lose about x eps of F's absolute accuracy (F is
-    // divided by D >= 1 - 2/e - e^{-2} for a >= 1), far inside the sampler's tolerance
-    R hm = -w_expm1(-x) - x * e1;
-    R hp = e2a - e2 * (R(1) - x);
-    *F = (hm - hp) * invD;
-    *pdf = a * x * (e1 - e2) * invD;
+    const R v = R(1) - rho;
+    const R y = a * v;
+    const R x = a * rho;
+    const R t = y * y;
+    const R e1 = w_exp(-x);
+    const R e2 = w_exp(-a - y);
+    const R P = FactPoly<R, 3, 0, NC>::eval(t);
+    const R C = FactPoly<R, 2, 0, NC>::eval(t);
+    const bool sm = y < R(1);
+    // series forms in units of K: S(y) + x (cosh y - 1) = a^3 v^2 (v P + rho C), and
+    // a x sinh y = a^3 rho v (1 + t P)
+    const R nsm = K * (v * v) * (v * P + rho * C);
+    const R ssm = K * (rho * v) * (R(1) + t * P);
+    const R nlg = ((e1 - e2) - R(2) * y * ea) + x * ((e1 + e2) - R(2) * ea);
+    const R slg = a * x * (e1 - e2);
+    *F = R(1) - (sm ? nsm : nlg) * invD;
+    *pdf = (sm ? ssm : slg) * invD;
   }
 };
 

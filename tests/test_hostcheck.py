@@ -69,6 +69,34 @@ def test_radial_cdf(hc, orc, dim, fp64):
         assert np.max(np.abs(P - Po)) / np.max(np.abs(Po)) < (1e-12 if fp64 else 5e-6), a
 
 
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_radial3_limits(hc, fp64):
+    """The 3D radial law's two limits, each a closed form: a -> 0 gives the Beta(2,2) law
+    F = 3 rho^2 - 2 rho^3 (density ~ rho (1 - rho)); large a gives the Gamma(2) law
+    1 - F = e^{-x} (1 + x), x = a rho, up to e^{-a} terms (density ~ rho e^{-a rho})."""
+    rho = np.concatenate([np.linspace(1e-6, 1 - 1e-6, 301), [1e-9, 1 - 1e-9]])
+    tol = 1e-14 if fp64 else 3e-7
+
+    def run(a):
+        F = np.zeros_like(rho)
+        P = np.zeros_like(rho)
+        hc.wos_hc_radial(3, fp64, C.c_double(a), rho.ctypes.data_as(DP), len(rho), F.ctypes.data_as(DP),
+                         P.ctypes.data_as(DP))
+        return F, P
+
+    for a in [0.0, 1e-30, 1e-9]:
+        F, P = run(a)
+        assert np.max(np.abs(F - (3 * rho ** 2 - 2 * rho ** 3))) < tol, a
+        assert np.max(np.abs(P - 6 * rho * (1 - rho))) < 4 * tol, a
+    for a in [150.0, 1000.0, 5000.0]:
+        F, P = run(a)
+        x = a * rho
+        assert np.all(np.isfinite(F)) and np.all(np.isfinite(P)), a
+        assert np.max(np.abs(F - (1 - np.exp(-x) * (1 + x)))) < tol, a
+        want_p = a * x * np.exp(-x)
+        assert np.max(np.abs(P - want_p)) / np.max(want_p) < 4 * tol, a
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_sampled_radius_inverts_cdf(hc, orc, dim, fp64):
