@@ -77,6 +77,18 @@ WOS_HD float w_rsqrt(float x) {
 #endif
 }
 WOS_HD double w_rsqrt(double x) { return 1.0 / sqrt(x); }
+// sqrt(x) for x >= 0 as x * rsqrt(x) on the device (two instructions against the IEEE-rounded
+// square root's longer sequence; a few ulp, where the walk's uses need ~1e-6).  x below the
+// smallest normal float is raised to it, so x = 0 gives ~1e-19 instead of 0 * inf.
+WOS_HD float w_sqrt_fast(float x) {
+#if defined(__CUDA_ARCH__)
+  x = fmaxf(x, 1.17549435e-38f);
+  return x * rsqrtf(x);
+#else
+  return sqrtf(x);
+#endif
+}
+WOS_HD double w_sqrt_fast(double x) { return sqrt(x); }
 WOS_HD float w_sin(float x) {
 #if defined(__CUDA_ARCH__)
   return __sinf(x);
@@ -373,19 +385,43 @@ WOS_HD double d_k0(double x) { return (x <= 2.0) ? d_k0_small(x) : exp(-x) * tra
 WOS_HD double d_k1(double x) { return (x <= 2.0) ? (1.0 - d_1m_xk1_small(x)) / x : exp(-x) * trap_ks(1, x); }
 
 // ---------------------------------------------------------------------------
+// 1/n! as a compile-time constant, and sum_{k<NT} t^k / (2k + OFF)! by Horner's rule with
+// the coefficients folded in (one FMA per term).
+// ---------------------------------------------------------------------------
+template <int N>
+struct RFact {
+  static constexpr double v = RFact<N - 1>::v / N;
+};
+template <>
+struct RFact<0> {
+  static constexpr double v = 1.0;
+};
+template <typename R, int OFF, int K, int NT, bool LAST = (K + 1 >= NT)>
+struct FactPoly {
+  static WOS_HD R eval(R t) { return R(RFact<2 * K + OFF>::v) + t * FactPoly<R, OFF, K + 1, NT>::eval(t); }
+};
+template <typename R, int OFF, int K, int NT>
+struct FactPoly<R, OFF, K, NT, true> {
+  static WOS_HD R eval(R) { return R(RFact<2 * K + OFF>::v); }
+};
+
+// ---------------------------------------------------------------------------
 // Green's function of Lap - sb on a ball of radius R centred at x
 // (Supplemental 1.1).  a = sqrt(sb) R.
 //   |G| = R^2 q(a) with 3D q = (1 - a/sinh a)/a^2, 2D q = (1 - 1/I0(a))/a^2,
 //   P^B = sb |G| = a^2 q(a).
 // ---------------------------------------------------------------------------
 WOS_HD float green_q3(float a) {
-  if (a < 0.5f) {  // (1 - a/sinh a)/a^2 = 1/6 - 7a^2/360 + 31a^4/15120 - 127a^6/604800
-    float t = a * a;
-    return 0.16666667f + t * (-0.019444444f + t * (0.0020502645f - t * 0.00020998677f));
-  }
-  float e = w_exp(-a);
-  float ratio = w_div(2.0f * a * e, 1.0f - e * e);  // a / sinh a
-  return w_div(1.0f - ratio, a * a);
+  // q = (1 - a/sinh a)/a^2 = S(a) / (a^2 sinh a), S(a) = sinh a - a.  a < 1: S(a) = a^3 P(a^2)
+  // and sinh a = a (1 + a^2 P(a^2)), P(t) = sum t^k/(2k+3)! (the radial CDF's series, which
+  // shares P(a^2) and e^{-a} with this); a >= 1: exponentials scaled by 2e^{-a}.  Chosen by a
+  // select, not a branch.
+  const float t = a * a;
+  const float P = FactPoly<float, 3, 0, 5>::eval(t);
+  const float e = w_exp(-a);
+  const float qs = w_div(P, 1.0f + t * P);
+  const float ql = w_div((1.0f - e * e) - 2.0f * a * e, t * (1.0f - e * e));
+  return (a < 1.0f) ? qs : ql;
 }
 WOS_HD double green_q3(double a) {
   if (a < 1.0) {  // (sinh a - a)/(a^2 sinh a) by the series of sinh a - a
@@ -900,27 +936,6 @@ WOS_HD R nf_free_radius(R k, R rm, R U) {
 }
 
 // ---------------------------------------------------------------------------
-// 1/n! as a compile-time constant, and sum_{k<NT} t^k / (2k + OFF)! by Horner's rule with
-// the coefficients folded in (one FMA per term).
-// ---------------------------------------------------------------------------
-template <int N>
-struct RFact {
-  static constexpr double v = RFact<N - 1>::v / N;
-};
-template <>
-struct RFact<0> {
-  static constexpr double v = 1.0;
-};
-template <typename R, int OFF, int K, int NT, bool LAST = (K + 1 >= NT)>
-struct FactPoly {
-  static WOS_HD R eval(R t) { return R(RFact<2 * K + OFF>::v) + t * FactPoly<R, OFF, K + 1, NT>::eval(t); }
-};
-template <typename R, int OFF, int K, int NT>
-struct FactPoly<R, OFF, K, NT, true> {
-  static WOS_HD R eval(R) { return R(RFact<2 * K + OFF>::v); }
-};
-
-// ---------------------------------------------------------------------------
 // Radial CDF F(rho) of y ~ G/|G|, rho = r/R, and its density, 3D.
 //   N(rho) = a^2 int_0^rho s sinh(a(1-s)) ds, F = N(rho)/N(1).
 // Integrating by parts, with v = 1 - rho, y = a v, x = a rho and S(y) = sinh y - y:
@@ -1267,7 +1282,8 @@ constexpr double kTabUHi = 1.0 - 2.0 / ((double)(kTabU - 1) * (double)(kTabU - 1
 
 WOS_HD double tab_u_of_t(double t) { return (t <= 0.5) ? 2.0 * t * t : 1.0 - 2.0 * (1.0 - t) * (1.0 - t); }
 WOS_HD float tab_t_of_u(float u) {
-  return (u <= 0.5f) ? w_sqrt(0.5f * u) : 1.0f - w_sqrt(0.5f * (1.0f - u));
+  const float r = w_sqrt_fast(0.5f * fminf(u, 1.0f - u));
+  return (u <= 0.5f) ? r : 1.0f - r;
 }
 
 WOS_HD float load_tab(const float* p) {

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
           w_sincospi2(to_uniform<R>(r0.x), &dz[1], &dz[0]);
         } else {
           R cz = R(1) - R(2) * to_uniform<R>(r0.x);
-          R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+          R sz = w_sqrt_fast(w_fmax(R(0), R(1) - cz * cz));
           R sp_, cp_;
           w_sincospi2(to_uniform<R>(r0.y), &sp_, &cp_);
           dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
       w_sincospi2(to_uniform<R>(r1.z), &wd[1], &wd[0]);
     } else {
       R cn = R(1) - R(2) * to_uniform<R>(r1.z);
-      R sn = w_sqrt(w_fmax(R(0), R(1) - cn * cn));
+      R sn = w_sqrt_fast(w_fmax(R(0), R(1) - cn * cn));
       R sp_, cp_;
       w_sincospi2(to_uniform<R>(r1.w), &sp_, &cp_);
       wd[0] = sn * cp_; wd[1] = sn * sp_; wd[2] = cn;

@@ -314,12 +314,12 @@ __global__ void __launch_bounds__(kWalkBlock,
       mu = u21<R>(f[0]);
       ur = u21<R>(f[1]);
       R cy = R(1) - R(2) * u21<R>(f[2]);
-      R sy = w_sqrt(w_fmax(R(0), R(1) - cy * cy));
+      R sy = w_sqrt_fast(w_fmax(R(0), R(1) - cy * cy));
       R sp_, cp_;
       w_sincospi2(u21<R>(f[3]), &sp_, &cp_);
       dy[0] = sy * cp_; dy[1] = sy * sp_; dy[2] = cy;
       R cz = R(1) - R(2) * u21<R>(f[4]);
-      R sz = w_sqrt(w_fmax(R(0), R(1) - cz * cz));
+      R sz = w_sqrt_fast(w_fmax(R(0), R(1) - cz * cz));
       w_sincospi2(u21<R>(f[5]), &sp_, &cp_);
       dz[0] = sz * cp_; dz[1] = sz * sp_; dz[2] = cz;
     }
