@@ -90,6 +90,18 @@ void wos_hc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
   out[3] = o.w;
 }
 
+// the walk kernels' form: round keys precomputed from the 64-bit seed (key[0] low word)
+void wos_hc_philox_rk(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  uint32_t rk[20];
+  wos::philox_round_keys(((uint64_t)key[1] << 32) | key[0], rk);
+  wos::U4 c = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  wos::U4 o = wos::philox4x32_10_rk(c, rk);
+  out[0] = o.x;
+  out[1] = o.y;
+  out[2] = o.z;
+  out[3] = o.w;
+}
+
 // the inverse-CDF table the library builds on the device, built here on the host
 static float g_tab[2][wos::kTabSize];
 static int g_tab_ready[2] = {0, 0};

@@ -62,6 +62,9 @@ struct WalkLaunch {
   uint32_t chunk;
   int32_t blocks_per_sm;
   int32_t regs_variant;
+  // Philox round keys of `seed`, set by the launch functions (philox_round_keys): in the
+  // kernel's parameter space each round's key is a constant operand of the XOR
+  uint32_t rk[20];
 };
 
 // adjoint launch: d(sum_p grad_u[p] mean_u[p]) / d(sigma grid nodes), added to grad_sigma

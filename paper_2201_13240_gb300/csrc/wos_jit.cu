@@ -259,8 +259,9 @@ std::string jit_source(const DevProblem<double>& P) {
     for (int i = 0; i < 16; ++i) s += (i ? ", " : "") + lit(P.dom[i]);
     s += "}\n";
   }
-  // resident blocks per SM: 3D 7 (72 registers), 2D 8 (64 registers), neither spills
-  s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 7\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
+  // resident blocks per SM: 3D 6 (80 registers; 7 blocks at 72 registers measured 0.6 %
+  // slower, 8 at 64 registers 5 % slower), 2D 8 (64 registers), neither spills
+  s += (dim == 3) ? "#define WOS_WALK_MIN_BLOCKS 6\n" : "#define WOS_WALK_MIN_BLOCKS 8\n";
   s += "#include \"wos_walk_impl.cuh\"\n#include \"wos_adjoint_impl.cuh\"\n\nnamespace wos {\n\n";
   s += "template <int DIM, typename R>\n";
   s += "__device__ __forceinline__ FieldVal<R> jit_field(const DevProblem<R>& P, int id, R x0, R x1, R x2, "

@@ -189,6 +189,33 @@ WOS_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The same generator with its ten rounds' keys given: rk[2r], rk[2r + 1] = (k0, k1) plus r
+// times the two Weyl increments, as the loop above advances them.
+WOS_HD void philox_round_keys(uint64_t seed, uint32_t rk[20]) {
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
+  for (int round = 0; round < 10; ++round) {
+    rk[2 * round] = k0;
+    rk[2 * round + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+WOS_HD U4 philox4x32_10_rk(U4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(0xD2511F53u, c.x, &hi0, &lo0);
+    mulhilo32(0xCD9E8D57u, c.z, &hi1, &lo1);
+    U4 n;
+    n.x = hi1 ^ c.y ^ rk[2 * round];
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ rk[2 * round + 1];
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
 // uniforms in (0,1): FP32 keeps the top 24 bits, FP64 all 32
 template <typename R>
 WOS_HD R to_uniform(uint32_t x);

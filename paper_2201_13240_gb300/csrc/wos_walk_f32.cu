@@ -27,6 +27,7 @@ cudaError_t launch_walks_kernel(const WalkLaunch& L, cudaKernel_t kernel, int re
   uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
   WalkLaunch arg = L;
+  philox_round_keys(arg.seed, arg.rk);
   void* args[] = {&arg};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kWalkBlock), args, smem, stream);
 }

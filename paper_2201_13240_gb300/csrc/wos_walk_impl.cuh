@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(kWalkBlock,
 
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
   const R eps = R(L.eps);
   const R s_root0 = w_sqrt(R(L.sigma_bar)), inv_sb0 = R(1) / R(L.sigma_bar);
   const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
@@ -299,7 +298,7 @@ __global__ void __launch_bounds__(kWalkBlock,
     const R dd = w_fmax(d, R(0));
     const uint32_t blk0 = WW ? (s.bid << 2) : 0u;  // branch b of a split walk: block word (b << 2) | block
 
-    U4 r0 = philox4x32_10(U4{s.p, s.w, s.k, blk0}, key0, key1);
+    U4 r0 = philox4x32_10_rk(U4{s.p, s.w, s.k, blk0}, L.rk);
     R mu, ur;
     R dy[3] = {R(0), R(0), R(0)}, dz[3] = {R(0), R(0), R(0)};
     if (DIM == 2) {
@@ -487,7 +486,7 @@ __global__ void __launch_bounds__(kWalkBlock,
         R aw = w_fabs(s.W);
         if (aw < ww_lo || aw > ww_hi) {
           // the window's own uniform: block 1, word 0 (2D) or word 2 (3D)
-          const U4 r1 = philox4x32_10(U4{s.p, s.w, s.k, blk0 | 1u}, key0, key1);
+          const U4 r1 = philox4x32_10_rk(U4{s.p, s.w, s.k, blk0 | 1u}, L.rk);
           R uww = to_uniform<R>((DIM == 3) ? r1.z : r1.x);
           if (aw < ww_lo) {  // Russian roulette: survive with |W| / lo, at weight lo
             if (uww < aw / ww_lo) s.W = (s.W < R(0)) ? -ww_lo : ww_lo;
@@ -585,7 +584,9 @@ cudaError_t launch_walks_m(const WalkLaunch& L, int num_sms, cudaStream_t stream
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kWalkBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB><<<grid, kWalkBlock, smem, stream>>>(L);
+  WalkLaunch arg = L;
+  philox_round_keys(arg.seed, arg.rk);
+  wos_walk_kernel<DIM, R, MESH, BATCHED, WW, GRAD, DRIFT, MINB><<<grid, kWalkBlock, smem, stream>>>(arg);
   return cudaGetLastError();
 }
 

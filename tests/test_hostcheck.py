@@ -123,6 +123,11 @@ def test_philox_matches_oracle(hc, orc):
         hc.wos_hc_philox(ctr.ctypes.data_as(C.POINTER(C.c_uint32)), key.ctypes.data_as(C.POINTER(C.c_uint32)),
                          out.ctypes.data_as(C.POINTER(C.c_uint32)))
         assert list(out) == orc.philox4x32_10(ctr, key)
+        # the walk kernels' form with the round keys precomputed from the seed
+        out_rk = np.zeros(4, dtype=np.uint32)
+        hc.wos_hc_philox_rk(ctr.ctypes.data_as(C.POINTER(C.c_uint32)), key.ctypes.data_as(C.POINTER(C.c_uint32)),
+                            out_rk.ctypes.data_as(C.POINTER(C.c_uint32)))
+        assert list(out_rk) == list(out)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
