@@ -54,10 +54,10 @@ RMS_TARGET = 1e-2
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one launch of the specialised walk kernel on the 64^3-point
 # workload, from the ncu capture summarised in profiles/wos_walk_spec_kernel_cube3d.md:
-# 9.52 MB read, 0 written, at 64 walks per point.  The bytes are per point (the points, the
+# 9.51 MB read, 0 written, at 64 walks per point.  The bytes are per point (the points, the
 # accumulators, the radial table); walk state stays in registers, so the 1024-walk launch
 # moves the same bytes.  Reported for 64^3 points only; re-take it whenever the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 9.518336e6
+TRAFFIC_BYTES_PER_LAUNCH = 9.506816e6
 
 
 def measure_unit_peaks(ctx):

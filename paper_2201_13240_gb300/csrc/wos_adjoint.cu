@@ -24,6 +24,7 @@ cudaError_t launch_adjoint_kernel(const AdjLaunch& L, cudaKernel_t kernel, int r
   uint64_t blocks_needed = (L.total_items + kAdjBlock - 1) / kAdjBlock;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
   AdjLaunch arg = L;
+  philox_round_keys(arg.seed, arg.rk);
   void* args[] = {&arg};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kAdjBlock), args, smem, stream);
 }

@@ -205,7 +205,6 @@ __global__ void __launch_bounds__(kAdjBlock, 4) WOS_ADJOINT_KERNEL(AdjLaunch L) 
   } while (0)
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
   const R eps = R(L.eps), s_root = w_sqrt(R(L.sigma_bar));
   const R inv_sb = R(1) / R(L.sigma_bar);
   const uint32_t max_k = (L.max_steps >= (int64_t)0xffffffffll) ? 0xffffffffu : (uint32_t)L.max_steps;
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(kAdjBlock, 4) WOS_ADJOINT_KERNEL(AdjLaunch L) 
       for (int i = 0; i < 3; ++i) xbp[i] = xb[i];
       ends = !(d >= eps) || k >= max_k;
       dd = w_fmax(d, R(0));
-      U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
+      U4 r0 = philox4x32_10_rk(U4{p, w, k, 0u}, L.rk);
       R ur;
       R dy[3] = {R(0), R(0), R(0)};
       if (DIM == 2) {
@@ -428,7 +427,9 @@ cudaError_t launch_adjoint_m(const AdjLaunch& L, int num_sms, cudaStream_t strea
   int grid = per_sm * num_sms;
   uint64_t blocks_needed = (L.total_items + kAdjBlock - 1) / kAdjBlock;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_adjoint_kernel<DIM, R, ALPHA, PASS><<<grid, kAdjBlock, smem, stream>>>(L);
+  AdjLaunch arg = L;
+  philox_round_keys(arg.seed, arg.rk);
+  wos_adjoint_kernel<DIM, R, ALPHA, PASS><<<grid, kAdjBlock, smem, stream>>>(arg);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,7 @@ struct AdjLaunch {
   const float* radial_tab;
   void* totals;                   // [total_items] walk totals in the walk's precision (pass 1 writes them)
   int pass;                       // 1: the walks' totals, 2: the replay that scatters
+  uint32_t rk[20];                // Philox round keys of `seed`, set by the launch (philox_round_keys)
 };
 
 #if !defined(__CUDACC_RTC__)

@@ -63,7 +63,6 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint32_t key0 = (uint32_t)(L.seed & 0xffffffffull), key1 = (uint32_t)(L.seed >> 32);
   const R eps = R(L.eps);
   const R sbar = R(L.sigma_bar);
   const R s_root = w_sqrt(sbar);
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
           nf_series_ball<DIM, R>(s_root * Rb, nser, ser_p, ser_ra);
           ser_n0 = nser + 12 + (int)w_fmin(s_root * Rb, R(4096));
         }
-        U4 r0 = philox4x32_10(U4{p, w, k, 0u}, key0, key1);
+        U4 r0 = philox4x32_10_rk(U4{p, w, k, 0u}, L.rk);
         R dz[3] = {R(0), R(0), R(0)};
         if (DIM == 2) {
           w_sincospi2(to_uniform<R>(r0.x), &dz[1], &dz[0]);
@@ -255,7 +254,7 @@ __global__ void __launch_bounds__(kNfBlock, (sizeof(R) == 4) ? 4 : 1) wos_nf_ker
         phase = 1;
       }
       // ---- the roulette of the ball's series ----
-      r1 = philox4x32_10(U4{p, w, k, j + 1u}, key0, key1);
+      r1 = philox4x32_10_rk(U4{p, w, k, j + 1u}, L.rk);
       pRR = w_fmin(R(1), w_fabs(T));
       bool stop = pRR < to_uniform<R>(r1.x);
       if (!stop && j >= max_j) {
@@ -383,7 +382,9 @@ cudaError_t launch_nf_m(const WalkLaunch& L, int num_sms, cudaStream_t stream) {
   uint64_t warps_needed = L.total_items / 32 + 1;
   uint64_t blocks_needed = warps_needed / (kNfBlock / 32) + 1;
   if ((uint64_t)grid > blocks_needed) grid = (int)(blocks_needed > 0 ? blocks_needed : 1);
-  wos_nf_kernel<DIM, R, MESH, SERIES><<<grid, kNfBlock, smem, stream>>>(L);
+  WalkLaunch arg = L;
+  philox_round_keys(arg.seed, arg.rk);
+  wos_nf_kernel<DIM, R, MESH, SERIES><<<grid, kNfBlock, smem, stream>>>(arg);
   return cudaGetLastError();
 }
 
