@@ -60,6 +60,11 @@ struct WalkState {
 };
 
 constexpr int kWWDepth = 8;  // most split copies a lane keeps waiting
+#if !defined(WOS_WALK_DEFER_LANES)
+#define WOS_WALK_DEFER_LANES 4
+#endif
+constexpr int kDeferLanes = WOS_WALK_DEFER_LANES;  // ended walks a warp gathers before finishing them
+static_assert(kDeferLanes >= 1 && kDeferLanes <= 32, "kDeferLanes must be 1..32");
 
 // e^{-gamma(x_0)} of point p (applied once per flush), in the walk's precision: the
 // FP32 walk's gamma carries FP32 rounding already, and an FP64 exp costs dozens of
@@ -227,31 +232,128 @@ __global__ void __launch_bounds__(kWalkBlock,
   const int ww_depth = WW ? (L.ww_depth < kWWDepth ? L.ww_depth : kWWDepth) : 0;
   const R ww_lo = R(L.ww_lo), ww_hi = R(L.ww_hi);
 
+  // a walk's end once g is added: the spatial gradient, the per-point partial sums (flushed
+  // when the lane moves to another point), the per-walk outputs and the statistics
+  auto finish_walk = [&](const DevProblem<R>& Pw, bool capped) {
+    // no FP64 arithmetic here unless a branch needs it: this block runs whenever a lane ends
+    R gv[3] = {R(0), R(0), R(0)};
+    if (GRAD) {
+      if (s.p != gg_p) {
+        gg_p = s.p;
+        R x0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x0[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)s.p])) : R(0);
+        grad_gamma_at<DIM>(Pw, x0, ggam);
+      }
+      // a walk that ends on its first step (start in the eps-shell) has no first ball
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) gv[i] = (s.k == 0) ? R(NAN) : s.acc * (s.gb[i] - ggam[i]) + s.gc[i];
+    }
+    if (accumulate && s.p != acc_p) {
+      if (acc_p != kNoPoint) {
+        double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
+        if (!GRAD) {
+          double c = (double)sh, n = (double)n_acc;
+          s1 = n * c + (double)d1;
+          s2 = n * c * c + 2.0 * c * (double)d1 + (double)d2;
+        }
+        atomicAdd(&L.sum[acc_p], s1 * e0);
+        atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
+        atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
+        if (GRAD) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            atomicAdd(&L.gsum[(int64_t)i * L.npts + acc_p], gs1[i] * e0);
+            atomicAdd(&L.gsumsq[(int64_t)i * L.npts + acc_p], gs2[i] * e0 * e0);
+            gs1[i] = 0.0;
+            gs2[i] = 0.0;
+          }
+        }
+      }
+      acc_p = s.p;
+      acc_prob = s.prob;
+      s1 = 0.0;
+      s2 = 0.0;
+      n_acc = 0;
+      sh = s.acc;
+      d1 = R(0);
+      d2 = R(0);
+    }
+    if (GRAD) {
+      const double acc_d = (double)s.acc;
+      s1 += acc_d;
+      s2 += acc_d * acc_d;
+    } else {
+      R dv = s.acc - sh;
+      d1 += dv;
+      d2 += dv * dv;
+    }
+    ++n_acc;
+    if (GRAD) {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        gs1[i] += (double)gv[i];
+        gs2[i] += (double)gv[i] * (double)gv[i];
+      }
+    }
+    if (L.uhat != nullptr) {
+      double e0 = point_factor<DIM, R>(L, Pw, s.p);
+      L.uhat[s.item] = (double)s.acc * e0;
+      L.steps_out[s.item] = WW ? (int64_t)s.steps_walk : (int64_t)s.k;
+      if (GRAD && L.ghat != nullptr) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) L.ghat[(uint64_t)i * L.total_items + s.item] = (double)gv[i] * e0;
+      }
+    }
+    if (!WW) st_steps += s.k;
+    ++st_walks;
+    if (capped) ++st_capped;
+    if (!isfinite(s.acc)) ++st_nonfinite;
+    active = false;
+  };
+  // Plain, drift and batched walks: a lane whose walk ended waits (with its closest point,
+  // gamma and capped flag) until kDeferLanes lanes of the warp have ended, or the work is
+  // exhausted; they then add g, finish their walks and claim new ones together.  The two
+  // divergent blocks (end and regeneration, run by one or two lanes) then run about once per
+  // kDeferLanes walk ends instead of in most iterations, while the waiting lanes sit out a
+  // few steps.
+  constexpr bool DEFER = !WW && !GRAD && !MESH;
+  bool pend = false, pcap = false;
+  R pgam = R(0), pxb[3] = {R(0), R(0), R(0)};
+
   for (;;) {
     // ---- regeneration: lanes without a walk claim the next items ----
     unsigned need = __ballot_sync(kFull, !active);
-    while (need != 0u && !exhausted) {
-      if (chunk_next >= chunk_end) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, (unsigned long long)chunk);
-        base = __shfl_sync(kFull, base, 0);
-        if (base >= total) {
-          exhausted = true;
-          break;
+    if (!DEFER || exhausted || __popc(need) >= kDeferLanes) {
+      if (DEFER && pend) {
+        const DevProblem<R>& Pe = BATCHED ? Pall[s.prob] : *Pshared;
+        if (!pcap) s.acc += s.W * w_exp(pgam) * g_at<DIM>(Pe, pxb);   // Alg. 1: g at the closest point
+        finish_walk(Pe, pcap);
+        pend = false;
+      }
+      while (need != 0u && !exhausted) {
+        if (chunk_next >= chunk_end) {
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(L.work_counter, (unsigned long long)chunk);
+          base = __shfl_sync(kFull, base, 0);
+          if (base >= total) {
+            exhausted = true;
+            break;
+          }
+          chunk_next = base;
+          chunk_end = (base + chunk < total) ? base + chunk : total;
         }
-        chunk_next = base;
-        chunk_end = (base + chunk < total) ? base + chunk : total;
+        unsigned nneed = __popc(need);
+        uint64_t avail = chunk_end - chunk_next;
+        unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
+        unsigned rank = __popc(need & lt_mask);
+        if (!active && rank < take) {
+          start_walk<DIM, R, BATCHED>(L, chunk_next + rank, magic, s);
+          active = true;
+        }
+        chunk_next += take;
+        need = __ballot_sync(kFull, !active);
       }
-      unsigned nneed = __popc(need);
-      uint64_t avail = chunk_end - chunk_next;
-      unsigned take = (avail < nneed) ? (unsigned)avail : nneed;
-      unsigned rank = __popc(need & lt_mask);
-      if (!active && rank < take) {
-        start_walk<DIM, R, BATCHED>(L, chunk_next + rank, magic, s);
-        active = true;
-      }
-      chunk_next += take;
-      need = __ballot_sync(kFull, !active);
     }
     if (__ballot_sync(kFull, active) == 0u) break;
     if (!active) continue;
@@ -359,8 +461,18 @@ __global__ void __launch_bounds__(kWalkBlock,
     if (ends) {
       const bool lost = WW && s.dead;
       bool capped = (d >= eps) && !lost;
-      if (!capped && !lost) s.acc += s.W * w_exp(gam) * g_at<DIM>(P, xb);   // Alg. 1: g at the closest point
       if (s.k == 0 && !(d > R(0))) ++st_outside;
+      if (DEFER) {
+        // the walk's end (g and the accumulation) waits for the loop's head
+        pend = true;
+        pcap = capped;
+        pgam = gam;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) pxb[i] = xb[i];
+        active = false;
+        continue;
+      }
+      if (!capped && !lost) s.acc += s.W * w_exp(gam) * g_at<DIM>(P, xb);   // Alg. 1: g at the closest point
       if (WW) {
         if (capped) ++st_capped;
         if (sp > 0) {  // the walk goes on with its last split copy
@@ -375,81 +487,7 @@ __global__ void __launch_bounds__(kWalkBlock,
         }
         capped = false;  // already counted per branch
       }
-      // no FP64 arithmetic here unless a branch needs it: this block runs whenever a lane ends
-      R gv[3] = {R(0), R(0), R(0)};
-      if (GRAD) {
-        if (s.p != gg_p) {
-          gg_p = s.p;
-          R x0[3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) x0[d] = (d < DIM) ? R(__ldg(&L.pts[(int64_t)d * L.npts + (int64_t)s.p])) : R(0);
-          grad_gamma_at<DIM>(P, x0, ggam);
-        }
-        // a walk that ends on its first step (start in the eps-shell) has no first ball
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) gv[i] = (s.k == 0) ? R(NAN) : s.acc * (s.gb[i] - ggam[i]) + s.gc[i];
-      }
-      if (accumulate && s.p != acc_p) {
-        if (acc_p != kNoPoint) {
-          double e0 = point_factor<DIM, R>(L, BATCHED ? Pall[acc_prob] : *Pshared, acc_p);
-          if (!GRAD) {
-            double c = (double)sh, n = (double)n_acc;
-            s1 = n * c + (double)d1;
-            s2 = n * c * c + 2.0 * c * (double)d1 + (double)d2;
-          }
-          atomicAdd(&L.sum[acc_p], s1 * e0);
-          atomicAdd(&L.sumsq[acc_p], s2 * e0 * e0);
-          atomicAdd(&L.count[acc_p], (unsigned long long)n_acc);
-          if (GRAD) {
-#pragma unroll
-            for (int i = 0; i < DIM; ++i) {
-              atomicAdd(&L.gsum[(int64_t)i * L.npts + acc_p], gs1[i] * e0);
-              atomicAdd(&L.gsumsq[(int64_t)i * L.npts + acc_p], gs2[i] * e0 * e0);
-              gs1[i] = 0.0;
-              gs2[i] = 0.0;
-            }
-          }
-        }
-        acc_p = s.p;
-        acc_prob = s.prob;
-        s1 = 0.0;
-        s2 = 0.0;
-        n_acc = 0;
-        sh = s.acc;
-        d1 = R(0);
-        d2 = R(0);
-      }
-      if (GRAD) {
-        const double acc_d = (double)s.acc;
-        s1 += acc_d;
-        s2 += acc_d * acc_d;
-      } else {
-        R dv = s.acc - sh;
-        d1 += dv;
-        d2 += dv * dv;
-      }
-      ++n_acc;
-      if (GRAD) {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          gs1[i] += (double)gv[i];
-          gs2[i] += (double)gv[i] * (double)gv[i];
-        }
-      }
-      if (L.uhat != nullptr) {
-        double e0 = point_factor<DIM, R>(L, P, s.p);
-        L.uhat[s.item] = (double)s.acc * e0;
-        L.steps_out[s.item] = WW ? (int64_t)s.steps_walk : (int64_t)s.k;
-        if (GRAD && L.ghat != nullptr) {
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) L.ghat[(uint64_t)i * L.total_items + s.item] = (double)gv[i] * e0;
-        }
-      }
-      if (!WW) st_steps += s.k;
-      ++st_walks;
-      if (capped) ++st_capped;
-      if (!isfinite(s.acc)) ++st_nonfinite;
-      active = false;
+      finish_walk(P, capped);
       continue;
     }
 
