@@ -57,7 +57,7 @@ L2_FLUSH_BYTES = 512 << 20
 # 9.51 MB read, 0 written, at 64 walks per point.  The bytes are per point (the points, the
 # accumulators, the radial table); walk state stays in registers, so the 1024-walk launch
 # moves the same bytes.  Reported for 64^3 points only; re-take it whenever the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 9.506816e6
+TRAFFIC_BYTES_PER_LAUNCH = 9.50784e6
 
 
 def measure_unit_peaks(ctx):

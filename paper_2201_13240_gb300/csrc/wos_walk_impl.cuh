@@ -151,7 +151,8 @@ __device__ __forceinline__ void start_walk(const WalkLaunch& L, uint64_t item, u
 // Compiled at run time for one problem (WOS_JIT_FIELDS) the kernel is named
 // wos_walk_spec_kernel, so that profiles tell the two apart.  WOS_WALK_MIN_BLOCKS is the
 // FP32 value kernel's resident-block target (the register cap): the generated source of a
-// 3D problem asks for seven (72 registers, no spills; measured 7% faster than five).
+// 3D problem asks for six (80 registers, no spills; five measured 7% slower than seven,
+// seven 0.6% slower than six).
 #if !defined(WOS_WALK_MIN_BLOCKS)
 #define WOS_WALK_MIN_BLOCKS 5
 #endif
